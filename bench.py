@@ -1,0 +1,366 @@
+"""Throughput of the fused multichannel filter chain on GB300.
+
+Workload (the configuration the headline metric is quoted on): 64 channels x
+2,880,000 samples (60 s at 48 kHz) of seeded pink noise through an 8th-order
+Chebyshev-I low-pass (4 sections), 4 peaking-EQ biquads and a 1025-tap
+low-pass FIR (TorchFX, arXiv 2504.08624: Sec. 3 filter chain, Sec. 4
+multichannel workloads).  One step = one pass of the whole chain over the
+whole signal.  Inputs (737 MB) exceed the 129 MB L2, so no flush is needed
+between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "channel-samples/s through filter chain (fwd) vs plain GPU; % HBM roofline"
+UNIT = "channel-samples/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--flags", type=int, default=0, help="TFX_PLAN_* bits for the timed plan")
+    ap.add_argument("--channels", type=int, default=None, help="override channel count (testing only)")
+    ap.add_argument("--samples", type=int, default=None, help="override samples per channel (testing only)")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(args):
+    from paper_2504_08624_gb300 import workloads as W
+    wl = W.multichannel_fused()
+    if args.channels:
+        wl.C = args.channels
+    if args.samples:
+        wl.N = args.samples
+    return wl
+
+
+def algorithmic(wl):
+    """Algorithmic work per channel-sample: 8 bytes (FP32 read + write, the
+    signal crosses HBM once), 10 flop per SOS section, 2L flop per L-tap FIR."""
+    S = sum(np.asarray(c).reshape(-1, 6).shape[0] for k, c in wl.stages if k == "sos")
+    L = sum(np.asarray(c).size for k, c in wl.stages if k == "fir")
+    return 8.0, 10.0 * S + 2.0 * L, S, L
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
+                "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0)), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+def n_units(stages) -> int:
+    """Fused kernels one execution launches: consecutive SOS stages merge
+    into one cascade and each FIR closes a unit (one launch per unit)."""
+    n, pending = 0, False
+    for kind, coef in stages:
+        if kind == "sos":
+            pending = pending or np.asarray(coef).size > 0
+        else:
+            n += 1
+            pending = False
+    return n + (1 if pending else 0)
+
+
+def fp32_alu_peak_tflops(sm_count: int, sm_mhz: float) -> float:
+    # 128 FP32 lanes per SM, one FMA (2 flop) per lane per clock
+    return sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def traffic_for(kernel: str, workload_name: str):
+    """DRAM bytes per launch of ``kernel`` from the committed ncu summary, or
+    None when the summary is missing or the kernel source changed since."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d[kernel][workload_name]
+        src = os.path.join(ROOT, e["source"])
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if h != e["source_sha256_16"]:
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "100"], stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.flush()
+        self.out.seek(0)
+        rows = [r.split(",") for r in self.out.read().strip().splitlines() if r.strip()]
+        self.out.close()
+        os.unlink(self.out.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [v.strip() for v in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def time_gpu(fn, steps, warmup, stream, torch, dist=None):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def cpu_oracle_rate(wl, C_sample: int, N_sample: int):
+    """Time the FP64 oracle (as it stands) on a bounded sample; returns
+    (channel-samples/s, seconds, threads)."""
+    import oracle
+    lib = oracle.load()
+    x = wl.make_signal(C_sample, N_sample)
+    t0 = time.perf_counter()
+    lib.chain(x, wl.stages)
+    dt = time.perf_counter() - t0
+    return C_sample * N_sample / dt, dt, lib.num_threads()
+
+
+def reference_arm(args, ws, rank):
+    if rank != 0:
+        return
+    wl = workload(args)
+    ncpu = os.cpu_count() or 1
+    Cs = min(wl.C, max(1, ncpu))
+    Ns = min(wl.N, 240000)
+    import oracle
+    lib = oracle.load()
+    x = wl.make_signal(Cs, Ns)
+    for _ in range(args.warmup):
+        lib.chain(x, wl.stages)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        lib.chain(x, wl.stages)
+    dt = (time.perf_counter() - t0) / max(1, args.steps)
+    rate = Cs * Ns / dt
+    sample = f"{Cs} channels x first {Ns} samples of the workload per step (FP64 oracle, OpenMP over channels)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "channels": wl.C, "samples": wl.N, "chain": "cheby1(8)+4 peaking+fir1025"},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": lib.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        reference_arm(args, ws, rank)
+        return
+
+    import torch
+    from paper_2504_08624_gb300 import api, _native as NAT
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist_mod
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+    dev = torch.device("cuda", local)
+    wl = workload(args)
+    bytes_ps, flops_ps, S, L = algorithmic(wl)
+    units = wl.C * wl.N
+
+    x_host = torch.from_numpy(wl.make_signal()).pin_memory()
+    x = x_host.to(dev)
+    y = torch.empty_like(x)
+    plan = api.Plan(wl.C, wl.N, wl.stages, flags=args.flags)
+    wsb = plan.workspace()
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.execute(x, y, wsb)
+
+    # device-resident throughput (the headline `value`)
+    sampler = ClockSampler(local)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    t_dev = time_gpu(step, args.steps, 0, stream, torch, dist)
+    clocks = sampler.stop()
+    err = plan.get_error()
+    if err != 0:
+        raise RuntimeError(f"device reported {NAT.STATUS.get(err, err)} during the timed run")
+    t_all = t_dev
+    if dist is not None:
+        tt = torch.tensor([t_dev], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_all = float(tt.item())
+    value = units * ws * args.steps / t_all
+    ms = t_all / args.steps * 1e3
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        y_host = torch.empty_like(x_host).pin_memory()
+
+        def e2e_step():
+            api.chain(x_host, wl.stages, out=y_host)
+
+        w_e2e, k_e2e = max(3, min(args.warmup, 5)), max(5, min(args.steps // 10, 30))
+        t_e2e = time_gpu(e2e_step, k_e2e, w_e2e, stream, torch, dist)
+        if dist is not None:
+            tt = torch.tensor([t_e2e], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_e2e = float(tt.item())
+        e2e = {"value": units * ws * k_e2e / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": int(x_host.numel() * 4), "d2h_bytes_per_step": int(y_host.numel() * 4),
+               "ms_per_step": t_e2e / k_e2e * 1e3, "steps": k_e2e}
+
+    # the plain sequential-per-channel GPU path on the same GB300
+    plain = None
+    if not args.no_plain:
+        def plain_step():
+            plan.execute(x, y, wsb, plain=True)
+        k_plain = 2
+        t_plain = time_gpu(plain_step, k_plain, 1, stream, torch, dist)
+        plain = {"value": units * k_plain / t_plain, "unit": UNIT, "ms_per_step": t_plain / k_plain * 1e3,
+                 "speedup": (units * args.steps / t_dev) / (units * k_plain / t_plain)}
+
+    pk = peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_count = props.multi_processor_count
+    kernel_s = t_dev / args.steps  # one fused-unit launch (plus its flag reset) per step
+    achieved_gbs = units * bytes_ps / kernel_s / 1e9
+    tensor_fir = (args.flags & NAT.TFX_PLAN_FIR_CUDA_CORES) == 0 and False  # set once the tcgen05 FIR is the path
+    if tensor_fir:
+        bound = {"bound": "tensor", "achieved": units * flops_ps / kernel_s / 1e12,
+                 "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s"}
+    else:
+        alu_peak = fp32_alu_peak_tflops(sm_count, pk["sm_max_mhz"])
+        bound = {"bound": "alu", "achieved": units * flops_ps / kernel_s / 1e12, "peak": alu_peak,
+                 "unit": "TFLOP/s", "peak_source": f"{sm_count} SMs x 128 FP32 FMA x 2 flop x {pk['sm_max_mhz']:.0f} MHz"}
+    bound["frac"] = bound["achieved"] / bound["peak"]
+    tr = traffic_for("k_unit", wl.name)
+    bound["traffic"] = tr
+    hbm = {"bound": "hbm", "achieved": achieved_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+           "frac": achieved_gbs / pk["hbm_gbs"], "peak_source": pk["source"]}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        ncpu = os.cpu_count() or 1
+        Cs = min(wl.C, ncpu)
+        rate, dt, thr = cpu_oracle_rate(wl, Cs, min(wl.N, 480000))
+        cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": f"{Cs} channels x first {min(wl.N, 480000)} samples, FP64 oracle chain, "
+                         f"{dt:.1f} s on {thr} threads"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name, "channels": wl.C, "samples": wl.N,
+                       "chain": f"cheby1 order 8 + 4 peaking (S={S}) + fir {L} taps",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                       "l2": "inputs 737 MB > 129 MB L2, no flush", "plan_flags": args.flags},
+            "roofline": bound, "roofline_hbm": hbm, "cpu_baseline": cpu, "e2e": e2e,
+            "plain_gpu": plain, "gpu_launches": int(args.steps * n_units(wl.stages)), "clocks": clocks,
+            "gpu": props.name,
+        }
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

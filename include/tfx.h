@@ -1,0 +1,170 @@
+/*
+ * tfx.h -- C ABI of libtfx: multichannel FIR / IIR filter chains on one GB300.
+ *
+ * The operation is the one TorchFX (arXiv 2504.08624) applies through its
+ * filter classes and pipe operator (Sec. 3): every channel of a
+ * [channels x samples] signal goes through an ordered chain of linear filters,
+ * each FIR filter a causal direct convolution and each IIR filter a
+ * difference equation with user-supplied coefficients (lfilter semantics),
+ * here given as a cascade of second-order sections.  Sec. 4 (Tables 2-4)
+ * benchmarks exactly these three shapes: FIR, IIR, and a chain.
+ *
+ * Definitions (zero initial state, output length N, per channel c):
+ *   SOS section, row (b0 b1 b2 a0 a1 a2):
+ *       a0*y[n] = b0*x[n] + b1*x[n-1] + b2*x[n-2] - a1*y[n-1] - a2*y[n-2]
+ *   FIR, taps h[0..L-1]:   y[n] = sum_{k=0}^{min(n,L-1)} h[k] * x[n-k]
+ *   chain: stages applied in list order, output of stage i feeds stage i+1.
+ *
+ * Data layout: x and y are FP32 device buffers, channel-major; sample n of
+ * channel c is at p[c*ld + n], ld >= N.  x == y (in place) is allowed; any
+ * other overlap of the two ranges is rejected.  No alignment is required
+ * (16-byte aligned rows take a vector fast path).
+ *
+ * Coefficients are FP64 host arrays, read during the call and not retained.
+ * The library converts them to the device representation (FP32 coefficients,
+ * FP64-computed matrix powers and Toeplitz tiles) when it builds a plan.
+ *
+ * Streams: every launch goes on the caller's stream `s` (NULL = legacy
+ * default stream).  Calls return once the work is enqueued; they never
+ * synchronise the device, print, or abort.
+ *
+ * Errors: every entry point returns a tfx_status.  Argument errors are
+ * detected before any launch (nothing is enqueued).  Errors the GPU detects
+ * (a bounded wait that ran out) are recorded in the plan's status word and
+ * returned by tfx_plan_get_error().
+ */
+#ifndef TFX_H
+#define TFX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; declared here so the header needs no CUDA headers. */
+typedef struct CUstream_st *tfx_stream;
+
+typedef enum {
+    TFX_OK = 0,
+    TFX_ERR_INVALID = -1,     /* bad pointer, size, stride, coefficient (a0 == 0) */
+    TFX_ERR_UNSTABLE = -2,    /* an SOS section has a pole with |p| >= 1 */
+    TFX_ERR_WORKSPACE = -3,   /* workspace missing or smaller than required */
+    TFX_ERR_CUDA = -4,        /* a CUDA runtime call failed */
+    TFX_ERR_TIMEOUT = -5,     /* a device-side bounded wait gave up (see tfx_plan_get_error) */
+    TFX_ERR_UNSUPPORTED = -6, /* valid request outside what this build implements */
+    TFX_ERR_NOMEM = -7        /* host or device allocation failed */
+} tfx_status;
+
+typedef enum { TFX_STAGE_FIR = 0, TFX_STAGE_SOS = 1 } tfx_stage_kind;
+
+/* One stage of a chain.  FIR: n taps at coef[0..n-1], n >= 1.
+ * SOS: n sections, row-major [n x 6] = b0 b1 b2 a0 a1 a2, n >= 0, a0 != 0,
+ * every pole strictly inside the unit circle.  Consecutive SOS stages form
+ * one cascade.  coef is a host pointer, read during the call only. */
+typedef struct {
+    int32_t kind;
+    int32_t n;
+    const double *coef;
+} tfx_stage;
+
+/* Plan flags (bitwise OR). */
+#define TFX_PLAN_DEFAULT 0u
+#define TFX_PLAN_FIR_CUDA_CORES 1u /* FIR stages on CUDA cores only (no tensor-core Toeplitz GEMM) */
+#define TFX_PLAN_UNFUSED 2u        /* one kernel per stage group; intermediates go through the workspace */
+#define TFX_PLAN_FIR_BF16_PLAIN 4u /* tensor-core FIR without the hi/lo correction (reported-only accuracy mode) */
+/* Test hook for failure detection: the first tile of channel 0 never publishes
+ * its carries, so its successor's bounded wait runs out; the execution
+ * completes (with wrong output) and tfx_plan_get_error() returns
+ * TFX_ERR_TIMEOUT.  Never set in production. */
+#define TFX_PLAN_TEST_DROP_PUBLISH 256u
+
+typedef struct tfx_plan tfx_plan;
+
+/*
+ * tfx_plan_create -- validate a chain and precompute its device constants.
+ * p      : out, receives the plan (owned by the caller; free with tfx_plan_destroy)
+ * C, N   : channels and samples per channel (C >= 0, N >= 0)
+ * ld     : row stride of x and y in elements, ld >= max(N, 1)
+ * st,nst : the stages (Sec. 3 chaining), nst >= 0; nst == 0 is the identity
+ * flags  : TFX_PLAN_* bits
+ * Allocates device memory for the plan's constants (host-synchronous).
+ * Errors: TFX_ERR_INVALID, TFX_ERR_UNSTABLE, TFX_ERR_NOMEM, TFX_ERR_CUDA.
+ */
+int tfx_plan_create(tfx_plan **p, int64_t C, int64_t N, int64_t ld,
+                    const tfx_stage *st, int32_t nst, uint32_t flags);
+
+/* Bytes of device workspace tfx_plan_execute needs (0 if none). */
+size_t tfx_plan_workspace_size(const tfx_plan *p);
+
+/*
+ * tfx_plan_execute -- run the chain: y = chain(x).  Asynchronous on s.
+ * x, y : device FP32 buffers laid out as the plan's (C, N, ld); x == y allowed
+ * ws   : device workspace of at least tfx_plan_workspace_size(p) bytes,
+ *        256-byte aligned, owned by the caller, not touched after the work
+ *        completes.  May be NULL only when the size is 0.
+ * Makes no allocation and no host synchronisation, so it can be captured in
+ * a CUDA graph.  Concurrent executions must use distinct workspaces.
+ * Errors: TFX_ERR_INVALID, TFX_ERR_WORKSPACE, TFX_ERR_CUDA.
+ */
+int tfx_plan_execute(tfx_plan *p, const float *x, float *y, void *ws,
+                     size_t ws_bytes, tfx_stream s);
+
+/*
+ * tfx_plan_execute_plain -- the same chain on the plain sequential path: one
+ * thread per channel walks each IIR stage over time, one thread per output
+ * sample sums each FIR stage, one kernel per stage.  It is the comparison
+ * baseline for the scan/fused kernels.  Same arguments and workspace.
+ */
+int tfx_plan_execute_plain(tfx_plan *p, const float *x, float *y, void *ws,
+                           size_t ws_bytes, tfx_stream s);
+
+/*
+ * tfx_plan_get_error -- status recorded by the GPU during this plan's
+ * executions (TFX_OK or TFX_ERR_TIMEOUT), then cleared.  Synchronises the
+ * device first, so it must not be called during stream capture.
+ */
+int tfx_plan_get_error(tfx_plan *p);
+
+/* Free the plan (synchronises the device).  NULL is a no-op. */
+void tfx_plan_destroy(tfx_plan *p);
+
+/*
+ * One-shot calls.  They build (or reuse from an internal cache keyed by the
+ * arguments and the stream) a plan with its own library-owned workspace, then
+ * execute it on s.  The first call for a configuration allocates and is
+ * host-synchronous; repeats allocate nothing.  Two overlapping calls with the
+ * same configuration and stream are ordered by the stream, so they are safe.
+ *
+ * tfx_fir  : one FIR stage (taps >= 1)       -- Sec. 3 FIR filters, Table 2
+ * tfx_sos  : one SOS cascade (sections >= 0) -- Sec. 3 IIR filters, Table 3
+ * tfx_chain: a chain (Sec. 3 pipe operator, Table 4).  If ws is non-NULL it
+ *            is used instead of the cached workspace (ws_bytes must be at
+ *            least tfx_chain_workspace_size()).
+ */
+int tfx_fir(const float *x, float *y, int64_t C, int64_t N, int64_t ld,
+            const double *h, int32_t taps, tfx_stream s);
+int tfx_sos(const float *x, float *y, int64_t C, int64_t N, int64_t ld,
+            const double *sos, int32_t sections, tfx_stream s);
+int tfx_chain(const float *x, float *y, int64_t C, int64_t N, int64_t ld,
+              const tfx_stage *st, int32_t nst, void *ws, size_t ws_bytes,
+              tfx_stream s);
+/* Workspace tfx_chain needs for these arguments (SIZE_MAX if invalid). */
+size_t tfx_chain_workspace_size(int64_t C, int64_t N, int64_t ld,
+                                const tfx_stage *st, int32_t nst);
+
+/* Release every cached one-shot plan (synchronises the device). */
+void tfx_cache_clear(void);
+
+/* Human-readable name of a tfx_status. */
+const char *tfx_strerror(int status);
+
+/* Library version, e.g. 0x000100 for 0.1.0. */
+int tfx_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TFX_H */

@@ -1,0 +1,127 @@
+"""ctypes binding of libtfx.so (declared in include/tfx.h).
+
+Argument marshalling only: every step of the filter path runs in the CUDA
+library.  Loading fails loudly when the library has not been built; there is
+no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libtfx.so")
+
+TFX_STAGE_FIR = 0
+TFX_STAGE_SOS = 1
+
+TFX_PLAN_DEFAULT = 0
+TFX_PLAN_FIR_CUDA_CORES = 1
+TFX_PLAN_UNFUSED = 2
+TFX_PLAN_FIR_BF16_PLAIN = 4
+TFX_PLAN_TEST_DROP_PUBLISH = 256
+
+STATUS = {
+    0: "TFX_OK", -1: "TFX_ERR_INVALID", -2: "TFX_ERR_UNSTABLE", -3: "TFX_ERR_WORKSPACE",
+    -4: "TFX_ERR_CUDA", -5: "TFX_ERR_TIMEOUT", -6: "TFX_ERR_UNSUPPORTED", -7: "TFX_ERR_NOMEM",
+}
+
+# every symbol include/tfx.h declares
+EXPORTS = [
+    "tfx_plan_create", "tfx_plan_workspace_size", "tfx_plan_execute", "tfx_plan_execute_plain",
+    "tfx_plan_get_error", "tfx_plan_destroy", "tfx_fir", "tfx_sos", "tfx_chain",
+    "tfx_chain_workspace_size", "tfx_cache_clear", "tfx_strerror", "tfx_version",
+]
+
+
+class TfxError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {STATUS.get(code, code)} ({strerror(code)})" if what else STATUS.get(code, str(code)))
+
+
+class Stage(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n", ctypes.c_int32), ("coef", ctypes.POINTER(ctypes.c_double))]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libtfx (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libtfx.so not found at {LIB_PATH}: build it first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = ctypes.CDLL(LIB_PATH)
+    i64, i32, u32, vp, sz = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_size_t
+    fp = ctypes.c_void_p
+    sp = ctypes.POINTER(Stage)
+    L.tfx_plan_create.argtypes = [ctypes.POINTER(vp), i64, i64, i64, sp, i32, u32]
+    L.tfx_plan_create.restype = ctypes.c_int
+    L.tfx_plan_workspace_size.argtypes = [vp]
+    L.tfx_plan_workspace_size.restype = sz
+    L.tfx_plan_execute.argtypes = [vp, fp, fp, vp, sz, vp]
+    L.tfx_plan_execute.restype = ctypes.c_int
+    L.tfx_plan_execute_plain.argtypes = [vp, fp, fp, vp, sz, vp]
+    L.tfx_plan_execute_plain.restype = ctypes.c_int
+    L.tfx_plan_get_error.argtypes = [vp]
+    L.tfx_plan_get_error.restype = ctypes.c_int
+    L.tfx_plan_destroy.argtypes = [vp]
+    L.tfx_plan_destroy.restype = None
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.tfx_fir.argtypes = [fp, fp, i64, i64, i64, dp, i32, vp]
+    L.tfx_fir.restype = ctypes.c_int
+    L.tfx_sos.argtypes = [fp, fp, i64, i64, i64, dp, i32, vp]
+    L.tfx_sos.restype = ctypes.c_int
+    L.tfx_chain.argtypes = [fp, fp, i64, i64, i64, sp, i32, vp, sz, vp]
+    L.tfx_chain.restype = ctypes.c_int
+    L.tfx_chain_workspace_size.argtypes = [i64, i64, i64, sp, i32]
+    L.tfx_chain_workspace_size.restype = sz
+    L.tfx_cache_clear.argtypes = []
+    L.tfx_cache_clear.restype = None
+    L.tfx_strerror.argtypes = [ctypes.c_int]
+    L.tfx_strerror.restype = ctypes.c_char_p
+    L.tfx_version.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def strerror(code: int) -> str:
+    try:
+        return lib().tfx_strerror(int(code)).decode()
+    except Exception:  # pragma: no cover
+        return STATUS.get(code, str(code))
+
+
+def check(rc: int, what: str) -> None:
+    if rc != 0:
+        raise TfxError(rc, what)
+
+
+class StageList:
+    """Stage array in the C layout; keeps the FP64 coefficient buffers alive."""
+
+    def __init__(self, stages):
+        self._keep = []
+        items = []
+        for kind, coef in stages:
+            if kind == "fir":
+                c = np.ascontiguousarray(np.asarray(coef, dtype=np.float64).ravel())
+                items.append((TFX_STAGE_FIR, c.size, c))
+            elif kind == "sos":
+                c = np.ascontiguousarray(np.asarray(coef, dtype=np.float64).reshape(-1, 6))
+                items.append((TFX_STAGE_SOS, c.shape[0], c))
+            else:
+                raise ValueError(f"unknown stage kind {kind!r} (use 'fir' or 'sos')")
+            self._keep.append(c)
+        self.n = len(items)
+        self.arr = (Stage * max(1, self.n))()
+        for i, (k, n, c) in enumerate(items):
+            self.arr[i].kind = k
+            self.arr[i].n = n
+            self.arr[i].coef = c.ctypes.data_as(ctypes.POINTER(ctypes.c_double))

@@ -1,0 +1,318 @@
+// Fused filter unit: an SOS cascade (chunked parallel scan over time) followed
+// by an FIR (sliding window over shared memory), one HBM read of x and one
+// HBM write of y per tile.
+//
+// Operation (TorchFX Sec. 3, lfilter semantics and pipe chaining): per channel,
+// each second-order section applies y[n] = b0 x[n] + b1 x[n-1] + b2 x[n-2]
+// - a1 y[n-1] - a2 y[n-2] (a0-normalised) with zero initial state, sections in
+// order, then y[n] = sum_k h[k] x[n-k].
+//
+// Decomposition.  A tile is TILE = NT*T samples of one channel; thread i owns
+// samples [i*T, (i+1)*T).  Each section runs in transposed direct form II with
+// state W = (w1, w2); over a chunk of T samples the state evolves as
+// W_end = A W_start + e, where A = M^T (M the 2x2 one-sample transfer matrix)
+// and e is the chunk's zero-state end state.  Per section:
+//   1. zero-state pass over the thread's chunk (outputs y_zs, end state e);
+//   2. warp Kogge-Stone scan of (A, e) using the powers A^1..A^16, then a
+//      Horner combination of the 8 warp totals with A^32;
+//   3. decoupled look-back across tiles of the same channel (tile transfer
+//      A^NT) for the tile's incoming state, with bounded waits;
+//   4. fix-up: y = y_zs + the homogeneous response from the true chunk start
+//      state, y_h[t] = -a1 y_h[t-1] - a2 y_h[t-2].
+// The FIR then reads the cascade output of this tile plus the last L-1
+// cascade outputs of the preceding tile(s), which each tile publishes to
+// scratch before the successor needs them (so x == y is safe).
+#include "tfx_common.cuh"
+
+namespace tfx {
+
+__device__ __forceinline__ int wphys(int p) { return p + (p >> 5); }
+
+template <int T>
+__device__ __forceinline__ void load_chunk(const float* row, int64_t n0, int64_t N, float (&u)[T]) {
+    const float* p = row + n0;
+    if (n0 + T <= N && ((reinterpret_cast<uintptr_t>(p) & 15) == 0)) {
+        const float4* p4 = reinterpret_cast<const float4*>(p);
+#pragma unroll
+        for (int i = 0; i < T / 4; ++i) {
+            float4 v = p4[i];
+            u[4 * i + 0] = v.x;
+            u[4 * i + 1] = v.y;
+            u[4 * i + 2] = v.z;
+            u[4 * i + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < T; ++i) u[i] = (n0 + i < N) ? p[i] : 0.f;
+    }
+}
+
+template <int T>
+__device__ __forceinline__ void store_chunk(float* row, int64_t n0, int64_t N, const float (&u)[T],
+                                            float g) {
+    float* p = row + n0;
+    if (n0 + T <= N && ((reinterpret_cast<uintptr_t>(p) & 15) == 0)) {
+        float4* p4 = reinterpret_cast<float4*>(p);
+#pragma unroll
+        for (int i = 0; i < T / 4; ++i)
+            p4[i] = make_float4(u[4 * i] * g, u[4 * i + 1] * g, u[4 * i + 2] * g, u[4 * i + 3] * g);
+    } else {
+#pragma unroll
+        for (int i = 0; i < T; ++i)
+            if (n0 + i < N) p[i] = u[i] * g;
+    }
+}
+
+// acc[r] = sum_{k < nkb*R} taps[k] * win[base + r - k], base = FIR_PAD + H + o0.
+// Register window xw[m] = win[base_kb - R + m]; taps walked R at a time.
+__device__ __forceinline__ void fir_block(const float* __restrict__ win, const float* __restrict__ taps,
+                                          int nkb, int base, float (&acc)[FIR_R]) {
+    constexpr int R = FIR_R;
+    float xw[2 * R];
+#pragma unroll
+    for (int m = 0; m < 2 * R; ++m) xw[m] = win[wphys(base - R + m)];
+    for (int kb = 0; kb < nkb; ++kb) {
+        const float4* h4 = reinterpret_cast<const float4*>(taps + kb * R);
+#pragma unroll
+        for (int q = 0; q < R / 4; ++q) {
+            const float4 hv = h4[q];
+            const float hk[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int kk = 4 * q + j;
+#pragma unroll
+                for (int r = 0; r < R; ++r) acc[r] = fmaf(hk[j], xw[R + r - kk], acc[r]);
+            }
+        }
+        const int nb = base - (kb + 1) * R;  // next block's base
+#pragma unroll
+        for (int m = 2 * R - 1; m >= R; --m) xw[m] = xw[m - R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) xw[m] = win[wphys(nb - R + m)];
+    }
+}
+
+template <bool HAS_FIR>
+__global__ void __launch_bounds__(NT, 2) k_unit(UnitArgs a) {
+    constexpr int T = T_CHUNK;
+    extern __shared__ float4 smem_f4[];
+    float* smem = reinterpret_cast<float*>(smem_f4);
+    __shared__ unsigned s_tile;
+    __shared__ float2 s_tot[NWARP];
+    __shared__ float2 s_win;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(a.sc.ticket, 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t c = tile % a.C;
+    const int64_t tt = tile / a.C;
+    const int64_t t0 = tt * TILE;
+    const int S = a.k.S;
+    unsigned* fl = a.sc.flags + tile * (S + 1);
+    float4* vl = a.sc.vals + tile * S;
+
+    float u[T];
+    load_chunk<T>(a.x + c * a.ldx, t0 + (int64_t)tid * T, a.N, u);
+
+    for (int s = 0; s < S; ++s) {
+        const float* cf = a.k.coef + 8 * s;
+        const float b0 = cf[0], b1 = cf[1], b2 = cf[2], a1 = cf[3], a2 = cf[4];
+        const float4* P = a.k.pw + (size_t)s * (NT + 1);
+
+        // 1. zero-state pass (transposed direct form II)
+        float w1 = 0.f, w2 = 0.f;
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const float yv = fmaf(b0, u[t], w1);
+            w1 = fmaf(b1, u[t], fmaf(-a1, yv, w2));
+            w2 = fmaf(b2, u[t], -a2 * yv);
+            u[t] = yv;
+        }
+
+        // 2. warp inclusive scan: v_l = sum_{m<=l} A^m e_{l-m}
+        float2 v = make_float2(w1, w2);
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const float ox = __shfl_up_sync(0xffffffffu, v.x, d);
+            const float oy = __shfl_up_sync(0xffffffffu, v.y, d);
+            if (lane >= d) {
+                const float2 t2 = mv2(P[d], make_float2(ox, oy));
+                v.x += t2.x;
+                v.y += t2.y;
+            }
+        }
+        if (lane == 31) s_tot[warp] = v;
+        const float px = __shfl_up_sync(0xffffffffu, v.x, 1);
+        const float py = __shfl_up_sync(0xffffffffu, v.y, 1);
+        __syncthreads();
+
+        const float4 A32 = P[32];
+        float2 X = make_float2(0.f, 0.f);  // state entering this warp (zero tile-in)
+        for (int w = 0; w < warp; ++w) {
+            X = mv2(A32, X);
+            X.x += s_tot[w].x;
+            X.y += s_tot[w].y;
+        }
+        float2 st = (lane > 0) ? make_float2(px, py) : make_float2(0.f, 0.f);
+        {
+            const float2 t2 = mv2(P[lane], X);
+            st.x += t2.x;
+            st.y += t2.y;
+        }
+
+        // 3. tile aggregate and decoupled look-back (one thread)
+        if (tid == 0) {
+            float2 agg = make_float2(0.f, 0.f);
+            for (int w = 0; w < NWARP; ++w) {
+                agg = mv2(A32, agg);
+                agg.x += s_tot[w].x;
+                agg.y += s_tot[w].y;
+            }
+            float2 win = make_float2(0.f, 0.f);
+            const bool pub = tile != a.drop_tile;
+            if (tt == 0) {
+                vl[s] = make_float4(agg.x, agg.y, agg.x, agg.y);
+                __threadfence();
+                if (pub) st_release_u32(&fl[s], 2u);
+            } else {
+                vl[s] = make_float4(agg.x, agg.y, 0.f, 0.f);
+                __threadfence();
+                if (pub) st_release_u32(&fl[s], 1u);
+                const float4 AT = P[NT];
+                float4 Mp = make_float4(1.f, 0.f, 0.f, 1.f);
+                int64_t j = tile - a.C;
+                for (;;) {
+                    const unsigned f = wait_flag(a.sc.flags + j * (S + 1) + s, 1u, a.status);
+                    if (f == 0u) break;  // gave up: status word records the timeout
+                    const float4 pv = ld_relaxed_f4(a.sc.vals + j * S + s);
+                    if (f >= 2u) {
+                        const float2 t2 = mv2(Mp, make_float2(pv.z, pv.w));
+                        win.x += t2.x;
+                        win.y += t2.y;
+                        break;
+                    }
+                    const float2 t2 = mv2(Mp, make_float2(pv.x, pv.y));
+                    win.x += t2.x;
+                    win.y += t2.y;
+                    Mp = mm2(Mp, AT);
+                    j -= a.C;
+                }
+                float2 incl = mv2(AT, win);
+                incl.x += agg.x;
+                incl.y += agg.y;
+                vl[s] = make_float4(agg.x, agg.y, incl.x, incl.y);
+                __threadfence();
+                if (pub) st_release_u32(&fl[s], 2u);
+            }
+            s_win = win;
+        }
+        __syncthreads();
+        {
+            const float2 t2 = mv2(P[tid], s_win);
+            st.x += t2.x;
+            st.y += t2.y;
+        }
+
+        // 4. fix-up with the homogeneous response from the true start state
+        float p = st.x;
+        float q = fmaf(-a1, st.x, st.y);
+        u[0] += p;
+        u[1] += q;
+#pragma unroll
+        for (int t = 2; t < T; ++t) {
+            const float r = fmaf(-a1, q, -a2 * p);
+            u[t] += r;
+            p = q;
+            q = r;
+        }
+    }
+
+    if constexpr (!HAS_FIR) {
+        store_chunk<T>(a.y + c * a.ldy, t0 + (int64_t)tid * T, a.N, u, a.k.gain);
+    } else {
+        const int H = a.k.H;
+        const int nkb = a.k.nkb;
+        const int win_len = wphys(FIR_PAD + H + TILE - 1) + 1;
+        float* win = smem;
+        float* taps = smem + ((win_len + 3) & ~3);
+
+        const int base = FIR_PAD + H + tid * T;
+#pragma unroll
+        for (int t = 0; t < T; ++t) win[wphys(base + t)] = u[t];
+        for (int i = tid; i < FIR_PAD; i += NT) win[wphys(i)] = 0.f;
+        for (int i = tid; i < nkb * FIR_R; i += NT) taps[i] = a.k.taps[i];
+        __syncthreads();
+
+        // publish this tile's last tail_len FIR-input samples for the successor
+        const int tl = a.sc.tail_len;
+        if (tt + 1 < a.ntt) {
+            float* dst = a.sc.tails + tile * (int64_t)tl;
+            for (int i = tid; i < tl; i += NT) dst[i] = win[wphys(FIR_PAD + H + TILE - tl + i)];
+            __threadfence();
+            __syncthreads();
+            if (tid == 0 && tile != a.drop_tile) st_release_u32(&fl[S], 1u);
+        }
+
+        // halo: samples [t0 - H, t0) at window positions [FIR_PAD, FIR_PAD + H)
+        int remaining = H;
+        for (int qb = 1; remaining > 0; ++qb) {
+            if (tt - qb < 0) {
+                for (int i = tid; i < remaining; i += NT) win[wphys(FIR_PAD + H - ((qb - 1) * TILE + 1 + i))] = 0.f;
+                break;
+            }
+            const int64_t jt = tile - (int64_t)qb * a.C;
+            if (tid == 0) wait_flag(a.sc.flags + jt * (S + 1) + S, 1u, a.status);
+            __syncthreads();
+            const float* src = a.sc.tails + jt * (int64_t)tl;
+            const int nq = remaining < tl ? remaining : tl;
+            for (int i = tid; i < nq; i += NT) {
+                const int m = (qb - 1) * TILE + 1 + i;  // samples back from t0
+                win[wphys(FIR_PAD + H - m)] = __ldcg(src + (tl - 1 - i));
+            }
+            remaining -= nq;
+        }
+        __syncthreads();
+
+        float* yrow = a.y + c * a.ldy;
+        for (int o0 = tid * FIR_R; o0 < TILE; o0 += NT * FIR_R) {
+            const int64_t n0 = t0 + o0;
+            if (n0 >= a.N) break;
+            float acc[FIR_R];
+#pragma unroll
+            for (int r = 0; r < FIR_R; ++r) acc[r] = 0.f;
+            fir_block(win, taps, nkb, FIR_PAD + H + o0, acc);
+            store_chunk<FIR_R>(yrow, n0, a.N, acc, 1.0f);
+        }
+    }
+}
+
+size_t unit_smem_bytes(const UnitConst& k) {
+    if (k.L <= 0) return 0;
+    const int win_len = (FIR_PAD + k.H + TILE - 1) + ((FIR_PAD + k.H + TILE - 1) >> 5) + 1;
+    return (size_t)(((win_len + 3) & ~3) + k.nkb * FIR_R) * sizeof(float);
+}
+
+// Raise the kernel's dynamic shared-memory limit once, at plan time, so that
+// launches (possibly under stream capture) make no attribute calls.
+cudaError_t prepare_unit(const UnitConst& k) {
+    static int set_bytes = 48 * 1024;
+    const size_t smem = unit_smem_bytes(k);
+    if (k.L <= 0 || (int)smem <= set_bytes) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_unit<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) set_bytes = (int)smem;
+    return e;
+}
+
+cudaError_t launch_unit(const UnitArgs& a, cudaStream_t s) {
+    const int64_t tiles = a.C * a.ntt;
+    if (tiles <= 0) return cudaSuccess;
+    if (a.k.L > 0) {
+        k_unit<true><<<(unsigned)tiles, NT, unit_smem_bytes(a.k), s>>>(a);
+    } else {
+        k_unit<false><<<(unsigned)tiles, NT, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace tfx

@@ -1,0 +1,536 @@
+// Host side of libtfx: argument validation, plan building (FP64 precompute of
+// device constants), workspace layout, launches, the one-shot plan cache and
+// the C-ABI entry points declared in include/tfx.h.
+#include <cmath>
+#include <cstring>
+#include <list>
+#include <mutex>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "tfx_common.cuh"
+
+using namespace tfx;
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+inline size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+struct HostUnit {
+    int S = 0;                  // sections
+    int L = 0;                  // FIR taps (0 = none)
+    std::vector<double> sec;    // [S][5] a0-normalised b0 b1 b2 a1 a2
+    std::vector<double> taps;   // [L]
+    // device constants (offsets into the plan's constant blob)
+    size_t off_coef = 0, off_pw = 0, off_taps = 0;
+    int nkb = 0;
+    int64_t ntt = 0;            // time tiles per channel
+    int tail_len = 0;
+    // scratch sizes (bytes)
+    size_t flags_bytes = 0, vals_bytes = 0, tails_bytes = 0;
+};
+
+struct PlainStage {
+    int kind;  // TFX_STAGE_FIR / TFX_STAGE_SOS
+    int n;
+    size_t off;  // FP32 coefficients in the constant blob (SOS: [n][8]; FIR: [n])
+};
+
+}  // namespace
+
+struct tfx_plan {
+    int64_t C = 0, N = 0, ld = 0;
+    uint32_t flags = 0;
+    std::vector<HostUnit> units;
+    std::vector<PlainStage> plain;
+    char* dconst = nullptr;
+    int* dstatus = nullptr;
+    // workspace layout
+    size_t scratch_hdr = 0;    // ticket + flags (memset per unit execution)
+    size_t scratch_bytes = 0;  // header + vals + tails
+    size_t buf_bytes = 0;      // one intermediate [C x N] buffer
+    size_t ws_fused = 0, ws_plain = 0;
+};
+
+namespace {
+
+bool finite_all(const double* p, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+// Normalise one row by a0 and check that both poles lie strictly inside the
+// unit circle: z^2 + al1 z + al2 has its roots in |z| < 1 iff |al2| < 1 and
+// |al1| < 1 + al2.
+int normalise_row(const double* r, double* out) {
+    if (r[3] == 0.0) return TFX_ERR_INVALID;
+    const double inv = 1.0 / r[3];
+    const double b0 = r[0] * inv, b1 = r[1] * inv, b2 = r[2] * inv, al1 = r[4] * inv, al2 = r[5] * inv;
+    if (!(std::fabs(al2) < 1.0 && std::fabs(al1) < 1.0 + al2)) return TFX_ERR_UNSTABLE;
+    out[0] = b0;
+    out[1] = b1;
+    out[2] = b2;
+    out[3] = al1;
+    out[4] = al2;
+    return TFX_OK;
+}
+
+struct M2 {
+    double a, b, c, d;
+};
+inline M2 mul(const M2& x, const M2& y) {
+    return {x.a * y.a + x.b * y.c, x.a * y.b + x.b * y.d, x.c * y.a + x.d * y.c, x.c * y.b + x.d * y.d};
+}
+
+int validate_stages(const tfx_stage* st, int32_t nst) {
+    if (nst < 0 || (nst > 0 && !st)) return TFX_ERR_INVALID;
+    for (int32_t i = 0; i < nst; ++i) {
+        const tfx_stage& s = st[i];
+        if (s.kind == TFX_STAGE_FIR) {
+            if (s.n < 1 || !s.coef || !finite_all(s.coef, (size_t)s.n)) return TFX_ERR_INVALID;
+        } else if (s.kind == TFX_STAGE_SOS) {
+            if (s.n < 0 || (s.n > 0 && !s.coef)) return TFX_ERR_INVALID;
+            if (s.n > 0 && !finite_all(s.coef, (size_t)s.n * 6)) return TFX_ERR_INVALID;
+            double tmp[5];
+            for (int r = 0; r < s.n; ++r) {
+                int e = normalise_row(s.coef + 6 * r, tmp);
+                if (e != TFX_OK) return e;
+            }
+        } else {
+            return TFX_ERR_INVALID;
+        }
+    }
+    return TFX_OK;
+}
+
+int check_dims(int64_t C, int64_t N, int64_t ld) {
+    if (C < 0 || N < 0) return TFX_ERR_INVALID;
+    if (ld < (N > 1 ? N : 1)) return TFX_ERR_INVALID;
+    if (C > 0 && N > 0) {
+        // tile counts and indices stay within 32-bit grid / ticket ranges
+        const int64_t ntt = (N + TILE - 1) / TILE;
+        if (C > (int64_t)INT32_MAX / ntt) return TFX_ERR_UNSUPPORTED;
+        if (C > INT64_MAX / ld) return TFX_ERR_INVALID;
+    }
+    return TFX_OK;
+}
+
+int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
+    // group stages: consecutive SOS stages merge into one cascade; an FIR
+    // closes the current unit.
+    HostUnit cur;
+    auto flush = [&]() {
+        if (cur.S > 0 || cur.L > 0) p->units.push_back(cur);
+        cur = HostUnit();
+    };
+    const bool unfused = (p->flags & TFX_PLAN_UNFUSED) != 0;
+    for (int32_t i = 0; i < nst; ++i) {
+        const tfx_stage& s = st[i];
+        if (s.kind == TFX_STAGE_SOS) {
+            if (cur.L > 0) flush();
+            for (int r = 0; r < s.n; ++r) {
+                double row[5];
+                normalise_row(s.coef + 6 * r, row);
+                cur.sec.insert(cur.sec.end(), row, row + 5);
+                cur.S++;
+            }
+        } else {
+            if (unfused && cur.S > 0) flush();
+            if (cur.L > 0) flush();
+            cur.L = s.n;
+            cur.taps.assign(s.coef, s.coef + s.n);
+            flush();
+        }
+    }
+    flush();
+
+    // constant blob layout
+    size_t off = 0;
+    for (HostUnit& u : p->units) {
+        u.off_coef = off;
+        off = align_up(off + (size_t)u.S * 8 * sizeof(float));
+        u.off_pw = off;
+        off = align_up(off + (size_t)u.S * (NT + 1) * sizeof(float4));
+        u.nkb = u.L > 0 ? (u.L + FIR_R - 1) / FIR_R : 0;
+        u.off_taps = off;
+        off = align_up(off + (size_t)u.nkb * FIR_R * sizeof(float));
+    }
+    for (int32_t i = 0; i < nst; ++i) {
+        PlainStage ps{st[i].kind, st[i].n, off};
+        p->plain.push_back(ps);
+        off = align_up(off + (size_t)(st[i].kind == TFX_STAGE_SOS ? st[i].n * 8 : st[i].n) * sizeof(float));
+    }
+    const size_t const_bytes = off;
+
+    std::vector<char> host(const_bytes > 0 ? const_bytes : 1, 0);
+    for (HostUnit& u : p->units) {
+        float* coef = reinterpret_cast<float*>(host.data() + u.off_coef);
+        float4* pw = reinterpret_cast<float4*>(host.data() + u.off_pw);
+        for (int s = 0; s < u.S; ++s) {
+            const double* r = &u.sec[5 * s];
+            for (int j = 0; j < 5; ++j) coef[8 * s + j] = (float)r[j];
+            // one-sample transfer of the TDF-II state (w1, w2) with zero input
+            const M2 m = {-r[3], 1.0, -r[4], 0.0};
+            M2 a = {1, 0, 0, 1};
+            for (int t = 0; t < T_CHUNK; ++t) a = mul(a, m);  // chunk transfer A = M^T
+            M2 pk = {1, 0, 0, 1};
+            for (int k = 0; k <= NT; ++k) {
+                pw[(size_t)s * (NT + 1) + k] = make_float4((float)pk.a, (float)pk.b, (float)pk.c, (float)pk.d);
+                pk = mul(pk, a);
+            }
+        }
+        float* taps = reinterpret_cast<float*>(host.data() + u.off_taps);
+        for (int k = 0; k < u.L; ++k) taps[k] = (float)u.taps[k];
+    }
+    for (int32_t i = 0; i < nst; ++i) {
+        float* d = reinterpret_cast<float*>(host.data() + p->plain[i].off);
+        if (st[i].kind == TFX_STAGE_SOS) {
+            for (int r = 0; r < st[i].n; ++r) {
+                double row[5];
+                normalise_row(st[i].coef + 6 * r, row);
+                for (int j = 0; j < 5; ++j) d[8 * r + j] = (float)row[j];
+            }
+        } else {
+            for (int k = 0; k < st[i].n; ++k) d[k] = (float)st[i].coef[k];
+        }
+    }
+
+    if (upload) {
+        if (cudaMalloc(&p->dconst, host.size()) != cudaSuccess) return TFX_ERR_NOMEM;
+        if (cudaMemcpy(p->dconst, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return TFX_ERR_CUDA;
+        if (cudaMalloc(&p->dstatus, sizeof(int)) != cudaSuccess) return TFX_ERR_NOMEM;
+        if (cudaMemset(p->dstatus, 0, sizeof(int)) != cudaSuccess) return TFX_ERR_CUDA;
+        for (HostUnit& u : p->units) {
+            UnitConst k{};
+            k.S = u.S;
+            k.L = u.L;
+            k.H = u.L > 0 ? u.L - 1 : 0;
+            k.nkb = u.nkb;
+            if (prepare_unit(k) != cudaSuccess) return TFX_ERR_UNSUPPORTED;
+        }
+    }
+
+    // workspace layout
+    const int64_t ntt = p->N > 0 ? (p->N + TILE - 1) / TILE : 0;
+    size_t hdr = 0, vals = 0, tails = 0;
+    for (HostUnit& u : p->units) {
+        u.ntt = ntt;
+        const int H = u.L > 0 ? u.L - 1 : 0;
+        u.tail_len = u.L > 0 ? (H < TILE ? H : TILE) : 0;
+        const int64_t tiles = p->C * ntt;
+        u.flags_bytes = (size_t)tiles * (u.S + 1) * sizeof(unsigned);
+        u.vals_bytes = (size_t)tiles * u.S * sizeof(float4);
+        u.tails_bytes = (size_t)tiles * u.tail_len * sizeof(float);
+        hdr = std::max(hdr, align_up(ALIGN + u.flags_bytes));
+        vals = std::max(vals, align_up(u.vals_bytes));
+        tails = std::max(tails, align_up(u.tails_bytes));
+    }
+    p->scratch_hdr = hdr;
+    p->scratch_bytes = hdr + vals + tails;
+    p->buf_bytes = align_up((size_t)p->C * (size_t)p->N * sizeof(float));
+    const size_t nbuf = p->units.size() > 2 ? 2 : (p->units.size() == 2 ? 1 : 0);
+    p->ws_fused = p->scratch_bytes + nbuf * p->buf_bytes;
+    p->ws_plain = (nst > 0 ? 2 : 0) * p->buf_bytes;
+    return TFX_OK;
+}
+
+bool ranges_overlap_not_equal(const float* x, const float* y, int64_t C, int64_t N, int64_t ld) {
+    if (x == y || C == 0 || N == 0) return false;
+    const char* xb = reinterpret_cast<const char*>(x);
+    const char* yb = reinterpret_cast<const char*>(y);
+    const size_t span = ((size_t)(C - 1) * (size_t)ld + (size_t)N) * sizeof(float);
+    return xb < yb + span && yb < xb + span;
+}
+
+int exec_fused(tfx_plan* p, const float* x, float* y, void* ws, cudaStream_t s) {
+    char* w = static_cast<char*>(ws);
+    const int nu = (int)p->units.size();
+    if (nu == 0) {
+        if (x != y) {
+            if (launch_copy_rows(x, y, p->C, p->N, p->ld, p->ld, s) != cudaSuccess) return TFX_ERR_CUDA;
+        }
+        return TFX_OK;
+    }
+    char* scratch = w;
+    float* buf[2] = {reinterpret_cast<float*>(w + p->scratch_bytes),
+                     reinterpret_cast<float*>(w + p->scratch_bytes + p->buf_bytes)};
+    for (int i = 0; i < nu; ++i) {
+        const HostUnit& u = p->units[i];
+        UnitArgs a;
+        a.x = i == 0 ? x : buf[(i - 1) & 1];
+        a.ldx = i == 0 ? p->ld : p->N;
+        a.y = i == nu - 1 ? y : buf[i & 1];
+        a.ldy = i == nu - 1 ? p->ld : p->N;
+        a.C = p->C;
+        a.N = p->N;
+        a.ntt = u.ntt;
+        a.k.S = u.S;
+        a.k.L = u.L;
+        a.k.H = u.L > 0 ? u.L - 1 : 0;
+        a.k.nkb = u.nkb;
+        a.k.gain = 1.0f;
+        a.k.coef = reinterpret_cast<const float*>(p->dconst + u.off_coef);
+        a.k.pw = reinterpret_cast<const float4*>(p->dconst + u.off_pw);
+        a.k.taps = reinterpret_cast<const float*>(p->dconst + u.off_taps);
+        a.sc.ticket = reinterpret_cast<unsigned*>(scratch);
+        a.sc.flags = reinterpret_cast<unsigned*>(scratch + ALIGN);
+        a.sc.vals = reinterpret_cast<float4*>(scratch + p->scratch_hdr);
+        a.sc.tails = reinterpret_cast<float*>(scratch + p->scratch_hdr + align_up(u.vals_bytes));
+        a.sc.tail_len = u.tail_len;
+        a.status = p->dstatus;
+        a.drop_tile = (p->flags & TFX_PLAN_TEST_DROP_PUBLISH) ? 0 : -1;
+        if (cudaMemsetAsync(scratch, 0, ALIGN + u.flags_bytes, s) != cudaSuccess) return TFX_ERR_CUDA;
+        if (launch_unit(a, s) != cudaSuccess) return TFX_ERR_CUDA;
+    }
+    return TFX_OK;
+}
+
+int exec_plain(tfx_plan* p, const float* x, float* y, void* ws, cudaStream_t s) {
+    const int ns = (int)p->plain.size();
+    for (const PlainStage& st : p->plain)
+        if (st.kind == TFX_STAGE_SOS && st.n > 64) return TFX_ERR_UNSUPPORTED;
+    if (ns == 0) {
+        if (x != y && launch_copy_rows(x, y, p->C, p->N, p->ld, p->ld, s) != cudaSuccess) return TFX_ERR_CUDA;
+        return TFX_OK;
+    }
+    float* buf[2] = {reinterpret_cast<float*>(ws), reinterpret_cast<float*>(static_cast<char*>(ws) + p->buf_bytes)};
+    const float* cur = x;
+    int64_t ldc = p->ld;
+    for (int i = 0; i < ns; ++i) {
+        const PlainStage& st = p->plain[i];
+        // the last stage writes y directly unless that would be an in-place FIR
+        const bool direct = i == ns - 1 && !(st.kind == TFX_STAGE_FIR && cur == y);
+        float* out = direct ? y : buf[i & 1];
+        int64_t ldo = direct ? p->ld : p->N;
+        if (st.kind == TFX_STAGE_SOS) {
+            if (launch_plain_sos(cur, out, p->C, p->N, ldc, ldo, st.n,
+                                 reinterpret_cast<const float*>(p->dconst + st.off), s) != cudaSuccess)
+                return TFX_ERR_CUDA;
+        } else {
+            if (launch_plain_fir(cur, out, p->C, p->N, ldc, ldo, st.n,
+                                 reinterpret_cast<const float*>(p->dconst + st.off), s) != cudaSuccess)
+                return TFX_ERR_CUDA;
+        }
+        cur = out;
+        ldc = ldo;
+    }
+    if (cur != y && launch_copy_rows(cur, y, p->C, p->N, ldc, p->ld, s) != cudaSuccess) return TFX_ERR_CUDA;
+    return TFX_OK;
+}
+
+int check_exec_args(tfx_plan* p, const float* x, float* y, void* ws, size_t ws_bytes, size_t need) {
+    if (!p) return TFX_ERR_INVALID;
+    if (p->C > 0 && p->N > 0 && (!x || !y)) return TFX_ERR_INVALID;
+    if (ranges_overlap_not_equal(x, y, p->C, p->N, p->ld)) return TFX_ERR_INVALID;
+    if (need > 0) {
+        if (!ws || ws_bytes < need) return TFX_ERR_WORKSPACE;
+        if (reinterpret_cast<uintptr_t>(ws) % ALIGN != 0) return TFX_ERR_WORKSPACE;
+    }
+    return TFX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// one-shot plan cache
+
+struct CacheEntry {
+    tfx_plan* plan = nullptr;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+};
+
+std::mutex g_mu;
+std::list<std::string> g_lru;
+std::unordered_map<std::string, std::pair<CacheEntry, std::list<std::string>::iterator>> g_cache;
+constexpr size_t CACHE_MAX = 32;
+
+std::string cache_key(int64_t C, int64_t N, int64_t ld, const tfx_stage* st, int32_t nst, cudaStream_t s) {
+    std::string k;
+    auto put = [&](const void* p, size_t n) { k.append(static_cast<const char*>(p), n); };
+    put(&C, 8);
+    put(&N, 8);
+    put(&ld, 8);
+    put(&s, sizeof(s));
+    put(&nst, 4);
+    for (int32_t i = 0; i < nst; ++i) {
+        put(&st[i].kind, 4);
+        put(&st[i].n, 4);
+        const size_t cnt = st[i].kind == TFX_STAGE_SOS ? (size_t)st[i].n * 6 : (size_t)st[i].n;
+        if (cnt) put(st[i].coef, cnt * sizeof(double));
+    }
+    return k;
+}
+
+void free_entry(CacheEntry& e) {
+    if (e.ws) cudaFree(e.ws);
+    tfx_plan_destroy(e.plan);
+    e = CacheEntry();
+}
+
+int cached_plan(int64_t C, int64_t N, int64_t ld, const tfx_stage* st, int32_t nst, cudaStream_t s,
+                CacheEntry* out) {
+    const std::string key = cache_key(C, N, ld, st, nst, s);
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) {
+        g_lru.splice(g_lru.begin(), g_lru, it->second.second);
+        *out = it->second.first;
+        return TFX_OK;
+    }
+    CacheEntry e;
+    int rc = tfx_plan_create(&e.plan, C, N, ld, st, nst, TFX_PLAN_DEFAULT);
+    if (rc != TFX_OK) return rc;
+    e.ws_bytes = tfx_plan_workspace_size(e.plan);
+    if (e.ws_bytes > 0 && cudaMalloc(&e.ws, e.ws_bytes) != cudaSuccess) {
+        free_entry(e);
+        return TFX_ERR_NOMEM;
+    }
+    if (g_cache.size() >= CACHE_MAX) {
+        const std::string& old = g_lru.back();
+        auto oit = g_cache.find(old);
+        free_entry(oit->second.first);
+        g_cache.erase(oit);
+        g_lru.pop_back();
+    }
+    g_lru.push_front(key);
+    g_cache.emplace(key, std::make_pair(e, g_lru.begin()));
+    *out = e;
+    return TFX_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+
+extern "C" {
+
+int tfx_plan_create(tfx_plan** out, int64_t C, int64_t N, int64_t ld, const tfx_stage* st, int32_t nst,
+                    uint32_t flags) {
+    if (!out) return TFX_ERR_INVALID;
+    *out = nullptr;
+    int rc = check_dims(C, N, ld);
+    if (rc != TFX_OK) return rc;
+    rc = validate_stages(st, nst);
+    if (rc != TFX_OK) return rc;
+    if (flags & ~(TFX_PLAN_FIR_CUDA_CORES | TFX_PLAN_UNFUSED | TFX_PLAN_FIR_BF16_PLAIN | TFX_PLAN_TEST_DROP_PUBLISH))
+        return TFX_ERR_INVALID;
+    tfx_plan* p = new (std::nothrow) tfx_plan();
+    if (!p) return TFX_ERR_NOMEM;
+    p->C = C;
+    p->N = N;
+    p->ld = ld;
+    p->flags = flags;
+    rc = build_plan(p, st, nst, true);
+    if (rc != TFX_OK) {
+        tfx_plan_destroy(p);
+        return rc;
+    }
+    *out = p;
+    return TFX_OK;
+}
+
+size_t tfx_plan_workspace_size(const tfx_plan* p) {
+    if (!p) return 0;
+    return p->ws_fused > p->ws_plain ? p->ws_fused : p->ws_plain;
+}
+
+int tfx_plan_execute(tfx_plan* p, const float* x, float* y, void* ws, size_t ws_bytes, tfx_stream s) {
+    const size_t need = p ? p->ws_fused : 0;
+    int rc = check_exec_args(p, x, y, ws, ws_bytes, need);
+    if (rc != TFX_OK) return rc;
+    if (p->C == 0 || p->N == 0) return TFX_OK;
+    return exec_fused(p, x, y, ws, reinterpret_cast<cudaStream_t>(s));
+}
+
+int tfx_plan_execute_plain(tfx_plan* p, const float* x, float* y, void* ws, size_t ws_bytes, tfx_stream s) {
+    const size_t need = p ? p->ws_plain : 0;
+    int rc = check_exec_args(p, x, y, ws, ws_bytes, need);
+    if (rc != TFX_OK) return rc;
+    if (p->C == 0 || p->N == 0) return TFX_OK;
+    return exec_plain(p, x, y, ws, reinterpret_cast<cudaStream_t>(s));
+}
+
+int tfx_plan_get_error(tfx_plan* p) {
+    if (!p || !p->dstatus) return TFX_ERR_INVALID;
+    if (cudaDeviceSynchronize() != cudaSuccess) return TFX_ERR_CUDA;
+    int v = 0;
+    if (cudaMemcpy(&v, p->dstatus, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return TFX_ERR_CUDA;
+    if (v != 0 && cudaMemset(p->dstatus, 0, sizeof(int)) != cudaSuccess) return TFX_ERR_CUDA;
+    return v;
+}
+
+void tfx_plan_destroy(tfx_plan* p) {
+    if (!p) return;
+    if (p->dconst || p->dstatus) cudaDeviceSynchronize();
+    if (p->dconst) cudaFree(p->dconst);
+    if (p->dstatus) cudaFree(p->dstatus);
+    delete p;
+}
+
+size_t tfx_chain_workspace_size(int64_t C, int64_t N, int64_t ld, const tfx_stage* st, int32_t nst) {
+    if (check_dims(C, N, ld) != TFX_OK || validate_stages(st, nst) != TFX_OK) return SIZE_MAX;
+    tfx_plan p;  // layout only: nothing is allocated or uploaded
+    p.C = C;
+    p.N = N;
+    p.ld = ld;
+    if (build_plan(&p, st, nst, false) != TFX_OK) return SIZE_MAX;
+    return p.ws_fused;
+}
+
+int tfx_chain(const float* x, float* y, int64_t C, int64_t N, int64_t ld, const tfx_stage* st, int32_t nst,
+              void* ws, size_t ws_bytes, tfx_stream s) {
+    int rc = check_dims(C, N, ld);
+    if (rc != TFX_OK) return rc;
+    rc = validate_stages(st, nst);
+    if (rc != TFX_OK) return rc;
+    if (C > 0 && N > 0 && (!x || !y)) return TFX_ERR_INVALID;
+    if (ranges_overlap_not_equal(x, y, C, N, ld)) return TFX_ERR_INVALID;
+    if (C == 0 || N == 0) return TFX_OK;
+    CacheEntry e;
+    rc = cached_plan(C, N, ld, st, nst, reinterpret_cast<cudaStream_t>(s), &e);
+    if (rc != TFX_OK) return rc;
+    if (ws) return tfx_plan_execute(e.plan, x, y, ws, ws_bytes, s);
+    return tfx_plan_execute(e.plan, x, y, e.ws, e.ws_bytes, s);
+}
+
+int tfx_fir(const float* x, float* y, int64_t C, int64_t N, int64_t ld, const double* h, int32_t taps,
+            tfx_stream s) {
+    tfx_stage st = {TFX_STAGE_FIR, taps, h};
+    return tfx_chain(x, y, C, N, ld, &st, 1, nullptr, 0, s);
+}
+
+int tfx_sos(const float* x, float* y, int64_t C, int64_t N, int64_t ld, const double* sos, int32_t sections,
+            tfx_stream s) {
+    tfx_stage st = {TFX_STAGE_SOS, sections, sos};
+    return tfx_chain(x, y, C, N, ld, &st, 1, nullptr, 0, s);
+}
+
+void tfx_cache_clear(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto& kv : g_cache) free_entry(kv.second.first);
+    g_cache.clear();
+    g_lru.clear();
+}
+
+const char* tfx_strerror(int status) {
+    switch (status) {
+        case TFX_OK: return "TFX_OK";
+        case TFX_ERR_INVALID: return "TFX_ERR_INVALID: invalid argument";
+        case TFX_ERR_UNSTABLE: return "TFX_ERR_UNSTABLE: SOS section with a pole on or outside the unit circle";
+        case TFX_ERR_WORKSPACE: return "TFX_ERR_WORKSPACE: workspace missing, too small or misaligned";
+        case TFX_ERR_CUDA: return "TFX_ERR_CUDA: CUDA runtime call failed";
+        case TFX_ERR_TIMEOUT: return "TFX_ERR_TIMEOUT: a device-side bounded wait gave up";
+        case TFX_ERR_UNSUPPORTED: return "TFX_ERR_UNSUPPORTED: request outside what this build implements";
+        case TFX_ERR_NOMEM: return "TFX_ERR_NOMEM: allocation failed";
+        default: return "unknown tfx status";
+    }
+}
+
+int tfx_version(void) { return 0x000100; }
+
+}  // extern "C"

@@ -1,0 +1,129 @@
+// Internal definitions shared by the libtfx kernels and the host plan code.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tfx.h"
+
+namespace tfx {
+
+// CTA shape of the scan / fused kernels: NT threads, each owning a contiguous
+// chunk of T samples, so one tile is NT*T samples of one channel.
+constexpr int NT = 256;
+constexpr int NWARP = NT / 32;
+constexpr int T_CHUNK = 32;
+constexpr int TILE = NT * T_CHUNK;  // 8192 samples
+// FIR register blocking: each thread produces FIR_R consecutive outputs per
+// pass and walks the taps FIR_R at a time.
+constexpr int FIR_R = 16;
+// Zero padding in front of the FIR window (shared memory), >= 2*FIR_R.
+constexpr int FIR_PAD = 32;
+// Device-side bounded waits give up after this long and record TFX_ERR_TIMEOUT.
+constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;
+
+// Per-unit device constants (one "unit" = an optional SOS cascade followed
+// by an optional FIR; consecutive SOS stages are merged into one cascade).
+struct UnitConst {
+    int S;             // sections
+    int L;             // FIR taps (0 = no FIR)
+    int H;             // FIR halo = L - 1 (0 without FIR)
+    int nkb;           // FIR tap blocks of FIR_R (taps zero-padded to nkb*FIR_R)
+    float gain;        // output scale when the unit ends without an FIR
+    const float* coef; // [S][8]: b0 b1 b2 a1 a2 (a0-normalised), 3 pad
+    const float4* pw;  // [S][NT+1]: A^k, A = chunk transfer matrix (row-major 2x2)
+    const float* taps; // [nkb*FIR_R] FP32 taps, zero-padded
+};
+
+// Scratch for one execution of one unit (inside the caller's workspace).
+struct UnitScratch {
+    unsigned* ticket;   // tile ticket counter (reset per execution)
+    unsigned* flags;    // [tiles][S+1]: per-section look-back flag, then tail flag
+    float4* vals;       // [tiles][S]: (agg.x, agg.y, incl.x, incl.y)
+    float* tails;       // [tiles][tail_len]: last FIR-input samples of each tile
+    int tail_len;       // min(H, TILE)
+};
+
+struct UnitArgs {
+    const float* x;
+    float* y;
+    int64_t ldx, ldy;
+    int64_t C, N;
+    int64_t ntt;  // time tiles per channel
+    UnitConst k;
+    UnitScratch sc;
+    int* status;     // device status word (TFX_OK or TFX_ERR_TIMEOUT)
+    int64_t drop_tile;  // test hook: this tile never publishes (-1 = off)
+};
+
+// ---------------------------------------------------------------------------
+// device helpers
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ float4 ld_relaxed_f4(const float4* p) {
+    float4 v;
+    asm volatile("ld.relaxed.gpu.global.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p)
+                 : "memory");
+    return v;
+}
+
+// Wait until *flag >= want.  Returns the flag value, or 0 if the wait gave up
+// (time limit reached, or another CTA already recorded an error), in which
+// case the status word holds TFX_ERR_TIMEOUT and the caller continues with
+// zero data so that every CTA still terminates.
+__device__ __forceinline__ unsigned wait_flag(const unsigned* flag, unsigned want, int* status) {
+    unsigned v = ld_acquire_u32(flag);
+    if (v >= want) return v;
+    unsigned long long t0 = global_ns();
+    unsigned ns = 32;
+    for (;;) {
+        __nanosleep(ns);
+        if (ns < 512) ns <<= 1;
+        v = ld_acquire_u32(flag);
+        if (v >= want) return v;
+        if (*(volatile int*)status != 0) return 0;
+        if (global_ns() - t0 > WAIT_LIMIT_NS) {
+            atomicCAS(status, 0, (int)TFX_ERR_TIMEOUT);
+            return 0;
+        }
+    }
+}
+
+// 2x2 row-major matrix (float4 = m00 m01 m10 m11) helpers
+__device__ __forceinline__ float2 mv2(float4 m, float2 v) {
+    return make_float2(fmaf(m.x, v.x, m.y * v.y), fmaf(m.z, v.x, m.w * v.y));
+}
+__device__ __forceinline__ float4 mm2(float4 a, float4 b) {
+    return make_float4(fmaf(a.x, b.x, a.y * b.z), fmaf(a.x, b.y, a.y * b.w),
+                       fmaf(a.z, b.x, a.w * b.z), fmaf(a.z, b.y, a.w * b.w));
+}
+
+// Launchers (defined in the kernel translation units).
+cudaError_t launch_unit(const UnitArgs& a, cudaStream_t s);
+cudaError_t launch_plain_sos(const float* x, float* y, int64_t C, int64_t N, int64_t ldx,
+                             int64_t ldy, int S, const float* coef, cudaStream_t s);
+cudaError_t launch_plain_fir(const float* x, float* y, int64_t C, int64_t N, int64_t ldx,
+                             int64_t ldy, int L, const float* taps, cudaStream_t s);
+cudaError_t launch_copy_rows(const float* x, float* y, int64_t C, int64_t N, int64_t ldx,
+                             int64_t ldy, cudaStream_t s);
+size_t unit_smem_bytes(const UnitConst& k);
+cudaError_t prepare_unit(const UnitConst& k);
+
+}  // namespace tfx

@@ -1,0 +1,200 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Sizes span several tiles (8192 samples) with ragged tails, taps shorter and
+longer than a tile, in-place operation, padded row strides and unaligned
+rows.  Tolerances: max|err| <= 1e-5 * peak|y| per channel for FIR-only
+chains and <= 1e-4 * peak|y| once IIR sections are present."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2504_08624_gb300 import workloads as W
+from tests.gpu_util import assert_close, oracle_chain, tol_for
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def run(x, stages, inplace=False, ld=None, offset=0, flags=None, plain=False):
+    from paper_2504_08624_gb300 import api
+    C, N = x.shape
+    ld = N if ld is None else ld
+    buf = torch.zeros(offset + C * ld + 8, dtype=torch.float32, device="cuda")
+    xv = buf[offset:offset + C * ld].view(C, ld)[:, :N]
+    xv.copy_(torch.from_numpy(x))
+    if flags is None and not plain:
+        if inplace:
+            api.chain(xv, stages, out=xv)
+            y = xv
+        else:
+            ybuf = torch.zeros_like(buf)
+            yv = ybuf[offset:offset + C * ld].view(C, ld)[:, :N]
+            api.chain(xv, stages, out=yv)
+            y = yv
+    else:
+        p = api.Plan(C, N, stages, ld=ld, flags=flags or 0)
+        y = xv if inplace else torch.zeros_like(buf)[offset:offset + C * ld].view(C, ld)[:, :N]
+        p.execute(xv, y, plain=plain)
+        torch.cuda.synchronize()
+        assert p.get_error() == 0
+        p.close()
+    torch.cuda.synchronize()
+    return y.cpu().numpy().astype(np.float64)
+
+
+def check(x, stages, tol=None, **kw):
+    got = run(x, stages, **kw)
+    ref = oracle_chain(x, stages)
+    return assert_close(got, ref, tol or tol_for(stages), str(kw))
+
+
+RNG = np.random.default_rng(2024)
+NS = [1, 7, 31, 32, 33, 8191, 8192, 8193, 3 * 8192 + 517]
+
+
+@pytest.mark.parametrize("N", NS)
+@pytest.mark.parametrize("S", [1, 2, 8])
+def test_sos_sizes(N, S):
+    x = W.white_uniform(3, N, 11)
+    rows = W.random_stable_sos(S, 100 + S, 0.3, 0.99)
+    check(x, [("sos", rows)])
+
+
+@pytest.mark.parametrize("L", [1, 2, 16, 17, 101, 1025])
+@pytest.mark.parametrize("N", [1, 100, 8192, 20001])
+def test_fir_sizes(L, N):
+    x = W.white_gauss(2, N, 12)
+    h = np.random.default_rng(L).standard_normal(L) / math.sqrt(L)
+    check(x, [("fir", h)])
+
+
+@pytest.mark.parametrize("L", [8192, 8193, 9000, 20000])
+def test_fir_halo_spans_tiles(L):
+    # halo of L-1 >= one tile: the window gathers from several predecessor tiles
+    x = W.white_gauss(2, 40000, 13)
+    h = np.random.default_rng(L).standard_normal(L) / math.sqrt(L)
+    check(x, [("fir", h)])
+
+
+def test_plain_chain_full_size():
+    wl = W.plain_chain()
+    x = wl.make_signal()
+    check(x, wl.stages, wl.tol)
+
+
+def test_multichannel_chain_reduced():
+    wl = W.multichannel_fused()
+    x = wl.make_signal(3, 60000)
+    check(x, wl.stages, wl.tol)
+
+
+@pytest.mark.parametrize("inplace", [False, True])
+@pytest.mark.parametrize("kind", ["sos", "fir", "chain", "fir_sos_fir"])
+def test_inplace_and_layouts(kind, inplace):
+    x = W.white_uniform(3, 3 * 8192 + 77, 14)
+    rows = W.butter_sos(4, 1000.0, 48000.0)
+    h = W.fir_highpass(101, 100.0, 48000.0)
+    stages = {"sos": [("sos", rows)], "fir": [("fir", h)], "chain": [("sos", rows), ("fir", h)],
+              "fir_sos_fir": [("fir", h), ("sos", rows), ("fir", W.fir_lowpass(33, 5000.0, 48000.0))]}[kind]
+    check(x, stages, inplace=inplace)
+    check(x, stages, inplace=inplace, ld=x.shape[1] + 5)        # padded rows
+    check(x, stages, inplace=inplace, ld=x.shape[1] + 3, offset=1)  # unaligned rows
+
+
+def test_a0_not_one_and_identity():
+    x = W.white_uniform(2, 10000, 15)
+    rows = W.butter_sos(4, 2000.0, 48000.0) * np.array([[2.5], [0.5]])  # a0 != 1
+    check(x, [("sos", rows)])
+    check(x, [("sos", np.zeros((0, 6)))])   # empty cascade = identity
+    check(x, [])                            # empty chain = identity
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_chains(seed):
+    stages = W.random_chain(seed)
+    rng = np.random.default_rng(seed)
+    C = int(rng.integers(1, 5))
+    N = int(rng.integers(1000, 60000))
+    x = W.white_uniform(C, N, 500 + seed)
+    check(x, stages)
+
+
+def test_high_q_pole():
+    # radius 0.999 (the upper end of the stated tolerance regime)
+    x = W.white_uniform(2, 50000, 16)
+    r, th = 0.999, 0.05
+    row = np.array([[1e-3, 0.0, -1e-3, 1.0, -2 * r * math.cos(th), r * r]])
+    check(x, [("sos", row)])
+
+
+@pytest.mark.parametrize("flags", ["unfused", "plain"])
+def test_alternate_paths(flags):
+    wl = W.plain_chain()
+    x = wl.make_signal(2, 30000)
+    if flags == "plain":
+        check(x, wl.stages, wl.tol, plain=True)
+    else:
+        from paper_2504_08624_gb300 import _native as N
+        check(x, wl.stages, wl.tol, flags=N.TFX_PLAN_UNFUSED)
+
+
+def test_empty_inputs():
+    from paper_2504_08624_gb300 import api
+    for shape in [(0, 100), (3, 0)]:
+        x = torch.zeros(shape, dtype=torch.float32, device="cuda")
+        y = api.chain(x, [("sos", W.butter_sos(2, 1000, 48000)), ("fir", [1.0, 0.5])])
+        assert tuple(y.shape) == shape
+
+
+def test_host_buffers_round_trip():
+    from paper_2504_08624_gb300 import api
+    wl = W.plain_chain()
+    x = wl.make_signal(2, 20000)
+    xt = torch.from_numpy(x).pin_memory()
+    y = api.chain(xt, wl.stages)
+    assert y.device.type == "cpu"
+    assert_close(y.numpy(), oracle_chain(x, wl.stages), wl.tol, "host buffers")
+
+
+def test_timeout_is_reported_not_hung():
+    """A tile that never publishes: its successor's bounded wait gives up, the
+    launch completes, and the plan reports TFX_ERR_TIMEOUT (no hang, no trap)."""
+    from paper_2504_08624_gb300 import api, _native as N
+    x = torch.from_numpy(W.white_uniform(2, 3 * 8192, 17)).cuda()
+    p = api.Plan(2, 3 * 8192, [("sos", W.butter_sos(2, 1000, 48000)), ("fir", [1.0, 0.5, 0.25])],
+                 flags=N.TFX_PLAN_TEST_DROP_PUBLISH)
+    p.execute(x)
+    torch.cuda.synchronize()
+    assert p.get_error() == -5
+    assert p.get_error() == 0  # cleared after reading
+    # the context is still usable
+    y = api.chain(x, [("fir", [2.0])])
+    torch.cuda.synchronize()
+    assert torch.allclose(y, 2 * x)
+    p.close()
+
+
+def test_plan_reuse_and_graph_capture():
+    from paper_2504_08624_gb300 import api
+    wl = W.plain_chain()
+    x = wl.make_signal(2, 30000)
+    xt = torch.from_numpy(x).cuda()
+    p = api.Plan(2, 30000, wl.stages)
+    y = torch.empty_like(xt)
+    ws = p.workspace()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        p.execute(xt, y, ws)  # warm-up on the capture stream
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        p.execute(xt, y, ws)
+    y.zero_()
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    assert_close(y.cpu().numpy(), oracle_chain(x, wl.stages), wl.tol, "graph replay")
+    p.close()
