@@ -1,0 +1,196 @@
+// Long FIR as a Toeplitz-block GEMM on the tcgen05 tensor cores.
+//
+// Operation (TorchFX Sec. 3 FIR filters, Table 2 workload): per channel,
+// y[n] = sum_{k<L} h[k] x[n-k], causal, zero history.
+//
+// Formulation.  Outputs are grouped into blocks of P = 128 samples; block n
+// needs the input window x[nP - W, nP + P) with W = L - 1 rounded up to 16,
+// so with kappa indexing that window,
+//     y[nP + i] = sum_kappa A[l][kappa] x[nP - W + kappa],
+//     A[l][kappa] = h[i + W - kappa],   i = 127 - l   (TMEM lane l <-> phase i).
+// One CTA computes NB output blocks of one channel: D[128 x NB] in TMEM,
+// accumulated over K = W + 128 in steps of 16 by tcgen05.mma (M = 128,
+// N = NB, K = 16, BF16 operands, FP32 accumulation).
+//
+// Both operands are Hankel/Toeplitz, and both are expressed with the
+// no-swizzle canonical layout without materialising the matrices:
+//  * A (taps): A[l][kappa] = g[l + kappa] with g[u] = h[W + 127 - u].  Storing
+//    8 copies of g shifted by 0..7 elements, interleaved in 16-byte chunks
+//    (chunk j, copy b holds g[8j + b .. 8j + b + 7]), makes every K-step a
+//    descriptor with LBO = SBO = 128 bytes starting at chunk 2k.
+//  * B (signal): the window is stored in 8-sample chunks, chunk g at column
+//    g % 16 and row g / 16 of a [rows x 16] grid laid out column-major
+//    (column stride CS = rows * 16 bytes).  Block n's row is then n and the
+//    K-step k operand starts at column 2k % 16, row k / 8, with LBO = CS and
+//    SBO = 128 bytes.
+// FP32 accuracy from BF16 products: x = x_hi + x_lo and h = h_hi + h_lo (each
+// BF16, residual ~2^-17 relative); D = A_hi B_hi + A_hi B_lo + A_lo B_hi.
+#include <cuda_bf16.h>
+
+#include "tc_ptx.cuh"
+#include "tfx_common.cuh"
+
+namespace tfx {
+
+__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo_half, __nv_bfloat16 hi_half) {
+    return (uint32_t)__bfloat16_as_ushort(lo_half) | ((uint32_t)__bfloat16_as_ushort(hi_half) << 16);
+}
+
+// Split 8 consecutive samples into BF16 hi / lo parts packed as 16-byte chunks.
+__device__ __forceinline__ void split8(const float (&v)[8], uint4& hi, uint4& lo) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * i]);
+        const __nv_bfloat16 h1 = __float2bfloat16_rn(v[2 * i + 1]);
+        const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * i] - __bfloat162float(h0));
+        const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * i + 1] - __bfloat162float(h1));
+        h[i] = pack_bf16x2(h0, h1);
+        l[i] = pack_bf16x2(l0, l1);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+__global__ void __launch_bounds__(256, 1) k_fir_tc(FirTcArgs a) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int J = a.a_chunks;
+    const int rows = a.rows;
+    const uint32_t CS = (uint32_t)rows * 16u;
+    uint8_t* A_hi = smem;
+    uint8_t* A_lo = A_hi + (size_t)J * 128;
+    uint8_t* B_hi = A_lo + (size_t)J * 128;
+    uint8_t* B_lo = B_hi + (size_t)16 * CS;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(B_lo + (size_t)16 * CS);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
+
+    const int64_t tile = blockIdx.x;
+    const int64_t c = tile / a.ntt;
+    const int64_t t0 = (tile % a.ntt) * (int64_t)(128 * a.NB);
+
+    if (warp == 0) {
+        tc::tmem_alloc(tmem_slot, (uint32_t)a.tmem_cols);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) tc::mbar_init(bar, 1);
+
+    // taps: both interleaved tables, straight copies
+    {
+        const uint4* src_hi = a.a_hi;
+        const uint4* src_lo = a.a_lo;
+        uint4* dhi = reinterpret_cast<uint4*>(A_hi);
+        uint4* dlo = reinterpret_cast<uint4*>(A_lo);
+        for (int i = tid; i < J * 8; i += blockDim.x) {
+            dhi[i] = src_hi[i];
+            dlo[i] = src_lo[i];
+        }
+    }
+    // signal window [t0 - W, t0 - W + rows*128) -> BF16 hi / lo chunks
+    {
+        const float* xr = a.x + c * a.ldx;
+        const int64_t s0 = t0 - a.W;
+        const int nchunks = rows * 16;
+        const bool vec = ((reinterpret_cast<uintptr_t>(xr + s0) & 15) == 0);
+        for (int g = tid; g < nchunks; g += blockDim.x) {
+            const int64_t t = s0 + 8 * (int64_t)g;
+            float v[8];
+            if (vec && t >= 0 && t + 8 <= a.N) {
+                const float4 p0 = *reinterpret_cast<const float4*>(xr + t);
+                const float4 p1 = *reinterpret_cast<const float4*>(xr + t + 4);
+                v[0] = p0.x; v[1] = p0.y; v[2] = p0.z; v[3] = p0.w;
+                v[4] = p1.x; v[5] = p1.y; v[6] = p1.z; v[7] = p1.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) v[i] = (t + i >= 0 && t + i < a.N) ? xr[t + i] : 0.f;
+            }
+            uint4 hi, lo;
+            split8(v, hi, lo);
+            const uint32_t off = (uint32_t)(g % 16) * CS + (uint32_t)(g / 16) * 16u;
+            *reinterpret_cast<uint4*>(B_hi + off) = hi;
+            *reinterpret_cast<uint4*>(B_lo + off) = lo;
+        }
+    }
+    tc::fence_proxy_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (tid == 0) {
+        const uint32_t idesc = tc::idesc_bf16_f32(128, a.NB);
+        const uint32_t ahi = tc::smem_u32(A_hi), alo = tc::smem_u32(A_lo);
+        const uint32_t bhi = tc::smem_u32(B_hi), blo = tc::smem_u32(B_lo);
+        for (int k = 0; k < a.nK; ++k) {
+            const uint32_t aoff = (uint32_t)(2 * k) * 128u;
+            const uint32_t boff = (uint32_t)((2 * k) & 15) * CS + (uint32_t)(k >> 3) * 16u;
+            const uint64_t dah = tc::desc_noswz(ahi + aoff, 128u, 128u);
+            const uint64_t dbh = tc::desc_noswz(bhi + boff, CS, 128u);
+            tc::mma_bf16(tmem, dah, dbh, idesc, k > 0 ? 1u : 0u);
+            if (!a.plain_bf16) {
+                const uint64_t dal = tc::desc_noswz(alo + aoff, 128u, 128u);
+                const uint64_t dbl = tc::desc_noswz(blo + boff, CS, 128u);
+                tc::mma_bf16(tmem, dah, dbl, idesc, 1u);
+                tc::mma_bf16(tmem, dal, dbh, idesc, 1u);
+            }
+        }
+        tc::mma_commit(bar);
+    }
+
+    // wait for the accumulator (bounded)
+    bool ok = true;
+    {
+        const unsigned long long tw = global_ns();
+        while (!tc::mbar_try_wait(bar, 0)) {
+            if (global_ns() - tw > WAIT_LIMIT_NS) {
+                atomicCAS(a.status, 0, (int)TFX_ERR_TIMEOUT);
+                ok = false;
+                break;
+            }
+        }
+    }
+    tc::tc_fence_after();
+
+    if (ok) {
+        // epilogue: warp w reads lanes [32 (w%4), +32) and half of the columns
+        const int quarter = warp & 3;
+        const int nhalf = a.NB / 2;
+        const int col0 = (warp >> 2) * nhalf;
+        const int l = quarter * 32 + lane;      // TMEM lane = 127 - phase
+        const int phase = 127 - l;
+        float* yr = a.y + c * a.ldy;
+        for (int cc = col0; cc < col0 + nhalf; cc += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cc, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int64_t n = t0 + (int64_t)(cc + j) * 128 + phase;
+                if (n < a.N) yr[n] = v[j];
+            }
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, (uint32_t)a.tmem_cols);
+}
+
+size_t fir_tc_smem_bytes(const FirTcArgs& a) {
+    return (size_t)a.a_chunks * 128 * 2 + (size_t)16 * a.rows * 16 * 2 + 16;
+}
+
+cudaError_t prepare_fir_tc(size_t smem) {
+    static size_t set_bytes = 0;
+    if (smem <= set_bytes) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_fir_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) set_bytes = smem;
+    return e;
+}
+
+cudaError_t launch_fir_tc(const FirTcArgs& a, cudaStream_t s) {
+    const int64_t tiles = a.C * a.ntt;
+    if (tiles <= 0) return cudaSuccess;
+    k_fir_tc<<<(unsigned)tiles, 256, fir_tc_smem_bytes(a), s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace tfx

@@ -7,8 +7,9 @@
 
 namespace tfx {
 
-// One thread per channel; the whole cascade (transposed direct form II per
-// section) is advanced one sample at a time.  coef rows: b0 b1 b2 a1 a2 (+3 pad).
+// One thread per channel; the whole cascade is advanced one sample at a time,
+// each section as the same 2-state recursion the scan kernel uses.
+// coef rows: b0 c1 c2 a1 a2 (+3 pad), c1 = b1 - a1 b0, c2 = b2 - a2 b0.
 __global__ void k_plain_sos(const float* __restrict__ x, float* __restrict__ y, int64_t C, int64_t N,
                             int64_t ldx, int64_t ldy, int S, const float* __restrict__ coef) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -23,8 +24,9 @@ __global__ void k_plain_sos(const float* __restrict__ x, float* __restrict__ y, 
         for (int s = 0; s < S; ++s) {
             const float* cf = coef + 8 * s;
             const float yv = fmaf(cf[0], v, w1[s]);
-            w1[s] = fmaf(cf[1], v, fmaf(-cf[3], yv, w2[s]));
-            w2[s] = fmaf(cf[2], v, -cf[4] * yv);
+            const float n1 = fmaf(cf[1], v, fmaf(-cf[3], w1[s], w2[s]));
+            w2[s] = fmaf(cf[2], v, -cf[4] * w1[s]);
+            w1[s] = n1;
             v = yv;
         }
         yr[n] = v;

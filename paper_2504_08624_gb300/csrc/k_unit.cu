@@ -8,8 +8,8 @@
 // order, then y[n] = sum_k h[k] x[n-k].
 //
 // Decomposition.  A tile is TILE = NT*T samples of one channel; thread i owns
-// samples [i*T, (i+1)*T).  Each section runs in transposed direct form II with
-// state W = (w1, w2); over a chunk of T samples the state evolves as
+// samples [i*T, (i+1)*T).  Each section runs as a 2-state recursion with the
+// transposed-direct-form-II state W = (w1, w2); over a chunk of T samples the state evolves as
 // W_end = A W_start + e, where A = M^T (M the 2x2 one-sample transfer matrix)
 // and e is the chunk's zero-state end state.  Per section:
 //   1. zero-state pass over the thread's chunk (outputs y_zs, end state e);
@@ -117,17 +117,21 @@ __global__ void __launch_bounds__(NT, 2) k_unit(UnitArgs a) {
 
     for (int s = 0; s < S; ++s) {
         const float* cf = a.k.coef + 8 * s;
-        const float b0 = cf[0], b1 = cf[1], b2 = cf[2], a1 = cf[3], a2 = cf[4];
+        const float b0 = cf[0], c1 = cf[1], c2 = cf[2], a1 = cf[3], a2 = cf[4];
         const float4* P = a.k.pw + (size_t)s * (NT + 1);
 
-        // 1. zero-state pass (transposed direct form II)
+        // 1. zero-state pass.  State (w1, w2) of the transposed direct form II,
+        // updated as w1' = c1 u - a1 w1 + w2, w2' = c2 u - a2 w1, y = b0 u + w1
+        // with c1 = b1 - a1 b0, c2 = b2 - a2 b0 formed in FP64 at plan time (this
+        // avoids the cancellation of b1 u against a1 y when b ~ a).
         float w1 = 0.f, w2 = 0.f;
 #pragma unroll
         for (int t = 0; t < T; ++t) {
-            const float yv = fmaf(b0, u[t], w1);
-            w1 = fmaf(b1, u[t], fmaf(-a1, yv, w2));
-            w2 = fmaf(b2, u[t], -a2 * yv);
-            u[t] = yv;
+            const float ut = u[t];
+            u[t] = fmaf(b0, ut, w1);
+            const float n1 = fmaf(c1, ut, fmaf(-a1, w1, w2));
+            w2 = fmaf(c2, ut, -a2 * w1);
+            w1 = n1;
         }
 
         // 2. warp inclusive scan: v_l = sum_{m<=l} A^m e_{l-m}

@@ -31,7 +31,15 @@ struct HostUnit {
     int tail_len = 0;
     // scratch sizes (bytes)
     size_t flags_bytes = 0, vals_bytes = 0, tails_bytes = 0;
+    // FIR on the tensor cores (Toeplitz-block GEMM); such a unit has S == 0
+    bool tc = false;
+    int W = 0, nK = 0, NB = 0, rows = 0, tmem_cols = 0, a_chunks = 0;
+    size_t off_ahi = 0, off_alo = 0, tc_smem = 0;
 };
+
+// Taps at or above this count go to the tensor cores (unless disabled).
+constexpr int TC_MIN_TAPS = 64;
+constexpr size_t SMEM_MAX = 227 * 1024;
 
 struct PlainStage {
     int kind;  // TFX_STAGE_FIR / TFX_STAGE_SOS
@@ -77,6 +85,56 @@ int normalise_row(const double* r, double* out) {
     out[3] = al1;
     out[4] = al2;
     return TFX_OK;
+}
+
+// Device coefficients of one a0-normalised section (b0 b1 b2 a1 a2): the
+// recursion w1' = c1 u - a1 w1 + w2, w2' = c2 u - a2 w1, y = b0 u + w1 uses
+// c1 = b1 - a1 b0 and c2 = b2 - a2 b0, formed here in FP64 before rounding.
+void sec_device_coefs(const double* r, float* out) {
+    out[0] = (float)r[0];
+    out[1] = (float)(r[1] - r[3] * r[0]);
+    out[2] = (float)(r[2] - r[4] * r[0]);
+    out[3] = (float)r[3];
+    out[4] = (float)r[4];
+}
+
+// Round-to-nearest-even FP32 -> BF16 bits, and back.
+uint16_t f2bf(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+float bf2f(uint16_t b) {
+    uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// Tensor-core FIR geometry for L taps and NB output blocks per tile.
+void tc_geometry(HostUnit& u, int NB) {
+    u.W = ((u.L - 1 + 15) / 16) * 16;
+    u.nK = (u.W + 128) / 16;
+    u.NB = NB;
+    u.rows = NB + (u.W + 127) / 128 + 1;
+    u.tmem_cols = NB <= 32 ? 32 : (NB <= 64 ? 64 : (NB <= 128 ? 128 : 256));
+    u.a_chunks = 2 * u.nK + 16;
+    u.tc_smem = (size_t)u.a_chunks * 128 * 2 + (size_t)16 * u.rows * 16 * 2 + 16;
+}
+
+// Pick the tile width for a tensor-core FIR: 128 blocks (16384 outputs) when
+// two CTAs fit on an SM, else the widest that fits one CTA; false if none does.
+bool choose_tc(HostUnit& u) {
+    const int cands[] = {128, 256, 64};
+    for (int nb : cands) {
+        tc_geometry(u, nb);
+        if (nb == 128 && u.tc_smem <= 110 * 1024) return true;
+        if (nb != 128 && u.tc_smem <= SMEM_MAX) return true;
+    }
+    tc_geometry(u, 128);
+    return u.tc_smem <= SMEM_MAX;
 }
 
 struct M2 {
@@ -148,6 +206,28 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
     }
     flush();
 
+    // long FIRs go to the tensor cores; an SOS cascade in front of one runs as
+    // its own unit (the cascade output crosses HBM once more)
+    if (!(p->flags & TFX_PLAN_FIR_CUDA_CORES)) {
+        std::vector<HostUnit> out;
+        for (HostUnit& u : p->units) {
+            HostUnit f = u;
+            if (u.L >= TC_MIN_TAPS && (f.S = 0, f.sec.clear(), choose_tc(f))) {
+                f.tc = true;
+                if (u.S > 0) {
+                    HostUnit sos = u;
+                    sos.L = 0;
+                    sos.taps.clear();
+                    out.push_back(sos);
+                }
+                out.push_back(f);
+            } else {
+                out.push_back(u);
+            }
+        }
+        p->units.swap(out);
+    }
+
     // constant blob layout
     size_t off = 0;
     for (HostUnit& u : p->units) {
@@ -158,6 +238,12 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         u.nkb = u.L > 0 ? (u.L + FIR_R - 1) / FIR_R : 0;
         u.off_taps = off;
         off = align_up(off + (size_t)u.nkb * FIR_R * sizeof(float));
+        if (u.tc) {
+            u.off_ahi = off;
+            off = align_up(off + (size_t)u.a_chunks * 128);
+            u.off_alo = off;
+            off = align_up(off + (size_t)u.a_chunks * 128);
+        }
     }
     for (int32_t i = 0; i < nst; ++i) {
         PlainStage ps{st[i].kind, st[i].n, off};
@@ -172,7 +258,7 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         float4* pw = reinterpret_cast<float4*>(host.data() + u.off_pw);
         for (int s = 0; s < u.S; ++s) {
             const double* r = &u.sec[5 * s];
-            for (int j = 0; j < 5; ++j) coef[8 * s + j] = (float)r[j];
+            sec_device_coefs(r, coef + 8 * s);
             // one-sample transfer of the TDF-II state (w1, w2) with zero input
             const M2 m = {-r[3], 1.0, -r[4], 0.0};
             M2 a = {1, 0, 0, 1};
@@ -185,6 +271,21 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         }
         float* taps = reinterpret_cast<float*>(host.data() + u.off_taps);
         for (int k = 0; k < u.L; ++k) taps[k] = (float)u.taps[k];
+        if (u.tc) {
+            // g[v] = h[W + 127 - v]; chunk j, copy b holds g[8j + b .. 8j + b + 7]
+            uint16_t* hi = reinterpret_cast<uint16_t*>(host.data() + u.off_ahi);
+            uint16_t* lo = reinterpret_cast<uint16_t*>(host.data() + u.off_alo);
+            for (int j = 0; j < u.a_chunks; ++j)
+                for (int b = 0; b < 8; ++b)
+                    for (int d = 0; d < 8; ++d) {
+                        const long idx = (long)u.W + 127 - (8L * j + b + d);
+                        const double h = (idx >= 0 && idx < u.L) ? u.taps[idx] : 0.0;
+                        const uint16_t bh = f2bf((float)h);
+                        const uint16_t bl = f2bf((float)(h - (double)bf2f(bh)));
+                        hi[(j * 8 + b) * 8 + d] = bh;
+                        lo[(j * 8 + b) * 8 + d] = bl;
+                    }
+        }
     }
     for (int32_t i = 0; i < nst; ++i) {
         float* d = reinterpret_cast<float*>(host.data() + p->plain[i].off);
@@ -192,7 +293,7 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
             for (int r = 0; r < st[i].n; ++r) {
                 double row[5];
                 normalise_row(st[i].coef + 6 * r, row);
-                for (int j = 0; j < 5; ++j) d[8 * r + j] = (float)row[j];
+                sec_device_coefs(row, d + 8 * r);
             }
         } else {
             for (int k = 0; k < st[i].n; ++k) d[k] = (float)st[i].coef[k];
@@ -206,6 +307,10 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         if (cudaMalloc(&p->dstatus, sizeof(int)) != cudaSuccess) return TFX_ERR_NOMEM;
         if (cudaMemset(p->dstatus, 0, sizeof(int)) != cudaSuccess) return TFX_ERR_CUDA;
         for (HostUnit& u : p->units) {
+            if (u.tc) {
+                if (prepare_fir_tc(u.tc_smem) != cudaSuccess) return TFX_ERR_UNSUPPORTED;
+                continue;
+            }
             UnitConst k{};
             k.S = u.S;
             k.L = u.L;
@@ -220,6 +325,10 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
     size_t hdr = 0, vals = 0, tails = 0;
     for (HostUnit& u : p->units) {
         u.ntt = ntt;
+        if (u.tc) {
+            u.ntt = p->N > 0 ? (p->N + 128 * u.NB - 1) / (128 * u.NB) : 0;
+            continue;
+        }
         const int H = u.L > 0 ? u.L - 1 : 0;
         u.tail_len = u.L > 0 ? (H < TILE ? H : TILE) : 0;
         const int64_t tiles = p->C * ntt;
@@ -233,7 +342,8 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
     p->scratch_hdr = hdr;
     p->scratch_bytes = hdr + vals + tails;
     p->buf_bytes = align_up((size_t)p->C * (size_t)p->N * sizeof(float));
-    const size_t nbuf = p->units.size() > 2 ? 2 : (p->units.size() == 2 ? 1 : 0);
+    size_t nbuf = p->units.size() > 2 ? 2 : (p->units.size() == 2 ? 1 : 0);
+    if (p->units.size() == 1 && p->units[0].tc) nbuf = 1;  // input copy for in-place operation
     p->ws_fused = p->scratch_bytes + nbuf * p->buf_bytes;
     p->ws_plain = (nst > 0 ? 2 : 0) * p->buf_bytes;
     return TFX_OK;
@@ -261,6 +371,34 @@ int exec_fused(tfx_plan* p, const float* x, float* y, void* ws, cudaStream_t s) 
                      reinterpret_cast<float*>(w + p->scratch_bytes + p->buf_bytes)};
     for (int i = 0; i < nu; ++i) {
         const HostUnit& u = p->units[i];
+        if (u.tc) {
+            FirTcArgs f{};
+            f.x = i == 0 ? x : buf[(i - 1) & 1];
+            f.ldx = i == 0 ? p->ld : p->N;
+            f.y = i == nu - 1 ? y : buf[i & 1];
+            f.ldy = i == nu - 1 ? p->ld : p->N;
+            if (f.x == f.y) {  // the halo is read from other tiles' input: copy it first
+                if (launch_copy_rows(f.x, buf[0], p->C, p->N, f.ldx, p->N, s) != cudaSuccess) return TFX_ERR_CUDA;
+                f.x = buf[0];
+                f.ldx = p->N;
+            }
+            f.C = p->C;
+            f.N = p->N;
+            f.ntt = u.ntt;
+            f.L = u.L;
+            f.W = u.W;
+            f.nK = u.nK;
+            f.NB = u.NB;
+            f.rows = u.rows;
+            f.tmem_cols = u.tmem_cols;
+            f.a_chunks = u.a_chunks;
+            f.plain_bf16 = (p->flags & TFX_PLAN_FIR_BF16_PLAIN) ? 1 : 0;
+            f.a_hi = reinterpret_cast<const uint4*>(p->dconst + u.off_ahi);
+            f.a_lo = reinterpret_cast<const uint4*>(p->dconst + u.off_alo);
+            f.status = p->dstatus;
+            if (launch_fir_tc(f, s) != cudaSuccess) return TFX_ERR_CUDA;
+            continue;
+        }
         UnitArgs a;
         a.x = i == 0 ? x : buf[(i - 1) & 1];
         a.ldx = i == 0 ? p->ld : p->N;

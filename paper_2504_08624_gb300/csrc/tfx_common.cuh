@@ -30,7 +30,7 @@ struct UnitConst {
     int H;             // FIR halo = L - 1 (0 without FIR)
     int nkb;           // FIR tap blocks of FIR_R (taps zero-padded to nkb*FIR_R)
     float gain;        // output scale when the unit ends without an FIR
-    const float* coef; // [S][8]: b0 b1 b2 a1 a2 (a0-normalised), 3 pad
+    const float* coef; // [S][8]: b0 c1 c2 a1 a2 (a0-normalised; c1 = b1 - a1 b0, c2 = b2 - a2 b0)
     const float4* pw;  // [S][NT+1]: A^k, A = chunk transfer matrix (row-major 2x2)
     const float* taps; // [nkb*FIR_R] FP32 taps, zero-padded
 };
@@ -54,6 +54,26 @@ struct UnitArgs {
     UnitScratch sc;
     int* status;     // device status word (TFX_OK or TFX_ERR_TIMEOUT)
     int64_t drop_tile;  // test hook: this tile never publishes (-1 = off)
+};
+
+// Tensor-core FIR (Toeplitz-block GEMM) launch arguments.
+struct FirTcArgs {
+    const float* x;
+    float* y;
+    int64_t ldx, ldy;
+    int64_t C, N;
+    int64_t ntt;      // tiles per channel (128 * NB output samples each)
+    int L;            // taps
+    int W;            // L - 1 rounded up to a multiple of 16
+    int nK;           // K-steps of 16: (W + 128) / 16
+    int NB;           // output blocks of 128 samples per tile (MMA N)
+    int rows;         // rows of the shared-memory signal window grid
+    int tmem_cols;    // TMEM columns allocated (power of two >= NB)
+    int a_chunks;     // 16-byte chunks per tap table = 2 * nK + 16
+    int plain_bf16;   // 1: hi*hi product only (accuracy-reduced mode)
+    const uint4* a_hi;  // [a_chunks][8 copies] BF16 high parts of the shifted taps
+    const uint4* a_lo;  // same, BF16 low parts
+    int* status;
 };
 
 // ---------------------------------------------------------------------------
@@ -124,6 +144,9 @@ cudaError_t launch_plain_fir(const float* x, float* y, int64_t C, int64_t N, int
 cudaError_t launch_copy_rows(const float* x, float* y, int64_t C, int64_t N, int64_t ldx,
                              int64_t ldy, cudaStream_t s);
 size_t unit_smem_bytes(const UnitConst& k);
+size_t fir_tc_smem_bytes(const FirTcArgs& a);
+cudaError_t prepare_fir_tc(size_t smem);
+cudaError_t launch_fir_tc(const FirTcArgs& a, cudaStream_t s);
 cudaError_t prepare_unit(const UnitConst& k);
 
 }  // namespace tfx
