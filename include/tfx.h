@@ -73,7 +73,8 @@ typedef struct {
 #define TFX_PLAN_DEFAULT 0u
 #define TFX_PLAN_FIR_CUDA_CORES 1u /* FIR stages on CUDA cores only (no tensor-core Toeplitz GEMM) */
 #define TFX_PLAN_UNFUSED 2u        /* one kernel per stage group; intermediates go through the workspace */
-#define TFX_PLAN_FIR_BF16_PLAIN 4u /* tensor-core FIR without the hi/lo correction (reported-only accuracy mode) */
+#define TFX_PLAN_FIR_BF16_PLAIN 4u /* tensor-core FIR, BF16 operands, no hi/lo correction (reported-only accuracy mode) */
+#define TFX_PLAN_FIR_BF16_SPLIT 8u /* tensor-core FIR with BF16 hi/lo operands instead of the default scaled FP16 hi/lo */
 /* Test hook for failure detection: the first tile of channel 0 never publishes
  * its carries, so its successor's bounded wait runs out; the execution
  * completes (with wrong output) and tfx_plan_get_error() returns
@@ -97,6 +98,11 @@ int tfx_plan_create(tfx_plan **p, int64_t C, int64_t N, int64_t ld,
 
 /* Bytes of device workspace tfx_plan_execute needs (0 if none). */
 size_t tfx_plan_workspace_size(const tfx_plan *p);
+
+/* Number of kernels one tfx_plan_execute launches (flag resets done with
+ * cudaMemsetAsync and input copies for in-place tensor-core FIRs excluded);
+ * -1 for a NULL plan. */
+int tfx_plan_launch_count(const tfx_plan *p);
 
 /*
  * tfx_plan_execute -- run the chain: y = chain(x).  Asynchronous on s.

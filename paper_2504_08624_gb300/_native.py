@@ -21,6 +21,7 @@ TFX_PLAN_DEFAULT = 0
 TFX_PLAN_FIR_CUDA_CORES = 1
 TFX_PLAN_UNFUSED = 2
 TFX_PLAN_FIR_BF16_PLAIN = 4
+TFX_PLAN_FIR_BF16_SPLIT = 8
 TFX_PLAN_TEST_DROP_PUBLISH = 256
 
 STATUS = {
@@ -30,7 +31,7 @@ STATUS = {
 
 # every symbol include/tfx.h declares
 EXPORTS = [
-    "tfx_plan_create", "tfx_plan_workspace_size", "tfx_plan_execute", "tfx_plan_execute_plain",
+    "tfx_plan_create", "tfx_plan_workspace_size", "tfx_plan_launch_count", "tfx_plan_execute", "tfx_plan_execute_plain",
     "tfx_plan_get_error", "tfx_plan_destroy", "tfx_fir", "tfx_sos", "tfx_chain",
     "tfx_chain_workspace_size", "tfx_cache_clear", "tfx_strerror", "tfx_version",
 ]
@@ -65,6 +66,8 @@ def lib():
     L.tfx_plan_create.restype = ctypes.c_int
     L.tfx_plan_workspace_size.argtypes = [vp]
     L.tfx_plan_workspace_size.restype = sz
+    L.tfx_plan_launch_count.argtypes = [vp]
+    L.tfx_plan_launch_count.restype = ctypes.c_int
     L.tfx_plan_execute.argtypes = [vp, fp, fp, vp, sz, vp]
     L.tfx_plan_execute.restype = ctypes.c_int
     L.tfx_plan_execute_plain.argtypes = [vp, fp, fp, vp, sz, vp]

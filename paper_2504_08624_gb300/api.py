@@ -105,6 +105,7 @@ class Plan:
             rc = N.lib().tfx_plan_create(ctypes.byref(self._h), self.C, self.N, self.ld, sl.arr, sl.n, flags)
         N.check(rc, "tfx_plan_create")
         self.workspace_size = int(N.lib().tfx_plan_workspace_size(self._h))
+        self.launches_per_execute = int(N.lib().tfx_plan_launch_count(self._h))
         self._ws = None
 
     def workspace(self) -> torch.Tensor:

@@ -23,21 +23,23 @@
 //    (column stride CS = rows * 16 bytes).  Block n's row is then n and the
 //    K-step k operand starts at column 2k % 16, row k / 8, with LBO = CS and
 //    SBO = 128 bytes.
-// FP32 accuracy from BF16 products: x = x_hi + x_lo and h = h_hi + h_lo (each
-// BF16, residual ~2^-17 relative); D = A_hi B_hi + A_hi B_lo + A_lo B_hi.
+// FP32-level accuracy from 16-bit products: x = x_hi + x_lo and h = h_hi + h_lo,
+// D = A_hi B_hi + A_hi B_lo + A_lo B_hi.  By default the parts are FP16 after
+// an exact power-of-two scaling (the tile's window max to [2^14, 2^15), the
+// taps likewise), leaving a residual of ~2^-22 of each product; the BF16
+// variant leaves ~2^-17, and plain BF16 (hi only) ~2^-9.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "tc_ptx.cuh"
 #include "tfx_common.cuh"
 
 namespace tfx {
 
-__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo_half, __nv_bfloat16 hi_half) {
-    return (uint32_t)__bfloat16_as_ushort(lo_half) | ((uint32_t)__bfloat16_as_ushort(hi_half) << 16);
-}
-
-// Split 8 consecutive samples into BF16 hi / lo parts packed as 16-byte chunks.
-__device__ __forceinline__ void split8(const float (&v)[8], uint4& hi, uint4& lo) {
+// Split 8 consecutive samples into hi / lo parts packed as 16-byte chunks:
+// BF16 hi + BF16 lo, or (after scaling by an exact power of two) FP16 hi +
+// FP16 lo.  The low part is the rounded residual v - hi, which is exact in FP32.
+__device__ __forceinline__ void split8_bf16(const float (&v)[8], uint4& hi, uint4& lo) {
     uint32_t h[4], l[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -45,11 +47,40 @@ __device__ __forceinline__ void split8(const float (&v)[8], uint4& hi, uint4& lo
         const __nv_bfloat16 h1 = __float2bfloat16_rn(v[2 * i + 1]);
         const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * i] - __bfloat162float(h0));
         const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * i + 1] - __bfloat162float(h1));
-        h[i] = pack_bf16x2(h0, h1);
-        l[i] = pack_bf16x2(l0, l1);
+        h[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+        l[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
     }
     hi = make_uint4(h[0], h[1], h[2], h[3]);
     lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+__device__ __forceinline__ void split8_f16(const float (&v)[8], float scale, uint4& hi, uint4& lo) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float s0 = v[2 * i] * scale, s1 = v[2 * i + 1] * scale;
+        const __half h0 = __float2half_rn(s0);
+        const __half h1 = __float2half_rn(s1);
+        const __half l0 = __float2half_rn(s0 - __half2float(h0));
+        const __half l1 = __float2half_rn(s1 - __half2float(h1));
+        h[i] = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
+        l[i] = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// 8 consecutive samples starting at t (zero outside [0, N)).
+__device__ __forceinline__ void load8(const float* xr, int64_t t, int64_t N, bool vec, float (&v)[8]) {
+    if (vec && t >= 0 && t + 8 <= N) {
+        const float4 p0 = *reinterpret_cast<const float4*>(xr + t);
+        const float4 p1 = *reinterpret_cast<const float4*>(xr + t + 4);
+        v[0] = p0.x; v[1] = p0.y; v[2] = p0.z; v[3] = p0.w;
+        v[4] = p1.x; v[5] = p1.y; v[6] = p1.z; v[7] = p1.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = (t + i >= 0 && t + i < N) ? xr[t + i] : 0.f;
+    }
 }
 
 __global__ void __launch_bounds__(256, 1) k_fir_tc(FirTcArgs a) {
@@ -73,7 +104,10 @@ __global__ void __launch_bounds__(256, 1) k_fir_tc(FirTcArgs a) {
         tc::tmem_alloc(tmem_slot, (uint32_t)a.tmem_cols);
         tc::tmem_relinquish();
     }
-    if (tid == 0) tc::mbar_init(bar, 1);
+    if (tid == 0) {
+        tc::mbar_init(bar, 1);
+        tc::mbar_init_fence();
+    }
 
     // taps: both interleaved tables, straight copies
     {
@@ -86,30 +120,47 @@ __global__ void __launch_bounds__(256, 1) k_fir_tc(FirTcArgs a) {
             dlo[i] = src_lo[i];
         }
     }
-    // signal window [t0 - W, t0 - W + rows*128) -> BF16 hi / lo chunks
-    {
-        const float* xr = a.x + c * a.ldx;
-        const int64_t s0 = t0 - a.W;
-        const int nchunks = rows * 16;
-        const bool vec = ((reinterpret_cast<uintptr_t>(xr + s0) & 15) == 0);
+    // signal window [t0 - W, t0 - W + rows*128) -> hi / lo chunks
+    __shared__ float s_red[8];
+    const float* xr = a.x + c * a.ldx;
+    const int64_t s0 = t0 - a.W;
+    const int nchunks = rows * 16;
+    const bool vec = ((reinterpret_cast<uintptr_t>(xr + s0) & 15) == 0);
+    const bool fp16 = a.mode == FIR_TC_FP16_SPLIT;
+    float xscale = 1.f, xunscale = 1.f;
+    if (fp16) {
+        // per-tile power-of-two scale: window max lands in [2^14, 2^15)
+        float m = 0.f;
         for (int g = tid; g < nchunks; g += blockDim.x) {
-            const int64_t t = s0 + 8 * (int64_t)g;
             float v[8];
-            if (vec && t >= 0 && t + 8 <= a.N) {
-                const float4 p0 = *reinterpret_cast<const float4*>(xr + t);
-                const float4 p1 = *reinterpret_cast<const float4*>(xr + t + 4);
-                v[0] = p0.x; v[1] = p0.y; v[2] = p0.z; v[3] = p0.w;
-                v[4] = p1.x; v[5] = p1.y; v[6] = p1.z; v[7] = p1.w;
-            } else {
+            load8(xr, s0 + 8 * (int64_t)g, a.N, vec, v);
 #pragma unroll
-                for (int i = 0; i < 8; ++i) v[i] = (t + i >= 0 && t + i < a.N) ? xr[t + i] : 0.f;
-            }
-            uint4 hi, lo;
-            split8(v, hi, lo);
-            const uint32_t off = (uint32_t)(g % 16) * CS + (uint32_t)(g / 16) * 16u;
-            *reinterpret_cast<uint4*>(B_hi + off) = hi;
-            *reinterpret_cast<uint4*>(B_lo + off) = lo;
+            for (int i = 0; i < 8; ++i) m = fmaxf(m, fabsf(v[i]));
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) s_red[warp] = m;
+        __syncthreads();
+        m = s_red[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, s_red[w]);
+        if (m > 0.f && isfinite(m)) {
+            int sh = 14 - ilogbf(m);
+            sh = sh > 126 ? 126 : (sh < -126 ? -126 : sh);
+            xscale = ldexpf(1.f, sh);
+            xunscale = ldexpf(1.f, -sh);
+        }
+    }
+    for (int g = tid; g < nchunks; g += blockDim.x) {
+        float v[8];
+        load8(xr, s0 + 8 * (int64_t)g, a.N, vec, v);
+        uint4 hi, lo;
+        if (fp16)
+            split8_f16(v, xscale, hi, lo);
+        else
+            split8_bf16(v, hi, lo);
+        const uint32_t off = (uint32_t)(g % 16) * CS + (uint32_t)(g / 16) * 16u;
+        *reinterpret_cast<uint4*>(B_hi + off) = hi;
+        *reinterpret_cast<uint4*>(B_lo + off) = lo;
     }
     tc::fence_proxy_async_smem();
     tc::tc_fence_before();
@@ -118,7 +169,7 @@ __global__ void __launch_bounds__(256, 1) k_fir_tc(FirTcArgs a) {
     const uint32_t tmem = *tmem_slot;
 
     if (tid == 0) {
-        const uint32_t idesc = tc::idesc_bf16_f32(128, a.NB);
+        const uint32_t idesc = tc::idesc_f16kind_f32(128, a.NB, !fp16);
         const uint32_t ahi = tc::smem_u32(A_hi), alo = tc::smem_u32(A_lo);
         const uint32_t bhi = tc::smem_u32(B_hi), blo = tc::smem_u32(B_lo);
         for (int k = 0; k < a.nK; ++k) {
@@ -127,7 +178,7 @@ __global__ void __launch_bounds__(256, 1) k_fir_tc(FirTcArgs a) {
             const uint64_t dah = tc::desc_noswz(ahi + aoff, 128u, 128u);
             const uint64_t dbh = tc::desc_noswz(bhi + boff, CS, 128u);
             tc::mma_bf16(tmem, dah, dbh, idesc, k > 0 ? 1u : 0u);
-            if (!a.plain_bf16) {
+            if (a.mode != FIR_TC_BF16_PLAIN) {
                 const uint64_t dal = tc::desc_noswz(alo + aoff, 128u, 128u);
                 const uint64_t dbl = tc::desc_noswz(blo + boff, CS, 128u);
                 tc::mma_bf16(tmem, dah, dbl, idesc, 1u);
@@ -149,6 +200,7 @@ __global__ void __launch_bounds__(256, 1) k_fir_tc(FirTcArgs a) {
             }
         }
     }
+    ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
     tc::tc_fence_after();
 
     if (ok) {
@@ -159,13 +211,14 @@ __global__ void __launch_bounds__(256, 1) k_fir_tc(FirTcArgs a) {
         const int l = quarter * 32 + lane;      // TMEM lane = 127 - phase
         const int phase = 127 - l;
         float* yr = a.y + c * a.ldy;
+        const float us = a.tap_unscale;
         for (int cc = col0; cc < col0 + nhalf; cc += 16) {
             float v[16];
             tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cc, v);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int64_t n = t0 + (int64_t)(cc + j) * 128 + phase;
-                if (n < a.N) yr[n] = v[j];
+                if (n < a.N) yr[n] = (v[j] * xunscale) * us;
             }
         }
     }

@@ -1,6 +1,7 @@
 // Host side of libtfx: argument validation, plan building (FP64 precompute of
 // device constants), workspace layout, launches, the one-shot plan cache and
 // the C-ABI entry points declared in include/tfx.h.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <list>
@@ -35,6 +36,8 @@ struct HostUnit {
     bool tc = false;
     int W = 0, nK = 0, NB = 0, rows = 0, tmem_cols = 0, a_chunks = 0;
     size_t off_ahi = 0, off_alo = 0, tc_smem = 0;
+    int tc_mode = 0;
+    float tap_unscale = 1.0f;
 };
 
 // Taps at or above this count go to the tensor cores (unless disabled).
@@ -105,6 +108,35 @@ uint16_t f2bf(float f) {
     if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;
     u += 0x7fffu + ((u >> 16) & 1u);
     return (uint16_t)(u >> 16);
+}
+// Round-to-nearest-even FP32 -> IEEE FP16 bits (subnormals included), and back.
+uint16_t f2h(float f) {
+    uint32_t x;
+    std::memcpy(&x, &f, 4);
+    const uint32_t sign = (x >> 16) & 0x8000u;
+    const uint32_t mant = x & 0x7fffffu;
+    const int exp = (int)((x >> 23) & 0xffu);
+    if (exp == 0xff) return (uint16_t)(sign | 0x7c00u | (mant ? 0x200u : 0u));
+    const int e = exp - 127;
+    if (e > 15) return (uint16_t)(sign | 0x7c00u);
+    if (e >= -14) {
+        uint32_t h = ((uint32_t)(e + 15) << 10) | (mant >> 13);
+        const uint32_t rem = mant & 0x1fffu;
+        if (rem > 0x1000u || (rem == 0x1000u && (h & 1u))) h += 1u;
+        return (uint16_t)(sign | h);
+    }
+    if (e < -25 || exp == 0) return (uint16_t)sign;
+    const uint32_t m = mant | 0x800000u;
+    const int shift = -e - 1;
+    uint32_t r = m >> shift;
+    const uint32_t rem = m & ((1u << shift) - 1u), half = 1u << (shift - 1);
+    if (rem > half || (rem == half && (r & 1u))) r += 1u;
+    return (uint16_t)(sign | r);
+}
+double h2d(uint16_t h) {
+    const int e = (h >> 10) & 0x1f, m = h & 0x3ff;
+    const double v = e == 0 ? std::ldexp((double)m, -24) : std::ldexp(1.0 + m / 1024.0, e - 15);
+    return (h & 0x8000u) ? -v : v;
 }
 float bf2f(uint16_t b) {
     uint32_t u = (uint32_t)b << 16;
@@ -272,18 +304,35 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         float* taps = reinterpret_cast<float*>(host.data() + u.off_taps);
         for (int k = 0; k < u.L; ++k) taps[k] = (float)u.taps[k];
         if (u.tc) {
-            // g[v] = h[W + 127 - v]; chunk j, copy b holds g[8j + b .. 8j + b + 7]
+            // g[v] = h[W + 127 - v]; chunk j, copy b holds g[8j + b .. 8j + b + 7].
+            // FP16 mode: taps scaled by 2^e so that max|h| lands in [2^14, 2^15).
+            u.tc_mode = (p->flags & TFX_PLAN_FIR_BF16_PLAIN) ? FIR_TC_BF16_PLAIN
+                        : (p->flags & TFX_PLAN_FIR_BF16_SPLIT) ? FIR_TC_BF16_SPLIT : FIR_TC_FP16_SPLIT;
+            double hmax = 0.0;
+            for (double v : u.taps) hmax = std::max(hmax, std::fabs(v));
+            int sh = 0;
+            if (u.tc_mode == FIR_TC_FP16_SPLIT && hmax > 0.0) {
+                sh = 14 - std::ilogb(hmax);
+                sh = sh > 126 ? 126 : (sh < -126 ? -126 : sh);
+            }
+            u.tap_unscale = (float)std::ldexp(1.0, -sh);
             uint16_t* hi = reinterpret_cast<uint16_t*>(host.data() + u.off_ahi);
             uint16_t* lo = reinterpret_cast<uint16_t*>(host.data() + u.off_alo);
             for (int j = 0; j < u.a_chunks; ++j)
                 for (int b = 0; b < 8; ++b)
                     for (int d = 0; d < 8; ++d) {
                         const long idx = (long)u.W + 127 - (8L * j + b + d);
-                        const double h = (idx >= 0 && idx < u.L) ? u.taps[idx] : 0.0;
-                        const uint16_t bh = f2bf((float)h);
-                        const uint16_t bl = f2bf((float)(h - (double)bf2f(bh)));
-                        hi[(j * 8 + b) * 8 + d] = bh;
-                        lo[(j * 8 + b) * 8 + d] = bl;
+                        const double h = (idx >= 0 && idx < u.L) ? std::ldexp(u.taps[idx], sh) : 0.0;
+                        uint16_t vh, vl;
+                        if (u.tc_mode == FIR_TC_FP16_SPLIT) {
+                            vh = f2h((float)h);
+                            vl = f2h((float)(h - h2d(vh)));
+                        } else {
+                            vh = f2bf((float)h);
+                            vl = f2bf((float)(h - (double)bf2f(vh)));
+                        }
+                        hi[(j * 8 + b) * 8 + d] = vh;
+                        lo[(j * 8 + b) * 8 + d] = vl;
                     }
         }
     }
@@ -392,7 +441,8 @@ int exec_fused(tfx_plan* p, const float* x, float* y, void* ws, cudaStream_t s) 
             f.rows = u.rows;
             f.tmem_cols = u.tmem_cols;
             f.a_chunks = u.a_chunks;
-            f.plain_bf16 = (p->flags & TFX_PLAN_FIR_BF16_PLAIN) ? 1 : 0;
+            f.mode = u.tc_mode;
+            f.tap_unscale = u.tap_unscale;
             f.a_hi = reinterpret_cast<const uint4*>(p->dconst + u.off_ahi);
             f.a_lo = reinterpret_cast<const uint4*>(p->dconst + u.off_alo);
             f.status = p->dstatus;
@@ -555,7 +605,8 @@ int tfx_plan_create(tfx_plan** out, int64_t C, int64_t N, int64_t ld, const tfx_
     if (rc != TFX_OK) return rc;
     rc = validate_stages(st, nst);
     if (rc != TFX_OK) return rc;
-    if (flags & ~(TFX_PLAN_FIR_CUDA_CORES | TFX_PLAN_UNFUSED | TFX_PLAN_FIR_BF16_PLAIN | TFX_PLAN_TEST_DROP_PUBLISH))
+    if (flags & ~(TFX_PLAN_FIR_CUDA_CORES | TFX_PLAN_UNFUSED | TFX_PLAN_FIR_BF16_PLAIN | TFX_PLAN_FIR_BF16_SPLIT |
+                  TFX_PLAN_TEST_DROP_PUBLISH))
         return TFX_ERR_INVALID;
     tfx_plan* p = new (std::nothrow) tfx_plan();
     if (!p) return TFX_ERR_NOMEM;
@@ -575,6 +626,12 @@ int tfx_plan_create(tfx_plan** out, int64_t C, int64_t N, int64_t ld, const tfx_
 size_t tfx_plan_workspace_size(const tfx_plan* p) {
     if (!p) return 0;
     return p->ws_fused > p->ws_plain ? p->ws_fused : p->ws_plain;
+}
+
+int tfx_plan_launch_count(const tfx_plan* p) {
+    if (!p) return -1;
+    if (p->C == 0 || p->N == 0) return 0;
+    return p->units.empty() ? 1 : (int)p->units.size();
 }
 
 int tfx_plan_execute(tfx_plan* p, const float* x, float* y, void* ws, size_t ws_bytes, tfx_stream s) {

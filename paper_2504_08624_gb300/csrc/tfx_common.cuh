@@ -56,6 +56,9 @@ struct UnitArgs {
     int64_t drop_tile;  // test hook: this tile never publishes (-1 = off)
 };
 
+// Operand precision of the tensor-core FIR.
+enum { FIR_TC_FP16_SPLIT = 0, FIR_TC_BF16_SPLIT = 1, FIR_TC_BF16_PLAIN = 2 };
+
 // Tensor-core FIR (Toeplitz-block GEMM) launch arguments.
 struct FirTcArgs {
     const float* x;
@@ -70,9 +73,10 @@ struct FirTcArgs {
     int rows;         // rows of the shared-memory signal window grid
     int tmem_cols;    // TMEM columns allocated (power of two >= NB)
     int a_chunks;     // 16-byte chunks per tap table = 2 * nK + 16
-    int plain_bf16;   // 1: hi*hi product only (accuracy-reduced mode)
-    const uint4* a_hi;  // [a_chunks][8 copies] BF16 high parts of the shifted taps
-    const uint4* a_lo;  // same, BF16 low parts
+    int mode;         // FIR_TC_FP16_SPLIT, FIR_TC_BF16_SPLIT or FIR_TC_BF16_PLAIN
+    float tap_unscale;  // 1 / (power-of-two scale applied to the FP16 taps)
+    const uint4* a_hi;  // [a_chunks][8 copies] high parts of the shifted (scaled) taps
+    const uint4* a_lo;  // same, low parts
     int* status;
 };
 

@@ -198,3 +198,31 @@ def test_plan_reuse_and_graph_capture():
     torch.cuda.synchronize()
     assert_close(y.cpu().numpy(), oracle_chain(x, wl.stages), wl.tol, "graph replay")
     p.close()
+
+
+@pytest.mark.parametrize("mode", ["fp16_split", "bf16_split", "bf16_plain", "cuda_cores"])
+def test_fir_precision_modes(mode):
+    """Tensor-core FIR operand modes against the oracle (white noise, 1025-tap
+    low-pass): scaled FP16 hi/lo (default) and BF16 hi/lo meet 1e-5 of the
+    peak; plain BF16 is an accuracy-reduced mode whose error is reported."""
+    from paper_2504_08624_gb300 import _native as N
+    flags = {"fp16_split": 0, "bf16_split": N.TFX_PLAN_FIR_BF16_SPLIT,
+             "bf16_plain": N.TFX_PLAN_FIR_BF16_PLAIN, "cuda_cores": N.TFX_PLAN_FIR_CUDA_CORES}[mode]
+    x = W.white_gauss(3, 2 * 16384 + 999, 21)
+    h = W.fir_lowpass(1025, 16000.0, 48000.0)
+    got = run(x, [("fir", h)], flags=flags)
+    ref = oracle_chain(x, [("fir", h)])
+    if mode == "bf16_plain":
+        from tests.gpu_util import per_channel_rel_err
+        rel = per_channel_rel_err(got, ref)[0].max()
+        assert 1e-5 < rel < 1e-2, rel
+    else:
+        assert_close(got, ref, 1e-5, mode)
+
+
+def test_strongly_attenuating_chain():
+    """Output ~70 dB below the input: the FIR sums terms that cancel to 1e-3 of
+    their magnitude.  The default scaled-FP16 split still meets 1e-4."""
+    stages = W.random_chain(5)
+    x = W.white_uniform(3, 48495, 505)
+    check(x, stages)
