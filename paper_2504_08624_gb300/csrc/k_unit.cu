@@ -18,7 +18,8 @@
 //   3. decoupled look-back across tiles of the same channel (tile transfer
 //      A^NT) for the tile's incoming state, with bounded waits;
 //   4. fix-up: y = y_zs + the homogeneous response from the true chunk start
-//      state, y_h[t] = -a1 y_h[t-1] - a2 y_h[t-2].
+//      state, y_h[t] = -a1 y_h[t-1] - a2 y_h[t-2] (done inside the next
+//      section's zero-state pass).
 // The FIR then reads the cascade output of this tile plus the last L-1
 // cascade outputs of the preceding tile(s), which each tile publishes to
 // scratch before the successor needs them (so x == y is safe).
@@ -93,7 +94,7 @@ __device__ __forceinline__ void fir_block(const float* __restrict__ win, const f
 }
 
 template <bool HAS_FIR>
-__global__ void __launch_bounds__(NT, 2) k_unit(UnitArgs a) {
+__global__ void __launch_bounds__(NT, HAS_FIR ? 2 : 3) k_unit(UnitArgs a) {
     constexpr int T = T_CHUNK;
     extern __shared__ float4 smem_f4[];
     float* smem = reinterpret_cast<float*>(smem_f4);
@@ -115,24 +116,47 @@ __global__ void __launch_bounds__(NT, 2) k_unit(UnitArgs a) {
     float u[T];
     load_chunk<T>(a.x + c * a.ldx, t0 + (int64_t)tid * T, a.N, u);
 
-    for (int s = 0; s < S; ++s) {
-        const float* cf = a.k.coef + 8 * s;
-        const float b0 = cf[0], c1 = cf[1], c2 = cf[2], a1 = cf[3], a2 = cf[4];
-        const float4* P = a.k.pw + (size_t)s * (NT + 1);
-
-        // 1. zero-state pass.  State (w1, w2) of the transposed direct form II,
-        // updated as w1' = c1 u - a1 w1 + w2, w2' = c2 u - a2 w1, y = b0 u + w1
-        // with c1 = b1 - a1 b0, c2 = b2 - a2 b0 formed in FP64 at plan time (this
-        // avoids the cancellation of b1 u against a1 y when b ~ a).
-        float w1 = 0.f, w2 = 0.f;
+    // Section s's zero-state pass runs fused with the fix-up of section s-1:
+    // the fix-up adds the homogeneous response of s-1 from its true chunk start
+    // state (yh[t] = -a1 yh[t-1] - a2 yh[t-2]) sample by sample, and the sum is
+    // section s's input.
+    float2 st = make_float2(0.f, 0.f);  // true chunk start state of the previous section
+    float pa1 = 0.f, pa2 = 0.f;         // its feedback coefficients
+    for (int s = 0; s <= S; ++s) {
+        const bool fix = s > 0, run = s < S;
+        float b0 = 0.f, c1 = 0.f, c2 = 0.f, a1 = 0.f, a2 = 0.f;
+        if (run) {
+            const float* cf = a.k.coef + 8 * s;
+            b0 = cf[0]; c1 = cf[1]; c2 = cf[2]; a1 = cf[3]; a2 = cf[4];
+        }
+        // 1. (fix-up of s-1 +) zero-state pass of s.  State (w1, w2) of the
+        // transposed direct form II, updated as w1' = c1 u - a1 w1 + w2,
+        // w2' = c2 u - a2 w1, y = b0 u + w1, with c1 = b1 - a1 b0, c2 = b2 - a2 b0
+        // formed in FP64 at plan time (avoids cancelling b1 u against a1 y).
+        float w1 = 0.f, w2 = 0.f, h1 = 0.f, h2 = 0.f;
 #pragma unroll
         for (int t = 0; t < T; ++t) {
-            const float ut = u[t];
-            u[t] = fmaf(b0, ut, w1);
-            const float n1 = fmaf(c1, ut, fmaf(-a1, w1, w2));
-            w2 = fmaf(c2, ut, -a2 * w1);
-            w1 = n1;
+            float v = u[t];
+            if (fix) {
+                float h;
+                if (t == 0) h = st.x;
+                else if (t == 1) h = fmaf(-pa1, h1, st.y);
+                else h = fmaf(-pa1, h1, -pa2 * h2);
+                h2 = h1;
+                h1 = h;
+                v += h;
+            }
+            if (run) {
+                u[t] = fmaf(b0, v, w1);
+                const float n1 = fmaf(c1, v, fmaf(-a1, w1, w2));
+                w2 = fmaf(c2, v, -a2 * w1);
+                w1 = n1;
+            } else {
+                u[t] = v;
+            }
         }
+        if (!run) break;
+        const float4* P = a.k.pw + (size_t)s * (NT + 1);
 
         // 2. warp inclusive scan: v_l = sum_{m<=l} A^m e_{l-m}
         float2 v = make_float2(w1, w2);
@@ -158,14 +182,15 @@ __global__ void __launch_bounds__(NT, 2) k_unit(UnitArgs a) {
             X.x += s_tot[w].x;
             X.y += s_tot[w].y;
         }
-        float2 st = (lane > 0) ? make_float2(px, py) : make_float2(0.f, 0.f);
+        st = (lane > 0) ? make_float2(px, py) : make_float2(0.f, 0.f);
         {
             const float2 t2 = mv2(P[lane], X);
             st.x += t2.x;
             st.y += t2.y;
         }
 
-        // 3. tile aggregate and decoupled look-back (one thread)
+        // 3. tile aggregate and decoupled look-back (one thread).  A release
+        // store publishes a flag after its data; readers acquire the flag.
         if (tid == 0) {
             float2 agg = make_float2(0.f, 0.f);
             for (int w = 0; w < NWARP; ++w) {
@@ -177,36 +202,39 @@ __global__ void __launch_bounds__(NT, 2) k_unit(UnitArgs a) {
             const bool pub = tile != a.drop_tile;
             if (tt == 0) {
                 vl[s] = make_float4(agg.x, agg.y, agg.x, agg.y);
-                __threadfence();
                 if (pub) st_release_u32(&fl[s], 2u);
             } else {
-                vl[s] = make_float4(agg.x, agg.y, 0.f, 0.f);
-                __threadfence();
-                if (pub) st_release_u32(&fl[s], 1u);
                 const float4 AT = P[NT];
-                float4 Mp = make_float4(1.f, 0.f, 0.f, 1.f);
                 int64_t j = tile - a.C;
-                for (;;) {
-                    const unsigned f = wait_flag(a.sc.flags + j * (S + 1) + s, 1u, a.status);
-                    if (f == 0u) break;  // gave up: status word records the timeout
+                unsigned f = ld_acquire_u32(a.sc.flags + j * (S + 1) + s);
+                if (f >= 2u) {  // predecessor already inclusive: no aggregate needed
                     const float4 pv = ld_relaxed_f4(a.sc.vals + j * S + s);
-                    if (f >= 2u) {
-                        const float2 t2 = mv2(Mp, make_float2(pv.z, pv.w));
+                    win = make_float2(pv.z, pv.w);
+                } else {
+                    vl[s] = make_float4(agg.x, agg.y, 0.f, 0.f);
+                    if (pub) st_release_u32(&fl[s], 1u);
+                    float4 Mp = make_float4(1.f, 0.f, 0.f, 1.f);
+                    for (;;) {
+                        f = wait_flag(a.sc.flags + j * (S + 1) + s, 1u, a.status);
+                        if (f == 0u) break;  // gave up: status word records the timeout
+                        const float4 pv = ld_relaxed_f4(a.sc.vals + j * S + s);
+                        if (f >= 2u) {
+                            const float2 t2 = mv2(Mp, make_float2(pv.z, pv.w));
+                            win.x += t2.x;
+                            win.y += t2.y;
+                            break;
+                        }
+                        const float2 t2 = mv2(Mp, make_float2(pv.x, pv.y));
                         win.x += t2.x;
                         win.y += t2.y;
-                        break;
+                        Mp = mm2(Mp, AT);
+                        j -= a.C;
                     }
-                    const float2 t2 = mv2(Mp, make_float2(pv.x, pv.y));
-                    win.x += t2.x;
-                    win.y += t2.y;
-                    Mp = mm2(Mp, AT);
-                    j -= a.C;
                 }
                 float2 incl = mv2(AT, win);
                 incl.x += agg.x;
                 incl.y += agg.y;
                 vl[s] = make_float4(agg.x, agg.y, incl.x, incl.y);
-                __threadfence();
                 if (pub) st_release_u32(&fl[s], 2u);
             }
             s_win = win;
@@ -217,19 +245,8 @@ __global__ void __launch_bounds__(NT, 2) k_unit(UnitArgs a) {
             st.x += t2.x;
             st.y += t2.y;
         }
-
-        // 4. fix-up with the homogeneous response from the true start state
-        float p = st.x;
-        float q = fmaf(-a1, st.x, st.y);
-        u[0] += p;
-        u[1] += q;
-#pragma unroll
-        for (int t = 2; t < T; ++t) {
-            const float r = fmaf(-a1, q, -a2 * p);
-            u[t] += r;
-            p = q;
-            q = r;
-        }
+        pa1 = a1;
+        pa2 = a2;
     }
 
     if constexpr (!HAS_FIR) {
