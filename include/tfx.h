@@ -163,6 +163,33 @@ size_t tfx_chain_workspace_size(int64_t C, int64_t N, int64_t ld,
 /* Release every cached one-shot plan (synchronises the device). */
 void tfx_cache_clear(void);
 
+/*
+ * tfx_sos_noalloc -- the SOS cascade of tfx_sos for callers that cannot
+ * allocate device memory: code running in a real-time audio callback or a
+ * plug-in host, where cudaMalloc's implicit device synchronisation and
+ * unbounded latency are not allowed, and programs whose device memory is all
+ * reserved up front by an allocator they do not control.  The paper has no
+ * counterpart; it is an extra entry point of this library.
+ *
+ * Same arguments, layout and result as tfx_sos (x == y allowed).  The call
+ * makes no cudaMalloc / cudaFree and uses no allocating library routine: the
+ * scan's scratch (tile ticket, status word, look-back flags and carries) and
+ * the section constants live in one fixed static device array of about 5.4 MB
+ * that every GPU loading the library holds until the process exits.
+ * Limits: sections <= 8 and C * ceil(N / 8192) <= 32768 (for example 64
+ * channels of up to 4.19 M samples); larger requests return
+ * TFX_ERR_UNSUPPORTED before anything is enqueued.
+ * The first call on a device looks up the array's device address (a host
+ * synchronising runtime query), so make that first call before any stream
+ * capture on that device.  All calls share the one array: calls whose work
+ * overlaps on the GPU (different streams, or host threads racing) corrupt
+ * each other's results; calls ordered on one stream are safe.  Device-side
+ * timeouts are not reported (there is no plan to hold a status).
+ * Errors: TFX_ERR_INVALID, TFX_ERR_UNSTABLE, TFX_ERR_UNSUPPORTED, TFX_ERR_CUDA.
+ */
+int tfx_sos_noalloc(const float *x, float *y, int64_t C, int64_t N, int64_t ld,
+                    const double *sos, int32_t sections, tfx_stream s);
+
 /* Human-readable name of a tfx_status. */
 const char *tfx_strerror(int status);
 
