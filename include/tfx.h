@@ -173,8 +173,8 @@ void tfx_cache_clear(void);
  *
  * Same arguments, layout and result as tfx_sos (x == y allowed).  The call
  * makes no cudaMalloc / cudaFree and uses no allocating library routine: the
- * scan's scratch (tile ticket, status word, look-back flags and carries) and
- * the section constants live in one fixed static device array of about 5.4 MB
+ * scan's scratch (tile ticket, status word, look-back carries) and the
+ * section constants live in one fixed static device array of about 4.2 MB
  * that every GPU loading the library holds until the process exits.
  * Limits: sections <= 8 and C * ceil(N / 8192) <= 32768 (for example 64
  * channels of up to 4.19 M samples); larger requests return

@@ -16,7 +16,8 @@
 //   2. warp Kogge-Stone scan of (A, e) using the powers A^1..A^16, then a
 //      Horner combination of the 8 warp totals with A^32;
 //   3. decoupled look-back across tiles of the same channel (tile transfer
-//      A^NT) for the tile's incoming state, with bounded waits;
+//      A^NT) for the tile's incoming state, with bounded waits; each carry
+//      and its status travel in one 16-byte word;
 //   4. fix-up: y = y_zs + the homogeneous response from the true chunk start
 //      state, y_h[t] = -a1 y_h[t-1] - a2 y_h[t-2] (done inside the next
 //      section's zero-state pass).
@@ -110,8 +111,6 @@ __global__ void __launch_bounds__(NT, HAS_FIR ? 2 : 3) k_unit(UnitArgs a) {
     const int64_t tt = tile / a.C;
     const int64_t t0 = tt * TILE;
     const int S = a.k.S;
-    unsigned* fl = a.sc.flags + tile * (S + 1);
-    float4* vl = a.sc.vals + tile * S;
 
     float u[T];
     load_chunk<T>(a.x + c * a.ldx, t0 + (int64_t)tid * T, a.N, u);
@@ -189,8 +188,9 @@ __global__ void __launch_bounds__(NT, HAS_FIR ? 2 : 3) k_unit(UnitArgs a) {
             st.y += t2.y;
         }
 
-        // 3. tile aggregate and decoupled look-back (one thread).  A release
-        // store publishes a flag after its data; readers acquire the flag.
+        // 3. tile aggregate and decoupled look-back (one thread).  Carries are
+        // published and read as single 16-byte words (status travels with the
+        // value), so neither side needs a fence.
         if (tid == 0) {
             float2 agg = make_float2(0.f, 0.f);
             for (int w = 0; w < NWARP; ++w) {
@@ -200,42 +200,35 @@ __global__ void __launch_bounds__(NT, HAS_FIR ? 2 : 3) k_unit(UnitArgs a) {
             }
             float2 win = make_float2(0.f, 0.f);
             const bool pub = tile != a.drop_tile;
+            Carry* mine = a.sc.carry + tile * S + s;
             if (tt == 0) {
-                vl[s] = make_float4(agg.x, agg.y, agg.x, agg.y);
-                if (pub) st_release_u32(&fl[s], 2u);
+                if (pub) publish_carry(mine, 2u, agg);
             } else {
                 const float4 AT = P[NT];
                 int64_t j = tile - a.C;
-                unsigned f = ld_acquire_u32(a.sc.flags + j * (S + 1) + s);
+                float2 pv;
+                unsigned f = read_carry(a.sc.carry + j * S + s, pv);
                 if (f >= 2u) {  // predecessor already inclusive: no aggregate needed
-                    const float4 pv = ld_relaxed_f4(a.sc.vals + j * S + s);
-                    win = make_float2(pv.z, pv.w);
+                    win = pv;
                 } else {
-                    vl[s] = make_float4(agg.x, agg.y, 0.f, 0.f);
-                    if (pub) st_release_u32(&fl[s], 1u);
+                    if (pub) publish_carry(mine, 1u, agg);
                     float4 Mp = make_float4(1.f, 0.f, 0.f, 1.f);
                     for (;;) {
-                        f = wait_flag(a.sc.flags + j * (S + 1) + s, 1u, a.status);
+                        if (f == 0u) f = wait_carry(a.sc.carry + j * S + s, pv, a.status);
                         if (f == 0u) break;  // gave up: status word records the timeout
-                        const float4 pv = ld_relaxed_f4(a.sc.vals + j * S + s);
-                        if (f >= 2u) {
-                            const float2 t2 = mv2(Mp, make_float2(pv.z, pv.w));
-                            win.x += t2.x;
-                            win.y += t2.y;
-                            break;
-                        }
-                        const float2 t2 = mv2(Mp, make_float2(pv.x, pv.y));
+                        const float2 t2 = mv2(Mp, pv);
                         win.x += t2.x;
                         win.y += t2.y;
+                        if (f >= 2u) break;
                         Mp = mm2(Mp, AT);
                         j -= a.C;
+                        f = read_carry(a.sc.carry + j * S + s, pv);
                     }
                 }
                 float2 incl = mv2(AT, win);
                 incl.x += agg.x;
                 incl.y += agg.y;
-                vl[s] = make_float4(agg.x, agg.y, incl.x, incl.y);
-                if (pub) st_release_u32(&fl[s], 2u);
+                if (pub) publish_carry(mine, 2u, incl);
             }
             s_win = win;
         }
@@ -272,7 +265,7 @@ __global__ void __launch_bounds__(NT, HAS_FIR ? 2 : 3) k_unit(UnitArgs a) {
             for (int i = tid; i < tl; i += NT) dst[i] = win[wphys(FIR_PAD + H + TILE - tl + i)];
             __threadfence();
             __syncthreads();
-            if (tid == 0 && tile != a.drop_tile) st_release_u32(&fl[S], 1u);
+            if (tid == 0 && tile != a.drop_tile) st_release_u32(a.sc.flags + tile, 1u);
         }
 
         // halo: samples [t0 - H, t0) at window positions [FIR_PAD, FIR_PAD + H)
@@ -283,7 +276,7 @@ __global__ void __launch_bounds__(NT, HAS_FIR ? 2 : 3) k_unit(UnitArgs a) {
                 break;
             }
             const int64_t jt = tile - (int64_t)qb * a.C;
-            if (tid == 0) wait_flag(a.sc.flags + jt * (S + 1) + S, 1u, a.status);
+            if (tid == 0) wait_flag(a.sc.flags + jt, 1u, a.status);
             __syncthreads();
             const float* src = a.sc.tails + jt * (int64_t)tl;
             const int nq = remaining < tl ? remaining : tl;

@@ -1,6 +1,6 @@
 // tfx_sos_noalloc: the SOS-cascade scan for callers that must not allocate
 // device memory (see include/tfx.h).  Everything the scan kernel needs beyond
-// x and y -- its tile ticket, status word, look-back flags and carries, and the
+// x and y -- its tile ticket, status word, look-back carries, and the
 // per-section constants -- lives in one file-scope static device array of fixed
 // size, so a call makes no cudaMalloc / cudaFree and uses no allocating
 // library routine.
@@ -18,15 +18,13 @@ constexpr int64_t NA_MAX_TILES = 32768;  // C * ceil(N / 8192)
 // Layout of the static array (byte offsets).
 constexpr size_t NA_OFF_TICKET = 0;
 constexpr size_t NA_OFF_STATUS = 128;
-constexpr size_t NA_OFF_FLAGS = 256;
-constexpr size_t NA_FLAGS_BYTES = (size_t)NA_MAX_TILES * (NA_MAX_SECTIONS + 1) * sizeof(unsigned);
-constexpr size_t NA_OFF_VALS = NA_OFF_FLAGS + NA_FLAGS_BYTES;
-constexpr size_t NA_VALS_BYTES = (size_t)NA_MAX_TILES * NA_MAX_SECTIONS * sizeof(float4);
-constexpr size_t NA_OFF_COEF = NA_OFF_VALS + NA_VALS_BYTES;
+constexpr size_t NA_OFF_CARRY = 256;
+constexpr size_t NA_CARRY_BYTES = (size_t)NA_MAX_TILES * NA_MAX_SECTIONS * sizeof(Carry);
+constexpr size_t NA_OFF_COEF = NA_OFF_CARRY + NA_CARRY_BYTES;
 constexpr size_t NA_COEF_BYTES = (size_t)NA_MAX_SECTIONS * 8 * sizeof(float);
 constexpr size_t NA_OFF_PW = NA_OFF_COEF + NA_COEF_BYTES;
 constexpr size_t NA_PW_BYTES = (size_t)NA_MAX_SECTIONS * (NT + 1) * sizeof(float4);
-constexpr size_t NA_BYTES = NA_OFF_PW + NA_PW_BYTES;  // about 5.4 MB
+constexpr size_t NA_BYTES = NA_OFF_PW + NA_PW_BYTES;  // about 4.2 MB
 
 constexpr int NA_MAX_DEVICES = 64;
 
@@ -118,8 +116,8 @@ extern "C" int tfx_sos_noalloc(const float* x, float* y, int64_t C, int64_t N, i
     int rc = na_scratch(&base);
     if (rc != TFX_OK) return rc;
     const int64_t tiles = C * ntt;
-    // ticket, status word and look-back flags must start at zero
-    if (cudaMemsetAsync(base, 0, NA_OFF_FLAGS + (size_t)tiles * (sections + 1) * sizeof(unsigned), s) != cudaSuccess)
+    // ticket, status word and look-back carries must start at zero
+    if (cudaMemsetAsync(base, 0, NA_OFF_CARRY + (size_t)tiles * sections * sizeof(Carry), s) != cudaSuccess)
         return TFX_ERR_CUDA;
     if (cudaMemcpyAsync(base + NA_OFF_COEF, coef, (size_t)sections * 8 * sizeof(float), cudaMemcpyHostToDevice,
                         s) != cudaSuccess)
@@ -145,8 +143,8 @@ extern "C" int tfx_sos_noalloc(const float* x, float* y, int64_t C, int64_t N, i
     a.k.pw = reinterpret_cast<const float4*>(base + NA_OFF_PW);
     a.k.taps = nullptr;
     a.sc.ticket = reinterpret_cast<unsigned*>(base + NA_OFF_TICKET);
-    a.sc.flags = reinterpret_cast<unsigned*>(base + NA_OFF_FLAGS);
-    a.sc.vals = reinterpret_cast<float4*>(base + NA_OFF_VALS);
+    a.sc.flags = nullptr;  // no FIR: no tails to flag
+    a.sc.carry = reinterpret_cast<Carry*>(base + NA_OFF_CARRY);
     a.sc.tails = nullptr;
     a.sc.tail_len = 0;
     a.status = reinterpret_cast<int*>(base + NA_OFF_STATUS);

@@ -60,8 +60,8 @@ struct tfx_plan {
     char* dconst = nullptr;
     int* dstatus = nullptr;
     // workspace layout
-    size_t scratch_hdr = 0;    // ticket + flags (memset per unit execution)
-    size_t scratch_bytes = 0;  // header + vals + tails
+    size_t scratch_hdr = 0;    // ticket + tail flags + carries (memset per unit execution)
+    size_t scratch_bytes = 0;  // header + tails
     size_t buf_bytes = 0;      // one intermediate [C x N] buffer
     size_t ws_fused = 0, ws_plain = 0;
 };
@@ -371,7 +371,7 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
 
     // workspace layout
     const int64_t ntt = p->N > 0 ? (p->N + TILE - 1) / TILE : 0;
-    size_t hdr = 0, vals = 0, tails = 0;
+    size_t hdr = 0, tails = 0;
     for (HostUnit& u : p->units) {
         u.ntt = ntt;
         if (u.tc) {
@@ -381,15 +381,15 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         const int H = u.L > 0 ? u.L - 1 : 0;
         u.tail_len = u.L > 0 ? (H < TILE ? H : TILE) : 0;
         const int64_t tiles = p->C * ntt;
-        u.flags_bytes = (size_t)tiles * (u.S + 1) * sizeof(unsigned);
-        u.vals_bytes = (size_t)tiles * u.S * sizeof(float4);
+        u.flags_bytes = align_up((size_t)tiles * sizeof(unsigned));
+        u.vals_bytes = (size_t)tiles * u.S * sizeof(Carry);
         u.tails_bytes = (size_t)tiles * u.tail_len * sizeof(float);
-        hdr = std::max(hdr, align_up(ALIGN + u.flags_bytes));
-        vals = std::max(vals, align_up(u.vals_bytes));
+        // header = ticket, tail flags and carries: all reset per execution
+        hdr = std::max(hdr, align_up(ALIGN + u.flags_bytes + u.vals_bytes));
         tails = std::max(tails, align_up(u.tails_bytes));
     }
     p->scratch_hdr = hdr;
-    p->scratch_bytes = hdr + vals + tails;
+    p->scratch_bytes = hdr + tails;
     p->buf_bytes = align_up((size_t)p->C * (size_t)p->N * sizeof(float));
     size_t nbuf = p->units.size() > 2 ? 2 : (p->units.size() == 2 ? 1 : 0);
     if (p->units.size() == 1 && p->units[0].tc) nbuf = 1;  // input copy for in-place operation
@@ -467,12 +467,12 @@ int exec_fused(tfx_plan* p, const float* x, float* y, void* ws, cudaStream_t s) 
         a.k.taps = reinterpret_cast<const float*>(p->dconst + u.off_taps);
         a.sc.ticket = reinterpret_cast<unsigned*>(scratch);
         a.sc.flags = reinterpret_cast<unsigned*>(scratch + ALIGN);
-        a.sc.vals = reinterpret_cast<float4*>(scratch + p->scratch_hdr);
-        a.sc.tails = reinterpret_cast<float*>(scratch + p->scratch_hdr + align_up(u.vals_bytes));
+        a.sc.carry = reinterpret_cast<Carry*>(scratch + ALIGN + u.flags_bytes);
+        a.sc.tails = reinterpret_cast<float*>(scratch + p->scratch_hdr);
         a.sc.tail_len = u.tail_len;
         a.status = p->dstatus;
         a.drop_tile = (p->flags & TFX_PLAN_TEST_DROP_PUBLISH) ? 0 : -1;
-        if (cudaMemsetAsync(scratch, 0, ALIGN + u.flags_bytes, s) != cudaSuccess) return TFX_ERR_CUDA;
+        if (cudaMemsetAsync(scratch, 0, ALIGN + u.flags_bytes + u.vals_bytes, s) != cudaSuccess) return TFX_ERR_CUDA;
         if (launch_unit(a, s) != cudaSuccess) return TFX_ERR_CUDA;
     }
     return TFX_OK;

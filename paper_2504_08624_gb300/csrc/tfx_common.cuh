@@ -35,11 +35,22 @@ struct UnitConst {
     const float* taps; // [nkb*FIR_R] FP32 taps, zero-padded
 };
 
+// Look-back carry of one (tile, section): a 2-vector published with a status
+// (0 = nothing yet, 1 = tile aggregate, 2 = inclusive prefix).  Stored as two
+// 8-byte halves {status, x} and {status, y}; each half is single-copy atomic,
+// and a reader accepts the word only when both halves carry the same status.
+struct __align__(16) Carry {
+    unsigned fx;
+    float x;
+    unsigned fy;
+    float y;
+};
+
 // Scratch for one execution of one unit (inside the caller's workspace).
 struct UnitScratch {
     unsigned* ticket;   // tile ticket counter (reset per execution)
-    unsigned* flags;    // [tiles][S+1]: per-section look-back flag, then tail flag
-    float4* vals;       // [tiles][S]: (agg.x, agg.y, incl.x, incl.y)
+    unsigned* flags;    // [tiles]: FIR-input tail published (reset per execution)
+    Carry* carry;       // [tiles][S] look-back carries (reset per execution)
     float* tails;       // [tiles][tail_len]: last FIR-input samples of each tile
     int tail_len;       // min(H, TILE)
 };
@@ -122,6 +133,46 @@ __device__ __forceinline__ unsigned wait_flag(const unsigned* flag, unsigned wan
         if (ns < 512) ns <<= 1;
         v = ld_acquire_u32(flag);
         if (v >= want) return v;
+        if (*(volatile int*)status != 0) return 0;
+        if (global_ns() - t0 > WAIT_LIMIT_NS) {
+            atomicCAS(status, 0, (int)TFX_ERR_TIMEOUT);
+            return 0;
+        }
+    }
+}
+
+__device__ __forceinline__ void publish_carry(Carry* p, unsigned status, float2 v) {
+    asm volatile("st.relaxed.gpu.global.v4.b32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(status),
+                 "r"(__float_as_uint(v.x)), "r"(status), "r"(__float_as_uint(v.y))
+                 : "memory");
+}
+
+// Status of a carry and its value (0 while nothing is published).
+__device__ __forceinline__ unsigned read_carry(const Carry* p, float2& v) {
+    for (;;) {
+        unsigned fx, x, fy, y;
+        asm volatile("ld.relaxed.gpu.global.v4.b32 {%0,%1,%2,%3}, [%4];"
+                     : "=r"(fx), "=r"(x), "=r"(fy), "=r"(y)
+                     : "l"(p)
+                     : "memory");
+        if (fx == fy) {
+            v = make_float2(__uint_as_float(x), __uint_as_float(y));
+            return fx;
+        }
+    }
+}
+
+// Wait (bounded, like wait_flag) until a carry has status >= 1.
+__device__ __forceinline__ unsigned wait_carry(const Carry* p, float2& v, int* status) {
+    unsigned f = read_carry(p, v);
+    if (f >= 1u) return f;
+    unsigned long long t0 = global_ns();
+    unsigned ns = 32;
+    for (;;) {
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
+        f = read_carry(p, v);
+        if (f >= 1u) return f;
         if (*(volatile int*)status != 0) return 0;
         if (global_ns() - t0 > WAIT_LIMIT_NS) {
             atomicCAS(status, 0, (int)TFX_ERR_TIMEOUT);
