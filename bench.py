@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--flags", type=int, default=0, help="TFX_PLAN_* bits for the timed plan")
     ap.add_argument("--channels", type=int, default=None, help="override channel count (testing only)")
     ap.add_argument("--samples", type=int, default=None, help="override samples per channel (testing only)")
+    ap.add_argument("--part", choices=["chain", "iir", "fir"], default="chain",
+                    help="time the whole chain (default) or only its IIR cascade / FIR stage (profiling)")
     return ap.parse_args()
 
 
@@ -65,6 +67,11 @@ def workload(args):
         wl.C = args.channels
     if args.samples:
         wl.N = args.samples
+    part = getattr(args, "part", "chain")
+    if part == "iir":
+        wl.stages = [st for st in wl.stages if st[0] == "sos"]
+    elif part == "fir":
+        wl.stages = [st for st in wl.stages if st[0] == "fir"]
     return wl
 
 
@@ -365,7 +372,8 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": wl.name, "channels": wl.C, "samples": wl.N,
+            "config": {"workload": wl.name if args.part == "chain" else f"{wl.name} ({args.part} only)",
+                       "channels": wl.C, "samples": wl.N,
                        "chain": f"cheby1 order 8 + 4 peaking (S={S}) + fir {L} taps",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "l2": "inputs 737 MB > 129 MB L2, no flush", "plan_flags": args.flags},

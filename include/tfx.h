@@ -75,6 +75,7 @@ typedef struct {
 #define TFX_PLAN_UNFUSED 2u        /* one kernel per stage group; intermediates go through the workspace */
 #define TFX_PLAN_FIR_BF16_PLAIN 4u /* tensor-core FIR, BF16 operands, no hi/lo correction (reported-only accuracy mode) */
 #define TFX_PLAN_FIR_BF16_SPLIT 8u /* tensor-core FIR with BF16 hi/lo operands instead of the default scaled FP16 hi/lo */
+#define TFX_PLAN_SCAN_WARP_TILES 16u /* cascade-only units: one warp per 1024-sample tile, warp-parallel look-back */
 /* Test hook for failure detection: the first tile of channel 0 never publishes
  * its carries, so its successor's bounded wait runs out; the execution
  * completes (with wrong output) and tfx_plan_get_error() returns
@@ -174,7 +175,7 @@ void tfx_cache_clear(void);
  * Same arguments, layout and result as tfx_sos (x == y allowed).  The call
  * makes no cudaMalloc / cudaFree and uses no allocating library routine: the
  * scan's scratch (tile ticket, status word, look-back carries) and the
- * section constants live in one fixed static device array of about 4.2 MB
+ * section constants live in one fixed static device array of about 4.3 MB
  * that every GPU loading the library holds until the process exits.
  * Limits: sections <= 8 and C * ceil(N / 8192) <= 32768 (for example 64
  * channels of up to 4.19 M samples); larger requests return

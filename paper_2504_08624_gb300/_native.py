@@ -22,6 +22,7 @@ TFX_PLAN_FIR_CUDA_CORES = 1
 TFX_PLAN_UNFUSED = 2
 TFX_PLAN_FIR_BF16_PLAIN = 4
 TFX_PLAN_FIR_BF16_SPLIT = 8
+TFX_PLAN_SCAN_WARP_TILES = 16
 TFX_PLAN_TEST_DROP_PUBLISH = 256
 
 STATUS = {

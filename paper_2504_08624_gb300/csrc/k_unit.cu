@@ -7,16 +7,17 @@
 // - a1 y[n-1] - a2 y[n-2] (a0-normalised) with zero initial state, sections in
 // order, then y[n] = sum_k h[k] x[n-k].
 //
-// Decomposition.  A tile is TILE = NT*T samples of one channel; thread i owns
-// samples [i*T, (i+1)*T).  Each section runs as a 2-state recursion with the
+// Decomposition.  A tile is TILE = NTH*T samples of one channel (256 threads x
+// 32 samples with an FIR, 128 x 64 without); thread i owns samples
+// [i*T, (i+1)*T).  Each section runs as a 2-state recursion with the
 // transposed-direct-form-II state W = (w1, w2); over a chunk of T samples the state evolves as
 // W_end = A W_start + e, where A = M^T (M the 2x2 one-sample transfer matrix)
 // and e is the chunk's zero-state end state.  Per section:
 //   1. zero-state pass over the thread's chunk (outputs y_zs, end state e);
 //   2. warp Kogge-Stone scan of (A, e) using the powers A^1..A^16, then a
-//      Horner combination of the 8 warp totals with A^32;
+//      Horner combination of the warp totals with A^32;
 //   3. decoupled look-back across tiles of the same channel (tile transfer
-//      A^NT) for the tile's incoming state, with bounded waits; each carry
+//      A^NTH) for the tile's incoming state, with bounded waits; each carry
 //      and its status travel in one 16-byte word;
 //   4. fix-up: y = y_zs + the homogeneous response from the true chunk start
 //      state, y_h[t] = -a1 y_h[t-1] - a2 y_h[t-2] (done inside the next
@@ -94,13 +95,14 @@ __device__ __forceinline__ void fir_block(const float* __restrict__ win, const f
     }
 }
 
-template <bool HAS_FIR>
-__global__ void __launch_bounds__(NT, HAS_FIR ? 2 : 3) k_unit(UnitArgs a) {
-    constexpr int T = T_CHUNK;
+template <bool HAS_FIR, int T, int NTH>
+__global__ void __launch_bounds__(NTH, HAS_FIR ? 2 : 4) k_unit(UnitArgs a) {
+    constexpr int NW = NTH / 32;
+    static_assert(NTH * T == TILE, "tile size");
     extern __shared__ float4 smem_f4[];
     float* smem = reinterpret_cast<float*>(smem_f4);
     __shared__ unsigned s_tile;
-    __shared__ float2 s_tot[NWARP];
+    __shared__ float2 s_tot[NW];
     __shared__ float2 s_win;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(NT, HAS_FIR ? 2 : 3) k_unit(UnitArgs a) {
             }
         }
         if (!run) break;
-        const float4* P = a.k.pw + (size_t)s * (NT + 1);
+        const float4* P = a.k.pw + (size_t)s * PW_LEN;
 
         // 2. warp inclusive scan: v_l = sum_{m<=l} A^m e_{l-m}
         float2 v = make_float2(w1, w2);
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(NT, HAS_FIR ? 2 : 3) k_unit(UnitArgs a) {
         // value), so neither side needs a fence.
         if (tid == 0) {
             float2 agg = make_float2(0.f, 0.f);
-            for (int w = 0; w < NWARP; ++w) {
+            for (int w = 0; w < NW; ++w) {
                 agg = mv2(A32, agg);
                 agg.x += s_tot[w].x;
                 agg.y += s_tot[w].y;
@@ -204,7 +206,7 @@ __global__ void __launch_bounds__(NT, HAS_FIR ? 2 : 3) k_unit(UnitArgs a) {
             if (tt == 0) {
                 if (pub) publish_carry(mine, 2u, agg);
             } else {
-                const float4 AT = P[NT];
+                const float4 AT = P[NTH];
                 int64_t j = tile - a.C;
                 float2 pv;
                 unsigned f = read_carry(a.sc.carry + j * S + s, pv);
@@ -254,15 +256,15 @@ __global__ void __launch_bounds__(NT, HAS_FIR ? 2 : 3) k_unit(UnitArgs a) {
         const int base = FIR_PAD + H + tid * T;
 #pragma unroll
         for (int t = 0; t < T; ++t) win[wphys(base + t)] = u[t];
-        for (int i = tid; i < FIR_PAD; i += NT) win[wphys(i)] = 0.f;
-        for (int i = tid; i < nkb * FIR_R; i += NT) taps[i] = a.k.taps[i];
+        for (int i = tid; i < FIR_PAD; i += NTH) win[wphys(i)] = 0.f;
+        for (int i = tid; i < nkb * FIR_R; i += NTH) taps[i] = a.k.taps[i];
         __syncthreads();
 
         // publish this tile's last tail_len FIR-input samples for the successor
         const int tl = a.sc.tail_len;
         if (tt + 1 < a.ntt) {
             float* dst = a.sc.tails + tile * (int64_t)tl;
-            for (int i = tid; i < tl; i += NT) dst[i] = win[wphys(FIR_PAD + H + TILE - tl + i)];
+            for (int i = tid; i < tl; i += NTH) dst[i] = win[wphys(FIR_PAD + H + TILE - tl + i)];
             __threadfence();
             __syncthreads();
             if (tid == 0 && tile != a.drop_tile) st_release_u32(a.sc.flags + tile, 1u);
@@ -272,7 +274,7 @@ __global__ void __launch_bounds__(NT, HAS_FIR ? 2 : 3) k_unit(UnitArgs a) {
         int remaining = H;
         for (int qb = 1; remaining > 0; ++qb) {
             if (tt - qb < 0) {
-                for (int i = tid; i < remaining; i += NT) win[wphys(FIR_PAD + H - ((qb - 1) * TILE + 1 + i))] = 0.f;
+                for (int i = tid; i < remaining; i += NTH) win[wphys(FIR_PAD + H - ((qb - 1) * TILE + 1 + i))] = 0.f;
                 break;
             }
             const int64_t jt = tile - (int64_t)qb * a.C;
@@ -280,7 +282,7 @@ __global__ void __launch_bounds__(NT, HAS_FIR ? 2 : 3) k_unit(UnitArgs a) {
             __syncthreads();
             const float* src = a.sc.tails + jt * (int64_t)tl;
             const int nq = remaining < tl ? remaining : tl;
-            for (int i = tid; i < nq; i += NT) {
+            for (int i = tid; i < nq; i += NTH) {
                 const int m = (qb - 1) * TILE + 1 + i;  // samples back from t0
                 win[wphys(FIR_PAD + H - m)] = __ldcg(src + (tl - 1 - i));
             }
@@ -289,7 +291,7 @@ __global__ void __launch_bounds__(NT, HAS_FIR ? 2 : 3) k_unit(UnitArgs a) {
         __syncthreads();
 
         float* yrow = a.y + c * a.ldy;
-        for (int o0 = tid * FIR_R; o0 < TILE; o0 += NT * FIR_R) {
+        for (int o0 = tid * FIR_R; o0 < TILE; o0 += NTH * FIR_R) {
             const int64_t n0 = t0 + o0;
             if (n0 >= a.N) break;
             float acc[FIR_R];
@@ -313,7 +315,8 @@ cudaError_t prepare_unit(const UnitConst& k) {
     static int set_bytes = 48 * 1024;
     const size_t smem = unit_smem_bytes(k);
     if (k.L <= 0 || (int)smem <= set_bytes) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_unit<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_unit<true, T_CHUNK, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e == cudaSuccess) set_bytes = (int)smem;
     return e;
 }
@@ -322,9 +325,9 @@ cudaError_t launch_unit(const UnitArgs& a, cudaStream_t s) {
     const int64_t tiles = a.C * a.ntt;
     if (tiles <= 0) return cudaSuccess;
     if (a.k.L > 0) {
-        k_unit<true><<<(unsigned)tiles, NT, unit_smem_bytes(a.k), s>>>(a);
+        k_unit<true, T_CHUNK, NT><<<(unsigned)tiles, NT, unit_smem_bytes(a.k), s>>>(a);
     } else {
-        k_unit<false><<<(unsigned)tiles, NT, 0, s>>>(a);
+        k_unit<false, T_CASCADE, NT_CASCADE><<<(unsigned)tiles, NT_CASCADE, 0, s>>>(a);
     }
     return cudaGetLastError();
 }

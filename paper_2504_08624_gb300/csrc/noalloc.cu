@@ -23,8 +23,8 @@ constexpr size_t NA_CARRY_BYTES = (size_t)NA_MAX_TILES * NA_MAX_SECTIONS * sizeo
 constexpr size_t NA_OFF_COEF = NA_OFF_CARRY + NA_CARRY_BYTES;
 constexpr size_t NA_COEF_BYTES = (size_t)NA_MAX_SECTIONS * 8 * sizeof(float);
 constexpr size_t NA_OFF_PW = NA_OFF_COEF + NA_COEF_BYTES;
-constexpr size_t NA_PW_BYTES = (size_t)NA_MAX_SECTIONS * (NT + 1) * sizeof(float4);
-constexpr size_t NA_BYTES = NA_OFF_PW + NA_PW_BYTES;  // about 4.2 MB
+constexpr size_t NA_PW_BYTES = (size_t)NA_MAX_SECTIONS * PW_LEN * sizeof(float4);
+constexpr size_t NA_BYTES = NA_OFF_PW + NA_PW_BYTES;  // about 4.3 MB
 
 constexpr int NA_MAX_DEVICES = 64;
 
@@ -86,7 +86,7 @@ extern "C" int tfx_sos_noalloc(const float* x, float* y, int64_t C, int64_t N, i
 
     // section constants, computed in FP64 on the stack (no heap use)
     float coef[NA_MAX_SECTIONS * 8] = {};
-    float4 pw[NA_MAX_SECTIONS * (NT + 1)];
+    float4 pw[NA_MAX_SECTIONS * PW_LEN];
     for (int s = 0; s < sections; ++s) {
         const double* r = sos + 6 * s;
         for (int j = 0; j < 6; ++j)
@@ -101,10 +101,10 @@ extern "C" int tfx_sos_noalloc(const float* x, float* y, int64_t C, int64_t N, i
         coef[8 * s + 4] = (float)a2;
         const NaM2 m = {-a1, 1.0, -a2, 0.0};
         NaM2 A = {1, 0, 0, 1};
-        for (int t = 0; t < T_CHUNK; ++t) A = na_mul(A, m);
+        for (int t = 0; t < T_CASCADE; ++t) A = na_mul(A, m);  // samples per thread of the cascade kernel
         NaM2 pk = {1, 0, 0, 1};
-        for (int k = 0; k <= NT; ++k) {
-            pw[s * (NT + 1) + k] = make_float4((float)pk.a, (float)pk.b, (float)pk.c, (float)pk.d);
+        for (int k = 0; k < PW_LEN; ++k) {
+            pw[s * PW_LEN + k] = make_float4((float)pk.a, (float)pk.b, (float)pk.c, (float)pk.d);
             pk = na_mul(pk, A);
         }
     }
@@ -122,7 +122,7 @@ extern "C" int tfx_sos_noalloc(const float* x, float* y, int64_t C, int64_t N, i
     if (cudaMemcpyAsync(base + NA_OFF_COEF, coef, (size_t)sections * 8 * sizeof(float), cudaMemcpyHostToDevice,
                         s) != cudaSuccess)
         return TFX_ERR_CUDA;
-    if (cudaMemcpyAsync(base + NA_OFF_PW, pw, (size_t)sections * (NT + 1) * sizeof(float4),
+    if (cudaMemcpyAsync(base + NA_OFF_PW, pw, (size_t)sections * PW_LEN * sizeof(float4),
                         cudaMemcpyHostToDevice, s) != cudaSuccess)
         return TFX_ERR_CUDA;
 

@@ -38,7 +38,11 @@ struct HostUnit {
     size_t off_ahi = 0, off_alo = 0, tc_smem = 0;
     int tc_mode = 0;
     float tap_unscale = 1.0f;
+    // cascade without an FIR: warp-per-tile scan (tiles of 32 * T_CHUNK samples)
+    bool warp = false;
 };
+
+constexpr int WARP_TILE = 32 * T_CHUNK;
 
 // Taps at or above this count go to the tensor cores (unless disabled).
 constexpr int TC_MIN_TAPS = 64;
@@ -260,13 +264,15 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         p->units.swap(out);
     }
 
+    for (HostUnit& u : p->units) u.warp = (u.S > 0 && u.L == 0) && (p->flags & TFX_PLAN_SCAN_WARP_TILES);
+
     // constant blob layout
     size_t off = 0;
     for (HostUnit& u : p->units) {
         u.off_coef = off;
         off = align_up(off + (size_t)u.S * 8 * sizeof(float));
         u.off_pw = off;
-        off = align_up(off + (size_t)u.S * (NT + 1) * sizeof(float4));
+        off = align_up(off + (size_t)u.S * PW_LEN * sizeof(float4));
         u.nkb = u.L > 0 ? (u.L + FIR_R - 1) / FIR_R : 0;
         u.off_taps = off;
         off = align_up(off + (size_t)u.nkb * FIR_R * sizeof(float));
@@ -294,10 +300,11 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
             // one-sample transfer of the TDF-II state (w1, w2) with zero input
             const M2 m = {-r[3], 1.0, -r[4], 0.0};
             M2 a = {1, 0, 0, 1};
-            for (int t = 0; t < T_CHUNK; ++t) a = mul(a, m);  // chunk transfer A = M^T
+            const int chunk = u.L == 0 && !u.warp ? T_CASCADE : T_CHUNK;  // samples per thread of u's kernel
+            for (int t = 0; t < chunk; ++t) a = mul(a, m);                 // chunk transfer A = M^chunk
             M2 pk = {1, 0, 0, 1};
-            for (int k = 0; k <= NT; ++k) {
-                pw[(size_t)s * (NT + 1) + k] = make_float4((float)pk.a, (float)pk.b, (float)pk.c, (float)pk.d);
+            for (int k = 0; k < PW_LEN; ++k) {
+                pw[(size_t)s * PW_LEN + k] = make_float4((float)pk.a, (float)pk.b, (float)pk.c, (float)pk.d);
                 pk = mul(pk, a);
             }
         }
@@ -378,9 +385,11 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
             u.ntt = p->N > 0 ? (p->N + 128 * u.NB - 1) / (128 * u.NB) : 0;
             continue;
         }
+        if (u.warp) u.ntt = p->N > 0 ? (p->N + WARP_TILE - 1) / WARP_TILE : 0;
         const int H = u.L > 0 ? u.L - 1 : 0;
         u.tail_len = u.L > 0 ? (H < TILE ? H : TILE) : 0;
-        const int64_t tiles = p->C * ntt;
+        const int64_t tiles = p->C * u.ntt;
+        if (tiles > (int64_t)INT32_MAX) return TFX_ERR_UNSUPPORTED;
         u.flags_bytes = align_up((size_t)tiles * sizeof(unsigned));
         u.vals_bytes = (size_t)tiles * u.S * sizeof(Carry);
         u.tails_bytes = (size_t)tiles * u.tail_len * sizeof(float);
@@ -406,6 +415,68 @@ bool ranges_overlap_not_equal(const float* x, const float* y, int64_t C, int64_t
     return xb < yb + span && yb < xb + span;
 }
 
+// Launch unit i for channels [c0, c0 + Cg) reading `in` (row stride ldin) and
+// writing `out` (row stride ldout).
+int launch_unit_range(tfx_plan* p, int i, const float* in, int64_t ldin, float* out, int64_t ldout, int64_t c0,
+                      int64_t Cg, char* scratch, float* copy_buf, cudaStream_t s) {
+    const HostUnit& u = p->units[i];
+    in += c0 * ldin;
+    out += c0 * ldout;
+    if (u.tc) {
+        FirTcArgs f{};
+        f.x = in;
+        f.ldx = ldin;
+        f.y = out;
+        f.ldy = ldout;
+        if (f.x == f.y) {  // the halo is read from other tiles' input: copy it first
+            if (launch_copy_rows(f.x, copy_buf, Cg, p->N, f.ldx, p->N, s) != cudaSuccess) return TFX_ERR_CUDA;
+            f.x = copy_buf;
+            f.ldx = p->N;
+        }
+        f.C = Cg;
+        f.N = p->N;
+        f.ntt = u.ntt;
+        f.L = u.L;
+        f.W = u.W;
+        f.nK = u.nK;
+        f.NB = u.NB;
+        f.rows = u.rows;
+        f.tmem_cols = u.tmem_cols;
+        f.a_chunks = u.a_chunks;
+        f.mode = u.tc_mode;
+        f.tap_unscale = u.tap_unscale;
+        f.a_hi = reinterpret_cast<const uint4*>(p->dconst + u.off_ahi);
+        f.a_lo = reinterpret_cast<const uint4*>(p->dconst + u.off_alo);
+        f.status = p->dstatus;
+        return launch_fir_tc(f, s) == cudaSuccess ? TFX_OK : TFX_ERR_CUDA;
+    }
+    UnitArgs a;
+    a.x = in;
+    a.ldx = ldin;
+    a.y = out;
+    a.ldy = ldout;
+    a.C = Cg;
+    a.N = p->N;
+    a.ntt = u.ntt;
+    a.k.S = u.S;
+    a.k.L = u.L;
+    a.k.H = u.L > 0 ? u.L - 1 : 0;
+    a.k.nkb = u.nkb;
+    a.k.gain = 1.0f;
+    a.k.coef = reinterpret_cast<const float*>(p->dconst + u.off_coef);
+    a.k.pw = reinterpret_cast<const float4*>(p->dconst + u.off_pw);
+    a.k.taps = reinterpret_cast<const float*>(p->dconst + u.off_taps);
+    a.sc.ticket = reinterpret_cast<unsigned*>(scratch);
+    a.sc.flags = reinterpret_cast<unsigned*>(scratch + ALIGN);
+    a.sc.carry = reinterpret_cast<Carry*>(scratch + ALIGN + u.flags_bytes);
+    a.sc.tails = reinterpret_cast<float*>(scratch + p->scratch_hdr);
+    a.sc.tail_len = u.tail_len;
+    a.status = p->dstatus;
+    a.drop_tile = (p->flags & TFX_PLAN_TEST_DROP_PUBLISH) ? 0 : -1;
+    if (cudaMemsetAsync(scratch, 0, ALIGN + u.flags_bytes + u.vals_bytes, s) != cudaSuccess) return TFX_ERR_CUDA;
+    return (u.warp ? launch_sos_warp(a, s) : launch_unit(a, s)) == cudaSuccess ? TFX_OK : TFX_ERR_CUDA;
+}
+
 int exec_fused(tfx_plan* p, const float* x, float* y, void* ws, cudaStream_t s) {
     char* w = static_cast<char*>(ws);
     const int nu = (int)p->units.size();
@@ -419,61 +490,12 @@ int exec_fused(tfx_plan* p, const float* x, float* y, void* ws, cudaStream_t s) 
     float* buf[2] = {reinterpret_cast<float*>(w + p->scratch_bytes),
                      reinterpret_cast<float*>(w + p->scratch_bytes + p->buf_bytes)};
     for (int i = 0; i < nu; ++i) {
-        const HostUnit& u = p->units[i];
-        if (u.tc) {
-            FirTcArgs f{};
-            f.x = i == 0 ? x : buf[(i - 1) & 1];
-            f.ldx = i == 0 ? p->ld : p->N;
-            f.y = i == nu - 1 ? y : buf[i & 1];
-            f.ldy = i == nu - 1 ? p->ld : p->N;
-            if (f.x == f.y) {  // the halo is read from other tiles' input: copy it first
-                if (launch_copy_rows(f.x, buf[0], p->C, p->N, f.ldx, p->N, s) != cudaSuccess) return TFX_ERR_CUDA;
-                f.x = buf[0];
-                f.ldx = p->N;
-            }
-            f.C = p->C;
-            f.N = p->N;
-            f.ntt = u.ntt;
-            f.L = u.L;
-            f.W = u.W;
-            f.nK = u.nK;
-            f.NB = u.NB;
-            f.rows = u.rows;
-            f.tmem_cols = u.tmem_cols;
-            f.a_chunks = u.a_chunks;
-            f.mode = u.tc_mode;
-            f.tap_unscale = u.tap_unscale;
-            f.a_hi = reinterpret_cast<const uint4*>(p->dconst + u.off_ahi);
-            f.a_lo = reinterpret_cast<const uint4*>(p->dconst + u.off_alo);
-            f.status = p->dstatus;
-            if (launch_fir_tc(f, s) != cudaSuccess) return TFX_ERR_CUDA;
-            continue;
-        }
-        UnitArgs a;
-        a.x = i == 0 ? x : buf[(i - 1) & 1];
-        a.ldx = i == 0 ? p->ld : p->N;
-        a.y = i == nu - 1 ? y : buf[i & 1];
-        a.ldy = i == nu - 1 ? p->ld : p->N;
-        a.C = p->C;
-        a.N = p->N;
-        a.ntt = u.ntt;
-        a.k.S = u.S;
-        a.k.L = u.L;
-        a.k.H = u.L > 0 ? u.L - 1 : 0;
-        a.k.nkb = u.nkb;
-        a.k.gain = 1.0f;
-        a.k.coef = reinterpret_cast<const float*>(p->dconst + u.off_coef);
-        a.k.pw = reinterpret_cast<const float4*>(p->dconst + u.off_pw);
-        a.k.taps = reinterpret_cast<const float*>(p->dconst + u.off_taps);
-        a.sc.ticket = reinterpret_cast<unsigned*>(scratch);
-        a.sc.flags = reinterpret_cast<unsigned*>(scratch + ALIGN);
-        a.sc.carry = reinterpret_cast<Carry*>(scratch + ALIGN + u.flags_bytes);
-        a.sc.tails = reinterpret_cast<float*>(scratch + p->scratch_hdr);
-        a.sc.tail_len = u.tail_len;
-        a.status = p->dstatus;
-        a.drop_tile = (p->flags & TFX_PLAN_TEST_DROP_PUBLISH) ? 0 : -1;
-        if (cudaMemsetAsync(scratch, 0, ALIGN + u.flags_bytes + u.vals_bytes, s) != cudaSuccess) return TFX_ERR_CUDA;
-        if (launch_unit(a, s) != cudaSuccess) return TFX_ERR_CUDA;
+        const float* in = i == 0 ? x : buf[(i - 1) & 1];
+        const int64_t ldin = i == 0 ? p->ld : p->N;
+        float* out = i == nu - 1 ? y : buf[i & 1];
+        const int64_t ldout = i == nu - 1 ? p->ld : p->N;
+        const int rc = launch_unit_range(p, i, in, ldin, out, ldout, 0, p->C, scratch, buf[0], s);
+        if (rc != TFX_OK) return rc;
     }
     return TFX_OK;
 }
@@ -606,7 +628,7 @@ int tfx_plan_create(tfx_plan** out, int64_t C, int64_t N, int64_t ld, const tfx_
     rc = validate_stages(st, nst);
     if (rc != TFX_OK) return rc;
     if (flags & ~(TFX_PLAN_FIR_CUDA_CORES | TFX_PLAN_UNFUSED | TFX_PLAN_FIR_BF16_PLAIN | TFX_PLAN_FIR_BF16_SPLIT |
-                  TFX_PLAN_TEST_DROP_PUBLISH))
+                  TFX_PLAN_SCAN_WARP_TILES | TFX_PLAN_TEST_DROP_PUBLISH))
         return TFX_ERR_INVALID;
     tfx_plan* p = new (std::nothrow) tfx_plan();
     if (!p) return TFX_ERR_NOMEM;

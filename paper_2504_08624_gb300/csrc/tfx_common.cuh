@@ -14,9 +14,16 @@ constexpr int NT = 256;
 constexpr int NWARP = NT / 32;
 constexpr int T_CHUNK = 32;
 constexpr int TILE = NT * T_CHUNK;  // 8192 samples
+// Cascade-only units (no FIR) run 128-thread CTAs with 64 samples per thread
+// (the same 8192-sample tile): fewer scan steps and barriers per sample.
+constexpr int NT_CASCADE = 128;
+constexpr int T_CASCADE = 64;
+static_assert(NT_CASCADE * T_CASCADE == TILE, "cascade tile must match the fused tile");
 // FIR register blocking: each thread produces FIR_R consecutive outputs per
 // pass and walks the taps FIR_R at a time.
 constexpr int FIR_R = 16;
+// Entries per section in the chunk-transfer power table: A^k, k = 0..1024.
+constexpr int PW_LEN = 1025;
 // Zero padding in front of the FIR window (shared memory), >= 2*FIR_R.
 constexpr int FIR_PAD = 32;
 // Device-side bounded waits give up after this long and record TFX_ERR_TIMEOUT.
@@ -31,7 +38,7 @@ struct UnitConst {
     int nkb;           // FIR tap blocks of FIR_R (taps zero-padded to nkb*FIR_R)
     float gain;        // output scale when the unit ends without an FIR
     const float* coef; // [S][8]: b0 c1 c2 a1 a2 (a0-normalised; c1 = b1 - a1 b0, c2 = b2 - a2 b0)
-    const float4* pw;  // [S][NT+1]: A^k, A = chunk transfer matrix (row-major 2x2)
+    const float4* pw;  // [S][PW_LEN]: A^k, A = chunk transfer matrix (row-major 2x2)
     const float* taps; // [nkb*FIR_R] FP32 taps, zero-padded
 };
 
@@ -192,6 +199,7 @@ __device__ __forceinline__ float4 mm2(float4 a, float4 b) {
 
 // Launchers (defined in the kernel translation units).
 cudaError_t launch_unit(const UnitArgs& a, cudaStream_t s);
+cudaError_t launch_sos_warp(const UnitArgs& a, cudaStream_t s);
 cudaError_t launch_plain_sos(const float* x, float* y, int64_t C, int64_t N, int64_t ldx,
                              int64_t ldy, int S, const float* coef, cudaStream_t s);
 cudaError_t launch_plain_fir(const float* x, float* y, int64_t C, int64_t N, int64_t ldx,

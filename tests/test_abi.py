@@ -79,6 +79,7 @@ def test_header_constants_match_binding():
                       ("TFX_PLAN_UNFUSED", N.TFX_PLAN_UNFUSED),
                       ("TFX_PLAN_FIR_BF16_PLAIN", N.TFX_PLAN_FIR_BF16_PLAIN),
                       ("TFX_PLAN_FIR_BF16_SPLIT", N.TFX_PLAN_FIR_BF16_SPLIT),
+                      ("TFX_PLAN_SCAN_WARP_TILES", N.TFX_PLAN_SCAN_WARP_TILES),
                       ("TFX_PLAN_TEST_DROP_PUBLISH", N.TFX_PLAN_TEST_DROP_PUBLISH)]:
         m = re.search(rf"#define {name} (\d+)u", txt)
         assert m and int(m.group(1)) == val

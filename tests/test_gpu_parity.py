@@ -226,3 +226,60 @@ def test_strongly_attenuating_chain():
     stages = W.random_chain(5)
     x = W.white_uniform(3, 48495, 505)
     check(x, stages)
+
+
+def test_timeout_cascade_only_warp_tiles():
+    """Same failure path for a cascade-only unit (warp-per-tile scan)."""
+    from paper_2504_08624_gb300 import api, _native as N
+    x = torch.from_numpy(W.white_uniform(2, 4 * 1024 + 5, 18)).cuda()
+    p = api.Plan(2, 4 * 1024 + 5, [("sos", W.butter_sos(4, 1000, 48000))],
+                 flags=N.TFX_PLAN_TEST_DROP_PUBLISH | N.TFX_PLAN_SCAN_WARP_TILES)
+    p.execute(x)
+    torch.cuda.synchronize()
+    assert p.get_error() == -5
+    y = api.chain(x, [("sos", W.butter_sos(4, 1000, 48000))])
+    torch.cuda.synchronize()
+    assert_close(y.cpu().numpy(), oracle_chain(x.cpu().numpy(), [("sos", W.butter_sos(4, 1000, 48000))]), 1e-4)
+    p.close()
+
+
+@pytest.mark.parametrize("N", [1, 1023, 1024, 1025, 5 * 1024 + 3, 40 * 1024 + 11])
+def test_cascade_warp_tile_edges(N):
+    from paper_2504_08624_gb300 import _native as N_
+    x = W.white_uniform(5, N, 19)
+    check(x, [("sos", W.random_stable_sos(8, 77, 0.3, 0.999))], flags=N_.TFX_PLAN_SCAN_WARP_TILES)
+    check(x, [("sos", W.random_stable_sos(8, 77, 0.3, 0.999))], flags=N_.TFX_PLAN_SCAN_WARP_TILES, inplace=True)
+
+
+@pytest.mark.parametrize("C", [1, 2, 5, 9])
+def test_cascade_then_tensor_fir(C):
+    wl = W.multichannel_fused()
+    x = wl.make_signal(C, 40000)
+    check(x, wl.stages, wl.tol)
+    check(x, wl.stages, wl.tol, flags=0, ld=40000 + 3, offset=1)
+
+
+def test_cascade_tensor_fir_graph_capture():
+    from paper_2504_08624_gb300 import api
+    wl = W.multichannel_fused()
+    x = wl.make_signal(5, 30000)
+    xt = torch.from_numpy(x).cuda()
+    p = api.Plan(5, 30000, wl.stages)
+    assert p.launches_per_execute == 2  # cascade kernel, tensor-core FIR kernel
+    y = torch.empty_like(xt)
+    ws = p.workspace()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        p.execute(xt, y, ws)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        p.execute(xt, y, ws)
+    y.zero_()
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    assert_close(y.cpu().numpy(), oracle_chain(x, wl.stages), wl.tol, "graph replay")
+    p.close()
