@@ -227,14 +227,268 @@ __global__ void __launch_bounds__(256, 1) k_fir_tc(FirTcArgs a) {
     if (warp == 0) tc::tmem_dealloc(tmem, (uint32_t)a.tmem_cols);
 }
 
+// ---------------------------------------------------------------------------
+// Persistent, warp-specialised variant (one CTA per SM, 416 threads):
+//   warps 0-7   producers: signal window of tile i -> hi/lo chunks in stage i%2
+//   warps 8-11  epilogue:  accumulator i%2 (TMEM columns 128*(i%2)) -> y
+//   warp  12    TMEM allocation; lane 0 issues the MMAs of tile i into
+//              accumulator i%2 and commits them to mma_done[i%2]
+// The tap tables are loaded once per CTA.  Hand-offs are mbarriers:
+//   full[s]      producers -> MMA      (window of stage s written)
+//   mma_done[s]  MMA -> producers (stage s free) and epilogue (accumulator s ready)
+//   acc_free[s]  epilogue -> MMA       (accumulator s drained)
+//   scale_rdy[k] producer -> epilogue  (per-tile FP16 scale, ring of 4)
+// Every wait is bounded; on a timeout the status word is set and all roles
+// leave their loops, so the CTA always reaches the TMEM release.
+
+namespace {
+
+constexpr int WS_THREADS = 416;
+constexpr int WS_PROD = 256;  // producer threads (warps 0-7)
+constexpr int WS_MMA_WARP = 12;
+
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, int* status) {
+    if (tc::mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        if (tc::mbar_try_wait(bar, parity)) return true;
+        if (*(volatile int*)status != 0) return false;
+        if (global_ns() - t0 > WAIT_LIMIT_NS) {
+            atomicCAS(status, 0, (int)TFX_ERR_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(WS_THREADS, 1) k_fir_tc_ws(FirTcArgs a) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int J = a.a_chunks;
+    const int rows = a.rows;
+    const uint32_t CS = (uint32_t)rows * 16u;
+    const size_t bstage = (size_t)16 * CS;  // bytes of one hi (or lo) window
+    uint8_t* A_hi = smem;
+    uint8_t* A_lo = A_hi + (size_t)J * 128;
+    uint8_t* Bbase = A_lo + (size_t)J * 128;  // [stage][hi, lo]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(Bbase + 4 * bstage);
+    uint64_t* full = bars;           // [2]
+    uint64_t* mma_done = bars + 2;   // [2]
+    uint64_t* acc_free = bars + 4;   // [2]
+    uint64_t* scale_rdy = bars + 6;  // [4]
+    float* s_scale = reinterpret_cast<float*>(bars + 10);  // [4]
+    float* s_red = s_scale + 4;                            // [8]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(s_red + 8);
+    int* s_ok = reinterpret_cast<int*>(tmem_slot + 1);  // producers' shared wait outcome
+
+    if (warp == WS_MMA_WARP) {
+        tc::tmem_alloc(tmem_slot, 256u);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int k = 0; k < 2; ++k) {
+            tc::mbar_init(&full[k], WS_PROD);
+            tc::mbar_init(&mma_done[k], 1);
+            tc::mbar_init(&acc_free[k], 128);  // epilogue threads
+        }
+        for (int k = 0; k < 4; ++k) tc::mbar_init(&scale_rdy[k], 1);
+        tc::mbar_init_fence();
+    }
+    {
+        uint4* dhi = reinterpret_cast<uint4*>(A_hi);
+        uint4* dlo = reinterpret_cast<uint4*>(A_lo);
+        for (int i = tid; i < J * 8; i += WS_THREADS) {
+            dhi[i] = a.a_hi[i];
+            dlo[i] = a.a_lo[i];
+        }
+    }
+    tc::fence_proxy_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int64_t tiles = a.C * a.ntt;
+    const int nt = (int)((tiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
+    const bool fp16 = a.mode == FIR_TC_FP16_SPLIT;
+
+    if (warp < WS_PROD / 32) {
+        // ---------------- producers ----------------
+        constexpr int U = 4;  // chunks in flight per thread
+        const int ptid = tid;
+        const int nchunks = rows * 16;
+        for (int i = 0; i < nt; ++i) {
+            const int st = i & 1;
+            if (i >= 2) {
+                // one thread waits, a named barrier shares the outcome (uniform exit)
+                if (ptid == 0) s_ok[0] = wait_bar(&mma_done[st], ((i - 2) >> 1) & 1, a.status) ? 1 : 0;
+                named_sync(2, WS_PROD);
+                if (!s_ok[0]) break;
+            }
+            const int64_t tile = blockIdx.x + (int64_t)i * gridDim.x;
+            const int64_t c = tile / a.ntt;
+            const int64_t t0 = (tile % a.ntt) * (int64_t)(128 * a.NB);
+            const float* xr = a.x + c * a.ldx;
+            const int64_t s0 = t0 - a.W;
+            const bool vec = ((reinterpret_cast<uintptr_t>(xr + s0) & 15) == 0);
+            float xscale = 1.f, xunscale = 1.f;
+            if (fp16) {
+                float m = 0.f;
+                for (int g0 = ptid; g0 < nchunks; g0 += U * WS_PROD) {
+                    float v[U][8];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int g = g0 + u * WS_PROD;
+                        if (g < nchunks) load8(xr, s0 + 8 * (int64_t)g, a.N, vec, v[u]);
+                        else {
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) v[u][q] = 0.f;
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) m = fmaxf(m, fabsf(v[u][q]));
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                if (lane == 0) s_red[warp] = m;
+                named_sync(1, WS_PROD);
+                m = s_red[0];
+#pragma unroll
+                for (int w = 1; w < WS_PROD / 32; ++w) m = fmaxf(m, s_red[w]);
+                named_sync(1, WS_PROD);  // s_red is reused by the next tile
+                if (m > 0.f && isfinite(m)) {
+                    int sh = 14 - ilogbf(m);
+                    sh = sh > 126 ? 126 : (sh < -126 ? -126 : sh);
+                    xscale = ldexpf(1.f, sh);
+                    xunscale = ldexpf(1.f, -sh);
+                }
+            }
+            uint8_t* Bhi = Bbase + (size_t)st * 2 * bstage;
+            uint8_t* Blo = Bhi + bstage;
+            for (int g0 = ptid; g0 < nchunks; g0 += U * WS_PROD) {
+                float v[U][8];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int g = g0 + u * WS_PROD;
+                    if (g < nchunks) load8(xr, s0 + 8 * (int64_t)g, a.N, vec, v[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int g = g0 + u * WS_PROD;
+                    if (g >= nchunks) break;
+                    uint4 hi, lo;
+                    if (fp16)
+                        split8_f16(v[u], xscale, hi, lo);
+                    else
+                        split8_bf16(v[u], hi, lo);
+                    const uint32_t off = (uint32_t)(g % 16) * CS + (uint32_t)(g / 16) * 16u;
+                    *reinterpret_cast<uint4*>(Bhi + off) = hi;
+                    *reinterpret_cast<uint4*>(Blo + off) = lo;
+                }
+            }
+            tc::fence_proxy_async_smem();
+            tc::mbar_arrive(&full[st]);
+            if (ptid == 0) {
+                s_scale[i & 3] = xunscale;
+                tc::mbar_arrive(&scale_rdy[i & 3]);
+            }
+        }
+    } else if (warp < WS_MMA_WARP) {
+        // ---------------- epilogue ----------------
+        const int quarter = warp & 3;
+        const int l = quarter * 32 + lane;  // TMEM lane = 127 - phase
+        const int phase = 127 - l;
+        const float us = a.tap_unscale;
+        for (int i = 0; i < nt; ++i) {
+            const int st = i & 1;
+            bool ok = wait_bar(&mma_done[st], (i >> 1) & 1, a.status);
+            ok = ok && wait_bar(&scale_rdy[i & 3], (i >> 2) & 1, a.status);
+            if (!__all_sync(0xffffffffu, ok)) break;  // tcgen05.ld below is warp-collective
+            tc::tc_fence_after();
+            const float xu = s_scale[i & 3];
+            const int64_t tile = blockIdx.x + (int64_t)i * gridDim.x;
+            const int64_t c = tile / a.ntt;
+            const int64_t t0 = (tile % a.ntt) * (int64_t)(128 * a.NB);
+            float* yr = a.y + c * a.ldy;
+            for (int cc = 0; cc < a.NB; cc += 16) {
+                float v[16];
+                tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(st * 128 + cc), v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int64_t n = t0 + (int64_t)(cc + j) * 128 + phase;
+                    if (n < a.N) yr[n] = (v[j] * xu) * us;
+                }
+            }
+            tc::tc_fence_before();
+            tc::mbar_arrive(&acc_free[st]);
+        }
+    } else if (lane == 0) {
+        // ---------------- MMA issue ----------------
+        const uint32_t idesc = tc::idesc_f16kind_f32(128, a.NB, !fp16);
+        const uint32_t ahi = tc::smem_u32(A_hi), alo = tc::smem_u32(A_lo);
+        int issued = 0;
+        for (int i = 0; i < nt; ++i) {
+            const int st = i & 1;
+            if (!wait_bar(&full[st], (i >> 1) & 1, a.status)) break;
+            if (i >= 2 && !wait_bar(&acc_free[st], ((i - 2) >> 1) & 1, a.status)) break;
+            tc::tc_fence_after();
+            const uint32_t bhi = tc::smem_u32(Bbase + (size_t)st * 2 * bstage);
+            const uint32_t blo = bhi + (uint32_t)bstage;
+            const uint32_t d = tmem + (uint32_t)(st * 128);
+            for (int k = 0; k < a.nK; ++k) {
+                const uint32_t aoff = (uint32_t)(2 * k) * 128u;
+                const uint32_t boff = (uint32_t)((2 * k) & 15) * CS + (uint32_t)(k >> 3) * 16u;
+                const uint64_t dah = tc::desc_noswz(ahi + aoff, 128u, 128u);
+                const uint64_t dbh = tc::desc_noswz(bhi + boff, CS, 128u);
+                tc::mma_bf16(d, dah, dbh, idesc, k > 0 ? 1u : 0u);
+                if (a.mode != FIR_TC_BF16_PLAIN) {
+                    const uint64_t dal = tc::desc_noswz(alo + aoff, 128u, 128u);
+                    const uint64_t dbl = tc::desc_noswz(blo + boff, CS, 128u);
+                    tc::mma_bf16(d, dah, dbl, idesc, 1u);
+                    tc::mma_bf16(d, dal, dbh, idesc, 1u);
+                }
+            }
+            tc::mma_commit(&mma_done[st]);
+            issued = i + 1;
+        }
+        // before the TMEM release: the last committed tile must have completed
+        if (issued > 0) wait_bar(&mma_done[(issued - 1) & 1], ((issued - 1) >> 1) & 1, a.status);
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == WS_MMA_WARP) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, 256u);
+    }
+}
+
 size_t fir_tc_smem_bytes(const FirTcArgs& a) {
+    if (a.persistent)
+        return (size_t)a.a_chunks * 128 * 2 + (size_t)16 * a.rows * 16 * 4 + 10 * 8 + 12 * 4 + 32;
     return (size_t)a.a_chunks * 128 * 2 + (size_t)16 * a.rows * 16 * 2 + 16;
 }
 
 cudaError_t prepare_fir_tc(size_t smem) {
     static size_t set_bytes = 0;
+    cudaError_t e = cudaSuccess;
+    if (smem > set_bytes) {
+        e = cudaFuncSetAttribute(k_fir_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) set_bytes = smem;
+    }
+    return e;
+}
+
+cudaError_t prepare_fir_tc_ws(size_t smem) {
+    static size_t set_bytes = 0;
     if (smem <= set_bytes) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_fir_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_fir_tc_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) set_bytes = smem;
     return e;
 }
@@ -242,7 +496,12 @@ cudaError_t prepare_fir_tc(size_t smem) {
 cudaError_t launch_fir_tc(const FirTcArgs& a, cudaStream_t s) {
     const int64_t tiles = a.C * a.ntt;
     if (tiles <= 0) return cudaSuccess;
-    k_fir_tc<<<(unsigned)tiles, 256, fir_tc_smem_bytes(a), s>>>(a);
+    if (a.persistent) {
+        const int64_t grid = tiles < a.grid ? tiles : a.grid;
+        k_fir_tc_ws<<<(unsigned)grid, WS_THREADS, fir_tc_smem_bytes(a), s>>>(a);
+    } else {
+        k_fir_tc<<<(unsigned)tiles, 256, fir_tc_smem_bytes(a), s>>>(a);
+    }
     return cudaGetLastError();
 }
 

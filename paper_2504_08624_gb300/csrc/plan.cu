@@ -38,6 +38,8 @@ struct HostUnit {
     size_t off_ahi = 0, off_alo = 0, tc_smem = 0;
     int tc_mode = 0;
     float tap_unscale = 1.0f;
+    bool tc_persistent = false;  // persistent warp-specialised kernel (2-stage windows fit)
+    size_t tc_smem_ws = 0;
     // cascade without an FIR: warp-per-tile scan (tiles of 32 * T_CHUNK samples)
     bool warp = false;
 };
@@ -68,6 +70,7 @@ struct tfx_plan {
     size_t scratch_bytes = 0;  // header + tails
     size_t buf_bytes = 0;      // one intermediate [C x N] buffer
     size_t ws_fused = 0, ws_plain = 0;
+    int sm_count = 1;  // persistent grid size
 };
 
 namespace {
@@ -163,6 +166,13 @@ void tc_geometry(HostUnit& u, int NB) {
 // Pick the tile width for a tensor-core FIR: 128 blocks (16384 outputs) when
 // two CTAs fit on an SM, else the widest that fits one CTA; false if none does.
 bool choose_tc(HostUnit& u) {
+    // persistent kernel: NB = 128, two window stages next to the resident taps
+    tc_geometry(u, 128);
+    u.tc_smem_ws = (size_t)u.a_chunks * 128 * 2 + (size_t)16 * u.rows * 16 * 4 + 10 * 8 + 12 * 4 + 32;
+    if (u.tc_smem_ws <= SMEM_MAX) {
+        u.tc_persistent = true;
+        return true;
+    }
     const int cands[] = {128, 256, 64};
     for (int nb : cands) {
         tc_geometry(u, nb);
@@ -357,6 +367,10 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
     }
 
     if (upload) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return TFX_ERR_CUDA;
         if (cudaMalloc(&p->dconst, host.size()) != cudaSuccess) return TFX_ERR_NOMEM;
         if (cudaMemcpy(p->dconst, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
             return TFX_ERR_CUDA;
@@ -364,7 +378,11 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         if (cudaMemset(p->dstatus, 0, sizeof(int)) != cudaSuccess) return TFX_ERR_CUDA;
         for (HostUnit& u : p->units) {
             if (u.tc) {
-                if (prepare_fir_tc(u.tc_smem) != cudaSuccess) return TFX_ERR_UNSUPPORTED;
+                if (u.tc_persistent) {
+                    if (prepare_fir_tc_ws(u.tc_smem_ws) != cudaSuccess) return TFX_ERR_UNSUPPORTED;
+                } else if (prepare_fir_tc(u.tc_smem) != cudaSuccess) {
+                    return TFX_ERR_UNSUPPORTED;
+                }
                 continue;
             }
             UnitConst k{};
@@ -445,6 +463,8 @@ int launch_unit_range(tfx_plan* p, int i, const float* in, int64_t ldin, float* 
         f.a_chunks = u.a_chunks;
         f.mode = u.tc_mode;
         f.tap_unscale = u.tap_unscale;
+        f.persistent = u.tc_persistent ? 1 : 0;
+        f.grid = p->sm_count;
         f.a_hi = reinterpret_cast<const uint4*>(p->dconst + u.off_ahi);
         f.a_lo = reinterpret_cast<const uint4*>(p->dconst + u.off_alo);
         f.status = p->dstatus;
