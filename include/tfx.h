@@ -157,6 +157,27 @@ int tfx_sos(const float *x, float *y, int64_t C, int64_t N, int64_t ld,
 int tfx_chain(const float *x, float *y, int64_t C, int64_t N, int64_t ld,
               const tfx_stage *st, int32_t nst, void *ws, size_t ws_bytes,
               tfx_stream s);
+/*
+ * tfx_chain_host -- the chain of tfx_chain over signals in HOST memory (the
+ * call a serving process makes with audio it holds on the host).  x and y are
+ * host pointers with the same [C x N] layout and row stride ld (x == y
+ * allowed); page-locked (pinned) buffers let the copies run asynchronously
+ * and overlap, pageable ones still work but serialise.  Channels are cut
+ * into groups of about 2^24 samples; group g is copied in, filtered and
+ * copied out on three library-owned streams through a ring of three device
+ * slots, so copies of neighbouring groups overlap each other and the
+ * filtering.  The work is ordered after prior work on s and s waits for it:
+ * synchronise s before reading y.  The first call for a configuration
+ * builds its plans and allocates the device slots (host-synchronous); later
+ * calls allocate nothing.
+ * Errors: as tfx_chain, plus TFX_ERR_NOMEM for the device slots.
+ */
+int tfx_chain_host(const float *x, float *y, int64_t C, int64_t N, int64_t ld,
+                   const tfx_stage *st, int32_t nst, tfx_stream s);
+
+/* Release the cached host-buffer pipelines (synchronises the device). */
+void tfx_host_cache_clear(void);
+
 /* Workspace tfx_chain needs for these arguments (SIZE_MAX if invalid). */
 size_t tfx_chain_workspace_size(int64_t C, int64_t N, int64_t ld,
                                 const tfx_stage *st, int32_t nst);

@@ -35,6 +35,7 @@ EXPORTS = [
     "tfx_plan_create", "tfx_plan_workspace_size", "tfx_plan_launch_count", "tfx_plan_execute", "tfx_plan_execute_plain",
     "tfx_plan_get_error", "tfx_plan_destroy", "tfx_fir", "tfx_sos", "tfx_chain",
     "tfx_chain_workspace_size", "tfx_cache_clear", "tfx_sos_noalloc", "tfx_strerror", "tfx_version",
+    "tfx_chain_host", "tfx_host_cache_clear",
 ]
 
 
@@ -84,6 +85,10 @@ def lib():
     L.tfx_sos.restype = ctypes.c_int
     L.tfx_chain.argtypes = [fp, fp, i64, i64, i64, sp, i32, vp, sz, vp]
     L.tfx_chain.restype = ctypes.c_int
+    L.tfx_chain_host.argtypes = [fp, fp, i64, i64, i64, sp, i32, vp]
+    L.tfx_chain_host.restype = ctypes.c_int
+    L.tfx_host_cache_clear.argtypes = []
+    L.tfx_host_cache_clear.restype = None
     L.tfx_chain_workspace_size.argtypes = [i64, i64, i64, sp, i32]
     L.tfx_chain_workspace_size.restype = sz
     L.tfx_sos_noalloc.argtypes = [fp, fp, i64, i64, i64, dp, i32, vp]

@@ -5,8 +5,9 @@ channel of a signal and chains them with a pipe operator; this module exposes
 the same operation: ``chain(x, stages)`` with stages applied in list order,
 plus ``fir`` / ``sos`` shortcuts and a reusable ``Plan``.  PyTorch supplies
 device memory and the current CUDA stream; the filtering itself runs in the
-CUDA library.  CPU tensors are accepted: they are copied to the GPU (from
-pinned memory when they are pinned), filtered there and copied back.
+CUDA library.  CPU tensors are accepted: ``tfx_chain_host`` copies channel
+groups to the GPU, filters them and copies them back with the copies and the
+filtering overlapped (pinned tensors let the copies run asynchronously).
 """
 from __future__ import annotations
 
@@ -47,7 +48,7 @@ def chain(x: torch.Tensor, stages, out: torch.Tensor | None = None) -> torch.Ten
     x2 = _check_signal(x)
     if not x2.is_cuda:
         y = _chain_host(x2, stages, out)
-        return y[0] if squeeze and out is None else y
+        return y[0] if squeeze and y.dim() == 2 and out is None else y
     if out is None:
         out2 = torch.empty_like(x2, memory_format=torch.contiguous_format)
         if x2.stride() != out2.stride():
@@ -71,12 +72,25 @@ def chain(x: torch.Tensor, stages, out: torch.Tensor | None = None) -> torch.Ten
 
 
 def _chain_host(x: torch.Tensor, stages, out):
-    dev = torch.device("cuda", torch.cuda.current_device())
-    xd = x.to(dev, non_blocking=x.is_pinned())
-    yd = chain(xd, stages, out=xd)
+    """Host tensors: tfx_chain_host copies channel groups in, filters them and
+    copies them out with the three overlapped (pinned buffers give overlap);
+    returns once the result is in host memory."""
     if out is None:
-        return yd.to("cpu")
-    out.copy_(yd, non_blocking=out.is_pinned())
+        out = torch.empty(x.shape, dtype=torch.float32, pin_memory=x.is_pinned())
+    out2 = _check_signal(out)
+    if out2.is_cuda or out2.shape != x.shape:
+        raise ValueError("out must be a host tensor of x's shape")
+    if out2.stride() != x.stride():
+        raise ValueError("out must have the same strides as x")
+    C, Ns = x.shape
+    ld = _row_stride(x)
+    sl = N.StageList(stages)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    rc = N.lib().tfx_chain_host(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out2.data_ptr()), C, Ns, ld,
+                                sl.arr, sl.n, ctypes.c_void_p(stream.cuda_stream))
+    N.check(rc, "tfx_chain_host")
+    stream.synchronize()
     return out
 
 

@@ -1,0 +1,207 @@
+// tfx_chain_host: a chain over signals that live in host memory.  The
+// channels are cut into groups of about 2^24 samples; group g is copied in
+// on one stream, filtered on a second and copied out on a third, through a
+// ring of three device slots, so that the host<->device copies of
+// neighbouring groups overlap each other and the filtering.  The plans,
+// slots, streams and events are library-owned and cached per configuration.
+#include <cstring>
+#include <list>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+
+#include "tfx_common.cuh"
+
+namespace {
+
+constexpr int RING = 3;
+constexpr int64_t GROUP_SAMPLES = int64_t(1) << 24;
+constexpr size_t HOST_CACHE_MAX = 4;
+
+struct HostPipe {
+    int64_t C = 0, N = 0, Cg = 0;
+    int G = 0;
+    tfx_plan* plan_full = nullptr;  // Cg channels
+    tfx_plan* plan_last = nullptr;  // the last group's channel count, if smaller
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    float* dx[RING] = {};
+    float* dy[RING] = {};
+    cudaStream_t sin = nullptr, scomp = nullptr, sout = nullptr;
+    cudaEvent_t ev_in[RING] = {}, ev_comp[RING] = {}, ev_out[RING] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[3] = {};
+};
+
+void destroy_pipe(HostPipe* h) {
+    if (!h) return;
+    cudaDeviceSynchronize();
+    tfx_plan_destroy(h->plan_full);
+    tfx_plan_destroy(h->plan_last);
+    if (h->ws) cudaFree(h->ws);
+    for (int r = 0; r < RING; ++r) {
+        if (h->dx[r]) cudaFree(h->dx[r]);
+        if (h->dy[r]) cudaFree(h->dy[r]);
+        for (cudaEvent_t e : {h->ev_in[r], h->ev_comp[r], h->ev_out[r]})
+            if (e) cudaEventDestroy(e);
+    }
+    for (cudaStream_t st : {h->sin, h->scomp, h->sout})
+        if (st) cudaStreamDestroy(st);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    for (cudaEvent_t e : h->ev_join)
+        if (e) cudaEventDestroy(e);
+    delete h;
+}
+
+int build_pipe(int64_t C, int64_t N, const tfx_stage* st, int32_t nst, HostPipe** out) {
+    HostPipe* h = new (std::nothrow) HostPipe();
+    if (!h) return TFX_ERR_NOMEM;
+    h->C = C;
+    h->N = N;
+    h->Cg = (GROUP_SAMPLES + N - 1) / N;
+    if (h->Cg < 1) h->Cg = 1;
+    if (h->Cg > C) h->Cg = C;
+    h->G = (int)((C + h->Cg - 1) / h->Cg);
+    const int64_t last = C - (int64_t)(h->G - 1) * h->Cg;
+    int rc = tfx_plan_create(&h->plan_full, h->Cg, N, N, st, nst, TFX_PLAN_DEFAULT);
+    if (rc == TFX_OK && last != h->Cg) rc = tfx_plan_create(&h->plan_last, last, N, N, st, nst, TFX_PLAN_DEFAULT);
+    if (rc != TFX_OK) {
+        destroy_pipe(h);
+        return rc;
+    }
+    h->ws_bytes = tfx_plan_workspace_size(h->plan_full);
+    if (h->plan_last && tfx_plan_workspace_size(h->plan_last) > h->ws_bytes)
+        h->ws_bytes = tfx_plan_workspace_size(h->plan_last);
+    const size_t slot = (size_t)h->Cg * (size_t)N * sizeof(float);
+    bool ok = h->ws_bytes == 0 || cudaMalloc(&h->ws, h->ws_bytes) == cudaSuccess;
+    for (int r = 0; r < RING && ok; ++r)
+        ok = cudaMalloc(&h->dx[r], slot) == cudaSuccess && cudaMalloc(&h->dy[r], slot) == cudaSuccess;
+    if (!ok) {
+        destroy_pipe(h);
+        return TFX_ERR_NOMEM;
+    }
+    ok = cudaStreamCreateWithFlags(&h->sin, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&h->scomp, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&h->sout, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int r = 0; r < RING && ok; ++r)
+        ok = cudaEventCreateWithFlags(&h->ev_in[r], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&h->ev_comp[r], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&h->ev_out[r], cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; k < 3 && ok; ++k) ok = cudaEventCreateWithFlags(&h->ev_join[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        destroy_pipe(h);
+        return TFX_ERR_CUDA;
+    }
+    *out = h;
+    return TFX_OK;
+}
+
+int run_pipe(HostPipe* h, const float* x, float* y, int64_t ld, cudaStream_t s) {
+    const int64_t N = h->N;
+#define TFX_CK(call)                              \
+    do {                                          \
+        if ((call) != cudaSuccess) return TFX_ERR_CUDA; \
+    } while (0)
+    TFX_CK(cudaEventRecord(h->ev_fork, s));
+    TFX_CK(cudaStreamWaitEvent(h->sin, h->ev_fork, 0));
+    TFX_CK(cudaStreamWaitEvent(h->scomp, h->ev_fork, 0));
+    TFX_CK(cudaStreamWaitEvent(h->sout, h->ev_fork, 0));
+    for (int g = 0; g < h->G; ++g) {
+        const int r = g % RING;
+        const int64_t c0 = (int64_t)g * h->Cg;
+        const int64_t cn = (g == h->G - 1) ? h->C - c0 : h->Cg;
+        tfx_plan* p = (cn == h->Cg) ? h->plan_full : h->plan_last;
+        // slot r is free once the copy-out of group g - RING has finished
+        if (g >= RING) TFX_CK(cudaStreamWaitEvent(h->sin, h->ev_out[r], 0));
+        TFX_CK(cudaMemcpy2DAsync(h->dx[r], (size_t)N * sizeof(float), x + c0 * ld, (size_t)ld * sizeof(float),
+                                 (size_t)N * sizeof(float), (size_t)cn, cudaMemcpyHostToDevice, h->sin));
+        TFX_CK(cudaEventRecord(h->ev_in[r], h->sin));
+        TFX_CK(cudaStreamWaitEvent(h->scomp, h->ev_in[r], 0));
+        const int rc = tfx_plan_execute(p, h->dx[r], h->dy[r], h->ws, h->ws_bytes, h->scomp);
+        if (rc != TFX_OK) return rc;
+        TFX_CK(cudaEventRecord(h->ev_comp[r], h->scomp));
+        TFX_CK(cudaStreamWaitEvent(h->sout, h->ev_comp[r], 0));
+        TFX_CK(cudaMemcpy2DAsync(y + c0 * ld, (size_t)ld * sizeof(float), h->dy[r], (size_t)N * sizeof(float),
+                                 (size_t)N * sizeof(float), (size_t)cn, cudaMemcpyDeviceToHost, h->sout));
+        TFX_CK(cudaEventRecord(h->ev_out[r], h->sout));
+    }
+    TFX_CK(cudaEventRecord(h->ev_join[0], h->sin));
+    TFX_CK(cudaEventRecord(h->ev_join[1], h->scomp));
+    TFX_CK(cudaEventRecord(h->ev_join[2], h->sout));
+    for (int k = 0; k < 3; ++k) TFX_CK(cudaStreamWaitEvent(s, h->ev_join[k], 0));
+#undef TFX_CK
+    return TFX_OK;
+}
+
+std::mutex g_hmu;
+std::list<std::string> g_hlru;
+std::unordered_map<std::string, std::pair<HostPipe*, std::list<std::string>::iterator>> g_hcache;
+
+std::string host_key(int64_t C, int64_t N, const tfx_stage* st, int32_t nst, cudaStream_t s) {
+    std::string k;
+    auto put = [&](const void* p, size_t n) { k.append(static_cast<const char*>(p), n); };
+    put(&C, 8);
+    put(&N, 8);
+    put(&s, sizeof(s));
+    put(&nst, 4);
+    for (int32_t i = 0; i < nst; ++i) {
+        put(&st[i].kind, 4);
+        put(&st[i].n, 4);
+        const size_t cnt = st[i].kind == TFX_STAGE_SOS ? (size_t)st[i].n * 6 : (size_t)st[i].n;
+        if (cnt && st[i].coef) put(st[i].coef, cnt * sizeof(double));
+    }
+    return k;
+}
+
+}  // namespace
+
+extern "C" int tfx_chain_host(const float* x, float* y, int64_t C, int64_t N, int64_t ld, const tfx_stage* st,
+                              int32_t nst, tfx_stream stream) {
+    if (C < 0 || N < 0 || ld < (N > 1 ? N : 1) || nst < 0 || (nst > 0 && !st)) return TFX_ERR_INVALID;
+    if (C == 0 || N == 0) return TFX_OK;
+    if (!x || !y) return TFX_ERR_INVALID;
+    if (x != y) {
+        const char* xb = reinterpret_cast<const char*>(x);
+        const char* yb = reinterpret_cast<const char*>(y);
+        const size_t span = ((size_t)(C - 1) * (size_t)ld + (size_t)N) * sizeof(float);
+        if (xb < yb + span && yb < xb + span) return TFX_ERR_INVALID;
+    }
+    // validate the stages the way a plan would, before anything is allocated
+    {
+        const size_t need = tfx_chain_workspace_size(1, N, N, st, nst);
+        if (need == SIZE_MAX) {
+            tfx_plan* probe = nullptr;
+            const int rc = tfx_plan_create(&probe, 0, N, N, st, nst, TFX_PLAN_DEFAULT);
+            tfx_plan_destroy(probe);
+            return rc != TFX_OK ? rc : TFX_ERR_INVALID;
+        }
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const std::string key = host_key(C, N, st, nst, s);
+    std::lock_guard<std::mutex> lk(g_hmu);
+    HostPipe* h = nullptr;
+    auto it = g_hcache.find(key);
+    if (it != g_hcache.end()) {
+        g_hlru.splice(g_hlru.begin(), g_hlru, it->second.second);
+        h = it->second.first;
+    } else {
+        if (g_hcache.size() >= HOST_CACHE_MAX) {
+            auto oit = g_hcache.find(g_hlru.back());
+            destroy_pipe(oit->second.first);
+            g_hcache.erase(oit);
+            g_hlru.pop_back();
+        }
+        const int rc = build_pipe(C, N, st, nst, &h);
+        if (rc != TFX_OK) return rc;
+        g_hlru.push_front(key);
+        g_hcache.emplace(key, std::make_pair(h, g_hlru.begin()));
+    }
+    return run_pipe(h, x, y, ld, s);
+}
+
+extern "C" void tfx_host_cache_clear(void) {
+    std::lock_guard<std::mutex> lk(g_hmu);
+    for (auto& kv : g_hcache) destroy_pipe(kv.second.first);
+    g_hcache.clear();
+    g_hlru.clear();
+}

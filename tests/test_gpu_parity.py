@@ -283,3 +283,27 @@ def test_cascade_tensor_fir_graph_capture():
     torch.cuda.synchronize()
     assert_close(y.cpu().numpy(), oracle_chain(x, wl.stages), wl.tol, "graph replay")
     p.close()
+
+
+@pytest.mark.parametrize("mode", ["pinned", "pageable", "inplace_padded"])
+def test_host_pipeline_groups(mode):
+    """tfx_chain_host: 600 channels x 100,000 samples cut into 4 groups of
+    about 2^24 samples, so the 3-slot device ring wraps."""
+    from paper_2504_08624_gb300 import api
+    stages = [("sos", W.butter_sos(2, 2000.0, 48000.0)), ("fir", W.fir_lowpass(33, 6000.0, 48000.0))]
+    C, Ns = 600, 100000
+    x = W.white_uniform(C, Ns, 61)
+    ref = oracle_chain(x, stages)
+    if mode == "inplace_padded":
+        ld = Ns + 9
+        buf = torch.zeros(C * ld, dtype=torch.float32).pin_memory()
+        v = buf.view(C, ld)[:, :Ns]
+        v.copy_(torch.from_numpy(x))
+        api.chain(v, stages, out=v)
+        got = v.numpy()
+    else:
+        xt = torch.from_numpy(x)
+        if mode == "pinned":
+            xt = xt.pin_memory()
+        got = api.chain(xt, stages).numpy()
+    assert_close(got, ref, tol_for(stages), mode)
