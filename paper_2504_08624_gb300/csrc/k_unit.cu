@@ -134,26 +134,62 @@ __global__ void __launch_bounds__(NTH, HAS_FIR ? 2 : 4) k_unit(UnitArgs a) {
         // transposed direct form II, updated as w1' = c1 u - a1 w1 + w2,
         // w2' = c2 u - a2 w1, y = b0 u + w1, with c1 = b1 - a1 b0, c2 = b2 - a2 b0
         // formed in FP64 at plan time (avoids cancelling b1 u against a1 y).
-        float w1 = 0.f, w2 = 0.f, h1 = 0.f, h2 = 0.f;
+        // Three loop bodies, so that no predicated-off instruction is issued.
+        float w1 = 0.f, w2 = 0.f;
+        if (run && !fix) {
 #pragma unroll
-        for (int t = 0; t < T; ++t) {
-            float v = u[t];
-            if (fix) {
-                float h;
-                if (t == 0) h = st.x;
-                else if (t == 1) h = fmaf(-pa1, h1, st.y);
-                else h = fmaf(-pa1, h1, -pa2 * h2);
-                h2 = h1;
-                h1 = h;
-                v += h;
-            }
-            if (run) {
+            for (int t = 0; t < T; ++t) {
+                const float v = u[t];
                 u[t] = fmaf(b0, v, w1);
                 const float n1 = fmaf(c1, v, fmaf(-a1, w1, w2));
                 w2 = fmaf(c2, v, -a2 * w1);
                 w1 = n1;
-            } else {
-                u[t] = v;
+            }
+        } else if (run) {
+            float h1 = st.x, h2 = 0.f;
+            {
+                const float v = u[0] + st.x;
+                u[0] = fmaf(b0, v, w1);
+                const float n1 = fmaf(c1, v, fmaf(-a1, w1, w2));
+                w2 = fmaf(c2, v, -a2 * w1);
+                w1 = n1;
+            }
+            {
+                const float h = fmaf(-pa1, h1, st.y);
+                h2 = h1;
+                h1 = h;
+                const float v = u[1] + h;
+                u[1] = fmaf(b0, v, w1);
+                const float n1 = fmaf(c1, v, fmaf(-a1, w1, w2));
+                w2 = fmaf(c2, v, -a2 * w1);
+                w1 = n1;
+            }
+#pragma unroll
+            for (int t = 2; t < T; ++t) {
+                const float h = fmaf(-pa1, h1, -pa2 * h2);
+                h2 = h1;
+                h1 = h;
+                const float v = u[t] + h;
+                u[t] = fmaf(b0, v, w1);
+                const float n1 = fmaf(c1, v, fmaf(-a1, w1, w2));
+                w2 = fmaf(c2, v, -a2 * w1);
+                w1 = n1;
+            }
+        } else if (fix) {
+            float h1 = st.x, h2 = 0.f;
+            u[0] += st.x;
+            {
+                const float h = fmaf(-pa1, h1, st.y);
+                h2 = h1;
+                h1 = h;
+                u[1] += h;
+            }
+#pragma unroll
+            for (int t = 2; t < T; ++t) {
+                const float h = fmaf(-pa1, h1, -pa2 * h2);
+                h2 = h1;
+                h1 = h;
+                u[t] += h;
             }
         }
         if (!run) break;
