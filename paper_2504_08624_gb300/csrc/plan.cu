@@ -38,7 +38,7 @@ struct HostUnit {
     size_t off_ahi = 0, off_alo = 0, tc_smem = 0;
     int tc_mode = 0;
     float tap_unscale = 1.0f;
-    bool tc_persistent = false;  // persistent warp-specialised kernel (2-stage windows fit)
+    int tc_variant = 0;  // 0: one tile per CTA, 1: persistent resident taps, 2: persistent streamed taps
     size_t tc_smem_ws = 0;
     // cascade without an FIR: warp-per-tile scan (tiles of 32 * T_CHUNK samples)
     bool warp = false;
@@ -170,7 +170,13 @@ bool choose_tc(HostUnit& u) {
     tc_geometry(u, 128);
     u.tc_smem_ws = (size_t)u.a_chunks * 128 * 2 + (size_t)16 * u.rows * 16 * 4 + 10 * 8 + 12 * 4 + 32;
     if (u.tc_smem_ws <= SMEM_MAX) {
-        u.tc_persistent = true;
+        u.tc_variant = 1;
+        return true;
+    }
+    // long FIRs: taps streamed in K-blocks, one resident window
+    u.tc_smem_ws = fir_tc_long_smem(u.rows);
+    if (u.tc_smem_ws <= SMEM_MAX) {
+        u.tc_variant = 2;
         return true;
     }
     const int cands[] = {128, 256, 64};
@@ -378,8 +384,10 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         if (cudaMemset(p->dstatus, 0, sizeof(int)) != cudaSuccess) return TFX_ERR_CUDA;
         for (HostUnit& u : p->units) {
             if (u.tc) {
-                if (u.tc_persistent) {
+                if (u.tc_variant == 1) {
                     if (prepare_fir_tc_ws(u.tc_smem_ws) != cudaSuccess) return TFX_ERR_UNSUPPORTED;
+                } else if (u.tc_variant == 2) {
+                    if (prepare_fir_tc_long(u.tc_smem_ws) != cudaSuccess) return TFX_ERR_UNSUPPORTED;
                 } else if (prepare_fir_tc(u.tc_smem) != cudaSuccess) {
                     return TFX_ERR_UNSUPPORTED;
                 }
@@ -463,7 +471,7 @@ int launch_unit_range(tfx_plan* p, int i, const float* in, int64_t ldin, float* 
         f.a_chunks = u.a_chunks;
         f.mode = u.tc_mode;
         f.tap_unscale = u.tap_unscale;
-        f.persistent = u.tc_persistent ? 1 : 0;
+        f.persistent = u.tc_variant;
         f.grid = p->sm_count;
         f.a_hi = reinterpret_cast<const uint4*>(p->dconst + u.off_ahi);
         f.a_lo = reinterpret_cast<const uint4*>(p->dconst + u.off_alo);

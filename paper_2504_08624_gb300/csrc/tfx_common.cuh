@@ -92,7 +92,8 @@ struct FirTcArgs {
     int tmem_cols;    // TMEM columns allocated (power of two >= NB)
     int a_chunks;     // 16-byte chunks per tap table = 2 * nK + 16
     int mode;         // FIR_TC_FP16_SPLIT, FIR_TC_BF16_SPLIT or FIR_TC_BF16_PLAIN
-    int persistent;   // 1: persistent warp-specialised kernel (NB = 128, 2-stage windows)
+    int persistent;   // 0: one tile per CTA; 1: persistent, resident taps, 2-stage windows;
+                      // 2: persistent, taps streamed in K-blocks, single window
     int grid;         // persistent grid size (one CTA per SM)
     float tap_unscale;  // 1 / (power-of-two scale applied to the FP16 taps)
     const uint4* a_hi;  // [a_chunks][8 copies] high parts of the shifted (scaled) taps
@@ -212,6 +213,9 @@ size_t unit_smem_bytes(const UnitConst& k);
 size_t fir_tc_smem_bytes(const FirTcArgs& a);
 cudaError_t prepare_fir_tc(size_t smem);
 cudaError_t prepare_fir_tc_ws(size_t smem);
+cudaError_t prepare_fir_tc_long(size_t smem);
+size_t fir_tc_long_smem(int rows);
+constexpr int TC_KBLK = 64;  // K-steps per streamed tap block
 cudaError_t launch_fir_tc(const FirTcArgs& a, cudaStream_t s);
 cudaError_t prepare_unit(const UnitConst& k);
 

@@ -307,3 +307,22 @@ def test_host_pipeline_groups(mode):
             xt = xt.pin_memory()
         got = api.chain(xt, stages).numpy()
     assert_close(got, ref, tol_for(stages), mode)
+
+
+@pytest.mark.parametrize("mode", ["fp16_split", "bf16_split", "bf16_plain"])
+def test_long_fir_streamed_taps(mode):
+    """The 16384-tap Kaiser band-pass of the long-FIR workload (tap tables
+    streamed through shared memory): split modes meet 1e-5 of the peak, plain
+    BF16 is reported."""
+    from paper_2504_08624_gb300 import _native as N
+    wl = W.long_fir()
+    flags = {"fp16_split": 0, "bf16_split": N.TFX_PLAN_FIR_BF16_SPLIT, "bf16_plain": N.TFX_PLAN_FIR_BF16_PLAIN}[mode]
+    x = wl.make_signal(2, 3 * 16384 + 1234)
+    got = run(x, wl.stages, flags=flags)
+    ref = oracle_chain(x, wl.stages)
+    if mode == "bf16_plain":
+        from tests.gpu_util import per_channel_rel_err
+        rel = per_channel_rel_err(got, ref)[0].max()
+        assert 1e-5 < rel < 1e-1, rel
+    else:
+        assert_close(got, ref, 1e-5, mode)
