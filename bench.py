@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--flags", type=int, default=0, help="TFX_PLAN_* bits for the timed plan")
     ap.add_argument("--channels", type=int, default=None, help="override channel count (testing only)")
     ap.add_argument("--samples", type=int, default=None, help="override samples per channel (testing only)")
+    ap.add_argument("--workload", default="multichannel_fused",
+                    choices=["multichannel_fused", "plain_chain", "long_fir", "table4_chain", "differentiable_chain"],
+                    help="configuration to time (default: the one the headline metric is quoted on)")
     ap.add_argument("--part", choices=["chain", "iir", "fir"], default="chain",
                     help="time the whole chain (default) or only its IIR cascade / FIR stage (profiling)")
     return ap.parse_args()
@@ -62,7 +65,7 @@ def dist_env():
 
 def workload(args):
     from paper_2504_08624_gb300 import workloads as W
-    wl = W.multichannel_fused()
+    wl = W.WORKLOADS[getattr(args, "workload", "multichannel_fused")]()
     if args.channels:
         wl.C = args.channels
     if args.samples:
@@ -329,6 +332,7 @@ def main():
     step_s = t_dev / args.steps
     achieved_gbs = units * bytes_ps / step_s / 1e9
     tensor_fir = (args.flags & NAT.TFX_PLAN_FIR_CUDA_CORES) == 0 and L >= 64
+    fir_kernel = "k_fir_tc_ws" if L <= 2048 else "k_fir_tc_long"
     if tensor_fir:
         # dominant kernel: the tensor-core Toeplitz FIR, timed alone with CUDA
         # events on its launch stream through a FIR-only plan (same kernel and
@@ -339,7 +343,7 @@ def main():
         k_fir = max(10, args.steps // 3)
         t_fir = time_gpu(lambda: fplan.execute(y, x_fir, fws), k_fir, 3, stream, torch, None) / k_fir
         fplan.close()
-        kern = "k_fir_tc_ws"  # the persistent kernel the plan picks for this tap count
+        kern = fir_kernel  # the persistent kernel the plan picks for this tap count
         K = -(-(L - 1) // 16) * 16 + 128
         bound = {"bound": "tensor", "kernel": kern, "achieved": units * 2.0 * L / t_fir / 1e12,
                  "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
@@ -362,9 +366,12 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         ncpu = os.cpu_count() or 1
         Cs = min(wl.C, ncpu)
-        rate, dt, thr = cpu_oracle_rate(wl, Cs, wl.N)
+        # bounded sample: about 1.6e11 multiply-adds (10-30 s on the host cores)
+        macs = max(1.0, flops_ps / 2.0)
+        Ns = int(min(wl.N, max(16384, 1.6e11 / (Cs * macs))))
+        rate, dt, thr = cpu_oracle_rate(wl, Cs, Ns)
         cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
-               "sample": f"{Cs} of {wl.C} channels at full length ({wl.N} samples), FP64 oracle chain, "
+               "sample": f"{Cs} of {wl.C} channels x first {Ns} of {wl.N} samples, FP64 oracle chain, "
                          f"{dt:.1f} s on {thr} threads"}
 
     if rank == 0:
@@ -374,7 +381,7 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl.name if args.part == "chain" else f"{wl.name} ({args.part} only)",
                        "channels": wl.C, "samples": wl.N,
-                       "chain": f"cheby1 order 8 + 4 peaking (S={S}) + fir {L} taps",
+                       "chain": f"{S} SOS sections + FIR of {L} taps",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "l2": "inputs 737 MB > 129 MB L2, no flush", "plan_flags": args.flags},
             "roofline": bound, "roofline_hbm": hbm, "cpu_baseline": cpu, "e2e": e2e,
