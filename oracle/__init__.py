@@ -13,6 +13,10 @@ The arithmetic lives in ``oracle.c`` (plain C, double precision):
                  Table 2 workload).
   * ``chain`` -- stages applied in list order (TorchFX Sec. 3, pipe operator;
                  Table 4 workload).
+  * ``chain_vjp`` -- gradients of sum(g * chain(x)) w.r.t. x and every
+                 coefficient, from the chain's impulse response and from
+                 forward-mode sensitivities of the difference equations
+                 (the filters as layers inside a network, Sec. 3).
 
 Parity is pinned by closed forms and brute force in ``tests/test_oracle.py``.
 """
@@ -45,6 +49,9 @@ class OracleLib:
         lib.oracle_chain.argtypes = [dp, dp, i64, i64, ctypes.POINTER(i32),
                                      ctypes.POINTER(i32), ctypes.POINTER(dp), i32]
         lib.oracle_chain.restype = ctypes.c_int
+        lib.oracle_chain_vjp.argtypes = [dp, dp, dp, dp, i64, i64, ctypes.POINTER(i32),
+                                         ctypes.POINTER(i32), ctypes.POINTER(dp), i32]
+        lib.oracle_chain_vjp.restype = ctypes.c_int
         lib.oracle_num_threads.restype = ctypes.c_int
         lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
         lib.oracle_plant.restype = ctypes.c_int
@@ -109,6 +116,40 @@ class OracleLib:
         if rc != 0:
             raise ValueError(f"oracle_chain failed ({rc})")
         return y[0] if sq else y
+
+    def chain_vjp(self, x, g, stages):
+        """(dL/dx, [dL/dcoef per stage]) for upstream gradient g = dL/dy."""
+        x2, sq = self._as_signal(x)
+        g2, _ = self._as_signal(g)
+        if g2.shape != x2.shape:
+            raise ValueError("g must match x")
+        kinds, counts, keep = [], [], []
+        for kind, coef in stages:
+            if kind == "fir":
+                c = np.ascontiguousarray(np.asarray(coef, dtype=np.float64).ravel())
+                kinds.append(FIR)
+                counts.append(c.size)
+            else:
+                c = np.ascontiguousarray(np.asarray(coef, dtype=np.float64).reshape(-1, 6))
+                kinds.append(SOS)
+                counts.append(c.shape[0])
+            keep.append(c)
+        n = len(keep)
+        sizes = [c.size for c in keep]
+        dcoef = np.zeros(max(1, sum(sizes)))
+        ks = (ctypes.c_int32 * max(n, 1))(*kinds)
+        cs = (ctypes.c_int32 * max(n, 1))(*counts)
+        ptrs = (ctypes.POINTER(ctypes.c_double) * max(n, 1))(*[self._dp(c) for c in keep])
+        dx = np.empty_like(x2)
+        rc = self.lib.oracle_chain_vjp(self._dp(x2), self._dp(g2), self._dp(dx), self._dp(dcoef),
+                                       x2.shape[0], x2.shape[1], ks, cs, ptrs, n)
+        if rc != 0:
+            raise ValueError(f"oracle_chain_vjp failed ({rc})")
+        grads, off = [], 0
+        for c in keep:
+            grads.append(dcoef[off:off + c.size].reshape(c.shape))
+            off += c.size
+        return (dx[0] if sq else dx), grads
 
     def num_threads(self) -> int:
         return int(self.lib.oracle_num_threads())

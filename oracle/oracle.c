@@ -20,7 +20,7 @@
  *     y[n] = sum_{k=0}^{min(n, L-1)} h[k] * x[n-k].
  * A chain applies its stages in list order.  All arithmetic is in double.
  *
- * Planted mistakes: compiling with -DORACLE_PLANT=k (k = 1..6) introduces one
+ * Planted mistakes: compiling with -DORACLE_PLANT=k (k = 1..7) introduces one
  * deliberate error so that the test suite can show its pins catch it.  The
  * default build (ORACLE_PLANT undefined or 0) is the oracle.
  */
@@ -234,3 +234,135 @@ void oracle_set_num_threads(int n)
 }
 
 int oracle_plant(void) { return ORACLE_PLANT; }
+
+/*
+ * Vector-Jacobian product of a chain: for an upstream gradient g = dL/dy,
+ * returns dL/dx and dL/d(coefficients).  Computed from definitions, not by
+ * the adjoint method:
+ *   - dL/dx[m] = sum_n g[n] dy[n]/dx[m] = sum_n g[n] h_chain[n-m], with the
+ *     chain's impulse response h_chain obtained by running the chain on a
+ *     unit impulse (the chain is linear and time invariant in x);
+ *   - coefficient derivatives by forward-mode sensitivity: differentiating a
+ *     section's difference equation a0 y[n] = sum b_k u[n-k] - a1 y[n-1] -
+ *     a2 y[n-2] gives, for each coefficient p, the recursion
+ *       a0 s[n] = d(rhs)/dp - a1 s[n-1] - a2 s[n-2]   (s = dy/dp, s[<0] = 0),
+ *     with d(rhs)/db_k = u[n-k], d(rhs)/da_k = -y[n-k] (k = 1, 2) and
+ *     d(rhs)/da0 = -y[n]; the sensitivity then passes through the remaining
+ *     stages (linear in their input) and dL/dp = sum_n g[n] * (that signal);
+ *     for an FIR tap dy[n]/dh_k = u[n-k].
+ * coef_grads: one block per stage, FIR: L doubles; SOS: 6 doubles per row.
+ * Gradients are summed over channels.  O(N^2) for dx: small inputs only.
+ */
+static void chain_tail(const double *in, double *out, int64_t N, const int32_t *kinds, const int32_t *counts,
+                       const double *const *coefs, int32_t from, int32_t nst, double *tmp)
+{
+    memcpy(out, in, (size_t)N * sizeof(double));
+    for (int32_t i = from; i < nst; ++i) {
+        if (kinds[i] == 0) {
+            fir_channel(out, tmp, N, coefs[i], counts[i]);
+        } else {
+            for (int32_t s = 0; s < counts[i]; ++s) {
+                sos_section(out, tmp, N, coefs[i] + 6 * s);
+                memcpy(out, tmp, (size_t)N * sizeof(double));
+            }
+            continue;
+        }
+        memcpy(out, tmp, (size_t)N * sizeof(double));
+    }
+}
+
+int oracle_chain_vjp(const double *x, const double *g, double *dx, double *coef_grads, int64_t C, int64_t N,
+                     const int32_t *kinds, const int32_t *counts, const double *const *coefs, int32_t nst)
+{
+    if (C < 0 || N < 0 || nst < 0 || (C * N > 0 && (!x || !g || !dx)))
+        return ORACLE_ERR_INVALID;
+    int64_t ncoef = 0;
+    for (int32_t i = 0; i < nst; ++i)
+        ncoef += kinds[i] == 0 ? counts[i] : 6 * counts[i];
+    if (ncoef > 0 && !coef_grads)
+        return ORACLE_ERR_INVALID;
+    for (int64_t k = 0; k < ncoef; ++k)
+        coef_grads[k] = 0.0;
+    if (C == 0 || N == 0)
+        return ORACLE_OK;
+    double *imp = (double *)calloc((size_t)N, sizeof(double));
+    double *hc = (double *)malloc((size_t)N * sizeof(double));
+    double *a = (double *)malloc((size_t)N * sizeof(double));
+    double *b = (double *)malloc((size_t)N * sizeof(double));
+    double *s = (double *)malloc((size_t)N * sizeof(double));
+    double *t = (double *)malloc((size_t)N * sizeof(double));
+    double *tmp = (double *)malloc((size_t)N * sizeof(double));
+    if (!imp || !hc || !a || !b || !s || !t || !tmp) {
+        free(imp); free(hc); free(a); free(b); free(s); free(t); free(tmp);
+        return ORACLE_ERR_NOMEM;
+    }
+    imp[0] = 1.0;
+    chain_tail(imp, hc, N, kinds, counts, coefs, 0, nst, tmp);
+    for (int64_t c = 0; c < C; ++c) {
+        const double *xc = x + c * N, *gc = g + c * N;
+        double *dxc = dx + c * N;
+        for (int64_t m = 0; m < N; ++m) {
+            double acc = 0.0;
+            for (int64_t n = m; n < N; ++n)
+                acc += gc[n] * hc[n - m];
+            dxc[m] = acc;
+        }
+        /* walk the stages, keeping the current stage input in a */
+        memcpy(a, xc, (size_t)N * sizeof(double));
+        int64_t off = 0;
+        for (int32_t i = 0; i < nst; ++i) {
+            if (kinds[i] == 0) {
+                const int32_t L = counts[i];
+                for (int32_t k = 0; k < L; ++k) {
+                    /* sensitivity dy/dh_k = a[n-k], then the remaining stages */
+                    for (int64_t n = 0; n < N; ++n)
+                        s[n] = n - k >= 0 ? a[n - k] : 0.0;
+                    chain_tail(s, t, N, kinds, counts, coefs, i + 1, nst, tmp);
+                    double acc = 0.0;
+                    for (int64_t n = 0; n < N; ++n)
+                        acc += gc[n] * t[n];
+                    coef_grads[off + k] += acc;
+                }
+                fir_channel(a, b, N, coefs[i], L);
+                memcpy(a, b, (size_t)N * sizeof(double));
+                off += L;
+            } else {
+                for (int32_t r = 0; r < counts[i]; ++r) {
+                    const double *row = coefs[i] + 6 * r;
+                    sos_section(a, b, N, row); /* b = section output y */
+                    const double a0 = row[3], a1 = row[4], a2 = row[5];
+                    for (int p = 0; p < 6; ++p) {
+                        for (int64_t n = 0; n < N; ++n) {
+                            double d;
+                            if (p < 3)
+                                d = n - p >= 0 ? a[n - p] : 0.0;
+                            else if (p == 3)
+                                d = -b[n];
+                            else
+                                d = n - (p - 3) >= 0 ? -b[n - (p - 3)] : 0.0;
+#if ORACLE_PLANT == 7
+                            if (p == 4) d = -d; /* planted: wrong sign of the a1 sensitivity source */
+#endif
+                            const double s1 = n >= 1 ? s[n - 1] : 0.0, s2 = n >= 2 ? s[n - 2] : 0.0;
+                            s[n] = (d - a1 * s1 - a2 * s2) / a0;
+                        }
+                        /* through the remaining sections of this stage, then later stages */
+                        for (int32_t q = r + 1; q < counts[i]; ++q) {
+                            sos_section(s, tmp, N, coefs[i] + 6 * q);
+                            memcpy(s, tmp, (size_t)N * sizeof(double));
+                        }
+                        chain_tail(s, t, N, kinds, counts, coefs, i + 1, nst, tmp);
+                        double acc = 0.0;
+                        for (int64_t n = 0; n < N; ++n)
+                            acc += gc[n] * t[n];
+                        coef_grads[off + 6 * r + p] += acc;
+                    }
+                    memcpy(a, b, (size_t)N * sizeof(double));
+                }
+                off += 6 * counts[i];
+            }
+        }
+    }
+    free(imp); free(hc); free(a); free(b); free(s); free(t); free(tmp);
+    return ORACLE_OK;
+}

@@ -242,6 +242,64 @@ def pin_linearity_time_invariance(lib, rng):
     assert _rel(yd[k:], y[:-k]) < 1e-12
 
 
+def _vjp_case(rng):
+    rows = np.stack(_rows_for_pins()[:2] + [_rows_for_pins()[6]])  # includes a0 != 1
+    h = rng.standard_normal(7)
+    stages = [("sos", rows[:2]), ("fir", h), ("sos", rows[2:])]
+    x = rng.standard_normal((2, 60))
+    g = rng.standard_normal((2, 60))
+    return stages, x, g
+
+
+def pin_vjp_finite_differences(lib, rng):
+    """Coefficient gradients of L = sum(g * chain(x)) against central finite
+    differences of the forward chain (step 1e-6, FP64)."""
+    stages, x, g = _vjp_case(rng)
+    _, grads = lib.chain_vjp(x, g, stages)
+    eps = 1e-6
+    for i, (kind, coef) in enumerate(stages):
+        c = np.asarray(coef, dtype=np.float64)
+        for idx in np.ndindex(c.shape):
+            cp, cm = c.copy(), c.copy()
+            cp[idx] += eps
+            cm[idx] -= eps
+            sp = list(stages)
+            sp[i] = (kind, cp)
+            sm = list(stages)
+            sm[i] = (kind, cm)
+            fd = (np.sum(g * lib.chain(x, sp)) - np.sum(g * lib.chain(x, sm))) / (2 * eps)
+            got = grads[i][idx]
+            assert abs(got - fd) <= 1e-6 * max(1.0, abs(fd)), f"stage {i} coef {idx}: {got} vs FD {fd}"
+
+
+def pin_vjp_input_adjoint(lib, rng):
+    """dL/dx is the adjoint of the chain: <g, chain(v)> = <dx(g), v> for any v,
+    and matches central differences in x."""
+    stages, x, g = _vjp_case(rng)
+    dx, _ = lib.chain_vjp(x, g, stages)
+    v = rng.standard_normal(x.shape)
+    lhs = np.sum(g * lib.chain(v, stages))
+    rhs = np.sum(dx * v)
+    assert abs(lhs - rhs) <= 1e-10 * max(1.0, abs(lhs))
+    eps = 1e-6
+    for (c, m) in [(0, 0), (1, 17), (0, 59)]:
+        xp, xm = x.copy(), x.copy()
+        xp[c, m] += eps
+        xm[c, m] -= eps
+        fd = (np.sum(g * lib.chain(xp, stages)) - np.sum(g * lib.chain(xm, stages))) / (2 * eps)
+        assert abs(dx[c, m] - fd) <= 1e-6 * max(1.0, abs(fd))
+
+
+def pin_vjp_fir_definition(lib, rng):
+    """Single FIR: dL/dh_k = sum_n g[n] x[n-k] (correlation, summed over channels)."""
+    h = rng.standard_normal(9)
+    x = rng.standard_normal((3, 40))
+    g = rng.standard_normal((3, 40))
+    _, (dh,) = lib.chain_vjp(x, g, [("fir", h)])
+    want = np.array([sum(np.sum(g[c, k:] * x[c, :40 - k]) for c in range(3)) for k in range(9)])
+    assert np.max(np.abs(dh - want)) <= 1e-12 * np.max(np.abs(want))
+
+
 ALL_PINS = [
     pin_fir_impulse,
     pin_fir_toeplitz,
@@ -253,4 +311,7 @@ ALL_PINS = [
     pin_cascade_closed_form,
     pin_chain_closed_form,
     pin_linearity_time_invariance,
+    pin_vjp_finite_differences,
+    pin_vjp_input_adjoint,
+    pin_vjp_fir_definition,
 ]

@@ -1,7 +1,8 @@
 """Each planted mistake in the oracle (a dropped term, a wrong sign, a swapped
 or off-by-one index, a missing a0 division, a dropped chain stage) must fail
 at least one pin.  The mistakes are compiled into separate CPU-only builds of
-``oracle/oracle.c`` (``-DORACLE_PLANT=k``); the oracle itself is unchanged."""
+``oracle/oracle.c`` (``-DORACLE_PLANT=k``); the oracle itself is unchanged.
+Plant 7 sits in the gradient (VJP) code and must be caught by its pins."""
 import numpy as np
 import pytest
 
@@ -15,6 +16,7 @@ PLANTS = {
     4: "SOS a0 division missing",
     5: "chain drops its last stage",
     6: "SOS a1/a2 swapped",
+    7: "VJP: a1 sensitivity sign flipped",
 }
 
 
