@@ -76,6 +76,11 @@ typedef struct {
 #define TFX_PLAN_FIR_BF16_PLAIN 4u /* tensor-core FIR, BF16 operands, no hi/lo correction (reported-only accuracy mode) */
 #define TFX_PLAN_FIR_BF16_SPLIT 8u /* tensor-core FIR with BF16 hi/lo operands instead of the default scaled FP16 hi/lo */
 #define TFX_PLAN_SCAN_WARP_TILES 16u /* cascade-only units: one warp per 1024-sample tile, warp-parallel look-back */
+/* The plan supports tfx_plan_forward_train / tfx_plan_backward (gradients of
+ * the chain for the filters used as network layers, Sec. 3).  Every FIR runs
+ * as a unit of its own and cascades as warp-tile scans of at most 8 sections
+ * (longer cascades are split); tfx_plan_execute still works on such a plan. */
+#define TFX_PLAN_TRAINABLE 32u
 /* Test hook for failure detection: the first tile of channel 0 never publishes
  * its carries, so its successor's bounded wait runs out; the execution
  * completes (with wrong output) and tfx_plan_get_error() returns
@@ -136,6 +141,74 @@ int tfx_plan_get_error(tfx_plan *p);
 
 /* Free the plan (synchronises the device).  NULL is a no-op. */
 void tfx_plan_destroy(tfx_plan *p);
+
+/*
+ * Gradients (TFX_PLAN_TRAINABLE plans).  Sec. 3 builds every filter as an
+ * nn.Module so that chains sit inside neural networks; these calls give the
+ * reverse-mode derivatives such a network needs.  For L = sum(g * y), y the
+ * chain's output and g = dL/dy:
+ *   dx    = dL/dx, [C x N] with the plan's row stride
+ *   dcoef = dL/d(every coefficient), FP64, stages in chain order: an FIR stage
+ *           contributes its n taps, an SOS stage its n rows of 6 raw values
+ *           (b0 b1 b2 a0 a1 a2, before the a0 normalisation); summed over
+ *           channels (the coefficients are shared by all channels).
+ *
+ * tfx_plan_saved_size     : bytes of device memory a training forward keeps
+ *                           for the backward: the input of every unit after
+ *                           the first (an intermediate of the chain), and
+ *                           each cascade's state at every 32-sample chunk
+ *                           start (8 bytes per section per chunk); 0 for a
+ *                           plan without TFX_PLAN_TRAINABLE.
+ * tfx_plan_backward_workspace_size : bytes of backward workspace (0 likewise).
+ * tfx_plan_coef_count     : doubles in dcoef (-1 for a NULL plan).
+ */
+size_t tfx_plan_saved_size(const tfx_plan *p);
+size_t tfx_plan_backward_workspace_size(const tfx_plan *p);
+int64_t tfx_plan_coef_count(const tfx_plan *p);
+
+/*
+ * tfx_plan_forward_train -- y = chain(x) as tfx_plan_execute, and fill
+ * `saved` (device, >= tfx_plan_saved_size bytes, 256-byte aligned, owned by
+ * the caller) with what tfx_plan_backward needs.  x == y is rejected (the
+ * backward reads x again); ws as for tfx_plan_execute.  Asynchronous, no
+ * allocation, capturable.
+ * Errors: TFX_ERR_INVALID (not trainable, x == y, overlapping buffers),
+ * TFX_ERR_WORKSPACE, TFX_ERR_CUDA.
+ */
+int tfx_plan_forward_train(tfx_plan *p, const float *x, float *y, void *saved,
+                           size_t saved_bytes, void *ws, size_t ws_bytes,
+                           tfx_stream s);
+
+/*
+ * tfx_plan_backward -- given the x and `saved` of a training forward (not
+ * modified since) and g = dL/dy (device, [C x N], the plan's row stride),
+ * write dx (may be NULL: not computed; may equal g; must not overlap x) and
+ * dcoef (device FP64, tfx_plan_coef_count values, fully overwritten; may be
+ * NULL: not computed).  ws: device, >= tfx_plan_backward_workspace_size
+ * bytes, 256-byte aligned.  The SOS cascades run as reverse-time adjoint
+ * scans that recompute their section outputs from the saved chunk-start
+ * states; FIRs as the FIR over the time-reversed gradient plus a tap
+ * correlation.  Asynchronous, no allocation, capturable; a device-side
+ * timeout is reported by tfx_plan_get_error.
+ * Errors: TFX_ERR_INVALID, TFX_ERR_WORKSPACE, TFX_ERR_CUDA.
+ */
+int tfx_plan_backward(tfx_plan *p, const float *x, const float *g, float *dx,
+                      double *dcoef, const void *saved, size_t saved_bytes,
+                      void *ws, size_t ws_bytes, tfx_stream s);
+
+/* Kernels one tfx_plan_backward launches with (with_dx, with_dcoef) set as
+ * (dx != NULL, dcoef != NULL); memsets excluded; -1 if not trainable. */
+int tfx_plan_backward_launch_count(const tfx_plan *p, int with_dx, int with_dcoef);
+
+/*
+ * tfx_mse -- mean squared error between y and target ([C x N], row stride
+ * ld, device): *loss = mean((y - target)^2) (device FP64 scalar, written
+ * after a reset on s), and g = dL/dy = 2 (y - target) / (C N) unless g is
+ * NULL.  The loss the differentiable-chain workload trains with.
+ * Errors: TFX_ERR_INVALID, TFX_ERR_CUDA.
+ */
+int tfx_mse(const float *y, const float *target, float *g, int64_t C,
+            int64_t N, int64_t ld, double *loss, tfx_stream s);
 
 /*
  * One-shot calls.  They build (or reuse from an internal cache keyed by the

@@ -16,7 +16,8 @@ The arithmetic lives in ``oracle.c`` (plain C, double precision):
   * ``chain_vjp`` -- gradients of sum(g * chain(x)) w.r.t. x and every
                  coefficient, from the chain's impulse response and from
                  forward-mode sensitivities of the difference equations
-                 (the filters as layers inside a network, Sec. 3).
+                 (the filters as layers inside a network, Sec. 3);
+                 ``chain_vjp_dx_at`` gives dL/dx at chosen samples only.
 
 Parity is pinned by closed forms and brute force in ``tests/test_oracle.py``.
 """
@@ -117,8 +118,9 @@ class OracleLib:
             raise ValueError(f"oracle_chain failed ({rc})")
         return y[0] if sq else y
 
-    def chain_vjp(self, x, g, stages):
-        """(dL/dx, [dL/dcoef per stage]) for upstream gradient g = dL/dy."""
+    def chain_vjp(self, x, g, stages, want_dx: bool = True):
+        """(dL/dx, [dL/dcoef per stage]) for upstream gradient g = dL/dy.
+        With want_dx=False the O(N^2) input gradient is skipped (dL/dx None)."""
         x2, sq = self._as_signal(x)
         g2, _ = self._as_signal(g)
         if g2.shape != x2.shape:
@@ -140,8 +142,9 @@ class OracleLib:
         ks = (ctypes.c_int32 * max(n, 1))(*kinds)
         cs = (ctypes.c_int32 * max(n, 1))(*counts)
         ptrs = (ctypes.POINTER(ctypes.c_double) * max(n, 1))(*[self._dp(c) for c in keep])
-        dx = np.empty_like(x2)
-        rc = self.lib.oracle_chain_vjp(self._dp(x2), self._dp(g2), self._dp(dx), self._dp(dcoef),
+        dx = np.empty_like(x2) if want_dx else None
+        rc = self.lib.oracle_chain_vjp(self._dp(x2), self._dp(g2), self._dp(dx) if want_dx else None,
+                                       self._dp(dcoef),
                                        x2.shape[0], x2.shape[1], ks, cs, ptrs, n)
         if rc != 0:
             raise ValueError(f"oracle_chain_vjp failed ({rc})")
@@ -149,7 +152,22 @@ class OracleLib:
         for c in keep:
             grads.append(dcoef[off:off + c.size].reshape(c.shape))
             off += c.size
+        if dx is None:
+            return None, grads
         return (dx[0] if sq else dx), grads
+
+    def chain_vjp_dx_at(self, g, stages, idx):
+        """dL/dx[m] of one channel at the sample indices idx, for long signals
+        where the full O(N^2) input gradient is too slow: the chain is linear
+        and time-invariant, so dL/dx[m] = sum_{n >= m} g[n] h[n - m] with h
+        the chain's impulse response (computed by ``chain``)."""
+        g = np.asarray(g, dtype=np.float64).ravel()
+        N = g.size
+        imp = np.zeros(N)
+        if N:
+            imp[0] = 1.0
+        h = self.chain(imp, stages)
+        return np.array([float(np.dot(g[m:], h[:N - m])) for m in idx])
 
     def num_threads(self) -> int:
         return int(self.lib.oracle_num_threads())

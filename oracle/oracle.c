@@ -274,7 +274,7 @@ static void chain_tail(const double *in, double *out, int64_t N, const int32_t *
 int oracle_chain_vjp(const double *x, const double *g, double *dx, double *coef_grads, int64_t C, int64_t N,
                      const int32_t *kinds, const int32_t *counts, const double *const *coefs, int32_t nst)
 {
-    if (C < 0 || N < 0 || nst < 0 || (C * N > 0 && (!x || !g || !dx)))
+    if (C < 0 || N < 0 || nst < 0 || (C * N > 0 && (!x || !g)))
         return ORACLE_ERR_INVALID;
     int64_t ncoef = 0;
     for (int32_t i = 0; i < nst; ++i)
@@ -285,84 +285,116 @@ int oracle_chain_vjp(const double *x, const double *g, double *dx, double *coef_
         coef_grads[k] = 0.0;
     if (C == 0 || N == 0)
         return ORACLE_OK;
-    double *imp = (double *)calloc((size_t)N, sizeof(double));
-    double *hc = (double *)malloc((size_t)N * sizeof(double));
-    double *a = (double *)malloc((size_t)N * sizeof(double));
-    double *b = (double *)malloc((size_t)N * sizeof(double));
-    double *s = (double *)malloc((size_t)N * sizeof(double));
-    double *t = (double *)malloc((size_t)N * sizeof(double));
-    double *tmp = (double *)malloc((size_t)N * sizeof(double));
-    if (!imp || !hc || !a || !b || !s || !t || !tmp) {
-        free(imp); free(hc); free(a); free(b); free(s); free(t); free(tmp);
+    double *hc = NULL;
+    if (dx) { /* the chain's impulse response, for dx */
+        double *imp = (double *)calloc((size_t)N, sizeof(double));
+        double *tmp = (double *)malloc((size_t)N * sizeof(double));
+        hc = (double *)malloc((size_t)N * sizeof(double));
+        if (!imp || !tmp || !hc) {
+            free(imp); free(tmp); free(hc);
+            return ORACLE_ERR_NOMEM;
+        }
+        imp[0] = 1.0;
+        chain_tail(imp, hc, N, kinds, counts, coefs, 0, nst, tmp);
+        free(imp); free(tmp);
+    }
+    /* per-channel gradient rows, summed in channel order afterwards */
+    double *rows = (double *)calloc((size_t)(C * (ncoef > 0 ? ncoef : 1)), sizeof(double));
+    if (!rows) {
+        free(hc);
         return ORACLE_ERR_NOMEM;
     }
-    imp[0] = 1.0;
-    chain_tail(imp, hc, N, kinds, counts, coefs, 0, nst, tmp);
-    for (int64_t c = 0; c < C; ++c) {
-        const double *xc = x + c * N, *gc = g + c * N;
-        double *dxc = dx + c * N;
-        for (int64_t m = 0; m < N; ++m) {
-            double acc = 0.0;
-            for (int64_t n = m; n < N; ++n)
-                acc += gc[n] * hc[n - m];
-            dxc[m] = acc;
+    int err = 0;
+#pragma omp parallel
+    {
+        double *a = (double *)malloc((size_t)N * sizeof(double));
+        double *b = (double *)malloc((size_t)N * sizeof(double));
+        double *s = (double *)malloc((size_t)N * sizeof(double));
+        double *t = (double *)malloc((size_t)N * sizeof(double));
+        double *tmp = (double *)malloc((size_t)N * sizeof(double));
+        const int ok = a && b && s && t && tmp;
+        if (!ok) {
+#pragma omp atomic write
+            err = 1;
         }
-        /* walk the stages, keeping the current stage input in a */
-        memcpy(a, xc, (size_t)N * sizeof(double));
-        int64_t off = 0;
-        for (int32_t i = 0; i < nst; ++i) {
-            if (kinds[i] == 0) {
-                const int32_t L = counts[i];
-                for (int32_t k = 0; k < L; ++k) {
-                    /* sensitivity dy/dh_k = a[n-k], then the remaining stages */
-                    for (int64_t n = 0; n < N; ++n)
-                        s[n] = n - k >= 0 ? a[n - k] : 0.0;
-                    chain_tail(s, t, N, kinds, counts, coefs, i + 1, nst, tmp);
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t c = 0; c < C; ++c) {
+            if (!ok)
+                continue;
+            const double *xc = x + c * N, *gc = g + c * N;
+            double *gr = rows + c * ncoef;
+            if (dx) {
+                double *dxc = dx + c * N;
+                for (int64_t m = 0; m < N; ++m) {
                     double acc = 0.0;
-                    for (int64_t n = 0; n < N; ++n)
-                        acc += gc[n] * t[n];
-                    coef_grads[off + k] += acc;
+                    for (int64_t n = m; n < N; ++n)
+                        acc += gc[n] * hc[n - m];
+                    dxc[m] = acc;
                 }
-                fir_channel(a, b, N, coefs[i], L);
-                memcpy(a, b, (size_t)N * sizeof(double));
-                off += L;
-            } else {
-                for (int32_t r = 0; r < counts[i]; ++r) {
-                    const double *row = coefs[i] + 6 * r;
-                    sos_section(a, b, N, row); /* b = section output y */
-                    const double a0 = row[3], a1 = row[4], a2 = row[5];
-                    for (int p = 0; p < 6; ++p) {
-                        for (int64_t n = 0; n < N; ++n) {
-                            double d;
-                            if (p < 3)
-                                d = n - p >= 0 ? a[n - p] : 0.0;
-                            else if (p == 3)
-                                d = -b[n];
-                            else
-                                d = n - (p - 3) >= 0 ? -b[n - (p - 3)] : 0.0;
-#if ORACLE_PLANT == 7
-                            if (p == 4) d = -d; /* planted: wrong sign of the a1 sensitivity source */
-#endif
-                            const double s1 = n >= 1 ? s[n - 1] : 0.0, s2 = n >= 2 ? s[n - 2] : 0.0;
-                            s[n] = (d - a1 * s1 - a2 * s2) / a0;
-                        }
-                        /* through the remaining sections of this stage, then later stages */
-                        for (int32_t q = r + 1; q < counts[i]; ++q) {
-                            sos_section(s, tmp, N, coefs[i] + 6 * q);
-                            memcpy(s, tmp, (size_t)N * sizeof(double));
-                        }
+            }
+            /* walk the stages, keeping the current stage input in a */
+            memcpy(a, xc, (size_t)N * sizeof(double));
+            int64_t off = 0;
+            for (int32_t i = 0; i < nst; ++i) {
+                if (kinds[i] == 0) {
+                    const int32_t L = counts[i];
+                    for (int32_t k = 0; k < L; ++k) {
+                        /* sensitivity dy/dh_k = a[n-k], then the remaining stages */
+                        for (int64_t n = 0; n < N; ++n)
+                            s[n] = n - k >= 0 ? a[n - k] : 0.0;
                         chain_tail(s, t, N, kinds, counts, coefs, i + 1, nst, tmp);
                         double acc = 0.0;
                         for (int64_t n = 0; n < N; ++n)
                             acc += gc[n] * t[n];
-                        coef_grads[off + 6 * r + p] += acc;
+                        gr[off + k] += acc;
                     }
+                    fir_channel(a, b, N, coefs[i], L);
                     memcpy(a, b, (size_t)N * sizeof(double));
+                    off += L;
+                } else {
+                    for (int32_t r = 0; r < counts[i]; ++r) {
+                        const double *row = coefs[i] + 6 * r;
+                        sos_section(a, b, N, row); /* b = section output y */
+                        const double a0 = row[3], a1 = row[4], a2 = row[5];
+                        for (int p = 0; p < 6; ++p) {
+                            for (int64_t n = 0; n < N; ++n) {
+                                double d;
+                                if (p < 3)
+                                    d = n - p >= 0 ? a[n - p] : 0.0;
+                                else if (p == 3)
+                                    d = -b[n];
+                                else
+                                    d = n - (p - 3) >= 0 ? -b[n - (p - 3)] : 0.0;
+#if ORACLE_PLANT == 7
+                                if (p == 4) d = -d; /* planted: wrong sign of the a1 sensitivity source */
+#endif
+                                const double s1 = n >= 1 ? s[n - 1] : 0.0, s2 = n >= 2 ? s[n - 2] : 0.0;
+                                s[n] = (d - a1 * s1 - a2 * s2) / a0;
+                            }
+                            /* through the remaining sections of this stage, then later stages */
+                            for (int32_t q = r + 1; q < counts[i]; ++q) {
+                                sos_section(s, tmp, N, coefs[i] + 6 * q);
+                                memcpy(s, tmp, (size_t)N * sizeof(double));
+                            }
+                            chain_tail(s, t, N, kinds, counts, coefs, i + 1, nst, tmp);
+                            double acc = 0.0;
+                            for (int64_t n = 0; n < N; ++n)
+                                acc += gc[n] * t[n];
+                            gr[off + 6 * r + p] += acc;
+                        }
+                        memcpy(a, b, (size_t)N * sizeof(double));
+                    }
+                    off += 6 * counts[i];
                 }
-                off += 6 * counts[i];
             }
         }
+        free(a); free(b); free(s); free(t); free(tmp);
     }
-    free(imp); free(hc); free(a); free(b); free(s); free(t); free(tmp);
-    return ORACLE_OK;
+    if (!err)
+        for (int64_t c = 0; c < C; ++c)
+            for (int64_t k = 0; k < ncoef; ++k)
+                coef_grads[k] += rows[c * ncoef + k];
+    free(rows);
+    free(hc);
+    return err ? ORACLE_ERR_NOMEM : ORACLE_OK;
 }

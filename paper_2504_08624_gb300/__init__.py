@@ -9,7 +9,7 @@ __version__ = "0.1.0"
 
 
 def __getattr__(name):
-    if name in ("chain", "fir", "sos", "Plan", "TfxError"):
+    if name in ("chain", "fir", "sos", "Plan", "TfxError", "chain_ad", "ChainFunction", "FilterChain", "mse"):
         from . import api
         return getattr(api, name)
     raise AttributeError(name)

@@ -23,6 +23,7 @@ TFX_PLAN_UNFUSED = 2
 TFX_PLAN_FIR_BF16_PLAIN = 4
 TFX_PLAN_FIR_BF16_SPLIT = 8
 TFX_PLAN_SCAN_WARP_TILES = 16
+TFX_PLAN_TRAINABLE = 32
 TFX_PLAN_TEST_DROP_PUBLISH = 256
 
 STATUS = {
@@ -36,6 +37,8 @@ EXPORTS = [
     "tfx_plan_get_error", "tfx_plan_destroy", "tfx_fir", "tfx_sos", "tfx_chain",
     "tfx_chain_workspace_size", "tfx_cache_clear", "tfx_sos_noalloc", "tfx_strerror", "tfx_version",
     "tfx_chain_host", "tfx_host_cache_clear",
+    "tfx_plan_saved_size", "tfx_plan_backward_workspace_size", "tfx_plan_coef_count", "tfx_plan_forward_train",
+    "tfx_plan_backward", "tfx_plan_backward_launch_count", "tfx_mse",
 ]
 
 
@@ -95,6 +98,20 @@ def lib():
     L.tfx_sos_noalloc.restype = ctypes.c_int
     L.tfx_cache_clear.argtypes = []
     L.tfx_cache_clear.restype = None
+    L.tfx_plan_saved_size.argtypes = [vp]
+    L.tfx_plan_saved_size.restype = sz
+    L.tfx_plan_backward_workspace_size.argtypes = [vp]
+    L.tfx_plan_backward_workspace_size.restype = sz
+    L.tfx_plan_coef_count.argtypes = [vp]
+    L.tfx_plan_coef_count.restype = i64
+    L.tfx_plan_forward_train.argtypes = [vp, fp, fp, vp, sz, vp, sz, vp]
+    L.tfx_plan_forward_train.restype = ctypes.c_int
+    L.tfx_plan_backward.argtypes = [vp, fp, fp, fp, fp, vp, sz, vp, sz, vp]
+    L.tfx_plan_backward.restype = ctypes.c_int
+    L.tfx_plan_backward_launch_count.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.tfx_plan_backward_launch_count.restype = ctypes.c_int
+    L.tfx_mse.argtypes = [fp, fp, fp, i64, i64, i64, fp, vp]
+    L.tfx_mse.restype = ctypes.c_int
     L.tfx_strerror.argtypes = [ctypes.c_int]
     L.tfx_strerror.restype = ctypes.c_char_p
     L.tfx_version.restype = ctypes.c_int

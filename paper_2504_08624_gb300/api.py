@@ -8,6 +8,11 @@ device memory and the current CUDA stream; the filtering itself runs in the
 CUDA library.  CPU tensors are accepted: ``tfx_chain_host`` copies channel
 groups to the GPU, filters them and copies them back with the copies and the
 filtering overlapped (pinned tensors let the copies run asynchronously).
+
+Gradients: ``chain_ad`` / ``FilterChain`` make the chain a differentiable
+layer (Sec. 3 builds the filters as ``nn.Module`` classes for networks): the
+forward keeps block-boundary states, the backward runs the library's
+reverse-time adjoint kernels and returns dL/dx and dL/d(coefficients).
 """
 from __future__ import annotations
 
@@ -150,6 +155,57 @@ class Plan:
         N.check(rc, "tfx_plan_execute_plain" if plain else "tfx_plan_execute")
         return y
 
+    # -- gradients (plans created with TFX_PLAN_TRAINABLE) -----------------
+
+    @property
+    def saved_size(self) -> int:
+        return int(N.lib().tfx_plan_saved_size(self._h))
+
+    @property
+    def backward_workspace_size(self) -> int:
+        return int(N.lib().tfx_plan_backward_workspace_size(self._h))
+
+    @property
+    def coef_count(self) -> int:
+        return int(N.lib().tfx_plan_coef_count(self._h))
+
+    def backward_launches(self, with_dx: bool = True, with_dcoef: bool = True) -> int:
+        return int(N.lib().tfx_plan_backward_launch_count(self._h, int(with_dx), int(with_dcoef)))
+
+    def new_saved(self) -> torch.Tensor:
+        return torch.empty(max(1, self.saved_size), dtype=torch.uint8, device=self.device)
+
+    def backward_workspace(self) -> torch.Tensor:
+        if getattr(self, "_bws", None) is None:
+            self._bws = torch.empty(max(1, self.backward_workspace_size), dtype=torch.uint8, device=self.device)
+        return self._bws
+
+    def forward_train(self, x: torch.Tensor, y: torch.Tensor, saved: torch.Tensor,
+                      ws: torch.Tensor | None = None) -> torch.Tensor:
+        x2, y2, w = self._args(x, y, ws)
+        with torch.cuda.device(self.device):
+            rc = N.lib().tfx_plan_forward_train(self._h, ctypes.c_void_p(x2.data_ptr()), ctypes.c_void_p(y2.data_ptr()),
+                                                ctypes.c_void_p(saved.data_ptr()), saved.numel(),
+                                                ctypes.c_void_p(w.data_ptr()), w.numel(), _stream_handle(self.device))
+        N.check(rc, "tfx_plan_forward_train")
+        return y
+
+    def backward(self, x: torch.Tensor, g: torch.Tensor, dx: torch.Tensor | None, dcoef: torch.Tensor | None,
+                 saved: torch.Tensor, ws: torch.Tensor | None = None) -> None:
+        x2, g2, _ = self._args(x, g, None)
+        if dx is not None:
+            self._args(dx, dx, None)
+        if dcoef is not None and (dcoef.dtype != torch.float64 or not dcoef.is_cuda
+                                  or dcoef.numel() < self.coef_count):
+            raise ValueError("dcoef must be a CUDA float64 tensor of coef_count values")
+        w = self.backward_workspace() if ws is None else ws
+        ptr = (lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None)
+        with torch.cuda.device(self.device):
+            rc = N.lib().tfx_plan_backward(self._h, ptr(x2), ptr(g2), ptr(dx), ptr(dcoef),
+                                           ctypes.c_void_p(saved.data_ptr()), saved.numel(),
+                                           ctypes.c_void_p(w.data_ptr()), w.numel(), _stream_handle(self.device))
+        N.check(rc, "tfx_plan_backward")
+
     def get_error(self) -> int:
         with torch.cuda.device(self.device):
             return int(N.lib().tfx_plan_get_error(self._h))
@@ -164,3 +220,118 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def mse(y: torch.Tensor, target: torch.Tensor, g: torch.Tensor | None = None) -> torch.Tensor:
+    """Mean squared error on the GPU: returns the loss (0-d float64 tensor) and,
+    if ``g`` is given, writes dL/dy = 2 (y - target) / numel into it."""
+    y2, t2 = _check_signal(y), _check_signal(target)
+    if y2.shape != t2.shape or y2.stride() != t2.stride() or not y2.is_cuda:
+        raise ValueError("y and target must be CUDA tensors of one shape and layout")
+    if g is not None:
+        g2 = _check_signal(g)
+        if g2.shape != y2.shape or g2.stride() != y2.stride():
+            raise ValueError("g must match y")
+    loss = torch.empty((), dtype=torch.float64, device=y2.device)
+    C, Ns = y2.shape
+    with torch.cuda.device(y2.device):
+        rc = N.lib().tfx_mse(ctypes.c_void_p(y2.data_ptr()), ctypes.c_void_p(t2.data_ptr()),
+                             ctypes.c_void_p(g.data_ptr()) if g is not None else None, C, Ns, _row_stride(y2),
+                             ctypes.c_void_p(loss.data_ptr()), _stream_handle(y2.device))
+    N.check(rc, "tfx_mse")
+    return loss
+
+
+# ---------------------------------------------------------------------------
+# autograd
+
+_TRAIN_PLANS: dict = {}
+_TRAIN_PLANS_MAX = 8
+
+
+def _train_plan(C: int, Ns: int, stages, device) -> Plan:
+    key = (C, Ns, str(device), tuple((k, c.shape, c.tobytes()) for k, c in stages))
+    p = _TRAIN_PLANS.pop(key, None)
+    if p is None:
+        p = Plan(C, Ns, stages, flags=N.TFX_PLAN_TRAINABLE, device=device.index)
+        if len(_TRAIN_PLANS) >= _TRAIN_PLANS_MAX:
+            # dropped, not closed: a pending backward may still hold it
+            _TRAIN_PLANS.pop(next(iter(_TRAIN_PLANS)))
+    _TRAIN_PLANS[key] = p  # most recent last
+    return p
+
+
+class ChainFunction(torch.autograd.Function):
+    """y = chain(x) with gradients for x and every coefficient tensor.
+
+    The coefficient values are read on the host to build (or reuse) a
+    trainable plan, so CUDA coefficient tensors cost one device-to-host copy
+    per call; x and the gradients stay on the GPU."""
+
+    @staticmethod
+    def forward(ctx, x, kinds, *coefs):
+        x2 = _check_signal(x).contiguous()
+        if not x2.is_cuda:
+            raise ValueError("chain_ad needs a CUDA signal")
+        stages = [(k, c.detach().to("cpu", torch.float64).numpy()) for k, c in zip(kinds, coefs)]
+        C, Ns = x2.shape
+        plan = _train_plan(C, Ns, stages, x2.device)
+        saved = plan.new_saved()
+        y = torch.empty_like(x2)
+        plan.forward_train(x2, y, saved)
+        ctx.plan = plan
+        ctx.meta = [(c.shape, c.dtype, c.device) for c in coefs]
+        ctx.kinds = kinds
+        ctx.squeeze = x.dim() == 1
+        ctx.save_for_backward(x2, saved)
+        return y[0] if ctx.squeeze else y
+
+    @staticmethod
+    def backward(ctx, gy):
+        x2, saved = ctx.saved_tensors
+        plan = ctx.plan
+        g2 = _check_signal(gy.to(torch.float32)).contiguous()
+        need_dx = ctx.needs_input_grad[0]
+        need_dc = any(ctx.needs_input_grad[2:])
+        if not (need_dx or need_dc):
+            return (None, None) + (None,) * len(ctx.meta)
+        dx = torch.empty_like(x2) if need_dx else None
+        dcoef = torch.empty(max(1, plan.coef_count), dtype=torch.float64, device=x2.device) if need_dc else None
+        plan.backward(x2, g2, dx, dcoef, saved)
+        grads, off = [], 0
+        for (shape, dtype, device), need in zip(ctx.meta, ctx.needs_input_grad[2:]):
+            n = 1
+            for d in shape:
+                n *= d
+            if need and dcoef is not None:
+                grads.append(dcoef[off:off + n].reshape(shape).to(device=device, dtype=dtype))
+            else:
+                grads.append(None)
+            off += n
+        if dx is not None and ctx.squeeze:
+            dx = dx[0]
+        return (dx, None, *grads)
+
+
+def chain_ad(x: torch.Tensor, stages) -> torch.Tensor:
+    """Differentiable chain: ``stages`` is a list of ("sos", rows [S x 6]) /
+    ("fir", taps [L]) with torch tensors (any that require grad receive
+    dL/d(coefficient); SOS rows as raw b0 b1 b2 a0 a1 a2)."""
+    kinds = tuple(k for k, _ in stages)
+    coefs = [c if torch.is_tensor(c) else torch.as_tensor(c, dtype=torch.float64) for _, c in stages]
+    return ChainFunction.apply(x, kinds, *coefs)
+
+
+class FilterChain(torch.nn.Module):
+    """A chain of filters as an ``nn.Module`` with learnable coefficients
+    (Sec. 3: the filters are modules that compose inside networks)."""
+
+    def __init__(self, stages, learnable: bool = True):
+        super().__init__()
+        self.kinds = tuple(k for k, _ in stages)
+        self.coefs = torch.nn.ParameterList(
+            [torch.nn.Parameter(torch.as_tensor(c, dtype=torch.float64).clone(), requires_grad=learnable)
+             for _, c in stages])
+
+    def forward(self, x: torch.Tensor) -> torch.Tensor:
+        return ChainFunction.apply(x, self.kinds, *self.coefs)

@@ -11,8 +11,11 @@
 // A^1..A^16 of the chunk transfer matrix A leaves the tile aggregate in lane
 // 31, and the warp resolves the tile's incoming state by a warp-parallel
 // decoupled look-back over the preceding tiles of the channel (one probe per
-// lane per round trip; tile transfer A^32, window transfer A^1024).  Tiles are handed out by an atomic ticket in time-major
-// order, so every predecessor is already running.
+// lane per round trip; tile transfer A^32, window transfer A^1024).  Tiles are
+// handed out by an atomic ticket in time-major order, so every predecessor is
+// already running.  In a training forward each lane also stores the true state
+// of every section at its chunk start: the checkpoints from which the adjoint
+// kernel recomputes the section outputs chunk by chunk.
 #include "tfx_common.cuh"
 
 namespace tfx {
@@ -191,6 +194,11 @@ __global__ void __launch_bounds__(128, 6) k_sos_warp(UnitArgs a) {
         const float2 t2 = mv2(Pl, win);
         st.x += t2.x;
         st.y += t2.y;
+        // training forward: keep the chunk-start state (block-boundary checkpoint)
+        if (a.ckpt) {
+            const int64_t chunk = tt * 32 + lane;
+            if (chunk < a.nch) a.ckpt[(c * S + s) * a.nch + chunk] = st;
+        }
         pa1 = a1;
         pa2 = a2;
     }

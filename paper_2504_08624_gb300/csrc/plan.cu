@@ -42,6 +42,16 @@ struct HostUnit {
     size_t tc_smem_ws = 0;
     // cascade without an FIR: warp-per-tile scan (tiles of 32 * T_CHUNK samples)
     bool warp = false;
+    // trainable plans: where each section's raw row (6 values) and the FIR's
+    // taps sit in the flat coefficient-gradient array, the raw rows for the
+    // a0 chain rule, and the unit's saved activations
+    std::vector<int64_t> dst;   // [S]
+    std::vector<double> raw;    // [S][6]
+    int64_t fir_dst = 0;
+    size_t off_raw = 0, off_dst = 0;  // constant blob
+    size_t off_act = 0;               // saved: this unit's input (units after the first)
+    size_t off_ckpt = 0;              // saved: chunk-start states [C][S][nch] (cascade units)
+    int Lp = 0;                       // FIR taps rounded up to 16
 };
 
 constexpr int WARP_TILE = 32 * T_CHUNK;
@@ -71,6 +81,13 @@ struct tfx_plan {
     size_t buf_bytes = 0;      // one intermediate [C x N] buffer
     size_t ws_fused = 0, ws_plain = 0;
     int sm_count = 1;  // persistent grid size
+    // trainable plans
+    bool train = false;
+    int64_t ncoef = 0;        // doubles in the coefficient-gradient array
+    int64_t nch = 0;          // 32-sample chunks per channel
+    size_t saved_bytes = 0;   // forward activations + checkpoints kept for the backward
+    size_t bws_bytes = 0;     // backward workspace
+    size_t b_scan = 0, b_part = 0, b_tmp = 0, b_gbuf = 0;  // backward workspace offsets
 };
 
 namespace {
@@ -100,12 +117,15 @@ int normalise_row(const double* r, double* out) {
 // Device coefficients of one a0-normalised section (b0 b1 b2 a1 a2): the
 // recursion w1' = c1 u - a1 w1 + w2, w2' = c2 u - a2 w1, y = b0 u + w1 uses
 // c1 = b1 - a1 b0 and c2 = b2 - a2 b0, formed here in FP64 before rounding.
+// Slot 5 holds d = a1 b2 - a2 b1, which maps the adjoint all-pole state to the
+// state of the section run backwards in time (used by the backward kernel).
 void sec_device_coefs(const double* r, float* out) {
     out[0] = (float)r[0];
     out[1] = (float)(r[1] - r[3] * r[0]);
     out[2] = (float)(r[2] - r[4] * r[0]);
     out[3] = (float)r[3];
     out[4] = (float)r[4];
+    out[5] = (float)(r[3] * r[2] - r[4] * r[1]);
 }
 
 // Round-to-nearest-even FP32 -> BF16 bits, and back.
@@ -237,26 +257,39 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         if (cur.S > 0 || cur.L > 0) p->units.push_back(cur);
         cur = HostUnit();
     };
-    const bool unfused = (p->flags & TFX_PLAN_UNFUSED) != 0;
+    // A trainable plan keeps every FIR in a unit of its own and at most
+    // BWD_SMAX sections per cascade, and records where each coefficient's
+    // gradient goes (stages in order; FIR: n taps, SOS: 6 values per row).
+    p->train = (p->flags & TFX_PLAN_TRAINABLE) != 0;
+    const bool unfused = (p->flags & TFX_PLAN_UNFUSED) != 0 || p->train;
+    int64_t coff = 0;
     for (int32_t i = 0; i < nst; ++i) {
         const tfx_stage& s = st[i];
         if (s.kind == TFX_STAGE_SOS) {
             if (cur.L > 0) flush();
             for (int r = 0; r < s.n; ++r) {
+                if (p->train && cur.S == BWD_SMAX) flush();
                 double row[5];
                 normalise_row(s.coef + 6 * r, row);
                 cur.sec.insert(cur.sec.end(), row, row + 5);
                 cur.S++;
+                cur.dst.push_back(coff + 6 * r);
+                cur.raw.insert(cur.raw.end(), s.coef + 6 * r, s.coef + 6 * r + 6);
             }
+            coff += 6 * (int64_t)s.n;
         } else {
             if (unfused && cur.S > 0) flush();
             if (cur.L > 0) flush();
             cur.L = s.n;
             cur.taps.assign(s.coef, s.coef + s.n);
+            cur.fir_dst = coff;
+            cur.Lp = (s.n + 15) / 16 * 16;
+            coff += s.n;
             flush();
         }
     }
     flush();
+    p->ncoef = coff;
 
     // long FIRs go to the tensor cores; an SOS cascade in front of one runs as
     // its own unit (the cascade output crosses HBM once more)
@@ -280,7 +313,8 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         p->units.swap(out);
     }
 
-    for (HostUnit& u : p->units) u.warp = (u.S > 0 && u.L == 0) && (p->flags & TFX_PLAN_SCAN_WARP_TILES);
+    for (HostUnit& u : p->units)
+        u.warp = (u.S > 0 && u.L == 0) && ((p->flags & TFX_PLAN_SCAN_WARP_TILES) || p->train);
 
     // constant blob layout
     size_t off = 0;
@@ -297,6 +331,12 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
             off = align_up(off + (size_t)u.a_chunks * 128);
             u.off_alo = off;
             off = align_up(off + (size_t)u.a_chunks * 128);
+        }
+        if (p->train && u.S > 0) {
+            u.off_raw = off;
+            off = align_up(off + (size_t)u.S * 6 * sizeof(double));
+            u.off_dst = off;
+            off = align_up(off + (size_t)u.S * sizeof(int64_t));
         }
     }
     for (int32_t i = 0; i < nst; ++i) {
@@ -326,6 +366,10 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         }
         float* taps = reinterpret_cast<float*>(host.data() + u.off_taps);
         for (int k = 0; k < u.L; ++k) taps[k] = (float)u.taps[k];
+        if (p->train && u.S > 0) {
+            std::memcpy(host.data() + u.off_raw, u.raw.data(), (size_t)u.S * 6 * sizeof(double));
+            std::memcpy(host.data() + u.off_dst, u.dst.data(), (size_t)u.S * sizeof(int64_t));
+        }
         if (u.tc) {
             // g[v] = h[W + 127 - v]; chunk j, copy b holds g[8j + b .. 8j + b + 7].
             // FP16 mode: taps scaled by 2^e so that max|h| lands in [2^14, 2^15).
@@ -399,6 +443,7 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
             k.H = u.L > 0 ? u.L - 1 : 0;
             k.nkb = u.nkb;
             if (prepare_unit(k) != cudaSuccess) return TFX_ERR_UNSUPPORTED;
+            if (p->train && u.S > 0 && prepare_sos_bwd(u.S) != cudaSuccess) return TFX_ERR_UNSUPPORTED;
         }
     }
 
@@ -430,6 +475,45 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
     if (p->units.size() == 1 && p->units[0].tc) nbuf = 1;  // input copy for in-place operation
     p->ws_fused = p->scratch_bytes + nbuf * p->buf_bytes;
     p->ws_plain = (nst > 0 ? 2 : 0) * p->buf_bytes;
+
+    if (p->train) {
+        // saved for the backward: the input of every unit after the first (the
+        // first unit's input is x itself) and each cascade's chunk-start states
+        p->nch = p->N > 0 ? (p->N + T_CHUNK - 1) / T_CHUNK : 0;
+        size_t so = 0;
+        for (size_t i = 0; i < p->units.size(); ++i) {
+            HostUnit& u = p->units[i];
+            if (i > 0) {
+                u.off_act = so;
+                so = align_up(so + p->buf_bytes);
+            }
+            if (u.S > 0) {
+                u.off_ckpt = so;
+                so = align_up(so + (size_t)p->C * u.S * p->nch * sizeof(float2));
+            }
+        }
+        p->saved_bytes = so;
+        // backward workspace: the forward scratch (FIR units run their forward
+        // kernels on the reversed gradient), the reverse look-back scratch,
+        // per-tile / per-block FP32 partials, FP64 column sums, two gradient buffers
+        size_t scan = 0, part = 0, tmp = 0;
+        for (const HostUnit& u : p->units) {
+            if (u.S > 0) {
+                const size_t tiles = (size_t)p->C * (size_t)u.ntt;
+                scan = std::max(scan, align_up(ALIGN + tiles * u.S * sizeof(Carry)));
+                part = std::max(part, align_up(tiles * u.S * 8 * sizeof(float)));
+                tmp = std::max(tmp, align_up((size_t)COLSUM_GROUPS * u.S * 8 * sizeof(double)));
+            } else if (u.L > 0) {
+                part = std::max(part, align_up((size_t)fir_dh_rows(p->C, p->N) * u.Lp * sizeof(float)));
+                tmp = std::max(tmp, align_up((size_t)COLSUM_GROUPS * u.L * sizeof(double)));
+            }
+        }
+        p->b_scan = p->scratch_bytes;
+        p->b_part = p->b_scan + scan;
+        p->b_tmp = p->b_part + part;
+        p->b_gbuf = p->b_tmp + tmp;
+        p->bws_bytes = p->b_gbuf + 2 * p->buf_bytes;
+    }
     return TFX_OK;
 }
 
@@ -444,7 +528,7 @@ bool ranges_overlap_not_equal(const float* x, const float* y, int64_t C, int64_t
 // Launch unit i for channels [c0, c0 + Cg) reading `in` (row stride ldin) and
 // writing `out` (row stride ldout).
 int launch_unit_range(tfx_plan* p, int i, const float* in, int64_t ldin, float* out, int64_t ldout, int64_t c0,
-                      int64_t Cg, char* scratch, float* copy_buf, cudaStream_t s) {
+                      int64_t Cg, char* scratch, float* copy_buf, cudaStream_t s, float2* ckpt = nullptr) {
     const HostUnit& u = p->units[i];
     in += c0 * ldin;
     out += c0 * ldout;
@@ -478,7 +562,7 @@ int launch_unit_range(tfx_plan* p, int i, const float* in, int64_t ldin, float* 
         f.status = p->dstatus;
         return launch_fir_tc(f, s) == cudaSuccess ? TFX_OK : TFX_ERR_CUDA;
     }
-    UnitArgs a;
+    UnitArgs a{};
     a.x = in;
     a.ldx = ldin;
     a.y = out;
@@ -501,6 +585,8 @@ int launch_unit_range(tfx_plan* p, int i, const float* in, int64_t ldin, float* 
     a.sc.tail_len = u.tail_len;
     a.status = p->dstatus;
     a.drop_tile = (p->flags & TFX_PLAN_TEST_DROP_PUBLISH) ? 0 : -1;
+    a.ckpt = u.warp ? ckpt : nullptr;
+    a.nch = p->nch;
     if (cudaMemsetAsync(scratch, 0, ALIGN + u.flags_bytes + u.vals_bytes, s) != cudaSuccess) return TFX_ERR_CUDA;
     return (u.warp ? launch_sos_warp(a, s) : launch_unit(a, s)) == cudaSuccess ? TFX_OK : TFX_ERR_CUDA;
 }
@@ -559,6 +645,148 @@ int exec_plain(tfx_plan* p, const float* x, float* y, void* ws, cudaStream_t s) 
     }
     if (cur != y && launch_copy_rows(cur, y, p->C, p->N, ldc, p->ld, s) != cudaSuccess) return TFX_ERR_CUDA;
     return TFX_OK;
+}
+
+// Training forward: the fused units of a trainable plan, with every
+// intermediate written to the saved buffer (the backward reads it) and every
+// cascade storing its chunk-start states there.
+int exec_train(tfx_plan* p, const float* x, float* y, char* saved, void* ws, cudaStream_t s) {
+    char* scratch = static_cast<char*>(ws);
+    const int nu = (int)p->units.size();
+    if (nu == 0) return launch_copy_rows(x, y, p->C, p->N, p->ld, p->ld, s) == cudaSuccess ? TFX_OK : TFX_ERR_CUDA;
+    for (int i = 0; i < nu; ++i) {
+        const HostUnit& u = p->units[i];
+        const float* in = i == 0 ? x : reinterpret_cast<const float*>(saved + u.off_act);
+        const int64_t ldin = i == 0 ? p->ld : p->N;
+        float* out = i == nu - 1 ? y : reinterpret_cast<float*>(saved + p->units[i + 1].off_act);
+        const int64_t ldout = i == nu - 1 ? p->ld : p->N;
+        float2* ck = u.S > 0 ? reinterpret_cast<float2*>(saved + u.off_ckpt) : nullptr;
+        const int rc = launch_unit_range(p, i, in, ldin, out, ldout, 0, p->C, scratch, nullptr, s, ck);
+        if (rc != TFX_OK) return rc;
+    }
+    return TFX_OK;
+}
+
+// Backward over the units, last to first.  Between units the gradient is
+// kept either in time order or time-reversed: an FIR's input gradient is the
+// same FIR applied to the reversed gradient (FIR^T = J FIR J, J the time
+// reversal), so FIR units take and produce the reversed form, and a cascade
+// in front of an FIR writes it reversed.  With count_only nothing is enqueued
+// and *nlaunch receives the number of kernels a real call launches.
+int run_backward(tfx_plan* p, const float* x, const float* g, float* dx, double* dcoef, const char* saved, char* ws,
+                 cudaStream_t s, bool count_only, int* nlaunch) {
+    int nl = 0;
+#define TFX_LAUNCH(call)                                                     \
+    do {                                                                     \
+        ++nl;                                                                \
+        if (!count_only && (call) != cudaSuccess) return TFX_ERR_CUDA;       \
+    } while (0)
+    const int nu = (int)p->units.size();
+    const int64_t C = p->C, N = p->N;
+    float* gbuf[2] = {reinterpret_cast<float*>(ws + p->b_gbuf), reinterpret_cast<float*>(ws + p->b_gbuf + p->buf_bytes)};
+    float* part = reinterpret_cast<float*>(ws + p->b_part);
+    double* tmp = reinterpret_cast<double*>(ws + p->b_tmp);
+    const float* gcur = g;
+    int64_t ldg = p->ld;
+    bool grev = false;
+    int cur = -1;  // gradient buffer holding gcur (-1: the caller's g)
+    if (nu == 0 && dx && dx != g) TFX_LAUNCH(launch_copy_rows(g, dx, C, N, p->ld, p->ld, s));
+    for (int i = nu - 1; i >= 0; --i) {
+        const HostUnit& u = p->units[i];
+        const float* uin = i == 0 ? x : reinterpret_cast<const float*>(saved + u.off_act);
+        const int64_t ldu = i == 0 ? p->ld : N;
+        const int nxt = cur == 0 ? 1 : 0;
+        if (u.S > 0) {
+            BwdArgs a{};
+            a.u0 = uin;
+            a.ldu = ldu;
+            a.g = gcur;
+            a.ldg = ldg;
+            a.g_rev = grev ? 1 : 0;
+            if (i == 0) {
+                a.gout = dx;
+                a.ldo = p->ld;
+                a.out_rev = 0;
+            } else {
+                a.gout = gbuf[nxt];
+                a.ldo = N;
+                a.out_rev = p->units[i - 1].S == 0 ? 1 : 0;
+            }
+            a.ckpt = reinterpret_cast<const float2*>(saved + u.off_ckpt);
+            a.nch = p->nch;
+            a.C = C;
+            a.N = N;
+            a.ntt = u.ntt;
+            a.k.S = u.S;
+            a.k.gain = 1.0f;
+            a.k.coef = reinterpret_cast<const float*>(p->dconst + u.off_coef);
+            a.k.pw = reinterpret_cast<const float4*>(p->dconst + u.off_pw);
+            a.ticket = reinterpret_cast<unsigned*>(ws + p->b_scan);
+            a.carry = reinterpret_cast<Carry*>(ws + p->b_scan + ALIGN);
+            a.part = part;
+            a.status = p->dstatus;
+            const int64_t tiles = C * u.ntt;
+            if (!count_only &&
+                cudaMemsetAsync(ws + p->b_scan, 0, ALIGN + (size_t)tiles * u.S * sizeof(Carry), s) != cudaSuccess)
+                return TFX_ERR_CUDA;
+            TFX_LAUNCH(launch_sos_bwd(a, s));
+            if (dcoef) {
+                TFX_LAUNCH(launch_colsum(part, tiles, (int64_t)u.S * 8, u.S * 8, tmp, COLSUM_GROUPS, s));
+                TFX_LAUNCH(launch_sos_grad_finalize(tmp, COLSUM_GROUPS, u.S,
+                                                    reinterpret_cast<const double*>(p->dconst + u.off_raw),
+                                                    reinterpret_cast<const int64_t*>(p->dconst + u.off_dst), dcoef,
+                                                    s));
+            }
+            if (i > 0) {
+                gcur = gbuf[nxt];
+                ldg = N;
+                grev = a.out_rev != 0;
+                cur = nxt;
+            }
+        } else {
+            if (dcoef) {
+                TFX_LAUNCH(launch_fir_dh(gcur, ldg, grev ? 1 : 0, uin, ldu, C, N, u.L, u.Lp, part, s));
+                TFX_LAUNCH(launch_colsum(part, fir_dh_rows(C, N), u.Lp, u.L, tmp, COLSUM_GROUPS, s));
+                TFX_LAUNCH(launch_fir_grad_finalize(tmp, COLSUM_GROUPS, u.L, dcoef + u.fir_dst, s));
+            }
+            if (i == 0 && !dx) continue;
+            if (!grev) {
+                TFX_LAUNCH(launch_flip_rows(gcur, gbuf[nxt], C, N, ldg, N, s));
+                gcur = gbuf[nxt];
+                ldg = N;
+                grev = true;
+                cur = nxt;
+            }
+            const int o = cur == 0 ? 1 : 0;
+            ++nl;
+            if (!count_only) {
+                const int rc = launch_unit_range(p, i, gcur, N, gbuf[o], N, 0, C, ws, nullptr, s);
+                if (rc != TFX_OK) return rc;
+            }
+            if (i == 0) {
+                TFX_LAUNCH(launch_flip_rows(gbuf[o], dx, C, N, N, p->ld, s));
+            } else {
+                gcur = gbuf[o];
+                ldg = N;
+                cur = o;
+            }
+        }
+    }
+#undef TFX_LAUNCH
+    if (nlaunch) *nlaunch = nl;
+    return TFX_OK;
+}
+
+// Byte span of a [C x N] signal with row stride ld.
+size_t signal_span(int64_t C, int64_t N, int64_t ld) {
+    return C == 0 || N == 0 ? 0 : ((size_t)(C - 1) * (size_t)ld + (size_t)N) * sizeof(float);
+}
+
+bool bytes_overlap(const void* a, size_t na, const void* b, size_t nb) {
+    if (!a || !b || na == 0 || nb == 0) return false;
+    const char* ab = static_cast<const char*>(a);
+    const char* bb = static_cast<const char*>(b);
+    return ab < bb + nb && bb < ab + na;
 }
 
 int check_exec_args(tfx_plan* p, const float* x, float* y, void* ws, size_t ws_bytes, size_t need) {
@@ -656,7 +884,7 @@ int tfx_plan_create(tfx_plan** out, int64_t C, int64_t N, int64_t ld, const tfx_
     rc = validate_stages(st, nst);
     if (rc != TFX_OK) return rc;
     if (flags & ~(TFX_PLAN_FIR_CUDA_CORES | TFX_PLAN_UNFUSED | TFX_PLAN_FIR_BF16_PLAIN | TFX_PLAN_FIR_BF16_SPLIT |
-                  TFX_PLAN_SCAN_WARP_TILES | TFX_PLAN_TEST_DROP_PUBLISH))
+                  TFX_PLAN_SCAN_WARP_TILES | TFX_PLAN_TRAINABLE | TFX_PLAN_TEST_DROP_PUBLISH))
         return TFX_ERR_INVALID;
     tfx_plan* p = new (std::nothrow) tfx_plan();
     if (!p) return TFX_ERR_NOMEM;
@@ -715,6 +943,72 @@ void tfx_plan_destroy(tfx_plan* p) {
     if (p->dconst) cudaFree(p->dconst);
     if (p->dstatus) cudaFree(p->dstatus);
     delete p;
+}
+
+size_t tfx_plan_saved_size(const tfx_plan* p) { return p && p->train ? p->saved_bytes : 0; }
+
+size_t tfx_plan_backward_workspace_size(const tfx_plan* p) { return p && p->train ? p->bws_bytes : 0; }
+
+int64_t tfx_plan_coef_count(const tfx_plan* p) { return p ? p->ncoef : -1; }
+
+int tfx_plan_forward_train(tfx_plan* p, const float* x, float* y, void* saved, size_t saved_bytes, void* ws,
+                           size_t ws_bytes, tfx_stream s) {
+    if (!p || !p->train) return TFX_ERR_INVALID;
+    int rc = check_exec_args(p, x, y, ws, ws_bytes, p->ws_fused);
+    if (rc != TFX_OK) return rc;
+    if (p->C == 0 || p->N == 0) return TFX_OK;
+    if (x == y) return TFX_ERR_INVALID;  // the backward reads x again
+    if (p->saved_bytes > 0 &&
+        (!saved || saved_bytes < p->saved_bytes || reinterpret_cast<uintptr_t>(saved) % ALIGN != 0))
+        return TFX_ERR_WORKSPACE;
+    const size_t span = signal_span(p->C, p->N, p->ld);
+    if (bytes_overlap(saved, p->saved_bytes, x, span) || bytes_overlap(saved, p->saved_bytes, y, span))
+        return TFX_ERR_INVALID;
+    return exec_train(p, x, y, static_cast<char*>(saved), ws, reinterpret_cast<cudaStream_t>(s));
+}
+
+int tfx_plan_backward(tfx_plan* p, const float* x, const float* g, float* dx, double* dcoef, const void* saved,
+                      size_t saved_bytes, void* ws, size_t ws_bytes, tfx_stream s) {
+    if (!p || !p->train) return TFX_ERR_INVALID;
+    if (!dx && !dcoef) return TFX_ERR_INVALID;
+    const int64_t C = p->C, N = p->N;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+    if (C == 0 || N == 0) {
+        if (dcoef && p->ncoef > 0 && cudaMemsetAsync(dcoef, 0, (size_t)p->ncoef * sizeof(double), st) != cudaSuccess)
+            return TFX_ERR_CUDA;
+        return TFX_OK;
+    }
+    if (!x || !g) return TFX_ERR_INVALID;
+    const size_t span = signal_span(C, N, p->ld);
+    if (dx && (ranges_overlap_not_equal(g, dx, C, N, p->ld) || bytes_overlap(x, span, dx, span)))
+        return TFX_ERR_INVALID;
+    if (p->bws_bytes > 0 && (!ws || ws_bytes < p->bws_bytes || reinterpret_cast<uintptr_t>(ws) % ALIGN != 0))
+        return TFX_ERR_WORKSPACE;
+    if (p->saved_bytes > 0 &&
+        (!saved || saved_bytes < p->saved_bytes || reinterpret_cast<uintptr_t>(saved) % ALIGN != 0))
+        return TFX_ERR_WORKSPACE;
+    return run_backward(p, x, g, dx, dcoef, static_cast<const char*>(saved), static_cast<char*>(ws), st, false,
+                        nullptr);
+}
+
+int tfx_plan_backward_launch_count(const tfx_plan* p, int with_dx, int with_dcoef) {
+    if (!p || !p->train) return -1;
+    if (p->C == 0 || p->N == 0) return 0;
+    int n = 0;
+    // count_only: no pointer is dereferenced and nothing is enqueued
+    float dummy_dx;
+    double dummy_dc;
+    run_backward(const_cast<tfx_plan*>(p), nullptr, nullptr, with_dx ? &dummy_dx : nullptr,
+                 with_dcoef ? &dummy_dc : nullptr, nullptr, nullptr, nullptr, true, &n);
+    return n;
+}
+
+int tfx_mse(const float* y, const float* target, float* g, int64_t C, int64_t N, int64_t ld, double* loss,
+            tfx_stream s) {
+    if (C < 0 || N < 0 || ld < (N > 1 ? N : 1) || !loss) return TFX_ERR_INVALID;
+    if (C > 0 && N > 0 && (!y || !target)) return TFX_ERR_INVALID;
+    return launch_mse(y, target, g, C, N, ld, loss, reinterpret_cast<cudaStream_t>(s)) == cudaSuccess ? TFX_OK
+                                                                                          : TFX_ERR_CUDA;
 }
 
 size_t tfx_chain_workspace_size(int64_t C, int64_t N, int64_t ld, const tfx_stage* st, int32_t nst) {

@@ -72,6 +72,31 @@ struct UnitArgs {
     UnitScratch sc;
     int* status;     // device status word (TFX_OK or TFX_ERR_TIMEOUT)
     int64_t drop_tile;  // test hook: this tile never publishes (-1 = off)
+    // training forward (warp-tile cascade only): the true state of every
+    // section at every 32-sample chunk start, [C][S][nch] float2, or null
+    float2* ckpt;
+    int64_t nch;
+};
+
+// Reverse-time adjoint of an SOS cascade (warp-tile geometry of the forward
+// training pass: 32 lanes x T_CHUNK samples per tile).
+struct BwdArgs {
+    const float* u0;   // the cascade's forward input, row stride ldu
+    int64_t ldu;
+    const float* g;    // dL/d(cascade output), row stride ldg
+    int64_t ldg;
+    int g_rev;         // 1: row holds the gradient time-reversed (sample n at N-1-n)
+    float* gout;       // dL/d(cascade input), row stride ldo (null: not written)
+    int64_t ldo;
+    int out_rev;       // 1: write gout time-reversed
+    const float2* ckpt;  // [C][S][nch] forward chunk-start states
+    int64_t nch;
+    int64_t C, N, ntt;   // ntt = tiles of 32 * T_CHUNK samples per channel
+    UnitConst k;         // coef rows [S][8]: b0 c1 c2 a1 a2 d (d = a1 b2 - a2 b1)
+    unsigned* ticket;
+    Carry* carry;        // [tiles][S] reverse look-back carries
+    float* part;         // [tiles][S][8]: per-tile partial dL/d(b0 b1 b2 a1 a2)
+    int* status;
 };
 
 // Operand precision of the tensor-core FIR.
@@ -218,5 +243,26 @@ size_t fir_tc_long_smem(int rows);
 constexpr int TC_KBLK = 64;  // K-steps per streamed tap block
 cudaError_t launch_fir_tc(const FirTcArgs& a, cudaStream_t s);
 cudaError_t prepare_unit(const UnitConst& k);
+
+// Backward (adjoint) launchers, defined in k_bwd.cu.
+constexpr int BWD_SMAX = 8;  // sections per cascade unit in a trainable plan
+size_t sos_bwd_smem_bytes(int S);
+cudaError_t prepare_sos_bwd(int S);
+cudaError_t launch_sos_bwd(const BwdArgs& a, cudaStream_t s);
+cudaError_t launch_flip_rows(const float* x, float* y, int64_t C, int64_t N, int64_t ldx, int64_t ldy,
+                             cudaStream_t s);
+constexpr int DH_BLOCK = 2048;  // samples per warp in the FIR tap-gradient kernel
+constexpr int DH_WIN = 256;     // lags per shared-memory window
+int64_t fir_dh_rows(int64_t C, int64_t N);
+cudaError_t launch_fir_dh(const float* g, int64_t ldg, int g_rev, const float* u, int64_t ldu, int64_t C,
+                          int64_t N, int L, int Lp, float* part, cudaStream_t s);
+cudaError_t launch_colsum(const float* part, int64_t rows, int64_t ld, int ncol, double* tmp, int groups,
+                          cudaStream_t s);
+constexpr int COLSUM_GROUPS = 64;
+cudaError_t launch_sos_grad_finalize(const double* tmp, int groups, int S, const double* raw,
+                                     const int64_t* dst, double* dcoef, cudaStream_t s);
+cudaError_t launch_fir_grad_finalize(const double* tmp, int groups, int L, double* dcoef, cudaStream_t s);
+cudaError_t launch_mse(const float* y, const float* t, float* g, int64_t C, int64_t N, int64_t ld,
+                       double* loss, cudaStream_t s);
 
 }  // namespace tfx

@@ -300,6 +300,21 @@ def pin_vjp_fir_definition(lib, rng):
     assert np.max(np.abs(dh - want)) <= 1e-12 * np.max(np.abs(want))
 
 
+def pin_vjp_dx_sampled(lib, rng):
+    """dL/dx at chosen samples (impulse-response route) against central
+    differences of the forward chain in those samples."""
+    stages, x, g = _vjp_case(rng)
+    idx = [0, 5, 31, 59]
+    got = lib.chain_vjp_dx_at(g[1], stages, idx)
+    eps = 1e-6
+    for m, v in zip(idx, got):
+        xp, xm = x[1].copy(), x[1].copy()
+        xp[m] += eps
+        xm[m] -= eps
+        fd = (np.sum(g[1] * lib.chain(xp, stages)) - np.sum(g[1] * lib.chain(xm, stages))) / (2 * eps)
+        assert abs(v - fd) <= 1e-6 * max(1.0, abs(fd)), f"sample {m}: {v} vs FD {fd}"
+
+
 ALL_PINS = [
     pin_fir_impulse,
     pin_fir_toeplitz,
@@ -314,4 +329,5 @@ ALL_PINS = [
     pin_vjp_finite_differences,
     pin_vjp_input_adjoint,
     pin_vjp_fir_definition,
+    pin_vjp_dx_sampled,
 ]
