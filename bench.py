@@ -32,7 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "channel-samples/s through filter chain (fwd) vs plain GPU; % HBM roofline"
+METRIC = "channel-samples/s through filter chain (fwd, fwd+bwd) vs plain GPU; % HBM roofline"
 UNIT = "channel-samples/s"
 
 
@@ -53,7 +53,15 @@ def parse():
                     help="configuration to time (default: the one the headline metric is quoted on)")
     ap.add_argument("--part", choices=["chain", "iir", "fir"], default="chain",
                     help="time the whole chain (default) or only its IIR cascade / FIR stage (profiling)")
-    return ap.parse_args()
+    ap.add_argument("--mode", choices=["fwd", "fwdbwd"], default=None,
+                    help="step = forward pass (default), or training forward + MSE + backward "
+                         "(default for the differentiable_chain workload)")
+    ap.add_argument("--no-fwdbwd", action="store_true",
+                    help="skip the fwd+bwd measurement added to a forward run")
+    args = ap.parse_args()
+    if args.mode is None:
+        args.mode = "fwdbwd" if args.workload == "differentiable_chain" else "fwd"
+    return args
 
 
 def dist_env():
@@ -246,6 +254,141 @@ def reference_arm(args, ws, rank):
     }), flush=True)
 
 
+BWD_FLOP_PER_SECTION = 30.0  # recompute 10 + adjoint all-pole 4 + input gradient 6 + coefficient sums 10
+FWDBWD_BYTES = 32.0          # fwd 8 + loss 12 (read y, target; write g) + bwd 12 (read g, x; write dx)
+
+
+def measure_fwdbwd(wl, steps, warmup, dev, stream, torch, dist, ws, rank, pk, sm_count, with_e2e, with_cpu):
+    """One training step of the chain: training forward (saves chunk-start
+    states), MSE against a target (loss and dL/dy in one kernel), backward
+    (dL/dx and dL/d(every coefficient)).  Inputs resident in HBM."""
+    from paper_2504_08624_gb300 import api, _native as NAT
+    units = wl.C * wl.N
+    S = sum(np.asarray(c).reshape(-1, 6).shape[0] for k, c in wl.stages if k == "sos")
+    x_host = torch.from_numpy(wl.make_signal()).pin_memory()
+    x = x_host.to(dev)
+    # the target: the input through the same chain with perturbed numerators
+    tstages = [(k, (np.asarray(c) * np.array([1.1, 0.9, 1.05, 1, 1, 1]) if k == "sos" else np.asarray(c) * 0.98))
+               for k, c in wl.stages]
+    target = api.chain(x, tstages)
+    plan = api.Plan(wl.C, wl.N, wl.stages, flags=NAT.TFX_PLAN_TRAINABLE)
+    saved = plan.new_saved()
+    fws = plan.workspace()
+    bws = plan.backward_workspace()
+    y = torch.empty_like(x)
+    g = torch.empty_like(x)
+    dx = torch.empty_like(x)
+    dcoef = torch.empty(plan.coef_count, dtype=torch.float64, device=dev)
+
+    def fwd():
+        plan.forward_train(x, y, saved, fws)
+
+    def loss_step():
+        return api.mse(y, target, g)
+
+    def bwd():
+        plan.backward(x, g, dx, dcoef, saved, bws)
+
+    def step():
+        fwd()
+        loss_step()
+        bwd()
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    t = time_gpu(step, steps, 0, stream, torch, dist)
+    if plan.get_error() != 0:
+        raise RuntimeError("device reported a timeout during the fwd+bwd run")
+    t_all = t
+    if dist is not None:
+        tt = torch.tensor([t], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_all = float(tt.item())
+    k_parts = max(5, steps // 4)
+    t_f = time_gpu(fwd, k_parts, 2, stream, torch, None) / k_parts
+    t_l = time_gpu(loss_step, k_parts, 2, stream, torch, None) / k_parts
+    t_b = time_gpu(bwd, k_parts, 2, stream, torch, None) / k_parts
+    launches = plan.launches_per_execute + 1 + plan.backward_launches(True, True)
+    step_s = t / steps
+
+    # dominant kernel: the cascade's reverse-time adjoint scan, timed alone
+    # through a cascade-only trainable plan's backward with only dL/dx asked
+    # (then that kernel is the only launch)
+    sos_stages = [st for st in wl.stages if st[0] == "sos"]
+    roof = None
+    if S > 0:
+        sp = api.Plan(wl.C, wl.N, sos_stages, flags=NAT.TFX_PLAN_TRAINABLE)
+        ssaved = sp.new_saved()
+        sp.forward_train(x, y, ssaved)
+        assert sp.backward_launches(True, False) == (S + 7) // 8
+        k_k = max(10, steps // 3)
+        t_k = time_gpu(lambda: sp.backward(x, g, dx, None, ssaved), k_k, 3, stream, torch, None) / k_k
+        sp.close()
+        alu_peak = fp32_alu_peak_tflops(sm_count, pk["sm_max_mhz"])
+        ach = units * BWD_FLOP_PER_SECTION * S / t_k / 1e12
+        roof = {"bound": "alu", "kernel": "k_sos_bwd", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": ach / alu_peak, "kernel_ms": t_k * 1e3, "share_of_step": t_k / step_s,
+                "traffic": traffic_for("k_sos_bwd", wl.name),
+                "peak_source": f"{sm_count} SMs x 128 FP32 FMA x 2 flop x {pk['sm_max_mhz']:.0f} MHz",
+                "note": f"{BWD_FLOP_PER_SECTION:.0f} algorithmic flop per sample per section"}
+    ach_gbs = units * FWDBWD_BYTES / step_s / 1e9
+    hbm = {"bound": "hbm", "achieved": ach_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+           "frac": ach_gbs / pk["hbm_gbs"], "peak_source": pk["source"],
+           "note": f"{FWDBWD_BYTES:.0f} B per channel-sample: forward 8, loss 12, backward 12"}
+
+    e2e = None
+    if with_e2e:
+        # the public API a training loop calls: host batch and target copied in,
+        # the FilterChain module forward, the fused MSE loss, autograd backward,
+        # the loss and coefficient gradients read back
+        t_host = target.cpu().pin_memory()
+        model = api.FilterChain(wl.stages)
+
+        def e2e_step():
+            for prm in model.parameters():
+                prm.grad = None
+            xd = x_host.to(dev, non_blocking=True)
+            td = t_host.to(dev, non_blocking=True)
+            loss = api.mse_loss(model(xd), td)
+            loss.backward()
+            return float(loss.detach())
+
+        w_e, k_e = 3, max(5, min(steps // 5, 30))
+        t_e = time_gpu(e2e_step, k_e, w_e, stream, torch, dist)
+        if dist is not None:
+            tt = torch.tensor([t_e], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_e = float(tt.item())
+        e2e = {"value": units * ws * k_e / t_e, "unit": UNIT, "h2d_bytes_per_step": int(2 * units * 4),
+               "d2h_bytes_per_step": int(8 + 8 * plan.coef_count), "ms_per_step": t_e / k_e * 1e3, "steps": k_e,
+               "api": "FilterChain + mse_loss + loss.backward()"}
+
+    cpu = None
+    if with_cpu and rank == 0 and ws == 1:
+        import oracle
+        lib = oracle.load()
+        # about 10-30 s on the host cores: the oracle's dL/dx is O(N^2) per channel
+        Cs = min(wl.C, 4 * (os.cpu_count() or 1))
+        Ns = min(wl.N, 65536)
+        xs = wl.make_signal(Cs, Ns).astype(np.float64)
+        gs = np.random.default_rng(5).standard_normal(xs.shape)
+        t0 = time.perf_counter()
+        lib.chain(xs, wl.stages)
+        lib.chain_vjp(xs, gs, wl.stages)
+        dt = time.perf_counter() - t0
+        cpu = {"value": Cs * Ns / dt, "unit": UNIT, "cores": lib.num_threads(), "kind": "oracle",
+               "sample": f"{Cs} channels x first {Ns} samples: FP64 oracle chain + vector-Jacobian product "
+                         f"(dL/dx from the impulse response, O(N^2) per channel; coefficient sensitivities), "
+                         f"{dt:.1f} s"}
+    plan.close()
+    return {"workload": wl.name, "value": units * ws * steps / t_all, "unit": UNIT, "ms_per_step": step_s * 1e3,
+            "steps": steps, "step": "training forward + MSE loss and dL/dy + backward (dL/dx, dL/dcoef)",
+            "fwd_ms": t_f * 1e3, "loss_ms": t_l * 1e3, "bwd_ms": t_b * 1e3, "gpu_launches_per_step": launches,
+            "roofline": roof, "roofline_hbm": hbm, "e2e": e2e, "cpu_baseline": cpu,
+            "dtype": "f32", "plain_gpu": None}
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -266,6 +409,10 @@ def main():
     wl = workload(args)
     bytes_ps, flops_ps, S, L = algorithmic(wl)
     units = wl.C * wl.N
+
+    if args.mode == "fwdbwd":
+        run_fwdbwd_main(args, wl, dev, torch, dist, ws, rank, local)
+        return
 
     x_host = torch.from_numpy(wl.make_signal()).pin_memory()
     x = x_host.to(dev)
@@ -374,6 +521,12 @@ def main():
                "sample": f"{Cs} of {wl.C} channels x first {Ns} of {wl.N} samples, FP64 oracle chain, "
                          f"{dt:.1f} s on {thr} threads"}
 
+    fwd_bwd = None
+    if not args.no_fwdbwd and args.part == "chain":
+        from paper_2504_08624_gb300 import workloads as W
+        fwd_bwd = measure_fwdbwd(W.differentiable_chain_forward(), min(args.steps, 100), max(3, args.warmup), dev,
+                                 stream, torch, dist, ws, rank, pk, sm_count, not args.no_e2e, False)
+
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -386,9 +539,41 @@ def main():
                        "l2": "inputs 737 MB > 129 MB L2, no flush", "plan_flags": args.flags},
             "roofline": bound, "roofline_hbm": hbm, "cpu_baseline": cpu, "e2e": e2e,
             "plain_gpu": plain, "gpu_launches": int(args.steps * plan.launches_per_execute), "clocks": clocks,
-            "gpu": props.name,
+            "gpu": props.name, "fwd_bwd": fwd_bwd,
         }
         print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_fwdbwd_main(args, wl, dev, torch, dist, ws, rank, local):
+    """--mode fwdbwd: the training step is the timed step (headline value)."""
+    stream = torch.cuda.current_stream(dev)
+    pk = peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    r = measure_fwdbwd(wl, args.steps, args.warmup, dev, stream, torch, dist, ws, rank, pk,
+                       props.multi_processor_count, not args.no_e2e, not args.no_cpu_baseline)
+    clocks = sampler.stop()
+    if rank == 0:
+        S = sum(np.asarray(c).reshape(-1, 6).shape[0] for k, c in wl.stages if k == "sos")
+        L = sum(np.asarray(c).size for k, c in wl.stages if k == "fir")
+        print(json.dumps({
+            "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name, "mode": "fwd+bwd", "channels": wl.C, "samples": wl.N,
+                       "chain": f"{S} SOS sections + FIR of {L} taps, MSE loss",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                       "l2": f"signals {wl.C * wl.N * 4 / 1e6:.0f} MB each, several per step > 129 MB L2, no flush"},
+            "roofline": r["roofline"], "roofline_hbm": r["roofline_hbm"], "cpu_baseline": r["cpu_baseline"],
+            "e2e": r["e2e"], "plain_gpu": r["plain_gpu"],
+            "gpu_launches": int(args.steps * r["gpu_launches_per_step"]), "clocks": clocks, "gpu": props.name,
+            "fwd_ms": r["fwd_ms"], "loss_ms": r["loss_ms"], "bwd_ms": r["bwd_ms"],
+        }), flush=True)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()

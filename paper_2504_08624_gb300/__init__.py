@@ -9,7 +9,8 @@ __version__ = "0.1.0"
 
 
 def __getattr__(name):
-    if name in ("chain", "fir", "sos", "Plan", "TfxError", "chain_ad", "ChainFunction", "FilterChain", "mse"):
+    if name in ("chain", "fir", "sos", "Plan", "TfxError", "chain_ad", "ChainFunction", "FilterChain", "mse",
+                "mse_loss"):
         from . import api
         return getattr(api, name)
     raise AttributeError(name)

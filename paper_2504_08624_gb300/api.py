@@ -245,6 +245,31 @@ def mse(y: torch.Tensor, target: torch.Tensor, g: torch.Tensor | None = None) ->
 # ---------------------------------------------------------------------------
 # autograd
 
+
+class MSELossFunction(torch.autograd.Function):
+    """mean((y - target)^2) with its gradient from the library's fused kernel
+    (one pass computes the loss and dL/dy)."""
+
+    @staticmethod
+    def forward(ctx, y, target):
+        y2 = _check_signal(y).contiguous()
+        t2 = _check_signal(target).contiguous()
+        g = torch.empty_like(y2)
+        loss = mse(y2, t2, g)
+        ctx.save_for_backward(g)
+        ctx.shape = y.shape
+        return loss
+
+    @staticmethod
+    def backward(ctx, gl):
+        (g,) = ctx.saved_tensors
+        return (g * gl.to(g.dtype)).reshape(ctx.shape), None
+
+
+def mse_loss(y: torch.Tensor, target: torch.Tensor) -> torch.Tensor:
+    """Differentiable MSE on the GPU kernel (the differentiable-chain workload's loss)."""
+    return MSELossFunction.apply(y, target)
+
 _TRAIN_PLANS: dict = {}
 _TRAIN_PLANS_MAX = 8
 

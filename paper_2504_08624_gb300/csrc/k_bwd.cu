@@ -252,10 +252,13 @@ __global__ void __launch_bounds__(32 * BWD_WPB) k_sos_bwd(BwdArgs a) {
             pt.db2 = warp_sum(pt.db2);
             pt.da1 = warp_sum(pt.da1);
             pt.da2 = warp_sum(pt.da2);
-            if (lane == 0) {
-                float4* pp = reinterpret_cast<float4*>(a.part + ((int64_t)tk * S + sf) * 8);
-                pp[0] = make_float4(pt.db0, pt.db1, pt.db2, -pt.da1);
-                pp[1] = make_float4(-pt.da2, 0.f, 0.f, 0.f);
+            if (lane == 0) {  // column-major partials: [S * 5][tiles]
+                float* pp = a.part + (int64_t)(sf * 5) * tiles + tk;
+                pp[0] = pt.db0;
+                pp[tiles] = pt.db1;
+                pp[2 * tiles] = pt.db2;
+                pp[3 * tiles] = -pt.da1;
+                pp[4 * tiles] = -pt.da2;
             }
         }
         if (sr < 0) break;
@@ -369,24 +372,46 @@ cudaError_t launch_sos_bwd(const BwdArgs& a, cudaStream_t s) {
 // time reversal of rows: y[c][n] = x[c][N-1-n]
 
 __global__ void k_flip_rows(const float* __restrict__ x, float* __restrict__ y, int64_t C, int64_t N, int64_t ldx,
-                            int64_t ldy) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= C * N) return;
-    const int64_t c = idx / N, n = idx % N;
-    y[c * ldy + n] = x[c * ldx + (N - 1 - n)];
+                            int64_t ldy, int vec) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = blockIdx.y; c < C; c += gridDim.y) {
+        const float* xr = x + c * ldx;
+        float* yr = y + c * ldy;
+        if (vec) {  // N, ldx, ldy multiples of 4 and 16-byte aligned rows
+            const int64_t n4 = N / 4;
+            const float4* x4 = reinterpret_cast<const float4*>(xr);
+            float4* y4 = reinterpret_cast<float4*>(yr);
+            for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+                const float4 v = x4[n4 - 1 - i];
+                y4[i] = make_float4(v.w, v.z, v.y, v.x);
+            }
+        } else {
+            for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += stride)
+                yr[n] = xr[N - 1 - n];
+        }
+    }
 }
 
 cudaError_t launch_flip_rows(const float* x, float* y, int64_t C, int64_t N, int64_t ldx, int64_t ldy,
                              cudaStream_t s) {
     if (C <= 0 || N <= 0) return cudaSuccess;
+    const int vec = (N % 4 == 0 && ldx % 4 == 0 && ldy % 4 == 0 && (reinterpret_cast<uintptr_t>(x) & 15) == 0 &&
+                     (reinterpret_cast<uintptr_t>(y) & 15) == 0)
+                        ? 1
+                        : 0;
     const int bs = 256;
-    k_flip_rows<<<(unsigned)((C * N + bs - 1) / bs), bs, 0, s>>>(x, y, C, N, ldx, ldy);
+    const int64_t per_row = vec ? N / 4 : N;
+    int64_t gx = (per_row + bs - 1) / bs;
+    if (gx > 1024) gx = 1024;
+    const int64_t gy = C < 65535 ? C : 65535;
+    k_flip_rows<<<dim3((unsigned)gx, (unsigned)gy), bs, 0, s>>>(x, y, C, N, ldx, ldy, vec);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// FIR tap gradient: part[blk][k] = sum over the DH_BLOCK samples n of block
-// blk of g[n] u[n-k], k < Lp (a multiple of 16 >= L).  One warp per block,
+// FIR tap gradient on CUDA cores (plans that keep FIRs off the tensor cores):
+// part[k][blk] = sum over the DH_BLOCK samples n of block blk of g[n] u[n-k],
+// k < L.  One warp per block,
 // lane l owns samples [64 l, 64 l + 64) of it; lags are walked in windows of
 // DH_WIN staged in shared memory, 16 lags per register pass.  Shared arrays
 // are padded by one word per 64 (index i at i + i/64) so that the 32 lanes'
@@ -470,7 +495,7 @@ __global__ void __launch_bounds__(32 * DH_WPB) k_fir_dh(const float* __restrict_
             }
             acc[0] += __shfl_xor_sync(FULL, acc[0], 1);
             const int k = wi * DH_WIN + 16 * kb + (lane >> 1);
-            if ((lane & 1) == 0 && k < Lp) part[blk * Lp + k] = acc[0];
+            if ((lane & 1) == 0 && k < L) part[(int64_t)k * (C * nbpc) + blk] = acc[0];  // [L][blocks]
         }
     }
 }
@@ -487,41 +512,41 @@ cudaError_t launch_fir_dh(const float* g, int64_t ldg, int g_rev, const float* u
 }
 
 // ---------------------------------------------------------------------------
-// FP64 column sums of FP32 partials: tmp[grp][col] = sum of part[r][col] over
-// the rows r = grp, grp + groups, ...
+// FP64 column sums of column-major FP32 partials: out[col] = sum_r part[col][r].
+// One CTA per column; the rows are read contiguously and reduced in a tree.
 
-__global__ void k_colsum(const float* __restrict__ part, int64_t rows, int64_t ld, int ncol, double* __restrict__ tmp,
-                         int groups) {
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
-    const int grp = blockIdx.y;
-    if (col >= ncol) return;
+__global__ void k_colsum(const float* __restrict__ part, int64_t rows, double* __restrict__ out) {
+    __shared__ double red[8];
+    const float* p = part + (int64_t)blockIdx.x * rows;
     double acc = 0.0;
-    for (int64_t r = grp; r < rows; r += groups) acc += (double)part[r * ld + col];
-    tmp[(int64_t)grp * ncol + col] = acc;
+    for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) acc += (double)p[r];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+        out[blockIdx.x] = s;
+    }
 }
 
-cudaError_t launch_colsum(const float* part, int64_t rows, int64_t ld, int ncol, double* tmp, int groups,
-                          cudaStream_t s) {
+cudaError_t launch_colsum(const float* part, int64_t rows, int ncol, double* out, cudaStream_t s) {
     if (ncol <= 0) return cudaSuccess;
-    const int bs = 128;
-    dim3 grid((unsigned)((ncol + bs - 1) / bs), (unsigned)groups);
-    k_colsum<<<grid, bs, 0, s>>>(part, rows, ld, ncol, tmp, groups);
+    k_colsum<<<(unsigned)ncol, 256, 0, s>>>(part, rows, out);
     return cudaGetLastError();
 }
 
-// Section gradients from the normalised-coefficient sums (columns s*8 + 0..4 of
-// tmp: b0 b1 b2 a1 a2) to the raw row (b0 b1 b2 a0 a1 a2), whose normalised
-// values are b/a0 and a/a0:
+// Section gradients from the normalised-coefficient sums (sums[s*5 + 0..4]:
+// b0 b1 b2 a1 a2) to the raw row (b0 b1 b2 a0 a1 a2), whose normalised values
+// are b/a0 and a/a0:
 //   dL/db_k = G_bk / a0,  dL/da_k = G_ak / a0 (k = 1, 2),
 //   dL/da0  = -(sum_k (b_k/a0) G_bk + sum_k (a_k/a0) G_ak) / a0.
-__global__ void k_sos_grad_finalize(const double* __restrict__ tmp, int groups, int S, const double* __restrict__ raw,
+__global__ void k_sos_grad_finalize(const double* __restrict__ sums, int S, const double* __restrict__ raw,
                                     const int64_t* __restrict__ dst, double* __restrict__ dcoef) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
-    const int ncol = S * 8;
-    double G[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int grp = 0; grp < groups; ++grp)
-        for (int k = 0; k < 5; ++k) G[k] += tmp[(int64_t)grp * ncol + s * 8 + k];
+    const double* G = sums + 5 * s;
     const double* r = raw + 6 * s;
     const double inv = 1.0 / r[3];
     double* o = dcoef + dst[s];
@@ -533,24 +558,10 @@ __global__ void k_sos_grad_finalize(const double* __restrict__ tmp, int groups, 
     o[3] = -(r[0] * G[0] + r[1] * G[1] + r[2] * G[2] + r[4] * G[3] + r[5] * G[4]) * inv * inv;
 }
 
-cudaError_t launch_sos_grad_finalize(const double* tmp, int groups, int S, const double* raw, const int64_t* dst,
+cudaError_t launch_sos_grad_finalize(const double* sums, int S, const double* raw, const int64_t* dst,
                                      double* dcoef, cudaStream_t s) {
     if (S <= 0) return cudaSuccess;
-    k_sos_grad_finalize<<<(unsigned)((S + 63) / 64), 64, 0, s>>>(tmp, groups, S, raw, dst, dcoef);
-    return cudaGetLastError();
-}
-
-__global__ void k_fir_grad_finalize(const double* __restrict__ tmp, int groups, int L, double* __restrict__ dcoef) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= L) return;
-    double acc = 0.0;
-    for (int grp = 0; grp < groups; ++grp) acc += tmp[(int64_t)grp * L + k];
-    dcoef[k] = acc;
-}
-
-cudaError_t launch_fir_grad_finalize(const double* tmp, int groups, int L, double* dcoef, cudaStream_t s) {
-    if (L <= 0) return cudaSuccess;
-    k_fir_grad_finalize<<<(unsigned)((L + 127) / 128), 128, 0, s>>>(tmp, groups, L, dcoef);
+    k_sos_grad_finalize<<<(unsigned)((S + 63) / 64), 64, 0, s>>>(sums, S, raw, dst, dcoef);
     return cudaGetLastError();
 }
 
@@ -559,19 +570,32 @@ cudaError_t launch_fir_grad_finalize(const double* tmp, int groups, int L, doubl
 // g = 2 (y - t) / (C N).  The loss is accumulated in FP64 (one atomic per CTA).
 
 __global__ void k_mse(const float* __restrict__ y, const float* __restrict__ t, float* __restrict__ g, int64_t C,
-                      int64_t N, int64_t ld, double* __restrict__ loss) {
+                      int64_t N, int64_t ld, double inv, double* __restrict__ loss, int flat4) {
     __shared__ double red[8];
-    const double inv = 1.0 / ((double)C * (double)N);
     const float ginv = (float)(2.0 * inv);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double acc = 0.0;
-    const int64_t total = C * N;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c = idx / N, n = idx % N;
-        const int64_t o = c * ld + n;
-        const float d = y[o] - t[o];
-        if (g) g[o] = d * ginv;
-        acc += (double)d * (double)d;
+    if (flat4) {  // dense rows (ld == N), 16-byte aligned, C N a multiple of 4
+        const int64_t n4 = C * N / 4;
+        const float4* y4 = reinterpret_cast<const float4*>(y);
+        const float4* t4 = reinterpret_cast<const float4*>(t);
+        float4* g4 = reinterpret_cast<float4*>(g);
+        for (int64_t i = i0; i < n4; i += stride) {
+            const float4 a = y4[i], b = t4[i];
+            const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
+            if (g) g4[i] = make_float4(d0 * ginv, d1 * ginv, d2 * ginv, d3 * ginv);
+            acc += (double)(d0 * d0 + d1 * d1) + (double)(d2 * d2 + d3 * d3);
+        }
+    } else {
+        for (int64_t c = 0; c < C; ++c) {
+            const int64_t o = c * ld;
+            for (int64_t n = i0; n < N; n += stride) {
+                const float d = y[o + n] - t[o + n];
+                if (g) g[o + n] = d * ginv;
+                acc += (double)d * (double)d;
+            }
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
@@ -588,10 +612,13 @@ cudaError_t launch_mse(const float* y, const float* t, float* g, int64_t C, int6
                        cudaStream_t s) {
     if (cudaMemsetAsync(loss, 0, sizeof(double), s) != cudaSuccess) return cudaGetLastError();
     if (C <= 0 || N <= 0) return cudaSuccess;
+    auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+    const int flat4 = (ld == N && (C * N) % 4 == 0 && al(y) && al(t) && (!g || al(g))) ? 1 : 0;
     const int bs = 256;
-    int64_t blocks = (C * N + bs - 1) / bs;
-    if (blocks > 4096) blocks = 4096;
-    k_mse<<<(unsigned)blocks, bs, 0, s>>>(y, t, g, C, N, ld, loss);
+    const int64_t work = flat4 ? C * N / 4 : N;
+    int64_t blocks = (work + bs - 1) / bs;
+    if (blocks > 1216) blocks = 1216;  // a few CTAs per SM: few loss atomics
+    k_mse<<<(unsigned)blocks, bs, 0, s>>>(y, t, g, C, N, ld, 1.0 / ((double)C * (double)N), loss, flat4);
     return cudaGetLastError();
 }
 

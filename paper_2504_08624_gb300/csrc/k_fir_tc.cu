@@ -31,57 +31,9 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
-#include "tc_ptx.cuh"
-#include "tfx_common.cuh"
+#include "tc_common.cuh"
 
 namespace tfx {
-
-// Split 8 consecutive samples into hi / lo parts packed as 16-byte chunks:
-// BF16 hi + BF16 lo, or (after scaling by an exact power of two) FP16 hi +
-// FP16 lo.  The low part is the rounded residual v - hi, which is exact in FP32.
-__device__ __forceinline__ void split8_bf16(const float (&v)[8], uint4& hi, uint4& lo) {
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * i]);
-        const __nv_bfloat16 h1 = __float2bfloat16_rn(v[2 * i + 1]);
-        const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * i] - __bfloat162float(h0));
-        const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * i + 1] - __bfloat162float(h1));
-        h[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-        l[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-    }
-    hi = make_uint4(h[0], h[1], h[2], h[3]);
-    lo = make_uint4(l[0], l[1], l[2], l[3]);
-}
-
-__device__ __forceinline__ void split8_f16(const float (&v)[8], float scale, uint4& hi, uint4& lo) {
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float s0 = v[2 * i] * scale, s1 = v[2 * i + 1] * scale;
-        const __half h0 = __float2half_rn(s0);
-        const __half h1 = __float2half_rn(s1);
-        const __half l0 = __float2half_rn(s0 - __half2float(h0));
-        const __half l1 = __float2half_rn(s1 - __half2float(h1));
-        h[i] = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
-        l[i] = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
-    }
-    hi = make_uint4(h[0], h[1], h[2], h[3]);
-    lo = make_uint4(l[0], l[1], l[2], l[3]);
-}
-
-// 8 consecutive samples starting at t (zero outside [0, N)).
-__device__ __forceinline__ void load8(const float* xr, int64_t t, int64_t N, bool vec, float (&v)[8]) {
-    if (vec && t >= 0 && t + 8 <= N) {
-        const float4 p0 = *reinterpret_cast<const float4*>(xr + t);
-        const float4 p1 = *reinterpret_cast<const float4*>(xr + t + 4);
-        v[0] = p0.x; v[1] = p0.y; v[2] = p0.z; v[3] = p0.w;
-        v[4] = p1.x; v[5] = p1.y; v[6] = p1.z; v[7] = p1.w;
-    } else {
-#pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = (t + i >= 0 && t + i < N) ? xr[t + i] : 0.f;
-    }
-}
 
 __global__ void __launch_bounds__(256, 1) k_fir_tc(FirTcArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -247,23 +199,6 @@ constexpr int WS_THREADS = 416;
 constexpr int WS_PROD = 256;  // producer threads (warps 0-7)
 constexpr int WS_MMA_WARP = 12;
 
-__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, int* status) {
-    if (tc::mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    for (;;) {
-        if (tc::mbar_try_wait(bar, parity)) return true;
-        if (*(volatile int*)status != 0) return false;
-        if (global_ns() - t0 > WAIT_LIMIT_NS) {
-            atomicCAS(status, 0, (int)TFX_ERR_TIMEOUT);
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void named_sync(int id, int nthreads) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-
 }  // namespace
 
 __global__ void __launch_bounds__(WS_THREADS, 1) k_fir_tc_ws(FirTcArgs a) {
@@ -284,7 +219,9 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_fir_tc_ws(FirTcArgs a) {
     float* s_scale = reinterpret_cast<float*>(bars + 10);  // [4]
     float* s_red = s_scale + 4;                            // [8]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(s_red + 8);
-    int* s_ok = reinterpret_cast<int*>(tmem_slot + 1);  // producers' shared wait outcome
+    // producers' shared wait outcome, two slots so that a late reader never
+    // sees the next tile's value
+    int* s_ok = reinterpret_cast<int*>(tmem_slot + 1);
 
     if (warp == WS_MMA_WARP) {
         tc::tmem_alloc(tmem_slot, 256u);
@@ -326,9 +263,9 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_fir_tc_ws(FirTcArgs a) {
             const int st = i & 1;
             if (i >= 2) {
                 // one thread waits, a named barrier shares the outcome (uniform exit)
-                if (ptid == 0) s_ok[0] = wait_bar(&mma_done[st], ((i - 2) >> 1) & 1, a.status) ? 1 : 0;
+                if (ptid == 0) s_ok[i & 1] = wait_bar(&mma_done[st], ((i - 2) >> 1) & 1, a.status) ? 1 : 0;
                 named_sync(2, WS_PROD);
-                if (!s_ok[0]) break;
+                if (!s_ok[i & 1]) break;
             }
             const int64_t tile = blockIdx.x + (int64_t)i * gridDim.x;
             const int64_t c = tile / a.ntt;
@@ -521,7 +458,7 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_fir_tc_long(FirTcArgs a) {
     float* s_scale = reinterpret_cast<float*>(bars + 16);  // [4]
     float* s_red = s_scale + 4;                            // [8]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(s_red + 8);
-    int* s_ok = reinterpret_cast<int*>(tmem_slot + 1);
+    int* s_ok = reinterpret_cast<int*>(tmem_slot + 1);  // [2], as in k_fir_tc_ws
 
     if (warp == LG_MMA_WARP) {
         tc::tmem_alloc(tmem_slot, 256u);
@@ -556,9 +493,9 @@ __global__ void __launch_bounds__(LG_THREADS, 1) k_fir_tc_long(FirTcArgs a) {
         const int nchunks = rows * 16;
         for (int i = 0; i < nt; ++i) {
             if (i >= 1) {
-                if (ptid == 0) s_ok[0] = wait_bar(tile_done, (i - 1) & 1, a.status) ? 1 : 0;
+                if (ptid == 0) s_ok[i & 1] = wait_bar(tile_done, (i - 1) & 1, a.status) ? 1 : 0;
                 named_sync(2, LG_PROD);
-                if (!s_ok[0]) break;
+                if (!s_ok[i & 1]) break;
             }
             const int64_t tile = blockIdx.x + (int64_t)i * gridDim.x;
             const int64_t c = tile / a.ntt;

@@ -445,6 +445,10 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
             if (prepare_unit(k) != cudaSuccess) return TFX_ERR_UNSUPPORTED;
             if (p->train && u.S > 0 && prepare_sos_bwd(u.S) != cudaSuccess) return TFX_ERR_UNSUPPORTED;
         }
+        if (p->train && !(p->flags & TFX_PLAN_FIR_CUDA_CORES)) {
+            for (HostUnit& u : p->units)
+                if (u.L > 0 && prepare_fir_dh_tc() != cudaSuccess) return TFX_ERR_UNSUPPORTED;
+        }
     }
 
     // workspace layout
@@ -501,11 +505,16 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
             if (u.S > 0) {
                 const size_t tiles = (size_t)p->C * (size_t)u.ntt;
                 scan = std::max(scan, align_up(ALIGN + tiles * u.S * sizeof(Carry)));
-                part = std::max(part, align_up(tiles * u.S * 8 * sizeof(float)));
-                tmp = std::max(tmp, align_up((size_t)COLSUM_GROUPS * u.S * 8 * sizeof(double)));
+                part = std::max(part, align_up(tiles * u.S * 5 * sizeof(float)));
+                tmp = std::max(tmp, align_up((size_t)u.S * 5 * sizeof(double)));
             } else if (u.L > 0) {
-                part = std::max(part, align_up((size_t)fir_dh_rows(p->C, p->N) * u.Lp * sizeof(float)));
-                tmp = std::max(tmp, align_up((size_t)COLSUM_GROUPS * u.L * sizeof(double)));
+                size_t rows = (size_t)fir_dh_rows(p->C, p->N);
+                if (!(p->flags & TFX_PLAN_FIR_CUDA_CORES)) {
+                    int G, nwin, LW, NQ;
+                    fir_dh_tc_geometry(p->C, p->N, u.L, p->sm_count, &G, &nwin, &LW, &NQ);
+                    rows = (size_t)G;
+                }
+                part = std::max(part, align_up(rows * u.L * sizeof(float)));
             }
         }
         p->b_scan = p->scratch_bytes;
@@ -695,7 +704,7 @@ int run_backward(tfx_plan* p, const float* x, const float* g, float* dx, double*
         const HostUnit& u = p->units[i];
         const float* uin = i == 0 ? x : reinterpret_cast<const float*>(saved + u.off_act);
         const int64_t ldu = i == 0 ? p->ld : N;
-        const int nxt = cur == 0 ? 1 : 0;
+        int nxt = cur == 0 ? 1 : 0;
         if (u.S > 0) {
             BwdArgs a{};
             a.u0 = uin;
@@ -731,9 +740,8 @@ int run_backward(tfx_plan* p, const float* x, const float* g, float* dx, double*
                 return TFX_ERR_CUDA;
             TFX_LAUNCH(launch_sos_bwd(a, s));
             if (dcoef) {
-                TFX_LAUNCH(launch_colsum(part, tiles, (int64_t)u.S * 8, u.S * 8, tmp, COLSUM_GROUPS, s));
-                TFX_LAUNCH(launch_sos_grad_finalize(tmp, COLSUM_GROUPS, u.S,
-                                                    reinterpret_cast<const double*>(p->dconst + u.off_raw),
+                TFX_LAUNCH(launch_colsum(part, tiles, u.S * 5, tmp, s));
+                TFX_LAUNCH(launch_sos_grad_finalize(tmp, u.S, reinterpret_cast<const double*>(p->dconst + u.off_raw),
                                                     reinterpret_cast<const int64_t*>(p->dconst + u.off_dst), dcoef,
                                                     s));
             }
@@ -744,12 +752,30 @@ int run_backward(tfx_plan* p, const float* x, const float* g, float* dx, double*
                 cur = nxt;
             }
         } else {
+            const bool want_out = i > 0 || dx != nullptr;
             if (dcoef) {
-                TFX_LAUNCH(launch_fir_dh(gcur, ldg, grev ? 1 : 0, uin, ldu, C, N, u.L, u.Lp, part, s));
-                TFX_LAUNCH(launch_colsum(part, fir_dh_rows(C, N), u.Lp, u.L, tmp, COLSUM_GROUPS, s));
-                TFX_LAUNCH(launch_fir_grad_finalize(tmp, COLSUM_GROUPS, u.L, dcoef + u.fir_dst, s));
+                if (p->flags & TFX_PLAN_FIR_CUDA_CORES) {
+                    TFX_LAUNCH(launch_fir_dh(gcur, ldg, grev ? 1 : 0, uin, ldu, C, N, u.L, u.Lp, part, s));
+                    TFX_LAUNCH(launch_colsum(part, fir_dh_rows(C, N), u.L, dcoef + u.fir_dst, s));
+                } else {
+                    // the tap-gradient GEMM also writes the reversed gradient the
+                    // input-gradient pass needs, so no separate flip follows
+                    float* gf = (!grev && want_out) ? gbuf[nxt] : nullptr;
+                    int G, nwin, LW, NQ;
+                    fir_dh_tc_geometry(C, N, u.L, p->sm_count, &G, &nwin, &LW, &NQ);
+                    TFX_LAUNCH(launch_fir_dh_tc(gcur, ldg, grev ? 1 : 0, uin, ldu, gf, C, N, u.L, p->sm_count, part,
+                                                p->dstatus, s));
+                    TFX_LAUNCH(launch_colsum(part, G, u.L, dcoef + u.fir_dst, s));
+                    if (gf) {
+                        gcur = gbuf[nxt];
+                        ldg = N;
+                        grev = true;
+                        cur = nxt;
+                    }
+                }
             }
-            if (i == 0 && !dx) continue;
+            if (!want_out) continue;
+            nxt = cur == 0 ? 1 : 0;
             if (!grev) {
                 TFX_LAUNCH(launch_flip_rows(gcur, gbuf[nxt], C, N, ldg, N, s));
                 gcur = gbuf[nxt];

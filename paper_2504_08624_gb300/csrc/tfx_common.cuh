@@ -95,7 +95,7 @@ struct BwdArgs {
     UnitConst k;         // coef rows [S][8]: b0 c1 c2 a1 a2 d (d = a1 b2 - a2 b1)
     unsigned* ticket;
     Carry* carry;        // [tiles][S] reverse look-back carries
-    float* part;         // [tiles][S][8]: per-tile partial dL/d(b0 b1 b2 a1 a2)
+    float* part;         // [S * 5][tiles]: per-tile partial dL/d(b0 b1 b2 a1 a2), column-major
     int* status;
 };
 
@@ -251,17 +251,21 @@ cudaError_t prepare_sos_bwd(int S);
 cudaError_t launch_sos_bwd(const BwdArgs& a, cudaStream_t s);
 cudaError_t launch_flip_rows(const float* x, float* y, int64_t C, int64_t N, int64_t ldx, int64_t ldy,
                              cudaStream_t s);
-constexpr int DH_BLOCK = 2048;  // samples per warp in the FIR tap-gradient kernel
+constexpr int DH_BLOCK = 2048;  // samples per warp in the CUDA-core FIR tap-gradient kernel
 constexpr int DH_WIN = 256;     // lags per shared-memory window
 int64_t fir_dh_rows(int64_t C, int64_t N);
 cudaError_t launch_fir_dh(const float* g, int64_t ldg, int g_rev, const float* u, int64_t ldu, int64_t C,
                           int64_t N, int L, int Lp, float* part, cudaStream_t s);
-cudaError_t launch_colsum(const float* part, int64_t rows, int64_t ld, int ncol, double* tmp, int groups,
-                          cudaStream_t s);
-constexpr int COLSUM_GROUPS = 64;
-cudaError_t launch_sos_grad_finalize(const double* tmp, int groups, int S, const double* raw,
-                                     const int64_t* dst, double* dcoef, cudaStream_t s);
-cudaError_t launch_fir_grad_finalize(const double* tmp, int groups, int L, double* dcoef, cudaStream_t s);
+// Tensor-core FIR tap gradient (k_fir_dh_tc.cu): partials [L][G], G K-range CTAs.
+void fir_dh_tc_geometry(int64_t C, int64_t N, int L, int sm_count, int* G, int* nwin, int* LW, int* NQ);
+size_t fir_dh_tc_smem(int NQ);
+cudaError_t prepare_fir_dh_tc();
+cudaError_t launch_fir_dh_tc(const float* g, int64_t ldg, int g_rev, const float* u, int64_t ldu, float* gflip,
+                             int64_t C, int64_t N, int L, int sm_count, float* part, int* status, cudaStream_t s);
+// FP64 sums of column-major FP32 partials [ncol][rows] -> out[ncol]
+cudaError_t launch_colsum(const float* part, int64_t rows, int ncol, double* out, cudaStream_t s);
+cudaError_t launch_sos_grad_finalize(const double* sums, int S, const double* raw, const int64_t* dst,
+                                     double* dcoef, cudaStream_t s);
 cudaError_t launch_mse(const float* y, const float* t, float* g, int64_t C, int64_t N, int64_t ld,
                        double* loss, cudaStream_t s);
 

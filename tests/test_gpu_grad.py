@@ -25,15 +25,15 @@ pytestmark = pytest.mark.gpu
 COEF_TOL = 1e-4
 
 
-def plan_for(C, N, stages):
+def plan_for(C, N, stages, flags=0):
     from paper_2504_08624_gb300 import api, _native
-    return api.Plan(C, N, stages, flags=_native.TFX_PLAN_TRAINABLE)
+    return api.Plan(C, N, stages, flags=_native.TFX_PLAN_TRAINABLE | flags)
 
 
-def run_grad(x, g, stages, want_dx=True, want_dc=True):
+def run_grad(x, g, stages, want_dx=True, want_dc=True, flags=0):
     """(y, dx, [dcoef per stage]) from forward_train + backward on the GPU."""
     C, N = x.shape
-    p = plan_for(C, N, stages)
+    p = plan_for(C, N, stages, flags)
     xd = torch.from_numpy(x.astype(np.float32)).cuda()
     gd = torch.from_numpy(g.astype(np.float32)).cuda()
     yd = torch.empty_like(xd)
@@ -70,8 +70,8 @@ def check_coefs(got, ref, stages, tol=COEF_TOL):
     return worst
 
 
-def check_grad(x, g, stages, tol_dx=None):
-    y, dx, grads = run_grad(x, g, stages)
+def check_grad(x, g, stages, tol_dx=None, flags=0):
+    y, dx, grads = run_grad(x, g, stages, flags=flags)
     lib = oracle.load()
     assert_close(y, lib.chain(x, stages), tol_for(stages), "training forward")
     dx_ref, grads_ref = lib.chain_vjp(x, g, stages)
@@ -117,13 +117,32 @@ def test_sos_grad_long_signal():
     check_coefs(grads, gref, [("sos", rows)])
 
 
-@pytest.mark.parametrize("L", [1, 5, 17, 63, 64, 257, 1025])
+@pytest.mark.parametrize("L", [1, 5, 17, 63, 64, 257, 385, 386, 1025])
 def test_fir_grad(L):
-    # L < 64: CUDA-core FIR unit; L >= 64: tensor-core FIR over the reversed gradient
+    # input gradient: L < 64 CUDA-core FIR unit, L >= 64 tensor-core FIR over
+    # the reversed gradient; tap gradient: the tensor-core correlation GEMM
+    # (one lag window up to 385 taps, windows of 384 beyond)
     x = W.white_gauss(2, 6000, 11)
     g = W.white_gauss(2, 6000, 12)
     h = np.random.default_rng(L).normal(0.0, 1.0 / np.sqrt(L), L)
     check_grad(x, g, [("fir", h)])
+
+
+@pytest.mark.parametrize("L", [5, 257, 700])
+def test_fir_grad_cuda_cores(L):
+    from paper_2504_08624_gb300 import _native
+    x = W.white_gauss(3, 5000, 24)
+    g = W.white_gauss(3, 5000, 25)
+    h = np.random.default_rng(L + 1).normal(0.0, 1.0 / np.sqrt(L), L)
+    check_grad(x, g, [("sos", W.random_stable_sos(2, 9, 0.5, 0.95)), ("fir", h)],
+               flags=_native.TFX_PLAN_FIR_CUDA_CORES)
+
+
+def test_fir_grad_channel_straddling_blocks():
+    # N not a multiple of 128: 16-block K-steps of the tap-gradient GEMM span channels
+    x = W.white_gauss(5, 1000, 26)
+    g = W.white_gauss(5, 1000, 27)
+    check_grad(x, g, [("fir", np.random.default_rng(3).normal(0, 0.1, 129))])
 
 
 @pytest.mark.parametrize("name", ["sos_fir", "fir_sos", "sos_sos", "fir_fir", "empty_sos", "sos_fir_sos"])
@@ -213,9 +232,10 @@ def test_grad_argument_errors():
 def test_launch_counts():
     stages = [("sos", W.random_stable_sos(6, 5, 0.5, 0.95)), ("fir", np.hanning(257))]
     p = plan_for(4, 5000, stages)
-    # cascade: adjoint scan + column sums + finalize; FIR: tap correlation +
-    # column sums + finalize + flip of g + FIR over the reversed gradient
-    assert p.backward_launches(True, True) == 3 + 5
+    # cascade: adjoint scan + column sums + finalize; FIR: tap-gradient GEMM
+    # (which also writes the reversed gradient) + column sums + FIR over the
+    # reversed gradient; without coefficient gradients the FIR needs a flip
+    assert p.backward_launches(True, True) == 3 + 3
     assert p.backward_launches(True, False) == 1 + 2
     assert p.launches_per_execute == 2
     p.close()
