@@ -360,3 +360,29 @@ class FilterChain(torch.nn.Module):
 
     def forward(self, x: torch.Tensor) -> torch.Tensor:
         return ChainFunction.apply(x, self.kinds, *self.coefs)
+
+
+class LearnableBiquadChain(torch.nn.Module):
+    """The differentiable chain: a cascade of biquads whose poles are
+    parameterised by radius r = rmin + rspan sigmoid(rho) and angle
+    theta = pi sigmoid(phi) (stable for any parameter values), with free
+    numerators, followed by a learnable FIR.  The SOS rows are built with torch
+    ops, so autograd carries the chain rule from dL/d(rows) to rho and phi."""
+
+    def __init__(self, rho, phi, b, h, rmin: float = 0.5, rspan: float = 0.49):
+        super().__init__()
+        f64 = dict(dtype=torch.float64)
+        self.rho = torch.nn.Parameter(torch.as_tensor(rho, **f64).clone())
+        self.phi = torch.nn.Parameter(torch.as_tensor(phi, **f64).clone())
+        self.b = torch.nn.Parameter(torch.as_tensor(b, **f64).reshape(-1, 3).clone())
+        self.h = torch.nn.Parameter(torch.as_tensor(h, **f64).clone())
+        self.rmin, self.rspan = rmin, rspan
+
+    def rows(self) -> torch.Tensor:
+        r = self.rmin + self.rspan * torch.sigmoid(self.rho)
+        th = torch.pi * torch.sigmoid(self.phi)
+        ones = torch.ones_like(r)
+        return torch.cat([self.b, torch.stack([ones, -2.0 * r * torch.cos(th), r * r], 1)], 1)
+
+    def forward(self, x: torch.Tensor) -> torch.Tensor:
+        return ChainFunction.apply(x, ("sos", "fir"), self.rows(), self.h)

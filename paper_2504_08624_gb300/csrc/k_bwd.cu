@@ -14,7 +14,9 @@
 // geometry of the training forward (32 lanes x 32 samples per tile):
 //   1. each lane recomputes every section's output over its chunk from the
 //      chunk-start states the forward stored (block-boundary checkpoints),
-//      keeping them in shared memory as a stack;
+//      keeping the upper half of them in shared memory; when the reverse
+//      sweep reaches the lower half, those are recomputed into the freed
+//      slots (S/2 + 1 slots instead of S + 1, for occupancy);
 //   2. per section, last to first: a zero-state reverse pass over the chunk
 //      gives lambda and dL/du with zero state beyond the chunk; the chunk
 //      states (lambda[n0], lambda[n0+1]) are combined by a reverse
@@ -180,13 +182,23 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// Shared-memory slots per warp for the section outputs u_0 (cascade input) ..
+// u_S.  Only u_{S1} .. u_S (S1 = S / 2) are kept at first; once the upper
+// sections are done, u_0 .. u_{S1-1} are recomputed into the freed slots.
+__host__ __device__ constexpr int bwd_slots(int S) {
+    return (S - S / 2 + 1) > (S / 2 + 1) ? (S - S / 2 + 1) : (S / 2 + 1);
+}
+
 template <int T>
-__global__ void __launch_bounds__(32 * BWD_WPB) k_sos_bwd(BwdArgs a) {
+__global__ void __launch_bounds__(32 * BWD_WPB, 8) k_sos_bwd(BwdArgs a) {
     extern __shared__ float4 bwd_smem4[];
     const int lane = threadIdx.x & 31;
     const int S = a.k.S;
-    // per-warp stack: [S + 1][T][32 lanes]; slot 0 = cascade input, slot s + 1 = output of section s
-    float* stk = reinterpret_cast<float*>(bwd_smem4) + (size_t)(threadIdx.x >> 5) * (S + 1) * T * 32 + lane;
+    const int S1 = S / 2;
+    const int NS = bwd_slots(S);
+    // per-warp slots [NS][T][32 lanes]: upper phase u_k in slot k - S1 (k >= S1);
+    // lower phase u_k in slot k + 1 (k < S1), u_{S1} staying in slot 0
+    float* stk = reinterpret_cast<float*>(bwd_smem4) + (size_t)(threadIdx.x >> 5) * NS * T * 32 + lane;
 
     unsigned tk = 0;
     if (lane == 0) tk = atomicAdd(a.ticket, 1u);
@@ -199,12 +211,15 @@ __global__ void __launch_bounds__(32 * BWD_WPB) k_sos_bwd(BwdArgs a) {
     const int64_t chunk = tt * 32 + lane;
     const int64_t n0 = chunk * T;
 
-    // 1. recompute the section outputs of this chunk from the stored chunk-start states
+    // 1. recompute the section outputs of this chunk from the stored chunk-start
+    //    states, keeping u_{S1} .. u_S
     {
         float r[T];
         bwd_load<T>(a.u0 + c * a.ldu, n0, a.N, false, r);
+        if (S1 == 0) {
 #pragma unroll
-        for (int t = 0; t < T; ++t) stk[t * 32] = r[t];
+            for (int t = 0; t < T; ++t) stk[t * 32] = r[t];
+        }
         for (int s = 0; s < S; ++s) {
             float2 st = make_float2(0.f, 0.f);
             if (chunk < a.nch) st = a.ckpt[(c * S + s) * a.nch + chunk];
@@ -219,9 +234,11 @@ __global__ void __launch_bounds__(32 * BWD_WPB) k_sos_bwd(BwdArgs a) {
                 w2 = fmaf(c2, v, -a2 * w1);
                 w1 = n1;
             }
-            float* o = stk + (size_t)(s + 1) * T * 32;
+            if (s + 1 >= S1) {
+                float* o = stk + (size_t)(s + 1 - S1) * T * 32;
 #pragma unroll
-            for (int t = 0; t < T; ++t) o[t * 32] = r[t];
+                for (int t = 0; t < T; ++t) o[t * 32] = r[t];
+            }
         }
     }
 
@@ -239,8 +256,47 @@ __global__ void __launch_bounds__(32 * BWD_WPB) k_sos_bwd(BwdArgs a) {
             const float* cf = a.k.coef + 8 * sr;
             r = RunSec{cf[0], cf[1], cf[2], cf[3], cf[4]};
         }
-        const float* xi = stk + (size_t)(sf < S ? sf : 0) * T * 32;
-        const float* xo = xi + (size_t)T * 32;
+        if (sf == S1 - 1) {
+            // lower phase: u_0 .. u_{S1-1} into slots 1 .. S1 (the upper sections'
+            // slots are free now), streaming through shared memory
+            float* d0 = stk + (size_t)T * 32;
+            const float* row = a.u0 + c * a.ldu;
+            if (n0 + T <= a.N && ((reinterpret_cast<uintptr_t>(row + n0) & 15) == 0)) {
+                const float4* p4 = reinterpret_cast<const float4*>(row + n0);
+#pragma unroll
+                for (int q = 0; q < T / 4; ++q) {
+                    const float4 w = p4[q];
+                    d0[(4 * q) * 32] = w.x;
+                    d0[(4 * q + 1) * 32] = w.y;
+                    d0[(4 * q + 2) * 32] = w.z;
+                    d0[(4 * q + 3) * 32] = w.w;
+                }
+            } else {
+#pragma unroll
+                for (int t = 0; t < T; ++t) d0[t * 32] = (n0 + t < a.N) ? row[n0 + t] : 0.f;
+            }
+            for (int k = 1; k < S1; ++k) {
+                float2 st0 = make_float2(0.f, 0.f);
+                if (chunk < a.nch) st0 = a.ckpt[(c * S + (k - 1)) * a.nch + chunk];
+                const float* cf = a.k.coef + 8 * (k - 1);
+                const float b0 = cf[0], c1 = cf[1], c2 = cf[2], a1 = cf[3], a2 = cf[4];
+                const float* src = stk + (size_t)k * T * 32;
+                float* dst = stk + (size_t)(k + 1) * T * 32;
+                float w1 = st0.x, w2 = st0.y;
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                    const float v = src[t * 32];
+                    dst[t * 32] = fmaf(b0, v, w1);
+                    const float n1 = fmaf(c1, v, fmaf(-a1, w1, w2));
+                    w2 = fmaf(c2, v, -a2 * w1);
+                    w1 = n1;
+                }
+            }
+        }
+        // slots holding the fixed section's input u_sf and output u_{sf+1}
+        const int sfx = sf < S ? sf : S1;
+        const float* xi = stk + (size_t)(sfx >= S1 ? sfx - S1 : sfx + 1) * T * 32;
+        const float* xo = stk + (size_t)(sfx + 1 >= S1 ? (sfx + 1 == S1 ? 0 : sfx + 1 - S1) : sfx + 2) * T * 32;
         Partials pt{0.f, 0.f, 0.f, 0.f, 0.f};
         float2 e;
         if (it == 0) e = bwd_pass<T, false, true>(gr, lam, xi, xo, f, r, pt);
@@ -351,7 +407,7 @@ __global__ void __launch_bounds__(32 * BWD_WPB) k_sos_bwd(BwdArgs a) {
     if (a.gout) bwd_store<T>(a.gout + c * a.ldo, n0, a.N, a.out_rev != 0, gr);
 }
 
-size_t sos_bwd_smem_bytes(int S) { return (size_t)BWD_WPB * (S + 1) * T_CHUNK * 32 * sizeof(float); }
+size_t sos_bwd_smem_bytes(int S) { return (size_t)BWD_WPB * bwd_slots(S) * T_CHUNK * 32 * sizeof(float); }
 
 cudaError_t prepare_sos_bwd(int S) {
     if (S < 1 || S > BWD_SMAX) return cudaErrorInvalidValue;

@@ -14,11 +14,15 @@
 // diagonal reduction of its 128 x NQ result.
 //
 // One CTA per (K range, lag window); 416 threads:
-//   warps 0-7   producers: for each K-step (16 blocks) gather A (128 x 16) and
-//               B (NQ x 16) from global memory, split each value into BF16
-//               hi + lo, store both in the canonical K-major no-swizzle layout
-//               of a 4-stage ring; they also write the time-reversed g, which
-//               the FIR's input-gradient pass consumes, when asked to
+//   warps 0-7   producers: stage each K-step's raw FP32 data (16 blocks of g
+//               and the u samples its B rows span, both contiguous) into a
+//               5-slot shared ring with cp.async four K-steps ahead, then
+//               gather A (128 x 16) and B (NQ x 16) from it, split each value
+//               into BF16 hi + lo, and store both in the canonical K-major
+//               no-swizzle layout of a 3-stage operand ring; K-steps at
+//               channel ends or signal edges read global memory directly.
+//               They also write the time-reversed g, which the FIR's
+//               input-gradient pass consumes, when asked to
 //   warps 8-11  epilogue: after the last K-step, each thread reads its TMEM
 //               lane j (one row of X), 16 columns at a time, into a shared
 //               tile; one thread per lag then sums that lag's anti-diagonal
@@ -37,13 +41,26 @@ namespace {
 constexpr int DT_THREADS = 416;
 constexpr int DT_PROD = 256;
 constexpr int DT_MMA_WARP = 12;
-constexpr int DT_STAGES = 4;
+constexpr int DT_STAGES = 3;
 constexpr int DT_LW_MAX = 385;  // one window covers up to this many lags (NQ <= 512)
 constexpr int DT_DH_WORDS = 512;
 constexpr uint32_t DT_A_BYTES = 2 * 128 * 16;  // one part (hi or lo) of A: 2 K-chunks x 128 rows x 16 B
 
 __host__ __device__ inline uint32_t dt_b_bytes(int NQ) { return 2u * (uint32_t)NQ * 16u; }
 __host__ __device__ inline uint32_t dt_stage_bytes(int NQ) { return 2 * DT_A_BYTES + 2 * dt_b_bytes(NQ); }
+// one raw staging slot: 2048 samples of g and 2048 + NQ - 128 of u, FP32
+__host__ __device__ inline uint32_t dt_raw_bytes(int NQ) { return (uint32_t)(2048 + 2048 + NQ - 128) * 4u; }
+
+constexpr int DT_RAW = 5;  // raw staging slots: four K-steps ahead
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 struct ChunkMap {
     bool valid, isA;
@@ -76,9 +93,9 @@ __global__ void __launch_bounds__(DT_THREADS, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t STAGE = dt_stage_bytes(NQ);
     const uint32_t BB = dt_b_bytes(NQ);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)DT_STAGES * STAGE);
-    uint64_t* full = bars;              // [4] producers -> MMA
-    uint64_t* empty = bars + 4;         // [4] MMA -> producers
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)DT_STAGES * STAGE + (size_t)DT_RAW * dt_raw_bytes(NQ));
+    uint64_t* full = bars;              // [DT_STAGES <= 4] producers -> MMA
+    uint64_t* empty = bars + 4;         // [DT_STAGES <= 4] MMA -> producers
     uint64_t* done = bars + 8;          // [1] MMA -> epilogue
     float* dh_s = reinterpret_cast<float*>(bars + 9);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(dh_s + DT_DH_WORDS);
@@ -132,27 +149,78 @@ __global__ void __launch_bounds__(DT_THREADS, 1)
             maps[k] = cm;
         }
         static_assert(MAXC <= 2 * U, "chunk map too small");
-        for (int i = 0; i < nk; ++i) {
-            const int st = i % DT_STAGES;
-            if (i >= DT_STAGES) {
-                // one thread waits, a named barrier shares the outcome (uniform exit);
-                // two slots, so a late reader never sees the next iteration's value
-                if (tid == 0) s_ok[i & 1] = wait_bar(&empty[st], ((i - DT_STAGES) / DT_STAGES) & 1, status) ? 1 : 0;
-                named_sync(1, DT_PROD);
-                if (!s_ok[i & 1]) break;
+        // raw FP32 staging ring, DT_RAW - 1 K-steps ahead (cp.async)
+        static_assert(DT_STAGES <= 4, "barrier slots");
+        const int BRAW = 2048 + NQ - 128;  // u samples one K-step's B rows span
+        const int RAWF = 2048 + BRAW;
+        float* raw = reinterpret_cast<float*>(smem + (size_t)DT_STAGES * STAGE);
+        const bool base_al = ((reinterpret_cast<uintptr_t>(g) | reinterpret_cast<uintptr_t>(u)) & 15) == 0;
+        // (channel, block) cursors advanced 16 blocks per K-step (no division in
+        // the loop): one for the K-step being converted, one for the prefetch
+        struct Cursor {
+            int64_t c, rq;
+        };
+        auto advance = [&](Cursor& cu, int64_t nb) {
+            cu.rq += nb;
+            while (cu.rq >= R) {
+                cu.rq -= R;
+                ++cu.c;
             }
+        };
+        Cursor cur{(ks0 * 16) / R, (ks0 * 16) % R};
+        Cursor pfc = cur;
+        // A K-step is staged when its 16 blocks lie in one channel and both raw
+        // ranges (2048 samples of g, BRAW of u) are inside the signal and
+        // 16-byte aligned; other K-steps (channel ends, signal edges) load directly.
+        auto staged = [&](int64_t rb, const Cursor& cu, int64_t& aoff, int64_t& boff) -> bool {
+            if (!base_al || rb + 16 > nblk) return false;
+            const int64_t a0 = 128 * cu.rq, m0 = a0 + 128 - NQ - k0;
+            if (cu.rq + 16 > R || a0 + 2048 > N || m0 < 0 || m0 + BRAW > N) return false;
+            aoff = g_rev ? cu.c * ldg + (N - 2048 - a0) : cu.c * ldg + a0;
+            boff = cu.c * ldu + m0;
+            return ((aoff | boff) & 3) == 0;
+        };
+        auto prefetch = [&](int i) {
+            int64_t aoff, boff;
+            if (i < nk && staged((ks0 + i) * 16, pfc, aoff, boff)) {
+                float* dst = raw + (size_t)(i % DT_RAW) * RAWF;
+                for (int q = tid; q < 512; q += DT_PROD) cp_async16(dst + 4 * q, g + aoff + 4 * q);
+                for (int q = tid; q < BRAW / 4; q += DT_PROD) cp_async16(dst + 2048 + 4 * q, u + boff + 4 * q);
+            }
+            cp_async_commit();  // one group per K-step, empty or not
+            advance(pfc, 16);
+        };
+        for (int i = 0; i < DT_RAW - 1; ++i) prefetch(i);
+        for (int i = 0; i < nk; ++i, advance(cur, 16)) {
+            const int st = i % DT_STAGES;
+            // everyone is done with K-step i-1 (whose raw slot the prefetch below
+            // refills) and, once the ring is full, the MMA has released stage st;
+            // one thread waits and a named barrier shares the outcome (two slots,
+            // so a late reader never sees the next iteration's value)
+            if (tid == 0)
+                s_ok[i & 1] = (i < DT_STAGES || wait_bar(&empty[st], ((i - DT_STAGES) / DT_STAGES) & 1, status)) ? 1 : 0;
+            named_sync(1, DT_PROD);
+            if (!s_ok[i & 1]) break;
+            prefetch(i + DT_RAW - 1);
+            cp_async_wait<DT_RAW - 1>();  // this thread's copies for K-step i have landed
+            named_sync(1, DT_PROD);      // and everyone else's
             const int64_t rb0 = (ks0 + i) * 16;  // first block of this K-step
+            int64_t aoff_i, boff_i;
+            const bool stg = staged(rb0, cur, aoff_i, boff_i);
+            const float* rawA = raw + (size_t)(i % DT_RAW) * RAWF;
+            const float* rawB = rawA + 2048;
             uint8_t* Ah = smem + (size_t)st * STAGE;
             uint8_t* Al = Ah + DT_A_BYTES;
             uint8_t* Bh = Al + DT_A_BYTES;
             uint8_t* Bl = Bh + BB;
             // (channel, block) of the first block of each K-chunk of 8 blocks, and
             // whether all 8 blocks lie in that channel
-            const int64_t cb0 = rb0 / R, rq0 = rb0 % R;
-            const int64_t cb1 = (rb0 + 8) / R, rq1 = (rb0 + 8) % R;
+            const int64_t cb0 = cur.c, rq0 = cur.rq;
+            Cursor c8 = cur;
+            advance(c8, 8);
+            const int64_t cb1 = c8.c, rq1 = c8.rq;
             const bool one0 = rb0 + 8 <= nblk && rq0 + 8 <= R;
             const bool one1 = rb0 + 16 <= nblk && rq1 + 8 <= R;
-            // U chunks per thread in flight: all loads first, then split + store
 #pragma unroll
             for (int it = 0; it < 2; ++it) {  // at most 1280 chunks: two passes of U x 256
                 const int ch0 = tid + it * U * DT_PROD;
@@ -160,10 +228,24 @@ __global__ void __launch_bounds__(DT_THREADS, 1)
                 float v[U][8];
 #pragma unroll
                 for (int uu = 0; uu < U; ++uu) {
-                    const int ch = ch0 + uu * DT_PROD;
                     const ChunkMap cm = maps[it * U + uu];
                     if (!cm.valid) continue;
                     const int kc = cm.kc;
+                    if (stg) {  // from the staged raw data
+                        if (cm.isA) {
+                            if (g_rev) {
+#pragma unroll
+                                for (int e = 0; e < 8; ++e) v[uu][e] = rawA[2047 - 128 * (8 * kc + e) - cm.row];
+                            } else {
+#pragma unroll
+                                for (int e = 0; e < 8; ++e) v[uu][e] = rawA[128 * (8 * kc + e) + cm.row];
+                            }
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) v[uu][e] = rawB[128 * (8 * kc + e) + NQ - 1 - cm.row];
+                        }
+                        continue;
+                    }
                     const int64_t c0 = kc ? cb1 : cb0, r0 = kc ? rq1 : rq0;
                     const bool onek = kc ? one1 : one0;
                     if (cm.isA) {
@@ -209,7 +291,6 @@ __global__ void __launch_bounds__(DT_THREADS, 1)
                             ++c;
                         }
                     }
-                    (void)ch;
                 }
 #pragma unroll
                 for (int uu = 0; uu < U; ++uu) {
@@ -219,7 +300,11 @@ __global__ void __launch_bounds__(DT_THREADS, 1)
                     split8_bf16x2(v[uu], hi, lo);
                     *reinterpret_cast<uint4*>((cm.isA ? Ah : Bh) + cm.off) = hi;
                     *reinterpret_cast<uint4*>((cm.isA ? Al : Bl) + cm.off) = lo;
-                    if (cm.isA && gf) {  // the reversed gradient, for the FIR's input-gradient pass
+                    if (cm.isA && gf && stg) {  // the reversed gradient, for the FIR's input-gradient pass
+                        float* gb = gf + cur.c * N + (N - 1 - 128 * cur.rq - cm.row - 1024 * cm.kc);
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) gb[-128 * e] = v[uu][e];
+                    } else if (cm.isA && gf) {
                         const int kc = cm.kc;
                         int64_t c = kc ? cb1 : cb0, rp = kc ? rq1 : rq0;
                         const int64_t rb = rb0 + 8 * kc;
@@ -238,6 +323,7 @@ __global__ void __launch_bounds__(DT_THREADS, 1)
             tc::fence_proxy_async_smem();
             tc::mbar_arrive(&full[st]);
         }
+        cp_async_wait<0>();  // no copy left in flight
     } else if (warp < DT_MMA_WARP) {
         // ---------------- epilogue ----------------
         // X is read 16 columns at a time into a shared tile (the stage ring is
@@ -333,7 +419,8 @@ void fir_dh_tc_geometry(int64_t C, int64_t N, int L, int sm_count, int* G, int* 
 
 // At least 120 KB, so that one CTA (and its up to 512 TMEM columns) holds an SM.
 size_t fir_dh_tc_smem(int NQ) {
-    const size_t need = (size_t)DT_STAGES * dt_stage_bytes(NQ) + 9 * sizeof(uint64_t) + DT_DH_WORDS * sizeof(float) + 16;
+    const size_t need = (size_t)DT_STAGES * dt_stage_bytes(NQ) + (size_t)DT_RAW * dt_raw_bytes(NQ) + 9 * sizeof(uint64_t) +
+                        DT_DH_WORDS * sizeof(float) + 16;
     return need > 120 * 1024 ? need : 120 * 1024;
 }
 

@@ -339,15 +339,52 @@ def long_fir() -> Workload:
                     1e-5, "gauss", 3)
 
 
-def differentiable_chain_forward() -> Workload:
-    """256 x 65,536 N(0,1), seed 4: 6 random stable biquads (radius
-    0.5-0.99) and a 257-tap FIR (unit impulse plus N(0, 1e-3) noise)."""
-    rng = np.random.default_rng(40)
-    h = rng.normal(0.0, 1e-3, 257)
+def biquad_rows(rho, phi, b, rmin: float = 0.5, rspan: float = 0.49) -> np.ndarray:
+    """SOS rows of the learnable cascade: pole radius r = rmin + rspan sigmoid(rho)
+    (so r stays in (0.5, 0.99)), pole angle theta = pi sigmoid(phi), a = [1,
+    -2 r cos theta, r^2]; the numerators b [n x 3] are free."""
+    rho, phi, b = np.asarray(rho, float), np.asarray(phi, float), np.asarray(b, float).reshape(-1, 3)
+    r = rmin + rspan / (1.0 + np.exp(-rho))
+    th = math.pi / (1.0 + np.exp(-phi))
+    return np.column_stack([b, np.ones_like(r), -2.0 * r * np.cos(th), r * r])
+
+
+def differentiable_chain_params(seed: int, n: int = 6, taps: int = 257) -> dict:
+    """Parameters of the differentiable chain: n biquads (rho, phi ~ N(0, 1.5),
+    numerators from random zeros scaled to max |H| = 1 at the initial poles)
+    and a taps-long FIR initialised to a unit impulse plus N(0, 1e-3) noise."""
+    rng = np.random.default_rng(seed)
+    rho = rng.normal(0.0, 1.5, n)
+    phi = rng.normal(0.0, 1.5, n)
+    a = biquad_rows(rho, phi, np.ones((n, 3)))[:, 3:]
+    w = np.linspace(0.0, math.pi, 4096)
+    zinv = np.exp(-1j * w)
+    b = np.empty((n, 3))
+    for i in range(n):
+        rz, tz = rng.uniform(0.0, 1.2), rng.uniform(0.0, math.pi)
+        bi = np.array([1.0, -2.0 * rz * math.cos(tz), rz * rz])
+        H = (bi[0] + bi[1] * zinv + bi[2] * zinv ** 2) / (a[i, 0] + a[i, 1] * zinv + a[i, 2] * zinv ** 2)
+        b[i] = bi / float(np.max(np.abs(H)))
+    h = rng.normal(0.0, 1e-3, taps)
     h[0] += 1.0
+    return {"rho": rho, "phi": phi, "b": b, "h": h}
+
+
+def differentiable_chain_forward() -> Workload:
+    """256 x 65,536 N(0,1), seed 4: the learnable chain at its initial
+    parameters (seed 41): 6 biquads with poles parameterised by radius in
+    (0.5, 0.99) and angle, free numerators, then a 257-tap FIR (unit impulse
+    plus N(0, 1e-3) noise).  Trained with the MSE to ``differentiable_chain_target``."""
+    p = differentiable_chain_params(41)
     return Workload("differentiable_chain_256x65536", 256, 65536,
-                    [("sos", random_stable_sos(6, 41, 0.5, 0.99)), ("fir", h)],
-                    1e-4, "gauss", 4)
+                    [("sos", biquad_rows(p["rho"], p["phi"], p["b"])), ("fir", p["h"])],
+                    1e-4, "gauss", 4, meta={"params": p})
+
+
+def differentiable_chain_target() -> list:
+    """The target chain: the same architecture with parameters from seed 141."""
+    p = differentiable_chain_params(141)
+    return [("sos", biquad_rows(p["rho"], p["phi"], p["b"])), ("fir", p["h"])]
 
 
 def table4_chain() -> Workload:

@@ -334,3 +334,32 @@ def test_differentiable_chain_full_size():
         assert np.max(np.abs(got - ref)) <= 1e-4 * scale, (c, got, ref)
     ys = lib.chain(x[:2], w.stages)
     assert_close(y[:2], ys, 1e-4, "training forward")
+
+
+def test_learnable_biquad_chain_parameter_grads():
+    """Gradients w.r.t. the pole radius / angle parameters, numerators and FIR
+    taps (autograd's chain rule on top of the adjoint kernels) against central
+    differences of the FP64 oracle forward in those parameters."""
+    from paper_2504_08624_gb300 import api
+    p = W.differentiable_chain_params(41, n=3, taps=17)
+    x = W.white_gauss(2, 3000, 30)
+    g = W.white_gauss(2, 3000, 31)
+    m = api.LearnableBiquadChain(p["rho"], p["phi"], p["b"], p["h"])
+    y = m(torch.from_numpy(x.astype(np.float32)).cuda())
+    y.backward(torch.from_numpy(g.astype(np.float32)).cuda())
+    lib = oracle.load()
+
+    def loss(pp):
+        st = [("sos", W.biquad_rows(pp["rho"], pp["phi"], pp["b"])), ("fir", pp["h"])]
+        return float(np.sum(g * lib.chain(x, st)))
+
+    grads = {"rho": m.rho.grad.numpy(), "phi": m.phi.grad.numpy(), "b": m.b.grad.numpy(), "h": m.h.grad.numpy()}
+    eps = 1e-6
+    for name, idx in [("rho", 0), ("rho", 2), ("phi", 1), ("phi", 2), ("b", (1, 2)), ("b", (0, 0)), ("h", 3)]:
+        pp = {k: np.array(v, dtype=np.float64) for k, v in p.items()}
+        pm = {k: np.array(v, dtype=np.float64) for k, v in p.items()}
+        pp[name][idx] += eps
+        pm[name][idx] -= eps
+        fd = (loss(pp) - loss(pm)) / (2 * eps)
+        scale = np.max(np.abs(grads[name]))
+        assert abs(grads[name][idx] - fd) <= 1e-4 * scale, (name, idx, grads[name][idx], fd)
