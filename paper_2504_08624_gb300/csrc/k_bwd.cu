@@ -631,7 +631,9 @@ __global__ void k_mse(const float* __restrict__ y, const float* __restrict__ t, 
     const float ginv = (float)(2.0 * inv);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double acc = 0.0;
+    // per-thread sums in FP32 (a few dozen terms each; FP64 arithmetic is slow
+    // on this part), combined in FP64 across threads and CTAs
+    float accf = 0.f;
     if (flat4) {  // dense rows (ld == N), 16-byte aligned, C N a multiple of 4
         const int64_t n4 = C * N / 4;
         const float4* y4 = reinterpret_cast<const float4*>(y);
@@ -641,7 +643,7 @@ __global__ void k_mse(const float* __restrict__ y, const float* __restrict__ t, 
             const float4 a = y4[i], b = t4[i];
             const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
             if (g) g4[i] = make_float4(d0 * ginv, d1 * ginv, d2 * ginv, d3 * ginv);
-            acc += (double)(d0 * d0 + d1 * d1) + (double)(d2 * d2 + d3 * d3);
+            accf = fmaf(d0, d0, fmaf(d1, d1, fmaf(d2, d2, fmaf(d3, d3, accf))));
         }
     } else {
         for (int64_t c = 0; c < C; ++c) {
@@ -649,10 +651,11 @@ __global__ void k_mse(const float* __restrict__ y, const float* __restrict__ t, 
             for (int64_t n = i0; n < N; n += stride) {
                 const float d = y[o + n] - t[o + n];
                 if (g) g[o + n] = d * ginv;
-                acc += (double)d * (double)d;
+                accf = fmaf(d, d, accf);
             }
         }
     }
+    double acc = (double)accf;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;

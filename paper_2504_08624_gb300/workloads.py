@@ -165,6 +165,26 @@ def peaking_sos(f0: float, Q: float, gain_db: float, fs: float) -> np.ndarray:
     return np.array([[b[0] / a[0], b[1] / a[0], b[2] / a[0], 1.0, a[1] / a[0], a[2] / a[0]]])
 
 
+def shelving_sos(kind: str, f0: float, gain_db: float, fs: float, slope: float = 1.0) -> np.ndarray:
+    """RBJ low/high shelving biquad (shelf slope S), normalised (a0 = 1).  The
+    low shelf has gain 10^(G/20) at DC and 1 at Nyquist, the high shelf the
+    reverse; both pass 10^(G/40) at f0."""
+    A = 10.0 ** (gain_db / 40.0)
+    w0 = 2.0 * math.pi * f0 / fs
+    cw = math.cos(w0)
+    alpha = math.sin(w0) / 2.0 * math.sqrt((A + 1.0 / A) * (1.0 / slope - 1.0) + 2.0)
+    q = 2.0 * math.sqrt(A) * alpha
+    if kind == "low":
+        b = [A * ((A + 1) - (A - 1) * cw + q), 2 * A * ((A - 1) - (A + 1) * cw), A * ((A + 1) - (A - 1) * cw - q)]
+        a = [(A + 1) + (A - 1) * cw + q, -2 * ((A - 1) + (A + 1) * cw), (A + 1) + (A - 1) * cw - q]
+    elif kind == "high":
+        b = [A * ((A + 1) + (A - 1) * cw + q), -2 * A * ((A - 1) + (A + 1) * cw), A * ((A + 1) + (A - 1) * cw - q)]
+        a = [(A + 1) - (A - 1) * cw + q, 2 * ((A - 1) - (A + 1) * cw), (A + 1) - (A - 1) * cw - q]
+    else:
+        raise ValueError("kind must be 'low' or 'high'")
+    return np.array([[b[0] / a[0], b[1] / a[0], b[2] / a[0], 1.0, a[1] / a[0], a[2] / a[0]]])
+
+
 def random_peaking_bank(n: int, fs: float, seed: int) -> np.ndarray:
     """n peaking biquads: f0 log-uniform [100 Hz, 10 kHz], Q log-uniform
     [0.5, 4], gain uniform [-12, 12] dB."""

@@ -124,3 +124,21 @@ def test_signals_are_seeded_and_shaped():
     assert 0.5 < hi / lo < 2.0
     u = W.white_uniform(3, 1000, 0)
     assert u.dtype == np.float32 and u.min() >= -1 and u.max() <= 1
+
+
+@pytest.mark.parametrize("kind", ["low", "high"])
+@pytest.mark.parametrize("gain", [-9.0, 6.0])
+def test_shelving(kind, gain):
+    """Shelf gain 10^(G/20) at the shelf end (DC for low, Nyquist for high), 1 at
+    the other end, 10^(G/40) at f0."""
+    fs, f0 = 48000.0, 2000.0
+    rows = W.shelving_sos(kind, f0, gain, fs)
+    def H(w):
+        z = np.exp(-1j * w)
+        r = rows[0]
+        return (r[0] + r[1] * z + r[2] * z * z) / (r[3] + r[4] * z + r[5] * z * z)
+    g = 10.0 ** (gain / 20.0)
+    lo, hi = (g, 1.0) if kind == "low" else (1.0, g)
+    assert abs(abs(H(0.0)) - lo) < 1e-12
+    assert abs(abs(H(np.pi)) - hi) < 1e-12
+    assert abs(abs(H(2 * np.pi * f0 / fs)) - 10.0 ** (gain / 40.0)) < 1e-12
