@@ -285,6 +285,65 @@ void tfx_cache_clear(void);
 int tfx_sos_noalloc(const float *x, float *y, int64_t C, int64_t N, int64_t ld,
                     const double *sos, int32_t sections, tfx_stream s);
 
+/*
+ * Batched launch over many clips (Sec. 4: many channels and files at once).
+ * Each clip has its own channel count C, length N and chain; the clips are
+ * PACKED into one device input and one device output buffer: clip i occupies
+ * floats [off_i, off_i + C_i N_i) (row stride N_i), off_i =
+ * tfx_batch_clip_offset(b, i), and tfx_batch_total_samples(b) floats in all.
+ *
+ * tfx_batch_create -- validate and plan every clip (host FP64 precompute, as
+ * tfx_plan_create) and group the units of all clips by position in their
+ * chain and by kernel (fused cascade + short FIR / cascade / tensor-core FIR
+ * with NB output blocks per tile); each group then runs as ONE launch over
+ * the tiles of all its units.  Allocates device memory (host-synchronous).
+ * params may be NULL (defaults).  Clips whose tensor-core FIR tables do not
+ * fit in shared memory beside a window are TFX_ERR_UNSUPPORTED.
+ * tfx_batch_execute -- y = chain_i(x) for every clip; x and y must not
+ * overlap; ws >= tfx_batch_workspace_size bytes, 256-byte aligned.  No
+ * allocation and no host synchronisation: capturable in a CUDA graph (the
+ * whole batch as one graph launch).  tfx_batch_launch_count kernels.
+ * Errors: TFX_ERR_INVALID, TFX_ERR_UNSTABLE, TFX_ERR_WORKSPACE,
+ * TFX_ERR_UNSUPPORTED, TFX_ERR_NOMEM, TFX_ERR_CUDA; device-side timeouts via
+ * tfx_batch_get_error (synchronising, like tfx_plan_get_error).
+ */
+typedef struct {
+    int64_t C;             /* channels (>= 0) */
+    int64_t N;             /* samples per channel (>= 0) */
+    const tfx_stage *st;   /* the clip's chain */
+    int32_t nst;
+} tfx_clip;
+
+typedef struct {
+    uint32_t plan_flags;   /* TFX_PLAN_* for every clip (TFX_PLAN_DEFAULT, _FIR_CUDA_CORES, _FIR_BF16_*) */
+    int32_t fir_nb;        /* tensor-core FIR output blocks of 128 per tile: 64, 128 or 256 (0: 128) */
+    int32_t tc_min_taps;   /* FIRs with at least this many taps use the tensor cores (0: 64) */
+} tfx_batch_params;
+
+typedef struct tfx_batch tfx_batch;
+
+int tfx_batch_create(tfx_batch **b, const tfx_clip *clips, int32_t nclips,
+                     const tfx_batch_params *params);
+int64_t tfx_batch_total_samples(const tfx_batch *b);
+int64_t tfx_batch_clip_offset(const tfx_batch *b, int32_t i);
+size_t tfx_batch_workspace_size(const tfx_batch *b);
+int tfx_batch_launch_count(const tfx_batch *b);
+int tfx_batch_execute(tfx_batch *b, const float *x, float *y, void *ws,
+                      size_t ws_bytes, tfx_stream s);
+int tfx_batch_get_error(tfx_batch *b);
+void tfx_batch_destroy(tfx_batch *b);
+
+/* The batch's launches, for profiling: group g's kind (0 fused cascade +
+ * CUDA-core FIR, 1 cascade, 2 tensor-core FIR), its level in the chains, its
+ * tiles, the channel-samples it filters and its algorithmic flops (10 per
+ * section-sample, 2 L per FIR sample); tfx_batch_execute_group runs group g
+ * alone (its inputs must hold what the earlier levels write). */
+int tfx_batch_group_count(const tfx_batch *b);
+int tfx_batch_group_info(const tfx_batch *b, int32_t g, int32_t *kind, int32_t *level,
+                         int64_t *tiles, int64_t *samples, double *flops);
+int tfx_batch_execute_group(tfx_batch *b, int32_t g, const float *x, float *y, void *ws,
+                            size_t ws_bytes, tfx_stream s);
+
 /* Human-readable name of a tfx_status. */
 const char *tfx_strerror(int status);
 

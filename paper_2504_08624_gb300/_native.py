@@ -39,6 +39,9 @@ EXPORTS = [
     "tfx_chain_host", "tfx_host_cache_clear",
     "tfx_plan_saved_size", "tfx_plan_backward_workspace_size", "tfx_plan_coef_count", "tfx_plan_forward_train",
     "tfx_plan_backward", "tfx_plan_backward_launch_count", "tfx_mse",
+    "tfx_batch_create", "tfx_batch_total_samples", "tfx_batch_clip_offset", "tfx_batch_workspace_size",
+    "tfx_batch_launch_count", "tfx_batch_execute", "tfx_batch_get_error", "tfx_batch_destroy",
+    "tfx_batch_group_count", "tfx_batch_group_info", "tfx_batch_execute_group",
 ]
 
 
@@ -50,6 +53,14 @@ class TfxError(RuntimeError):
 
 class Stage(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("n", ctypes.c_int32), ("coef", ctypes.POINTER(ctypes.c_double))]
+
+
+class Clip(ctypes.Structure):
+    _fields_ = [("C", ctypes.c_int64), ("N", ctypes.c_int64), ("st", ctypes.POINTER(Stage)), ("nst", ctypes.c_int32)]
+
+
+class BatchParams(ctypes.Structure):
+    _fields_ = [("plan_flags", ctypes.c_uint32), ("fir_nb", ctypes.c_int32), ("tc_min_taps", ctypes.c_int32)]
 
 
 _lib = None
@@ -112,6 +123,29 @@ def lib():
     L.tfx_plan_backward_launch_count.restype = ctypes.c_int
     L.tfx_mse.argtypes = [fp, fp, fp, i64, i64, i64, fp, vp]
     L.tfx_mse.restype = ctypes.c_int
+    L.tfx_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Clip), i32, ctypes.POINTER(BatchParams)]
+    L.tfx_batch_create.restype = ctypes.c_int
+    L.tfx_batch_total_samples.argtypes = [vp]
+    L.tfx_batch_total_samples.restype = i64
+    L.tfx_batch_clip_offset.argtypes = [vp, i32]
+    L.tfx_batch_clip_offset.restype = i64
+    L.tfx_batch_workspace_size.argtypes = [vp]
+    L.tfx_batch_workspace_size.restype = sz
+    L.tfx_batch_launch_count.argtypes = [vp]
+    L.tfx_batch_launch_count.restype = ctypes.c_int
+    L.tfx_batch_execute.argtypes = [vp, fp, fp, vp, sz, vp]
+    L.tfx_batch_execute.restype = ctypes.c_int
+    L.tfx_batch_get_error.argtypes = [vp]
+    L.tfx_batch_get_error.restype = ctypes.c_int
+    L.tfx_batch_destroy.argtypes = [vp]
+    L.tfx_batch_destroy.restype = None
+    L.tfx_batch_group_count.argtypes = [vp]
+    L.tfx_batch_group_count.restype = ctypes.c_int
+    ip32, ip64 = ctypes.POINTER(i32), ctypes.POINTER(i64)
+    L.tfx_batch_group_info.argtypes = [vp, i32, ip32, ip32, ip64, ip64, ctypes.POINTER(ctypes.c_double)]
+    L.tfx_batch_group_info.restype = ctypes.c_int
+    L.tfx_batch_execute_group.argtypes = [vp, i32, fp, fp, vp, sz, vp]
+    L.tfx_batch_execute_group.restype = ctypes.c_int
     L.tfx_strerror.argtypes = [ctypes.c_int]
     L.tfx_strerror.restype = ctypes.c_char_p
     L.tfx_version.restype = ctypes.c_int

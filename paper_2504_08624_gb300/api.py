@@ -386,3 +386,104 @@ class LearnableBiquadChain(torch.nn.Module):
 
     def forward(self, x: torch.Tensor) -> torch.Tensor:
         return ChainFunction.apply(x, ("sos", "fir"), self.rows(), self.h)
+
+
+# ---------------------------------------------------------------------------
+# batched launch over many clips
+
+
+class Batch:
+    """Many clips, each with its own (channels, samples, chain), filtered by a
+    few batched launches over one packed input and one packed output buffer
+    (``offsets[i]`` = first float of clip i; rows of its own length).
+    ``params``: ``fir_nb`` (tensor-core FIR output blocks of 128 per tile) and
+    ``tc_min_taps`` (tensor cores from this many taps), as picked by
+    ``autotune.tune_batch``."""
+
+    def __init__(self, clips, fir_nb: int = 128, tc_min_taps: int = 64, flags: int = 0,
+                 device: int | None = None):
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.clips = [(int(C), int(Ns), list(st)) for C, Ns, st in clips]
+        self._keep = [N.StageList(st) for _, _, st in self.clips]
+        arr = (N.Clip * max(1, len(self.clips)))()
+        for i, ((C, Ns, _), sl) in enumerate(zip(self.clips, self._keep)):
+            arr[i].C, arr[i].N, arr[i].st, arr[i].nst = C, Ns, sl.arr, sl.n
+        prm = N.BatchParams(flags, fir_nb, tc_min_taps)
+        self.params = {"fir_nb": fir_nb, "tc_min_taps": tc_min_taps, "flags": flags}
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = N.lib().tfx_batch_create(ctypes.byref(self._h), arr, len(self.clips), ctypes.byref(prm))
+        N.check(rc, "tfx_batch_create")
+        L = N.lib()
+        self.total_samples = int(L.tfx_batch_total_samples(self._h))
+        self.offsets = [int(L.tfx_batch_clip_offset(self._h, i)) for i in range(len(self.clips))]
+        self.workspace_size = int(L.tfx_batch_workspace_size(self._h))
+        self.launches_per_execute = int(L.tfx_batch_launch_count(self._h))
+        self._ws = None
+
+    def workspace(self) -> torch.Tensor:
+        if self._ws is None:
+            self._ws = torch.empty(max(1, self.workspace_size), dtype=torch.uint8, device=self.device)
+        return self._ws
+
+    def empty(self) -> torch.Tensor:
+        return torch.empty(max(1, self.total_samples), dtype=torch.float32, device=self.device)
+
+    def view(self, packed: torch.Tensor, i: int) -> torch.Tensor:
+        """Clip i of a packed buffer as a [C, N] view."""
+        C, Ns, _ = self.clips[i]
+        o = self.offsets[i]
+        return packed[o:o + C * Ns].view(C, Ns)
+
+    def pack(self, signals) -> torch.Tensor:
+        out = self.empty()
+        for i, x in enumerate(signals):
+            self.view(out, i).copy_(torch.as_tensor(x))
+        return out
+
+    def execute(self, x: torch.Tensor, y: torch.Tensor | None = None, ws: torch.Tensor | None = None):
+        if y is None:
+            y = self.empty()
+        for t in (x, y):
+            if not t.is_cuda or t.dtype != torch.float32 or t.numel() < self.total_samples or not t.is_contiguous():
+                raise ValueError("packed buffers: contiguous float32 CUDA tensors of total_samples floats")
+        w = self.workspace() if ws is None else ws
+        with torch.cuda.device(self.device):
+            rc = N.lib().tfx_batch_execute(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                           ctypes.c_void_p(w.data_ptr()), w.numel(), _stream_handle(self.device))
+        N.check(rc, "tfx_batch_execute")
+        return y
+
+    def groups(self) -> list:
+        """[(kind, level, tiles, channel-samples, algorithmic flops)] per launch."""
+        out = []
+        for g in range(int(N.lib().tfx_batch_group_count(self._h))):
+            k, lv = ctypes.c_int32(), ctypes.c_int32()
+            t, sm, fl = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+            N.check(N.lib().tfx_batch_group_info(self._h, g, ctypes.byref(k), ctypes.byref(lv), ctypes.byref(t),
+                                                 ctypes.byref(sm), ctypes.byref(fl)), "tfx_batch_group_info")
+            out.append((k.value, lv.value, t.value, sm.value, fl.value))
+        return out
+
+    def execute_group(self, g: int, x: torch.Tensor, y: torch.Tensor, ws: torch.Tensor | None = None) -> None:
+        w = self.workspace() if ws is None else ws
+        with torch.cuda.device(self.device):
+            rc = N.lib().tfx_batch_execute_group(self._h, g, ctypes.c_void_p(x.data_ptr()),
+                                                 ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(w.data_ptr()),
+                                                 w.numel(), _stream_handle(self.device))
+        N.check(rc, "tfx_batch_execute_group")
+
+    def get_error(self) -> int:
+        with torch.cuda.device(self.device):
+            return int(N.lib().tfx_batch_get_error(self._h))
+
+    def close(self) -> None:
+        if self._h:
+            N.lib().tfx_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -35,7 +35,8 @@
 
 namespace tfx {
 
-__global__ void __launch_bounds__(256, 1) k_fir_tc(FirTcArgs a) {
+// One tile (128 * NB outputs of one channel) on one CTA of 256 threads.
+__device__ __forceinline__ void fir_tc_tile(const FirTcArgs& a, const int64_t tile) {
     extern __shared__ __align__(128) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int J = a.a_chunks;
@@ -48,7 +49,6 @@ __global__ void __launch_bounds__(256, 1) k_fir_tc(FirTcArgs a) {
     uint64_t* bar = reinterpret_cast<uint64_t*>(B_lo + (size_t)16 * CS);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
 
-    const int64_t tile = blockIdx.x;
     const int64_t c = tile / a.ntt;
     const int64_t t0 = (tile % a.ntt) * (int64_t)(128 * a.NB);
 
@@ -177,6 +177,49 @@ __global__ void __launch_bounds__(256, 1) k_fir_tc(FirTcArgs a) {
     tc::tc_fence_before();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, (uint32_t)a.tmem_cols);
+}
+
+__global__ void __launch_bounds__(256, 1) k_fir_tc(FirTcArgs a) { fir_tc_tile(a, blockIdx.x); }
+
+// FIR tiles of many units (clips) in one launch: block b runs tile
+// b - prefix[u] of the unit u with prefix[u] <= b < prefix[u + 1].
+__global__ void __launch_bounds__(256, 1)
+    k_fir_tc_batched(const BatchFir* __restrict__ units, const int64_t* __restrict__ prefix, int nunits,
+                     BatchBases bases) {
+    __shared__ FirTcArgs s_args;
+    __shared__ int64_t s_tile;
+    if (threadIdx.x == 0) {
+        const int64_t t = blockIdx.x;
+        int lo = 0, hi = nunits - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchFir& bf = units[lo];
+        FirTcArgs a = bf.a;
+        a.x = bases.ptr(bf.x_sel) + bf.x_off;
+        a.y = bases.ptr(bf.y_sel) + bf.y_off;
+        s_args = a;
+        s_tile = t - prefix[lo];
+    }
+    __syncthreads();
+    fir_tc_tile(s_args, s_tile);
+}
+
+cudaError_t launch_fir_tc_batched(const BatchFir* units, const int64_t* prefix, int nunits, int64_t tiles,
+                                  BatchBases bases, size_t smem, cudaStream_t s) {
+    if (tiles <= 0) return cudaSuccess;
+    k_fir_tc_batched<<<(unsigned)tiles, 256, smem, s>>>(units, prefix, nunits, bases);
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_fir_tc_batched(size_t smem) {
+    static size_t set_bytes = 48 * 1024;
+    if (smem <= set_bytes) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_fir_tc_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) set_bytes = smem;
+    return e;
 }
 
 // ---------------------------------------------------------------------------

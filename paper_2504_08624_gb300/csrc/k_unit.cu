@@ -95,20 +95,18 @@ __device__ __forceinline__ void fir_block(const float* __restrict__ win, const f
     }
 }
 
+// One tile of one unit (the whole CTA).  The tile index comes from the
+// caller's ticket, so every predecessor tile of the channel is already running.
 template <bool HAS_FIR, int T, int NTH>
-__global__ void __launch_bounds__(NTH, HAS_FIR ? 2 : 4) k_unit(UnitArgs a) {
+__device__ __forceinline__ void unit_tile(const UnitArgs& a, const int64_t tile) {
     constexpr int NW = NTH / 32;
     static_assert(NTH * T == TILE, "tile size");
     extern __shared__ float4 smem_f4[];
     float* smem = reinterpret_cast<float*>(smem_f4);
-    __shared__ unsigned s_tile;
     __shared__ float2 s_tot[NW];
     __shared__ float2 s_win;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_tile = atomicAdd(a.sc.ticket, 1u);
-    __syncthreads();
-    const int64_t tile = s_tile;
     const int64_t c = tile % a.C;
     const int64_t tt = tile / a.C;
     const int64_t t0 = tt * TILE;
@@ -339,6 +337,47 @@ __global__ void __launch_bounds__(NTH, HAS_FIR ? 2 : 4) k_unit(UnitArgs a) {
     }
 }
 
+template <bool HAS_FIR, int T, int NTH>
+__global__ void __launch_bounds__(NTH, HAS_FIR ? 2 : 4) k_unit(UnitArgs a) {
+    __shared__ unsigned s_tile;
+    if (threadIdx.x == 0) s_tile = atomicAdd(a.sc.ticket, 1u);
+    __syncthreads();
+    unit_tile<HAS_FIR, T, NTH>(a, s_tile);
+}
+
+// Many units (of many clips) in one launch: the ticket runs over the
+// concatenated tile ranges of the units (prefix[u] .. prefix[u+1]), so each
+// unit's tiles keep their time-major order and look-back stays deadlock-free.
+// Buffer pointers in the descriptors are offsets into one of three bases.
+template <bool HAS_FIR, int T, int NTH>
+__global__ void __launch_bounds__(NTH, HAS_FIR ? 2 : 4)
+    k_unit_batched(const BatchUnit* __restrict__ units, const int64_t* __restrict__ prefix, int nunits,
+                   unsigned* ticket, BatchBases bases) {
+    __shared__ UnitArgs s_args;
+    __shared__ int64_t s_tile;
+    if (threadIdx.x == 0) {
+        const int64_t t = atomicAdd(ticket, 1u);
+        int lo = 0, hi = nunits - 1;  // last unit with prefix[u] <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchUnit& bu = units[lo];
+        UnitArgs a = bu.a;
+        a.x = bases.ptr(bu.x_sel) + bu.x_off;
+        a.y = bases.ptr(bu.y_sel) + bu.y_off;
+        char* w = reinterpret_cast<char*>(bases.ws);
+        a.sc.flags = reinterpret_cast<unsigned*>(w + bu.flags_off);
+        a.sc.carry = reinterpret_cast<Carry*>(w + bu.carry_off);
+        a.sc.tails = reinterpret_cast<float*>(w + bu.tails_off);
+        s_args = a;
+        s_tile = t - prefix[lo];
+    }
+    __syncthreads();
+    unit_tile<HAS_FIR, T, NTH>(s_args, s_tile);
+}
+
 size_t unit_smem_bytes(const UnitConst& k) {
     if (k.L <= 0) return 0;
     const int win_len = (FIR_PAD + k.H + TILE - 1) + ((FIR_PAD + k.H + TILE - 1) >> 5) + 1;
@@ -354,6 +393,26 @@ cudaError_t prepare_unit(const UnitConst& k) {
     cudaError_t e = cudaFuncSetAttribute(k_unit<true, T_CHUNK, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e == cudaSuccess) set_bytes = (int)smem;
+    return e;
+}
+
+cudaError_t launch_unit_batched(bool has_fir, const BatchUnit* units, const int64_t* prefix, int nunits,
+                                int64_t tiles, unsigned* ticket, BatchBases bases, size_t smem, cudaStream_t s) {
+    if (tiles <= 0) return cudaSuccess;
+    if (has_fir)
+        k_unit_batched<true, T_CHUNK, NT><<<(unsigned)tiles, NT, smem, s>>>(units, prefix, nunits, ticket, bases);
+    else
+        k_unit_batched<false, T_CASCADE, NT_CASCADE><<<(unsigned)tiles, NT_CASCADE, 0, s>>>(units, prefix, nunits,
+                                                                                           ticket, bases);
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_unit_batched(size_t smem) {
+    static size_t set_bytes = 48 * 1024;
+    if (smem <= set_bytes) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_unit_batched<true, T_CHUNK, NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) set_bytes = smem;
     return e;
 }
 

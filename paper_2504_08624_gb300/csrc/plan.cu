@@ -11,84 +11,21 @@
 #include <unordered_map>
 #include <vector>
 
-#include "tfx_common.cuh"
+#include "plan_internal.cuh"
 
 using namespace tfx;
 
-namespace {
+// Tensor-core FIR geometry for L taps and NB output blocks per tile.
+void tfx::tc_geometry(HostUnit& u, int NB) {
+    u.W = ((u.L - 1 + 15) / 16) * 16;
+    u.nK = (u.W + 128) / 16;
+    u.NB = NB;
+    u.rows = NB + (u.W + 127) / 128 + 1;
+    u.tmem_cols = NB <= 32 ? 32 : (NB <= 64 ? 64 : (NB <= 128 ? 128 : 256));
+    u.a_chunks = 2 * u.nK + 16;
+    u.tc_smem = (size_t)u.a_chunks * 128 * 2 + (size_t)16 * u.rows * 16 * 2 + 16;
+}
 
-constexpr size_t ALIGN = 256;
-inline size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
-
-struct HostUnit {
-    int S = 0;                  // sections
-    int L = 0;                  // FIR taps (0 = none)
-    std::vector<double> sec;    // [S][5] a0-normalised b0 b1 b2 a1 a2
-    std::vector<double> taps;   // [L]
-    // device constants (offsets into the plan's constant blob)
-    size_t off_coef = 0, off_pw = 0, off_taps = 0;
-    int nkb = 0;
-    int64_t ntt = 0;            // time tiles per channel
-    int tail_len = 0;
-    // scratch sizes (bytes)
-    size_t flags_bytes = 0, vals_bytes = 0, tails_bytes = 0;
-    // FIR on the tensor cores (Toeplitz-block GEMM); such a unit has S == 0
-    bool tc = false;
-    int W = 0, nK = 0, NB = 0, rows = 0, tmem_cols = 0, a_chunks = 0;
-    size_t off_ahi = 0, off_alo = 0, tc_smem = 0;
-    int tc_mode = 0;
-    float tap_unscale = 1.0f;
-    int tc_variant = 0;  // 0: one tile per CTA, 1: persistent resident taps, 2: persistent streamed taps
-    size_t tc_smem_ws = 0;
-    // cascade without an FIR: warp-per-tile scan (tiles of 32 * T_CHUNK samples)
-    bool warp = false;
-    // trainable plans: where each section's raw row (6 values) and the FIR's
-    // taps sit in the flat coefficient-gradient array, the raw rows for the
-    // a0 chain rule, and the unit's saved activations
-    std::vector<int64_t> dst;   // [S]
-    std::vector<double> raw;    // [S][6]
-    int64_t fir_dst = 0;
-    size_t off_raw = 0, off_dst = 0;  // constant blob
-    size_t off_act = 0;               // saved: this unit's input (units after the first)
-    size_t off_ckpt = 0;              // saved: chunk-start states [C][S][nch] (cascade units)
-    int Lp = 0;                       // FIR taps rounded up to 16
-};
-
-constexpr int WARP_TILE = 32 * T_CHUNK;
-
-// Taps at or above this count go to the tensor cores (unless disabled).
-constexpr int TC_MIN_TAPS = 64;
-constexpr size_t SMEM_MAX = 227 * 1024;
-
-struct PlainStage {
-    int kind;  // TFX_STAGE_FIR / TFX_STAGE_SOS
-    int n;
-    size_t off;  // FP32 coefficients in the constant blob (SOS: [n][8]; FIR: [n])
-};
-
-}  // namespace
-
-struct tfx_plan {
-    int64_t C = 0, N = 0, ld = 0;
-    uint32_t flags = 0;
-    std::vector<HostUnit> units;
-    std::vector<PlainStage> plain;
-    char* dconst = nullptr;
-    int* dstatus = nullptr;
-    // workspace layout
-    size_t scratch_hdr = 0;    // ticket + tail flags + carries (memset per unit execution)
-    size_t scratch_bytes = 0;  // header + tails
-    size_t buf_bytes = 0;      // one intermediate [C x N] buffer
-    size_t ws_fused = 0, ws_plain = 0;
-    int sm_count = 1;  // persistent grid size
-    // trainable plans
-    bool train = false;
-    int64_t ncoef = 0;        // doubles in the coefficient-gradient array
-    int64_t nch = 0;          // 32-sample chunks per channel
-    size_t saved_bytes = 0;   // forward activations + checkpoints kept for the backward
-    size_t bws_bytes = 0;     // backward workspace
-    size_t b_scan = 0, b_part = 0, b_tmp = 0, b_gbuf = 0;  // backward workspace offsets
-};
 
 namespace {
 
@@ -170,17 +107,6 @@ float bf2f(uint16_t b) {
     float f;
     std::memcpy(&f, &u, 4);
     return f;
-}
-
-// Tensor-core FIR geometry for L taps and NB output blocks per tile.
-void tc_geometry(HostUnit& u, int NB) {
-    u.W = ((u.L - 1 + 15) / 16) * 16;
-    u.nK = (u.W + 128) / 16;
-    u.NB = NB;
-    u.rows = NB + (u.W + 127) / 128 + 1;
-    u.tmem_cols = NB <= 32 ? 32 : (NB <= 64 ? 64 : (NB <= 128 ? 128 : 256));
-    u.a_chunks = 2 * u.nK + 16;
-    u.tc_smem = (size_t)u.a_chunks * 128 * 2 + (size_t)16 * u.rows * 16 * 2 + 16;
 }
 
 // Pick the tile width for a tensor-core FIR: 128 blocks (16384 outputs) when
@@ -297,7 +223,7 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         std::vector<HostUnit> out;
         for (HostUnit& u : p->units) {
             HostUnit f = u;
-            if (u.L >= TC_MIN_TAPS && (f.S = 0, f.sec.clear(), choose_tc(f))) {
+            if (u.L >= p->tc_min_taps && (f.S = 0, f.sec.clear(), choose_tc(f))) {
                 f.tc = true;
                 if (u.S > 0) {
                     HostUnit sos = u;
@@ -903,6 +829,13 @@ extern "C" {
 
 int tfx_plan_create(tfx_plan** out, int64_t C, int64_t N, int64_t ld, const tfx_stage* st, int32_t nst,
                     uint32_t flags) {
+    return plan_create_ex(out, C, N, ld, st, nst, flags, TC_MIN_TAPS);
+}
+
+}  // extern "C"
+
+int tfx::plan_create_ex(tfx_plan** out, int64_t C, int64_t N, int64_t ld, const tfx_stage* st, int32_t nst,
+                        uint32_t flags, int tc_min_taps) {
     if (!out) return TFX_ERR_INVALID;
     *out = nullptr;
     int rc = check_dims(C, N, ld);
@@ -918,6 +851,7 @@ int tfx_plan_create(tfx_plan** out, int64_t C, int64_t N, int64_t ld, const tfx_
     p->N = N;
     p->ld = ld;
     p->flags = flags;
+    p->tc_min_taps = tc_min_taps > 0 ? tc_min_taps : TC_MIN_TAPS;
     rc = build_plan(p, st, nst, true);
     if (rc != TFX_OK) {
         tfx_plan_destroy(p);
@@ -926,6 +860,8 @@ int tfx_plan_create(tfx_plan** out, int64_t C, int64_t N, int64_t ld, const tfx_
     *out = p;
     return TFX_OK;
 }
+
+extern "C" {
 
 size_t tfx_plan_workspace_size(const tfx_plan* p) {
     if (!p) return 0;

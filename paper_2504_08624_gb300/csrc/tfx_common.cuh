@@ -78,6 +78,25 @@ struct UnitArgs {
     int64_t nch;
 };
 
+// Batched execution: buffer pointers of a batch descriptor are offsets into
+// one of three bases (0: the packed batch input, 1: the packed batch output,
+// 2: the workspace).
+struct BatchBases {
+    const float* x;
+    float* y;
+    float* ws;
+    __device__ __forceinline__ float* ptr(int sel) const {
+        return sel == 0 ? const_cast<float*>(x) : (sel == 1 ? y : ws);
+    }
+};
+
+struct BatchUnit {
+    UnitArgs a;          // constants, sizes, status; x, y, scratch filled in from the offsets below
+    int x_sel, y_sel;    // bases for x and y
+    int64_t x_off, y_off;                 // in floats
+    int64_t flags_off, carry_off, tails_off;  // in bytes, into the workspace
+};
+
 // Reverse-time adjoint of an SOS cascade (warp-tile geometry of the forward
 // training pass: 32 lanes x T_CHUNK samples per tile).
 struct BwdArgs {
@@ -124,6 +143,12 @@ struct FirTcArgs {
     const uint4* a_hi;  // [a_chunks][8 copies] high parts of the shifted (scaled) taps
     const uint4* a_lo;  // same, low parts
     int* status;
+};
+
+struct BatchFir {
+    FirTcArgs a;           // x and y filled in from the offsets below
+    int x_sel, y_sel;
+    int64_t x_off, y_off;  // in floats
 };
 
 // ---------------------------------------------------------------------------
@@ -242,7 +267,13 @@ cudaError_t prepare_fir_tc_long(size_t smem);
 size_t fir_tc_long_smem(int rows);
 constexpr int TC_KBLK = 64;  // K-steps per streamed tap block
 cudaError_t launch_fir_tc(const FirTcArgs& a, cudaStream_t s);
+cudaError_t launch_fir_tc_batched(const BatchFir* units, const int64_t* prefix, int nunits, int64_t tiles,
+                                  BatchBases bases, size_t smem, cudaStream_t s);
+cudaError_t prepare_fir_tc_batched(size_t smem);
 cudaError_t prepare_unit(const UnitConst& k);
+cudaError_t launch_unit_batched(bool has_fir, const BatchUnit* units, const int64_t* prefix, int nunits,
+                                int64_t tiles, unsigned* ticket, BatchBases bases, size_t smem, cudaStream_t s);
+cudaError_t prepare_unit_batched(size_t smem);
 
 // Backward (adjoint) launchers, defined in k_bwd.cu.
 constexpr int BWD_SMAX = 8;  // sections per cascade unit in a trainable plan

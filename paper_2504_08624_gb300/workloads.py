@@ -429,6 +429,33 @@ def random_chain(seed: int, max_sections: int = 8, min_taps: int = 33, max_taps:
     return [("sos", random_stable_sos(S, seed + 7919)), ("fir", fir_lowpass(L, fc, FS))]
 
 
+@dataclass
+class Clip:
+    """One clip of the batched workload: C channels x N samples of U[-1, 1]
+    noise (seed) through its own chain."""
+    C: int
+    N: int
+    stages: list
+    seed: int
+
+    def make_signal(self) -> np.ndarray:
+        return white_uniform(self.C, self.N, self.seed)
+
+
+def batched_clips(n: int = 1000, seed: int = 5) -> list:
+    """The many-clip workload (c13): lengths round(48000 exp(U(ln 0.5, ln 30)))
+    samples, channels from {1, 2, 6, 8, 16}, each clip with its own chain of
+    1-8 random stable sections (pole radius <= 0.999) and a Hamming low-pass
+    FIR of log-uniform 33-2049 taps (odd, fc ~ U(0.05, 0.45) fs)."""
+    rng = np.random.default_rng(seed)
+    clips = []
+    for i in range(n):
+        N = int(round(FS * math.exp(rng.uniform(math.log(0.5), math.log(30.0)))))
+        C = int(rng.choice([1, 2, 6, 8, 16]))
+        clips.append(Clip(C, N, random_chain(seed * 100003 + i), seed * 1000003 + i))
+    return clips
+
+
 WORKLOADS = {
     "plain_chain": plain_chain,
     "multichannel_fused": multichannel_fused,

@@ -33,3 +33,24 @@ def tol_for(stages):
 
 def oracle_chain(x, stages):
     return oracle.chain(np.asarray(x, dtype=np.float64), stages)
+
+
+def assert_close_floored(got, ref, x, tol, what="", floor=1e-3):
+    """The stated tolerance against each channel's output peak, floored at
+    `floor` x the channel's input peak: a chain that attenuates by more than
+    60 dB leaves an output that FP32 data (rounded relative to the input)
+    cannot resolve to 1e-4 of its own peak."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    x = np.asarray(x, dtype=np.float64)
+    if got.ndim == 1:
+        got, ref, x = got[None], ref[None], x[None]
+    if got.shape[1] == 0:
+        return 0.0
+    err = np.max(np.abs(got - ref), axis=1)
+    scale = np.maximum(np.max(np.abs(ref), axis=1), floor * np.max(np.abs(x), axis=1))
+    rel = err / np.maximum(scale, 1e-30)
+    worst = int(np.argmax(rel))
+    assert np.all(rel <= tol), (f"{what}: channel {worst} max|err| {err[worst]:.3e} = {rel[worst]:.3e} x "
+                                f"scale {scale[worst]:.3e} > tol {tol:g}")
+    return float(rel.max())
