@@ -344,6 +344,58 @@ int tfx_batch_group_info(const tfx_batch *b, int32_t g, int32_t *kind, int32_t *
 int tfx_batch_execute_group(tfx_batch *b, int32_t g, const float *x, float *y, void *ws,
                             size_t ws_bytes, tfx_stream s);
 
+/*
+ * Filter design on the GPU in FP64, and coefficient updates without a host
+ * round trip.  Sec. 3 builds IIR filters from design parameters (cutoff,
+ * order, ripple, gain, Q); these calls compute the sections on the device.
+ *
+ * tfx_design: one filter.  kind / fields used:
+ *   TFX_DESIGN_BUTTER_LOW / _HIGH : order (1..16), f1 = fc (-3 dB), fs
+ *   TFX_DESIGN_CHEBY1_LOW         : order, f1 = passband edge, p1 = ripple dB, fs
+ *   TFX_DESIGN_PEAKING            : f1 = f0, p1 = Q, p2 = gain dB, fs (RBJ)
+ *   TFX_DESIGN_LOW_SHELF / _HIGH  : f1 = f0, p1 = gain dB, p2 = shelf slope (0: 1), fs (RBJ)
+ *   TFX_DESIGN_BIQUAD_POLAR       : poles r = f1 + f2 sigmoid(p1), theta = pi sigmoid(p2),
+ *                                   numerator b[0..2] (the learnable cascade's parameters)
+ * Butterworth / Chebyshev-I: bilinear transform of the analog prototype with
+ * the cutoff prewarped to tan(pi fc / fs); sections by increasing pole
+ * radius, zeros at z = -1 (low-pass) or +1 (high-pass), unit gain at DC
+ * (low) or Nyquist (high); even-order Chebyshev-I has DC gain 10^(-rp/20).
+ * tfx_design_sections: sections the spec produces (-1 if invalid).
+ * tfx_design_device: specs, row_off (first output row of each spec) and
+ *   rows (6 doubles per row, raw b0 b1 b2 a0 a1 a2) in device memory; one
+ *   thread per spec; invalid specs set *status (device int) to
+ *   TFX_ERR_INVALID.  Asynchronous on s, capturable.
+ * tfx_plan_update_sos: recompute the plan's section constants (normalisation,
+ *   recursion coefficients, chunk-transfer powers; FP64 on the GPU) from
+ *   rows = device FP64 array of every SOS row of the plan's chain in order
+ *   (tfx_plan_sos_rows of them).  The plan's structure (units, kernels, the
+ *   FP64-carry routing chosen at creation) is kept; FIR taps are not
+ *   changed.  An unstable or invalid row sets the status read by
+ *   tfx_plan_get_error.  The first call uploads per-section descriptors
+ *   (host-synchronous: make it before any capture); later calls are one
+ *   launch, capturable.  Must not overlap an execution of the plan.
+ */
+#define TFX_DESIGN_BUTTER_LOW 0
+#define TFX_DESIGN_BUTTER_HIGH 1
+#define TFX_DESIGN_CHEBY1_LOW 2
+#define TFX_DESIGN_PEAKING 3
+#define TFX_DESIGN_LOW_SHELF 4
+#define TFX_DESIGN_HIGH_SHELF 5
+#define TFX_DESIGN_BIQUAD_POLAR 6
+
+typedef struct {
+    int32_t kind;
+    int32_t order;
+    double f1, f2, fs, p1, p2;
+    double b[3];
+} tfx_design;
+
+int tfx_design_sections(const tfx_design *spec);
+int tfx_design_device(const tfx_design *specs, int32_t n, const int64_t *row_off,
+                      double *rows, int *status, tfx_stream s);
+int tfx_plan_update_sos(tfx_plan *p, const double *rows, tfx_stream s);
+int64_t tfx_plan_sos_rows(const tfx_plan *p);
+
 /* Human-readable name of a tfx_status. */
 const char *tfx_strerror(int status);
 

@@ -10,7 +10,7 @@ __version__ = "0.1.0"
 
 def __getattr__(name):
     if name in ("chain", "fir", "sos", "Plan", "TfxError", "chain_ad", "ChainFunction", "FilterChain", "mse",
-                "mse_loss", "LearnableBiquadChain", "Batch"):
+                "mse_loss", "LearnableBiquadChain", "Batch", "design"):
         from . import api
         return getattr(api, name)
     raise AttributeError(name)

@@ -42,6 +42,7 @@ EXPORTS = [
     "tfx_batch_create", "tfx_batch_total_samples", "tfx_batch_clip_offset", "tfx_batch_workspace_size",
     "tfx_batch_launch_count", "tfx_batch_execute", "tfx_batch_get_error", "tfx_batch_destroy",
     "tfx_batch_group_count", "tfx_batch_group_info", "tfx_batch_execute_group",
+    "tfx_design_sections", "tfx_design_device", "tfx_plan_update_sos", "tfx_plan_sos_rows",
 ]
 
 
@@ -57,6 +58,16 @@ class Stage(ctypes.Structure):
 
 class Clip(ctypes.Structure):
     _fields_ = [("C", ctypes.c_int64), ("N", ctypes.c_int64), ("st", ctypes.POINTER(Stage)), ("nst", ctypes.c_int32)]
+
+
+class Design(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("order", ctypes.c_int32), ("f1", ctypes.c_double), ("f2", ctypes.c_double),
+                ("fs", ctypes.c_double), ("p1", ctypes.c_double), ("p2", ctypes.c_double),
+                ("b", ctypes.c_double * 3)]
+
+
+DESIGN_KINDS = {"butter_low": 0, "butter_high": 1, "cheby1_low": 2, "peaking": 3, "low_shelf": 4,
+                "high_shelf": 5, "biquad_polar": 6}
 
 
 class BatchParams(ctypes.Structure):
@@ -146,6 +157,14 @@ def lib():
     L.tfx_batch_group_info.restype = ctypes.c_int
     L.tfx_batch_execute_group.argtypes = [vp, i32, fp, fp, vp, sz, vp]
     L.tfx_batch_execute_group.restype = ctypes.c_int
+    L.tfx_design_sections.argtypes = [ctypes.POINTER(Design)]
+    L.tfx_design_sections.restype = ctypes.c_int
+    L.tfx_design_device.argtypes = [vp, i32, vp, vp, vp, vp]
+    L.tfx_design_device.restype = ctypes.c_int
+    L.tfx_plan_update_sos.argtypes = [vp, vp, vp]
+    L.tfx_plan_update_sos.restype = ctypes.c_int
+    L.tfx_plan_sos_rows.argtypes = [vp]
+    L.tfx_plan_sos_rows.restype = i64
     L.tfx_strerror.argtypes = [ctypes.c_int]
     L.tfx_strerror.restype = ctypes.c_char_p
     L.tfx_version.restype = ctypes.c_int

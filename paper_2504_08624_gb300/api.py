@@ -155,6 +155,22 @@ class Plan:
         N.check(rc, "tfx_plan_execute_plain" if plain else "tfx_plan_execute")
         return y
 
+    # -- coefficient updates on the device ----------------------------------
+
+    @property
+    def sos_rows(self) -> int:
+        return int(N.lib().tfx_plan_sos_rows(self._h))
+
+    def update_sos(self, rows: torch.Tensor) -> None:
+        """Recompute the plan's section constants on the GPU from ``rows`` (CUDA
+        float64 [sos_rows x 6], every SOS row of the chain in order)."""
+        if not rows.is_cuda or rows.dtype != torch.float64 or rows.numel() != 6 * self.sos_rows:
+            raise ValueError("rows: CUDA float64 tensor of sos_rows x 6 values")
+        rows = rows.contiguous()
+        with torch.cuda.device(self.device):
+            rc = N.lib().tfx_plan_update_sos(self._h, ctypes.c_void_p(rows.data_ptr()), _stream_handle(self.device))
+        N.check(rc, "tfx_plan_update_sos")
+
     # -- gradients (plans created with TFX_PLAN_TRAINABLE) -----------------
 
     @property
@@ -487,3 +503,55 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# filter design on the GPU (FP64)
+
+
+def design(specs, device=None) -> list:
+    """Design filters on the GPU in FP64.  ``specs``: list of dicts with
+    ``kind`` in butter_low / butter_high / cheby1_low (order, fc, fs[, ripple_db]),
+    peaking (f0, Q, gain_db, fs), low_shelf / high_shelf (f0, gain_db, fs[, slope]),
+    biquad_polar (rho, phi, b[, rmin, rspan]).  Returns one CUDA float64
+    [sections x 6] tensor of raw rows per spec."""
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    arr = (N.Design * max(1, len(specs)))()
+    counts = []
+    for i, sp in enumerate(specs):
+        d = arr[i]
+        kind = sp["kind"]
+        d.kind = N.DESIGN_KINDS[kind]
+        d.fs = float(sp.get("fs", 48000.0))
+        if kind in ("butter_low", "butter_high", "cheby1_low"):
+            d.order, d.f1, d.p1 = int(sp["order"]), float(sp["fc"]), float(sp.get("ripple_db", 0.0))
+        elif kind == "peaking":
+            d.f1, d.p1, d.p2 = float(sp["f0"]), float(sp["Q"]), float(sp["gain_db"])
+        elif kind in ("low_shelf", "high_shelf"):
+            d.f1, d.p1, d.p2 = float(sp["f0"]), float(sp["gain_db"]), float(sp.get("slope", 1.0))
+        elif kind == "biquad_polar":
+            d.f1, d.f2 = float(sp.get("rmin", 0.5)), float(sp.get("rspan", 0.49))
+            d.p1, d.p2 = float(sp["rho"]), float(sp["phi"])
+            for j in range(3):
+                d.b[j] = float(sp["b"][j])
+        n = int(N.lib().tfx_design_sections(ctypes.byref(d)))
+        if n < 0:
+            raise ValueError(f"invalid design spec {sp}")
+        counts.append(n)
+    offs = [0]
+    for n in counts:
+        offs.append(offs[-1] + n)
+    raw = ctypes.string_at(ctypes.addressof(arr), len(specs) * ctypes.sizeof(N.Design))
+    dspecs = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(dev) if specs else torch.empty(1, dtype=torch.uint8, device=dev)
+    doff = torch.tensor(offs[:-1] or [0], dtype=torch.int64, device=dev)
+    rows = torch.empty(max(1, offs[-1]) * 6, dtype=torch.float64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    with torch.cuda.device(dev):
+        rc = N.lib().tfx_design_device(ctypes.c_void_p(dspecs.data_ptr()), len(specs), ctypes.c_void_p(doff.data_ptr()),
+                                       ctypes.c_void_p(rows.data_ptr()), ctypes.c_void_p(status.data_ptr()),
+                                       _stream_handle(dev))
+    N.check(rc, "tfx_design_device")
+    st = int(status.item())
+    if st != 0:
+        raise N.TfxError(st, "tfx_design_device")
+    return [rows[6 * a:6 * b].view(b - a, 6) for a, b in zip(offs[:-1], offs[1:])]

@@ -83,8 +83,9 @@ int batch_build(tfx_batch* b, const tfx_clip* clips, int32_t n, const tfx_batch_
         b->off[i] = off;
         if (c.C > 0 && c.N > INT64_MAX / c.C) return TFX_ERR_INVALID;
         off += c.C * c.N;
+        // the batched cascade kernel carries in FP32: no FP64-carry routing
         const int rc = plan_create_ex(&b->plans[i], c.C, c.N, c.N > 0 ? c.N : 1, c.st, c.nst, pflags,
-                                      prm.tc_min_taps);
+                                      prm.tc_min_taps, false);
         if (rc != TFX_OK) return rc;
     }
     b->total = off;

@@ -53,8 +53,8 @@ __device__ __forceinline__ void warp_store(float* row, int64_t n0, int64_t N, co
     }
 }
 
-template <int T>
-__global__ void __launch_bounds__(128, 6) k_sos_warp(UnitArgs a) {
+template <int T, bool F64>
+__global__ void __launch_bounds__(128, F64 ? 4 : 6) k_sos_warp(UnitArgs a) {
     const int lane = threadIdx.x & 31;
     unsigned tk = 0;
     if (lane == 0) tk = atomicAdd(a.sc.ticket, 1u);
@@ -130,7 +130,69 @@ __global__ void __launch_bounds__(128, 6) k_sos_warp(UnitArgs a) {
         // walk, every aggregate before it contributes through powers of the
         // tile transfer T32 = A^32: win = sum_m T32^m v_(tile-1-m).
         float2 win = make_float2(0.f, 0.f);
-        {
+        if (F64) {
+            // the same walk with FP64 carries, FP64 powers and an FP64 window;
+            // the chunk start state is formed in FP64 and rounded once
+            const double4* P64 = a.k.pw64 + (size_t)s * PW_LEN;
+            const double2 agg = make_double2(ax, ay);
+            const bool pub = tile != a.drop_tile;
+            Carry* mine = a.sc.carry + tile * S + s;
+            double2 wd = make_double2(0.0, 0.0);
+            if (tt == 0) {
+                if (lane == 0 && pub) publish_carry64(mine, 2u, agg);
+            } else {
+                const double4 PL = P64[32 * lane];
+                double4 Mw = make_double4(1.0, 0.0, 0.0, 1.0);
+                int64_t jt0 = tt - 1;
+                bool published = false;
+                for (;;) {
+                    const int64_t jt = jt0 - lane;
+                    double2 pv = make_double2(0.0, 0.0);
+                    unsigned f = 2u;
+                    if (jt >= 0) f = read_carry64(a.sc.carry + (jt * a.C + c) * S + s, pv);
+                    const unsigned incl_mask = __ballot_sync(0xffffffffu, f >= 2u);
+                    const unsigned none_mask = __ballot_sync(0xffffffffu, f == 0u);
+                    if (!published && !(incl_mask & 1u)) {
+                        if (lane == 0 && pub) publish_carry64(mine, 1u, agg);
+                        published = true;
+                    }
+                    const int first = incl_mask ? (__ffs(incl_mask) - 1) : 32;
+                    const unsigned need = first >= 31 ? 0xffffffffu : ((2u << first) - 1u);
+                    if (none_mask & need) {
+                        const int wl = __ffs(none_mask & need) - 1;
+                        unsigned got = 1u;
+                        if (lane == wl) {
+                            double2 dummy;
+                            got = wait_carry64(a.sc.carry + (jt * a.C + c) * S + s, dummy, a.status);
+                        }
+                        got = __shfl_sync(0xffffffffu, got, wl);
+                        if (got == 0u) break;
+                        continue;
+                    }
+                    double2 cntb = make_double2(0.0, 0.0);
+                    if (lane <= first) cntb = mv2d(mm2d(Mw, PL), pv);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        cntb.x += __shfl_xor_sync(0xffffffffu, cntb.x, o);
+                        cntb.y += __shfl_xor_sync(0xffffffffu, cntb.y, o);
+                    }
+                    wd.x += cntb.x;
+                    wd.y += cntb.y;
+                    if (first < 32) break;
+                    Mw = mm2d(Mw, P64[1024]);
+                    jt0 -= 32;
+                }
+                if (lane == 0 && pub) {
+                    double2 incl = mv2d(P64[32], wd);
+                    incl.x += agg.x;
+                    incl.y += agg.y;
+                    publish_carry64(mine, 2u, incl);
+                }
+            }
+            const double2 t2d = mv2d(P64[lane], wd);
+            st = (lane > 0) ? make_float2((float)((double)px + t2d.x), (float)((double)py + t2d.y))
+                            : make_float2((float)t2d.x, (float)t2d.y);
+        } else {
             const float2 agg = make_float2(ax, ay);
             const bool pub = tile != a.drop_tile;
             Carry* mine = a.sc.carry + tile * S + s;
@@ -188,12 +250,12 @@ __global__ void __launch_bounds__(128, 6) k_sos_warp(UnitArgs a) {
                     publish_carry(mine, 2u, incl);
                 }
             }
+            // true start state of this lane's chunk
+            st = (lane > 0) ? make_float2(px, py) : make_float2(0.f, 0.f);
+            const float2 t2 = mv2(Pl, win);
+            st.x += t2.x;
+            st.y += t2.y;
         }
-        // true start state of this lane's chunk
-        st = (lane > 0) ? make_float2(px, py) : make_float2(0.f, 0.f);
-        const float2 t2 = mv2(Pl, win);
-        st.x += t2.x;
-        st.y += t2.y;
         // training forward: keep the chunk-start state (block-boundary checkpoint)
         if (a.ckpt) {
             const int64_t chunk = tt * 32 + lane;
@@ -209,7 +271,10 @@ cudaError_t launch_sos_warp(const UnitArgs& a, cudaStream_t s) {
     const int64_t tiles = a.C * a.ntt;
     if (tiles <= 0) return cudaSuccess;
     const int64_t ctas = (tiles + 3) / 4;
-    k_sos_warp<T_CHUNK><<<(unsigned)ctas, 128, 0, s>>>(a);
+    if (a.k.pw64)
+        k_sos_warp<T_CHUNK, true><<<(unsigned)ctas, 128, 0, s>>>(a);
+    else
+        k_sos_warp<T_CHUNK, false><<<(unsigned)ctas, 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 

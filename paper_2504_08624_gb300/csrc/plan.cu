@@ -217,6 +217,36 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
     flush();
     p->ncoef = coff;
 
+    // cascades with a pole of radius > HIQ_RADIUS run the warp-tile scan with
+    // FP64 cross-tile carries; a short FIR fused behind one becomes its own unit
+    if (p->allow_hiq) {
+        std::vector<HostUnit> out;
+        for (HostUnit& u : p->units) {
+            for (int s = 0; s < u.S; ++s) {
+                const double a1 = u.sec[5 * s + 3], a2 = u.sec[5 * s + 4];
+                const double disc = a1 * a1 - 4.0 * a2;
+                const double r = disc < 0.0 ? std::sqrt(a2)
+                                            : std::max(std::fabs(-a1 + std::sqrt(disc)), std::fabs(-a1 - std::sqrt(disc))) / 2.0;
+                if (r > HIQ_RADIUS) u.hiq = true;
+            }
+            if (u.hiq && u.L > 0) {
+                HostUnit sos = u, fir = u;
+                sos.L = 0;
+                sos.taps.clear();
+                fir.S = 0;
+                fir.sec.clear();
+                fir.hiq = false;
+                fir.dst.clear();
+                fir.raw.clear();
+                out.push_back(sos);
+                out.push_back(fir);
+            } else {
+                out.push_back(u);
+            }
+        }
+        p->units.swap(out);
+    }
+
     // long FIRs go to the tensor cores; an SOS cascade in front of one runs as
     // its own unit (the cascade output crosses HBM once more)
     if (!(p->flags & TFX_PLAN_FIR_CUDA_CORES)) {
@@ -240,7 +270,7 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
     }
 
     for (HostUnit& u : p->units)
-        u.warp = (u.S > 0 && u.L == 0) && ((p->flags & TFX_PLAN_SCAN_WARP_TILES) || p->train);
+        u.warp = (u.S > 0 && u.L == 0) && ((p->flags & TFX_PLAN_SCAN_WARP_TILES) || p->train || u.hiq);
 
     // constant blob layout
     size_t off = 0;
@@ -249,6 +279,10 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         off = align_up(off + (size_t)u.S * 8 * sizeof(float));
         u.off_pw = off;
         off = align_up(off + (size_t)u.S * PW_LEN * sizeof(float4));
+        if (u.hiq) {
+            u.off_pw64 = off;
+            off = align_up(off + (size_t)u.S * PW_LEN * sizeof(double4));
+        }
         u.nkb = u.L > 0 ? (u.L + FIR_R - 1) / FIR_R : 0;
         u.off_taps = off;
         off = align_up(off + (size_t)u.nkb * FIR_R * sizeof(float));
@@ -285,8 +319,10 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
             const int chunk = u.L == 0 && !u.warp ? T_CASCADE : T_CHUNK;  // samples per thread of u's kernel
             for (int t = 0; t < chunk; ++t) a = mul(a, m);                 // chunk transfer A = M^chunk
             M2 pk = {1, 0, 0, 1};
+            double4* pw64 = u.hiq ? reinterpret_cast<double4*>(host.data() + u.off_pw64) : nullptr;
             for (int k = 0; k < PW_LEN; ++k) {
                 pw[(size_t)s * PW_LEN + k] = make_float4((float)pk.a, (float)pk.b, (float)pk.c, (float)pk.d);
+                if (pw64) pw64[(size_t)s * PW_LEN + k] = make_double4(pk.a, pk.b, pk.c, pk.d);
                 pk = mul(pk, a);
             }
         }
@@ -513,6 +549,7 @@ int launch_unit_range(tfx_plan* p, int i, const float* in, int64_t ldin, float* 
     a.k.coef = reinterpret_cast<const float*>(p->dconst + u.off_coef);
     a.k.pw = reinterpret_cast<const float4*>(p->dconst + u.off_pw);
     a.k.taps = reinterpret_cast<const float*>(p->dconst + u.off_taps);
+    a.k.pw64 = u.hiq ? reinterpret_cast<const double4*>(p->dconst + u.off_pw64) : nullptr;
     a.sc.ticket = reinterpret_cast<unsigned*>(scratch);
     a.sc.flags = reinterpret_cast<unsigned*>(scratch + ALIGN);
     a.sc.carry = reinterpret_cast<Carry*>(scratch + ALIGN + u.flags_bytes);
@@ -835,7 +872,7 @@ int tfx_plan_create(tfx_plan** out, int64_t C, int64_t N, int64_t ld, const tfx_
 }  // extern "C"
 
 int tfx::plan_create_ex(tfx_plan** out, int64_t C, int64_t N, int64_t ld, const tfx_stage* st, int32_t nst,
-                        uint32_t flags, int tc_min_taps) {
+                        uint32_t flags, int tc_min_taps, bool allow_hiq) {
     if (!out) return TFX_ERR_INVALID;
     *out = nullptr;
     int rc = check_dims(C, N, ld);
@@ -852,6 +889,7 @@ int tfx::plan_create_ex(tfx_plan** out, int64_t C, int64_t N, int64_t ld, const 
     p->ld = ld;
     p->flags = flags;
     p->tc_min_taps = tc_min_taps > 0 ? tc_min_taps : TC_MIN_TAPS;
+    p->allow_hiq = allow_hiq;
     rc = build_plan(p, st, nst, true);
     if (rc != TFX_OK) {
         tfx_plan_destroy(p);
@@ -904,6 +942,7 @@ void tfx_plan_destroy(tfx_plan* p) {
     if (p->dconst || p->dstatus) cudaDeviceSynchronize();
     if (p->dconst) cudaFree(p->dconst);
     if (p->dstatus) cudaFree(p->dstatus);
+    if (p->dsec) cudaFree(p->dsec);
     delete p;
 }
 

@@ -34,6 +34,10 @@ struct HostUnit {
     size_t tc_smem_ws = 0;
     // cascade without an FIR: warp-per-tile scan (tiles of 32 * T_CHUNK samples)
     bool warp = false;
+    // a section with a pole of radius > 0.999: warp-tile scan with FP64
+    // cross-tile carries and an FP64 copy of the power table
+    bool hiq = false;
+    size_t off_pw64 = 0;
     // trainable plans: where each section's raw row (6 values) and the FIR's
     // taps sit in the flat coefficient-gradient array, the raw rows for the
     // a0 chain rule, and the unit's saved activations
@@ -82,6 +86,10 @@ struct tfx_plan {
     size_t bws_bytes = 0;     // backward workspace
     size_t b_scan = 0, b_part = 0, b_tmp = 0, b_gbuf = 0;  // backward workspace offsets
     int tc_min_taps = tfx::TC_MIN_TAPS;  // FIRs with at least this many taps go to the tensor cores
+    bool allow_hiq = true;               // route cascades with poles of radius > 0.999 to FP64 carries
+    // device-side coefficient updates (tfx_plan_update_sos): per-section descriptors
+    char* dsec = nullptr;
+    int nsec = -1;  // -1: not built yet
 };
 
 namespace tfx {
@@ -89,6 +97,10 @@ namespace tfx {
 void tc_geometry(HostUnit& u, int NB);
 // Create a plan with a tensor-core tap threshold other than the default.
 int plan_create_ex(tfx_plan** out, int64_t C, int64_t N, int64_t ld, const tfx_stage* st, int32_t nst,
-                   uint32_t flags, int tc_min_taps);
+                   uint32_t flags, int tc_min_taps, bool allow_hiq = true);
+// Pole radius above which a cascade's cross-tile carries run in FP64.
+constexpr double HIQ_RADIUS = 0.999;
+// Recompute the plan's section constants on the GPU from raw FP64 rows (design.cu).
+int plan_update_sections(tfx_plan* p, const double* rows_dev, cudaStream_t s);
 }  // namespace tfx
 

@@ -40,6 +40,7 @@ struct UnitConst {
     const float* coef; // [S][8]: b0 c1 c2 a1 a2 (a0-normalised; c1 = b1 - a1 b0, c2 = b2 - a2 b0)
     const float4* pw;  // [S][PW_LEN]: A^k, A = chunk transfer matrix (row-major 2x2)
     const float* taps; // [nkb*FIR_R] FP32 taps, zero-padded
+    const double4* pw64;  // cascades with a pole of radius > 0.999: the same powers in FP64, else null
 };
 
 // Look-back carry of one (tile, section): a 2-vector published with a status
@@ -239,6 +240,52 @@ __device__ __forceinline__ unsigned wait_carry(const Carry* p, float2& v, int* s
             return 0;
         }
     }
+}
+
+// FP64 carries (cascades with a pole of radius > 0.999): the same 16-byte
+// word, two doubles whose two lowest mantissa bits hold the status (a
+// perturbation of 2^-51 relative, far below the FP32 data).
+__device__ __forceinline__ void publish_carry64(Carry* p, unsigned status, double2 v) {
+    const unsigned long long x = (__double_as_longlong(v.x) & ~3ull) | status;
+    const unsigned long long y = (__double_as_longlong(v.y) & ~3ull) | status;
+    asm volatile("st.relaxed.gpu.global.v2.b64 [%0], {%1,%2};" ::"l"(p), "l"(x), "l"(y) : "memory");
+}
+
+__device__ __forceinline__ unsigned read_carry64(const Carry* p, double2& v) {
+    for (;;) {
+        unsigned long long x, y;
+        asm volatile("ld.relaxed.gpu.global.v2.b64 {%0,%1}, [%2];" : "=l"(x), "=l"(y) : "l"(p) : "memory");
+        if ((x & 3ull) == (y & 3ull)) {
+            v = make_double2(__longlong_as_double((long long)(x & ~3ull)), __longlong_as_double((long long)(y & ~3ull)));
+            return (unsigned)(x & 3ull);
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned wait_carry64(const Carry* p, double2& v, int* status) {
+    unsigned f = read_carry64(p, v);
+    if (f >= 1u) return f;
+    unsigned long long t0 = global_ns();
+    unsigned ns = 32;
+    for (;;) {
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
+        f = read_carry64(p, v);
+        if (f >= 1u) return f;
+        if (*(volatile int*)status != 0) return 0;
+        if (global_ns() - t0 > WAIT_LIMIT_NS) {
+            atomicCAS(status, 0, (int)TFX_ERR_TIMEOUT);
+            return 0;
+        }
+    }
+}
+
+__device__ __forceinline__ double2 mv2d(double4 m, double2 v) {
+    return make_double2(fma(m.x, v.x, m.y * v.y), fma(m.z, v.x, m.w * v.y));
+}
+__device__ __forceinline__ double4 mm2d(double4 a, double4 b) {
+    return make_double4(fma(a.x, b.x, a.y * b.z), fma(a.x, b.y, a.y * b.w), fma(a.z, b.x, a.w * b.z),
+                        fma(a.z, b.y, a.w * b.w));
 }
 
 // 2x2 row-major matrix (float4 = m00 m01 m10 m11) helpers

@@ -326,3 +326,43 @@ def test_long_fir_streamed_taps(mode):
         assert 1e-5 < rel < 1e-1, rel
     else:
         assert_close(got, ref, 1e-5, mode)
+
+
+def _resonator(r, th):
+    a = np.array([1.0, -2 * r * math.cos(th), r * r])
+    b = np.array([1.0, 0.0, -1.0])
+    w = np.linspace(0, math.pi, 65536)
+    z = np.exp(-1j * w)
+    H = (b[0] + b[1] * z + b[2] * z * z) / (a[0] + a[1] * z + a[2] * z * z)
+    return np.array([[*(b / np.max(np.abs(H))), *a]])
+
+
+@pytest.mark.parametrize("r", [0.9995, 0.9999, 0.99999])
+@pytest.mark.parametrize("th", [0.05, 0.5])
+def test_poles_beyond_0999_fp64_carries(r, th):
+    """Poles of radius > 0.999: the cascade runs the warp-tile scan with FP64
+    cross-tile carries and powers (FP32 carries measured 1.9e-4 at r = 0.99995
+    and 3.8e-4 at 0.99999 for a low-angle pole; FP64 carries <= 3.3e-5)."""
+    x = W.white_uniform(2, 1 << 20, 77)
+    rows = np.concatenate([_resonator(r, th), W.butter_sos(2, 2000.0, 48000.0)])
+    check(x, [("sos", rows)])
+
+
+def test_high_q_cascade_with_fused_and_tensor_core_firs():
+    # a short FIR behind a high-Q cascade is split into its own unit; a long
+    # one goes to the tensor cores as usual
+    x = W.white_uniform(2, 300000, 78)
+    rows = np.concatenate([_resonator(0.9999, 0.1), W.butter_sos(2, 3000.0, 48000.0)])
+    check(x, [("sos", rows), ("fir", W.fir_lowpass(31, 6000.0, W.FS))])
+    check(x, [("sos", rows), ("fir", W.fir_lowpass(513, 6000.0, W.FS))])
+
+
+def test_timeout_fp64_carries():
+    """The FP64-carry look-back gives up the same way: status word, no hang."""
+    from paper_2504_08624_gb300 import api, _native as N
+    x = torch.from_numpy(W.white_uniform(2, 4 * 1024 + 5, 19)).cuda()
+    p = api.Plan(2, 4 * 1024 + 5, [("sos", _resonator(0.9999, 0.2))], flags=N.TFX_PLAN_TEST_DROP_PUBLISH)
+    p.execute(x)
+    torch.cuda.synchronize()
+    assert p.get_error() == -5
+    p.close()
