@@ -24,6 +24,14 @@ TFX_PLAN_FIR_BF16_PLAIN = 4
 TFX_PLAN_FIR_BF16_SPLIT = 8
 TFX_PLAN_SCAN_WARP_TILES = 16
 TFX_PLAN_TRAINABLE = 32
+TFX_PLAN_FIR_FFT = 64
+
+
+def TFX_PLAN_FIR_FFT_LOG(m: int) -> int:
+    """Plan flag bits fixing the overlap-save transform size at 2^m points (m = 10..13)."""
+    return (int(m) & 15) << 16
+
+
 TFX_PLAN_TEST_DROP_PUBLISH = 256
 
 STATUS = {

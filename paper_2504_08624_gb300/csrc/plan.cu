@@ -3,6 +3,7 @@
 // the C-ABI entry points declared in include/tfx.h.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <list>
 #include <mutex>
@@ -26,6 +27,49 @@ void tfx::tc_geometry(HostUnit& u, int NB) {
     u.tc_smem = (size_t)u.a_chunks * 128 * 2 + (size_t)16 * u.rows * 16 * 2 + 16;
 }
 
+
+namespace {
+
+// FFT size for an L-tap FIR by overlap-save: the M = 2^m (m = 10..13) with
+// the least estimated work per output, M (m + 3) / (M - L + 1) (m radix-2
+// levels of butterflies plus the loads, product and stores), among those
+// whose block B = M - (L - 1) is at least M/4; `force` (10..13) picks M when
+// that M qualifies.  0 if none does.
+int fft_size_for(int L, int force) {
+    if (force >= 10 && force <= 13 && (1 << force) - (L - 1) >= (1 << force) / 4) return 1 << force;
+    int best = 0;
+    double cost = 0.0;
+    for (int m = 10; m <= 13; ++m) {
+        const int M = 1 << m, B = M - (L - 1);
+        if (B < M / 4) continue;
+        const double c = (double)M * (m + 3) / B;
+        if (best == 0 || c < cost) best = M, cost = c;
+    }
+    return best;
+}
+
+// In-place iterative radix-2 FFT (FP64), natural order in and out.
+void host_fft(std::vector<std::complex<double>>& a) {
+    const size_t n = a.size();
+    for (size_t i = 1, j = 0; i < n; ++i) {
+        size_t bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) std::swap(a[i], a[j]);
+    }
+    for (size_t len = 2; len <= n; len <<= 1) {
+        const double ang = -2.0 * M_PI / (double)len;
+        for (size_t i = 0; i < n; i += len)
+            for (size_t k = 0; k < len / 2; ++k) {
+                const std::complex<double> w(std::cos(ang * k), std::sin(ang * k));
+                const std::complex<double> u = a[i + k], v = a[i + k + len / 2] * w;
+                a[i + k] = u + v;
+                a[i + k + len / 2] = u - v;
+            }
+    }
+}
+
+}  // namespace
 
 namespace {
 
@@ -253,7 +297,28 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         std::vector<HostUnit> out;
         for (HostUnit& u : p->units) {
             HostUnit f = u;
-            if (u.L >= p->tc_min_taps && (f.S = 0, f.sec.clear(), choose_tc(f))) {
+            const int fftM = (p->flags & TFX_PLAN_FIR_FFT) && u.L >= 64
+                                 ? fft_size_for(u.L, (int)((p->flags & TFX_PLAN_FIR_FFT_LOG_MASK) >> 16))
+                                 : 0;
+            if (fftM > 0) {
+                f.S = 0;
+                f.sec.clear();
+                f.hiq = false;
+                f.dst.clear();
+                f.raw.clear();
+                f.fft = true;
+                f.fft_M = fftM;
+                f.fft_m = 0;
+                while ((1 << f.fft_m) < fftM) ++f.fft_m;
+                f.fft_B = fftM - (u.L - 1);
+                if (u.S > 0) {
+                    HostUnit sos = u;
+                    sos.L = 0;
+                    sos.taps.clear();
+                    out.push_back(sos);
+                }
+                out.push_back(f);
+            } else if (u.L >= p->tc_min_taps && (f.S = 0, f.sec.clear(), choose_tc(f))) {
                 f.tc = true;
                 if (u.S > 0) {
                     HostUnit sos = u;
@@ -292,6 +357,12 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
             u.off_alo = off;
             off = align_up(off + (size_t)u.a_chunks * 128);
         }
+        if (u.fft) {
+            u.off_H = off;
+            off = align_up(off + (size_t)u.fft_M * sizeof(float2));
+            u.off_tw = off;
+            off = align_up(off + (size_t)(u.fft_M / 2) * sizeof(float2));
+        }
         if (p->train && u.S > 0) {
             u.off_raw = off;
             off = align_up(off + (size_t)u.S * 6 * sizeof(double));
@@ -328,6 +399,25 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         }
         float* taps = reinterpret_cast<float*>(host.data() + u.off_taps);
         for (int k = 0; k < u.L; ++k) taps[k] = (float)u.taps[k];
+        if (u.fft) {
+            // spectrum of h zero-padded to M, scaled by 1/M (the inverse FFT's
+            // normalisation), in bit-reversed order; twiddles e^(-2 pi i k / M)
+            const int M = u.fft_M;
+            std::vector<std::complex<double>> Hc(M, 0.0);
+            for (int k = 0; k < u.L; ++k) Hc[k] = u.taps[k];
+            host_fft(Hc);
+            float2* Hd = reinterpret_cast<float2*>(host.data() + u.off_H);
+            for (int k = 0; k < M; ++k) {
+                int r = 0;
+                for (int b = 0; b < u.fft_m; ++b) r |= ((k >> b) & 1) << (u.fft_m - 1 - b);
+                Hd[k] = make_float2((float)(Hc[r].real() / M), (float)(Hc[r].imag() / M));
+            }
+            float2* tw = reinterpret_cast<float2*>(host.data() + u.off_tw);
+            for (int k = 0; k < M / 2; ++k) {
+                const double ang = -2.0 * M_PI * (double)k / (double)M;
+                tw[k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+            }
+        }
         if (p->train && u.S > 0) {
             std::memcpy(host.data() + u.off_raw, u.raw.data(), (size_t)u.S * 6 * sizeof(double));
             std::memcpy(host.data() + u.off_dst, u.dst.data(), (size_t)u.S * sizeof(int64_t));
@@ -389,6 +479,10 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         if (cudaMalloc(&p->dstatus, sizeof(int)) != cudaSuccess) return TFX_ERR_NOMEM;
         if (cudaMemset(p->dstatus, 0, sizeof(int)) != cudaSuccess) return TFX_ERR_CUDA;
         for (HostUnit& u : p->units) {
+            if (u.fft) {
+                if (prepare_fir_fft(u.fft_M) != cudaSuccess) return TFX_ERR_UNSUPPORTED;
+                continue;
+            }
             if (u.tc) {
                 if (u.tc_variant == 1) {
                     if (prepare_fir_tc_ws(u.tc_smem_ws) != cudaSuccess) return TFX_ERR_UNSUPPORTED;
@@ -422,6 +516,10 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
             u.ntt = p->N > 0 ? (p->N + 128 * u.NB - 1) / (128 * u.NB) : 0;
             continue;
         }
+        if (u.fft) {
+            u.ntt = p->N > 0 ? (p->N + u.fft_B - 1) / u.fft_B : 0;
+            continue;
+        }
         if (u.warp) u.ntt = p->N > 0 ? (p->N + WARP_TILE - 1) / WARP_TILE : 0;
         const int H = u.L > 0 ? u.L - 1 : 0;
         u.tail_len = u.L > 0 ? (H < TILE ? H : TILE) : 0;
@@ -438,7 +536,7 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
     p->scratch_bytes = hdr + tails;
     p->buf_bytes = align_up((size_t)p->C * (size_t)p->N * sizeof(float));
     size_t nbuf = p->units.size() > 2 ? 2 : (p->units.size() == 2 ? 1 : 0);
-    if (p->units.size() == 1 && p->units[0].tc) nbuf = 1;  // input copy for in-place operation
+    if (p->units.size() == 1 && (p->units[0].tc || p->units[0].fft)) nbuf = 1;  // input copy for in-place operation
     p->ws_fused = p->scratch_bytes + nbuf * p->buf_bytes;
     p->ws_plain = (nst > 0 ? 2 : 0) * p->buf_bytes;
 
@@ -503,6 +601,29 @@ int launch_unit_range(tfx_plan* p, int i, const float* in, int64_t ldin, float* 
     const HostUnit& u = p->units[i];
     in += c0 * ldin;
     out += c0 * ldout;
+    if (u.fft) {
+        FirFftArgs f{};
+        f.x = in;
+        f.ldx = ldin;
+        f.y = out;
+        f.ldy = ldout;
+        if (f.x == f.y) {  // blocks read their predecessors' input: copy it first
+            if (launch_copy_rows(f.x, copy_buf, Cg, p->N, f.ldx, p->N, s) != cudaSuccess) return TFX_ERR_CUDA;
+            f.x = copy_buf;
+            f.ldx = p->N;
+        }
+        f.C = Cg;
+        f.N = p->N;
+        f.L = u.L;
+        f.M = u.fft_M;
+        f.m = u.fft_m;
+        f.B = u.fft_B;
+        f.nbpc = u.ntt;
+        f.nb = Cg * u.ntt;
+        f.H = reinterpret_cast<const float2*>(p->dconst + u.off_H);
+        f.tw = reinterpret_cast<const float2*>(p->dconst + u.off_tw);
+        return launch_fir_fft(f, s) == cudaSuccess ? TFX_OK : TFX_ERR_CUDA;
+    }
     if (u.tc) {
         FirTcArgs f{};
         f.x = in;
@@ -880,7 +1001,8 @@ int tfx::plan_create_ex(tfx_plan** out, int64_t C, int64_t N, int64_t ld, const 
     rc = validate_stages(st, nst);
     if (rc != TFX_OK) return rc;
     if (flags & ~(TFX_PLAN_FIR_CUDA_CORES | TFX_PLAN_UNFUSED | TFX_PLAN_FIR_BF16_PLAIN | TFX_PLAN_FIR_BF16_SPLIT |
-                  TFX_PLAN_SCAN_WARP_TILES | TFX_PLAN_TRAINABLE | TFX_PLAN_TEST_DROP_PUBLISH))
+                  TFX_PLAN_SCAN_WARP_TILES | TFX_PLAN_TRAINABLE | TFX_PLAN_FIR_FFT | TFX_PLAN_FIR_FFT_LOG_MASK |
+                  TFX_PLAN_TEST_DROP_PUBLISH))
         return TFX_ERR_INVALID;
     tfx_plan* p = new (std::nothrow) tfx_plan();
     if (!p) return TFX_ERR_NOMEM;

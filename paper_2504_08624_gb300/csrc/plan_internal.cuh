@@ -38,6 +38,10 @@ struct HostUnit {
     // cross-tile carries and an FP64 copy of the power table
     bool hiq = false;
     size_t off_pw64 = 0;
+    // FIR by FFT overlap-save (TFX_PLAN_FIR_FFT)
+    bool fft = false;
+    int fft_M = 0, fft_m = 0, fft_B = 0;
+    size_t off_H = 0, off_tw = 0;
     // trainable plans: where each section's raw row (6 values) and the FIR's
     // taps sit in the flat coefficient-gradient array, the raw rows for the
     // a0 chain rule, and the unit's saved activations

@@ -146,6 +146,20 @@ struct FirTcArgs {
     int* status;
 };
 
+// FIR by FFT overlap-save: blocks of B = M - (L - 1) outputs, two blocks per CTA.
+struct FirFftArgs {
+    const float* x;
+    float* y;
+    int64_t ldx, ldy;
+    int64_t C, N;
+    int L;
+    int M, m;          // FFT size M = 2^m (complex points)
+    int B;             // outputs per block
+    int64_t nbpc, nb;  // blocks per channel, blocks in all
+    const float2* H;   // [M] spectrum of h (zero-padded), bit-reversed order, scaled by 1/M
+    const float2* tw;  // [M/2] e^(-2 pi i k / M)
+};
+
 struct BatchFir {
     FirTcArgs a;           // x and y filled in from the offsets below
     int x_sel, y_sel;
@@ -314,6 +328,9 @@ cudaError_t prepare_fir_tc_long(size_t smem);
 size_t fir_tc_long_smem(int rows);
 constexpr int TC_KBLK = 64;  // K-steps per streamed tap block
 cudaError_t launch_fir_tc(const FirTcArgs& a, cudaStream_t s);
+size_t fir_fft_smem_bytes(int M);
+cudaError_t prepare_fir_fft(int M);
+cudaError_t launch_fir_fft(const FirFftArgs& a, cudaStream_t s);
 cudaError_t launch_fir_tc_batched(const BatchFir* units, const int64_t* prefix, int nunits, int64_t tiles,
                                   BatchBases bases, size_t smem, cudaStream_t s);
 cudaError_t prepare_fir_tc_batched(size_t smem);

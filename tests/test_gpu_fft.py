@@ -1,0 +1,143 @@
+"""FFT overlap-save FIR path (TFX_PLAN_FIR_FFT) against the FP64 oracle.
+
+Block sizes: an L-tap FIR uses M = 2^m complex points (1024..16384) and
+B = M - (L - 1) outputs per block, two blocks per CTA (real and imaginary
+parts of one transform).  The cases cover one partial block, an odd block
+count (the last CTA's second block is empty), lengths that end one sample
+before / on / after a block boundary, channel counts that put the two blocks
+of a CTA in different channels, in-place operation, padded strides, a cascade
+ahead of the FFT unit, and the gradient of a trainable plan (the transposed
+FIR runs on the same FFT unit).  Tolerance: 1e-5 of each channel's peak, as
+for every FIR-only chain."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2504_08624_gb300 import workloads as W
+from tests.gpu_util import assert_close, oracle_chain, tol_for
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _fft_block(L):
+    """(M, B) the plan's cost model picks: least M (m + 3) / B over m = 10..13
+    with B = M - (L - 1) >= M/4."""
+    best = None
+    for m in range(10, 14):
+        M = 1 << m
+        B = M - (L - 1)
+        if B >= M // 4 and (best is None or M * (m + 3) / B < best[0]):
+            best = (M * (m + 3) / B, M, B)
+    return best[1], best[2]
+
+
+def run_fft(x, stages, inplace=False, ld=None, flags=0):
+    from paper_2504_08624_gb300 import _native as N_
+    from paper_2504_08624_gb300 import api
+    C, Ns = x.shape
+    ld = Ns if ld is None else ld
+    buf = torch.zeros(C * ld + 8, dtype=torch.float32, device="cuda")
+    xv = buf[:C * ld].view(C, ld)[:, :Ns]
+    xv.copy_(torch.from_numpy(x))
+    p = api.Plan(C, Ns, stages, ld=ld, flags=N_.TFX_PLAN_FIR_FFT | flags)
+    y = xv if inplace else torch.zeros_like(buf)[:C * ld].view(C, ld)[:, :Ns]
+    p.execute(xv, y)
+    torch.cuda.synchronize()
+    assert p.get_error() == 0
+    p.close()
+    return y.cpu().numpy().astype(np.float64)
+
+
+def check_fft(x, stages, tol=None, **kw):
+    got = run_fft(x, stages, **kw)
+    ref = oracle_chain(x, stages)
+    return assert_close(got, ref, tol or tol_for(stages), str(kw))
+
+
+def _taps(L, seed):
+    return np.random.default_rng(seed).standard_normal(L) / math.sqrt(L)
+
+
+@pytest.mark.parametrize("L", [64, 65, 129, 257, 335, 1025, 2049, 4097, 6145])
+def test_fft_fir_lengths(L):
+    M, B = _fft_block(L)
+    for Ns in (1, B - 1, B, B + 1, 3 * B + 17):
+        x = W.white_gauss(3, Ns, 31)
+        check_fft(x, [("fir", _taps(L, L))])
+
+
+@pytest.mark.parametrize("C", [1, 2, 5])
+def test_fft_fir_blocks_across_channels(C):
+    L = 1025
+    M, B = _fft_block(L)
+    x = W.pink(C, 2 * B + 300, 32)
+    check_fft(x, [("fir", W.fir_lowpass(L, 4000.0, 48000.0))])
+
+
+@pytest.mark.parametrize("inplace", [False, True])
+def test_fft_fir_inplace_and_stride(inplace):
+    x = W.white_gauss(3, 50000, 33)
+    check_fft(x, [("fir", _taps(513, 5))], inplace=inplace, ld=50000 + 37)
+
+
+def test_fft_fir_behind_cascade():
+    """Cascade then a long FIR: the cascade runs as its own unit, then the FFT unit."""
+    wl = W.multichannel_fused()
+    x = wl.make_signal(3, 40000)
+    check_fft(x, wl.stages, wl.tol)
+
+
+def test_fft_fir_lowpass_and_bandpass():
+    x = W.pink(2, 100000, 34)
+    for h in (W.fir_lowpass(1025, 2000.0, 48000.0, ("kaiser", 8.0)),
+              W.fir_bandpass(4097, 300.0, 3000.0, 48000.0, ("kaiser", 10.0)),
+              W.fir_highpass(257, 8000.0, 48000.0)):
+        check_fft(x, [("fir", h)])
+
+
+def test_fft_fir_empty():
+    from paper_2504_08624_gb300 import _native as N_
+    from paper_2504_08624_gb300 import api
+    for C, Ns in ((0, 100), (2, 0)):
+        p = api.Plan(C, Ns, [("fir", _taps(300, 1))], flags=N_.TFX_PLAN_FIR_FFT)
+        x = torch.zeros(C, Ns, device="cuda")
+        y = torch.zeros_like(x)
+        p.execute(x, y)
+        torch.cuda.synchronize()
+        p.close()
+
+
+def test_fft_fir_too_long_stays_on_tensor_cores():
+    """Beyond 6145 taps no transform size leaves a block of M/4: the FIR runs
+    on the Toeplitz GEMM path, still within tolerance."""
+    x = W.white_gauss(2, 30000, 35)
+    check_fft(x, [("fir", _taps(6146, 9))])
+
+
+@pytest.mark.parametrize("m", [10, 11, 12, 13])
+def test_fft_fir_every_transform_size(m):
+    """Each transform size (radix-4, -8, -16 and -2 first passes) on a FIR it
+    can hold, with a ragged tail."""
+    from paper_2504_08624_gb300 import _native as N_
+    L = (1 << m) // 4 + 1
+    B = (1 << m) - (L - 1)
+    x = W.white_gauss(3, 5 * B + 77, 38)
+    check_fft(x, [("fir", _taps(L, m))], flags=N_.TFX_PLAN_FIR_FFT_LOG(m))
+    x = W.white_gauss(2, 4 * B, 39)
+    check_fft(x, [("fir", _taps(100, m))], flags=N_.TFX_PLAN_FIR_FFT_LOG(m))
+
+
+@pytest.mark.parametrize("L", [257, 700])
+def test_fft_fir_gradient_matches_oracle(L):
+    """Trainable plan with the FFT flag: the input gradient's transposed FIR
+    runs on the FFT unit; y, dx and every coefficient gradient against the
+    oracle VJP."""
+    from paper_2504_08624_gb300 import _native as N_
+    from tests.test_gpu_grad import check_grad
+    rows = W.random_stable_sos(2, 7, 0.3, 0.95)
+    stages = [("sos", rows), ("fir", _taps(L, 3)), ("sos", W.random_stable_sos(1, 8, 0.3, 0.9))]
+    x = W.white_gauss(3, 30000, 36)
+    g = W.white_gauss(3, 30000, 37)
+    check_grad(x, g, stages, flags=N_.TFX_PLAN_FIR_FFT)
