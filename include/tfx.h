@@ -81,14 +81,18 @@ typedef struct {
  * as a unit of its own and cascades as warp-tile scans of at most 8 sections
  * (longer cascades are split); tfx_plan_execute still works on such a plan. */
 #define TFX_PLAN_TRAINABLE 32u
-/* FIRs of 64 to 6145 taps by FFT overlap-save instead of the tensor-core
- * Toeplitz GEMM: blocks of B = M - (L - 1) outputs, M = 1024..8192 points,
- * two blocks per complex transform, hand-written register-resident radix-16
- * FFTs (FP32; the error is ~log2(M) eps of each block's energy rather than
- * per product).  Longer FIRs stay on the tensor cores.  The transform size
- * is chosen per FIR from a cost model unless TFX_PLAN_FIR_FFT_LOG(m) fixes
- * M = 2^m (m = 10..13; FIRs for which the block would be under M/4 keep the
- * automatic size). */
+/* FIRs of 64 taps or more by FFT overlap-save instead of the tensor-core
+ * Toeplitz GEMM, with hand-written register-resident radix-16 FFTs of
+ * M = 1024..8192 points (FP32; the error is ~log2(M) eps of each block's
+ * energy rather than per product).  Up to 6145 taps: blocks of
+ * B = M - (L - 1) outputs, two blocks per complex transform.  Longer:
+ * partitioned overlap-save, h cut into P = ceil(L / (M/2)) partitions, every
+ * input segment transformed once (two channels per complex transform) into a
+ * workspace of ceil(C/2) x ceil(N / (M/2)) x M complex values, and each output
+ * block the inverse transform of the sum of the P partition products (two
+ * launches).  The transform size is chosen per FIR from a cost model unless
+ * TFX_PLAN_FIR_FFT_LOG(m) fixes M = 2^m (m = 10..13; a FIR for which a single
+ * block would be under M/4 is partitioned at that size). */
 #define TFX_PLAN_FIR_FFT 64u
 #define TFX_PLAN_FIR_FFT_LOG(m) ((uint32_t)(m) << 16)
 #define TFX_PLAN_FIR_FFT_LOG_MASK (15u << 16)

@@ -1,5 +1,12 @@
 // FIR by FFT overlap-save (the FFT route for long FIRs): y[n] = sum_k h[k] x[n-k].
 //
+// Two schemes share the transforms.  Single-block (L - 1 < 3M/4), below:
+// each block's segment is transformed, multiplied by the spectrum of h and
+// transformed back.  Partitioned (any L): h is cut into P partitions of
+// B = M/2 taps, every input segment is transformed once (k_fir_fft_spec) and
+// block b's spectrum is the sum over p of H_p Z_(b-p) (k_fir_fft_conv), with
+// the two channels of a pair as the real and imaginary parts.
+//
 // Blocks of B = M - (L - 1) outputs; block b reads the input segment
 // x[n0 - (L - 1), n0 + B) (zero outside the signal), whose circular
 // convolution with h (zero-padded to M) equals the linear one in its last B
@@ -24,10 +31,10 @@
 // product needs no permutation, and the inverse runs the passes backwards
 // (conjugate twiddles, then the DIT G-point DFT), ending in natural order in
 // the layout the input was loaded in: point t + T*j in register j, so both the
-// input loads and the output stores are coalesced.  A group's twiddle
-// w^k is applied as the product of w^(2^b) over the set bits b of k, each
-// read from a table of e^(-2 pi i k / M), k < M/2, computed in FP64 at plan
-// time (at most four roundings per point and pass).
+// input loads and the output stores are coalesced.  Each pass with twiddles
+// reads them from its own table, [slot q - 1][group position i], computed in
+// FP64 at plan time and rounded once: consecutive threads read consecutive
+// words, and every point takes one complex multiply per pass.
 #include "tfx_common.cuh"
 
 namespace tfx {
@@ -101,33 +108,17 @@ __device__ __forceinline__ void dft_dit(float2 (&v)[16]) {
     if constexpr (G >= 16) stage<G, ST, OFF, 8, true>(v);
 }
 
-__host__ __device__ constexpr int brev(int q, int bits) {
-    int r = 0;
-    for (int b = 0; b < bits; ++b) r |= ((q >> b) & 1) << (bits - 1 - b);
-    return r;
-}
-
-// Multiply every slot q of the group v[OFF + q*ST] whose exponent bitrev(q)
-// has bit B set by w (INV: by conj(w)).
-template <int G, int ST, int OFF, int B, bool INV, int Q = 1>
-__device__ __forceinline__ void apply_bit(float2 (&v)[16], float2 w) {
+// Multiply slot q (q = Q..G-1) of the group v[OFF + q*ST] by the pass
+// twiddle w_S^(i * bitrev(q)) (INV: its conjugate), read from the pass's
+// table at [q - 1][i] (row length `sub`): consecutive i are consecutive words.
+template <int G, int ST, int OFF, bool INV, int Q = 1>
+__device__ __forceinline__ void twiddle_group(float2 (&v)[16], const float2* __restrict__ tp, int sub) {
     if constexpr (Q < G) {
-        constexpr int RB = G == 16 ? 4 : G == 8 ? 3 : G == 4 ? 2 : 1;
-        constexpr int k = brev(Q, RB), i = OFF + Q * ST;
-        if constexpr ((k >> B) & 1) v[i] = INV ? cmulc(v[i], w) : cmul(v[i], w);
-        apply_bit<G, ST, OFF, B, INV, Q + 1>(v, w);
+        constexpr int i = OFF + Q * ST;
+        const float2 w = __ldg(tp + (Q - 1) * sub);
+        v[i] = INV ? cmulc(v[i], w) : cmul(v[i], w);
+        twiddle_group<G, ST, OFF, INV, Q + 1>(v, tp, sub);
     }
-}
-
-// Multiply slot q of the group v[OFF + q*ST] by w^bitrev(q) (INV: its
-// conjugate) in factored form: w^k = prod over the set bits b of k of
-// w^(2^b) = tw[2^b * e]; no table of all powers is held in registers.
-template <int G, int ST, int OFF, bool INV>
-__device__ __forceinline__ void twiddle_group(float2 (&v)[16], const float2* __restrict__ tw, int e) {
-    if constexpr (G >= 16) apply_bit<G, ST, OFF, 3, INV>(v, __ldg(tw + 8 * e));
-    if constexpr (G >= 8) apply_bit<G, ST, OFF, 2, INV>(v, __ldg(tw + 4 * e));
-    if constexpr (G >= 4) apply_bit<G, ST, OFF, 1, INV>(v, __ldg(tw + 2 * e));
-    apply_bit<G, ST, OFF, 0, INV>(v, __ldg(tw + e));
 }
 
 // Padded shared-memory index: one float2 of padding per 16.
@@ -141,35 +132,53 @@ struct FftShape {
     static constexpr int G0 = R0 ? 1 << R0 : 16;
     static constexpr int NP = R0 ? 1 + LOGM / 4 : LOGM / 4;  // passes
     static constexpr int span(int p) { return p == 0 ? M : (M / G0) >> (4 * (p - 1)); }
+    static constexpr int radix(int p) { return p == 0 ? G0 : 16; }
+    static constexpr int sub(int p) { return span(p) / radix(p); }
+    // offset of pass p's twiddle table ((radix - 1) rows of `sub` entries;
+    // passes with sub = 1 have none)
+    static constexpr int tw_off(int p) {
+        int o = 0;
+        for (int q = 0; q < p; ++q)
+            if (sub(q) > 1) o += (radix(q) - 1) * sub(q);
+        return o;
+    }
 };
 
-// Position of register j of thread t in pass P.  Pass 0 (span M): point
-// t + T*j.  A radix-16 pass over span S (sub = S/16): point
-// (t / sub) * S + t % sub + j * sub.
+// Padded shared-memory position of register j of thread t in pass P, as
+// base(t) + j * STRIDE.  Pass 0 (span M): point t + T*j.  A radix-16 pass over
+// span S (sub = S/16, which is 256, 16 or 1): point (t / sub) * S + t % sub +
+// j * sub; with sub a multiple of 16 the padding adds j * sub/16, and with
+// sub = 1 the point is 16t + j, padded 17t + j.
 template <int LOGM, int P>
-__device__ __forceinline__ int ppos(int t, int j) {
+struct Layout {
     using F = FftShape<LOGM>;
-    if constexpr (P == 0) {
-        return t + F::T * j;
-    } else {
-        constexpr int S = F::span(P), sub = S / 16;
-        return (t / sub) * S + (t % sub) + j * sub;
+    static constexpr int S = F::span(P), SUB = P == 0 ? F::T : S / 16;
+    static_assert(SUB == 1 || SUB % 16 == 0, "pass layout");
+    static constexpr int STRIDE = SUB == 1 ? 1 : SUB + SUB / 16;
+    __device__ static __forceinline__ int base(int t) {
+        if constexpr (P == 0) {
+            return pad(t);
+        } else if constexpr (SUB == 1) {
+            return 17 * t;
+        } else {
+            return pad((t / SUB) * S + t % SUB);
+        }
     }
-}
+};
 
 // First pass when G0 < 16: groups c < 16/G0, slot q of group c in register
 // c + q*(16/G0), group position i = t + T*c.
 template <int LOGM, bool INV, int C = 0>
 __device__ __forceinline__ void first_groups(float2 (&v)[16], const float2* __restrict__ tw, int t) {
     using F = FftShape<LOGM>;
-    constexpr int G = F::G0, NG = 16 / G;
+    constexpr int G = F::G0, NG = 16 / G, sub = F::M / G;
     if constexpr (C < NG) {
-        const int e = t + F::T * C;  // i * (M / S) with S = M
+        const float2* tp = tw + t + F::T * C;
         if constexpr (!INV) {
             dft_dif<G, NG, C>(v);
-            twiddle_group<G, NG, C, false>(v, tw, e);
+            twiddle_group<G, NG, C, false>(v, tp, sub);
         } else {
-            twiddle_group<G, NG, C, true>(v, tw, e);
+            twiddle_group<G, NG, C, true>(v, tp, sub);
             dft_dit<G, NG, C>(v);
         }
         first_groups<LOGM, INV, C + 1>(v, tw, t);
@@ -180,15 +189,15 @@ template <int LOGM, int P, bool INV>
 __device__ __forceinline__ void run_pass(float2 (&v)[16], const float2* __restrict__ tw, int t) {
     using F = FftShape<LOGM>;
     if constexpr (P == 0 && F::R0 != 0) {
-        first_groups<LOGM, INV>(v, tw, t);
+        first_groups<LOGM, INV>(v, tw + F::tw_off(0), t);
     } else {
-        constexpr int S = F::span(P), sub = S / 16;
-        const int e = (t % sub) * (F::M / S);
+        constexpr int sub = F::sub(P);
+        const float2* tp = tw + F::tw_off(P) + t % sub;
         if constexpr (!INV) {
             dft_dif<16, 1, 0>(v);
-            if constexpr (sub > 1) twiddle_group<16, 1, 0, false>(v, tw, e);
+            if constexpr (sub > 1) twiddle_group<16, 1, 0, false>(v, tp, sub);
         } else {
-            if constexpr (sub > 1) twiddle_group<16, 1, 0, true>(v, tw, e);
+            if constexpr (sub > 1) twiddle_group<16, 1, 0, true>(v, tp, sub);
             dft_dit<16, 1, 0>(v);
         }
     }
@@ -197,11 +206,13 @@ __device__ __forceinline__ void run_pass(float2 (&v)[16], const float2* __restri
 // Move the points from pass P's layout to pass Q's through shared memory.
 template <int LOGM, int P, int Q>
 __device__ __forceinline__ void exchange(float2 (&v)[16], float2* sb, int t) {
+    float2* w = sb + Layout<LOGM, P>::base(t);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) sb[pad(ppos<LOGM, P>(t, j))] = v[j];
+    for (int j = 0; j < 16; ++j) w[j * Layout<LOGM, P>::STRIDE] = v[j];
     __syncthreads();
+    const float2* r = sb + Layout<LOGM, Q>::base(t);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = sb[pad(ppos<LOGM, Q>(t, j))];
+    for (int j = 0; j < 16; ++j) v[j] = r[j * Layout<LOGM, Q>::STRIDE];
     __syncthreads();
 }
 
@@ -223,6 +234,44 @@ __device__ __forceinline__ void inverse_from(float2 (&v)[16], const float2* __re
     }
 }
 
+// Two segments as the real and imaginary parts of z: point n = t + T*j is
+// x0[s0 + n] (re) and x1[s1 + n] (im), zero outside [0, N) or when !live1.
+template <int LOGM>
+__device__ __forceinline__ void load_pair(float2 (&v)[16], const float* x0, const float* x1, bool live1, int64_t s0,
+                                          int64_t s1, int64_t N, int t) {
+    using F = FftShape<LOGM>;
+    if (live1 && s0 >= 0 && s1 >= 0 && s0 + F::M <= N && s1 + F::M <= N) {
+        const float* p0 = x0 + s0 + t;
+        const float* p1 = x1 + s1 + t;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = make_float2(__ldg(p0 + F::T * j), __ldg(p1 + F::T * j));
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int64_t n0 = s0 + t + F::T * j, n1 = s1 + t + F::T * j;
+            v[j].x = (n0 >= 0 && n0 < N) ? __ldg(x0 + n0) : 0.f;
+            v[j].y = (live1 && n1 >= 0 && n1 < N) ? __ldg(x1 + n1) : 0.f;
+        }
+    }
+}
+
+// Points n >= first of each segment are outputs n - first of its block: the
+// real parts to y0[0, m0), the imaginary parts to y1[0, m1).
+template <int LOGM>
+__device__ __forceinline__ void store_pair(const float2 (&v)[16], float* y0, float* y1, int first, int64_t m0,
+                                           int64_t m1, int t) {
+    using F = FftShape<LOGM>;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const int o = t + F::T * j - first;
+        if (o >= 0) {
+            if (o < m0) y0[o] = v[j].x;
+            if (o < m1) y1[o] = v[j].y;
+        }
+    }
+}
+
+// Single-block overlap-save: CTA k transforms blocks 2k and 2k + 1.
 template <int LOGM>
 __global__ void __launch_bounds__((1 << LOGM) / 16) k_fir_fft(FirFftArgs a) {
     using F = FftShape<LOGM>;
@@ -233,17 +282,8 @@ __global__ void __launch_bounds__((1 << LOGM) / 16) k_fir_fft(FirFftArgs a) {
     const int64_t c0 = k0 / a.nbpc, c1 = live1 ? (k0 + 1) / a.nbpc : c0;
     const int64_t n00 = (k0 % a.nbpc) * (int64_t)a.B, n01 = live1 ? ((k0 + 1) % a.nbpc) * (int64_t)a.B : 0;
     const int Hh = a.L - 1;
-    const float* x0 = a.x + c0 * a.ldx;
-    const float* x1 = a.x + c1 * a.ldx;
     float2 v[16];
-    // point n = t + T*j is sample n0 - (L - 1) + n: re = block k0, im = block k0 + 1
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        const int n = t + F::T * j;
-        const int64_t s0 = n00 - Hh + n, s1 = n01 - Hh + n;
-        v[j].x = (s0 >= 0 && s0 < a.N) ? __ldg(x0 + s0) : 0.f;
-        v[j].y = (live1 && s1 >= 0 && s1 < a.N) ? __ldg(x1 + s1) : 0.f;
-    }
+    load_pair<LOGM>(v, a.x + c0 * a.ldx, a.x + c1 * a.ldx, live1, n00 - Hh, n01 - Hh, a.N, t);
     forward_from<LOGM, 0>(v, a.tw, sb, t);
     // spectrum product: thread t holds positions 16t .. 16t + 15
     const float4* h4 = reinterpret_cast<const float4*>(a.H) + 8 * t;
@@ -254,32 +294,92 @@ __global__ void __launch_bounds__((1 << LOGM) / 16) k_fir_fft(FirFftArgs a) {
         v[2 * q + 1] = cmul(v[2 * q + 1], make_float2(h.z, h.w));
     }
     inverse_from<LOGM, F::NP - 1>(v, a.tw, sb, t);
-    // the last B points of each segment are the block's outputs
     const int64_t m0 = a.N - n00 < a.B ? a.N - n00 : a.B;
     const int64_t m1 = live1 ? (a.N - n01 < a.B ? a.N - n01 : a.B) : 0;
-    float* y0 = a.y + c0 * a.ldy + n00;
-    float* y1 = a.y + c1 * a.ldy + n01;
+    store_pair<LOGM>(v, a.y + c0 * a.ldy + n00, a.y + c1 * a.ldy + n01, Hh, m0, m1, t);
+}
+
+// Partitioned overlap-save, step 1: the spectrum of segment b of a channel
+// pair, x[(b - 1) B, (b + 1) B) of channels 2r (re) and 2r + 1 (im), stored in
+// the transform's output order (thread t's 16 points contiguous).
+template <int LOGM>
+__global__ void __launch_bounds__((1 << LOGM) / 16) k_fir_fft_spec(FirFftArgs a) {
+    using F = FftShape<LOGM>;
+    extern __shared__ float2 sb[];
+    const int t = threadIdx.x;
+    const int64_t pb = blockIdx.x, r = pb / a.nbpc, b = pb % a.nbpc;
+    const int64_t c0 = 2 * r;
+    const bool live1 = c0 + 1 < a.C;
+    const float* x0 = a.x + c0 * a.ldx;
+    const int64_t s0 = (b - 1) * (int64_t)a.B;
+    float2 v[16];
+    load_pair<LOGM>(v, x0, live1 ? x0 + a.ldx : x0, live1, s0, s0, a.N, t);
+    forward_from<LOGM, 0>(v, a.tw, sb, t);
+    float4* z = reinterpret_cast<float4*>(a.Z + pb * F::M) + 8 * t;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        const int o = t + F::T * j - Hh;  // output index within the block
-        if (o >= 0) {
-            if (o < m0) y0[o] = v[j].x;
-            if (o < m1) y1[o] = v[j].y;
+    for (int q = 0; q < 8; ++q) z[q] = make_float4(v[2 * q].x, v[2 * q].y, v[2 * q + 1].x, v[2 * q + 1].y);
+}
+
+// Partitioned overlap-save, step 2: block b of a channel pair is the inverse
+// transform of sum over partitions p <= b of H_p Z_(b-p) (h split into P
+// partitions of B taps, h_p[k] = h[pB + k]), whose last B points are outputs
+// [bB, (b + 1) B).
+template <int LOGM>
+__global__ void __launch_bounds__((1 << LOGM) / 16) k_fir_fft_conv(FirFftArgs a) {
+    using F = FftShape<LOGM>;
+    extern __shared__ float2 sb[];
+    const int t = threadIdx.x;
+    const int64_t pb = blockIdx.x, r = pb / a.nbpc, b = pb % a.nbpc;
+    const int64_t c0 = 2 * r;
+    const bool live1 = c0 + 1 < a.C;
+    float2 v[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = make_float2(0.f, 0.f);
+    const int np = (int)(b + 1 < a.P ? b + 1 : a.P);
+    for (int p = 0; p < np; ++p) {
+        const float4* h4 = reinterpret_cast<const float4*>(a.H + (int64_t)p * F::M) + 8 * t;
+        const float4* z4 = reinterpret_cast<const float4*>(a.Z + (pb - p) * F::M) + 8 * t;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const float4 h = __ldg(h4 + q), z = __ldg(z4 + q);
+            v[2 * q].x = fmaf(z.x, h.x, fmaf(-z.y, h.y, v[2 * q].x));
+            v[2 * q].y = fmaf(z.x, h.y, fmaf(z.y, h.x, v[2 * q].y));
+            v[2 * q + 1].x = fmaf(z.z, h.z, fmaf(-z.w, h.w, v[2 * q + 1].x));
+            v[2 * q + 1].y = fmaf(z.z, h.w, fmaf(z.w, h.z, v[2 * q + 1].y));
         }
     }
+    inverse_from<LOGM, F::NP - 1>(v, a.tw, sb, t);
+    const int64_t n0 = b * (int64_t)a.B;
+    const int64_t m0 = a.N - n0 < a.B ? a.N - n0 : a.B;
+    float* y0 = a.y + c0 * a.ldy + n0;
+    store_pair<LOGM>(v, y0, live1 ? y0 + a.ldy : y0, F::M - a.B, m0, live1 ? m0 : 0, t);
 }
 
 template <int LOGM>
 cudaError_t launch_log(const FirFftArgs& a, cudaStream_t s) {
-    const int64_t ctas = (a.nb + 1) / 2;
-    k_fir_fft<LOGM><<<(unsigned)ctas, (1 << LOGM) / 16, fir_fft_smem_bytes(1 << LOGM), s>>>(a);
+    constexpr int T = (1 << LOGM) / 16;
+    const size_t smem = fir_fft_smem_bytes(1 << LOGM);
+    if (a.P == 0) {
+        k_fir_fft<LOGM><<<(unsigned)((a.nb + 1) / 2), T, smem, s>>>(a);
+    } else {
+        const int64_t ctas = (a.C + 1) / 2 * a.nbpc;
+        k_fir_fft_spec<LOGM><<<(unsigned)ctas, T, smem, s>>>(a);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_fir_fft_conv<LOGM><<<(unsigned)ctas, T, smem, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
 template <int LOGM>
 cudaError_t prepare_log() {
-    return cudaFuncSetAttribute(k_fir_fft<LOGM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)fir_fft_smem_bytes(1 << LOGM));
+    const int smem = (int)fir_fft_smem_bytes(1 << LOGM);
+    cudaError_t e = cudaFuncSetAttribute(k_fir_fft<LOGM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fir_fft_spec<LOGM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fir_fft_conv<LOGM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e;
 }
 
 }  // namespace

@@ -33,10 +33,10 @@ namespace {
 // FFT size for an L-tap FIR by overlap-save: the M = 2^m (m = 10..13) with
 // the least estimated work per output, M (m + 3) / (M - L + 1) (m radix-2
 // levels of butterflies plus the loads, product and stores), among those
-// whose block B = M - (L - 1) is at least M/4; `force` (10..13) picks M when
-// that M qualifies.  0 if none does.
+// whose block B = M - (L - 1) is at least M/4; `force` (10..13) allows only
+// that M.  0 if none qualifies.
 int fft_size_for(int L, int force) {
-    if (force >= 10 && force <= 13 && (1 << force) - (L - 1) >= (1 << force) / 4) return 1 << force;
+    if (force >= 10 && force <= 13) return (1 << force) - (L - 1) >= (1 << force) / 4 ? 1 << force : 0;
     int best = 0;
     double cost = 0.0;
     for (int m = 10; m <= 13; ++m) {
@@ -44,6 +44,23 @@ int fft_size_for(int L, int force) {
         if (B < M / 4) continue;
         const double c = (double)M * (m + 3) / B;
         if (best == 0 || c < cost) best = M, cost = c;
+    }
+    return best;
+}
+
+// Transform size for partitioned overlap-save of an L-tap FIR (partitions of
+// B = M/2 taps, P = ceil(L / B) of them): the M = 2^m (m = 11..13) with the
+// least estimated work per output, 2 (m + 3) + 2P (a forward and an inverse
+// transform per segment; per point and partition a complex multiply-add and
+// two 16-byte reads from L2); `force` (10..13) picks M.
+int fft_part_size_for(int L, int force) {
+    if (force >= 10 && force <= 13) return 1 << force;
+    int best = 0;
+    double cost = 0.0;
+    for (int m = 11; m <= 13; ++m) {
+        const int B = (1 << m) / 2;
+        const double c = 2.0 * (m + 3) + 2.0 * (double)((L + B - 1) / B);
+        if (best == 0 || c < cost) best = 1 << m, cost = c;
     }
     return best;
 }
@@ -67,6 +84,37 @@ void host_fft(std::vector<std::complex<double>>& a) {
                 a[i + k + len / 2] = u - v;
             }
     }
+}
+
+// Twiddle tables of the overlap-save transform of M = 2^m points: its passes
+// run over spans M, M/G0, ..., 16 (G0 = 2^(m mod 4), or 16), radix G0 first
+// and 16 after; a pass over span S with radix G and sub = S/G > 1 has a table
+// [q - 1][i] = e^(-2 pi i * i * bitrev_G(q) / S), q = 1..G-1, i < sub.
+std::vector<std::complex<double>> fft_pass_twiddles(int m) {
+    std::vector<std::complex<double>> out;
+    const int M = 1 << m, r = m % 4;
+    std::vector<std::pair<int, int>> passes;
+    int S = M;
+    if (r) {
+        passes.push_back({S, 1 << r});
+        S >>= r;
+    }
+    for (; S >= 16; S >>= 4) passes.push_back({S, 16});
+    for (const auto& ps : passes) {
+        const int Sp = ps.first, G = ps.second, sub = Sp / G;
+        if (sub == 1) continue;
+        int bits = 0;
+        while ((1 << bits) < G) ++bits;
+        for (int q = 1; q < G; ++q) {
+            int kq = 0;
+            for (int b = 0; b < bits; ++b) kq |= ((q >> b) & 1) << (bits - 1 - b);
+            for (int i = 0; i < sub; ++i) {
+                const double ang = -2.0 * M_PI * (double)(((int64_t)i * kq) % Sp) / (double)Sp;
+                out.push_back(std::complex<double>(std::cos(ang), std::sin(ang)));
+            }
+        }
+    }
+    return out;
 }
 
 }  // namespace
@@ -297,9 +345,13 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         std::vector<HostUnit> out;
         for (HostUnit& u : p->units) {
             HostUnit f = u;
-            const int fftM = (p->flags & TFX_PLAN_FIR_FFT) && u.L >= 64
-                                 ? fft_size_for(u.L, (int)((p->flags & TFX_PLAN_FIR_FFT_LOG_MASK) >> 16))
-                                 : 0;
+            const int force = (int)((p->flags & TFX_PLAN_FIR_FFT_LOG_MASK) >> 16);
+            const bool want_fft = (p->flags & TFX_PLAN_FIR_FFT) && u.L >= 64;
+            int fftM = want_fft ? fft_size_for(u.L, force) : 0, fftP = 0;
+            if (want_fft && fftM == 0) {  // too long for one block: partitioned
+                fftM = fft_part_size_for(u.L, force);
+                fftP = (u.L + fftM / 2 - 1) / (fftM / 2);
+            }
             if (fftM > 0) {
                 f.S = 0;
                 f.sec.clear();
@@ -310,7 +362,8 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
                 f.fft_M = fftM;
                 f.fft_m = 0;
                 while ((1 << f.fft_m) < fftM) ++f.fft_m;
-                f.fft_B = fftM - (u.L - 1);
+                f.fft_P = fftP;
+                f.fft_B = fftP > 0 ? fftM / 2 : fftM - (u.L - 1);
                 if (u.S > 0) {
                     HostUnit sos = u;
                     sos.L = 0;
@@ -359,9 +412,9 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         }
         if (u.fft) {
             u.off_H = off;
-            off = align_up(off + (size_t)u.fft_M * sizeof(float2));
+            off = align_up(off + (size_t)std::max(u.fft_P, 1) * u.fft_M * sizeof(float2));
             u.off_tw = off;
-            off = align_up(off + (size_t)(u.fft_M / 2) * sizeof(float2));
+            off = align_up(off + fft_pass_twiddles(u.fft_m).size() * sizeof(float2));
         }
         if (p->train && u.S > 0) {
             u.off_raw = off;
@@ -402,21 +455,23 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         if (u.fft) {
             // spectrum of h zero-padded to M, scaled by 1/M (the inverse FFT's
             // normalisation), in bit-reversed order; twiddles e^(-2 pi i k / M)
+            // (partitioned: of each partition h[pB, (p + 1) B))
             const int M = u.fft_M;
-            std::vector<std::complex<double>> Hc(M, 0.0);
-            for (int k = 0; k < u.L; ++k) Hc[k] = u.taps[k];
-            host_fft(Hc);
-            float2* Hd = reinterpret_cast<float2*>(host.data() + u.off_H);
-            for (int k = 0; k < M; ++k) {
-                int r = 0;
-                for (int b = 0; b < u.fft_m; ++b) r |= ((k >> b) & 1) << (u.fft_m - 1 - b);
-                Hd[k] = make_float2((float)(Hc[r].real() / M), (float)(Hc[r].imag() / M));
+            const int parts = std::max(u.fft_P, 1), plen = u.fft_P > 0 ? u.fft_B : u.L;
+            for (int q = 0; q < parts; ++q) {
+                std::vector<std::complex<double>> Hc(M, 0.0);
+                for (int k = 0; k < plen && q * plen + k < u.L; ++k) Hc[k] = u.taps[q * plen + k];
+                host_fft(Hc);
+                float2* Hd = reinterpret_cast<float2*>(host.data() + u.off_H) + (size_t)q * M;
+                for (int k = 0; k < M; ++k) {
+                    int r = 0;
+                    for (int b = 0; b < u.fft_m; ++b) r |= ((k >> b) & 1) << (u.fft_m - 1 - b);
+                    Hd[k] = make_float2((float)(Hc[r].real() / M), (float)(Hc[r].imag() / M));
+                }
             }
+            const std::vector<std::complex<double>> twd = fft_pass_twiddles(u.fft_m);
             float2* tw = reinterpret_cast<float2*>(host.data() + u.off_tw);
-            for (int k = 0; k < M / 2; ++k) {
-                const double ang = -2.0 * M_PI * (double)k / (double)M;
-                tw[k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
-            }
+            for (size_t k = 0; k < twd.size(); ++k) tw[k] = make_float2((float)twd[k].real(), (float)twd[k].imag());
         }
         if (p->train && u.S > 0) {
             std::memcpy(host.data() + u.off_raw, u.raw.data(), (size_t)u.S * 6 * sizeof(double));
@@ -509,7 +564,7 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
 
     // workspace layout
     const int64_t ntt = p->N > 0 ? (p->N + TILE - 1) / TILE : 0;
-    size_t hdr = 0, tails = 0;
+    size_t hdr = 0, tails = 0, zbytes = 0;
     for (HostUnit& u : p->units) {
         u.ntt = ntt;
         if (u.tc) {
@@ -518,6 +573,8 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         }
         if (u.fft) {
             u.ntt = p->N > 0 ? (p->N + u.fft_B - 1) / u.fft_B : 0;
+            if (u.fft_P > 0)  // segment spectra of every channel pair, in the scratch region
+                zbytes = std::max(zbytes, align_up((size_t)((p->C + 1) / 2) * (size_t)u.ntt * u.fft_M * sizeof(float2)));
             continue;
         }
         if (u.warp) u.ntt = p->N > 0 ? (p->N + WARP_TILE - 1) / WARP_TILE : 0;
@@ -533,10 +590,11 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         tails = std::max(tails, align_up(u.tails_bytes));
     }
     p->scratch_hdr = hdr;
-    p->scratch_bytes = hdr + tails;
+    p->scratch_bytes = std::max(hdr + tails, zbytes);
     p->buf_bytes = align_up((size_t)p->C * (size_t)p->N * sizeof(float));
     size_t nbuf = p->units.size() > 2 ? 2 : (p->units.size() == 2 ? 1 : 0);
-    if (p->units.size() == 1 && (p->units[0].tc || p->units[0].fft)) nbuf = 1;  // input copy for in-place operation
+    if (p->units.size() == 1 && (p->units[0].tc || (p->units[0].fft && p->units[0].fft_P == 0)))
+        nbuf = 1;  // input copy for in-place operation
     p->ws_fused = p->scratch_bytes + nbuf * p->buf_bytes;
     p->ws_plain = (nst > 0 ? 2 : 0) * p->buf_bytes;
 
@@ -607,7 +665,10 @@ int launch_unit_range(tfx_plan* p, int i, const float* in, int64_t ldin, float* 
         f.ldx = ldin;
         f.y = out;
         f.ldy = ldout;
-        if (f.x == f.y) {  // blocks read their predecessors' input: copy it first
+        // single-block: blocks read their predecessors' input, so an in-place
+        // call copies it first; partitioned: every segment is transformed
+        // before any output is written
+        if (f.x == f.y && u.fft_P == 0) {
             if (launch_copy_rows(f.x, copy_buf, Cg, p->N, f.ldx, p->N, s) != cudaSuccess) return TFX_ERR_CUDA;
             f.x = copy_buf;
             f.ldx = p->N;
@@ -618,8 +679,10 @@ int launch_unit_range(tfx_plan* p, int i, const float* in, int64_t ldin, float* 
         f.M = u.fft_M;
         f.m = u.fft_m;
         f.B = u.fft_B;
+        f.P = u.fft_P;
         f.nbpc = u.ntt;
-        f.nb = Cg * u.ntt;
+        f.nb = (u.fft_P > 0 ? (Cg + 1) / 2 : Cg) * u.ntt;
+        f.Z = reinterpret_cast<float2*>(scratch);
         f.H = reinterpret_cast<const float2*>(p->dconst + u.off_H);
         f.tw = reinterpret_cast<const float2*>(p->dconst + u.off_tw);
         return launch_fir_fft(f, s) == cudaSuccess ? TFX_OK : TFX_ERR_CUDA;
@@ -1031,7 +1094,9 @@ size_t tfx_plan_workspace_size(const tfx_plan* p) {
 int tfx_plan_launch_count(const tfx_plan* p) {
     if (!p) return -1;
     if (p->C == 0 || p->N == 0) return 0;
-    return p->units.empty() ? 1 : (int)p->units.size();
+    int n = 0;
+    for (const HostUnit& u : p->units) n += u.fft && u.fft_P > 0 ? 2 : 1;
+    return p->units.empty() ? 1 : n;
 }
 
 int tfx_plan_execute(tfx_plan* p, const float* x, float* y, void* ws, size_t ws_bytes, tfx_stream s) {

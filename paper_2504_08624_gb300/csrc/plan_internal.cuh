@@ -41,6 +41,7 @@ struct HostUnit {
     // FIR by FFT overlap-save (TFX_PLAN_FIR_FFT)
     bool fft = false;
     int fft_M = 0, fft_m = 0, fft_B = 0;
+    int fft_P = 0;  // 0: single-block overlap-save; else partitions of fft_B = M/2 taps
     size_t off_H = 0, off_tw = 0;
     // trainable plans: where each section's raw row (6 values) and the FIR's
     // taps sit in the flat coefficient-gradient array, the raw rows for the

@@ -156,8 +156,10 @@ struct FirFftArgs {
     int M, m;          // FFT size M = 2^m (complex points)
     int B;             // outputs per block
     int64_t nbpc, nb;  // blocks per channel, blocks in all
-    const float2* H;   // [M] spectrum of h (zero-padded), bit-reversed order, scaled by 1/M
-    const float2* tw;  // [M/2] e^(-2 pi i k / M)
+    const float2* H;   // [max(P,1)][M] spectra of h (or of its partitions), bit-reversed order, scaled by 1/M
+    const float2* tw;  // per-pass twiddle tables (see k_fir_fft.cu)
+    int P;             // 0: single-block overlap-save; else partitions of B = M/2 taps
+    float2* Z;         // partitioned: [ceil(C/2)][nbpc][M] segment spectra (workspace)
 };
 
 struct BatchFir {

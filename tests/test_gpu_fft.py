@@ -109,11 +109,50 @@ def test_fft_fir_empty():
         p.close()
 
 
-def test_fft_fir_too_long_stays_on_tensor_cores():
-    """Beyond 6145 taps no transform size leaves a block of M/4: the FIR runs
-    on the Toeplitz GEMM path, still within tolerance."""
-    x = W.white_gauss(2, 30000, 35)
-    check_fft(x, [("fir", _taps(6146, 9))])
+def _part_block(L, m=None):
+    """(M, B, P) of the partitioned scheme: least 2 (m + 3) + 2P over m = 11..13."""
+    if m is None:
+        m = min(range(11, 14), key=lambda q: 2 * (q + 3) + 2 * -(-L // ((1 << q) // 2)))
+    M = 1 << m
+    return M, M // 2, -(-L // (M // 2))
+
+
+@pytest.mark.parametrize("L", [6146, 8193, 16384, 20000])
+def test_partitioned_fir_lengths(L):
+    """Beyond 6145 taps the FIR is partitioned: lengths shorter than one
+    block, on and around block multiples, and an odd channel count (the last
+    pair has no imaginary channel)."""
+    M, B, P = _part_block(L)
+    for C, Ns in ((3, 1), (3, B - 1), (2, B + 1), (3, 3 * B), (3, (P + 2) * B + 333)):
+        x = W.white_gauss(C, Ns, 40)
+        check_fft(x, [("fir", _taps(L, L))])
+
+
+@pytest.mark.parametrize("m", [10, 11, 12, 13])
+def test_partitioned_every_transform_size(m):
+    """Partitioned scheme at each forced transform size, P from 2 to 5."""
+    from paper_2504_08624_gb300 import _native as N_
+    M, B = 1 << m, (1 << m) // 2
+    for L, C in ((M - M // 4 + 2, 3), (2 * M + 5, 4)):
+        x = W.white_gauss(C, 4 * B + 19, 41)
+        check_fft(x, [("fir", _taps(L, m + L))], flags=N_.TFX_PLAN_FIR_FFT_LOG(m))
+
+
+@pytest.mark.parametrize("inplace", [False, True])
+def test_partitioned_inplace_and_stride(inplace):
+    x = W.white_gauss(5, 40000, 42)
+    check_fft(x, [("fir", _taps(9000, 4))], inplace=inplace, ld=40000 + 9)
+
+
+def test_partitioned_long_bandpass():
+    """The 16384-tap Kaiser band-pass of the long-FIR workload, on its signal
+    recipe, partitioned (and at both of the large transform sizes)."""
+    from paper_2504_08624_gb300 import _native as N_
+    wl = W.long_fir()
+    x = wl.make_signal(3, 3 * 16384 + 1234)
+    check_fft(x, wl.stages, 1e-5)
+    for m in (12, 13):
+        check_fft(x, wl.stages, 1e-5, flags=N_.TFX_PLAN_FIR_FFT_LOG(m))
 
 
 @pytest.mark.parametrize("m", [10, 11, 12, 13])
@@ -129,7 +168,7 @@ def test_fft_fir_every_transform_size(m):
     check_fft(x, [("fir", _taps(100, m))], flags=N_.TFX_PLAN_FIR_FFT_LOG(m))
 
 
-@pytest.mark.parametrize("L", [257, 700])
+@pytest.mark.parametrize("L", [257, 700, 7000])
 def test_fft_fir_gradient_matches_oracle(L):
     """Trainable plan with the FFT flag: the input gradient's transposed FIR
     runs on the FFT unit; y, dx and every coefficient gradient against the
