@@ -82,7 +82,10 @@ typedef struct {
  * (longer cascades are split); tfx_plan_execute still works on such a plan. */
 #define TFX_PLAN_TRAINABLE 32u
 /* FIRs of 64 taps or more by FFT overlap-save instead of the tensor-core
- * Toeplitz GEMM, with hand-written register-resident radix-16 FFTs of
+ * Toeplitz GEMM (without this flag, FIRs of 768 taps or more take the FFT
+ * route unless TFX_PLAN_FIR_TC, _FIR_BF16_PLAIN or _FIR_BF16_SPLIT is set or
+ * the FIR stages run on CUDA cores), with hand-written register-resident
+ * radix-16 FFTs of
  * M = 1024..8192 points (FP32; the error is ~log2(M) eps of each block's
  * energy rather than per product).  Up to 6145 taps: blocks of
  * B = M - (L - 1) outputs, two blocks per complex transform.  Longer:
@@ -90,10 +93,13 @@ typedef struct {
  * input segment transformed once (two channels per complex transform) into a
  * workspace of ceil(C/2) x ceil(N / (M/2)) x M complex values, and each output
  * block the inverse transform of the sum of the P partition products (two
- * launches).  The transform size is chosen per FIR from a cost model unless
- * TFX_PLAN_FIR_FFT_LOG(m) fixes M = 2^m (m = 10..13; a FIR for which a single
- * block would be under M/4 is partitioned at that size). */
+ * launches).  The scheme and transform size are chosen per FIR from a cost
+ * model fitted to GB300 timings unless TFX_PLAN_FIR_FFT_LOG(m) fixes
+ * M = 2^m (m = 10..13; the scheme is still chosen by the model). */
 #define TFX_PLAN_FIR_FFT 64u
+/* Every FIR of TC_MIN_TAPS (64) taps or more on the tensor-core Toeplitz
+ * GEMM, none by FFT. */
+#define TFX_PLAN_FIR_TC 128u
 #define TFX_PLAN_FIR_FFT_LOG(m) ((uint32_t)(m) << 16)
 #define TFX_PLAN_FIR_FFT_LOG_MASK (15u << 16)
 /* Test hook for failure detection: the first tile of channel 0 never publishes
@@ -330,7 +336,8 @@ typedef struct {
 } tfx_clip;
 
 typedef struct {
-    uint32_t plan_flags;   /* TFX_PLAN_* for every clip (TFX_PLAN_DEFAULT, _FIR_CUDA_CORES, _FIR_BF16_*) */
+    uint32_t plan_flags;   /* TFX_PLAN_* for every clip (TFX_PLAN_DEFAULT, _FIR_CUDA_CORES, _FIR_BF16_*);
+                              long FIRs stay on the tensor cores (_FIR_FFT is rejected) */
     int32_t fir_nb;        /* tensor-core FIR output blocks of 128 per tile: 64, 128 or 256 (0: 128) */
     int32_t tc_min_taps;   /* FIRs with at least this many taps use the tensor cores (0: 64) */
 } tfx_batch_params;

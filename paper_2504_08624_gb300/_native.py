@@ -25,6 +25,7 @@ TFX_PLAN_FIR_BF16_SPLIT = 8
 TFX_PLAN_SCAN_WARP_TILES = 16
 TFX_PLAN_TRAINABLE = 32
 TFX_PLAN_FIR_FFT = 64
+TFX_PLAN_FIR_TC = 128
 
 
 def TFX_PLAN_FIR_FFT_LOG(m: int) -> int:

@@ -70,8 +70,11 @@ void batch_free(tfx_batch* b) {
 int batch_build(tfx_batch* b, const tfx_clip* clips, int32_t n, const tfx_batch_params& prm) {
     const int NB = prm.fir_nb > 0 ? prm.fir_nb : 128;
     if (NB != 64 && NB != 128 && NB != 256) return TFX_ERR_INVALID;
-    const uint32_t pflags = prm.plan_flags;
-    if (pflags & (TFX_PLAN_SCAN_WARP_TILES | TFX_PLAN_TRAINABLE | TFX_PLAN_TEST_DROP_PUBLISH | TFX_PLAN_UNFUSED))
+    // the batched groups run FIRs on the tensor cores or fused with a cascade:
+    // no FFT units
+    const uint32_t pflags = prm.plan_flags | TFX_PLAN_FIR_TC;
+    if (pflags & (TFX_PLAN_SCAN_WARP_TILES | TFX_PLAN_TRAINABLE | TFX_PLAN_TEST_DROP_PUBLISH | TFX_PLAN_UNFUSED |
+                  TFX_PLAN_FIR_FFT))
         return TFX_ERR_UNSUPPORTED;
     b->nclips = n;
     b->plans.assign(n, nullptr);

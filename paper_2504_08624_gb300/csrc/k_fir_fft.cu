@@ -27,8 +27,10 @@
 // between passes through shared memory padded by one word per 16 (no bank
 // conflicts for any pass's pattern).  After the last pass (span 16) thread t
 // holds points 16t..16t+15 of the spectrum in bit-reversed order; the
-// spectrum of h is stored in that order with the 1/M scale folded in, so the
-// product needs no permutation, and the inverse runs the passes backwards
+// spectrum of h is stored in that order with the 1/M scale folded in (float4
+// q of thread t, points 16t + 2q and 16t + 2q + 1, at index q*T + t, so that
+// a warp's reads are contiguous), the product needs no permutation, and the
+// inverse runs the passes backwards
 // (conjugate twiddles, then the DIT G-point DFT), ending in natural order in
 // the layout the input was loaded in: point t + T*j in register j, so both the
 // input loads and the output stores are coalesced.  Each pass with twiddles
@@ -285,11 +287,12 @@ __global__ void __launch_bounds__((1 << LOGM) / 16) k_fir_fft(FirFftArgs a) {
     float2 v[16];
     load_pair<LOGM>(v, a.x + c0 * a.ldx, a.x + c1 * a.ldx, live1, n00 - Hh, n01 - Hh, a.N, t);
     forward_from<LOGM, 0>(v, a.tw, sb, t);
-    // spectrum product: thread t holds positions 16t .. 16t + 15
-    const float4* h4 = reinterpret_cast<const float4*>(a.H) + 8 * t;
+    // spectrum product: thread t holds positions 16t .. 16t + 15, stored as
+    // float4 q (positions 16t + 2q, 16t + 2q + 1) at index q*T + t
+    const float4* h4 = reinterpret_cast<const float4*>(a.H) + t;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        const float4 h = __ldg(h4 + q);
+        const float4 h = __ldg(h4 + q * F::T);
         v[2 * q] = cmul(v[2 * q], make_float2(h.x, h.y));
         v[2 * q + 1] = cmul(v[2 * q + 1], make_float2(h.z, h.w));
     }
@@ -300,8 +303,8 @@ __global__ void __launch_bounds__((1 << LOGM) / 16) k_fir_fft(FirFftArgs a) {
 }
 
 // Partitioned overlap-save, step 1: the spectrum of segment b of a channel
-// pair, x[(b - 1) B, (b + 1) B) of channels 2r (re) and 2r + 1 (im), stored in
-// the transform's output order (thread t's 16 points contiguous).
+// pair, x[(b - 1) B, (b + 1) B) of channels 2r (re) and 2r + 1 (im), stored
+// like H: float4 q of thread t (positions 16t + 2q, 16t + 2q + 1) at q*T + t.
 template <int LOGM>
 __global__ void __launch_bounds__((1 << LOGM) / 16) k_fir_fft_spec(FirFftArgs a) {
     using F = FftShape<LOGM>;
@@ -315,9 +318,9 @@ __global__ void __launch_bounds__((1 << LOGM) / 16) k_fir_fft_spec(FirFftArgs a)
     float2 v[16];
     load_pair<LOGM>(v, x0, live1 ? x0 + a.ldx : x0, live1, s0, s0, a.N, t);
     forward_from<LOGM, 0>(v, a.tw, sb, t);
-    float4* z = reinterpret_cast<float4*>(a.Z + pb * F::M) + 8 * t;
+    float4* z = reinterpret_cast<float4*>(a.Z + pb * F::M) + t;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) z[q] = make_float4(v[2 * q].x, v[2 * q].y, v[2 * q + 1].x, v[2 * q + 1].y);
+    for (int q = 0; q < 8; ++q) z[q * F::T] = make_float4(v[2 * q].x, v[2 * q].y, v[2 * q + 1].x, v[2 * q + 1].y);
 }
 
 // Partitioned overlap-save, step 2: block b of a channel pair is the inverse
@@ -337,11 +340,11 @@ __global__ void __launch_bounds__((1 << LOGM) / 16) k_fir_fft_conv(FirFftArgs a)
     for (int j = 0; j < 16; ++j) v[j] = make_float2(0.f, 0.f);
     const int np = (int)(b + 1 < a.P ? b + 1 : a.P);
     for (int p = 0; p < np; ++p) {
-        const float4* h4 = reinterpret_cast<const float4*>(a.H + (int64_t)p * F::M) + 8 * t;
-        const float4* z4 = reinterpret_cast<const float4*>(a.Z + (pb - p) * F::M) + 8 * t;
+        const float4* h4 = reinterpret_cast<const float4*>(a.H + (int64_t)p * F::M) + t;
+        const float4* z4 = reinterpret_cast<const float4*>(a.Z + (pb - p) * F::M) + t;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const float4 h = __ldg(h4 + q), z = __ldg(z4 + q);
+            const float4 h = __ldg(h4 + q * F::T), z = __ldg(z4 + q * F::T);
             v[2 * q].x = fmaf(z.x, h.x, fmaf(-z.y, h.y, v[2 * q].x));
             v[2 * q].y = fmaf(z.x, h.y, fmaf(z.y, h.x, v[2 * q].y));
             v[2 * q + 1].x = fmaf(z.z, h.z, fmaf(-z.w, h.w, v[2 * q + 1].x));

@@ -30,37 +30,36 @@ void tfx::tc_geometry(HostUnit& u, int NB) {
 
 namespace {
 
-// FFT size for an L-tap FIR by overlap-save: the M = 2^m (m = 10..13) with
-// the least estimated work per output, M (m + 3) / (M - L + 1) (m radix-2
-// levels of butterflies plus the loads, product and stores), among those
-// whose block B = M - (L - 1) is at least M/4; `force` (10..13) allows only
-// that M.  0 if none qualifies.
-int fft_size_for(int L, int force) {
-    if (force >= 10 && force <= 13) return (1 << force) - (L - 1) >= (1 << force) / 4 ? 1 << force : 0;
-    int best = 0;
+// Overlap-save scheme for an L-tap FIR: transform size M = 2^m and number of
+// partitions P (0: single-block, B = M - (L - 1) outputs per block; else
+// partitions of B = M/2 taps).  The choice minimises a cost model fitted to
+// measured GB300 times per output (16 channels x 2.88M samples, microseconds
+// for the whole signal): single-block 55 + k_m M / B with
+// k = 71, 77.5, 87.6, 130 for m = 10..13 (the 55 is the memory traffic, the
+// rest the transforms); partitioned I_m + 22 P with I = 217, 246, 343 for
+// m = 11..13 (two launches and the spectra traffic).  A single block must
+// hold B >= M/8 outputs.  `force` (10..13) restricts the choice to that m.
+struct FftScheme {
+    int M = 0, P = 0;
+};
+
+FftScheme fft_scheme_for(int L, int force) {
+    static const double K[4] = {71.0, 77.5, 87.6, 130.0};
+    static const double I[4] = {0.0, 217.0, 246.0, 343.0};
+    FftScheme best;
     double cost = 0.0;
     for (int m = 10; m <= 13; ++m) {
+        if (force >= 10 && force <= 13 && m != force) continue;
         const int M = 1 << m, B = M - (L - 1);
-        if (B < M / 4) continue;
-        const double c = (double)M * (m + 3) / B;
-        if (best == 0 || c < cost) best = M, cost = c;
-    }
-    return best;
-}
-
-// Transform size for partitioned overlap-save of an L-tap FIR (partitions of
-// B = M/2 taps, P = ceil(L / B) of them): the M = 2^m (m = 11..13) with the
-// least estimated work per output, 2 (m + 3) + 2P (a forward and an inverse
-// transform per segment; per point and partition a complex multiply-add and
-// two 16-byte reads from L2); `force` (10..13) picks M.
-int fft_part_size_for(int L, int force) {
-    if (force >= 10 && force <= 13) return 1 << force;
-    int best = 0;
-    double cost = 0.0;
-    for (int m = 11; m <= 13; ++m) {
-        const int B = (1 << m) / 2;
-        const double c = 2.0 * (m + 3) + 2.0 * (double)((L + B - 1) / B);
-        if (best == 0 || c < cost) best = 1 << m, cost = c;
+        if (B >= M / 8) {
+            const double c = 55.0 + K[m - 10] * M / B;
+            if (best.M == 0 || c < cost) best.M = M, best.P = 0, cost = c;
+        }
+        if (m >= 11 || force == m) {
+            const int P = (L + M / 2 - 1) / (M / 2);
+            const double c = (m >= 11 ? I[m - 10] : 200.0) + 22.0 * P;
+            if (best.M == 0 || c < cost) best.M = M, best.P = P, cost = c;
+        }
     }
     return best;
 }
@@ -345,13 +344,13 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         std::vector<HostUnit> out;
         for (HostUnit& u : p->units) {
             HostUnit f = u;
+            // FFT overlap-save: forced for 64 taps or more, by default from
+            // FFT_MIN_TAPS on unless a tensor-core mode or precision is asked for
             const int force = (int)((p->flags & TFX_PLAN_FIR_FFT_LOG_MASK) >> 16);
-            const bool want_fft = (p->flags & TFX_PLAN_FIR_FFT) && u.L >= 64;
-            int fftM = want_fft ? fft_size_for(u.L, force) : 0, fftP = 0;
-            if (want_fft && fftM == 0) {  // too long for one block: partitioned
-                fftM = fft_part_size_for(u.L, force);
-                fftP = (u.L + fftM / 2 - 1) / (fftM / 2);
-            }
+            const bool tc_only = (p->flags & (TFX_PLAN_FIR_TC | TFX_PLAN_FIR_BF16_PLAIN | TFX_PLAN_FIR_BF16_SPLIT)) != 0;
+            const bool want_fft = (p->flags & TFX_PLAN_FIR_FFT) ? u.L >= 64 : (!tc_only && u.L >= FFT_MIN_TAPS);
+            const FftScheme sch = want_fft ? fft_scheme_for(u.L, force) : FftScheme();
+            const int fftM = sch.M, fftP = sch.P;
             if (fftM > 0) {
                 f.S = 0;
                 f.sec.clear();
@@ -462,11 +461,15 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
                 std::vector<std::complex<double>> Hc(M, 0.0);
                 for (int k = 0; k < plen && q * plen + k < u.L; ++k) Hc[k] = u.taps[q * plen + k];
                 host_fft(Hc);
+                // position k = 16t + 2c + e (thread t, float4 c, half e) holds
+                // H[bitrev(k)] / M and is stored at float2 index 2 (c T + t) + e
                 float2* Hd = reinterpret_cast<float2*>(host.data() + u.off_H) + (size_t)q * M;
+                const int T = M / 16;
                 for (int k = 0; k < M; ++k) {
                     int r = 0;
                     for (int b = 0; b < u.fft_m; ++b) r |= ((k >> b) & 1) << (u.fft_m - 1 - b);
-                    Hd[k] = make_float2((float)(Hc[r].real() / M), (float)(Hc[r].imag() / M));
+                    const int t = k / 16, c = (k % 16) / 2, e = k % 2;
+                    Hd[2 * (c * T + t) + e] = make_float2((float)(Hc[r].real() / M), (float)(Hc[r].imag() / M));
                 }
             }
             const std::vector<std::complex<double>> twd = fft_pass_twiddles(u.fft_m);
@@ -1064,7 +1067,8 @@ int tfx::plan_create_ex(tfx_plan** out, int64_t C, int64_t N, int64_t ld, const 
     rc = validate_stages(st, nst);
     if (rc != TFX_OK) return rc;
     if (flags & ~(TFX_PLAN_FIR_CUDA_CORES | TFX_PLAN_UNFUSED | TFX_PLAN_FIR_BF16_PLAIN | TFX_PLAN_FIR_BF16_SPLIT |
-                  TFX_PLAN_SCAN_WARP_TILES | TFX_PLAN_TRAINABLE | TFX_PLAN_FIR_FFT | TFX_PLAN_FIR_FFT_LOG_MASK |
+                  TFX_PLAN_SCAN_WARP_TILES | TFX_PLAN_TRAINABLE | TFX_PLAN_FIR_FFT | TFX_PLAN_FIR_TC |
+                  TFX_PLAN_FIR_FFT_LOG_MASK |
                   TFX_PLAN_TEST_DROP_PUBLISH))
         return TFX_ERR_INVALID;
     tfx_plan* p = new (std::nothrow) tfx_plan();

@@ -60,6 +60,9 @@ constexpr int WARP_TILE = 32 * T_CHUNK;
 // Taps at or above this count go to the tensor cores (unless disabled or
 // overridden per plan).
 constexpr int TC_MIN_TAPS = 64;
+// FIRs from this many taps run by FFT overlap-save unless the plan asks for
+// the tensor cores: measured faster on GB300 from about 700 taps.
+constexpr int FFT_MIN_TAPS = 768;
 constexpr size_t SMEM_MAX = 227 * 1024;
 
 struct PlainStage {

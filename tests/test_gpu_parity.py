@@ -69,12 +69,15 @@ def test_fir_sizes(L, N):
     check(x, [("fir", h)])
 
 
+@pytest.mark.parametrize("route", ["tensor_cores", "default"])
 @pytest.mark.parametrize("L", [8192, 8193, 9000, 20000])
-def test_fir_halo_spans_tiles(L):
-    # halo of L-1 >= one tile: the window gathers from several predecessor tiles
+def test_fir_halo_spans_tiles(L, route):
+    # tensor cores: a halo of L-1 >= one tile gathers from several predecessor
+    # tiles; default: these lengths take the partitioned FFT route
+    from paper_2504_08624_gb300 import _native as N_
     x = W.white_gauss(2, 40000, 13)
     h = np.random.default_rng(L).standard_normal(L) / math.sqrt(L)
-    check(x, [("fir", h)])
+    check(x, [("fir", h)], flags=N_.TFX_PLAN_FIR_TC if route == "tensor_cores" else None)
 
 
 def test_plain_chain_full_size():
@@ -200,14 +203,16 @@ def test_plan_reuse_and_graph_capture():
     p.close()
 
 
-@pytest.mark.parametrize("mode", ["fp16_split", "bf16_split", "bf16_plain", "cuda_cores"])
+@pytest.mark.parametrize("mode", ["fp16_split", "bf16_split", "bf16_plain", "cuda_cores", "default_fft"])
 def test_fir_precision_modes(mode):
-    """Tensor-core FIR operand modes against the oracle (white noise, 1025-tap
-    low-pass): scaled FP16 hi/lo (default) and BF16 hi/lo meet 1e-5 of the
-    peak; plain BF16 is an accuracy-reduced mode whose error is reported."""
+    """FIR routes against the oracle (white noise, 1025-tap low-pass): the
+    tensor cores with scaled FP16 hi/lo and BF16 hi/lo operands meet 1e-5 of
+    the peak, plain BF16 is an accuracy-reduced mode whose error is reported;
+    CUDA cores and the default FFT route meet 1e-5."""
     from paper_2504_08624_gb300 import _native as N
-    flags = {"fp16_split": 0, "bf16_split": N.TFX_PLAN_FIR_BF16_SPLIT,
-             "bf16_plain": N.TFX_PLAN_FIR_BF16_PLAIN, "cuda_cores": N.TFX_PLAN_FIR_CUDA_CORES}[mode]
+    flags = {"fp16_split": N.TFX_PLAN_FIR_TC, "bf16_split": N.TFX_PLAN_FIR_BF16_SPLIT,
+             "bf16_plain": N.TFX_PLAN_FIR_BF16_PLAIN, "cuda_cores": N.TFX_PLAN_FIR_CUDA_CORES,
+             "default_fft": 0}[mode]
     x = W.white_gauss(3, 2 * 16384 + 999, 21)
     h = W.fir_lowpass(1025, 16000.0, 48000.0)
     got = run(x, [("fir", h)], flags=flags)
@@ -220,12 +225,15 @@ def test_fir_precision_modes(mode):
         assert_close(got, ref, 1e-5, mode)
 
 
-def test_strongly_attenuating_chain():
+@pytest.mark.parametrize("route", ["tensor_cores", "default"])
+def test_strongly_attenuating_chain(route):
     """Output ~70 dB below the input: the FIR sums terms that cancel to 1e-3 of
-    their magnitude.  The default scaled-FP16 split still meets 1e-4."""
+    their magnitude.  The tensor cores' scaled-FP16 split and the default
+    route still meet 1e-4."""
+    from paper_2504_08624_gb300 import _native as N_
     stages = W.random_chain(5)
     x = W.white_uniform(3, 48495, 505)
-    check(x, stages)
+    check(x, stages, flags=N_.TFX_PLAN_FIR_TC if route == "tensor_cores" else None)
 
 
 def test_timeout_cascade_only_warp_tiles():
@@ -253,19 +261,25 @@ def test_cascade_warp_tile_edges(N):
 
 @pytest.mark.parametrize("C", [1, 2, 5, 9])
 def test_cascade_then_tensor_fir(C):
+    """The multichannel chain (cascade, then a 1025-tap FIR): default route
+    (FFT), then the tensor cores and the default with a padded, unaligned layout."""
+    from paper_2504_08624_gb300 import _native as N_
     wl = W.multichannel_fused()
     x = wl.make_signal(C, 40000)
     check(x, wl.stages, wl.tol)
+    check(x, wl.stages, wl.tol, flags=N_.TFX_PLAN_FIR_TC, ld=40000 + 3, offset=1)
     check(x, wl.stages, wl.tol, flags=0, ld=40000 + 3, offset=1)
 
 
-def test_cascade_tensor_fir_graph_capture():
+@pytest.mark.parametrize("route", ["tensor_cores", "default"])
+def test_cascade_tensor_fir_graph_capture(route):
+    from paper_2504_08624_gb300 import _native as N_
     from paper_2504_08624_gb300 import api
     wl = W.multichannel_fused()
     x = wl.make_signal(5, 30000)
     xt = torch.from_numpy(x).cuda()
-    p = api.Plan(5, 30000, wl.stages)
-    assert p.launches_per_execute == 2  # cascade kernel, tensor-core FIR kernel
+    p = api.Plan(5, 30000, wl.stages, flags=N_.TFX_PLAN_FIR_TC if route == "tensor_cores" else 0)
+    assert p.launches_per_execute == 2  # cascade kernel, FIR kernel (tensor cores or FFT)
     y = torch.empty_like(xt)
     ws = p.workspace()
     s = torch.cuda.Stream()
@@ -316,7 +330,8 @@ def test_long_fir_streamed_taps(mode):
     BF16 is reported."""
     from paper_2504_08624_gb300 import _native as N
     wl = W.long_fir()
-    flags = {"fp16_split": 0, "bf16_split": N.TFX_PLAN_FIR_BF16_SPLIT, "bf16_plain": N.TFX_PLAN_FIR_BF16_PLAIN}[mode]
+    flags = {"fp16_split": N.TFX_PLAN_FIR_TC, "bf16_split": N.TFX_PLAN_FIR_BF16_SPLIT,
+             "bf16_plain": N.TFX_PLAN_FIR_BF16_PLAIN}[mode]
     x = wl.make_signal(2, 3 * 16384 + 1234)
     got = run(x, wl.stages, flags=flags)
     ref = oracle_chain(x, wl.stages)
