@@ -127,6 +127,66 @@ def fp32_alu_peak_tflops(sm_count: int, sm_mhz: float) -> float:
     return sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
+def unit_stages(desc, stages):
+    """Pair each unit of a plan description with the stages it runs: a
+    cascade takes the SOS stages up to the next FIR, a fused unit those and
+    the FIR, a FIR unit one FIR stage."""
+    out, i = [], 0
+    for u in desc:
+        take = []
+        if u["kind"] in ("cascade", "fused"):
+            while i < len(stages) and stages[i][0] == "sos":
+                take.append(stages[i])
+                i += 1
+        if u["kind"] != "cascade" and i < len(stages) and stages[i][0] == "fir":
+            take.append(stages[i])
+            i += 1
+        out.append((u, take))
+    return out
+
+
+def fft_flops_per_output(u) -> float:
+    """Algorithmic flops per output of the FFT FIR: 5 M log2 M per complex
+    transform of M points; single-block: a forward and an inverse transform
+    and M complex products (6 flop) per two blocks of B outputs;
+    partitioned: the two transforms and P complex multiply-adds (8 flop) per
+    point per M outputs (two channels x B)."""
+    M, B, P = u["M"], u["B"], u["P"]
+    m = M.bit_length() - 1
+    if P == 0:
+        return (10.0 * M * m + 6.0 * M) / (2.0 * B)
+    return (10.0 * M * m + 8.0 * P * M) / M
+
+
+def unit_roofline(u, units, t, step_s, pk, alu_peak) -> dict:
+    k = u["kind"]
+    row = {"route": k, "kernel_ms": t * 1e3, "share_of_step": t / step_s}
+    if k == "fir_tc":
+        L = u["L"]
+        K = -(-(L - 1) // 16) * 16 + 128
+        row.update({"bound": "tensor", "kernel": u["kernel"], "achieved": units * 2.0 * L / t / 1e12,
+                    "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                    "peak_source": f"{pk['source']} dense bf16/fp16 sustained",
+                    "executed_tflops": units * 2.0 * 3 * K / t / 1e12,
+                    "note": "achieved counts algorithmic 2L flop/sample; executed counts 3 split products x (W+128) K"})
+    elif k == "fir_fft":
+        f = fft_flops_per_output(u)
+        row.update({"bound": "alu", "kernel": "k_fir_fft" if u["P"] == 0 else "k_fir_fft_spec+k_fir_fft_conv",
+                    "achieved": units * f / t / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+                    "peak_source": "SMs x 128 FP32 lanes x 2 flop x max SM clock",
+                    "config": {"L": u["L"], "M": u["M"], "B": u["B"], "P": u["P"]},
+                    "note": f"{f:.1f} algorithmic flop per output (5 M log2 M per transform)"})
+    else:
+        S, L = u.get("S", 0), u.get("L", 0)
+        row.update({"bound": "alu", "kernel": "k_sos_warp" if u.get("scan") == "warp" else "k_unit",
+                    "achieved": units * (10.0 * S + 2.0 * L) / t / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+                    "peak_source": "SMs x 128 FP32 lanes x 2 flop x max SM clock",
+                    "note": "10 flop per SOS section, 2L per FIR tap, per sample"})
+        row["hbm_frac"] = units * 8.0 / t / 1e9 / pk["hbm_gbs"]
+    row["frac"] = row["achieved"] / row["peak"]
+    return row
+
+
 def traffic_for(kernel: str, workload_name: str):
     """DRAM bytes per launch of ``kernel`` from the committed ncu summary, or
     None when the summary is missing or the kernel source changed since."""
@@ -542,33 +602,25 @@ def main():
     sm_count = props.multi_processor_count
     step_s = t_dev / args.steps
     achieved_gbs = units * bytes_ps / step_s / 1e9
-    tensor_fir = (args.flags & NAT.TFX_PLAN_FIR_CUDA_CORES) == 0 and L >= 64
-    fir_kernel = "k_fir_tc_ws" if L <= 2048 else "k_fir_tc_long"
-    if tensor_fir:
-        # dominant kernel: the tensor-core Toeplitz FIR, timed alone with CUDA
-        # events on its launch stream through a FIR-only plan (same kernel and
-        # launch configuration as inside the chain)
-        taps = [c for k, c in wl.stages if k == "fir"][-1]
-        fplan = api.Plan(wl.C, wl.N, [("fir", taps)], flags=args.flags)
-        fws = fplan.workspace()
-        k_fir = max(10, args.steps // 3)
-        t_fir = time_gpu(lambda: fplan.execute(y, x_fir, fws), k_fir, 3, stream, torch, None) / k_fir
-        fplan.close()
-        kern = fir_kernel  # the persistent kernel the plan picks for this tap count
-        K = -(-(L - 1) // 16) * 16 + 128
-        bound = {"bound": "tensor", "kernel": kern, "achieved": units * 2.0 * L / t_fir / 1e12,
-                 "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
-                 "peak_source": f"{pk['source']} dense bf16/fp16 sustained",
-                 "kernel_ms": t_fir * 1e3, "share_of_step": t_fir / step_s,
-                 "executed_tflops": units * 2.0 * 3 * K / t_fir / 1e12,
-                 "note": "achieved counts algorithmic 2L flop/sample; executed counts 3 split products x (W+128) K"}
-    else:
-        kern = "k_unit"
-        alu_peak = fp32_alu_peak_tflops(sm_count, pk["sm_max_mhz"])
-        bound = {"bound": "alu", "kernel": kern, "achieved": units * flops_ps / step_s / 1e12, "peak": alu_peak,
-                 "unit": "TFLOP/s", "peak_source": f"{sm_count} SMs x 128 FP32 FMA x 2 flop x {pk['sm_max_mhz']:.0f} MHz"}
+    # every unit of the chain timed alone (a plan of the unit's stages, same
+    # flags, so the same kernels and launch configuration as inside the
+    # chain, CUDA events on the launch stream); the dominant one against its
+    # roofline
+    alu_peak = fp32_alu_peak_tflops(sm_count, pk["sm_max_mhz"])
+    unit_rows = []
+    for u, ust in unit_stages(plan.describe(), wl.stages):
+        uplan = api.Plan(wl.C, wl.N, ust, flags=args.flags)
+        uws = uplan.workspace()
+        k_u = max(10, args.steps // 3)
+        t_u = time_gpu(lambda: uplan.execute(x, x_fir, uws), k_u, 3, stream, torch, None) / k_u
+        uplan.close()
+        del uws
+        unit_rows.append(unit_roofline(u, units, t_u, step_s, pk, alu_peak))
+    bound = max(unit_rows, key=lambda r: r["kernel_ms"]) if unit_rows else {
+        "bound": "hbm", "kernel": "copy", "achieved": achieved_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s"}
+    bound = dict(bound)
     bound["frac"] = bound["achieved"] / bound["peak"]
-    bound["traffic"] = traffic_for(kern, wl.name)
+    bound["traffic"] = traffic_for(bound["kernel"], wl.name)
     hbm = {"bound": "hbm", "achieved": achieved_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
            "frac": achieved_gbs / pk["hbm_gbs"], "peak_source": pk["source"],
            "note": "8 B per channel-sample over the whole step"}
@@ -601,7 +653,7 @@ def main():
                        "chain": f"{S} SOS sections + FIR of {L} taps",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "l2": "inputs 737 MB > 129 MB L2, no flush", "plan_flags": args.flags},
-            "roofline": bound, "roofline_hbm": hbm, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": bound, "roofline_hbm": hbm, "units": unit_rows, "cpu_baseline": cpu, "e2e": e2e,
             "plain_gpu": plain, "gpu_launches": int(args.steps * plan.launches_per_execute), "clocks": clocks,
             "gpu": props.name, "fwd_bwd": fwd_bwd,
         }

@@ -127,9 +127,21 @@ int tfx_plan_create(tfx_plan **p, int64_t C, int64_t N, int64_t ld,
 size_t tfx_plan_workspace_size(const tfx_plan *p);
 
 /* Number of kernels one tfx_plan_execute launches (flag resets done with
- * cudaMemsetAsync and input copies for in-place tensor-core FIRs excluded);
- * -1 for a NULL plan. */
+ * cudaMemsetAsync and input copies for in-place tensor-core or single-block
+ * FFT FIRs excluded); -1 for a NULL plan. */
 int tfx_plan_launch_count(const tfx_plan *p);
+
+/* One line describing the plan's units in execution order, separated by
+ * ';', each "kind:key=value,...":
+ *   cascade:S=..,scan=block|warp,carry=fp32|fp64     (SOS sections only)
+ *   fused:S=..,L=..                                  (cascade + FIR, CUDA cores)
+ *   fir:L=..                                         (FIR on CUDA cores)
+ *   fir_tc:L=..,kernel=k_fir_tc|k_fir_tc_ws|k_fir_tc_long
+ *   fir_fft:L=..,M=..,B=..,P=..                      (P = 0: single-block)
+ * Writes at most len bytes including the terminating NUL into buf (buf may be
+ * NULL when len is 0) and returns the length of the full description (as
+ * snprintf does), or -1 for a NULL plan. */
+int tfx_plan_describe(const tfx_plan *p, char *buf, size_t len);
 
 /*
  * tfx_plan_execute -- run the chain: y = chain(x).  Asynchronous on s.

@@ -42,7 +42,8 @@ STATUS = {
 
 # every symbol include/tfx.h declares
 EXPORTS = [
-    "tfx_plan_create", "tfx_plan_workspace_size", "tfx_plan_launch_count", "tfx_plan_execute", "tfx_plan_execute_plain",
+    "tfx_plan_create", "tfx_plan_workspace_size", "tfx_plan_launch_count", "tfx_plan_describe", "tfx_plan_execute",
+    "tfx_plan_execute_plain",
     "tfx_plan_get_error", "tfx_plan_destroy", "tfx_fir", "tfx_sos", "tfx_chain",
     "tfx_chain_workspace_size", "tfx_cache_clear", "tfx_sos_noalloc", "tfx_strerror", "tfx_version",
     "tfx_chain_host", "tfx_host_cache_clear",
@@ -100,6 +101,8 @@ def lib():
     sp = ctypes.POINTER(Stage)
     L.tfx_plan_create.argtypes = [ctypes.POINTER(vp), i64, i64, i64, sp, i32, u32]
     L.tfx_plan_create.restype = ctypes.c_int
+    L.tfx_plan_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
+    L.tfx_plan_describe.restype = ctypes.c_int
     L.tfx_plan_workspace_size.argtypes = [vp]
     L.tfx_plan_workspace_size.restype = sz
     L.tfx_plan_launch_count.argtypes = [vp]

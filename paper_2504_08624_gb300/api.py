@@ -127,6 +127,23 @@ class Plan:
         self.launches_per_execute = int(N.lib().tfx_plan_launch_count(self._h))
         self._ws = None
 
+    def describe(self) -> list:
+        """The plan's units in execution order, e.g.
+        [{"kind": "cascade", "S": 8, "scan": "block", "carry": "fp32"},
+         {"kind": "fir_fft", "L": 1025, "M": 4096, "B": 3072, "P": 0}]."""
+        n = N.lib().tfx_plan_describe(self._h, None, 0)
+        buf = ctypes.create_string_buffer(n + 1)
+        N.lib().tfx_plan_describe(self._h, buf, n + 1)
+        units = []
+        for item in buf.value.decode().split(";") if n > 0 else []:
+            kind, _, rest = item.partition(":")
+            u = {"kind": kind}
+            for kv in rest.split(","):
+                k, _, v = kv.partition("=")
+                u[k] = int(v) if v.lstrip("-").isdigit() else v
+            units.append(u)
+        return units
+
     def workspace(self) -> torch.Tensor:
         if self._ws is None:
             self._ws = torch.empty(max(1, self.workspace_size), dtype=torch.uint8, device=self.device)

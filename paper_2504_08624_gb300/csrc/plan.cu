@@ -35,17 +35,19 @@ namespace {
 // partitions of B = M/2 taps).  The choice minimises a cost model fitted to
 // measured GB300 times per output (16 channels x 2.88M samples, microseconds
 // for the whole signal): single-block 55 + k_m M / B with
-// k = 71, 77.5, 87.6, 130 for m = 10..13 (the 55 is the memory traffic, the
-// rest the transforms); partitioned I_m + 22 P with I = 217, 246, 343 for
-// m = 11..13 (two launches and the spectra traffic).  A single block must
-// hold B >= M/8 outputs.  `force` (10..13) restricts the choice to that m.
+// k = 68, 75, 86, 130 for m = 10..13 (the 55 is the memory traffic, the rest
+// the transforms); partitioned I_m + s_m P with I = 218, 246, 343 and
+// s = 22.6, 23.5, 19 for m = 11..13 (two launches and the spectra traffic).
+// A single block must hold B >= M/8 outputs.  `force` (10..13) restricts the
+// choice to that m.
 struct FftScheme {
     int M = 0, P = 0;
 };
 
 FftScheme fft_scheme_for(int L, int force) {
-    static const double K[4] = {71.0, 77.5, 87.6, 130.0};
-    static const double I[4] = {0.0, 217.0, 246.0, 343.0};
+    static const double K[4] = {68.0, 75.0, 86.0, 130.0};
+    static const double I[4] = {0.0, 218.0, 246.0, 343.0};
+    static const double SP[4] = {22.0, 22.6, 23.5, 19.0};
     FftScheme best;
     double cost = 0.0;
     for (int m = 10; m <= 13; ++m) {
@@ -57,7 +59,7 @@ FftScheme fft_scheme_for(int L, int force) {
         }
         if (m >= 11 || force == m) {
             const int P = (L + M / 2 - 1) / (M / 2);
-            const double c = (m >= 11 ? I[m - 10] : 200.0) + 22.0 * P;
+            const double c = (m >= 11 ? I[m - 10] : 200.0) + SP[m - 10] * P;
             if (best.M == 0 || c < cost) best.M = M, best.P = P, cost = c;
         }
     }
@@ -1101,6 +1103,35 @@ int tfx_plan_launch_count(const tfx_plan* p) {
     int n = 0;
     for (const HostUnit& u : p->units) n += u.fft && u.fft_P > 0 ? 2 : 1;
     return p->units.empty() ? 1 : n;
+}
+
+int tfx_plan_describe(const tfx_plan* p, char* buf, size_t len) {
+    if (!p) return -1;
+    std::string d;
+    char item[160];
+    for (const HostUnit& u : p->units) {
+        if (!d.empty()) d += ';';
+        if (u.fft) {
+            snprintf(item, sizeof item, "fir_fft:L=%d,M=%d,B=%d,P=%d", u.L, u.fft_M, u.fft_B, u.fft_P);
+        } else if (u.tc) {
+            snprintf(item, sizeof item, "fir_tc:L=%d,kernel=%s", u.L,
+                     u.tc_variant == 1 ? "k_fir_tc_ws" : u.tc_variant == 2 ? "k_fir_tc_long" : "k_fir_tc");
+        } else if (u.S > 0 && u.L > 0) {
+            snprintf(item, sizeof item, "fused:S=%d,L=%d", u.S, u.L);
+        } else if (u.S > 0) {
+            snprintf(item, sizeof item, "cascade:S=%d,scan=%s,carry=%s", u.S, u.warp ? "warp" : "block",
+                     u.hiq ? "fp64" : "fp32");
+        } else {
+            snprintf(item, sizeof item, "fir:L=%d", u.L);
+        }
+        d += item;
+    }
+    if (buf && len > 0) {
+        const size_t n = std::min(len - 1, d.size());
+        memcpy(buf, d.data(), n);
+        buf[n] = '\0';
+    }
+    return (int)d.size();
 }
 
 int tfx_plan_execute(tfx_plan* p, const float* x, float* y, void* ws, size_t ws_bytes, tfx_stream s) {

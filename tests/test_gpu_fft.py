@@ -21,16 +21,35 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def _fft_block(L):
-    """(M, B) the plan's cost model picks: least M (m + 3) / B over m = 10..13
-    with B = M - (L - 1) >= M/4."""
+def _scheme(L, force=None):
+    """(M, P) the plan's cost model picks (P = 0: single block): single-block
+    55 + k_m M / B (B >= M/8), partitioned I_m + s_m P, fitted per m."""
+    K = {10: 68.0, 11: 75.0, 12: 86.0, 13: 130.0}
+    I = {11: 218.0, 12: 246.0, 13: 343.0}
+    SP = {10: 22.0, 11: 22.6, 12: 23.5, 13: 19.0}
     best = None
     for m in range(10, 14):
+        if force is not None and m != force:
+            continue
         M = 1 << m
         B = M - (L - 1)
-        if B >= M // 4 and (best is None or M * (m + 3) / B < best[0]):
-            best = (M * (m + 3) / B, M, B)
+        if B >= M // 8:
+            c = 55.0 + K[m] * M / B
+            if best is None or c < best[0]:
+                best = (c, M, 0)
+        if m >= 11 or force == m:
+            P = -(-L // (M // 2))
+            c = (I[m] if m >= 11 else 200.0) + SP[m] * P
+            if best is None or c < best[0]:
+                best = (c, M, P)
     return best[1], best[2]
+
+
+def _fft_block(L):
+    """(M, B) of the single-block scheme the model picks for L."""
+    M, P = _scheme(L)
+    assert P == 0
+    return M, M - (L - 1)
 
 
 def run_fft(x, stages, inplace=False, ld=None, flags=0):
@@ -60,8 +79,9 @@ def _taps(L, seed):
     return np.random.default_rng(seed).standard_normal(L) / math.sqrt(L)
 
 
-@pytest.mark.parametrize("L", [64, 65, 129, 257, 335, 1025, 2049, 4097, 6145])
+@pytest.mark.parametrize("L", [64, 65, 129, 257, 335, 1025, 2049, 4097])
 def test_fft_fir_lengths(L):
+    """Forced FFT route (the model picks single-block for these lengths)."""
     M, B = _fft_block(L)
     for Ns in (1, B - 1, B, B + 1, 3 * B + 17):
         x = W.white_gauss(3, Ns, 31)
@@ -109,12 +129,11 @@ def test_fft_fir_empty():
         p.close()
 
 
-def _part_block(L, m=None):
-    """(M, B, P) of the partitioned scheme: least 2 (m + 3) + 2P over m = 11..13."""
-    if m is None:
-        m = min(range(11, 14), key=lambda q: 2 * (q + 3) + 2 * -(-L // ((1 << q) // 2)))
-    M = 1 << m
-    return M, M // 2, -(-L // (M // 2))
+def _part_block(L):
+    """(M, B, P) of the partitioned scheme the model picks for L."""
+    M, P = _scheme(L)
+    assert P > 0
+    return M, M // 2, P
 
 
 @pytest.mark.parametrize("L", [6146, 8193, 16384, 20000])
@@ -180,3 +199,24 @@ def test_fft_fir_gradient_matches_oracle(L):
     x = W.white_gauss(3, 30000, 36)
     g = W.white_gauss(3, 30000, 37)
     check_grad(x, g, stages, flags=N_.TFX_PLAN_FIR_FFT)
+
+
+def test_plan_describe_routes():
+    """The plan description names each unit's route: the default sends a
+    1025-tap FIR to the FFT, TFX_PLAN_FIR_TC keeps it on the tensor cores, a
+    16384-tap FIR is partitioned, a short FIR behind a cascade stays fused."""
+    from paper_2504_08624_gb300 import _native as N_
+    from paper_2504_08624_gb300 import api
+    wl = W.multichannel_fused()
+    d = api.Plan(4, 100000, wl.stages).describe()
+    assert [u["kind"] for u in d] == ["cascade", "fir_fft"]
+    assert d[0]["S"] == 8 and d[1]["L"] == 1025 and d[1]["P"] == 0 and d[1]["B"] == d[1]["M"] - 1024
+    d = api.Plan(4, 100000, wl.stages, flags=N_.TFX_PLAN_FIR_TC).describe()
+    assert [u["kind"] for u in d] == ["cascade", "fir_tc"] and d[1]["kernel"].startswith("k_fir_tc")
+    d = api.Plan(2, 100000, W.long_fir().stages).describe()
+    assert d[0]["kind"] == "fir_fft" and d[0]["P"] == -(-16384 // (d[0]["M"] // 2))
+    d = api.Plan(2, 100000, [("sos", W.butter_sos(4, 1000.0, W.FS)), ("fir", _taps(31, 1))]).describe()
+    assert [u["kind"] for u in d] == ["fused"]
+    p = api.Plan(2, 100000, W.long_fir().stages)
+    assert p.launches_per_execute == 2
+    p.close()
