@@ -178,7 +178,8 @@ def unit_roofline(u, units, t, step_s, pk, alu_peak) -> dict:
                     "note": f"{f:.1f} algorithmic flop per output (5 M log2 M per transform)"})
     else:
         S, L = u.get("S", 0), u.get("L", 0)
-        row.update({"bound": "alu", "kernel": "k_sos_warp" if u.get("scan") == "warp" else "k_unit",
+        kern = {"warp": "k_sos_warp", "seg": "k_sos_seg+k_sos_seg_fix"}.get(u.get("scan"), "k_unit")
+        row.update({"bound": "alu", "kernel": kern,
                     "achieved": units * (10.0 * S + 2.0 * L) / t / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
                     "peak_source": "SMs x 128 FP32 lanes x 2 flop x max SM clock",
                     "note": "10 flop per SOS section, 2L per FIR tap, per sample"})

@@ -102,6 +102,19 @@ typedef struct {
 #define TFX_PLAN_FIR_TC 128u
 #define TFX_PLAN_FIR_FFT_LOG(m) ((uint32_t)(m) << 16)
 #define TFX_PLAN_FIR_FFT_LOG_MASK (15u << 16)
+/* Cascade-only units of at most 8 sections (poles of radius <= 0.999) run
+ * on the tensor cores by default: blocks of 112 samples, the zero-state
+ * response and the block end state by one GEMM (lower-triangular Toeplitz
+ * of the cascade's impulse response, FP16 hi/lo operands, FP32 accumulation),
+ * a 16-dimensional scan of the block start states, their free responses by
+ * a second GEMM.  Channels are cut into segments walked by one persistent
+ * CTA per SM; each segment but a channel's first starts from zero state and
+ * a second launch adds the free response of its true start state over its
+ * first D samples, D chosen at plan time so that the remaining tail is below
+ * 1e-9 of the free response's initial size (the unit keeps the look-back scan
+ * when no such D fits).  With this flag such units run the CUDA-core
+ * block-tile scan with decoupled look-back instead. */
+#define TFX_PLAN_SCAN_LOOKBACK 512u
 /* Test hook for failure detection: the first tile of channel 0 never publishes
  * its carries, so its successor's bounded wait runs out; the execution
  * completes (with wrong output) and tfx_plan_get_error() returns
@@ -134,6 +147,7 @@ int tfx_plan_launch_count(const tfx_plan *p);
 /* One line describing the plan's units in execution order, separated by
  * ';', each "kind:key=value,...":
  *   cascade:S=..,scan=block|warp,carry=fp32|fp64     (SOS sections only)
+ *   cascade:S=..,scan=seg,carry=fp32,segments=..,D=..  (by channel segments)
  *   fused:S=..,L=..                                  (cascade + FIR, CUDA cores)
  *   fir:L=..                                         (FIR on CUDA cores)
  *   fir_tc:L=..,kernel=k_fir_tc|k_fir_tc_ws|k_fir_tc_long
@@ -403,8 +417,10 @@ int tfx_batch_execute_group(tfx_batch *b, int32_t g, const float *x, float *y, v
  *   recursion coefficients, chunk-transfer powers; FP64 on the GPU) from
  *   rows = device FP64 array of every SOS row of the plan's chain in order
  *   (tfx_plan_sos_rows of them).  The plan's structure (units, kernels, the
- *   FP64-carry routing chosen at creation) is kept; FIR taps are not
- *   changed.  An unstable or invalid row sets the status read by
+ *   FP64-carry routing chosen at creation) is kept, except that cascades
+ *   running on the tensor cores (whose GEMM tables are derived from the
+ *   coefficients on the host) run the look-back scan from the first update
+ *   on; FIR taps are not changed.  An unstable or invalid row sets the status read by
  *   tfx_plan_get_error.  The first call uploads per-section descriptors
  *   (host-synchronous: make it before any capture); later calls are one
  *   launch, capturable.  Must not overlap an execution of the plan.

@@ -34,6 +34,7 @@ def TFX_PLAN_FIR_FFT_LOG(m: int) -> int:
 
 
 TFX_PLAN_TEST_DROP_PUBLISH = 256
+TFX_PLAN_SCAN_LOOKBACK = 512
 
 STATUS = {
     0: "TFX_OK", -1: "TFX_ERR_INVALID", -2: "TFX_ERR_UNSTABLE", -3: "TFX_ERR_WORKSPACE",

@@ -72,7 +72,7 @@ int batch_build(tfx_batch* b, const tfx_clip* clips, int32_t n, const tfx_batch_
     if (NB != 64 && NB != 128 && NB != 256) return TFX_ERR_INVALID;
     // the batched groups run FIRs on the tensor cores or fused with a cascade:
     // no FFT units
-    const uint32_t pflags = prm.plan_flags | TFX_PLAN_FIR_TC;
+    const uint32_t pflags = prm.plan_flags | TFX_PLAN_FIR_TC | TFX_PLAN_SCAN_LOOKBACK;
     if (pflags & (TFX_PLAN_SCAN_WARP_TILES | TFX_PLAN_TRAINABLE | TFX_PLAN_TEST_DROP_PUBLISH | TFX_PLAN_UNFUSED |
                   TFX_PLAN_FIR_FFT))
         return TFX_ERR_UNSUPPORTED;

@@ -290,6 +290,10 @@ int tfx_design_device(const tfx_design* specs, int32_t n, const int64_t* row_off
 // The per-section update descriptors of a plan are built and uploaded once
 // (host-synchronous); every update after that is one launch.
 int tfx::plan_update_sections(tfx_plan* p, const double* rows_dev, cudaStream_t s) {
+    // tensor-core cascades hold GEMM tables derived from the coefficients on
+    // the host: such units run the look-back scan (whose constants are the
+    // ones updated here) from the first update on
+    for (HostUnit& u : p->units) u.seg = false;
     if (!p->dsec && p->nsec != 0) {
         std::vector<SecUpdate> v;
         int64_t row = 0;

@@ -25,46 +25,11 @@
 // The FIR then reads the cascade output of this tile plus the last L-1
 // cascade outputs of the preceding tile(s), which each tile publishes to
 // scratch before the successor needs them (so x == y is safe).
-#include "tfx_common.cuh"
+#include "sos_pass.cuh"
 
 namespace tfx {
 
 __device__ __forceinline__ int wphys(int p) { return p + (p >> 5); }
-
-template <int T>
-__device__ __forceinline__ void load_chunk(const float* row, int64_t n0, int64_t N, float (&u)[T]) {
-    const float* p = row + n0;
-    if (n0 + T <= N && ((reinterpret_cast<uintptr_t>(p) & 15) == 0)) {
-        const float4* p4 = reinterpret_cast<const float4*>(p);
-#pragma unroll
-        for (int i = 0; i < T / 4; ++i) {
-            float4 v = p4[i];
-            u[4 * i + 0] = v.x;
-            u[4 * i + 1] = v.y;
-            u[4 * i + 2] = v.z;
-            u[4 * i + 3] = v.w;
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < T; ++i) u[i] = (n0 + i < N) ? p[i] : 0.f;
-    }
-}
-
-template <int T>
-__device__ __forceinline__ void store_chunk(float* row, int64_t n0, int64_t N, const float (&u)[T],
-                                            float g) {
-    float* p = row + n0;
-    if (n0 + T <= N && ((reinterpret_cast<uintptr_t>(p) & 15) == 0)) {
-        float4* p4 = reinterpret_cast<float4*>(p);
-#pragma unroll
-        for (int i = 0; i < T / 4; ++i)
-            p4[i] = make_float4(u[4 * i] * g, u[4 * i + 1] * g, u[4 * i + 2] * g, u[4 * i + 3] * g);
-    } else {
-#pragma unroll
-        for (int i = 0; i < T; ++i)
-            if (n0 + i < N) p[i] = u[i] * g;
-    }
-}
 
 // acc[r] = sum_{k < nkb*R} taps[k] * win[base + r - k], base = FIR_PAD + H + o0.
 // Register window xw[m] = win[base_kb - R + m]; taps walked R at a time.
@@ -128,68 +93,9 @@ __device__ __forceinline__ void unit_tile(const UnitArgs& a, const int64_t tile)
             const float* cf = a.k.coef + 8 * s;
             b0 = cf[0]; c1 = cf[1]; c2 = cf[2]; a1 = cf[3]; a2 = cf[4];
         }
-        // 1. (fix-up of s-1 +) zero-state pass of s.  State (w1, w2) of the
-        // transposed direct form II, updated as w1' = c1 u - a1 w1 + w2,
-        // w2' = c2 u - a2 w1, y = b0 u + w1, with c1 = b1 - a1 b0, c2 = b2 - a2 b0
-        // formed in FP64 at plan time (avoids cancelling b1 u against a1 y).
-        // Three loop bodies, so that no predicated-off instruction is issued.
-        float w1 = 0.f, w2 = 0.f;
-        if (run && !fix) {
-#pragma unroll
-            for (int t = 0; t < T; ++t) {
-                const float v = u[t];
-                u[t] = fmaf(b0, v, w1);
-                const float n1 = fmaf(c1, v, fmaf(-a1, w1, w2));
-                w2 = fmaf(c2, v, -a2 * w1);
-                w1 = n1;
-            }
-        } else if (run) {
-            float h1 = st.x, h2 = 0.f;
-            {
-                const float v = u[0] + st.x;
-                u[0] = fmaf(b0, v, w1);
-                const float n1 = fmaf(c1, v, fmaf(-a1, w1, w2));
-                w2 = fmaf(c2, v, -a2 * w1);
-                w1 = n1;
-            }
-            {
-                const float h = fmaf(-pa1, h1, st.y);
-                h2 = h1;
-                h1 = h;
-                const float v = u[1] + h;
-                u[1] = fmaf(b0, v, w1);
-                const float n1 = fmaf(c1, v, fmaf(-a1, w1, w2));
-                w2 = fmaf(c2, v, -a2 * w1);
-                w1 = n1;
-            }
-#pragma unroll
-            for (int t = 2; t < T; ++t) {
-                const float h = fmaf(-pa1, h1, -pa2 * h2);
-                h2 = h1;
-                h1 = h;
-                const float v = u[t] + h;
-                u[t] = fmaf(b0, v, w1);
-                const float n1 = fmaf(c1, v, fmaf(-a1, w1, w2));
-                w2 = fmaf(c2, v, -a2 * w1);
-                w1 = n1;
-            }
-        } else if (fix) {
-            float h1 = st.x, h2 = 0.f;
-            u[0] += st.x;
-            {
-                const float h = fmaf(-pa1, h1, st.y);
-                h2 = h1;
-                h1 = h;
-                u[1] += h;
-            }
-#pragma unroll
-            for (int t = 2; t < T; ++t) {
-                const float h = fmaf(-pa1, h1, -pa2 * h2);
-                h2 = h1;
-                h1 = h;
-                u[t] += h;
-            }
-        }
+        // 1. (fix-up of s-1 +) zero-state pass of s
+        float w1, w2;
+        section_pass<T>(u, fix, run, b0, c1, c2, a1, a2, st, pa1, pa2, w1, w2);
         if (!run) break;
         const float4* P = a.k.pw + (size_t)s * PW_LEN;
 

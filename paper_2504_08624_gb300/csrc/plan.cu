@@ -2,6 +2,7 @@
 // device constants), workspace layout, launches, the one-shot plan cache and
 // the C-ABI entry points declared in include/tfx.h.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -29,6 +30,221 @@ void tfx::tc_geometry(HostUnit& u, int NB) {
 
 
 namespace {
+
+// One step of a cascade's whole state in FP64 with input u: x = (w1_0, w2_0,
+// ..., w1_(S-1), w2_(S-1)) -> x', each section driven by the previous one's
+// output; returns the cascade output y = C x + D u.
+double cascade_free_step(const std::vector<double>& sec, int S, const double* x, double* xn, double u) {
+    double v = u;
+    for (int i = 0; i < S; ++i) {
+        const double* r = &sec[5 * (size_t)i];  // b0 b1 b2 a1 a2 (a0-normalised)
+        const double c1 = r[1] - r[3] * r[0], c2 = r[2] - r[4] * r[0];
+        const double w1 = x[2 * i], w2 = x[2 * i + 1];
+        const double out = r[0] * v + w1;
+        xn[2 * i] = c1 * v - r[3] * w1 + w2;
+        xn[2 * i + 1] = c2 * v - r[4] * w1;
+        v = out;
+    }
+    return v;
+}
+
+// 16 x 16 row-major products (state dimension 2S <= 16, zero-padded).
+using Mat16 = std::array<double, 256>;
+Mat16 mat_mul(const Mat16& a, const Mat16& b) {
+    Mat16 c{};
+    for (int r = 0; r < 16; ++r)
+        for (int k = 0; k < 16; ++k) {
+            const double ark = a[r * 16 + k];
+            if (ark == 0.0) continue;
+            for (int m = 0; m < 16; ++m) c[r * 16 + m] += ark * b[k * 16 + m];
+        }
+    return c;
+}
+Mat16 mat_eye() {
+    Mat16 e{};
+    for (int i = 0; i < 16; ++i) e[i * 17] = 1.0;
+    return e;
+}
+
+uint16_t f2h(float f);  // FP32 -> FP16 bits and back, defined with the FIR tables below
+double h2d(uint16_t h);
+
+// Store v (row r, column k of a [rows x K] operand) into a canonical
+// no-swizzle K-major FP16 table: (r % 8) * 16 + (r / 8) * SBO + (k % 8) * 2 +
+// (k / 8) * 128 bytes.
+void canon_put(uint8_t* base, int r, int k, int K, uint16_t v) {
+    const size_t off = (size_t)(r % 8) * 16 + (size_t)(r / 8) * (K / 8) * 128 + (size_t)(k % 8) * 2 + (size_t)(k / 8) * 128;
+    std::memcpy(base + off, &v, 2);
+}
+
+// Decide whether cascade unit u runs on the tensor cores by channel segments
+// (k_sos_tc + k_sos_seg_fix) and build its tables.  D: the free response
+// y_n = C A^n s falls below 1e-9 of its initial size (the largest
+// ||C A^n||_1 over n < 64) after n = D0 (the search stops once it has stayed
+// below for D0 + 1024 steps, and gives up at 65536); D = 1.25 D0 rounded up
+// to 64 samples.  Segments: lengths a multiple of the 14336-sample tile and
+// at least 4 D, their number P per channel minimising the per-SM work
+// ceil(C P / SMs) x (tiles per segment + D / tile) (one persistent CTA per SM
+// walks its segments).
+void choose_segments(const tfx_plan* p, HostUnit& u, int sm_count) {
+    const int S = u.S, n2 = 2 * S;
+    Mat16 A{};
+    std::vector<double> Crow(n2, 0.0);
+    for (int m = 0; m < n2; ++m) {
+        double x[16] = {0}, xn[16] = {0};
+        x[m] = 1.0;
+        Crow[m] = cascade_free_step(u.sec, S, x, xn, 0.0);
+        for (int r = 0; r < n2; ++r) A[r * 16 + m] = xn[r];
+    }
+    std::vector<double> R = Crow, Rn(n2);
+    double ref = 0.0;
+    int64_t last = 0;
+    bool decayed = false;
+    for (int64_t n = 0; n < 65536; ++n) {
+        double norm = 0.0;
+        for (int r = 0; r < n2; ++r) norm += std::fabs(R[r]);
+        if (n < 64) {
+            ref = std::max(ref, norm);
+        } else if (norm > 1e-9 * ref) {
+            last = n;
+        } else if (n > 2 * last + 1024) {
+            decayed = true;
+            break;
+        }
+        for (int m = 0; m < n2; ++m) {
+            double acc = 0.0;
+            for (int r = 0; r < n2; ++r) acc += R[r] * A[r * 16 + m];
+            Rn[m] = acc;
+        }
+        R.swap(Rn);
+    }
+    if (!decayed) return;
+    const int D = (int)(((int64_t)(1.25 * (double)(last + 1)) + 63) / 64 * 64);
+    if ((int64_t)D > 64 * ((int64_t)1 << SEG_NPOW)) return;
+    const int64_t tiles = (p->N + TCS_TILE - 1) / TCS_TILE;
+    int64_t bestP = 1;
+    double best = 0.0;
+    for (int64_t P = 1; P <= tiles; ++P) {
+        const int64_t tps = (tiles + P - 1) / P;  // tiles per segment
+        if (P > 1 && tps * TCS_TILE < 4 * (int64_t)D) break;
+        const double work = (double)((p->C * P + sm_count - 1) / sm_count) *
+                            ((double)tps + (P > 1 ? (double)D / TCS_TILE : 0.0));
+        if (P == 1 || work < best) bestP = P, best = work;
+    }
+    const int64_t tps = (tiles + bestP - 1) / bestP;
+    const int64_t Lseg = tps * TCS_TILE;
+    const int64_t P = (p->N + Lseg - 1) / Lseg;
+    u.seg = true;
+    u.seg_P = P;
+    u.seg_len = Lseg;
+    u.seg_D = P > 1 ? D : 0;
+
+    // fix-up tables: A^(64 * 2^k), k < SEG_NPOW; A^Lseg
+    Mat16 A64 = mat_eye();
+    for (int t = 0; t < 64; ++t) A64 = mat_mul(A64, A);
+    u.segtab.assign((size_t)(SEG_NPOW + 1) * 256, 0.f);
+    Mat16 pk = A64;
+    for (int b = 0; b < SEG_NPOW; ++b) {
+        for (int i = 0; i < 256; ++i) u.segtab[(size_t)b * 256 + i] = (float)pk[i];
+        pk = mat_mul(pk, pk);
+    }
+    Mat16 phi = mat_eye(), base = A64;
+    for (int64_t e = Lseg / 64; e > 0; e >>= 1) {
+        if (e & 1) phi = mat_mul(phi, base);
+        base = mat_mul(base, base);
+    }
+    for (int i = 0; i < 256; ++i) u.segtab[(size_t)SEG_NPOW * 256 + i] = (float)phi[i];
+    auto norm_inf = [](const Mat16& m) {
+        double b = 0.0;
+        for (int r = 0; r < 16; ++r) {
+            double row = 0.0;
+            for (int c = 0; c < 16; ++c) row += std::fabs(m[r * 16 + c]);
+            b = std::max(b, row);
+        }
+        return b;
+    };
+    u.seg_J = 1;
+    Mat16 pj = phi;
+    while (norm_inf(pj) > 1e-12 && u.seg_J < P) {
+        pj = mat_mul(pj, phi);
+        ++u.seg_J;
+    }
+
+    // tensor-core tables.  Impulse response h, input-to-state columns
+    // A^(111-k) B, free-response rows C A^m, block transfer A^112.
+    double Bv[16] = {0}, x0[16] = {0};
+    const double Dd = cascade_free_step(u.sec, S, x0, Bv, 1.0);
+    std::vector<double> h(TCS_KB);
+    h[0] = Dd;
+    {
+        double x[16], xn[16];
+        std::copy(Bv, Bv + 16, x);
+        for (int n = 1; n < TCS_KB; ++n) {
+            double acc = 0.0;
+            for (int r = 0; r < n2; ++r) acc += Crow[r] * x[r];
+            h[n] = acc;
+            for (int r = 0; r < 16; ++r) xn[r] = 0.0;
+            for (int r = 0; r < n2; ++r)
+                for (int m = 0; m < n2; ++m) xn[r] += A[r * 16 + m] * x[m];
+            std::copy(xn, xn + 16, x);
+        }
+    }
+    std::vector<double> A1((size_t)128 * TCS_KB, 0.0), A2((size_t)128 * 16, 0.0);
+    for (int m = 0; m < TCS_KB; ++m)
+        for (int k = 0; k <= m; ++k) A1[(size_t)m * TCS_KB + k] = h[m - k];
+    {
+        double col[16];
+        std::copy(Bv, Bv + 16, col);  // A^0 B for k = 111
+        for (int k = TCS_KB - 1; k >= 0; --k) {
+            for (int r = 0; r < 16; ++r) A1[(size_t)(TCS_KB + r) * TCS_KB + k] = col[r];
+            double nx[16] = {0};
+            for (int r = 0; r < n2; ++r)
+                for (int m = 0; m < n2; ++m) nx[r] += A[r * 16 + m] * col[m];
+            std::copy(nx, nx + 16, col);
+        }
+        std::vector<double> row(Crow.begin(), Crow.end());
+        row.resize(16, 0.0);
+        for (int m = 0; m < TCS_KB; ++m) {
+            for (int r = 0; r < 16; ++r) A2[(size_t)m * 16 + r] = row[r];
+            double nr[16] = {0};
+            for (int c = 0; c < n2; ++c)
+                for (int r = 0; r < n2; ++r) nr[c] += row[r] * A[r * 16 + c];
+            std::copy(nr, nr + 16, row.begin());
+        }
+    }
+    u.tc_a1.assign((size_t)2 * TCS_A1_BYTES, 0);
+    u.tc_a2.assign((size_t)2 * TCS_A2_BYTES, 0);
+    u.tc_rowinv.assign(128, 1.f);
+    for (int m = 0; m < 128; ++m) {
+        double mx = 0.0;
+        for (int k = 0; k < TCS_KB; ++k) mx = std::max(mx, std::fabs(A1[(size_t)m * TCS_KB + k]));
+        for (int r = 0; r < 16; ++r) mx = std::max(mx, std::fabs(A2[(size_t)m * 16 + r]));
+        int sh = 0;
+        if (mx > 0.0) sh = std::max(-126, std::min(126, 14 - std::ilogb(mx)));
+        const double sc = std::ldexp(1.0, sh);
+        u.tc_rowinv[m] = (float)std::ldexp(1.0, -sh);
+        for (int k = 0; k < TCS_KB; ++k) {
+            const float v = (float)(A1[(size_t)m * TCS_KB + k] * sc);
+            const uint16_t hi = f2h(v), lo = f2h((float)(v - h2d(hi)));
+            canon_put(u.tc_a1.data(), m, k, TCS_KB, hi);
+            canon_put(u.tc_a1.data() + TCS_A1_BYTES, m, k, TCS_KB, lo);
+        }
+        for (int r = 0; r < 16; ++r) {
+            const float v = (float)(A2[(size_t)m * 16 + r] * sc);
+            const uint16_t hi = f2h(v), lo = f2h((float)(v - h2d(hi)));
+            canon_put(u.tc_a2.data(), m, r, 16, hi);
+            canon_put(u.tc_a2.data() + TCS_A2_BYTES, m, r, 16, lo);
+        }
+    }
+    Mat16 phib = mat_eye();
+    for (int t = 0; t < TCS_KB; ++t) phib = mat_mul(phib, A);
+    u.tc_phib.assign(8 * 256, 0.f);
+    Mat16 phj = phib;
+    for (int j = 0; j < 8; ++j) {
+        for (int i = 0; i < 256; ++i) u.tc_phib[(size_t)j * 256 + i] = (float)phj[i];
+        phj = mat_mul(phj, phib);
+    }
+}
 
 // Overlap-save scheme for an L-tap FIR: transform size M = 2^m and number of
 // partitions P (0: single-block, B = M - (L - 1) outputs per block; else
@@ -391,6 +607,16 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
     for (HostUnit& u : p->units)
         u.warp = (u.S > 0 && u.L == 0) && ((p->flags & TFX_PLAN_SCAN_WARP_TILES) || p->train || u.hiq);
 
+    // cascade-only block-tile units by channel segments where the free
+    // response decays early enough
+    if (!(p->flags & (TFX_PLAN_SCAN_LOOKBACK | TFX_PLAN_TEST_DROP_PUBLISH)) && p->C > 0 && p->N > 0) {
+        int sm_count = 152, dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess)
+            cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
+        for (HostUnit& u : p->units)
+            if (u.S > 0 && u.S <= SEG_SMAX && u.L == 0 && !u.warp && !u.hiq) choose_segments(p, u, sm_count);
+    }
+
     // constant blob layout
     size_t off = 0;
     for (HostUnit& u : p->units) {
@@ -410,6 +636,12 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
             off = align_up(off + (size_t)u.a_chunks * 128);
             u.off_alo = off;
             off = align_up(off + (size_t)u.a_chunks * 128);
+        }
+        if (u.seg) {
+            u.off_seg = off;
+            off = align_up(off + u.segtab.size() * sizeof(float));
+            u.off_tc = off;
+            off = align_up(off + u.tc_a1.size() + u.tc_a2.size() + (u.tc_rowinv.size() + u.tc_phib.size()) * 4);
         }
         if (u.fft) {
             u.off_H = off;
@@ -453,6 +685,15 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         }
         float* taps = reinterpret_cast<float*>(host.data() + u.off_taps);
         for (int k = 0; k < u.L; ++k) taps[k] = (float)u.taps[k];
+        if (u.seg) {
+            std::memcpy(host.data() + u.off_seg, u.segtab.data(), u.segtab.size() * sizeof(float));
+            char* t = host.data() + u.off_tc;
+            std::memcpy(t, u.tc_a1.data(), u.tc_a1.size());
+            std::memcpy(t + u.tc_a1.size(), u.tc_a2.data(), u.tc_a2.size());
+            std::memcpy(t + u.tc_a1.size() + u.tc_a2.size(), u.tc_rowinv.data(), u.tc_rowinv.size() * 4);
+            std::memcpy(t + u.tc_a1.size() + u.tc_a2.size() + u.tc_rowinv.size() * 4, u.tc_phib.data(),
+                        u.tc_phib.size() * 4);
+        }
         if (u.fft) {
             // spectrum of h zero-padded to M, scaled by 1/M (the inverse FFT's
             // normalisation), in bit-reversed order; twiddles e^(-2 pi i k / M)
@@ -543,6 +784,10 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
                 if (prepare_fir_fft(u.fft_M) != cudaSuccess) return TFX_ERR_UNSUPPORTED;
                 continue;
             }
+            if (u.seg) {
+                if (prepare_sos_tc() != cudaSuccess) return TFX_ERR_UNSUPPORTED;
+                continue;
+            }
             if (u.tc) {
                 if (u.tc_variant == 1) {
                     if (prepare_fir_tc_ws(u.tc_smem_ws) != cudaSuccess) return TFX_ERR_UNSUPPORTED;
@@ -582,6 +827,9 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
                 zbytes = std::max(zbytes, align_up((size_t)((p->C + 1) / 2) * (size_t)u.ntt * u.fft_M * sizeof(float2)));
             continue;
         }
+        if (u.seg)  // segment end states in the scratch region (the look-back fields
+                    // below are kept too: a coefficient update switches the unit to that scan)
+            zbytes = std::max(zbytes, align_up((size_t)p->C * (size_t)u.seg_P * SEG_SMAX * sizeof(float2)));
         if (u.warp) u.ntt = p->N > 0 ? (p->N + WARP_TILE - 1) / WARP_TILE : 0;
         const int H = u.L > 0 ? u.L - 1 : 0;
         u.tail_len = u.L > 0 ? (H < TILE ? H : TILE) : 0;
@@ -721,6 +969,34 @@ int launch_unit_range(tfx_plan* p, int i, const float* in, int64_t ldin, float* 
         f.a_lo = reinterpret_cast<const uint4*>(p->dconst + u.off_alo);
         f.status = p->dstatus;
         return launch_fir_tc(f, s) == cudaSuccess ? TFX_OK : TFX_ERR_CUDA;
+    }
+    if (u.seg) {
+        SegArgs g{};
+        g.x = in;
+        g.ldx = ldin;
+        g.y = out;
+        g.ldy = ldout;
+        g.C = Cg;
+        g.N = p->N;
+        g.S = u.S;
+        g.gain = 1.0f;
+        g.coef = reinterpret_cast<const float*>(p->dconst + u.off_coef);
+        g.Lseg = u.seg_len;
+        g.P = u.seg_P;
+        g.e_out = reinterpret_cast<float2*>(scratch);
+        g.D = u.seg_D;
+        g.J = u.seg_J;
+        const float* tab = reinterpret_cast<const float*>(p->dconst + u.off_seg);
+        g.Pk = tab;
+        g.Phi = tab + SEG_NPOW * 256;
+        const char* t = p->dconst + u.off_tc;
+        g.a1 = reinterpret_cast<const uint4*>(t);
+        g.a2 = reinterpret_cast<const uint4*>(t + u.tc_a1.size());
+        g.rowinv = reinterpret_cast<const float*>(t + u.tc_a1.size() + u.tc_a2.size());
+        g.phib = g.rowinv + u.tc_rowinv.size();
+        g.status = p->dstatus;
+        if (launch_sos_tc(g, p->sm_count, s) != cudaSuccess) return TFX_ERR_CUDA;
+        return launch_seg_fix(g, s) == cudaSuccess ? TFX_OK : TFX_ERR_CUDA;
     }
     UnitArgs a{};
     a.x = in;
@@ -1070,8 +1346,7 @@ int tfx::plan_create_ex(tfx_plan** out, int64_t C, int64_t N, int64_t ld, const 
     if (rc != TFX_OK) return rc;
     if (flags & ~(TFX_PLAN_FIR_CUDA_CORES | TFX_PLAN_UNFUSED | TFX_PLAN_FIR_BF16_PLAIN | TFX_PLAN_FIR_BF16_SPLIT |
                   TFX_PLAN_SCAN_WARP_TILES | TFX_PLAN_TRAINABLE | TFX_PLAN_FIR_FFT | TFX_PLAN_FIR_TC |
-                  TFX_PLAN_FIR_FFT_LOG_MASK |
-                  TFX_PLAN_TEST_DROP_PUBLISH))
+                  TFX_PLAN_FIR_FFT_LOG_MASK | TFX_PLAN_SCAN_LOOKBACK | TFX_PLAN_TEST_DROP_PUBLISH))
         return TFX_ERR_INVALID;
     tfx_plan* p = new (std::nothrow) tfx_plan();
     if (!p) return TFX_ERR_NOMEM;
@@ -1101,7 +1376,7 @@ int tfx_plan_launch_count(const tfx_plan* p) {
     if (!p) return -1;
     if (p->C == 0 || p->N == 0) return 0;
     int n = 0;
-    for (const HostUnit& u : p->units) n += u.fft && u.fft_P > 0 ? 2 : 1;
+    for (const HostUnit& u : p->units) n += (u.fft && u.fft_P > 0) || (u.seg && u.seg_P > 1 && u.seg_D > 0) ? 2 : 1;
     return p->units.empty() ? 1 : n;
 }
 
@@ -1118,6 +1393,9 @@ int tfx_plan_describe(const tfx_plan* p, char* buf, size_t len) {
                      u.tc_variant == 1 ? "k_fir_tc_ws" : u.tc_variant == 2 ? "k_fir_tc_long" : "k_fir_tc");
         } else if (u.S > 0 && u.L > 0) {
             snprintf(item, sizeof item, "fused:S=%d,L=%d", u.S, u.L);
+        } else if (u.S > 0 && u.seg) {
+            snprintf(item, sizeof item, "cascade:S=%d,scan=tc,carry=fp32,segments=%lld,D=%d", u.S,
+                     (long long)u.seg_P, u.seg_D);
         } else if (u.S > 0) {
             snprintf(item, sizeof item, "cascade:S=%d,scan=%s,carry=%s", u.S, u.warp ? "warp" : "block",
                      u.hiq ? "fp64" : "fp32");

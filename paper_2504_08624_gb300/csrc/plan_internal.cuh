@@ -42,6 +42,16 @@ struct HostUnit {
     bool fft = false;
     int fft_M = 0, fft_m = 0, fft_B = 0;
     int fft_P = 0;  // 0: single-block overlap-save; else partitions of fft_B = M/2 taps
+    // cascade on the tensor cores by channel segments (k_sos_tc): segments per
+    // channel, their length, free-response length, fix-up power tables
+    // Q[32], A^2048, A^Lseg
+    bool seg = false;
+    int64_t seg_P = 0, seg_len = 0;
+    int seg_D = 0, seg_J = 1;
+    size_t off_seg = 0, off_tc = 0;
+    std::vector<float> segtab;
+    std::vector<uint8_t> tc_a1, tc_a2;       // GEMM operands (hi, lo), canonical FP16 layout
+    std::vector<float> tc_rowinv, tc_phib;   // 1 / row scales, block transfer A^112
     size_t off_H = 0, off_tw = 0;
     // trainable plans: where each section's raw row (6 values) and the FIR's
     // taps sit in the flat coefficient-gradient array, the raw rows for the

@@ -146,6 +146,42 @@ struct FirTcArgs {
     int* status;
 };
 
+// Cascade on the tensor cores by channel segments (k_sos_tc, k_sos_seg_fix).
+// Blocks of TCS_KB samples; per block, one M = 128 GEMM row set gives the
+// TCS_KB outputs of the block's zero-state response (lower-triangular
+// Toeplitz of the cascade's impulse response) and the 16 components of its
+// zero-start end state; a 16-dimensional scan over blocks gives each block's
+// start state s_b, and a K = 16 GEMM adds the free response O s_b.
+constexpr int SEG_SMAX = 8;                  // sections (state dimension 2S <= 16)
+constexpr int SEG_NPOW = 11;                 // powers A^(64 * 2^k): fix-ups of up to 2^11 chunks of 64 samples
+constexpr int TCS_KB = 112;                  // samples per block (M rows 0..111; 112..127: end state)
+constexpr int TCS_NB = 128;                  // blocks per tile (N)
+constexpr int TCS_TILE = TCS_KB * TCS_NB;    // 14336 samples
+constexpr int TCS_A1_BYTES = 128 * TCS_KB * 2;  // one 16-bit [128 x 112] operand, canonical K-major
+constexpr int TCS_A2_BYTES = 128 * 16 * 2;      // one 16-bit [128 x 16] operand
+struct SegArgs {
+    const float* x;
+    float* y;
+    int64_t ldx, ldy;
+    int64_t C, N;
+    int S;
+    float gain;
+    const float* coef;  // [S][8] as UnitConst::coef
+    int64_t Lseg;       // segment length, a multiple of TCS_TILE
+    int64_t P;          // segments per channel
+    float2* e_out;      // [C * P][SEG_SMAX]: each segment's end state from zero start
+    int D;              // samples of free response added at each segment start (multiple of 64)
+    int J;              // segments back whose end state still reaches a start state (||A^(J Lseg)|| tiny)
+    const float* Pk;    // [SEG_NPOW][16][16]: A^(64 * 2^k), A the one-sample transfer of the whole cascade state
+    const float* Phi;   // [16][16]: A^Lseg
+    // tensor-core segment kernel
+    const uint4* a1;       // [2][TCS_A1_BYTES / 16]: [Toeplitz rows; end-state rows], hi then lo (FP16, row-scaled)
+    const uint4* a2;       // [2][TCS_A2_BYTES / 16]: free-response rows O, hi then lo (same row scales)
+    const float* rowinv;   // [128]: 1 / row scale
+    const float* phib;     // [8][16][16]: (A^TCS_KB)^j, j = 1..8 (block transfer powers)
+    int* status;
+};
+
 // FIR by FFT overlap-save: blocks of B = M - (L - 1) outputs, two blocks per CTA.
 struct FirFftArgs {
     const float* x;
@@ -315,6 +351,10 @@ __device__ __forceinline__ float4 mm2(float4 a, float4 b) {
 
 // Launchers (defined in the kernel translation units).
 cudaError_t launch_unit(const UnitArgs& a, cudaStream_t s);
+cudaError_t launch_sos_tc(const SegArgs& a, int grid, cudaStream_t s);
+cudaError_t prepare_sos_tc();
+size_t sos_tc_smem_bytes();
+cudaError_t launch_seg_fix(const SegArgs& a, cudaStream_t s);
 cudaError_t launch_sos_warp(const UnitArgs& a, cudaStream_t s);
 cudaError_t launch_plain_sos(const float* x, float* y, int64_t C, int64_t N, int64_t ldx,
                              int64_t ldy, int S, const float* coef, cudaStream_t s);

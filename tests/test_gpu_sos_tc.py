@@ -1,0 +1,127 @@
+"""Cascade on the tensor cores (k_sos_tc + k_sos_seg_fix) against the FP64
+oracle and against the CUDA-core look-back scan (TFX_PLAN_SCAN_LOOKBACK).
+
+The route: blocks of 112 samples, zero-state responses and zero-start end
+states by GEMM, a 16-dimensional scan of the block start states, their free
+responses by a second GEMM; channels cut into segments (one persistent CTA
+per SM walks its segments), segment starts corrected by the free response of
+their true start state over D samples.  Cases: every section count up to 8,
+poles up to radius 0.996 (D of several thousand samples), lengths ending
+inside a block and a tile, single-segment and many-segment channels, loud
+tiles next to quiet ones (per-tile scales), in-place operation and padded
+strides.  Tolerance 1e-4 of each channel's peak."""
+import numpy as np
+import pytest
+
+from paper_2504_08624_gb300 import workloads as W
+from tests.gpu_util import assert_close, oracle_chain
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TILE = 112 * 128
+
+
+def _run(x, stages, flags=0, inplace=False, ld=None):
+    from paper_2504_08624_gb300 import api
+    C, Ns = x.shape
+    ld = Ns if ld is None else ld
+    buf = torch.zeros(C * ld + 8, dtype=torch.float32, device="cuda")
+    xv = buf[:C * ld].view(C, ld)[:, :Ns]
+    xv.copy_(torch.from_numpy(x))
+    p = api.Plan(C, Ns, stages, ld=ld, flags=flags)
+    desc = p.describe()
+    y = xv if inplace else torch.zeros_like(buf)[:C * ld].view(C, ld)[:, :Ns]
+    p.execute(xv, y)
+    torch.cuda.synchronize()
+    assert p.get_error() == 0
+    p.close()
+    return y.cpu().numpy().astype(np.float64), desc
+
+
+def _check(x, stages, oracle_channels=None, min_segments=1, **kw):
+    """oracle_channels: compare only these channels with the oracle (the
+    channels are independent; long multichannel cases keep the oracle short)."""
+    from paper_2504_08624_gb300 import _native as N_
+    got, desc = _run(x, stages, **kw)
+    assert desc[0]["kind"] == "cascade" and desc[0]["scan"] == "tc", desc
+    assert desc[0]["segments"] >= min_segments, desc
+    sel = slice(None) if oracle_channels is None else oracle_channels
+    assert_close(got[sel], oracle_chain(x[sel], stages), 1e-4, str(kw))
+    lb, d2 = _run(x, stages, flags=N_.TFX_PLAN_SCAN_LOOKBACK)
+    assert d2[0]["scan"] == "block"
+    assert_close(got, lb, 1e-4, "vs look-back scan")
+    return desc[0]
+
+
+@pytest.mark.parametrize("S", [1, 2, 3, 4, 5, 8])
+def test_tc_cascade_sections(S):
+    x = W.white_uniform(3, 3 * TILE + 1001, 50 + S)
+    _check(x, [("sos", W.random_stable_sos(S, 60 + S, 0.3, 0.99))])
+
+
+@pytest.mark.parametrize("N", [1, 111, 112, 113, TILE - 1, TILE, TILE + 1, 5 * TILE + 7777])
+def test_tc_cascade_lengths(N):
+    x = W.white_gauss(2, N, 51)
+    _check(x, [("sos", W.butter_sos(4, 3000.0, W.FS))])
+
+
+def test_tc_cascade_many_segments():
+    """Few channels, long signal: each channel is cut into many segments whose
+    starts are fixed up (the multichannel workload's 8 sections, poles to
+    0.996, D ~ 6000)."""
+    wl = W.multichannel_fused()
+    sos = [st for st in wl.stages if st[0] == "sos"]
+    x = wl.make_signal(2, 3_000_000)
+    d = _check(x, sos, min_segments=8)
+    assert d["D"] >= 4096
+
+
+def test_tc_cascade_multichannel_chain():
+    """The multichannel workload's cascade on 16 channels of its recipe."""
+    wl = W.multichannel_fused()
+    sos = [st for st in wl.stages if st[0] == "sos"]
+    x = wl.make_signal(16, 1_000_000)
+    _check(x, sos, oracle_channels=slice(0, 16, 5))
+
+
+def test_tc_cascade_loud_then_quiet():
+    """Per-tile scales: tiles 1e4 louder next to near-silent ones (the carried
+    state of a loud tile enters a quiet tile's free-response operand)."""
+    rng = np.random.default_rng(54)
+    N = 6 * TILE + 500
+    x = rng.uniform(-1, 1, (2, N)).astype(np.float32)
+    x[:, : 2 * TILE] *= 1e4
+    x[:, 3 * TILE: 4 * TILE] *= 1e-4
+    rows = W.random_stable_sos(4, 55, 0.5, 0.99)
+    got, desc = _run(x, [("sos", rows)])
+    assert desc[0]["scan"] == "tc"
+    from tests.gpu_util import assert_close_floored
+    assert_close_floored(got, oracle_chain(x, [("sos", rows)]), x, 1e-4, "loud/quiet")
+
+
+@pytest.mark.parametrize("inplace", [False, True])
+def test_tc_cascade_inplace_and_stride(inplace):
+    x = W.white_uniform(3, 900_000, 52)
+    _check(x, [("sos", W.random_peaking_bank(4, W.FS, 7))], inplace=inplace, ld=900_000 + 13)
+
+
+def test_tc_cascade_then_fir():
+    """Cascade on the tensor cores, then the FFT FIR unit (the headline chain's layout)."""
+    wl = W.multichannel_fused()
+    x = wl.make_signal(16, 1_100_000)
+    got, d = _run(x, wl.stages)
+    assert d[0]["scan"] == "tc" and d[1]["kind"] == "fir_fft", d
+    assert_close(got[:2], oracle_chain(x[:2], wl.stages), wl.tol, "chain")
+
+
+def test_tc_route_not_for_high_q_or_long_cascades():
+    """Poles beyond 0.999 keep the FP64-carry warp scan, cascades of more than
+    8 sections the look-back scan."""
+    from paper_2504_08624_gb300 import api
+    p = api.Plan(2, 100_000, [("sos", np.array([[1.0, 0.0, -1.0, 1.0, -1.9994, 0.9995]]))])
+    assert p.describe()[0]["scan"] == "warp"
+    p.close()
+    p = api.Plan(2, 100_000, [("sos", W.random_stable_sos(9, 3, 0.3, 0.95))])
+    assert p.describe()[0]["scan"] == "block"
+    p.close()
