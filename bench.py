@@ -176,9 +176,18 @@ def unit_roofline(u, units, t, step_s, pk, alu_peak) -> dict:
                     "peak_source": "SMs x 128 FP32 lanes x 2 flop x max SM clock",
                     "config": {"L": u["L"], "M": u["M"], "B": u["B"], "P": u["P"]},
                     "note": f"{f:.1f} algorithmic flop per output (5 M log2 M per transform)"})
+    elif k == "cascade" and u.get("scan") == "tc":
+        # tensor-core cascade: streams the signal once (8 B per sample); its tensor
+        # work (GEMM1 128 x 112 and GEMM2 128 x 16 per 112-sample block, 3 split
+        # products) takes under half the time the HBM traffic does at peak
+        execf = 2.0 * 3 * 128 * (112 + 16) / 112
+        row.update({"bound": "hbm", "kernel": "k_sos_tc+k_sos_seg_fix", "achieved": units * 8.0 / t / 1e9,
+                    "peak": pk["hbm_gbs"], "unit": "GB/s", "peak_source": pk["source"],
+                    "executed_tflops": units * execf / t / 1e12,
+                    "note": "8 B per sample (FP32 read + write); executed tensor flop per sample %.0f" % execf})
     else:
         S, L = u.get("S", 0), u.get("L", 0)
-        kern = {"warp": "k_sos_warp", "seg": "k_sos_seg+k_sos_seg_fix"}.get(u.get("scan"), "k_unit")
+        kern = {"warp": "k_sos_warp"}.get(u.get("scan"), "k_unit")
         row.update({"bound": "alu", "kernel": kern,
                     "achieved": units * (10.0 * S + 2.0 * L) / t / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
                     "peak_source": "SMs x 128 FP32 lanes x 2 flop x max SM clock",
