@@ -625,7 +625,9 @@ def main():
         t_u = time_gpu(lambda: uplan.execute(x, x_fir, uws), k_u, 3, stream, torch, None) / k_u
         uplan.close()
         del uws
-        unit_rows.append(unit_roofline(u, units, t_u, step_s, pk, alu_peak))
+        row = unit_roofline(u, units, t_u, step_s, pk, alu_peak)
+        row["traffic"] = traffic_for(row["kernel"], wl.name)
+        unit_rows.append(row)
     bound = max(unit_rows, key=lambda r: r["kernel_ms"]) if unit_rows else {
         "bound": "hbm", "kernel": "copy", "achieved": achieved_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s"}
     bound = dict(bound)

@@ -82,9 +82,10 @@ typedef struct {
  * (longer cascades are split); tfx_plan_execute still works on such a plan. */
 #define TFX_PLAN_TRAINABLE 32u
 /* FIRs of 64 taps or more by FFT overlap-save instead of the tensor-core
- * Toeplitz GEMM (without this flag, FIRs of 768 taps or more take the FFT
- * route unless TFX_PLAN_FIR_TC, _FIR_BF16_PLAIN or _FIR_BF16_SPLIT is set or
- * the FIR stages run on CUDA cores), with hand-written register-resident
+ * Toeplitz GEMM.  This is also the default route (measured faster on GB300
+ * at every length from 65 taps); the flag keeps it when TFX_PLAN_FIR_TC,
+ * _FIR_BF16_PLAIN or _FIR_BF16_SPLIT is set too, and FIR stages on CUDA cores
+ * (TFX_PLAN_FIR_CUDA_CORES) never take it.  Hand-written register-resident
  * radix-16 FFTs of
  * M = 1024..8192 points (FP32; the error is ~log2(M) eps of each block's
  * energy rather than per product).  Up to 6145 taps: blocks of

@@ -110,6 +110,21 @@ __device__ __forceinline__ void dft_dit(float2 (&v)[16]) {
     if constexpr (G >= 16) stage<G, ST, OFF, 8, true>(v);
 }
 
+// A table entry by an ordinary global load, kept in program order: read-only
+// (non-coherent) loads may be hoisted across the passes' barriers, and the
+// kernel then holds later passes' twiddles (and the inverse's) in registers
+// through the earlier ones.
+__device__ __forceinline__ float2 ld_tw(const float2* p) {
+    float2 r;
+    asm volatile("ld.global.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "l"(p));
+    return r;
+}
+__device__ __forceinline__ float4 ld_tw4(const float4* p) {
+    float4 r;
+    asm volatile("ld.global.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "l"(p));
+    return r;
+}
+
 // Multiply slot q (q = Q..G-1) of the group v[OFF + q*ST] by the pass
 // twiddle w_S^(i * bitrev(q)) (INV: its conjugate), read from the pass's
 // table at [q - 1][i] (row length `sub`): consecutive i are consecutive words.
@@ -117,7 +132,7 @@ template <int G, int ST, int OFF, bool INV, int Q = 1>
 __device__ __forceinline__ void twiddle_group(float2 (&v)[16], const float2* __restrict__ tp, int sub) {
     if constexpr (Q < G) {
         constexpr int i = OFF + Q * ST;
-        const float2 w = __ldg(tp + (Q - 1) * sub);
+        const float2 w = ld_tw(tp + (Q - 1) * sub);
         v[i] = INV ? cmulc(v[i], w) : cmul(v[i], w);
         twiddle_group<G, ST, OFF, INV, Q + 1>(v, tp, sub);
     }
@@ -292,7 +307,7 @@ __global__ void __launch_bounds__((1 << LOGM) / 16) k_fir_fft(FirFftArgs a) {
     const float4* h4 = reinterpret_cast<const float4*>(a.H) + t;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        const float4 h = __ldg(h4 + q * F::T);
+        const float4 h = ld_tw4(h4 + q * F::T);
         v[2 * q] = cmul(v[2 * q], make_float2(h.x, h.y));
         v[2 * q + 1] = cmul(v[2 * q + 1], make_float2(h.z, h.w));
     }

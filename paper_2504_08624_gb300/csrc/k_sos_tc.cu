@@ -35,7 +35,8 @@
 //
 // Persistent kernel, one CTA per SM, 416 threads:
 //   warps 0-3    epilogue (TMEM lane quadrant = warp): y = acc1 / (row tau_b) + acc2 / (row rho)
-//   warps 4-7    producers: two threads per block -> max -> tau_b -> hi/lo operand stage i % 2
+//   warps 4-7    producers: two threads per block -> max -> tau_b -> hi/lo operand stage i % 2;
+//                thread 128 prefetches the next tile's samples into L2
 //   warps 8-11   scan group; warp 11 (lane quadrant 3) reads the end-state rows
 //   warp 12      TMEM allocation; lane 0 issues GEMM1 of tile i, then GEMM2 of tile i - 1
 // A CTA walks its segments (g = blockIdx.x + j * gridDim.x) tile by tile;
@@ -59,6 +60,9 @@ constexpr int TCS_MMA_WARP = 12;
 constexpr int TCS_GROUPS = TCS_NB / 8;             // scan groups of 8 blocks
 constexpr uint32_t TCS_SBO1 = (TCS_KB / 8) * 128;  // 1792
 constexpr uint32_t TCS_S_BYTES = TCS_NB * 16 * 2;   // one 16-bit [128 blocks x 16] operand
+// Row stride of the transposed end states seT[row][block]: a multiple of 4
+// (16-byte stores of 4 blocks) that spreads the rows over the banks.
+constexpr int TCS_SE_LD = TCS_NB + 4;
 constexpr int BAR_PROD = 1, BAR_SCAN = 2;           // named barriers
 
 struct Smem {
@@ -67,9 +71,9 @@ struct Smem {
     uint8_t u[2][2][TCS_A1_BYTES];  // [stage][hi, lo]: [128 blocks x 112]
     uint8_t sop[2][2][TCS_S_BYTES]; // [buffer][hi, lo]: [128 blocks x 16]
     __align__(16) float sf[TCS_NB][16];         // block start states s_b of the tile being scanned
-    __align__(16) float se[TCS_NB][16];         // zero-start block end states e_b
+    __align__(16) float seT[16][TCS_SE_LD];     // zero-start block end states, seT[row][b] = e_b[row]
     __align__(16) float sg[TCS_GROUPS][8][16];  // group terms G_(g,j), j = 2..8 at [j - 1]
-    float taub[4][TCS_NB];                       // 1 / tau_b per tile (ring of 4)
+    __align__(16) float taub[4][TCS_NB];         // 1 / tau_b per tile (ring of 4)
     float rowinv[128];
     uint64_t full[2], g1_done[2], s_ready[2], g2_done[2], acc_free[2];
     float rho[4];  // 1 / rho per tile (ring of 4)
@@ -134,6 +138,20 @@ __device__ __forceinline__ float dot16(const float (&row)[16], const float* v, f
     p1 = fmaf(row[13], q3.y, p1);
     p2 = fmaf(row[14], q3.z, p2);
     p3 = fmaf(row[15], q3.w, p3);
+    return (p0 + p1) + (p2 + p3);
+}
+
+// dot(row, v) + add with v[m] at p[m * ld] (a column of the transposed end states).
+__device__ __forceinline__ float dot16_col(const float (&row)[16], const float* p, float add) {
+    float p0 = fmaf(row[0], p[0], add), p1 = row[1] * p[TCS_SE_LD], p2 = row[2] * p[2 * TCS_SE_LD],
+          p3 = row[3] * p[3 * TCS_SE_LD];
+#pragma unroll
+    for (int m = 4; m < 16; m += 4) {
+        p0 = fmaf(row[m], p[m * TCS_SE_LD], p0);
+        p1 = fmaf(row[m + 1], p[(m + 1) * TCS_SE_LD], p1);
+        p2 = fmaf(row[m + 2], p[(m + 2) * TCS_SE_LD], p2);
+        p3 = fmaf(row[m + 3], p[(m + 3) * TCS_SE_LD], p3);
+    }
     return (p0 + p1) + (p2 + p3);
 }
 
@@ -207,6 +225,19 @@ __global__ void __launch_bounds__(TCS_THREADS, 1) k_sos_tc(SegArgs a) {
         for (TileWalk w(a); w.valid(); w.next()) {
             const int64_t i = w.i;
             const int st = (int)(i & 1);
+            if (ptid == 0) {
+                // the next tile's samples into L2 while this one is converted: the
+                // 16-byte-aligned interior of its range within the channel row
+                TileWalk nx = w;
+                nx.next();
+                if (nx.valid()) {
+                    const float* row = a.x + nx.c * a.ldx;
+                    const int64_t e = a.N < nx.n0() + TCS_TILE ? a.N : nx.n0() + TCS_TILE;
+                    const uintptr_t lo = (reinterpret_cast<uintptr_t>(row + nx.n0()) + 15) & ~uintptr_t(15);
+                    const uintptr_t hi = reinterpret_cast<uintptr_t>(row + e) & ~uintptr_t(15);
+                    if (hi > lo) tc::bulk_prefetch_l2(reinterpret_cast<const void*>(lo), (uint32_t)(hi - lo));
+                }
+            }
             if (i >= 2) {
                 if (ptid == 0) sm.ok_prod[st] = wait_bar(&sm.g1_done[st], (uint32_t)((i - 2) >> 1) & 1u, a.status) ? 1 : 0;
                 named_sync(BAR_PROD, TCS_PROD);
@@ -271,41 +302,54 @@ __global__ void __launch_bounds__(TCS_THREADS, 1) k_sos_tc(SegArgs a) {
             }
             named_sync(BAR_SCAN, 128);
             if (!sm.ok_scan[q]) break;
-            // end states: warp 11 reads TMEM lanes 96..127 (lanes 16..31: rows 112 + r)
+            // end states: warp 11 reads TMEM lanes 96..127 (lanes 16..31: rows 112 + er)
+            // and writes row er of seT, four blocks per 16-byte store
             if (warp == 11) {
                 tc::tc_fence_after();
                 const int er = lane - 16;
                 const float einv = er >= 0 ? sm.rowinv[TCS_KB + er] : 0.f;
-                const float* tb = sm.taub[i & 3];
+                const float4* tb4 = reinterpret_cast<const float4*>(sm.taub[i & 3]);
                 for (int cc = 0; cc < TCS_NB; cc += 16) {
                     float e[16];
                     tc::tmem_ld16(tmem + (96u << 16) + (uint32_t)(q * 128 + cc), e);
                     if (er >= 0) {
+                        float4* dst = reinterpret_cast<float4*>(&sm.seT[er][cc]);
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) sm.se[cc + j][er] = er < n2 ? e[j] * einv * tb[cc + j] : 0.f;
+                        for (int u = 0; u < 4; ++u) {
+                            const float4 t = tb4[cc / 4 + u];
+                            dst[u] = er < n2 ? make_float4(e[4 * u] * einv * t.x, e[4 * u + 1] * einv * t.y,
+                                                           e[4 * u + 2] * einv * t.z, e[4 * u + 3] * einv * t.w)
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
                     }
                 }
                 tc::tc_fence_before();
             }
             if (jj == 8) sm.sf[0][r] = carry;
             named_sync(BAR_SCAN, 128);
-            // group terms by Horner, 16 groups in parallel (the 8 threads of a group share a warp)
+            // group terms by Horner, 16 groups in parallel (the 8 threads of a group share a warp):
+            // G_2 = Phi e_8g + e_(8g+1) from the end states' column 8g, then G_(j+1) = Phi G_j + e_(8g+j)
             {
-                const float* prev = sm.se[8 * hg];
-                for (int j = 1; j < 8; ++j) {
-                    const float g0 = dot16(ph0, prev, sm.se[8 * hg + j][hr]);
-                    const float g1 = dot16(ph1, prev, sm.se[8 * hg + j][hr + 8]);
+                const float* e8 = &sm.seT[0][8 * hg];
+                const float g0 = dot16_col(ph0, e8, sm.seT[hr][8 * hg + 1]);
+                const float g1 = dot16_col(ph1, e8, sm.seT[hr + 8][8 * hg + 1]);
+                sm.sg[hg][1][hr] = g0;
+                sm.sg[hg][1][hr + 8] = g1;
+                __syncwarp();
+                for (int j = 2; j < 8; ++j) {
+                    const float* prev = sm.sg[hg][j - 1];
+                    const float h0 = dot16(ph0, prev, sm.seT[hr][8 * hg + j]);
+                    const float h1 = dot16(ph1, prev, sm.seT[hr + 8][8 * hg + j]);
                     __syncwarp();
-                    sm.sg[hg][j][hr] = g0;
-                    sm.sg[hg][j][hr + 8] = g1;
+                    sm.sg[hg][j][hr] = h0;
+                    sm.sg[hg][j][hr + 8] = h1;
                     __syncwarp();
-                    prev = sm.sg[hg][j];
                 }
             }
             named_sync(BAR_SCAN, 128);
             // chain: 16 steps of 8 blocks
             for (int g = 0; g < TCS_GROUPS; ++g) {
-                const float add = jj == 1 ? sm.se[8 * g][r] : sm.sg[g][jj - 1][r];
+                const float add = jj == 1 ? sm.seT[r][8 * g] : sm.sg[g][jj - 1][r];
                 const float v = r < n2 ? dot16(pj, sm.sf[8 * g], add) : 0.f;
                 if (8 * g + jj < TCS_NB) sm.sf[8 * g + jj][r] = v;
                 else carry = v;

@@ -250,32 +250,32 @@ void choose_segments(const tfx_plan* p, HostUnit& u, int sm_count) {
 // partitions P (0: single-block, B = M - (L - 1) outputs per block; else
 // partitions of B = M/2 taps).  The choice minimises a cost model fitted to
 // measured GB300 times per output (16 channels x 2.88M samples, microseconds
-// for the whole signal): single-block 55 + k_m M / B with
-// k = 68, 75, 86, 130 for m = 10..13 (the 55 is the memory traffic, the rest
-// the transforms); partitioned I_m + s_m P with I = 218, 246, 343 and
-// s = 22.6, 23.5, 19 for m = 11..13 (two launches and the spectra traffic).
-// A single block must hold B >= M/8 outputs.  `force` (10..13) restricts the
-// choice to that m.
+// for the whole signal): single-block 30 + k_m M / B with
+// k = 71, 74, 85, 121 for m = 10..13 (the 30 is the memory traffic, the rest
+// the transforms); partitioned I_m + s_m P with I = 219, 230, 253, 326 and
+// s = 20, 21.4, 23.6, 24.7 for m = 10..13 (two launches and the spectra
+// traffic).  A single block must hold B >= M/8 outputs.  `force` (10..13)
+// restricts the choice to that m.
 struct FftScheme {
     int M = 0, P = 0;
 };
 
 FftScheme fft_scheme_for(int L, int force) {
-    static const double K[4] = {68.0, 75.0, 86.0, 130.0};
-    static const double I[4] = {0.0, 218.0, 246.0, 343.0};
-    static const double SP[4] = {22.0, 22.6, 23.5, 19.0};
+    static const double K[4] = {71.0, 74.0, 85.0, 121.0};
+    static const double I[4] = {219.0, 230.0, 253.0, 326.0};
+    static const double SP[4] = {20.0, 21.4, 23.6, 24.7};
     FftScheme best;
     double cost = 0.0;
     for (int m = 10; m <= 13; ++m) {
         if (force >= 10 && force <= 13 && m != force) continue;
         const int M = 1 << m, B = M - (L - 1);
         if (B >= M / 8) {
-            const double c = 55.0 + K[m - 10] * M / B;
+            const double c = 30.0 + K[m - 10] * M / B;
             if (best.M == 0 || c < cost) best.M = M, best.P = 0, cost = c;
         }
         if (m >= 11 || force == m) {
             const int P = (L + M / 2 - 1) / (M / 2);
-            const double c = (m >= 11 ? I[m - 10] : 200.0) + SP[m - 10] * P;
+            const double c = I[m - 10] + SP[m - 10] * P;
             if (best.M == 0 || c < cost) best.M = M, best.P = P, cost = c;
         }
     }

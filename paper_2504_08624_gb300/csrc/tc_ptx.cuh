@@ -52,6 +52,13 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
+// Bulk prefetch of [src, src + bytes) into L2 (a hint: no completion, no
+// destination).  src 16-byte aligned, bytes a multiple of 16, the range inside
+// one allocation.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // --- fences -----------------------------------------------------------------
 // Make generic-proxy shared-memory writes visible to the tensor core (async proxy).
 __device__ __forceinline__ void fence_proxy_async_smem() {

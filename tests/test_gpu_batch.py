@@ -54,7 +54,7 @@ def run_batch(clips, **params):
 
 def _single_tc(xi, st):
     """The single-clip path with the batch's routing: long FIRs on the tensor
-    cores (the default single-clip route sends FIRs of 768+ taps to the FFT)."""
+    cores (the default single-clip route sends FIRs of 64+ taps to the FFT)."""
     from paper_2504_08624_gb300 import _native as N_
     from paper_2504_08624_gb300 import api
     C, Ns = xi.shape

@@ -23,10 +23,10 @@ pytestmark = pytest.mark.gpu
 
 def _scheme(L, force=None):
     """(M, P) the plan's cost model picks (P = 0: single block): single-block
-    55 + k_m M / B (B >= M/8), partitioned I_m + s_m P, fitted per m."""
-    K = {10: 68.0, 11: 75.0, 12: 86.0, 13: 130.0}
-    I = {11: 218.0, 12: 246.0, 13: 343.0}
-    SP = {10: 22.0, 11: 22.6, 12: 23.5, 13: 19.0}
+    30 + k_m M / B (B >= M/8), partitioned I_m + s_m P, fitted per m."""
+    K = {10: 71.0, 11: 74.0, 12: 85.0, 13: 121.0}
+    I = {10: 219.0, 11: 230.0, 12: 253.0, 13: 326.0}
+    SP = {10: 20.0, 11: 21.4, 12: 23.6, 13: 24.7}
     best = None
     for m in range(10, 14):
         if force is not None and m != force:
@@ -34,12 +34,12 @@ def _scheme(L, force=None):
         M = 1 << m
         B = M - (L - 1)
         if B >= M // 8:
-            c = 55.0 + K[m] * M / B
+            c = 30.0 + K[m] * M / B
             if best is None or c < best[0]:
                 best = (c, M, 0)
         if m >= 11 or force == m:
             P = -(-L // (M // 2))
-            c = (I[m] if m >= 11 else 200.0) + SP[m] * P
+            c = I[m] + SP[m] * P
             if best is None or c < best[0]:
                 best = (c, M, P)
     return best[1], best[2]
