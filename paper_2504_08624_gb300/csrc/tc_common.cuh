@@ -32,14 +32,13 @@ __device__ __forceinline__ void split8_bf16(const float (&v)[8], uint4& hi, uint
 __device__ __forceinline__ void split8_f16(const float (&v)[8], float scale, uint4& hi, uint4& lo) {
     uint32_t h[4], l[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 4; ++i) {  // pairs by the packed conversions (same roundings)
         const float s0 = v[2 * i] * scale, s1 = v[2 * i + 1] * scale;
-        const __half h0 = __float2half_rn(s0);
-        const __half h1 = __float2half_rn(s1);
-        const __half l0 = __float2half_rn(s0 - __half2float(h0));
-        const __half l1 = __float2half_rn(s1 - __half2float(h1));
-        h[i] = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
-        l[i] = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
+        const __half2 hh = __floats2half2_rn(s0, s1);
+        const float2 hf = __half22float2(hh);
+        const __half2 ll = __floats2half2_rn(s0 - hf.x, s1 - hf.y);
+        h[i] = *reinterpret_cast<const uint32_t*>(&hh);
+        l[i] = *reinterpret_cast<const uint32_t*>(&ll);
     }
     hi = make_uint4(h[0], h[1], h[2], h[3]);
     lo = make_uint4(l[0], l[1], l[2], l[3]);
