@@ -208,10 +208,16 @@ __global__ void __launch_bounds__(TCS_THREADS, 1) k_sos_tc(SegArgs a) {
                 tc::tmem_ld16(tmem + lane_base + (uint32_t)(q * 128 + cc), v1);
                 tc::tmem_ld16(tmem + lane_base + (uint32_t)(256 + q * 128 + cc), v2);
                 if (act) {
+                    float t16[16];  // the 16 blocks' 1 / tau_b, four 16-byte loads
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float4 t4 = reinterpret_cast<const float4*>(tb + cc)[u];
+                        t16[4 * u] = t4.x, t16[4 * u + 1] = t4.y, t16[4 * u + 2] = t4.z, t16[4 * u + 3] = t4.w;
+                    }
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const int64_t o = (int64_t)(cc + j) * TCS_KB + m;
-                        if (o < lim) yr[o] = fmaf(v1[j], rinv * tb[cc + j], v2[j] * u2);
+                        if (o < lim) yr[o] = fmaf(v1[j], rinv * t16[j], v2[j] * u2);
                     }
                 }
             }
@@ -220,7 +226,9 @@ __global__ void __launch_bounds__(TCS_THREADS, 1) k_sos_tc(SegArgs a) {
         }
     } else if (warp < 8) {
         // ---------------- producers ----------------
-        // thread pair (2 b, 2 b + 1) holds block b: 7 chunks of 8 samples each
+        // lanes l and l + 16 of a producer warp hold the two halves of one block
+        // (7 chunks of 8 samples each), so the 8 lanes of a quarter-warp store
+        // 8 different blocks' chunks: distinct bank groups of the operand layout
         const int ptid = tid - 128;
         for (TileWalk w(a); w.valid(); w.next()) {
             const int64_t i = w.i;
@@ -246,21 +254,22 @@ __global__ void __launch_bounds__(TCS_THREADS, 1) k_sos_tc(SegArgs a) {
             const float* xr = a.x + w.c * a.ldx;
             const int64_t n0 = w.n0();
             const bool vec = ((reinterpret_cast<uintptr_t>(xr + n0) & 15) == 0);
+            const bool vec32 = ((reinterpret_cast<uintptr_t>(xr + n0) & 31) == 0);
             uint8_t* uh = &sm.u[st][0][0];
             uint8_t* ul = &sm.u[st][1][0];
 #pragma unroll 1
             for (int it = 0; it < 2; ++it) {
-                const int hb = ptid + it * TCS_PROD;
-                const int b = hb >> 1, half = hb & 1;
+                const int b = it * (TCS_NB / 2) + (ptid >> 5) * 16 + (ptid & 15), half = (ptid >> 4) & 1;
                 float v[7][8];
 #pragma unroll
-                for (int j = 0; j < 7; ++j) load8(xr, n0 + (int64_t)b * TCS_KB + 8 * (7 * half + j), a.N, vec, v[j]);
+                for (int j = 0; j < 7; ++j)
+                    load8_32(xr, n0 + (int64_t)b * TCS_KB + 8 * (7 * half + j), a.N, vec32, vec, v[j]);
                 float mx = 0.f;
 #pragma unroll
                 for (int j = 0; j < 7; ++j)
 #pragma unroll
                     for (int e = 0; e < 8; ++e) mx = fmaxf(mx, fabsf(v[j][e]));
-                mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+                mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
                 const float tau = pow2_scale(mx);
 #pragma unroll
                 for (int j = 0; j < 7; ++j) {
