@@ -217,6 +217,9 @@ def test_plan_describe_routes():
     assert d[0]["kind"] == "fir_fft" and d[0]["P"] == -(-16384 // (d[0]["M"] // 2))
     d = api.Plan(2, 100000, [("sos", W.butter_sos(4, 1000.0, W.FS)), ("fir", _taps(31, 1))]).describe()
     assert [u["kind"] for u in d] == ["fused"]
+    # the FFT route is the default from 64 taps; shorter FIRs stay on the CUDA cores
+    assert api.Plan(2, 100000, [("fir", _taps(64, 2))]).describe()[0]["kind"] == "fir_fft"
+    assert api.Plan(2, 100000, [("fir", _taps(63, 2))]).describe()[0]["kind"] != "fir_fft"
     p = api.Plan(2, 100000, W.long_fir().stages)
     assert p.launches_per_execute == 2
     p.close()

@@ -101,9 +101,13 @@ def test_tc_cascade_loud_then_quiet():
 
 
 @pytest.mark.parametrize("inplace", [False, True])
-def test_tc_cascade_inplace_and_stride(inplace):
+@pytest.mark.parametrize("pad", [13, 4, 8])
+def test_tc_cascade_inplace_and_stride(inplace, pad):
+    """Row strides of N + pad floats: pad 8 keeps every row 32-byte aligned
+    (one 32-byte load per 8-sample chunk), pad 4 alternates 32- and 16-byte
+    aligned rows, pad 13 leaves rows 1 and 2 unaligned (scalar loads)."""
     x = W.white_uniform(3, 900_000, 52)
-    _check(x, [("sos", W.random_peaking_bank(4, W.FS, 7))], inplace=inplace, ld=900_000 + 13)
+    _check(x, [("sos", W.random_peaking_bank(4, W.FS, 7))], inplace=inplace, ld=900_000 + pad)
 
 
 def test_tc_cascade_then_fir():
