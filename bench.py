@@ -181,7 +181,7 @@ def unit_roofline(u, units, t, step_s, pk, alu_peak) -> dict:
         # work (GEMM1 128 x 112 and GEMM2 128 x 16 per 112-sample block, 3 split
         # products) takes under half the time the HBM traffic does at peak
         execf = 2.0 * 3 * 128 * (112 + 16) / 112
-        row.update({"bound": "hbm", "kernel": "k_sos_tc+k_sos_seg_fix", "achieved": units * 8.0 / t / 1e9,
+        row.update({"bound": "hbm", "kernel": "k_sos_tc", "achieved": units * 8.0 / t / 1e9,
                     "peak": pk["hbm_gbs"], "unit": "GB/s", "peak_source": pk["source"],
                     "executed_tflops": units * execf / t / 1e12,
                     "note": "8 B per sample (FP32 read + write); executed tensor flop per sample %.0f" % execf})

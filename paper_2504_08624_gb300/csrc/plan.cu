@@ -78,12 +78,14 @@ void canon_put(uint8_t* base, int r, int k, int K, uint16_t v) {
 }
 
 // Decide whether cascade unit u runs on the tensor cores by channel segments
-// (k_sos_tc + k_sos_seg_fix) and build its tables.  D: the free response
-// y_n = C A^n s falls below 1e-9 of its initial size (the largest
-// ||C A^n||_1 over n < 64) after n = D0 (the search stops once it has stayed
-// below for D0 + 1024 steps, and gives up at 65536); D = 1.25 D0 rounded up
-// to 64 samples.  Segments: lengths a multiple of the 14336-sample tile and
-// at least 4 D, their number P per channel minimising the per-SM work
+// (k_sos_tc) and build its tables.  D: the free response y_n = C A^n s falls
+// below 1e-9 of its initial size (the largest ||C A^n||_1 over n < 64) after
+// n = D0 (the search stops once it has stayed below for D0 + 1024 steps, and
+// gives up at 65536); D = 1.25 D0 rounded up to whole 112-sample blocks.
+// Every segment but a channel's first runs D warm-up samples from zero state
+// before its own range, so its state there is the true one to that accuracy.
+// Segments: lengths a multiple of the 14336-sample tile and at least 4 D,
+// their number P per channel minimising the per-SM work
 // ceil(C P / SMs) x (tiles per segment + D / tile) (one persistent CTA per SM
 // walks its segments).
 void choose_segments(const tfx_plan* p, HostUnit& u, int sm_count) {
@@ -119,8 +121,7 @@ void choose_segments(const tfx_plan* p, HostUnit& u, int sm_count) {
         R.swap(Rn);
     }
     if (!decayed) return;
-    const int D = (int)(((int64_t)(1.25 * (double)(last + 1)) + 63) / 64 * 64);
-    if ((int64_t)D > 64 * ((int64_t)1 << SEG_NPOW)) return;
+    const int D = (int)(((int64_t)(1.25 * (double)(last + 1)) + TCS_KB - 1) / TCS_KB * TCS_KB);
     const int64_t tiles = (p->N + TCS_TILE - 1) / TCS_TILE;
     int64_t bestP = 1;
     double best = 0.0;
@@ -138,37 +139,6 @@ void choose_segments(const tfx_plan* p, HostUnit& u, int sm_count) {
     u.seg_P = P;
     u.seg_len = Lseg;
     u.seg_D = P > 1 ? D : 0;
-
-    // fix-up tables: A^(64 * 2^k), k < SEG_NPOW; A^Lseg
-    Mat16 A64 = mat_eye();
-    for (int t = 0; t < 64; ++t) A64 = mat_mul(A64, A);
-    u.segtab.assign((size_t)(SEG_NPOW + 1) * 256, 0.f);
-    Mat16 pk = A64;
-    for (int b = 0; b < SEG_NPOW; ++b) {
-        for (int i = 0; i < 256; ++i) u.segtab[(size_t)b * 256 + i] = (float)pk[i];
-        pk = mat_mul(pk, pk);
-    }
-    Mat16 phi = mat_eye(), base = A64;
-    for (int64_t e = Lseg / 64; e > 0; e >>= 1) {
-        if (e & 1) phi = mat_mul(phi, base);
-        base = mat_mul(base, base);
-    }
-    for (int i = 0; i < 256; ++i) u.segtab[(size_t)SEG_NPOW * 256 + i] = (float)phi[i];
-    auto norm_inf = [](const Mat16& m) {
-        double b = 0.0;
-        for (int r = 0; r < 16; ++r) {
-            double row = 0.0;
-            for (int c = 0; c < 16; ++c) row += std::fabs(m[r * 16 + c]);
-            b = std::max(b, row);
-        }
-        return b;
-    };
-    u.seg_J = 1;
-    Mat16 pj = phi;
-    while (norm_inf(pj) > 1e-12 && u.seg_J < P) {
-        pj = mat_mul(pj, phi);
-        ++u.seg_J;
-    }
 
     // tensor-core tables.  Impulse response h, input-to-state columns
     // A^(111-k) B, free-response rows C A^m, block transfer A^112.
@@ -638,8 +608,6 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
             off = align_up(off + (size_t)u.a_chunks * 128);
         }
         if (u.seg) {
-            u.off_seg = off;
-            off = align_up(off + u.segtab.size() * sizeof(float));
             u.off_tc = off;
             off = align_up(off + u.tc_a1.size() + u.tc_a2.size() + (u.tc_rowinv.size() + u.tc_phib.size()) * 4);
         }
@@ -686,7 +654,6 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         float* taps = reinterpret_cast<float*>(host.data() + u.off_taps);
         for (int k = 0; k < u.L; ++k) taps[k] = (float)u.taps[k];
         if (u.seg) {
-            std::memcpy(host.data() + u.off_seg, u.segtab.data(), u.segtab.size() * sizeof(float));
             char* t = host.data() + u.off_tc;
             std::memcpy(t, u.tc_a1.data(), u.tc_a1.size());
             std::memcpy(t + u.tc_a1.size(), u.tc_a2.data(), u.tc_a2.size());
@@ -827,9 +794,8 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
                 zbytes = std::max(zbytes, align_up((size_t)((p->C + 1) / 2) * (size_t)u.ntt * u.fft_M * sizeof(float2)));
             continue;
         }
-        if (u.seg)  // segment end states in the scratch region (the look-back fields
-                    // below are kept too: a coefficient update switches the unit to that scan)
-            zbytes = std::max(zbytes, align_up((size_t)p->C * (size_t)u.seg_P * SEG_SMAX * sizeof(float2)));
+        // (a tensor-core cascade unit keeps the look-back fields below too: a
+        // coefficient update switches the unit to that scan)
         if (u.warp) u.ntt = p->N > 0 ? (p->N + WARP_TILE - 1) / WARP_TILE : 0;
         const int H = u.L > 0 ? u.L - 1 : 0;
         u.tail_len = u.L > 0 ? (H < TILE ? H : TILE) : 0;
@@ -983,20 +949,14 @@ int launch_unit_range(tfx_plan* p, int i, const float* in, int64_t ldin, float* 
         g.coef = reinterpret_cast<const float*>(p->dconst + u.off_coef);
         g.Lseg = u.seg_len;
         g.P = u.seg_P;
-        g.e_out = reinterpret_cast<float2*>(scratch);
         g.D = u.seg_D;
-        g.J = u.seg_J;
-        const float* tab = reinterpret_cast<const float*>(p->dconst + u.off_seg);
-        g.Pk = tab;
-        g.Phi = tab + SEG_NPOW * 256;
         const char* t = p->dconst + u.off_tc;
         g.a1 = reinterpret_cast<const uint4*>(t);
         g.a2 = reinterpret_cast<const uint4*>(t + u.tc_a1.size());
         g.rowinv = reinterpret_cast<const float*>(t + u.tc_a1.size() + u.tc_a2.size());
         g.phib = g.rowinv + u.tc_rowinv.size();
         g.status = p->dstatus;
-        if (launch_sos_tc(g, p->sm_count, s) != cudaSuccess) return TFX_ERR_CUDA;
-        return launch_seg_fix(g, s) == cudaSuccess ? TFX_OK : TFX_ERR_CUDA;
+        return launch_sos_tc(g, p->sm_count, s) == cudaSuccess ? TFX_OK : TFX_ERR_CUDA;
     }
     UnitArgs a{};
     a.x = in;
@@ -1376,7 +1336,7 @@ int tfx_plan_launch_count(const tfx_plan* p) {
     if (!p) return -1;
     if (p->C == 0 || p->N == 0) return 0;
     int n = 0;
-    for (const HostUnit& u : p->units) n += (u.fft && u.fft_P > 0) || (u.seg && u.seg_P > 1 && u.seg_D > 0) ? 2 : 1;
+    for (const HostUnit& u : p->units) n += u.fft && u.fft_P > 0 ? 2 : 1;
     return p->units.empty() ? 1 : n;
 }
 

@@ -43,13 +43,11 @@ struct HostUnit {
     int fft_M = 0, fft_m = 0, fft_B = 0;
     int fft_P = 0;  // 0: single-block overlap-save; else partitions of fft_B = M/2 taps
     // cascade on the tensor cores by channel segments (k_sos_tc): segments per
-    // channel, their length, free-response length, fix-up power tables
-    // Q[32], A^2048, A^Lseg
+    // channel, their length, warm-up length
     bool seg = false;
     int64_t seg_P = 0, seg_len = 0;
-    int seg_D = 0, seg_J = 1;
-    size_t off_seg = 0, off_tc = 0;
-    std::vector<float> segtab;
+    int seg_D = 0;  // warm-up samples before every segment but a channel's first
+    size_t off_tc = 0;
     std::vector<uint8_t> tc_a1, tc_a2;       // GEMM operands (hi, lo), canonical FP16 layout
     std::vector<float> tc_rowinv, tc_phib;   // 1 / row scales, block transfer A^112
     size_t off_H = 0, off_tw = 0;

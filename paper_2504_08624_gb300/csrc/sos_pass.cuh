@@ -1,7 +1,6 @@
-// Per-thread pieces of the SOS cascade scans shared by the block-tile kernel
-// (k_unit) and the segment kernel (k_sos_seg): chunk loads and stores, and one
-// section's pass over a thread's chunk fused with the previous section's
-// fix-up.
+// Per-thread pieces of the block-tile SOS cascade scan (k_unit): chunk loads
+// and stores, and one section's pass over a thread's chunk fused with the
+// previous section's fix-up.
 #pragma once
 
 #include "tfx_common.cuh"

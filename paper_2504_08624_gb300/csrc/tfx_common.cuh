@@ -146,14 +146,13 @@ struct FirTcArgs {
     int* status;
 };
 
-// Cascade on the tensor cores by channel segments (k_sos_tc, k_sos_seg_fix).
+// Cascade on the tensor cores by channel segments (k_sos_tc).
 // Blocks of TCS_KB samples; per block, one M = 128 GEMM row set gives the
 // TCS_KB outputs of the block's zero-state response (lower-triangular
 // Toeplitz of the cascade's impulse response) and the 16 components of its
 // zero-start end state; a 16-dimensional scan over blocks gives each block's
 // start state s_b, and a K = 16 GEMM adds the free response O s_b.
 constexpr int SEG_SMAX = 8;                  // sections (state dimension 2S <= 16)
-constexpr int SEG_NPOW = 11;                 // powers A^(64 * 2^k): fix-ups of up to 2^11 chunks of 64 samples
 constexpr int TCS_KB = 112;                  // samples per block (M rows 0..111; 112..127: end state)
 constexpr int TCS_NB = 128;                  // blocks per tile (N)
 constexpr int TCS_TILE = TCS_KB * TCS_NB;    // 14336 samples
@@ -169,11 +168,7 @@ struct SegArgs {
     const float* coef;  // [S][8] as UnitConst::coef
     int64_t Lseg;       // segment length, a multiple of TCS_TILE
     int64_t P;          // segments per channel
-    float2* e_out;      // [C * P][SEG_SMAX]: each segment's end state from zero start
-    int D;              // samples of free response added at each segment start (multiple of 64)
-    int J;              // segments back whose end state still reaches a start state (||A^(J Lseg)|| tiny)
-    const float* Pk;    // [SEG_NPOW][16][16]: A^(64 * 2^k), A the one-sample transfer of the whole cascade state
-    const float* Phi;   // [16][16]: A^Lseg
+    int D;              // warm-up samples run before every segment but a channel's first (multiple of TCS_KB)
     // tensor-core segment kernel
     const uint4* a1;       // [2][TCS_A1_BYTES / 16]: [Toeplitz rows; end-state rows], hi then lo (FP16, row-scaled)
     const uint4* a2;       // [2][TCS_A2_BYTES / 16]: free-response rows O, hi then lo (same row scales)
@@ -354,7 +349,6 @@ cudaError_t launch_unit(const UnitArgs& a, cudaStream_t s);
 cudaError_t launch_sos_tc(const SegArgs& a, int grid, cudaStream_t s);
 cudaError_t prepare_sos_tc();
 size_t sos_tc_smem_bytes();
-cudaError_t launch_seg_fix(const SegArgs& a, cudaStream_t s);
 cudaError_t launch_sos_warp(const UnitArgs& a, cudaStream_t s);
 cudaError_t launch_plain_sos(const float* x, float* y, int64_t C, int64_t N, int64_t ldx,
                              int64_t ldy, int S, const float* coef, cudaStream_t s);

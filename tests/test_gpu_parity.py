@@ -280,9 +280,8 @@ def test_cascade_tensor_fir_graph_capture(route):
     xt = torch.from_numpy(x).cuda()
     p = api.Plan(5, 30000, wl.stages, flags=N_.TFX_PLAN_FIR_TC if route == "tensor_cores" else 0)
     d = p.describe()
-    # cascade (plus the segment fix-up when its channels have several segments), FIR
-    expect = sum(2 if (u.get("scan") == "tc" and u["segments"] > 1 and u["D"] > 0) or u.get("P", 0) > 0 else 1
-                 for u in d)
+    # one launch per unit; a partitioned FFT FIR takes two (segment spectra, convolution)
+    expect = sum(2 if u.get("P", 0) > 0 else 1 for u in d)
     assert p.launches_per_execute == expect, d
     y = torch.empty_like(xt)
     ws = p.workspace()

@@ -1,11 +1,11 @@
-"""Cascade on the tensor cores (k_sos_tc + k_sos_seg_fix) against the FP64
+"""Cascade on the tensor cores (k_sos_tc) against the FP64
 oracle and against the CUDA-core look-back scan (TFX_PLAN_SCAN_LOOKBACK).
 
 The route: blocks of 112 samples, zero-state responses and zero-start end
 states by GEMM, a 16-dimensional scan of the block start states, their free
 responses by a second GEMM; channels cut into segments (one persistent CTA
-per SM walks its segments), segment starts corrected by the free response of
-their true start state over D samples.  Cases: every section count up to 8,
+per SM walks its segments), every segment but a channel's first started D
+samples early from zero state, its warm-up outputs discarded.  Cases: every section count up to 8,
 poles up to radius 0.996 (D of several thousand samples), lengths ending
 inside a block and a tile, single-segment and many-segment channels, loud
 tiles next to quiet ones (per-tile scales), in-place operation and padded
