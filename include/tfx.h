@@ -109,12 +109,12 @@ typedef struct {
  * of the cascade's impulse response, FP16 hi/lo operands, FP32 accumulation),
  * a 16-dimensional scan of the block start states, their free responses by
  * a second GEMM.  Channels are cut into segments walked by one persistent
- * CTA per SM; each segment but a channel's first starts from zero state and
- * a second launch adds the free response of its true start state over its
- * first D samples, D chosen at plan time so that the remaining tail is below
- * 1e-9 of the free response's initial size (the unit keeps the look-back scan
- * when no such D fits).  With this flag such units run the CUDA-core
- * block-tile scan with decoupled look-back instead. */
+ * CTA per SM; each segment but a channel's first starts D samples early
+ * from zero state (its warm-up outputs are discarded), D chosen at plan time
+ * so that the free response of the true state is below 1e-9 of its initial
+ * size after D samples (the unit keeps the look-back scan when no such D
+ * fits within 65536 samples).  One launch.  With this flag such units run
+ * the CUDA-core block-tile scan with decoupled look-back instead. */
 #define TFX_PLAN_SCAN_LOOKBACK 512u
 /* Test hook for failure detection: the first tile of channel 0 never publishes
  * its carries, so its successor's bounded wait runs out; the execution
