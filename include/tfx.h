@@ -141,8 +141,10 @@ int tfx_plan_create(tfx_plan **p, int64_t C, int64_t N, int64_t ld,
 size_t tfx_plan_workspace_size(const tfx_plan *p);
 
 /* Number of kernels one tfx_plan_execute launches (flag resets done with
- * cudaMemsetAsync and input copies for in-place tensor-core or single-block
- * FFT FIRs excluded); -1 for a NULL plan. */
+ * cudaMemsetAsync excluded, and so is the input copy an in-place call makes
+ * when its single unit reads other tiles' or segments' input: a tensor-core
+ * or single-block FFT FIR, or a segmented tensor-core cascade); -1 for a
+ * NULL plan. */
 int tfx_plan_launch_count(const tfx_plan *p);
 
 /* One line describing the plan's units in execution order, separated by

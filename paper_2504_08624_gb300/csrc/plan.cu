@@ -812,8 +812,11 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
     p->scratch_bytes = std::max(hdr + tails, zbytes);
     p->buf_bytes = align_up((size_t)p->C * (size_t)p->N * sizeof(float));
     size_t nbuf = p->units.size() > 2 ? 2 : (p->units.size() == 2 ? 1 : 0);
-    if (p->units.size() == 1 && (p->units[0].tc || (p->units[0].fft && p->units[0].fft_P == 0)))
-        nbuf = 1;  // input copy for in-place operation
+    if (p->units.size() == 1) {
+        // input copy for in-place operation: the unit reads other tiles' or segments' input
+        const HostUnit& u0 = p->units[0];
+        if (u0.tc || (u0.fft && u0.fft_P == 0) || (u0.seg && u0.seg_P > 1 && u0.seg_D > 0)) nbuf = 1;
+    }
     p->ws_fused = p->scratch_bytes + nbuf * p->buf_bytes;
     p->ws_plain = (nst > 0 ? 2 : 0) * p->buf_bytes;
 
@@ -950,6 +953,12 @@ int launch_unit_range(tfx_plan* p, int i, const float* in, int64_t ldin, float* 
         g.Lseg = u.seg_len;
         g.P = u.seg_P;
         g.D = u.seg_D;
+        if (g.x == g.y && g.P > 1 && g.D > 0) {  // warm-ups read the preceding segment's input: copy it first
+            if (!copy_buf) return TFX_ERR_INVALID;
+            if (launch_copy_rows(g.x, copy_buf, Cg, p->N, g.ldx, p->N, s) != cudaSuccess) return TFX_ERR_CUDA;
+            g.x = copy_buf;
+            g.ldx = p->N;
+        }
         const char* t = p->dconst + u.off_tc;
         g.a1 = reinterpret_cast<const uint4*>(t);
         g.a2 = reinterpret_cast<const uint4*>(t + u.tc_a1.size());

@@ -67,9 +67,9 @@ def test_tc_cascade_lengths(N):
 
 
 def test_tc_cascade_many_segments():
-    """Few channels, long signal: each channel is cut into many segments whose
-    starts are fixed up (the multichannel workload's 8 sections, poles to
-    0.996, D ~ 6000)."""
+    """Few channels, long signal: each channel is cut into many segments, each
+    but the first started D samples early (the multichannel workload's 8
+    sections, poles to 0.996, D ~ 6000)."""
     wl = W.multichannel_fused()
     sos = [st for st in wl.stages if st[0] == "sos"]
     x = wl.make_signal(2, 3_000_000)
@@ -98,6 +98,17 @@ def test_tc_cascade_loud_then_quiet():
     assert desc[0]["scan"] == "tc"
     from tests.gpu_util import assert_close_floored
     assert_close_floored(got, oracle_chain(x, [("sos", rows)]), x, 1e-4, "loud/quiet")
+
+
+def test_tc_cascade_inplace_many_rounds():
+    """In place, with more segments than CTAs (448 segments over the SMs, several
+    rounds of the persistent walk): a segment's warm-up reads the preceding
+    segment's input, which an in-place call must not see overwritten."""
+    wl = W.multichannel_fused()
+    sos = [st for st in wl.stages if st[0] == "sos"]
+    x = wl.make_signal(64, 200_000)
+    d = _check(x, sos, oracle_channels=slice(0, 64, 7), min_segments=4, inplace=True)
+    assert d["D"] > 0, d
 
 
 @pytest.mark.parametrize("inplace", [False, True])
