@@ -286,7 +286,7 @@ int tfx_chain(const float *x, float *y, int64_t C, int64_t N, int64_t ld,
  * host pointers with the same [C x N] layout and row stride ld (x == y
  * allowed); page-locked (pinned) buffers let the copies run asynchronously
  * and overlap, pageable ones still work but serialise.  Channels are cut
- * into groups of about 2^24 samples; group g is copied in, filtered and
+ * into groups of about 2^23 samples; group g is copied in, filtered and
  * copied out on three library-owned streams through a ring of three device
  * slots, so copies of neighbouring groups overlap each other and the
  * filtering.  The work is ordered after prior work on s and s waits for it:

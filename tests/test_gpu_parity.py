@@ -304,8 +304,8 @@ def test_cascade_tensor_fir_graph_capture(route):
 
 @pytest.mark.parametrize("mode", ["pinned", "pageable", "inplace_padded"])
 def test_host_pipeline_groups(mode):
-    """tfx_chain_host: 600 channels x 100,000 samples cut into 4 groups of
-    about 2^24 samples, so the 3-slot device ring wraps."""
+    """tfx_chain_host: 600 channels x 100,000 samples cut into 8 groups of
+    about 2^23 samples, so the 3-slot device ring wraps."""
     from paper_2504_08624_gb300 import api
     stages = [("sos", W.butter_sos(2, 2000.0, 48000.0)), ("fir", W.fir_lowpass(33, 6000.0, 48000.0))]
     C, Ns = 600, 100000
