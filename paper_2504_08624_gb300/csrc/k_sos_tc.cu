@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(TCS_THREADS, 1) k_sos_tc(SegArgs a) {
                     }
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        const int64_t o = (int64_t)(cc + j) * TCS_KB + m;
+                        const int o = (cc + j) * TCS_KB + m;  // within the tile: 32-bit
                         if (whole || (o >= lo && o < hi)) yr[o] = fmaf(v1[j], rinv * t16[j], v2[j] * u2);
                     }
                 }
