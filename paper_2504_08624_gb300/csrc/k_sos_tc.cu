@@ -35,8 +35,9 @@
 //
 // Persistent kernel, one CTA per SM, 416 threads:
 //   warps 0-3    epilogue (TMEM lane quadrant = warp): y = acc1 / (row tau_b) + acc2 / (row rho)
-//   warps 4-7    producers: two threads per block -> max -> tau_b -> hi/lo operand stage i % 2;
-//                thread 128 prefetches the next tile's samples into L2
+//   warps 4-7    producers: two threads per block (lanes l and l + 16) read its samples in
+//                32-byte chunks that do not allocate in L1 -> max -> tau_b -> hi/lo operand
+//                stage i % 2; thread 128 prefetches the next tile's samples into L2
 //   warps 8-11   scan group; warp 11 (lane quadrant 3) reads the end-state rows
 //   warp 12      TMEM allocation; lane 0 issues GEMM1 of tile i, then GEMM2 of tile i - 1
 // A CTA walks its segments (g = blockIdx.x + j * gridDim.x) tile by tile;
