@@ -11,6 +11,7 @@ The arithmetic lives in ``oracle.c`` (plain C, double precision):
                  lfilter with user-supplied coefficients).
   * ``fir``   -- causal direct convolution, output length N (TorchFX Sec. 3,
                  Table 2 workload).
+  * ``fir_at`` -- the same convolution at chosen output positions only.
   * ``chain`` -- stages applied in list order (TorchFX Sec. 3, pipe operator;
                  Table 4 workload).
   * ``chain_vjp`` -- gradients of sum(g * chain(x)) w.r.t. x and every
@@ -53,6 +54,8 @@ class OracleLib:
         lib.oracle_chain_vjp.argtypes = [dp, dp, dp, dp, i64, i64, ctypes.POINTER(i32),
                                          ctypes.POINTER(i32), ctypes.POINTER(dp), i32]
         lib.oracle_chain_vjp.restype = ctypes.c_int
+        lib.oracle_fir_at.argtypes = [dp, i64, dp, i32, ctypes.POINTER(i64), i64, dp]
+        lib.oracle_fir_at.restype = ctypes.c_int
         lib.oracle_num_threads.restype = ctypes.c_int
         lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
         lib.oracle_plant.restype = ctypes.c_int
@@ -90,6 +93,20 @@ class OracleLib:
         if rc != 0:
             raise ValueError(f"oracle_fir failed ({rc})")
         return y[0] if sq else y
+
+    def fir_at(self, x, h, idx):
+        """Causal direct convolution of one channel x with taps h, evaluated
+        only at the output positions idx (for signals too long to filter
+        whole in the time a check may take)."""
+        xx = np.ascontiguousarray(np.asarray(x, dtype=np.float64).ravel())
+        hh = np.ascontiguousarray(np.asarray(h, dtype=np.float64).ravel())
+        ii = np.ascontiguousarray(np.asarray(idx, dtype=np.int64).ravel())
+        out = np.empty(ii.size)
+        rc = self.lib.oracle_fir_at(self._dp(xx), xx.size, self._dp(hh), hh.size,
+                                    ii.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ii.size, self._dp(out))
+        if rc != 0:
+            raise ValueError(f"oracle_fir_at failed ({rc})")
+        return out
 
     def chain(self, x, stages):
         """stages: list of ("fir", taps) or ("sos", [S x 6] rows)."""
@@ -194,3 +211,7 @@ def fir(x, h):
 
 def chain(x, stages):
     return load().chain(x, stages)
+
+
+def fir_at(x, h, idx):
+    return load().fir_at(x, h, idx)

@@ -20,7 +20,7 @@
  *     y[n] = sum_{k=0}^{min(n, L-1)} h[k] * x[n-k].
  * A chain applies its stages in list order.  All arithmetic is in double.
  *
- * Planted mistakes: compiling with -DORACLE_PLANT=k (k = 1..7) introduces one
+ * Planted mistakes: compiling with -DORACLE_PLANT=k (k = 1..8) introduces one
  * deliberate error so that the test suite can show its pins catch it.  The
  * default build (ORACLE_PLANT undefined or 0) is the oracle.
  */
@@ -87,6 +87,37 @@ static void fir_channel(const double *x, double *y, int64_t N, const double *h, 
 #endif
         y[n] = acc;
     }
+}
+
+/*
+ * The causal direct convolution of one channel at chosen output positions
+ * only: out[i] = sum_{k=0}^{min(n, L-1)} h[k] * x[n-k] with n = idx[i]
+ * (0 <= n < N).  For long signals and long filters, where the whole output
+ * would take too long, a sample of it can still be checked one by one.
+ */
+int oracle_fir_at(const double *x, int64_t N, const double *h, int32_t L,
+                  const int64_t *idx, int64_t n_idx, double *out)
+{
+    if (N < 0 || L < 1 || !h || n_idx < 0 || (n_idx > 0 && (!idx || !out || !x)))
+        return ORACLE_ERR_INVALID;
+    for (int64_t i = 0; i < n_idx; ++i)
+        if (idx[i] < 0 || idx[i] >= N)
+            return ORACLE_ERR_INVALID;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n_idx; ++i) {
+        const int64_t n = idx[i];
+#if ORACLE_PLANT == 8
+        /* planted: the last tap dropped */
+        const int64_t kmax = n < (int64_t)(L - 2) ? n : (int64_t)(L - 2);
+#else
+        const int64_t kmax = n < (int64_t)(L - 1) ? n : (int64_t)(L - 1);
+#endif
+        double acc = 0.0;
+        for (int64_t k = 0; k <= kmax; ++k)
+            acc += h[k] * x[n - k];
+        out[i] = acc;
+    }
+    return ORACLE_OK;
 }
 
 static int check_sos(const double *sos, int32_t S)

@@ -86,6 +86,27 @@ def pin_fir_toeplitz(lib, rng):
         assert _rel(got, want) < 1e-13, f"FIR Toeplitz mismatch N={N} L={L}"
 
 
+def pin_fir_at_sampled(lib, rng):
+    """The FIR at chosen output positions: a unit impulse at position p gives
+    h[n - p] at every sampled n (zero before p and beyond p + L - 1), and a
+    random signal gives the rows of the explicit Toeplitz matrix product at
+    the sampled positions, including the first outputs (fewer than L terms)."""
+    L, N, p = 29, 300, 41
+    h = rng.standard_normal(L)
+    x = np.zeros(N)
+    x[p] = 1.0
+    idx = np.array([0, p - 1, p, p + 5, p + L - 1, p + L, N - 1])
+    want = np.array([h[n - p] if 0 <= n - p < L else 0.0 for n in idx])
+    assert np.array_equal(lib.fir_at(x, h, idx), want), "sampled FIR impulse mismatch"
+    x = rng.standard_normal(N)
+    T = np.zeros((N, N))
+    for i in range(N):
+        for k in range(min(L, i + 1)):
+            T[i, i - k] = h[k]
+    idx = np.array([0, 1, L - 2, L - 1, L, 150, N - 1])
+    assert _rel(lib.fir_at(x, h, idx), (T @ x)[idx]) < 1e-13, "sampled FIR Toeplitz mismatch"
+
+
 def pin_fir_dc_nyquist(lib, rng):
     """Constant input gives sum(h) once the delay line is full; (-1)^n gives
     (-1)^n sum_k (-1)^k h[k]."""
@@ -318,6 +339,7 @@ def pin_vjp_dx_sampled(lib, rng):
 ALL_PINS = [
     pin_fir_impulse,
     pin_fir_toeplitz,
+    pin_fir_at_sampled,
     pin_fir_dc_nyquist,
     pin_sos_impulse_closed_form,
     pin_sos_steady_state,

@@ -17,6 +17,7 @@ PLANTS = {
     5: "chain drops its last stage",
     6: "SOS a1/a2 swapped",
     7: "VJP: a1 sensitivity sign flipped",
+    8: "sampled FIR drops its last tap",
 }
 
 
