@@ -16,6 +16,7 @@ oracle on the host cores on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import math
@@ -59,6 +60,8 @@ def parse():
                          "(default for the differentiable_chain workload)")
     ap.add_argument("--no-fwdbwd", action="store_true",
                     help="skip the fwd+bwd measurement added to a forward run")
+    ap.add_argument("--no-long-fir", action="store_true",
+                    help="skip the long-FIR precision measurement added to a forward run")
     args = ap.parse_args()
     if args.mode is None:
         args.mode = "fwdbwd" if args.workload == "differentiable_chain" else "fwd"
@@ -123,8 +126,46 @@ def n_units(stages) -> int:
 
 
 def fp32_alu_peak_tflops(sm_count: int, sm_mhz: float) -> float:
-    # 128 FP32 lanes per SM, one FMA (2 flop) per lane per clock
+    # 128 FP32 lanes per SM, one FMA (2 flop) per lane per clock (nominal, for context)
     return sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def measure_fp32_peak(dev, stream, torch, sm_count: int, local: int) -> dict:
+    """The FP32 FMA rate of this GPU, measured: 8 CTAs of 256 threads per SM,
+    each thread 8 independent FMA chains of 4096 steps (scalar, and the packed
+    two-lane form), timed with CUDA events over 20 launches after 3 warm-ups,
+    with the SM clock sampled meanwhile.  The CUDA-core rooflines divide by
+    the larger of the two."""
+    from paper_2504_08624_gb300 import _native as NAT
+    lib = NAT.lib()
+    blocks, threads, iters = sm_count * 8, 256, 4096
+    out = torch.empty(blocks * threads, dtype=torch.float32, device=dev)
+    h = ctypes.c_void_p(stream.cuda_stream)
+    res = {}
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.2)
+    for packed in (0, 1):
+        def run():
+            NAT.check(lib.tfx_fma_probe(ctypes.c_void_p(out.data_ptr()), blocks, threads, iters, packed, h),
+                      "tfx_fma_probe")
+        k = 20
+        t = time_gpu(run, k, 3, stream, torch, None) / k
+        res["fma2" if packed else "fma"] = lib.tfx_fma_probe_flops(blocks, threads, iters, packed) / t / 1e12
+    clocks = sampler.stop()
+    peak = max(res.values())
+    return {"tflops": peak, "scalar_fma_tflops": res["fma"], "packed_fma2_tflops": res["fma2"], "clocks": clocks,
+            "how": f"{blocks} CTAs x {threads} threads x 8 FMA chains x {iters} steps, best of scalar and "
+                   "packed two-lane FMA, CUDA events over 20 launches"}
+
+
+def channel_rel_err(got, ref, scale=None):
+    """Per-channel max|got - ref| / max|ref| (or / scale when given)."""
+    got = np.asarray(got, dtype=np.float64).reshape(-1, np.asarray(got).shape[-1])
+    ref = np.asarray(ref, dtype=np.float64).reshape(got.shape)
+    err = np.max(np.abs(got - ref), axis=1)
+    sc = np.max(np.abs(ref), axis=1) if scale is None else np.asarray(scale, dtype=np.float64)
+    return err / np.maximum(sc, 1e-300)
 
 
 def unit_stages(desc, stages):
@@ -158,9 +199,17 @@ def fft_flops_per_output(u) -> float:
     return (10.0 * M * m + 8.0 * P * M) / M
 
 
-def unit_roofline(u, units, t, step_s, pk, alu_peak) -> dict:
+def unit_roofline(u, units, t, step_s, pk, fp32) -> dict:
+    """One unit of a plan against its roofline (per-unit algorithmic work as
+    stated in the module docstring).  The FFT FIR and the tensor-core cascade
+    stream the signal once and do less arithmetic than direct filtering, so
+    their bound is HBM at 8 B per sample; their own flop counts are stated
+    beside it.  The tensor-core FIR is bound by the tensor pipe (2L flop per
+    sample), the CUDA-core scans by the measured FP32 FMA rate (10 flop per
+    section, 2L per fused FIR tap)."""
     k = u["kind"]
     row = {"route": k, "kernel_ms": t * 1e3, "share_of_step": t / step_s}
+    hbm_ach = units * 8.0 / t / 1e9
     if k == "fir_tc":
         L = u["L"]
         K = -(-(L - 1) // 16) * 16 + 128
@@ -169,30 +218,34 @@ def unit_roofline(u, units, t, step_s, pk, alu_peak) -> dict:
                     "peak_source": f"{pk['source']} dense bf16/fp16 sustained",
                     "executed_tflops": units * 2.0 * 3 * K / t / 1e12,
                     "note": "achieved counts algorithmic 2L flop/sample; executed counts 3 split products x (W+128) K"})
-    elif k == "fir_fft":
+    elif k in ("fir_fft", "chain_fft"):
         f = fft_flops_per_output(u)
-        row.update({"bound": "alu", "kernel": "k_fir_fft" if u["P"] == 0 else "k_fir_fft_spec+k_fir_fft_conv",
-                    "achieved": units * f / t / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
-                    "peak_source": "SMs x 128 FP32 lanes x 2 flop x max SM clock",
-                    "config": {"L": u["L"], "M": u["M"], "B": u["B"], "P": u["P"]},
-                    "note": f"{f:.1f} algorithmic flop per output (5 M log2 M per transform)"})
+        kern = {"fir_fft": "k_fir_fft" if u["P"] == 0 else "k_fir_fft_spec+k_fir_fft_conv",
+                "chain_fft": "k_fir_fft"}[k]
+        row.update({"bound": "hbm", "kernel": kern, "achieved": hbm_ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "peak_source": f"{pk['source']} HBM copy bandwidth",
+                    "config": {kk: u[kk] for kk in ("L", "M", "B", "P") if kk in u},
+                    "fft_tflops": units * f / t / 1e12,
+                    "fft_frac_of_fp32": units * f / t / 1e12 / fp32["tflops"],
+                    "note": f"8 B per sample (FP32 read + write); {f:.1f} transform flop per output "
+                            "(5 M log2 M per transform) stated beside, against the measured FP32 FMA rate"})
     elif k == "cascade" and u.get("scan") == "tc":
         # tensor-core cascade: streams the signal once (8 B per sample); its tensor
         # work (GEMM1 128 x 112 and GEMM2 128 x 16 per 112-sample block, 3 split
         # products) takes under half the time the HBM traffic does at peak
         execf = 2.0 * 3 * 128 * (112 + 16) / 112
-        row.update({"bound": "hbm", "kernel": "k_sos_tc", "achieved": units * 8.0 / t / 1e9,
-                    "peak": pk["hbm_gbs"], "unit": "GB/s", "peak_source": pk["source"],
+        row.update({"bound": "hbm", "kernel": "k_sos_tc", "achieved": hbm_ach,
+                    "peak": pk["hbm_gbs"], "unit": "GB/s", "peak_source": f"{pk['source']} HBM copy bandwidth",
                     "executed_tflops": units * execf / t / 1e12,
                     "note": "8 B per sample (FP32 read + write); executed tensor flop per sample %.0f" % execf})
     else:
         S, L = u.get("S", 0), u.get("L", 0)
         kern = {"warp": "k_sos_warp"}.get(u.get("scan"), "k_unit")
         row.update({"bound": "alu", "kernel": kern,
-                    "achieved": units * (10.0 * S + 2.0 * L) / t / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
-                    "peak_source": "SMs x 128 FP32 lanes x 2 flop x max SM clock",
+                    "achieved": units * (10.0 * S + 2.0 * L) / t / 1e12, "peak": fp32["tflops"], "unit": "TFLOP/s",
+                    "peak_source": "measured FP32 FMA rate (bench.measure_fp32_peak)",
                     "note": "10 flop per SOS section, 2L per FIR tap, per sample"})
-        row["hbm_frac"] = units * 8.0 / t / 1e9 / pk["hbm_gbs"]
+        row["hbm_frac"] = hbm_ach / pk["hbm_gbs"]
     row["frac"] = row["achieved"] / row["peak"]
     return row
 
@@ -330,10 +383,66 @@ def reference_arm(args, ws, rank):
 
 
 BWD_FLOP_PER_SECTION = 30.0  # recompute 10 + adjoint all-pole 4 + input gradient 6 + coefficient sums 10
-FWDBWD_BYTES = 32.0          # fwd 8 + loss 12 (read y, target; write g) + bwd 12 (read g, x; write dx)
+FWDBWD_BYTES = 20.0          # fwd 8 (read x, write y) + bwd 12 (read g and x, write dx)
+FWDBWD_BYTES_WITH_LOSS = 32.0  # plus the loss 12 (read y and the target, write g)
 
 
-def measure_fwdbwd(wl, steps, warmup, dev, stream, torch, dist, ws, rank, pk, sm_count, with_e2e, with_cpu):
+def fwdbwd_parity(wl, x, y, g, dx, torch, api, NAT) -> dict:
+    """The timed training step's results against the FP64 oracle: the
+    training forward's output on four whole channels, dL/dx at 56 sampled
+    positions of the same channels (the oracle's impulse-response route,
+    given the step's own dL/dy; scale: the channel's largest |dL/dx|), and the
+    coefficient gradients of the same plan kind run on the first 8 channels
+    (the oracle's vector-Jacobian product sums over exactly those)."""
+    import oracle
+    lib = oracle.load()
+    chs = sorted({0, wl.C // 3, 2 * wl.C // 3, wl.C - 1})
+    xs = x[chs].double().cpu().numpy()
+    gs = g[chs].double().cpu().numpy()
+    ys = y[chs].double().cpu().numpy()
+    dxs = dx[chs].double().cpu().numpy()
+    fwd_err = channel_rel_err(ys, lib.chain(xs, wl.stages))
+    idx = np.unique(np.concatenate([np.linspace(0, wl.N - 1, 48).astype(np.int64),
+                                    np.arange(max(0, wl.N - 8), wl.N)]))
+    dx_err = []
+    for i in range(len(chs)):
+        ref = lib.chain_vjp_dx_at(gs[i], wl.stages, idx)
+        dx_err.append(float(np.max(np.abs(dxs[i][idx] - ref)) / max(np.max(np.abs(dxs[i])), 1e-300)))
+    Cs = min(8, wl.C)
+    sub = api.Plan(Cs, wl.N, wl.stages, flags=NAT.TFX_PLAN_TRAINABLE)
+    x8 = x[:Cs].contiguous()
+    g8 = g[:Cs].contiguous()
+    y8 = torch.empty_like(x8)
+    dx8 = torch.empty_like(x8)
+    dc8 = torch.empty(sub.coef_count, dtype=torch.float64, device=x.device)
+    sv = sub.new_saved()
+    sub.forward_train(x8, y8, sv)
+    sub.backward(x8, g8, dx8, dc8, sv)
+    torch.cuda.synchronize()
+    if sub.get_error() != 0:
+        raise RuntimeError("device reported a timeout in the parity backward")
+    sub.close()
+    _, grads = lib.chain_vjp(x8.double().cpu().numpy(), g8.double().cpu().numpy(), wl.stages, want_dx=False)
+    got = dc8.cpu().numpy()
+    coef_err, off = [], 0
+    for (kind, _), gr in zip(wl.stages, grads):
+        ref = gr.ravel()
+        coef_err.append({"stage": kind, "max_rel_err": float(np.max(np.abs(got[off:off + ref.size] - ref)) /
+                                                           max(np.max(np.abs(ref)), 1e-300))})
+        off += ref.size
+    return {"reference": "FP64 oracle", "tol_output": 1e-4, "tol_coef_grad": 1e-4,
+            "forward_max_rel_err": float(fwd_err.max()), "forward_per_channel": [float(v) for v in fwd_err],
+            "dx_max_rel_err": float(max(dx_err)), "dx_per_channel": dx_err, "channels": chs,
+            "dx_positions": int(idx.size), "coef_grad": coef_err,
+            "coef_grad_max_rel_err": float(max(e["max_rel_err"] for e in coef_err)),
+            "coef_grad_channels": Cs,
+            "note": "forward: whole channels; dL/dx: sampled positions, scale = the channel's largest |dL/dx|; "
+                    "coefficient gradients: the first 8 channels through a plan of the same stages (per-stage "
+                    "error relative to the stage's largest gradient)"}
+
+
+def measure_fwdbwd(wl, steps, warmup, dev, stream, torch, dist, ws, rank, pk, sm_count, with_e2e, with_cpu,
+                   fp32=None, with_parity=True):
     """One training step of the chain: training forward (saves chunk-start
     states), MSE against a target (loss and dL/dy in one kernel), backward
     (dL/dx and dL/d(every coefficient)).  Inputs resident in HBM."""
@@ -407,6 +516,9 @@ def measure_fwdbwd(wl, steps, warmup, dev, stream, torch, dist, ws, rank, pk, sm
     t_f = time_gpu(fwd, k_parts, 2, stream, torch, None) / k_parts
     t_l = time_gpu(loss_step, k_parts, 2, stream, torch, None) / k_parts
     t_b = time_gpu(bwd, k_parts, 2, stream, torch, None) / k_parts
+    torch.cuda.synchronize()
+    # y, g, dx and dcoef now hold one consistent training step
+    parity = fwdbwd_parity(wl, x, y, g, dx, torch, api, NAT) if (with_parity and rank == 0) else None
     launches = plan.launches_per_execute + 1 + plan.backward_launches(True, True)
     step_s = t / steps
 
@@ -423,17 +535,21 @@ def measure_fwdbwd(wl, steps, warmup, dev, stream, torch, dist, ws, rank, pk, sm
         k_k = max(10, steps // 3)
         t_k = time_gpu(lambda: sp.backward(x, g, dx, None, ssaved), k_k, 3, stream, torch, None) / k_k
         sp.close()
-        alu_peak = fp32_alu_peak_tflops(sm_count, pk["sm_max_mhz"])
+        alu_peak = fp32["tflops"] if fp32 else fp32_alu_peak_tflops(sm_count, pk["sm_max_mhz"])
         ach = units * BWD_FLOP_PER_SECTION * S / t_k / 1e12
         roof = {"bound": "alu", "kernel": "k_sos_bwd", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": ach / alu_peak, "kernel_ms": t_k * 1e3, "share_of_step": t_k / step_s,
                 "traffic": traffic_for("k_sos_bwd", wl.name),
-                "peak_source": f"{sm_count} SMs x 128 FP32 FMA x 2 flop x {pk['sm_max_mhz']:.0f} MHz",
+                "peak_source": "measured FP32 FMA rate (bench.measure_fp32_peak)" if fp32 else
+                               f"{sm_count} SMs x 128 FP32 FMA x 2 flop x {pk['sm_max_mhz']:.0f} MHz (nominal)",
+                "hbm_frac": units * 20.0 / t_k / 1e9 / pk["hbm_gbs"],
                 "note": f"{BWD_FLOP_PER_SECTION:.0f} algorithmic flop per sample per section"}
     ach_gbs = units * FWDBWD_BYTES / step_s / 1e9
     hbm = {"bound": "hbm", "achieved": ach_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
            "frac": ach_gbs / pk["hbm_gbs"], "peak_source": pk["source"],
-           "note": f"{FWDBWD_BYTES:.0f} B per channel-sample: forward 8, loss 12, backward 12"}
+           "frac_with_loss_bytes": units * FWDBWD_BYTES_WITH_LOSS / step_s / 1e9 / pk["hbm_gbs"],
+           "note": f"{FWDBWD_BYTES:.0f} B per channel-sample: forward 8 (read x, write y), backward 12 "
+                   f"(read g and x, write dx); with the MSE loss's 12 B it is {FWDBWD_BYTES_WITH_LOSS:.0f}"}
 
     e2e = None
     if with_e2e:
@@ -470,9 +586,9 @@ def measure_fwdbwd(wl, steps, warmup, dev, stream, torch, dist, ws, rank, pk, sm
     if with_cpu and rank == 0 and ws == 1:
         import oracle
         lib = oracle.load()
-        # about 10-30 s on the host cores: the oracle's dL/dx is O(N^2) per channel
-        Cs = min(wl.C, 4 * (os.cpu_count() or 1))
-        Ns = min(wl.N, 65536)
+        # a few seconds on the host cores: the oracle's dL/dx is O(N^2) per channel
+        Cs = min(wl.C, 16)
+        Ns = min(wl.N, 16384)
         xs = wl.make_signal(Cs, Ns).astype(np.float64)
         gs = np.random.default_rng(5).standard_normal(xs.shape)
         t0 = time.perf_counter()
@@ -488,7 +604,7 @@ def measure_fwdbwd(wl, steps, warmup, dev, stream, torch, dist, ws, rank, pk, sm
             "steps": steps, "step": "training forward + MSE loss and dL/dy + backward (dL/dx, dL/dcoef)",
             "cuda_graph": graph is not None, "eager_ms_per_step": t_eager / steps * 1e3,
             "fwd_ms": t_f * 1e3, "loss_ms": t_l * 1e3, "bwd_ms": t_b * 1e3, "gpu_launches_per_step": launches,
-            "roofline": roof, "roofline_hbm": hbm, "e2e": e2e, "cpu_baseline": cpu,
+            "roofline": roof, "roofline_hbm": hbm, "e2e": e2e, "cpu_baseline": cpu, "parity": parity,
             "dtype": "f32", "plain_gpu": None}
 
 
@@ -518,6 +634,57 @@ def reference_arm_batched(args):
         "cpu_baseline": {"value": rate, "unit": UNIT, "cores": lib.num_threads(), "kind": "oracle", "sample": sample},
         "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+LONG_FIR_ROUTES = [("fft", 0), ("tensor cores, FP16 hi/lo split", "TFX_PLAN_FIR_TC"),
+                   ("tensor cores, BF16 hi/lo split", "TFX_PLAN_FIR_BF16_SPLIT"),
+                   ("tensor cores, plain BF16 (reported only)", "TFX_PLAN_FIR_BF16_PLAIN")]
+
+
+def measure_long_fir_precision(dev, stream, torch) -> dict:
+    """The long-FIR configuration (128 x 4,194,304 Gaussian noise, 16384-tap
+    Kaiser band-pass) on a bounded channel sample: its first 16 channels at
+    full length through each FIR route, the error of each against the FP64
+    oracle at 8 channels x 544 sampled outputs (the oracle's convolution at
+    chosen positions; 32 of them within the first 16384 samples, where fewer
+    than L terms enter), relative to the channel's largest |y| (from the
+    default route's whole output), and each route's time beside."""
+    from paper_2504_08624_gb300 import api, _native as NAT, workloads as W
+    import oracle
+    wl = W.WORKLOADS["long_fir"]()
+    C = 16
+    h = np.asarray(wl.stages[0][1], dtype=np.float64)
+    xh = wl.make_signal(C, wl.N)
+    x = torch.from_numpy(xh).to(dev)
+    y = torch.empty_like(x)
+    chs = list(range(0, C, 2))
+    idx = np.unique(np.concatenate([np.linspace(0, wl.N - 1, 512).astype(np.int64),
+                                    np.linspace(0, h.size - 1, 32).astype(np.int64)]))
+    lib = oracle.load()
+    ref = np.stack([lib.fir_at(xh[c].astype(np.float64), h, idx) for c in chs])
+    out, scale = [], None
+    for name, flag in LONG_FIR_ROUTES:
+        flags = getattr(NAT, flag) if flag else 0
+        plan = api.Plan(C, wl.N, wl.stages, flags=flags)
+        wsb = plan.workspace()
+        k = 5
+        t = time_gpu(lambda: plan.execute(x, y, wsb), k, 2, stream, torch, None) / k
+        torch.cuda.synchronize()
+        if plan.get_error() != 0:
+            raise RuntimeError(f"device reported a timeout on the long FIR ({name})")
+        desc = plan.describe()
+        plan.close()
+        yc = y[chs]
+        if scale is None:
+            scale = yc.abs().amax(dim=1).double().cpu().numpy()
+        got = yc[:, torch.from_numpy(idx).to(dev)].double().cpu().numpy()
+        rel = channel_rel_err(got, ref, scale)
+        out.append({"route": name, "plan": desc, "ms": t * 1e3, "channel_samples_per_s": C * wl.N / t,
+                    "max_rel_err": float(rel.max()), "per_channel": [float(v) for v in rel],
+                    "meets_1e-5": bool(rel.max() <= 1e-5)})
+    return {"workload": f"{wl.name} (first {C} of {wl.C} channels, full length)", "taps": int(h.size),
+            "reference": "FP64 oracle at sampled outputs", "tol": 1e-5, "channels_checked": chs,
+            "positions_per_channel": int(idx.size), "routes": out}
 
 
 def main():
@@ -610,13 +777,13 @@ def main():
     pk = peaks()
     props = torch.cuda.get_device_properties(dev)
     sm_count = props.multi_processor_count
+    fp32 = measure_fp32_peak(dev, stream, torch, sm_count, local)
     step_s = t_dev / args.steps
     achieved_gbs = units * bytes_ps / step_s / 1e9
     # every unit of the chain timed alone (a plan of the unit's stages, same
     # flags, so the same kernels and launch configuration as inside the
     # chain, CUDA events on the launch stream); the dominant one against its
     # roofline
-    alu_peak = fp32_alu_peak_tflops(sm_count, pk["sm_max_mhz"])
     unit_rows = []
     for u, ust in unit_stages(plan.describe(), wl.stages):
         uplan = api.Plan(wl.C, wl.N, ust, flags=args.flags)
@@ -625,7 +792,7 @@ def main():
         t_u = time_gpu(lambda: uplan.execute(x, x_fir, uws), k_u, 3, stream, torch, None) / k_u
         uplan.close()
         del uws
-        row = unit_roofline(u, units, t_u, step_s, pk, alu_peak)
+        row = unit_roofline(u, units, t_u, step_s, pk, fp32)
         row["traffic"] = traffic_for(row["kernel"], wl.name)
         unit_rows.append(row)
     bound = max(unit_rows, key=lambda r: r["kernel_ms"]) if unit_rows else {
@@ -638,22 +805,44 @@ def main():
            "note": "8 B per channel-sample over the whole step"}
 
     cpu = None
+    parity = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        lib = oracle.load()
         ncpu = os.cpu_count() or 1
         Cs = min(wl.C, ncpu)
         # bounded sample: about 1.6e11 multiply-adds (10-30 s on the host cores)
         macs = max(1.0, flops_ps / 2.0)
         Ns = int(min(wl.N, max(16384, 1.6e11 / (Cs * macs))))
-        rate, dt, thr = cpu_oracle_rate(wl, Cs, Ns)
-        cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
+        xs = x_host[:Cs, :Ns].double().numpy()
+        t0 = time.perf_counter()
+        ref = lib.chain(xs, wl.stages)
+        dt = time.perf_counter() - t0
+        thr = lib.num_threads()
+        cpu = {"value": Cs * Ns / dt, "unit": UNIT, "cores": thr, "kind": "oracle",
                "sample": f"{Cs} of {wl.C} channels x first {Ns} of {wl.N} samples, FP64 oracle chain, "
                          f"{dt:.1f} s on {thr} threads"}
+        # the timed plan's output on the same channels (causal: the first Ns
+        # outputs depend on the first Ns inputs only) against the oracle's
+        step()
+        torch.cuda.synchronize()
+        got = y[:Cs, :Ns].double().cpu().numpy()
+        rel = channel_rel_err(got, ref)
+        parity = {"reference": "FP64 oracle", "tol": wl.tol, "max_rel_err": float(rel.max()),
+                  "per_channel": [float(v) for v in rel], "channels": Cs, "samples": Ns,
+                  "pass": bool(rel.max() <= wl.tol),
+                  "note": "per channel: max|y - y_oracle| / max|y_oracle| over the channel, the timed plan's output"}
 
     fwd_bwd = None
     if not args.no_fwdbwd and args.part == "chain":
         from paper_2504_08624_gb300 import workloads as W
         fwd_bwd = measure_fwdbwd(W.differentiable_chain_forward(), min(args.steps, 100), max(3, args.warmup), dev,
-                                 stream, torch, dist, ws, rank, pk, sm_count, not args.no_e2e, False)
+                                 stream, torch, dist, ws, rank, pk, sm_count, not args.no_e2e,
+                                 rank == 0 and ws == 1 and not args.no_cpu_baseline, fp32,
+                                 with_parity=not args.no_cpu_baseline)
+    long_fir = None
+    if not args.no_long_fir and args.part == "chain" and rank == 0:
+        long_fir = measure_long_fir_precision(dev, stream, torch)
 
     if rank == 0:
         out = {
@@ -666,8 +855,9 @@ def main():
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "l2": "inputs 737 MB > 129 MB L2, no flush", "plan_flags": args.flags},
             "roofline": bound, "roofline_hbm": hbm, "units": unit_rows, "cpu_baseline": cpu, "e2e": e2e,
-            "plain_gpu": plain, "gpu_launches": int(args.steps * plan.launches_per_execute), "clocks": clocks,
-            "gpu": props.name, "fwd_bwd": fwd_bwd,
+            "parity": parity, "plain_gpu": plain, "gpu_launches": int(args.steps * plan.launches_per_execute),
+            "clocks": clocks, "gpu": props.name, "fp32_peak": fp32, "fwd_bwd": fwd_bwd,
+            "long_fir_precision": long_fir,
         }
         print(json.dumps(out), flush=True)
     if dist is not None:
@@ -813,11 +1003,13 @@ def run_fwdbwd_main(args, wl, dev, torch, dist, ws, rank, local):
     stream = torch.cuda.current_stream(dev)
     pk = peaks()
     props = torch.cuda.get_device_properties(dev)
+    fp32 = measure_fp32_peak(dev, stream, torch, props.multi_processor_count, local)
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
     r = measure_fwdbwd(wl, args.steps, args.warmup, dev, stream, torch, dist, ws, rank, pk,
-                       props.multi_processor_count, not args.no_e2e, not args.no_cpu_baseline)
+                       props.multi_processor_count, not args.no_e2e, not args.no_cpu_baseline, fp32,
+                       with_parity=not args.no_cpu_baseline)
     clocks = sampler.stop()
     if rank == 0:
         S = sum(np.asarray(c).reshape(-1, 6).shape[0] for k, c in wl.stages if k == "sos")
@@ -833,7 +1025,8 @@ def run_fwdbwd_main(args, wl, dev, torch, dist, ws, rank, local):
             "roofline": r["roofline"], "roofline_hbm": r["roofline_hbm"], "cpu_baseline": r["cpu_baseline"],
             "e2e": r["e2e"], "plain_gpu": r["plain_gpu"],
             "gpu_launches": int(args.steps * r["gpu_launches_per_step"]), "clocks": clocks, "gpu": props.name,
-            "fwd_ms": r["fwd_ms"], "loss_ms": r["loss_ms"], "bwd_ms": r["bwd_ms"],
+            "fwd_ms": r["fwd_ms"], "loss_ms": r["loss_ms"], "bwd_ms": r["bwd_ms"], "parity": r["parity"],
+            "fp32_peak": fp32,
         }), flush=True)
     if dist is not None:
         dist.barrier()

@@ -316,20 +316,27 @@ void tfx_cache_clear(void);
  * reserved up front by an allocator they do not control.  The paper has no
  * counterpart; it is an extra entry point of this library.
  *
- * Same arguments, layout and result as tfx_sos (x == y allowed).  The call
+ * Same arguments, layout and result as tfx_sos (x == y allowed), for
+ * cascades whose poles all have radius <= 0.999: this entry point keeps FP32
+ * cross-tile carries, so a section with a pole beyond that radius (where
+ * tfx_sos switches to FP64 carries) returns TFX_ERR_UNSUPPORTED.  The call
  * makes no cudaMalloc / cudaFree and uses no allocating library routine: the
  * scan's scratch (tile ticket, status word, look-back carries) and the
  * section constants live in one fixed static device array of about 4.3 MB
- * that every GPU loading the library holds until the process exits.
+ * that every GPU loading the library holds until the process exits.  The
+ * host normalises the rows in FP64 (a few hundred bytes of stack) and passes
+ * them to a set-up kernel by value, which builds the section constants in
+ * the array; nothing is copied from host memory.
  * Limits: sections <= 8 and C * ceil(N / 8192) <= 32768 (for example 64
  * channels of up to 4.19 M samples); larger requests return
  * TFX_ERR_UNSUPPORTED before anything is enqueued.
  * The first call on a device looks up the array's device address (a host
  * synchronising runtime query), so make that first call before any stream
- * capture on that device.  All calls share the one array: calls whose work
- * overlaps on the GPU (different streams, or host threads racing) corrupt
- * each other's results; calls ordered on one stream are safe.  Device-side
- * timeouts are not reported (there is no plan to hold a status).
+ * capture on that device.  All calls share the one array and each call
+ * overwrites what the previous one left there: calls whose work overlaps on
+ * the GPU (different streams, or host threads racing) corrupt each other's
+ * results; calls ordered on one stream are safe.  Device-side timeouts are
+ * not reported (there is no plan to hold a status).
  * Errors: TFX_ERR_INVALID, TFX_ERR_UNSTABLE, TFX_ERR_UNSUPPORTED, TFX_ERR_CUDA.
  */
 int tfx_sos_noalloc(const float *x, float *y, int64_t C, int64_t N, int64_t ld,
@@ -448,6 +455,22 @@ int tfx_design_device(const tfx_design *specs, int32_t n, const int64_t *row_off
                       double *rows, int *status, tfx_stream s);
 int tfx_plan_update_sos(tfx_plan *p, const double *rows, tfx_stream s);
 int64_t tfx_plan_sos_rows(const tfx_plan *p);
+
+/*
+ * Measurement helper (the paper has no counterpart): the FP32 multiply-add
+ * rate of this GPU, the denominator of the CUDA-core rooflines, which must
+ * be measured rather than derived from clock and unit counts.
+ * tfx_fma_probe enqueues `blocks` CTAs of `threads` threads (a multiple of
+ * 32, at most 1024) that each run 8 independent chains of `iters` FP32 FMAs
+ * (packed != 0: the two-lane packed FMA, two per instruction) and write one
+ * float per thread to `out` (device, blocks * threads floats).  Time it with
+ * events on s; tfx_fma_probe_flops gives the flops one launch performs.
+ * Errors: TFX_ERR_INVALID, TFX_ERR_CUDA.
+ */
+int tfx_fma_probe(float *out, int32_t blocks, int32_t threads, int32_t iters,
+                  int32_t packed, tfx_stream s);
+double tfx_fma_probe_flops(int32_t blocks, int32_t threads, int32_t iters,
+                           int32_t packed);
 
 /* Human-readable name of a tfx_status. */
 const char *tfx_strerror(int status);

@@ -54,6 +54,7 @@ EXPORTS = [
     "tfx_batch_launch_count", "tfx_batch_execute", "tfx_batch_get_error", "tfx_batch_destroy",
     "tfx_batch_group_count", "tfx_batch_group_info", "tfx_batch_execute_group",
     "tfx_design_sections", "tfx_design_device", "tfx_plan_update_sos", "tfx_plan_sos_rows",
+    "tfx_fma_probe", "tfx_fma_probe_flops",
 ]
 
 
@@ -178,6 +179,10 @@ def lib():
     L.tfx_plan_update_sos.restype = ctypes.c_int
     L.tfx_plan_sos_rows.argtypes = [vp]
     L.tfx_plan_sos_rows.restype = i64
+    L.tfx_fma_probe.argtypes = [fp, i32, i32, i32, i32, vp]
+    L.tfx_fma_probe.restype = ctypes.c_int
+    L.tfx_fma_probe_flops.argtypes = [i32, i32, i32, i32]
+    L.tfx_fma_probe_flops.restype = ctypes.c_double
     L.tfx_strerror.argtypes = [ctypes.c_int]
     L.tfx_strerror.restype = ctypes.c_char_p
     L.tfx_version.restype = ctypes.c_int

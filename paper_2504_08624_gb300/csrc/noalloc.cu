@@ -4,10 +4,11 @@
 // per-section constants -- lives in one file-scope static device array of fixed
 // size, so a call makes no cudaMalloc / cudaFree and uses no allocating
 // library routine.
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 
-#include "tfx_common.cuh"
+#include "plan_internal.cuh"
 
 namespace tfx {
 namespace {
@@ -56,11 +57,56 @@ int na_scratch(unsigned char** out) {
     return TFX_OK;
 }
 
-struct NaM2 {
-    double a, b, c, d;
+// Section constants of one call, passed to the set-up kernel by value (no
+// host-to-device copy): the a0-normalised c-form coefficients in FP64.
+struct NaSections {
+    double b0[NA_MAX_SECTIONS], c1[NA_MAX_SECTIONS], c2[NA_MAX_SECTIONS], a1[NA_MAX_SECTIONS],
+        a2[NA_MAX_SECTIONS];
 };
-inline NaM2 na_mul(const NaM2& x, const NaM2& y) {
-    return {x.a * y.a + x.b * y.c, x.a * y.b + x.b * y.d, x.c * y.a + x.d * y.c, x.c * y.b + x.d * y.d};
+
+// One CTA per section: its FP32 coefficients, and the chunk-transfer powers
+// A^k (k < PW_LEN, A = M^T_CASCADE, M = [[-a1, 1], [-a2, 0]] the one-sample
+// transfer of the c-form state) in FP64 by binary exponentiation, rounded
+// once, written into the static array where the scan kernel reads them.
+__global__ void k_noalloc_setup(NaSections sp, float* __restrict__ coef, float4* __restrict__ pw) {
+    const int s = blockIdx.x;
+    const double a1 = sp.a1[s], a2 = sp.a2[s];
+    if (threadIdx.x == 0) {
+        float* c = coef + 8 * s;
+        c[0] = (float)sp.b0[s];
+        c[1] = (float)sp.c1[s];
+        c[2] = (float)sp.c2[s];
+        c[3] = (float)a1;
+        c[4] = (float)a2;
+        c[5] = c[6] = c[7] = 0.f;
+    }
+    double m00 = -a1, m01 = 1.0, m10 = -a2, m11 = 0.0;
+    double A00 = 1.0, A01 = 0.0, A10 = 0.0, A11 = 1.0;
+    for (int e = T_CASCADE; e > 0; e >>= 1) {
+        if (e & 1) {
+            const double t00 = A00 * m00 + A01 * m10, t01 = A00 * m01 + A01 * m11;
+            const double t10 = A10 * m00 + A11 * m10, t11 = A10 * m01 + A11 * m11;
+            A00 = t00, A01 = t01, A10 = t10, A11 = t11;
+        }
+        const double q00 = m00 * m00 + m01 * m10, q01 = m00 * m01 + m01 * m11;
+        const double q10 = m10 * m00 + m11 * m10, q11 = m10 * m01 + m11 * m11;
+        m00 = q00, m01 = q01, m10 = q10, m11 = q11;
+    }
+    for (int k = threadIdx.x; k < PW_LEN; k += blockDim.x) {
+        double p00 = 1.0, p01 = 0.0, p10 = 0.0, p11 = 1.0;
+        double b00 = A00, b01 = A01, b10 = A10, b11 = A11;
+        for (int e = k; e > 0; e >>= 1) {
+            if (e & 1) {
+                const double t00 = p00 * b00 + p01 * b10, t01 = p00 * b01 + p01 * b11;
+                const double t10 = p10 * b00 + p11 * b10, t11 = p10 * b01 + p11 * b11;
+                p00 = t00, p01 = t01, p10 = t10, p11 = t11;
+            }
+            const double q00 = b00 * b00 + b01 * b10, q01 = b00 * b01 + b01 * b11;
+            const double q10 = b10 * b00 + b11 * b10, q11 = b10 * b01 + b11 * b11;
+            b00 = q00, b01 = q01, b10 = q10, b11 = q11;
+        }
+        pw[(size_t)s * PW_LEN + k] = make_float4((float)p00, (float)p01, (float)p10, (float)p11);
+    }
 }
 
 }  // namespace
@@ -84,9 +130,10 @@ extern "C" int tfx_sos_noalloc(const float* x, float* y, int64_t C, int64_t N, i
     const int64_t ntt = (N + TILE - 1) / TILE;
     if (C > NA_MAX_TILES / ntt) return TFX_ERR_UNSUPPORTED;
 
-    // section constants, computed in FP64 on the stack (no heap use)
-    float coef[NA_MAX_SECTIONS * 8] = {};
-    float4 pw[NA_MAX_SECTIONS * PW_LEN];
+    // normalise and check every row on the host (FP64, a few doubles on the
+    // stack); the device tables are built by a set-up kernel from these
+    // values passed by value, so the call copies nothing from host memory
+    NaSections sp{};
     for (int s = 0; s < sections; ++s) {
         const double* r = sos + 6 * s;
         for (int j = 0; j < 6; ++j)
@@ -94,19 +141,17 @@ extern "C" int tfx_sos_noalloc(const float* x, float* y, int64_t C, int64_t N, i
         if (r[3] == 0.0) return TFX_ERR_INVALID;
         const double b0 = r[0] / r[3], b1 = r[1] / r[3], b2 = r[2] / r[3], a1 = r[4] / r[3], a2 = r[5] / r[3];
         if (!(std::fabs(a2) < 1.0 && std::fabs(a1) < 1.0 + a2)) return TFX_ERR_UNSTABLE;
-        coef[8 * s + 0] = (float)b0;
-        coef[8 * s + 1] = (float)(b1 - a1 * b0);
-        coef[8 * s + 2] = (float)(b2 - a2 * b0);
-        coef[8 * s + 3] = (float)a1;
-        coef[8 * s + 4] = (float)a2;
-        const NaM2 m = {-a1, 1.0, -a2, 0.0};
-        NaM2 A = {1, 0, 0, 1};
-        for (int t = 0; t < T_CASCADE; ++t) A = na_mul(A, m);  // samples per thread of the cascade kernel
-        NaM2 pk = {1, 0, 0, 1};
-        for (int k = 0; k < PW_LEN; ++k) {
-            pw[s * PW_LEN + k] = make_float4((float)pk.a, (float)pk.b, (float)pk.c, (float)pk.d);
-            pk = na_mul(pk, A);
-        }
+        // this entry point keeps FP32 cross-tile carries: a pole beyond the
+        // radius where the plans switch to FP64 carries is not supported
+        const double disc = a1 * a1 - 4.0 * a2;
+        const double rad = disc < 0.0 ? std::sqrt(a2)
+                                      : std::max(std::fabs(-a1 + std::sqrt(disc)), std::fabs(-a1 - std::sqrt(disc))) / 2.0;
+        if (rad > HIQ_RADIUS) return TFX_ERR_UNSUPPORTED;
+        sp.b0[s] = b0;
+        sp.c1[s] = b1 - a1 * b0;
+        sp.c2[s] = b2 - a2 * b0;
+        sp.a1[s] = a1;
+        sp.a2[s] = a2;
     }
 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -119,12 +164,9 @@ extern "C" int tfx_sos_noalloc(const float* x, float* y, int64_t C, int64_t N, i
     // ticket, status word and look-back carries must start at zero
     if (cudaMemsetAsync(base, 0, NA_OFF_CARRY + (size_t)tiles * sections * sizeof(Carry), s) != cudaSuccess)
         return TFX_ERR_CUDA;
-    if (cudaMemcpyAsync(base + NA_OFF_COEF, coef, (size_t)sections * 8 * sizeof(float), cudaMemcpyHostToDevice,
-                        s) != cudaSuccess)
-        return TFX_ERR_CUDA;
-    if (cudaMemcpyAsync(base + NA_OFF_PW, pw, (size_t)sections * PW_LEN * sizeof(float4),
-                        cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return TFX_ERR_CUDA;
+    k_noalloc_setup<<<sections, 256, 0, s>>>(sp, reinterpret_cast<float*>(base + NA_OFF_COEF),
+                                             reinterpret_cast<float4*>(base + NA_OFF_PW));
+    if (cudaGetLastError() != cudaSuccess) return TFX_ERR_CUDA;
 
     UnitArgs a{};
     a.x = x;

@@ -35,22 +35,19 @@ def oracle_chain(x, stages):
     return oracle.chain(np.asarray(x, dtype=np.float64), stages)
 
 
-def assert_close_floored(got, ref, x, tol, what="", floor=1e-3):
-    """The stated tolerance against each channel's output peak, floored at
-    `floor` x the channel's input peak: a chain that attenuates by more than
-    60 dB leaves an output that FP32 data (rounded relative to the input)
-    cannot resolve to 1e-4 of its own peak."""
-    got = np.asarray(got, dtype=np.float64)
-    ref = np.asarray(ref, dtype=np.float64)
-    x = np.asarray(x, dtype=np.float64)
-    if got.ndim == 1:
-        got, ref, x = got[None], ref[None], x[None]
-    if got.shape[1] == 0:
-        return 0.0
-    err = np.max(np.abs(got - ref), axis=1)
-    scale = np.maximum(np.max(np.abs(ref), axis=1), floor * np.max(np.abs(x), axis=1))
-    rel = err / np.maximum(scale, 1e-30)
-    worst = int(np.argmax(rel))
-    assert np.all(rel <= tol), (f"{what}: channel {worst} max|err| {err[worst]:.3e} = {rel[worst]:.3e} x "
-                                f"scale {scale[worst]:.3e} > tol {tol:g}")
-    return float(rel.max())
+def assert_close_or_as_plain(got, ref, plain, tol, what="", factor=2.0):
+    """The stated tolerance per channel against its own output peak, unfloored.
+
+    Where the chain attenuates so strongly that an FP32 computation cannot
+    resolve the output to `tol` of its own peak, the plain sequential FP32
+    path (one thread per channel walking each section in time order, the
+    comparison baseline) misses `tol` too; there the channel may not be more
+    than `factor` times less accurate than that path.  Returns the per-channel
+    errors of both (for the test's record)."""
+    rel, err, peak = per_channel_rel_err(got, ref)
+    rel_plain, _, _ = per_channel_rel_err(plain, ref)
+    bad = [(c, rel[c], rel_plain[c]) for c in range(rel.size)
+           if not (rel[c] <= tol or rel[c] <= factor * rel_plain[c])]
+    assert not bad, (f"{what}: channel {bad[0][0]} error {bad[0][1]:.3e} of its peak exceeds tol {tol:g} and "
+                     f"{factor:g} x the plain FP32 path's {bad[0][2]:.3e}")
+    return rel, rel_plain
