@@ -175,6 +175,10 @@ def unit_stages(desc, stages):
     out, i = [], 0
     for u in desc:
         take = []
+        if u["kind"] == "chain_fft":  # the whole chain in one unit
+            out.append((u, list(stages)))
+            i = len(stages)
+            continue
         if u["kind"] in ("cascade", "fused"):
             while i < len(stages) and stages[i][0] == "sos":
                 take.append(stages[i])
@@ -192,7 +196,7 @@ def fft_flops_per_output(u) -> float:
     and M complex products (6 flop) per two blocks of B outputs;
     partitioned: the two transforms and P complex multiply-adds (8 flop) per
     point per M outputs (two channels x B)."""
-    M, B, P = u["M"], u["B"], u["P"]
+    M, B, P = u["M"], u["B"], u.get("P", 0)
     m = M.bit_length() - 1
     if P == 0:
         return (10.0 * M * m + 6.0 * M) / (2.0 * B)
@@ -220,11 +224,11 @@ def unit_roofline(u, units, t, step_s, pk, fp32) -> dict:
                     "note": "achieved counts algorithmic 2L flop/sample; executed counts 3 split products x (W+128) K"})
     elif k in ("fir_fft", "chain_fft"):
         f = fft_flops_per_output(u)
-        kern = {"fir_fft": "k_fir_fft" if u["P"] == 0 else "k_fir_fft_spec+k_fir_fft_conv",
+        kern = {"fir_fft": "k_fir_fft" if u.get("P", 0) == 0 else "k_fir_fft_spec+k_fir_fft_conv",
                 "chain_fft": "k_fir_fft"}[k]
         row.update({"bound": "hbm", "kernel": kern, "achieved": hbm_ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "peak_source": f"{pk['source']} HBM copy bandwidth",
-                    "config": {kk: u[kk] for kk in ("L", "M", "B", "P") if kk in u},
+                    "config": {kk: u[kk] for kk in ("S", "L", "D", "Lc", "M", "B", "P") if kk in u},
                     "fft_tflops": units * f / t / 1e12,
                     "fft_frac_of_fp32": units * f / t / 1e12 / fp32["tflops"],
                     "note": f"8 B per sample (FP32 read + write); {f:.1f} transform flop per output "
@@ -764,6 +768,18 @@ def main():
                "h2d_bytes_per_step": int(x_host.numel() * 4), "d2h_bytes_per_step": int(y_host.numel() * 4),
                "ms_per_step": t_e2e / k_e2e * 1e3, "steps": k_e2e}
 
+    # the same chain with its units kept separate (no composite response), for context
+    separate = None
+    if any(u["kind"] == "chain_fft" for u in plan.describe()):
+        splan = api.Plan(wl.C, wl.N, wl.stages, flags=args.flags | NAT.TFX_PLAN_NO_COMPOSE)
+        sws = splan.workspace()
+        k_s = max(10, args.steps // 5)
+        t_s = time_gpu(lambda: splan.execute(x, x_fir, sws), k_s, 3, stream, torch, None) / k_s
+        separate = {"ms_per_step": t_s * 1e3, "value": units / t_s, "plan": splan.describe(),
+                    "launches": splan.launches_per_execute}
+        splan.close()
+        del sws
+
     # the plain sequential-per-channel GPU path on the same GB300
     plain = None
     if not args.no_plain:
@@ -855,7 +871,8 @@ def main():
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "l2": "inputs 737 MB > 129 MB L2, no flush", "plan_flags": args.flags},
             "roofline": bound, "roofline_hbm": hbm, "units": unit_rows, "cpu_baseline": cpu, "e2e": e2e,
-            "parity": parity, "plain_gpu": plain, "gpu_launches": int(args.steps * plan.launches_per_execute),
+            "parity": parity, "plain_gpu": plain, "separate_units": separate, "plan": plan.describe(),
+            "gpu_launches": int(args.steps * plan.launches_per_execute),
             "clocks": clocks, "gpu": props.name, "fp32_peak": fp32, "fwd_bwd": fwd_bwd,
             "long_fir_precision": long_fir,
         }

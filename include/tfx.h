@@ -83,20 +83,23 @@ typedef struct {
 #define TFX_PLAN_TRAINABLE 32u
 /* FIRs of 64 taps or more by FFT overlap-save instead of the tensor-core
  * Toeplitz GEMM.  This is also the default route (measured faster on GB300
- * at every length from 65 taps); the flag keeps it when TFX_PLAN_FIR_TC,
+ * at every length from 65 taps) for signals of at least 2L samples (the
+ * transforms round relative to each block's energy, and a shorter signal is
+ * all leading transient); the flag forces it for any length, and keeps it when TFX_PLAN_FIR_TC,
  * _FIR_BF16_PLAIN or _FIR_BF16_SPLIT is set too, and FIR stages on CUDA cores
  * (TFX_PLAN_FIR_CUDA_CORES) never take it.  Hand-written register-resident
  * radix-16 FFTs of
- * M = 1024..8192 points (FP32; the error is ~log2(M) eps of each block's
- * energy rather than per product).  Up to 6145 taps: blocks of
- * B = M - (L - 1) outputs, two blocks per complex transform.  Longer:
+ * M = 1024..16384 points (FP32; the error is ~log2(M) eps of each block's
+ * energy rather than per product).  Up to 12289 taps: blocks of
+ * B = M - (L - 1) outputs, two blocks per complex transform (16384 points
+ * only in this single-block form).  Longer:
  * partitioned overlap-save, h cut into P = ceil(L / (M/2)) partitions, every
  * input segment transformed once (two channels per complex transform) into a
  * workspace of ceil(C/2) x ceil(N / (M/2)) x M complex values, and each output
  * block the inverse transform of the sum of the P partition products (two
  * launches).  The scheme and transform size are chosen per FIR from a cost
  * model fitted to GB300 timings unless TFX_PLAN_FIR_FFT_LOG(m) fixes
- * M = 2^m (m = 10..13; the scheme is still chosen by the model). */
+ * M = 2^m (m = 10..14; the scheme is still chosen by the model). */
 #define TFX_PLAN_FIR_FFT 64u
 /* Every FIR of TC_MIN_TAPS (64) taps or more on the tensor-core Toeplitz
  * GEMM, none by FFT. */
@@ -116,6 +119,24 @@ typedef struct {
  * fits within 65536 samples).  One launch.  With this flag such units run
  * the CUDA-core block-tile scan with decoupled look-back instead. */
 #define TFX_PLAN_SCAN_LOOKBACK 512u
+/* A whole chain of SOS cascades and FIRs is one linear time-invariant
+ * filter (Sec. 3: the pipe composes the stages in order), and when its
+ * cascades' impulse response g decays it is run by default as ONE kernel:
+ * the composite impulse response h_c = g * f (f: every FIR's taps
+ * convolved) is formed in FP64 at plan time, g truncated at the first D
+ * samples beyond which sum|g| x sum|f| is below 1e-8 of the chain's RMS gain
+ * ||h_c||_2 (g must have decayed within 65536 samples: the last 4096 of them
+ * below 1e-14 of sum|g|; otherwise the chain keeps its separate units), and
+ * the signal is filtered by FFT overlap-save with h_c (single-block,
+ * M = 4096..16384 points), so it crosses HBM once.  The truncation changes
+ * no output by more than 1e-8 ||h_c||_2 max|x|; the FP32 transforms round
+ * relative to each block's energy.  Chosen when the signal holds at least
+ * 2 (D + L - 1) samples and a cost model fitted to GB300 timings predicts it
+ * faster than the separate units; plans with TFX_PLAN_TRAINABLE, a
+ * tensor-core, CUDA-core, transform-size or scan flag, or a pole of radius
+ * > 0.999 never take it.  tfx_plan_update_sos switches such a plan back to
+ * its separate units.  This flag disables the composition. */
+#define TFX_PLAN_NO_COMPOSE 1024u
 /* Test hook for failure detection: the first tile of channel 0 never publishes
  * its carries, so its successor's bounded wait runs out; the execution
  * completes (with wrong output) and tfx_plan_get_error() returns
@@ -155,6 +176,9 @@ int tfx_plan_launch_count(const tfx_plan *p);
  *   fir:L=..                                         (FIR on CUDA cores)
  *   fir_tc:L=..,kernel=k_fir_tc|k_fir_tc_ws|k_fir_tc_long
  *   fir_fft:L=..,M=..,B=..,P=..                      (P = 0: single-block)
+ *   chain_fft:S=..,L=..,D=..,Lc=..,M=..,B=..   (the whole chain as one FIR of
+ *                                               Lc = D + L - 1 taps; L: the FIRs'
+ *                                               combined length)
  * Writes at most len bytes including the terminating NUL into buf (buf may be
  * NULL when len is 0) and returns the length of the full description (as
  * snprintf does), or -1 for a NULL plan. */

@@ -29,12 +29,13 @@ TFX_PLAN_FIR_TC = 128
 
 
 def TFX_PLAN_FIR_FFT_LOG(m: int) -> int:
-    """Plan flag bits fixing the overlap-save transform size at 2^m points (m = 10..13)."""
+    """Plan flag bits fixing the overlap-save transform size at 2^m points (m = 10..14; 14: single-block only)."""
     return (int(m) & 15) << 16
 
 
 TFX_PLAN_TEST_DROP_PUBLISH = 256
 TFX_PLAN_SCAN_LOOKBACK = 512
+TFX_PLAN_NO_COMPOSE = 1024
 
 STATUS = {
     0: "TFX_OK", -1: "TFX_ERR_INVALID", -2: "TFX_ERR_UNSTABLE", -3: "TFX_ERR_WORKSPACE",

@@ -187,6 +187,8 @@ class Plan:
         with torch.cuda.device(self.device):
             rc = N.lib().tfx_plan_update_sos(self._h, ctypes.c_void_p(rows.data_ptr()), _stream_handle(self.device))
         N.check(rc, "tfx_plan_update_sos")
+        # a composed chain falls back to its separate units after an update
+        self.launches_per_execute = int(N.lib().tfx_plan_launch_count(self._h))
 
     # -- gradients (plans created with TFX_PLAN_TRAINABLE) -----------------
 

@@ -294,6 +294,9 @@ int tfx::plan_update_sections(tfx_plan* p, const double* rows_dev, cudaStream_t 
     // the host: such units run the look-back scan (whose constants are the
     // ones updated here) from the first update on
     for (HostUnit& u : p->units) u.seg = false;
+    // a composed chain's spectrum is derived from the coefficients on the
+    // host too: such a plan runs its separate units from now on
+    p->use_chain = false;
     if (!p->dsec && p->nsec != 0) {
         std::vector<SecUpdate> v;
         int64_t row = 0;

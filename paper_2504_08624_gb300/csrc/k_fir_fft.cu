@@ -220,35 +220,74 @@ __device__ __forceinline__ void run_pass(float2 (&v)[16], const float2* __restri
     }
 }
 
-// Move the points from pass P's layout to pass Q's through shared memory.
-template <int LOGM, int P, int Q>
+// Threads that exchange points between pass p and pass p + 1 (either way):
+// those of one span block of pass p, a contiguous run of span(p) / 16
+// threads (all of them after the first pass).
+template <int LOGM>
+constexpr int xgroup(int p) {
+    return p == 0 ? FftShape<LOGM>::T : FftShape<LOGM>::span(p) / 16;
+}
+
+// Barrier over the G-thread group of thread t: the whole CTA, a warp, or a
+// named barrier per group (ids 1..T/G).
+template <int LOGM, int G>
+__device__ __forceinline__ void group_sync(int t) {
+    if constexpr (G >= FftShape<LOGM>::T) {
+        __syncthreads();
+    } else if constexpr (G <= 32) {
+        __syncwarp();
+    } else {
+        static_assert(FftShape<LOGM>::T / G <= 15, "named barrier ids");
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + t / G), "r"(G) : "memory");
+    }
+}
+
+// Move the points from pass P's layout to pass Q's (Q = P +- 1) through
+// shared memory.  Only the threads of one span block of the wider pass take
+// part, so the barrier between the writes and the reads is over that group;
+// before the writes, every thread that may still be reading the same words
+// from the previous exchange (group size PREVG, 0: none) must be done, so the
+// barrier there covers the wider of the two groups.
+template <int LOGM, int P, int Q, int PREVG>
 __device__ __forceinline__ void exchange(float2 (&v)[16], float2* sb, int t) {
+    constexpr int G = xgroup<LOGM>(P < Q ? P : Q);
+    constexpr int PRE = PREVG > G ? PREVG : G;
+    if constexpr (PREVG > 0) group_sync<LOGM, PRE>(t);
     float2* w = sb + Layout<LOGM, P>::base(t);
 #pragma unroll
     for (int j = 0; j < 16; ++j) w[j * Layout<LOGM, P>::STRIDE] = v[j];
-    __syncthreads();
+    group_sync<LOGM, G>(t);
     const float2* r = sb + Layout<LOGM, Q>::base(t);
 #pragma unroll
     for (int j = 0; j < 16; ++j) v[j] = r[j * Layout<LOGM, Q>::STRIDE];
-    __syncthreads();
 }
 
-template <int LOGM, int P>
+// Forward passes P.. and inverse passes ..0; PREVG is the group of the
+// exchange before (0: none).  Returns nothing; the exchange group sizes are
+// compile-time, so the barriers cost only what the data movement requires.
+template <int LOGM, int P, int PREVG = 0>
 __device__ __forceinline__ void forward_from(float2 (&v)[16], const float2* __restrict__ tw, float2* sb, int t) {
     run_pass<LOGM, P, false>(v, tw, t);
     if constexpr (P + 1 < FftShape<LOGM>::NP) {
-        exchange<LOGM, P, P + 1>(v, sb, t);
-        forward_from<LOGM, P + 1>(v, tw, sb, t);
+        exchange<LOGM, P, P + 1, PREVG>(v, sb, t);
+        forward_from<LOGM, P + 1, xgroup<LOGM>(P)>(v, tw, sb, t);
     }
 }
 
-template <int LOGM, int P>
+template <int LOGM, int P, int PREVG = 0>
 __device__ __forceinline__ void inverse_from(float2 (&v)[16], const float2* __restrict__ tw, float2* sb, int t) {
     run_pass<LOGM, P, true>(v, tw, t);
     if constexpr (P > 0) {
-        exchange<LOGM, P, P - 1>(v, sb, t);
-        inverse_from<LOGM, P - 1>(v, tw, sb, t);
+        exchange<LOGM, P, P - 1, PREVG>(v, sb, t);
+        inverse_from<LOGM, P - 1, xgroup<LOGM>(P - 1)>(v, tw, sb, t);
     }
+}
+
+// Group size of the last exchange of a forward transform (0: none), the
+// PREVG of an inverse transform that follows it in the same CTA.
+template <int LOGM>
+constexpr int last_forward_group() {
+    return FftShape<LOGM>::NP >= 2 ? xgroup<LOGM>(FftShape<LOGM>::NP - 2) : 0;
 }
 
 // Two segments as the real and imaginary parts of z: point n = t + T*j is
@@ -290,7 +329,7 @@ __device__ __forceinline__ void store_pair(const float2 (&v)[16], float* y0, flo
 
 // Single-block overlap-save: CTA k transforms blocks 2k and 2k + 1.
 template <int LOGM>
-__global__ void __launch_bounds__((1 << LOGM) / 16) k_fir_fft(FirFftArgs a) {
+__global__ void __launch_bounds__((1 << LOGM) / 16, 16384 >> LOGM) k_fir_fft(FirFftArgs a) {
     using F = FftShape<LOGM>;
     extern __shared__ float2 sb[];
     const int t = threadIdx.x;
@@ -311,7 +350,7 @@ __global__ void __launch_bounds__((1 << LOGM) / 16) k_fir_fft(FirFftArgs a) {
         v[2 * q] = cmul(v[2 * q], make_float2(h.x, h.y));
         v[2 * q + 1] = cmul(v[2 * q + 1], make_float2(h.z, h.w));
     }
-    inverse_from<LOGM, F::NP - 1>(v, a.tw, sb, t);
+    inverse_from<LOGM, F::NP - 1, last_forward_group<LOGM>()>(v, a.tw, sb, t);
     const int64_t m0 = a.N - n00 < a.B ? a.N - n00 : a.B;
     const int64_t m1 = live1 ? (a.N - n01 < a.B ? a.N - n01 : a.B) : 0;
     store_pair<LOGM>(v, a.y + c0 * a.ldy + n00, a.y + c1 * a.ldy + n01, Hh, m0, m1, t);
@@ -321,7 +360,7 @@ __global__ void __launch_bounds__((1 << LOGM) / 16) k_fir_fft(FirFftArgs a) {
 // pair, x[(b - 1) B, (b + 1) B) of channels 2r (re) and 2r + 1 (im), stored
 // like H: float4 q of thread t (positions 16t + 2q, 16t + 2q + 1) at q*T + t.
 template <int LOGM>
-__global__ void __launch_bounds__((1 << LOGM) / 16) k_fir_fft_spec(FirFftArgs a) {
+__global__ void __launch_bounds__((1 << LOGM) / 16, 16384 >> LOGM) k_fir_fft_spec(FirFftArgs a) {
     using F = FftShape<LOGM>;
     extern __shared__ float2 sb[];
     const int t = threadIdx.x;
@@ -343,7 +382,7 @@ __global__ void __launch_bounds__((1 << LOGM) / 16) k_fir_fft_spec(FirFftArgs a)
 // partitions of B taps, h_p[k] = h[pB + k]), whose last B points are outputs
 // [bB, (b + 1) B).
 template <int LOGM>
-__global__ void __launch_bounds__((1 << LOGM) / 16) k_fir_fft_conv(FirFftArgs a) {
+__global__ void __launch_bounds__((1 << LOGM) / 16, 16384 >> LOGM) k_fir_fft_conv(FirFftArgs a) {
     using F = FftShape<LOGM>;
     extern __shared__ float2 sb[];
     const int t = threadIdx.x;
@@ -410,6 +449,7 @@ cudaError_t prepare_fir_fft(int M) {
         case 2048: return prepare_log<11>();
         case 4096: return prepare_log<12>();
         case 8192: return prepare_log<13>();
+        case 16384: return prepare_log<14>();
         default: return cudaErrorInvalidValue;
     }
 }
@@ -421,6 +461,7 @@ cudaError_t launch_fir_fft(const FirFftArgs& a, cudaStream_t s) {
         case 11: return launch_log<11>(a, s);
         case 12: return launch_log<12>(a, s);
         case 13: return launch_log<13>(a, s);
+        case 14: return launch_log<14>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }

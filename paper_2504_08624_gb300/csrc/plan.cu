@@ -230,25 +230,34 @@ struct FftScheme {
     int M = 0, P = 0;
 };
 
-FftScheme fft_scheme_for(int L, int force) {
-    static const double K[4] = {71.0, 74.0, 85.0, 121.0};
+// Single-block cost per (M / B) for m = 10..14 (m = 14: one 1024-thread CTA
+// per SM, 16384 points).
+const double FFT_K[5] = {71.0, 74.0, 85.0, 121.0, 142.0};
+
+double fft_single_cost(int m, int L) {
+    const int M = 1 << m, B = M - (L - 1);
+    return B >= M / 8 ? 30.0 + FFT_K[m - 10] * M / B : -1.0;
+}
+
+FftScheme fft_scheme_for(int L, int force, double* cost_out = nullptr) {
     static const double I[4] = {219.0, 230.0, 253.0, 326.0};
     static const double SP[4] = {20.0, 21.4, 23.6, 24.7};
     FftScheme best;
     double cost = 0.0;
-    for (int m = 10; m <= 13; ++m) {
-        if (force >= 10 && force <= 13 && m != force) continue;
-        const int M = 1 << m, B = M - (L - 1);
-        if (B >= M / 8) {
-            const double c = 30.0 + K[m - 10] * M / B;
-            if (best.M == 0 || c < cost) best.M = M, best.P = 0, cost = c;
-        }
-        if (m >= 11 || force == m) {
+    for (int m = 10; m <= 14; ++m) {
+        if (force >= 10 && force <= 14 && m != force) continue;
+        // 16384 points: single-block only, and only where smaller transforms cannot hold the taps
+        if (m == 14 && force != 14 && L - 1 < 3 * 8192 / 4) continue;
+        const double c1 = fft_single_cost(m, L);
+        if (c1 > 0.0 && (best.M == 0 || c1 < cost)) best.M = 1 << m, best.P = 0, cost = c1;
+        if (m <= 13 && (m >= 11 || force == m)) {
+            const int M = 1 << m;
             const int P = (L + M / 2 - 1) / (M / 2);
             const double c = I[m - 10] + SP[m - 10] * P;
             if (best.M == 0 || c < cost) best.M = M, best.P = P, cost = c;
         }
     }
+    if (cost_out) *cost_out = cost;
     return best;
 }
 
@@ -454,6 +463,152 @@ int check_dims(int64_t C, int64_t N, int64_t ld) {
     return TFX_OK;
 }
 
+// Estimated time of a unit on 16 channels x 2.88M samples (microseconds, the
+// scale of the FFT cost model), to compare a composed chain with its units.
+double unit_cost_estimate(const HostUnit& u) {
+    if (u.fft) {
+        double c = 0.0;
+        const FftScheme sch = fft_scheme_for(u.L, u.fft_P > 0 ? 0 : u.fft_m, &c);
+        return sch.M > 0 ? c : 200.0;
+    }
+    if (u.tc) return 60.0 + 0.15 * u.L;  // persistent tensor-core GEMM, ~209 us at 1025 taps
+    if (u.seg) return 125.0;             // tensor-core cascade by segments
+    if (u.S > 0) return 220.0 + (u.L > 0 ? 2.0 * u.L : 0.0);  // look-back scan (+ fused CUDA-core FIR)
+    return 40.0 + 2.0 * u.L;             // CUDA-core FIR
+}
+
+// The whole chain as one FIR (the pipe composes linear time-invariant stages,
+// so the chain is the convolution with its composite impulse response).  The
+// cascades' impulse response g (all sections in chain order, FP64, zero
+// state) is computed over 65536 samples and must have decayed there (the
+// absolute sum of its last 4096 samples below 1e-14 of the whole).  With f
+// every FIR's taps convolved (FP64), g is truncated at the first D for which
+// sum_(n >= D) |g[n]| * sum |f| <= 1e-8 ||h_c||_2: the truncated tail changes
+// no output by more than that times max|x|, and ||h_c||_2 is the chain's RMS
+// gain for white input (taken over the first 16384 samples of h_c = g * f, a
+// lower bound).  The composite h_c = g[0, D) * f has Lc = D + Lf - 1 taps and
+// runs by single-block overlap-save with the transform size of least
+// modelled cost, if that beats the separate units; the signal must hold at
+// least 2 Lc samples (the transform's rounding is relative to each block's
+// energy, so a signal shorter than the response would be compared with an
+// output made only of its smallest leading terms).
+void compose_chain(tfx_plan* p) {
+    int S = 0;
+    std::vector<double> sec;
+    std::vector<double> f(1, 1.0);
+    int maxL = 0;
+    double separate = 0.0;
+    for (const HostUnit& u : p->units) {
+        if (u.hiq) return;
+        sec.insert(sec.end(), u.sec.begin(), u.sec.end());
+        S += u.S;
+        if (u.L > 0) {
+            std::vector<double> g(f.size() + u.taps.size() - 1, 0.0);
+            for (size_t i = 0; i < f.size(); ++i)
+                for (size_t k = 0; k < u.taps.size(); ++k) g[i + k] += f[i] * u.taps[k];
+            f.swap(g);
+            maxL = std::max(maxL, u.L);
+        }
+        separate += unit_cost_estimate(u);
+    }
+    if (S == 0 || maxL < FFT_MIN_TAPS) return;
+    const int W = 65536, HEAD = 16384;
+    std::vector<double> g(W);
+    std::vector<double> w1(S, 0.0), w2(S, 0.0);
+    for (int n = 0; n < W; ++n) {
+        double v = n == 0 ? 1.0 : 0.0;
+        for (int i = 0; i < S; ++i) {
+            const double* r = &sec[5 * (size_t)i];  // b0 b1 b2 a1 a2
+            const double c1 = r[1] - r[3] * r[0], c2 = r[2] - r[4] * r[0];
+            const double out = r[0] * v + w1[i];
+            const double n1 = c1 * v - r[3] * w1[i] + w2[i];
+            w2[i] = c2 * v - r[4] * w1[i];
+            w1[i] = n1;
+            v = out;
+        }
+        g[n] = v;
+    }
+    double total = 0.0, last = 0.0;
+    for (int n = 0; n < W; ++n) total += std::fabs(g[n]);
+    for (int n = W - 4096; n < W; ++n) last += std::fabs(g[n]);
+    if (!(total > 0.0) || !(last <= 1e-14 * total)) return;
+    const int Lf = (int)f.size();
+    double f1 = 0.0, n2 = 0.0;
+    for (double v : f) f1 += std::fabs(v);
+    {
+        std::vector<double> hc(HEAD, 0.0);
+        for (int i = 0; i < HEAD; ++i)
+            for (int k = 0; k < Lf && i + k < HEAD; ++k) hc[i + k] += g[i] * f[k];
+        for (double v : hc) n2 += v * v;
+        n2 = std::sqrt(n2);
+    }
+    if (!(n2 > 0.0)) return;
+    int D = W;
+    double tail = 0.0;
+    for (int n = W - 1; n >= 1; --n) {
+        if ((tail + std::fabs(g[n])) * f1 > 1e-8 * n2) {
+            D = n + 1;
+            break;
+        }
+        tail += std::fabs(g[n]);
+        D = n;
+    }
+    const int64_t Lc = (int64_t)D + Lf - 1;
+    if (p->N < 2 * Lc) return;
+    int bestm = 0;
+    double best = 0.0;
+    for (int m = 12; m <= 14; ++m) {
+        const int M = 1 << m;
+        if (Lc - 1 > M - M / 4) continue;  // at least M/4 outputs per block
+        const double c = fft_single_cost(m, (int)Lc);
+        if (c > 0.0 && (bestm == 0 || c < best)) bestm = m, best = c;
+    }
+    if (bestm == 0 || !(best < 0.95 * separate)) return;
+    HostUnit c;
+    c.L = (int)Lc;
+    c.taps.assign((size_t)Lc, 0.0);
+    for (int i = 0; i < D; ++i)
+        for (int k = 0; k < Lf; ++k) c.taps[(size_t)i + k] += g[i] * f[k];
+    c.fft = true;
+    c.fft_m = bestm;
+    c.fft_M = 1 << bestm;
+    c.fft_P = 0;
+    c.fft_B = c.fft_M - (c.L - 1);
+    p->chain = c;
+    p->use_chain = true;
+    p->chain_S = S;
+    p->chain_L = Lf;
+    p->chain_D = D;
+}
+
+// Spectrum of an FFT unit's taps (or of each partition) and its pass
+// twiddles into the constant blob at the unit's offsets.
+void fill_fft_tables(const HostUnit& u, char* host) {
+    // spectrum of h zero-padded to M, scaled by 1/M (the inverse FFT's
+    // normalisation), in bit-reversed order; twiddles e^(-2 pi i k / M)
+    // (partitioned: of each partition h[pB, (p + 1) B))
+    const int M = u.fft_M;
+    const int parts = std::max(u.fft_P, 1), plen = u.fft_P > 0 ? u.fft_B : u.L;
+    for (int q = 0; q < parts; ++q) {
+        std::vector<std::complex<double>> Hc(M, 0.0);
+        for (int k = 0; k < plen && q * plen + k < u.L; ++k) Hc[k] = u.taps[q * plen + k];
+        host_fft(Hc);
+        // position k = 16t + 2c + e (thread t, float4 c, half e) holds
+        // H[bitrev(k)] / M and is stored at float2 index 2 (c T + t) + e
+        float2* Hd = reinterpret_cast<float2*>(host + u.off_H) + (size_t)q * M;
+        const int T = M / 16;
+        for (int k = 0; k < M; ++k) {
+            int r = 0;
+            for (int b = 0; b < u.fft_m; ++b) r |= ((k >> b) & 1) << (u.fft_m - 1 - b);
+            const int t = k / 16, c = (k % 16) / 2, e = k % 2;
+            Hd[2 * (c * T + t) + e] = make_float2((float)(Hc[r].real() / M), (float)(Hc[r].imag() / M));
+        }
+    }
+    const std::vector<std::complex<double>> twd = fft_pass_twiddles(u.fft_m);
+    float2* tw = reinterpret_cast<float2*>(host + u.off_tw);
+    for (size_t k = 0; k < twd.size(); ++k) tw[k] = make_float2((float)twd[k].real(), (float)twd[k].imag());
+}
+
 int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
     // group stages: consecutive SOS stages merge into one cascade; an FIR
     // closes the current unit.
@@ -536,7 +691,12 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
             // FFT_MIN_TAPS on unless a tensor-core mode or precision is asked for
             const int force = (int)((p->flags & TFX_PLAN_FIR_FFT_LOG_MASK) >> 16);
             const bool tc_only = (p->flags & (TFX_PLAN_FIR_TC | TFX_PLAN_FIR_BF16_PLAIN | TFX_PLAN_FIR_BF16_SPLIT)) != 0;
-            const bool want_fft = (p->flags & TFX_PLAN_FIR_FFT) ? u.L >= 64 : (!tc_only && u.L >= FFT_MIN_TAPS);
+            // (by default only for signals of at least 2L samples: the
+            // transform rounds relative to each block's energy, and a signal
+            // shorter than the taps is all leading transient)
+            const bool want_fft = (p->flags & TFX_PLAN_FIR_FFT)
+                                      ? u.L >= 64
+                                      : (!tc_only && u.L >= FFT_MIN_TAPS && p->N >= 2 * (int64_t)u.L);
             const FftScheme sch = want_fft ? fft_scheme_for(u.L, force) : FftScheme();
             const int fftM = sch.M, fftP = sch.P;
             if (fftM > 0) {
@@ -587,6 +747,14 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
             if (u.S > 0 && u.S <= SEG_SMAX && u.L == 0 && !u.warp && !u.hiq) choose_segments(p, u, sm_count);
     }
 
+    // the whole chain as one FFT FIR of its composite response
+    p->use_chain = false;
+    if (!(p->flags & (TFX_PLAN_NO_COMPOSE | TFX_PLAN_FIR_CUDA_CORES | TFX_PLAN_UNFUSED | TFX_PLAN_FIR_BF16_PLAIN |
+                      TFX_PLAN_FIR_BF16_SPLIT | TFX_PLAN_SCAN_WARP_TILES | TFX_PLAN_FIR_TC | TFX_PLAN_SCAN_LOOKBACK |
+                      TFX_PLAN_TEST_DROP_PUBLISH | TFX_PLAN_FIR_FFT_LOG_MASK)) &&
+        !p->train && p->C > 0 && p->N > 0)
+        compose_chain(p);
+
     // constant blob layout
     size_t off = 0;
     for (HostUnit& u : p->units) {
@@ -623,6 +791,12 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
             u.off_dst = off;
             off = align_up(off + (size_t)u.S * sizeof(int64_t));
         }
+    }
+    if (p->use_chain) {
+        p->chain.off_H = off;
+        off = align_up(off + (size_t)p->chain.fft_M * sizeof(float2));
+        p->chain.off_tw = off;
+        off = align_up(off + fft_pass_twiddles(p->chain.fft_m).size() * sizeof(float2));
     }
     for (int32_t i = 0; i < nst; ++i) {
         PlainStage ps{st[i].kind, st[i].n, off};
@@ -661,31 +835,7 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
             std::memcpy(t + u.tc_a1.size() + u.tc_a2.size() + u.tc_rowinv.size() * 4, u.tc_phib.data(),
                         u.tc_phib.size() * 4);
         }
-        if (u.fft) {
-            // spectrum of h zero-padded to M, scaled by 1/M (the inverse FFT's
-            // normalisation), in bit-reversed order; twiddles e^(-2 pi i k / M)
-            // (partitioned: of each partition h[pB, (p + 1) B))
-            const int M = u.fft_M;
-            const int parts = std::max(u.fft_P, 1), plen = u.fft_P > 0 ? u.fft_B : u.L;
-            for (int q = 0; q < parts; ++q) {
-                std::vector<std::complex<double>> Hc(M, 0.0);
-                for (int k = 0; k < plen && q * plen + k < u.L; ++k) Hc[k] = u.taps[q * plen + k];
-                host_fft(Hc);
-                // position k = 16t + 2c + e (thread t, float4 c, half e) holds
-                // H[bitrev(k)] / M and is stored at float2 index 2 (c T + t) + e
-                float2* Hd = reinterpret_cast<float2*>(host.data() + u.off_H) + (size_t)q * M;
-                const int T = M / 16;
-                for (int k = 0; k < M; ++k) {
-                    int r = 0;
-                    for (int b = 0; b < u.fft_m; ++b) r |= ((k >> b) & 1) << (u.fft_m - 1 - b);
-                    const int t = k / 16, c = (k % 16) / 2, e = k % 2;
-                    Hd[2 * (c * T + t) + e] = make_float2((float)(Hc[r].real() / M), (float)(Hc[r].imag() / M));
-                }
-            }
-            const std::vector<std::complex<double>> twd = fft_pass_twiddles(u.fft_m);
-            float2* tw = reinterpret_cast<float2*>(host.data() + u.off_tw);
-            for (size_t k = 0; k < twd.size(); ++k) tw[k] = make_float2((float)twd[k].real(), (float)twd[k].imag());
-        }
+        if (u.fft) fill_fft_tables(u, host.data());
         if (p->train && u.S > 0) {
             std::memcpy(host.data() + u.off_raw, u.raw.data(), (size_t)u.S * 6 * sizeof(double));
             std::memcpy(host.data() + u.off_dst, u.dst.data(), (size_t)u.S * sizeof(int64_t));
@@ -723,6 +873,7 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
                     }
         }
     }
+    if (p->use_chain) fill_fft_tables(p->chain, host.data());
     for (int32_t i = 0; i < nst; ++i) {
         float* d = reinterpret_cast<float*>(host.data() + p->plain[i].off);
         if (st[i].kind == TFX_STAGE_SOS) {
@@ -777,6 +928,7 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
             for (HostUnit& u : p->units)
                 if (u.L > 0 && prepare_fir_dh_tc() != cudaSuccess) return TFX_ERR_UNSUPPORTED;
         }
+        if (p->use_chain && prepare_fir_fft(p->chain.fft_M) != cudaSuccess) return TFX_ERR_UNSUPPORTED;
     }
 
     // workspace layout
@@ -816,6 +968,10 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         // input copy for in-place operation: the unit reads other tiles' or segments' input
         const HostUnit& u0 = p->units[0];
         if (u0.tc || (u0.fft && u0.fft_P == 0) || (u0.seg && u0.seg_P > 1 && u0.seg_D > 0)) nbuf = 1;
+    }
+    if (p->use_chain) {
+        p->chain.ntt = p->N > 0 ? (p->N + p->chain.fft_B - 1) / p->chain.fft_B : 0;
+        nbuf = std::max<size_t>(nbuf, 1);  // input copy for in-place operation
     }
     p->ws_fused = p->scratch_bytes + nbuf * p->buf_bytes;
     p->ws_plain = (nst > 0 ? 2 : 0) * p->buf_bytes;
@@ -876,9 +1032,8 @@ bool ranges_overlap_not_equal(const float* x, const float* y, int64_t C, int64_t
 
 // Launch unit i for channels [c0, c0 + Cg) reading `in` (row stride ldin) and
 // writing `out` (row stride ldout).
-int launch_unit_range(tfx_plan* p, int i, const float* in, int64_t ldin, float* out, int64_t ldout, int64_t c0,
-                      int64_t Cg, char* scratch, float* copy_buf, cudaStream_t s, float2* ckpt = nullptr) {
-    const HostUnit& u = p->units[i];
+int launch_unit_range(tfx_plan* p, const HostUnit& u, const float* in, int64_t ldin, float* out, int64_t ldout,
+                      int64_t c0, int64_t Cg, char* scratch, float* copy_buf, cudaStream_t s, float2* ckpt = nullptr) {
     in += c0 * ldin;
     out += c0 * ldout;
     if (u.fft) {
@@ -1009,12 +1164,13 @@ int exec_fused(tfx_plan* p, const float* x, float* y, void* ws, cudaStream_t s) 
     char* scratch = w;
     float* buf[2] = {reinterpret_cast<float*>(w + p->scratch_bytes),
                      reinterpret_cast<float*>(w + p->scratch_bytes + p->buf_bytes)};
+    if (p->use_chain) return launch_unit_range(p, p->chain, x, p->ld, y, p->ld, 0, p->C, scratch, buf[0], s);
     for (int i = 0; i < nu; ++i) {
         const float* in = i == 0 ? x : buf[(i - 1) & 1];
         const int64_t ldin = i == 0 ? p->ld : p->N;
         float* out = i == nu - 1 ? y : buf[i & 1];
         const int64_t ldout = i == nu - 1 ? p->ld : p->N;
-        const int rc = launch_unit_range(p, i, in, ldin, out, ldout, 0, p->C, scratch, buf[0], s);
+        const int rc = launch_unit_range(p, p->units[i], in, ldin, out, ldout, 0, p->C, scratch, buf[0], s);
         if (rc != TFX_OK) return rc;
     }
     return TFX_OK;
@@ -1067,7 +1223,7 @@ int exec_train(tfx_plan* p, const float* x, float* y, char* saved, void* ws, cud
         float* out = i == nu - 1 ? y : reinterpret_cast<float*>(saved + p->units[i + 1].off_act);
         const int64_t ldout = i == nu - 1 ? p->ld : p->N;
         float2* ck = u.S > 0 ? reinterpret_cast<float2*>(saved + u.off_ckpt) : nullptr;
-        const int rc = launch_unit_range(p, i, in, ldin, out, ldout, 0, p->C, scratch, nullptr, s, ck);
+        const int rc = launch_unit_range(p, p->units[i], in, ldin, out, ldout, 0, p->C, scratch, nullptr, s, ck);
         if (rc != TFX_OK) return rc;
     }
     return TFX_OK;
@@ -1183,7 +1339,7 @@ int run_backward(tfx_plan* p, const float* x, const float* g, float* dx, double*
             const int o = cur == 0 ? 1 : 0;
             ++nl;
             if (!count_only) {
-                const int rc = launch_unit_range(p, i, gcur, N, gbuf[o], N, 0, C, ws, nullptr, s);
+                const int rc = launch_unit_range(p, p->units[i], gcur, N, gbuf[o], N, 0, C, ws, nullptr, s);
                 if (rc != TFX_OK) return rc;
             }
             if (i == 0) {
@@ -1315,7 +1471,8 @@ int tfx::plan_create_ex(tfx_plan** out, int64_t C, int64_t N, int64_t ld, const 
     if (rc != TFX_OK) return rc;
     if (flags & ~(TFX_PLAN_FIR_CUDA_CORES | TFX_PLAN_UNFUSED | TFX_PLAN_FIR_BF16_PLAIN | TFX_PLAN_FIR_BF16_SPLIT |
                   TFX_PLAN_SCAN_WARP_TILES | TFX_PLAN_TRAINABLE | TFX_PLAN_FIR_FFT | TFX_PLAN_FIR_TC |
-                  TFX_PLAN_FIR_FFT_LOG_MASK | TFX_PLAN_SCAN_LOOKBACK | TFX_PLAN_TEST_DROP_PUBLISH))
+                  TFX_PLAN_FIR_FFT_LOG_MASK | TFX_PLAN_SCAN_LOOKBACK | TFX_PLAN_TEST_DROP_PUBLISH |
+                  TFX_PLAN_NO_COMPOSE))
         return TFX_ERR_INVALID;
     tfx_plan* p = new (std::nothrow) tfx_plan();
     if (!p) return TFX_ERR_NOMEM;
@@ -1344,6 +1501,7 @@ size_t tfx_plan_workspace_size(const tfx_plan* p) {
 int tfx_plan_launch_count(const tfx_plan* p) {
     if (!p) return -1;
     if (p->C == 0 || p->N == 0) return 0;
+    if (p->use_chain) return 1;
     int n = 0;
     for (const HostUnit& u : p->units) n += u.fft && u.fft_P > 0 ? 2 : 1;
     return p->units.empty() ? 1 : n;
@@ -1353,7 +1511,13 @@ int tfx_plan_describe(const tfx_plan* p, char* buf, size_t len) {
     if (!p) return -1;
     std::string d;
     char item[160];
-    for (const HostUnit& u : p->units) {
+    if (p->use_chain) {
+        const HostUnit& c = p->chain;
+        snprintf(item, sizeof item, "chain_fft:S=%d,L=%d,D=%d,Lc=%d,M=%d,B=%d", p->chain_S, p->chain_L, p->chain_D,
+                 c.L, c.fft_M, c.fft_B);
+        d = item;
+    }
+    for (const HostUnit& u : (p->use_chain ? std::vector<HostUnit>() : p->units)) {
         if (!d.empty()) d += ';';
         if (u.fft) {
             snprintf(item, sizeof item, "fir_fft:L=%d,M=%d,B=%d,P=%d", u.L, u.fft_M, u.fft_B, u.fft_P);

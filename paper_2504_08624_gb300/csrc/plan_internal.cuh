@@ -108,6 +108,12 @@ struct tfx_plan {
     // device-side coefficient updates (tfx_plan_update_sos): per-section descriptors
     char* dsec = nullptr;
     int nsec = -1;  // -1: not built yet
+    // the whole chain as one FFT FIR of its composite impulse response
+    // (chain_fft); the separate units above stay built for after a
+    // coefficient update
+    bool use_chain = false;
+    tfx::HostUnit chain;
+    int chain_S = 0, chain_L = 0, chain_D = 0;  // sections, combined FIR length, cascade response length
 };
 
 namespace tfx {

@@ -1,0 +1,166 @@
+"""The whole chain as one FFT FIR of its composite impulse response
+(chain_fft; the pipe composes linear time-invariant stages, Sec. 3) against
+the FP64 oracle.  Cases: the multichannel chain, chains with several
+cascades and FIRs interleaved, ragged lengths around the block size, one
+sample, channel counts that pair blocks of different channels, in place,
+padded strides, graph capture, the switch back to separate units after a
+coefficient update, and the cases that must keep their units (short FIRs,
+poles beyond 0.999, slowly decaying cascades).  Tolerance: 1e-4 of each
+channel's peak (the chains contain SOS stages)."""
+import numpy as np
+import pytest
+
+from paper_2504_08624_gb300 import workloads as W
+from tests.gpu_util import assert_close, oracle_chain
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def run(x, stages, flags=0, inplace=False, ld=None):
+    from paper_2504_08624_gb300 import api
+    C, Ns = x.shape
+    ld = Ns if ld is None else ld
+    buf = torch.full((C * ld + 8,), 5.0, dtype=torch.float32, device="cuda")
+    xv = buf[:C * ld].view(C, ld)[:, :Ns]
+    xv.copy_(torch.from_numpy(x))
+    p = api.Plan(C, Ns, stages, ld=ld, flags=flags)
+    d = p.describe()
+    out = torch.full_like(buf, -7.0)
+    y = xv if inplace else out[:C * ld].view(C, ld)[:, :Ns]
+    p.execute(xv, y)
+    torch.cuda.synchronize()
+    assert p.get_error() == 0
+    assert p.launches_per_execute == 1 or d[0]["kind"] != "chain_fft"
+    p.close()
+    if not inplace and ld > Ns:  # the row padding is not written
+        assert torch.all(out[:C * ld].view(C, ld)[:, Ns:] == -7.0)
+    return y.cpu().numpy().astype(np.float64), d
+
+
+def check(x, stages, expect_chain=True, **kw):
+    got, d = run(x, stages, **kw)
+    assert (d[0]["kind"] == "chain_fft") == expect_chain, d
+    return assert_close(got, oracle_chain(x, stages), 1e-4, f"{d} {kw}"), d
+
+
+def test_multichannel_chain_composed():
+    wl = W.multichannel_fused()
+    x = wl.make_signal(5, 250_000)
+    err, d = check(x, wl.stages)
+    assert d[0]["S"] == 8 and d[0]["L"] == 1025 and d[0]["M"] == 16384
+    print("multichannel chain composed:", d, f"max rel err {err:.2e}")
+
+
+def test_ragged_lengths_around_the_block():
+    """Lengths around the block size B and around 2 Lc (below it the chain
+    keeps its units: a signal shorter than twice the composite response is
+    not composed); one to three channels, so the two blocks of a CTA fall in
+    the same or in different channels."""
+    wl = W.multichannel_fused()
+    from paper_2504_08624_gb300 import api
+    p = api.Plan(1, 100_000, wl.stages)
+    d = p.describe()[0]
+    p.close()
+    B, Lc = d["B"], d["Lc"]
+    for Ns in (1, 2, 2 * Lc - 1, 2 * Lc, B - 1, B, B + 1, 2 * B, 3 * B + 17):
+        for C in (1, 2, 3):
+            x = W.white_uniform(C, Ns, 700 + Ns % 97)
+            check(x, wl.stages, expect_chain=Ns >= 2 * Lc)
+
+
+@pytest.mark.parametrize("inplace", [False, True])
+def test_inplace_and_padded_stride(inplace):
+    wl = W.multichannel_fused()
+    x = wl.make_signal(3, 70_000)
+    check(x, wl.stages, inplace=inplace, ld=70_000 + 13)
+
+
+def test_interleaved_cascades_and_firs():
+    """cascade, FIR, cascade, FIR, FIR: one composite of all of them."""
+    stages = [("sos", W.butter_sos(4, 3000.0, W.FS)), ("fir", W.fir_lowpass(257, 9000.0, W.FS)),
+              ("sos", W.random_peaking_bank(3, W.FS, 11)), ("fir", W.fir_lowpass(129, 12000.0, W.FS)),
+              ("fir", W.fir_highpass(101, 100.0, W.FS))]
+    x = W.white_uniform(4, 90_000, 701)
+    err, d = check(x, stages)
+    assert d[0]["L"] == 257 + 129 + 101 - 2 and d[0]["S"] == 2 + 3
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_random_chains_with_long_firs(seed):
+    """Random stable cascades (poles up to 0.99) before a FIR of 200-2000 taps."""
+    rng = np.random.default_rng(seed)
+    L = int(rng.integers(200, 2000))
+    stages = [("sos", W.random_stable_sos(int(rng.integers(1, 9)), 800 + seed, 0.3, 0.99)),
+              ("fir", W.fir_lowpass(L, float(rng.uniform(2000, 20000)), W.FS))]
+    x = W.white_uniform(int(rng.integers(1, 5)), int(rng.integers(20_000, 120_000)), 710 + seed)
+    from paper_2504_08624_gb300 import _native as N_
+    got, d = run(x, stages)
+    ref = oracle_chain(x, stages)
+    sep, _ = run(x, stages, flags=N_.TFX_PLAN_NO_COMPOSE)
+    assert_close(got, ref, 1e-4, str(d))
+    assert_close(sep, ref, 1e-4, "separate units")
+
+
+def test_stays_separate_where_it_must():
+    """Short FIRs stay fused with the cascade on the CUDA cores; a pole beyond
+    0.999 keeps the FP64-carry scan; FIR-only and cascade-only chains have
+    nothing to compose; the flag keeps the units."""
+    from paper_2504_08624_gb300 import _native as N_
+    x = W.white_uniform(2, 40_000, 720)
+    check(x, [("sos", W.butter_sos(4, 1000.0, W.FS)), ("fir", W.fir_lowpass(31, 9000.0, W.FS))],
+          expect_chain=False)
+    r, th = 0.9995, 0.3
+    hi = np.array([[1e-3, 0.0, -1e-3, 1.0, -2 * r * np.cos(th), r * r]])
+    check(x, [("sos", hi), ("fir", W.fir_lowpass(513, 9000.0, W.FS))], expect_chain=False)
+    check(x, [("fir", W.fir_lowpass(513, 9000.0, W.FS))], expect_chain=False)
+    check(x, [("sos", W.butter_sos(4, 1000.0, W.FS))], expect_chain=False)
+    wl = W.multichannel_fused()
+    check(x, wl.stages, expect_chain=False, flags=N_.TFX_PLAN_NO_COMPOSE)
+
+
+def test_graph_capture():
+    from paper_2504_08624_gb300 import api
+    wl = W.multichannel_fused()
+    x = wl.make_signal(3, 60_000)
+    xt = torch.from_numpy(x).cuda()
+    p = api.Plan(3, 60_000, wl.stages)
+    assert p.describe()[0]["kind"] == "chain_fft" and p.launches_per_execute == 1
+    y = torch.empty_like(xt)
+    ws = p.workspace()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        p.execute(xt, y, ws)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    y2 = torch.zeros_like(xt)
+    with torch.cuda.graph(g):
+        p.execute(xt, y2, ws)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(y, y2)
+    p.close()
+
+
+def test_update_switches_back_to_units():
+    """After a device-side coefficient update the plan runs its separate
+    units with the new coefficients (the composite spectrum was built on the
+    host from the old ones)."""
+    from paper_2504_08624_gb300 import api
+    wl = W.multichannel_fused()
+    x = wl.make_signal(2, 50_000)
+    p = api.Plan(2, 50_000, wl.stages)
+    assert p.describe()[0]["kind"] == "chain_fft"
+    rows = np.concatenate([np.asarray(c).reshape(-1, 6) for k, c in wl.stages if k == "sos"])
+    new_rows = rows.copy()
+    new_rows[:, :3] *= 0.5
+    p.update_sos(torch.from_numpy(new_rows).cuda())
+    assert p.describe()[0]["kind"] != "chain_fft" and p.launches_per_execute == 2
+    y = p.execute(torch.from_numpy(x).cuda())
+    torch.cuda.synchronize()
+    assert p.get_error() == 0
+    p.close()
+    new_stages = [("sos", new_rows)] + [st for st in wl.stages if st[0] == "fir"]
+    assert_close(y.cpu().numpy(), oracle_chain(x, new_stages), 1e-4, "after update")

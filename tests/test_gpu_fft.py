@@ -24,12 +24,15 @@ pytestmark = pytest.mark.gpu
 def _scheme(L, force=None):
     """(M, P) the plan's cost model picks (P = 0: single block): single-block
     30 + k_m M / B (B >= M/8), partitioned I_m + s_m P, fitted per m."""
-    K = {10: 71.0, 11: 74.0, 12: 85.0, 13: 121.0}
+    K = {10: 71.0, 11: 74.0, 12: 85.0, 13: 121.0, 14: 110.0}
     I = {10: 219.0, 11: 230.0, 12: 253.0, 13: 326.0}
     SP = {10: 20.0, 11: 21.4, 12: 23.6, 13: 24.7}
     best = None
-    for m in range(10, 14):
+    for m in range(10, 15):
         if force is not None and m != force:
+            continue
+        # 16384 points: single-block only, where smaller transforms cannot hold the taps
+        if m == 14 and force != 14 and L - 1 < 3 * 8192 // 4:
             continue
         M = 1 << m
         B = M - (L - 1)
@@ -37,7 +40,7 @@ def _scheme(L, force=None):
             c = 30.0 + K[m] * M / B
             if best is None or c < best[0]:
                 best = (c, M, 0)
-        if m >= 11 or force == m:
+        if m <= 13 and (m >= 11 or force == m):
             P = -(-L // (M // 2))
             c = I[m] + SP[m] * P
             if best is None or c < best[0]:
@@ -102,11 +105,15 @@ def test_fft_fir_inplace_and_stride(inplace):
     check_fft(x, [("fir", _taps(513, 5))], inplace=inplace, ld=50000 + 37)
 
 
-def test_fft_fir_behind_cascade():
-    """Cascade then a long FIR: the cascade runs as its own unit, then the FFT unit."""
+@pytest.mark.parametrize("compose", [True, False])
+def test_fft_fir_behind_cascade(compose):
+    """Cascade then a long FIR: by default the whole chain is one FFT FIR of
+    its composite response; with TFX_PLAN_NO_COMPOSE the cascade runs as its
+    own unit, then the FFT unit."""
+    from paper_2504_08624_gb300 import _native as N_
     wl = W.multichannel_fused()
     x = wl.make_signal(3, 40000)
-    check_fft(x, wl.stages, wl.tol)
+    check_fft(x, wl.stages, wl.tol, flags=0 if compose else N_.TFX_PLAN_NO_COMPOSE)
 
 
 def test_fft_fir_lowpass_and_bandpass():
@@ -174,10 +181,10 @@ def test_partitioned_long_bandpass():
         check_fft(x, wl.stages, 1e-5, flags=N_.TFX_PLAN_FIR_FFT_LOG(m))
 
 
-@pytest.mark.parametrize("m", [10, 11, 12, 13])
+@pytest.mark.parametrize("m", [10, 11, 12, 13, 14])
 def test_fft_fir_every_transform_size(m):
-    """Each transform size (radix-4, -8, -16 and -2 first passes) on a FIR it
-    can hold, with a ragged tail."""
+    """Each transform size (radix-4, -8, -16, -2 and -4 first passes; 16384
+    points with 1024-thread CTAs) on a FIR it can hold, with a ragged tail."""
     from paper_2504_08624_gb300 import _native as N_
     L = (1 << m) // 4 + 1
     B = (1 << m) - (L - 1)
@@ -209,6 +216,10 @@ def test_plan_describe_routes():
     from paper_2504_08624_gb300 import api
     wl = W.multichannel_fused()
     d = api.Plan(4, 100000, wl.stages).describe()
+    assert [u["kind"] for u in d] == ["chain_fft"]
+    assert d[0]["S"] == 8 and d[0]["L"] == 1025 and d[0]["Lc"] == d[0]["D"] + 1024
+    assert d[0]["B"] == d[0]["M"] - (d[0]["Lc"] - 1)
+    d = api.Plan(4, 100000, wl.stages, flags=N_.TFX_PLAN_NO_COMPOSE).describe()
     assert [u["kind"] for u in d] == ["cascade", "fir_fft"]
     assert d[0]["S"] == 8 and d[1]["L"] == 1025 and d[1]["P"] == 0 and d[1]["B"] == d[1]["M"] - 1024
     d = api.Plan(4, 100000, wl.stages, flags=N_.TFX_PLAN_FIR_TC).describe()

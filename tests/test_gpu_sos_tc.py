@@ -127,10 +127,12 @@ def test_tc_cascade_inplace_and_stride(inplace, pad):
 
 
 def test_tc_cascade_then_fir():
-    """Cascade on the tensor cores, then the FFT FIR unit (the headline chain's layout)."""
+    """Cascade on the tensor cores, then the FFT FIR unit (the headline chain's
+    layout when its units stay separate)."""
+    from paper_2504_08624_gb300 import _native as N_
     wl = W.multichannel_fused()
     x = wl.make_signal(16, 1_100_000)
-    got, d = _run(x, wl.stages)
+    got, d = _run(x, wl.stages, flags=N_.TFX_PLAN_NO_COMPOSE)
     assert d[0]["scan"] == "tc" and d[1]["kind"] == "fir_fft", d
     assert_close(got[:2], oracle_chain(x[:2], wl.stages), wl.tol, "chain")
 
