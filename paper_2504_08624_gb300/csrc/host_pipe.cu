@@ -166,17 +166,11 @@ extern "C" int tfx_chain_host(const float* x, float* y, int64_t C, int64_t N, in
         const size_t span = ((size_t)(C - 1) * (size_t)ld + (size_t)N) * sizeof(float);
         if (xb < yb + span && yb < xb + span) return TFX_ERR_INVALID;
     }
-    // validate the stages the way a plan would, before anything is allocated
-    {
-        const size_t need = tfx_chain_workspace_size(1, N, N, st, nst);
-        if (need == SIZE_MAX) {
-            tfx_plan* probe = nullptr;
-            const int rc = tfx_plan_create(&probe, 0, N, N, st, nst, TFX_PLAN_DEFAULT);
-            tfx_plan_destroy(probe);
-            return rc != TFX_OK ? rc : TFX_ERR_INVALID;
-        }
-    }
+    for (int32_t i = 0; i < nst; ++i)
+        if ((st[i].kind != TFX_STAGE_FIR && st[i].kind != TFX_STAGE_SOS) || st[i].n < 0 || (st[i].n > 0 && !st[i].coef))
+            return TFX_ERR_INVALID;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // the key holds every coefficient: a cached pipeline's stages were validated when it was built
     const std::string key = host_key(C, N, st, nst, s);
     std::lock_guard<std::mutex> lk(g_hmu);
     HostPipe* h = nullptr;
@@ -185,6 +179,14 @@ extern "C" int tfx_chain_host(const float* x, float* y, int64_t C, int64_t N, in
         g_hlru.splice(g_hlru.begin(), g_hlru, it->second.second);
         h = it->second.first;
     } else {
+        // validate the stages the way a plan would, before anything is allocated
+        const size_t need = tfx_chain_workspace_size(1, N, N, st, nst);
+        if (need == SIZE_MAX) {
+            tfx_plan* probe = nullptr;
+            const int rc = tfx_plan_create(&probe, 0, N, N, st, nst, TFX_PLAN_DEFAULT);
+            tfx_plan_destroy(probe);
+            return rc != TFX_OK ? rc : TFX_ERR_INVALID;
+        }
         if (g_hcache.size() >= HOST_CACHE_MAX) {
             auto oit = g_hcache.find(g_hlru.back());
             destroy_pipe(oit->second.first);

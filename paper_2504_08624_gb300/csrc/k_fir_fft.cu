@@ -34,16 +34,41 @@
 // (conjugate twiddles, then the DIT G-point DFT), ending in natural order in
 // the layout the input was loaded in: point t + T*j in register j, so both the
 // input loads and the output stores are coalesced.  Each pass with twiddles
-// reads them from its own table, [slot q - 1][group position i], computed in
-// FP64 at plan time and rounded once: consecutive threads read consecutive
-// words, and every point takes one complex multiply per pass.
+// reads them from its own table (two slots' twiddles per 16-byte word, by
+// group position), computed in FP64 at plan time and rounded once:
+// consecutive threads read consecutive words, and every point takes one
+// complex multiply per pass.  Complex sums and differences are packed
+// two-lane FP32 instructions (real and imaginary part in one register pair).
 #include "tfx_common.cuh"
 
 namespace tfx {
 namespace {
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex sum and difference as one packed two-lane FP32 instruction each
+// (the real and imaginary parts are the two lanes; each lane rounds as the
+// scalar instruction does).
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+    float2 r;
+    asm("{.reg .b64 ra, rb, rr;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rr, ra, rb;\n\t"
+        "mov.b64 {%0, %1}, rr;}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+    float2 r;
+    asm("{.reg .b64 ra, rb, rr;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rr, ra, rb;\n\t"
+        "mov.b64 {%0, %1}, rr;}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -71,21 +96,36 @@ __device__ __forceinline__ float2 twc(float2 v) {
 }
 
 // One radix-2 stage (half-distance H) of the G-point DFT over registers
-// v[OFF + q*ST], q < G; butterflies q = Q, Q+1, ... by recursion.
+// v[OFF + q*ST], q < G; butterflies q = Q, Q+1, ... by recursion.  Sums and
+// differences are packed two-lane instructions; a quarter-turn twiddle
+// (multiplication by -i or +i, which swaps the lanes) is folded into scalar
+// sums and differences instead.
 template <int G, int ST, int OFF, int H, bool INV, int Q = 0>
 __device__ __forceinline__ void stage(float2 (&v)[16]) {
     if constexpr (Q < G) {
         if constexpr ((Q / H) % 2 == 0) {
             constexpr int i0 = OFF + Q * ST, i1 = OFF + (Q + H) * ST;
+            constexpr int T16 = (16 / (2 * H)) * (Q % H);  // twiddle in sixteenths of a turn
             const float2 a = v[i0];
-            if constexpr (!INV) {  // DIF: (a, c) -> (a + c, (a - c) w)
-                const float2 c = v[i1];
+            const float2 c = v[i1];
+            if constexpr (T16 == 0) {
+                v[i0] = cadd(a, c);
+                v[i1] = csub(a, c);
+            } else if constexpr (T16 == 4) {
+                if constexpr (!INV) {  // DIF: (a + c, (a - c)(-i))
+                    v[i0] = cadd(a, c);
+                    v[i1] = make_float2(a.y - c.y, c.x - a.x);
+                } else {  // DIT: (a + c i, a - c i)
+                    v[i0] = make_float2(a.x - c.y, a.y + c.x);
+                    v[i1] = make_float2(a.x + c.y, a.y - c.x);
+                }
+            } else if constexpr (!INV) {  // DIF: (a, c) -> (a + c, (a - c) w)
                 v[i0] = cadd(a, c);
                 v[i1] = twc<Q % H, 2 * H, false>(csub(a, c));
             } else {  // DIT: (a, c) -> (a + c w*, a - c w*)
-                const float2 c = twc<Q % H, 2 * H, true>(v[i1]);
-                v[i0] = cadd(a, c);
-                v[i1] = csub(a, c);
+                const float2 cw = twc<Q % H, 2 * H, true>(c);
+                v[i0] = cadd(a, cw);
+                v[i1] = csub(a, cw);
             }
         }
         stage<G, ST, OFF, H, INV, Q + 1>(v);
@@ -127,14 +167,24 @@ __device__ __forceinline__ float4 ld_tw4(const float4* p) {
 
 // Multiply slot q (q = Q..G-1) of the group v[OFF + q*ST] by the pass
 // twiddle w_S^(i * bitrev(q)) (INV: its conjugate), read from the pass's
-// table at [q - 1][i] (row length `sub`): consecutive i are consecutive words.
+// table tp (row length `sub`): the twiddles of slots 2k + 1 and 2k + 2 are
+// interleaved as one float4 per group position i at float4 index k*sub + i
+// (one 16-byte load for two slots; consecutive i are consecutive words), and
+// the last slot of an odd count is a plain row of float2 after the pairs.
 template <int G, int ST, int OFF, bool INV, int Q = 1>
-__device__ __forceinline__ void twiddle_group(float2 (&v)[16], const float2* __restrict__ tp, int sub) {
+__device__ __forceinline__ void twiddle_group(float2 (&v)[16], const float2* __restrict__ tp, int i, int sub) {
     if constexpr (Q < G) {
-        constexpr int i = OFF + Q * ST;
-        const float2 w = ld_tw(tp + (Q - 1) * sub);
-        v[i] = INV ? cmulc(v[i], w) : cmul(v[i], w);
-        twiddle_group<G, ST, OFF, INV, Q + 1>(v, tp, sub);
+        constexpr int j0 = OFF + Q * ST;
+        if constexpr (Q + 1 < G) {
+            constexpr int j1 = OFF + (Q + 1) * ST;
+            const float4 w = ld_tw4(reinterpret_cast<const float4*>(tp) + ((Q - 1) / 2) * sub + i);
+            v[j0] = INV ? cmulc(v[j0], make_float2(w.x, w.y)) : cmul(v[j0], make_float2(w.x, w.y));
+            v[j1] = INV ? cmulc(v[j1], make_float2(w.z, w.w)) : cmul(v[j1], make_float2(w.z, w.w));
+            twiddle_group<G, ST, OFF, INV, Q + 2>(v, tp, i, sub);
+        } else {
+            const float2 w = ld_tw(tp + 2 * ((G - 1) / 2) * sub + i);
+            v[j0] = INV ? cmulc(v[j0], w) : cmul(v[j0], w);
+        }
     }
 }
 
@@ -190,12 +240,12 @@ __device__ __forceinline__ void first_groups(float2 (&v)[16], const float2* __re
     using F = FftShape<LOGM>;
     constexpr int G = F::G0, NG = 16 / G, sub = F::M / G;
     if constexpr (C < NG) {
-        const float2* tp = tw + t + F::T * C;
+        const int i = t + F::T * C;
         if constexpr (!INV) {
             dft_dif<G, NG, C>(v);
-            twiddle_group<G, NG, C, false>(v, tp, sub);
+            twiddle_group<G, NG, C, false>(v, tw, i, sub);
         } else {
-            twiddle_group<G, NG, C, true>(v, tp, sub);
+            twiddle_group<G, NG, C, true>(v, tw, i, sub);
             dft_dit<G, NG, C>(v);
         }
         first_groups<LOGM, INV, C + 1>(v, tw, t);
@@ -209,12 +259,13 @@ __device__ __forceinline__ void run_pass(float2 (&v)[16], const float2* __restri
         first_groups<LOGM, INV>(v, tw + F::tw_off(0), t);
     } else {
         constexpr int sub = F::sub(P);
-        const float2* tp = tw + F::tw_off(P) + t % sub;
+        const float2* tp = tw + F::tw_off(P);
+        const int i = t % sub;
         if constexpr (!INV) {
             dft_dif<16, 1, 0>(v);
-            if constexpr (sub > 1) twiddle_group<16, 1, 0, false>(v, tp, sub);
+            if constexpr (sub > 1) twiddle_group<16, 1, 0, false>(v, tp, i, sub);
         } else {
-            if constexpr (sub > 1) twiddle_group<16, 1, 0, true>(v, tp, sub);
+            if constexpr (sub > 1) twiddle_group<16, 1, 0, true>(v, tp, i, sub);
             dft_dit<16, 1, 0>(v);
         }
     }
@@ -327,17 +378,15 @@ __device__ __forceinline__ void store_pair(const float2 (&v)[16], float* y0, flo
     }
 }
 
-// Single-block overlap-save: CTA k transforms blocks 2k and 2k + 1.
+// One block pair of the single-block scheme: blocks 2pr and 2pr + 1.
 template <int LOGM>
-__global__ void __launch_bounds__((1 << LOGM) / 16, 16384 >> LOGM) k_fir_fft(FirFftArgs a) {
+__device__ __forceinline__ void fft_block_pair(const FirFftArgs& a, int64_t pr, float2* sb, int t) {
     using F = FftShape<LOGM>;
-    extern __shared__ float2 sb[];
-    const int t = threadIdx.x;
-    const int64_t k0 = 2 * (int64_t)blockIdx.x;
+    const int Hh = a.L - 1;
+    const int64_t k0 = 2 * pr;
     const bool live1 = k0 + 1 < a.nb;
     const int64_t c0 = k0 / a.nbpc, c1 = live1 ? (k0 + 1) / a.nbpc : c0;
     const int64_t n00 = (k0 % a.nbpc) * (int64_t)a.B, n01 = live1 ? ((k0 + 1) % a.nbpc) * (int64_t)a.B : 0;
-    const int Hh = a.L - 1;
     float2 v[16];
     load_pair<LOGM>(v, a.x + c0 * a.ldx, a.x + c1 * a.ldx, live1, n00 - Hh, n01 - Hh, a.N, t);
     forward_from<LOGM, 0>(v, a.tw, sb, t);
@@ -354,6 +403,13 @@ __global__ void __launch_bounds__((1 << LOGM) / 16, 16384 >> LOGM) k_fir_fft(Fir
     const int64_t m0 = a.N - n00 < a.B ? a.N - n00 : a.B;
     const int64_t m1 = live1 ? (a.N - n01 < a.B ? a.N - n01 : a.B) : 0;
     store_pair<LOGM>(v, a.y + c0 * a.ldy + n00, a.y + c1 * a.ldy + n01, Hh, m0, m1, t);
+}
+
+// Single-block overlap-save: CTA k transforms blocks 2k and 2k + 1.
+template <int LOGM>
+__global__ void __launch_bounds__((1 << LOGM) / 16, 16384 >> LOGM) k_fir_fft(FirFftArgs a) {
+    extern __shared__ float2 sb[];
+    fft_block_pair<LOGM>(a, blockIdx.x, sb, threadIdx.x);
 }
 
 // Partitioned overlap-save, step 1: the spectrum of segment b of a channel

@@ -232,7 +232,7 @@ struct FftScheme {
 
 // Single-block cost per (M / B) for m = 10..14 (m = 14: one 1024-thread CTA
 // per SM, 16384 points).
-const double FFT_K[5] = {71.0, 74.0, 85.0, 121.0, 142.0};
+const double FFT_K[5] = {71.0, 74.0, 77.0, 113.0, 143.0};
 
 double fft_single_cost(int m, int L) {
     const int M = 1 << m, B = M - (L - 1);
@@ -284,8 +284,10 @@ void host_fft(std::vector<std::complex<double>>& a) {
 
 // Twiddle tables of the overlap-save transform of M = 2^m points: its passes
 // run over spans M, M/G0, ..., 16 (G0 = 2^(m mod 4), or 16), radix G0 first
-// and 16 after; a pass over span S with radix G and sub = S/G > 1 has a table
-// [q - 1][i] = e^(-2 pi i * i * bitrev_G(q) / S), q = 1..G-1, i < sub.
+// and 16 after; a pass over span S with radix G and sub = S/G > 1 has the
+// twiddles w(q, i) = e^(-2 pi i * i * bitrev_G(q) / S), q = 1..G-1, i < sub,
+// stored as pairs (w(2k + 1, i), w(2k + 2, i)) at [k][i], then the row of
+// w(G - 1, i) when G - 1 is odd.
 std::vector<std::complex<double>> fft_pass_twiddles(int m) {
     std::vector<std::complex<double>> out;
     const int M = 1 << m, r = m % 4;
@@ -301,14 +303,21 @@ std::vector<std::complex<double>> fft_pass_twiddles(int m) {
         if (sub == 1) continue;
         int bits = 0;
         while ((1 << bits) < G) ++bits;
-        for (int q = 1; q < G; ++q) {
+        auto tw = [&](int q, int i) {
             int kq = 0;
             for (int b = 0; b < bits; ++b) kq |= ((q >> b) & 1) << (bits - 1 - b);
+            const double ang = -2.0 * M_PI * (double)(((int64_t)i * kq) % Sp) / (double)Sp;
+            return std::complex<double>(std::cos(ang), std::sin(ang));
+        };
+        // slots 2k + 1 and 2k + 2 interleaved per group position, then the
+        // last slot of an odd count alone
+        for (int q = 1; q + 1 < G; q += 2)
             for (int i = 0; i < sub; ++i) {
-                const double ang = -2.0 * M_PI * (double)(((int64_t)i * kq) % Sp) / (double)Sp;
-                out.push_back(std::complex<double>(std::cos(ang), std::sin(ang)));
+                out.push_back(tw(q, i));
+                out.push_back(tw(q + 1, i));
             }
-        }
+        if ((G - 1) % 2 == 1)
+            for (int i = 0; i < sub; ++i) out.push_back(tw(G - 1, i));
     }
     return out;
 }
@@ -472,7 +481,7 @@ double unit_cost_estimate(const HostUnit& u) {
         return sch.M > 0 ? c : 200.0;
     }
     if (u.tc) return 60.0 + 0.15 * u.L;  // persistent tensor-core GEMM, ~209 us at 1025 taps
-    if (u.seg) return 125.0;             // tensor-core cascade by segments
+    if (u.seg) return 140.0;             // tensor-core cascade by segments (8 sections, 16 x 2.88M: ~140 us)
     if (u.S > 0) return 220.0 + (u.L > 0 ? 2.0 * u.L : 0.0);  // look-back scan (+ fused CUDA-core FIR)
     return 40.0 + 2.0 * u.L;             // CUDA-core FIR
 }
@@ -563,7 +572,7 @@ void compose_chain(tfx_plan* p) {
         const double c = fft_single_cost(m, (int)Lc);
         if (c > 0.0 && (bestm == 0 || c < best)) bestm = m, best = c;
     }
-    if (bestm == 0 || !(best < 0.95 * separate)) return;
+    if (bestm == 0 || !(best < separate)) return;
     HostUnit c;
     c.L = (int)Lc;
     c.taps.assign((size_t)Lc, 0.0);

@@ -24,7 +24,7 @@ pytestmark = pytest.mark.gpu
 def _scheme(L, force=None):
     """(M, P) the plan's cost model picks (P = 0: single block): single-block
     30 + k_m M / B (B >= M/8), partitioned I_m + s_m P, fitted per m."""
-    K = {10: 71.0, 11: 74.0, 12: 85.0, 13: 121.0, 14: 110.0}
+    K = {10: 71.0, 11: 74.0, 12: 77.0, 13: 113.0, 14: 143.0}
     I = {10: 219.0, 11: 230.0, 12: 253.0, 13: 326.0}
     SP = {10: 20.0, 11: 21.4, 12: 23.6, 13: 24.7}
     best = None
@@ -82,7 +82,7 @@ def _taps(L, seed):
     return np.random.default_rng(seed).standard_normal(L) / math.sqrt(L)
 
 
-@pytest.mark.parametrize("L", [64, 65, 129, 257, 335, 1025, 2049, 4097])
+@pytest.mark.parametrize("L", [64, 65, 129, 257, 335, 1025, 2049, 4097, 6146, 8193])
 def test_fft_fir_lengths(L):
     """Forced FFT route (the model picks single-block for these lengths)."""
     M, B = _fft_block(L)
@@ -143,9 +143,9 @@ def _part_block(L):
     return M, M // 2, P
 
 
-@pytest.mark.parametrize("L", [6146, 8193, 16384, 20000])
+@pytest.mark.parametrize("L", [12290, 13000, 16384, 20000])
 def test_partitioned_fir_lengths(L):
-    """Beyond 6145 taps the FIR is partitioned: lengths shorter than one
+    """Beyond 12289 taps the FIR is partitioned: lengths shorter than one
     block, on and around block multiples, and an odd channel count (the last
     pair has no imaginary channel)."""
     M, B, P = _part_block(L)
