@@ -481,6 +481,28 @@ int tfx_plan_update_sos(tfx_plan *p, const double *rows, tfx_stream s);
 int64_t tfx_plan_sos_rows(const tfx_plan *p);
 
 /*
+ * tfx_plan_update_coefs -- every coefficient of the plan's chain from device
+ * memory, without a host round trip: the update a training step makes after
+ * its optimizer step (Sec. 3: filters as trainable modules).  coef: device
+ * FP64, tfx_plan_coef_count values in the layout of tfx_plan_backward's
+ * dcoef (stages in chain order; an FIR stage its taps, an SOS stage its raw
+ * rows b0 b1 b2 a0 a1 a2).  Recomputes on the GPU the section constants (as
+ * tfx_plan_update_sos), the FIR taps' FP32 copies and, for FIRs run by FFT,
+ * their spectra (FP32 transform of the taps, as the filter's own).  The
+ * plan's structure stays as created (units, kernels, transform sizes, the
+ * FP64-carry routing); a tensor-core cascade runs the look-back scan and a
+ * composed chain its separate units from the first update on.  FIRs on the
+ * tensor cores (tap tables scaled on the host) are TFX_ERR_UNSUPPORTED.  The
+ * first call builds the update descriptors (host-synchronous: make it before
+ * any capture); later calls are tfx_plan_update_coefs_launch_count launches,
+ * asynchronous and capturable.  An unstable or invalid row sets the status
+ * read by tfx_plan_get_error.  Must not overlap an execution of the plan.
+ * Errors: TFX_ERR_INVALID, TFX_ERR_UNSUPPORTED, TFX_ERR_NOMEM, TFX_ERR_CUDA.
+ */
+int tfx_plan_update_coefs(tfx_plan *p, const double *coef, tfx_stream s);
+int tfx_plan_update_coefs_launch_count(const tfx_plan *p);
+
+/*
  * Measurement helper (the paper has no counterpart): the FP32 multiply-add
  * rate of this GPU, the denominator of the CUDA-core rooflines, which must
  * be measured rather than derived from clock and unit counts.

@@ -55,7 +55,7 @@ EXPORTS = [
     "tfx_batch_launch_count", "tfx_batch_execute", "tfx_batch_get_error", "tfx_batch_destroy",
     "tfx_batch_group_count", "tfx_batch_group_info", "tfx_batch_execute_group",
     "tfx_design_sections", "tfx_design_device", "tfx_plan_update_sos", "tfx_plan_sos_rows",
-    "tfx_fma_probe", "tfx_fma_probe_flops",
+    "tfx_fma_probe", "tfx_fma_probe_flops", "tfx_plan_update_coefs", "tfx_plan_update_coefs_launch_count",
 ]
 
 
@@ -178,6 +178,10 @@ def lib():
     L.tfx_design_device.restype = ctypes.c_int
     L.tfx_plan_update_sos.argtypes = [vp, vp, vp]
     L.tfx_plan_update_sos.restype = ctypes.c_int
+    L.tfx_plan_update_coefs.argtypes = [vp, vp, vp]
+    L.tfx_plan_update_coefs.restype = ctypes.c_int
+    L.tfx_plan_update_coefs_launch_count.argtypes = [vp]
+    L.tfx_plan_update_coefs_launch_count.restype = ctypes.c_int
     L.tfx_plan_sos_rows.argtypes = [vp]
     L.tfx_plan_sos_rows.restype = i64
     L.tfx_fma_probe.argtypes = [fp, i32, i32, i32, i32, vp]

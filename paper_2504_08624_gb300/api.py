@@ -190,6 +190,19 @@ class Plan:
         # a composed chain falls back to its separate units after an update
         self.launches_per_execute = int(N.lib().tfx_plan_launch_count(self._h))
 
+    def update_coefs(self, coef: torch.Tensor) -> None:
+        """Set every coefficient of the chain from ``coef`` (CUDA float64,
+        ``coef_count`` values in the layout of the backward's dcoef: stages in
+        order, an FIR its taps, an SOS stage its raw rows) on the GPU, with no
+        host round trip (tfx_plan_update_coefs)."""
+        if not coef.is_cuda or coef.dtype != torch.float64 or coef.numel() != self.coef_count:
+            raise ValueError("coef: CUDA float64 tensor of coef_count values")
+        coef = coef.contiguous()
+        with torch.cuda.device(self.device):
+            rc = N.lib().tfx_plan_update_coefs(self._h, ctypes.c_void_p(coef.data_ptr()), _stream_handle(self.device))
+        N.check(rc, "tfx_plan_update_coefs")
+        self.launches_per_execute = int(N.lib().tfx_plan_launch_count(self._h))
+
     # -- gradients (plans created with TFX_PLAN_TRAINABLE) -----------------
 
     @property
@@ -305,40 +318,83 @@ def mse_loss(y: torch.Tensor, target: torch.Tensor) -> torch.Tensor:
     """Differentiable MSE on the GPU kernel (the differentiable-chain workload's loss)."""
     return MSELossFunction.apply(y, target)
 
-_TRAIN_PLANS: dict = {}
-_TRAIN_PLANS_MAX = 8
+# Trainable plans for ChainFunction, pooled by shape and chain structure
+# (stage kinds and sizes), not by coefficient values: a training step updates
+# a pooled plan's coefficients on the device (tfx_plan_update_coefs) instead
+# of copying them to the host and building a new plan.  A plan is lent to
+# one forward until its backward has run (its coefficients and saved state
+# belong to that forward), so a pool holds as many plans as forwards are
+# pending at once (one in a plain training loop).
+_TRAIN_POOLS: dict = {}
+_TRAIN_POOLS_MAX = 8   # structures kept
+_TRAIN_POOL_PLANS = 4  # plans per structure
 
 
-def _train_plan(C: int, Ns: int, stages, device) -> Plan:
-    key = (C, Ns, str(device), tuple((k, c.shape, c.tobytes()) for k, c in stages))
-    p = _TRAIN_PLANS.pop(key, None)
-    if p is None:
-        p = Plan(C, Ns, stages, flags=N.TFX_PLAN_TRAINABLE, device=device.index)
-        if len(_TRAIN_PLANS) >= _TRAIN_PLANS_MAX:
-            # dropped, not closed: a pending backward may still hold it
-            _TRAIN_PLANS.pop(next(iter(_TRAIN_PLANS)))
-    _TRAIN_PLANS[key] = p  # most recent last
-    return p
+def _pool_key(C: int, Ns: int, device, coefs, kinds):
+    return (C, Ns, str(device), tuple((k, tuple(c.shape)) for k, c in zip(kinds, coefs)))
+
+
+def _release(plan: Plan) -> None:
+    plan._pending = max(0, plan._pending - 1)
+    if plan._pending == 0 and getattr(plan, "_evicted", False):
+        plan.close()
+
+
+def _lend_train_plan(C: int, Ns: int, device, kinds, coefs):
+    """(plan, fresh): a pooled trainable plan with no pending backward, or a
+    new one built from the current coefficient values (fresh = True)."""
+    key = _pool_key(C, Ns, device, coefs, kinds)
+    pool = _TRAIN_POOLS.pop(key, None)
+    if pool is None:
+        pool = []
+        if len(_TRAIN_POOLS) >= _TRAIN_POOLS_MAX:
+            old = _TRAIN_POOLS.pop(next(iter(_TRAIN_POOLS)))
+            for q in old:  # closed now, or by the backward that still holds it
+                q._evicted = True
+                if q._pending == 0:
+                    q.close()
+    _TRAIN_POOLS[key] = pool  # most recent last
+    for q in pool:
+        if q._pending == 0:
+            return q, False
+    stages = [(k, c.detach().to("cpu", torch.float64).numpy()) for k, c in zip(kinds, coefs)]
+    q = Plan(C, Ns, stages, flags=N.TFX_PLAN_TRAINABLE, device=device.index)
+    q._pending = 0
+    if len(pool) >= _TRAIN_POOL_PLANS:
+        # more forwards pending than the pool keeps: the oldest idle-by-then plan is closed after its backward
+        old = pool.pop(0)
+        old._evicted = True
+        if old._pending == 0:
+            old.close()
+    pool.append(q)
+    return q, True
 
 
 class ChainFunction(torch.autograd.Function):
     """y = chain(x) with gradients for x and every coefficient tensor.
 
-    The coefficient values are read on the host to build (or reuse) a
-    trainable plan, so CUDA coefficient tensors cost one device-to-host copy
-    per call; x and the gradients stay on the GPU."""
+    The plan comes from a pool keyed by shape and chain structure; its
+    coefficients are set on the GPU from the coefficient tensors (one FP64
+    concatenation and one update launch group), so a training loop with CUDA
+    coefficient tensors makes no host round trip and allocates no plan after
+    its first step.  Only a newly built plan reads the values on the host."""
 
     @staticmethod
-    def forward(ctx, x, kinds, *coefs):
+    def forward(ctx, x, kinds, hold, *coefs):
         x2 = _check_signal(x).contiguous()
         if not x2.is_cuda:
             raise ValueError("chain_ad needs a CUDA signal")
-        stages = [(k, c.detach().to("cpu", torch.float64).numpy()) for k, c in zip(kinds, coefs)]
         C, Ns = x2.shape
-        plan = _train_plan(C, Ns, stages, x2.device)
+        plan, fresh = _lend_train_plan(C, Ns, x2.device, kinds, coefs)
+        if not fresh:
+            flat = torch.cat([c.detach().reshape(-1).to(device=x2.device, dtype=torch.float64) for c in coefs]) \
+                if coefs else torch.zeros(0, dtype=torch.float64, device=x2.device)
+            plan.update_coefs(flat)
         saved = plan.new_saved()
         y = torch.empty_like(x2)
         plan.forward_train(x2, y, saved)
+        if hold:
+            plan._pending += 1  # held until the backward has read the coefficients
         ctx.plan = plan
         ctx.meta = [(c.shape, c.dtype, c.device) for c in coefs]
         ctx.kinds = kinds
@@ -350,16 +406,19 @@ class ChainFunction(torch.autograd.Function):
     def backward(ctx, gy):
         x2, saved = ctx.saved_tensors
         plan = ctx.plan
-        g2 = _check_signal(gy.to(torch.float32)).contiguous()
-        need_dx = ctx.needs_input_grad[0]
-        need_dc = any(ctx.needs_input_grad[2:])
-        if not (need_dx or need_dc):
-            return (None, None) + (None,) * len(ctx.meta)
-        dx = torch.empty_like(x2) if need_dx else None
-        dcoef = torch.empty(max(1, plan.coef_count), dtype=torch.float64, device=x2.device) if need_dc else None
-        plan.backward(x2, g2, dx, dcoef, saved)
+        try:
+            g2 = _check_signal(gy.to(torch.float32)).contiguous()
+            need_dx = ctx.needs_input_grad[0]
+            need_dc = any(ctx.needs_input_grad[3:])
+            if not (need_dx or need_dc):
+                return (None, None, None) + (None,) * len(ctx.meta)
+            dx = torch.empty_like(x2) if need_dx else None
+            dcoef = torch.empty(max(1, plan.coef_count), dtype=torch.float64, device=x2.device) if need_dc else None
+            plan.backward(x2, g2, dx, dcoef, saved)
+        finally:
+            _release(plan)
         grads, off = [], 0
-        for (shape, dtype, device), need in zip(ctx.meta, ctx.needs_input_grad[2:]):
+        for (shape, dtype, device), need in zip(ctx.meta, ctx.needs_input_grad[3:]):
             n = 1
             for d in shape:
                 n *= d
@@ -370,7 +429,15 @@ class ChainFunction(torch.autograd.Function):
             off += n
         if dx is not None and ctx.squeeze:
             dx = dx[0]
-        return (dx, None, *grads)
+        return (dx, None, None, *grads)
+
+
+def _chain_apply(x: torch.Tensor, kinds, coefs) -> torch.Tensor:
+    """ChainFunction.apply, telling it whether a backward will follow (grad
+    mode on and something requiring grad): only then does the forward keep
+    its plan lent until that backward."""
+    hold = torch.is_grad_enabled() and (x.requires_grad or any(c.requires_grad for c in coefs))
+    return ChainFunction.apply(x, tuple(kinds), hold, *coefs)
 
 
 def chain_ad(x: torch.Tensor, stages) -> torch.Tensor:
@@ -379,7 +446,7 @@ def chain_ad(x: torch.Tensor, stages) -> torch.Tensor:
     dL/d(coefficient); SOS rows as raw b0 b1 b2 a0 a1 a2)."""
     kinds = tuple(k for k, _ in stages)
     coefs = [c if torch.is_tensor(c) else torch.as_tensor(c, dtype=torch.float64) for _, c in stages]
-    return ChainFunction.apply(x, kinds, *coefs)
+    return _chain_apply(x, kinds, coefs)
 
 
 class FilterChain(torch.nn.Module):
@@ -394,7 +461,7 @@ class FilterChain(torch.nn.Module):
              for _, c in stages])
 
     def forward(self, x: torch.Tensor) -> torch.Tensor:
-        return ChainFunction.apply(x, self.kinds, *self.coefs)
+        return _chain_apply(x, self.kinds, list(self.coefs))
 
 
 class LearnableBiquadChain(torch.nn.Module):
@@ -420,7 +487,7 @@ class LearnableBiquadChain(torch.nn.Module):
         return torch.cat([self.b, torch.stack([ones, -2.0 * r * torch.cos(th), r * r], 1)], 1)
 
     def forward(self, x: torch.Tensor) -> torch.Tensor:
-        return ChainFunction.apply(x, ("sos", "fir"), self.rows(), self.h)
+        return _chain_apply(x, ("sos", "fir"), [self.rows(), self.h])
 
 
 # ---------------------------------------------------------------------------

@@ -191,18 +191,38 @@ __global__ void k_design(const tfx_design* __restrict__ specs, int n, const int6
 // Section constants of one plan section from its raw row: grid (sections),
 // block PW_LEN-ish threads, thread k writes A^k.
 struct SecUpdate {
-    int64_t row;        // raw row index in the caller's array (6 doubles per row)
+    int64_t row;        // raw row index in a compact rows array (6 doubles per row)
+    int64_t flat;       // offset of the raw row in the chain's flat coefficient array
     float* coef;        // [8]
     float4* pw;         // [PW_LEN]
     double4* pw64;      // [PW_LEN] or null
     double* raw_copy;   // trainable plans: the raw row for the a0 chain rule, or null
+    float* plain;       // [8]: the plain path's copy of the section constants
     int chunk;          // samples per thread of the unit's scan
 };
 
-__global__ void k_update_sections(const SecUpdate* __restrict__ secs, const double* __restrict__ rows,
+// One FIR stage's FP32 taps from the flat coefficient array: the CUDA-core
+// and plain-path copies (zero-padded to `lpad` and `L`).
+struct FirUpdate {
+    int64_t flat;
+    int L, lpad;
+    float* taps;
+    float* plain;
+};
+
+__global__ void k_update_fir_taps(const FirUpdate* __restrict__ firs, const double* __restrict__ coef) {
+    const FirUpdate f = firs[blockIdx.x];
+    for (int k = threadIdx.x; k < f.lpad; k += blockDim.x) {
+        const float v = k < f.L ? (float)coef[f.flat + k] : 0.f;
+        f.taps[k] = v;
+        if (k < f.L) f.plain[k] = v;
+    }
+}
+
+__global__ void k_update_sections(const SecUpdate* __restrict__ secs, const double* __restrict__ rows, int flat,
                                   int* __restrict__ status) {
     const SecUpdate su = secs[blockIdx.x];
-    const double* r = rows + 6 * su.row;
+    const double* r = rows + (flat ? su.flat : 6 * su.row);
     if (r[3] == 0.0 || !isfinite(r[0] + r[1] + r[2] + r[3] + r[4] + r[5])) {
         if (threadIdx.x == 0) atomicCAS(status, 0, (int)TFX_ERR_INVALID);
         return;
@@ -222,6 +242,7 @@ __global__ void k_update_sections(const SecUpdate* __restrict__ secs, const doub
         su.coef[5] = (float)(a1 * b2 - a2 * b1);
         if (su.raw_copy)
             for (int j = 0; j < 6; ++j) su.raw_copy[j] = r[j];
+        for (int j = 0; j < 6; ++j) su.plain[j] = su.coef[j];
     }
     // A = M^chunk, M = [[-a1, 1], [-a2, 0]] (one-sample transfer of the c-form state)
     double m00 = -a1, m01 = 1.0, m10 = -a2, m11 = 0.0;
@@ -287,39 +308,94 @@ int tfx_design_device(const tfx_design* specs, int32_t n, const int64_t* row_off
 
 }  // extern "C"
 
-// The per-section update descriptors of a plan are built and uploaded once
-// (host-synchronous); every update after that is one launch.
-int tfx::plan_update_sections(tfx_plan* p, const double* rows_dev, cudaStream_t s) {
-    // tensor-core cascades hold GEMM tables derived from the coefficients on
-    // the host: such units run the look-back scan (whose constants are the
-    // ones updated here) from the first update on
-    for (HostUnit& u : p->units) u.seg = false;
-    // a composed chain's spectrum is derived from the coefficients on the
-    // host too: such a plan runs its separate units from now on
-    p->use_chain = false;
-    if (!p->dsec && p->nsec != 0) {
-        std::vector<SecUpdate> v;
-        int64_t row = 0;
-        for (HostUnit& u : p->units) {
-            for (int k = 0; k < u.S; ++k) {
-                SecUpdate su{};
-                su.row = row++;
-                su.coef = reinterpret_cast<float*>(p->dconst + u.off_coef) + 8 * k;
-                su.pw = reinterpret_cast<float4*>(p->dconst + u.off_pw) + (size_t)k * PW_LEN;
-                su.pw64 = u.hiq ? reinterpret_cast<double4*>(p->dconst + u.off_pw64) + (size_t)k * PW_LEN : nullptr;
-                su.raw_copy = p->train ? reinterpret_cast<double*>(p->dconst + u.off_raw) + 6 * k : nullptr;
-                su.chunk = (u.L == 0 && !u.warp) ? T_CASCADE : T_CHUNK;
-                v.push_back(su);
-            }
+namespace {
+
+// Plain-path constants of every chain stage, by the stage's offset in the
+// flat coefficient array (stages in order; SOS: 6 values per row, FIR: n).
+std::vector<std::pair<int64_t, float*>> plain_by_flat(tfx_plan* p) {
+    std::vector<std::pair<int64_t, float*>> out;
+    int64_t off = 0;
+    for (const PlainStage& st : p->plain) {
+        float* base = reinterpret_cast<float*>(p->dconst + st.off);
+        if (st.kind == TFX_STAGE_SOS) {
+            for (int r = 0; r < st.n; ++r) out.push_back({off + 6 * r, base + 8 * r});
+            off += 6 * (int64_t)st.n;
+        } else {
+            out.push_back({off, base});
+            off += st.n;
         }
-        p->nsec = (int)v.size();
-        if (p->nsec == 0) return TFX_OK;
-        if (cudaMalloc(&p->dsec, v.size() * sizeof(SecUpdate)) != cudaSuccess) return TFX_ERR_NOMEM;
-        if (cudaMemcpy(p->dsec, v.data(), v.size() * sizeof(SecUpdate), cudaMemcpyHostToDevice) != cudaSuccess)
-            return TFX_ERR_CUDA;
     }
-    if (p->nsec == 0) return TFX_OK;
-    k_update_sections<<<(unsigned)p->nsec, 256, 0, s>>>(reinterpret_cast<const SecUpdate*>(p->dsec), rows_dev,
+    return out;
+}
+
+float* plain_at(const std::vector<std::pair<int64_t, float*>>& m, int64_t flat) {
+    for (const auto& e : m)
+        if (e.first == flat) return e.second;
+    return nullptr;
+}
+
+// The per-section (and per-FIR) update descriptors, built and uploaded once
+// (host-synchronous); every update after that is a few launches.
+int build_update_descriptors(tfx_plan* p) {
+    if (p->dsec || p->nsec == 0) return TFX_OK;
+    const auto pm = plain_by_flat(p);
+    std::vector<SecUpdate> v;
+    std::vector<FirUpdate> f;
+    int64_t row = 0;
+    for (HostUnit& u : p->units) {
+        for (int k = 0; k < u.S; ++k) {
+            SecUpdate su{};
+            su.row = row++;
+            su.flat = u.dst[k];
+            su.coef = reinterpret_cast<float*>(p->dconst + u.off_coef) + 8 * k;
+            su.pw = reinterpret_cast<float4*>(p->dconst + u.off_pw) + (size_t)k * PW_LEN;
+            su.pw64 = u.hiq ? reinterpret_cast<double4*>(p->dconst + u.off_pw64) + (size_t)k * PW_LEN : nullptr;
+            su.raw_copy = p->train ? reinterpret_cast<double*>(p->dconst + u.off_raw) + 6 * k : nullptr;
+            su.plain = plain_at(pm, su.flat);
+            su.chunk = (u.L == 0 && !u.warp) ? T_CASCADE : T_CHUNK;
+            if (!su.plain) return TFX_ERR_INVALID;
+            v.push_back(su);
+        }
+        if (u.L > 0) {
+            FirUpdate fu{};
+            fu.flat = u.fir_dst;
+            fu.L = u.L;
+            fu.lpad = u.nkb * FIR_R;
+            fu.taps = reinterpret_cast<float*>(p->dconst + u.off_taps);
+            fu.plain = plain_at(pm, fu.flat);
+            if (!fu.plain) return TFX_ERR_INVALID;
+            f.push_back(fu);
+        }
+    }
+    p->nsec = (int)v.size();
+    p->nfir = (int)f.size();
+    const size_t bytes = v.size() * sizeof(SecUpdate) + f.size() * sizeof(FirUpdate);
+    if (bytes == 0) return TFX_OK;
+    if (cudaMalloc(&p->dsec, bytes) != cudaSuccess) return TFX_ERR_NOMEM;
+    if (!v.empty() && cudaMemcpy(p->dsec, v.data(), v.size() * sizeof(SecUpdate), cudaMemcpyHostToDevice) != cudaSuccess)
+        return TFX_ERR_CUDA;
+    if (!f.empty() && cudaMemcpy(p->dsec + v.size() * sizeof(SecUpdate), f.data(), f.size() * sizeof(FirUpdate),
+                                 cudaMemcpyHostToDevice) != cudaSuccess)
+        return TFX_ERR_CUDA;
+    return TFX_OK;
+}
+
+// Coefficients derived on the host (the tensor-core cascade's GEMM tables,
+// a composed chain's spectrum) go stale with an update: such units run the
+// look-back scan, and the chain its separate units, from now on.
+void drop_host_derived(tfx_plan* p) {
+    for (HostUnit& u : p->units) u.seg = false;
+    p->use_chain = false;
+}
+
+}  // namespace
+
+int tfx::plan_update_sections(tfx_plan* p, const double* rows_dev, cudaStream_t s) {
+    drop_host_derived(p);
+    const int rc = build_update_descriptors(p);
+    if (rc != TFX_OK) return rc;
+    if (p->nsec <= 0) return TFX_OK;
+    k_update_sections<<<(unsigned)p->nsec, 256, 0, s>>>(reinterpret_cast<const SecUpdate*>(p->dsec), rows_dev, 0,
                                                          p->dstatus);
     return cudaGetLastError() == cudaSuccess ? TFX_OK : TFX_ERR_CUDA;
 }
@@ -330,6 +406,49 @@ extern "C" int tfx_plan_update_sos(tfx_plan* p, const double* rows, tfx_stream s
     for (const HostUnit& u : p->units) nrows += u.S;
     if (nrows > 0 && !rows) return TFX_ERR_INVALID;
     return plan_update_sections(p, rows, reinterpret_cast<cudaStream_t>(s));
+}
+
+extern "C" int tfx_plan_update_coefs(tfx_plan* p, const double* coef, tfx_stream stream) {
+    if (!p) return TFX_ERR_INVALID;
+    if (p->ncoef > 0 && !coef) return TFX_ERR_INVALID;
+    for (const HostUnit& u : p->units)
+        if (u.tc) return TFX_ERR_UNSUPPORTED;  // tap tables scaled on the host
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    drop_host_derived(p);
+    const int rc = build_update_descriptors(p);
+    if (rc != TFX_OK) return rc;
+    if (p->nsec > 0) {
+        k_update_sections<<<(unsigned)p->nsec, 256, 0, s>>>(reinterpret_cast<const SecUpdate*>(p->dsec), coef, 1,
+                                                             p->dstatus);
+        if (cudaGetLastError() != cudaSuccess) return TFX_ERR_CUDA;
+    }
+    if (p->nfir > 0) {
+        k_update_fir_taps<<<(unsigned)p->nfir, 256, 0, s>>>(
+            reinterpret_cast<const FirUpdate*>(p->dsec + (size_t)p->nsec * sizeof(SecUpdate)), coef);
+        if (cudaGetLastError() != cudaSuccess) return TFX_ERR_CUDA;
+    }
+    for (const HostUnit& u : p->units) {
+        if (!u.fft) continue;
+        if (launch_fir_fft_spectrum(coef + u.fir_dst, u.L, u.fft_M, u.fft_B, u.fft_P,
+                                    reinterpret_cast<const float2*>(p->dconst + u.off_tw),
+                                    reinterpret_cast<float2*>(p->dconst + u.off_H), s) != cudaSuccess)
+            return TFX_ERR_CUDA;
+    }
+    return TFX_OK;
+}
+
+extern "C" int tfx_plan_update_coefs_launch_count(const tfx_plan* p) {
+    if (!p) return -1;
+    int64_t S = 0;
+    int n = 0;
+    for (const HostUnit& u : p->units) {
+        if (u.tc) return -1;
+        S += u.S;
+        if (u.fft) ++n;
+    }
+    bool fir = false;
+    for (const HostUnit& u : p->units) fir = fir || u.L > 0;
+    return (S > 0 ? 1 : 0) + (fir ? 1 : 0) + n;
 }
 
 extern "C" int64_t tfx_plan_sos_rows(const tfx_plan* p) {

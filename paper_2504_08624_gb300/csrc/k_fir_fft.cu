@@ -468,6 +468,46 @@ __global__ void __launch_bounds__((1 << LOGM) / 16, 16384 >> LOGM) k_fir_fft_con
     store_pair<LOGM>(v, y0, live1 ? y0 + a.ldy : y0, F::M - a.B, m0, live1 ? m0 : 0, t);
 }
 
+// Spectrum of a FIR (or of each of its P partitions of B taps) computed on
+// the device from FP64 taps, for coefficient updates without a host round
+// trip: CTA p transforms h[pB, pB + len) (len = B, or L when P = 0) zero-
+// padded to M points with the same forward transform the filter uses, and
+// stores it as the filter reads it: scaled by 1/M, bit-reversed, float4 q of
+// thread t at q*T + t.
+template <int LOGM>
+__global__ void __launch_bounds__((1 << LOGM) / 16, 16384 >> LOGM)
+    k_fir_fft_spectrum(const double* __restrict__ taps, int L, int B, int P, const float2* __restrict__ tw,
+                       float2* __restrict__ H) {
+    using F = FftShape<LOGM>;
+    extern __shared__ float2 sb[];
+    const int t = threadIdx.x;
+    const int part = blockIdx.x;
+    const int64_t first = P > 0 ? (int64_t)part * B : 0;
+    const int len = P > 0 ? B : L;
+    float2 v[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const int n = t + F::T * j;
+        const int64_t k = first + n;
+        v[j] = make_float2(n < len && k < L ? (float)taps[k] : 0.f, 0.f);
+    }
+    forward_from<LOGM, 0>(v, tw, sb, t);
+    const float inv = 1.0f / (float)F::M;
+    float4* h4 = reinterpret_cast<float4*>(H + (int64_t)part * F::M) + t;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        h4[q * F::T] = make_float4(v[2 * q].x * inv, v[2 * q].y * inv, v[2 * q + 1].x * inv, v[2 * q + 1].y * inv);
+}
+
+template <int LOGM>
+cudaError_t launch_spectrum_log(const double* taps, int L, int B, int P, const float2* tw, float2* H,
+                                cudaStream_t s) {
+    constexpr int T = (1 << LOGM) / 16;
+    const size_t smem = fir_fft_smem_bytes(1 << LOGM);
+    k_fir_fft_spectrum<LOGM><<<(unsigned)(P > 0 ? P : 1), T, smem, s>>>(taps, L, B, P, tw, H);
+    return cudaGetLastError();
+}
+
 template <int LOGM>
 cudaError_t launch_log(const FirFftArgs& a, cudaStream_t s) {
     constexpr int T = (1 << LOGM) / 16;
@@ -492,6 +532,8 @@ cudaError_t prepare_log() {
         e = cudaFuncSetAttribute(k_fir_fft_spec<LOGM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_fir_fft_conv<LOGM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fir_fft_spectrum<LOGM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     return e;
 }
 
@@ -506,6 +548,18 @@ cudaError_t prepare_fir_fft(int M) {
         case 4096: return prepare_log<12>();
         case 8192: return prepare_log<13>();
         case 16384: return prepare_log<14>();
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_fir_fft_spectrum(const double* taps, int L, int M, int B, int P, const float2* tw, float2* H,
+                                    cudaStream_t s) {
+    switch (M) {
+        case 1024: return launch_spectrum_log<10>(taps, L, B, P, tw, H, s);
+        case 2048: return launch_spectrum_log<11>(taps, L, B, P, tw, H, s);
+        case 4096: return launch_spectrum_log<12>(taps, L, B, P, tw, H, s);
+        case 8192: return launch_spectrum_log<13>(taps, L, B, P, tw, H, s);
+        case 16384: return launch_spectrum_log<14>(taps, L, B, P, tw, H, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -106,8 +106,9 @@ struct tfx_plan {
     int tc_min_taps = tfx::TC_MIN_TAPS;  // FIRs with at least this many taps go to the tensor cores
     bool allow_hiq = true;               // route cascades with poles of radius > 0.999 to FP64 carries
     // device-side coefficient updates (tfx_plan_update_sos): per-section descriptors
-    char* dsec = nullptr;
+    char* dsec = nullptr;  // section descriptors, then FIR descriptors
     int nsec = -1;  // -1: not built yet
+    int nfir = 0;
     // the whole chain as one FFT FIR of its composite impulse response
     // (chain_fft); the separate units above stay built for after a
     // coefficient update

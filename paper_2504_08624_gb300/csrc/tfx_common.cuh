@@ -367,6 +367,8 @@ cudaError_t launch_fir_tc(const FirTcArgs& a, cudaStream_t s);
 size_t fir_fft_smem_bytes(int M);
 cudaError_t prepare_fir_fft(int M);
 cudaError_t launch_fir_fft(const FirFftArgs& a, cudaStream_t s);
+cudaError_t launch_fir_fft_spectrum(const double* taps, int L, int M, int B, int P, const float2* tw, float2* H,
+                                    cudaStream_t s);
 cudaError_t launch_fir_tc_batched(const BatchFir* units, const int64_t* prefix, int nunits, int64_t tiles,
                                   BatchBases bases, size_t smem, cudaStream_t s);
 cudaError_t prepare_fir_tc_batched(size_t smem);
