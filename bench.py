@@ -62,6 +62,8 @@ def parse():
                     help="skip the fwd+bwd measurement added to a forward run")
     ap.add_argument("--no-long-fir", action="store_true",
                     help="skip the long-FIR precision measurement added to a forward run")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the many-clip batched measurement added to a forward run")
     args = ap.parse_args()
     if args.mode is None:
         args.mode = "fwdbwd" if args.workload == "differentiable_chain" else "fwd"
@@ -861,6 +863,11 @@ def main():
     long_fir = None
     if not args.no_long_fir and args.part == "chain" and rank == 0:
         long_fir = measure_long_fir_precision(dev, stream, torch)
+    batched = None
+    if not args.no_batched and args.part == "chain":
+        batched = measure_batched(dev, stream, torch, dist, ws, rank, local, pk, fp32, 10, 3,
+                                  with_e2e=not args.no_e2e, with_plain=False, with_cpu=False,
+                                  with_parity=not args.no_cpu_baseline)
 
     if rank == 0:
         out = {
@@ -876,7 +883,7 @@ def main():
             "parity": parity, "plain_gpu": plain, "separate_units": separate, "plan": plan.describe(),
             "gpu_launches": int(args.steps * plan.launches_per_execute),
             "clocks": clocks, "gpu": props.name, "fp32_peak": fp32, "fwd_bwd": fwd_bwd,
-            "long_fir_precision": long_fir,
+            "long_fir_precision": long_fir, "batched": batched,
         }
         print(json.dumps(out), flush=True)
     if dist is not None:
@@ -884,26 +891,47 @@ def main():
         dist.destroy_process_group()
 
 
-def run_batched_main(args, dev, torch, dist, ws, rank, local):
+def measure_batched(dev, stream, torch, dist, ws, rank, local, pk, fp32, steps, warmup, with_e2e=True,
+                    with_plain=True, with_cpu=True, with_parity=True) -> dict:
     """The many-clip workload: 1000 clips, each its own length, channel count
-    and chain, filtered by the batched launch (a few launches over all clips)
-    replayed from one CUDA graph, with the autotuned tile parameters."""
+    and chain, filtered by the batched launches (composed chains by FFT, one
+    launch per transform size; the other clips' units grouped by level and
+    kernel) replayed from one CUDA graph, with the autotuned parameters."""
     from paper_2504_08624_gb300 import api, autotune, workloads as W
-    stream = torch.cuda.current_stream(dev)
-    pk = peaks()
-    props = torch.cuda.get_device_properties(dev)
     clips = W.batched_clips()
     spec = [(c.C, c.N, c.stages) for c in clips]
-    b0 = api.Batch(spec)
-    total = b0.total_samples
+    total = sum(C * Ns for C, Ns, _ in spec)
     gen = torch.Generator(device=dev).manual_seed(5)
     x = torch.rand(total, device=dev, generator=gen) * 2 - 1
-    b0.close()
     cands = [{"fir_nb": nb, "tc_min_taps": t} for nb in (128, 256) for t in (64, 128)]
-    tuned = autotune.tune_batch(spec, x, reps=2, candidates=cands)
-    b = api.Batch(spec, fir_nb=tuned["fir_nb"], tc_min_taps=tuned["tc_min_taps"])
+    t0 = time.perf_counter()
+    tuned = autotune.tune_batch(spec, reps=2, candidates=cands)
+    tune_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    b = api.Batch(spec, fir_nb=tuned["fir_nb"], tc_min_taps=tuned["tc_min_taps"], fft_m=tuned["fft_m"])
+    plan_s = time.perf_counter() - t0
     y = b.empty()
     wsb = b.workspace()
+    parity = None
+    if with_parity and rank == 0:
+        # a sample of clips with their seeded signals against the oracle
+        import oracle
+        sample = [0, 17, 333, 998]
+        xp = x.clone()
+        for i in sample:
+            b.view(xp, i).copy_(torch.from_numpy(clips[i].make_signal()))
+        yp = b.execute(xp)
+        torch.cuda.synchronize()
+        errs = []
+        for i in sample:
+            c = clips[i]
+            n = min(c.N, 200000)
+            xs = np.ascontiguousarray(c.make_signal()[:, :n])
+            got = b.view(yp, i).cpu().numpy().astype(np.float64)[:, :n]
+            errs.append(float(channel_rel_err(got, oracle.chain(xs, c.stages)).max()))
+        parity = {"reference": "FP64 oracle", "clips": sample, "max_rel_err": max(errs), "per_clip": errs,
+                  "tol": 1e-4, "note": "first 200000 samples of each sampled clip, per channel"}
+        del xp, yp
     side = torch.cuda.Stream(dev)
     side.wait_stream(stream)
     with torch.cuda.stream(side):
@@ -914,12 +942,11 @@ def run_batched_main(args, dev, torch, dist, ws, rank, local):
     with torch.cuda.graph(graph):
         b.execute(x, y, wsb)
     sampler = ClockSampler(local)
-    for _ in range(max(3, args.warmup)):
+    for _ in range(max(3, warmup)):
         graph.replay()
     torch.cuda.synchronize()
     sampler.start()
     time.sleep(0.3)
-    steps = min(args.steps, 30)
     t = time_gpu(graph.replay, steps, 0, stream, torch, dist)
     clocks = sampler.stop()
     if b.get_error() != 0:
@@ -935,25 +962,33 @@ def run_batched_main(args, dev, torch, dist, ws, rank, local):
     for g, (kind, level, tiles, samples, flops) in enumerate(b.groups()):
         k_g = 5
         t_g = time_gpu(lambda: b.execute_group(g, x, y, wsb), k_g, 2, stream, torch, None) / k_g
-        groups.append({"kind": ["fused cascade+FIR", "cascade", "tensor-core FIR"][kind], "level": level,
+        groups.append({"kind": ["fused cascade+FIR", "cascade", "tensor-core FIR", "composed chain (FFT)"][kind],
+                       "level": level,
                        "tiles": tiles, "channel_samples": samples, "ms": t_g * 1e3,
                        "algorithmic_tflops": flops / t_g / 1e12})
     dom = max(range(len(groups)), key=lambda i: groups[i]["ms"])
     dg = groups[dom]
     if dg["kind"] == "tensor-core FIR":
         roof = {"bound": "tensor", "kernel": "k_fir_tc_batched", "peak": pk["bf16_tflops_sustained"],
-                "peak_source": f"{pk['source']} dense bf16/fp16 sustained"}
+                "peak_source": f"{pk['source']} dense bf16/fp16 sustained", "achieved": dg["algorithmic_tflops"],
+                "unit": "TFLOP/s"}
+    elif dg["kind"] == "composed chain (FFT)":
+        roof = {"bound": "hbm", "kernel": "k_fir_fft_batched", "peak": pk["hbm_gbs"],
+                "peak_source": f"{pk['source']} HBM copy bandwidth", "unit": "GB/s",
+                "achieved": dg["channel_samples"] * 8.0 / (dg["ms"] * 1e-3) / 1e9,
+                "note": "8 B per sample (FP32 read + write) of the group's clips"}
     else:
-        roof = {"bound": "alu", "kernel": "k_unit_batched", "peak": fp32_alu_peak_tflops(
-            props.multi_processor_count, pk["sm_max_mhz"]), "peak_source": "FP32 FMA units x max SM clock"}
-    roof.update({"achieved": dg["algorithmic_tflops"], "unit": "TFLOP/s", "kernel_ms": dg["ms"],
-                 "share_of_step": dg["ms"] / (step_s * 1e3), "traffic": traffic_for(roof["kernel"], "batched_clips")})
+        roof = {"bound": "alu", "kernel": "k_unit_batched", "peak": fp32["tflops"],
+                "peak_source": "measured FP32 FMA rate (bench.measure_fp32_peak)", "achieved": dg["algorithmic_tflops"],
+                "unit": "TFLOP/s"}
+    roof.update({"kernel_ms": dg["ms"], "share_of_step": dg["ms"] / (step_s * 1e3),
+                 "traffic": traffic_for(roof["kernel"], "batched_clips")})
     roof["frac"] = roof["achieved"] / roof["peak"]
     ach_gbs = total * 8.0 / step_s / 1e9
     hbm = {"bound": "hbm", "achieved": ach_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
            "frac": ach_gbs / pk["hbm_gbs"], "peak_source": pk["source"], "note": "8 B per channel-sample"}
     e2e = None
-    if not args.no_e2e:
+    if with_e2e:
         x_host = x.cpu().pin_memory()
         y_host = torch.empty_like(x_host).pin_memory()
         xd = torch.empty_like(x)
@@ -968,8 +1003,9 @@ def run_batched_main(args, dev, torch, dist, ws, rank, local):
         e2e = {"value": total * ws * k_e / t_e, "unit": UNIT, "h2d_bytes_per_step": int(total * 4),
                "d2h_bytes_per_step": int(total * 4), "ms_per_step": t_e / k_e * 1e3, "steps": k_e,
                "api": "packed pinned host buffers, Batch.execute"}
+        del x_host, y_host, xd
     plain = None
-    if not args.no_plain:
+    if with_plain:
         # the plain sequential path on the first 20 clips (it runs at ~1e8 ch-samples/s)
         ps = [api.Plan(C, Ns, st) for C, Ns, st in spec[:20] if C * Ns > 0]
         xs = [torch.rand(p.C, p.N, device=dev) for p in ps]
@@ -982,7 +1018,7 @@ def run_batched_main(args, dev, torch, dist, ws, rank, local):
         for p in ps:
             p.close()
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if with_cpu and rank == 0 and ws == 1:
         import oracle
         lib = oracle.load()
         t0 = time.perf_counter()
@@ -996,22 +1032,43 @@ def run_batched_main(args, dev, torch, dist, ws, rank, local):
         dt = time.perf_counter() - t0
         cpu = {"value": n_cpu / dt, "unit": UNIT, "cores": lib.num_threads(), "kind": "oracle",
                "sample": f"clips in order until 15 s ({n_cpu} channel-samples incl. signal generation), {dt:.1f} s"}
-    if rank == 0:
-        print(json.dumps({
-            "metric": METRIC, "value": total * ws * steps / t_all, "unit": UNIT, "n_gpus": ws, "steps": steps,
-            "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"batched_clips_{len(clips)}", "clips": len(clips), "channel_samples": total,
-                       "chains": "1-8 random stable sections + 33-2049-tap FIR per clip",
-                       "launches": b.launches_per_execute, "cuda_graph": True,
-                       "autotuned": {k: tuned[k] for k in ("fir_nb", "tc_min_taps", "cached")},
-                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                       "l2": f"{total * 4 / 1e9:.1f} GB in and out per step > 129 MB L2, no flush"},
-            "roofline": roof, "roofline_hbm": hbm, "groups": groups, "cpu_baseline": cpu, "e2e": e2e,
-            "plain_gpu": plain, "gpu_launches": int(steps * b.launches_per_execute), "clocks": clocks,
-            "gpu": props.name,
-        }), flush=True)
+    out = {
+        "workload": f"batched_clips_{len(clips)}", "value": total * ws * steps / t_all, "unit": UNIT,
+        "ms_per_step": step_s * 1e3, "steps": steps,
+        "config": {"workload": f"batched_clips_{len(clips)}", "clips": len(clips), "channel_samples": total,
+                   "chains": "1-8 random stable sections + 33-2049-tap FIR per clip",
+                   "launches": b.launches_per_execute, "cuda_graph": True,
+                   "autotuned": {k: tuned[k] for k in ("fir_nb", "tc_min_taps", "fft_m", "cached")},
+                   "tune_s": tune_s, "plan_s": plan_s,
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "l2": f"{total * 4 / 1e9:.1f} GB in and out per step > 129 MB L2, no flush"},
+        "roofline": roof, "roofline_hbm": hbm, "groups": groups, "cpu_baseline": cpu, "e2e": e2e,
+        "plain_gpu": plain, "parity": parity, "gpu_launches": int(steps * b.launches_per_execute),
+        "clocks": clocks,
+    }
     b.close()
+    del x, y, wsb
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batched_main(args, dev, torch, dist, ws, rank, local):
+    """--workload batched_clips: the many-clip batch is the timed step."""
+    stream = torch.cuda.current_stream(dev)
+    pk = peaks()
+    props = torch.cuda.get_device_properties(dev)
+    fp32 = measure_fp32_peak(dev, stream, torch, props.multi_processor_count, local)
+    r = measure_batched(dev, stream, torch, dist, ws, rank, local, pk, fp32, min(args.steps, 30), args.warmup,
+                        not args.no_e2e, not args.no_plain, not args.no_cpu_baseline, not args.no_cpu_baseline)
+    if rank == 0:
+        out = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": r["steps"],
+               "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": r["config"]}
+        out.update({k: r[k] for k in ("roofline", "roofline_hbm", "groups", "cpu_baseline", "e2e", "plain_gpu",
+                                      "parity", "gpu_launches", "clocks")})
+        out["gpu"] = props.name
+        out["fp32_peak"] = fp32
+        print(json.dumps(out), flush=True)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()

@@ -374,10 +374,16 @@ int tfx_sos_noalloc(const float *x, float *y, int64_t C, int64_t N, int64_t ld,
  * tfx_batch_clip_offset(b, i), and tfx_batch_total_samples(b) floats in all.
  *
  * tfx_batch_create -- validate and plan every clip (host FP64 precompute, as
- * tfx_plan_create) and group the units of all clips by position in their
- * chain and by kernel (fused cascade + short FIR / cascade / tensor-core FIR
- * with NB output blocks per tile); each group then runs as ONE launch over
- * the tiles of all its units.  Allocates device memory (host-synchronous).
+ * tfx_plan_create).  A clip whose chain composes into one FIR (its cascades'
+ * impulse response decays: the composite-response reading of
+ * TFX_PLAN_NO_COMPOSE) runs by FFT overlap-save, and all such clips of one
+ * transform size run as ONE launch (each CTA finds its clip by binary
+ * search and uses the clip's own spectrum).  The units of the other clips
+ * are grouped by position in their chain and by kernel (fused cascade +
+ * short FIR / cascade / tensor-core FIR with NB output blocks per tile);
+ * each group runs as ONE launch over the tiles of all its units.
+ * TFX_PLAN_NO_COMPOSE in plan_flags keeps every clip on the grouped units.
+ * Allocates device memory (host-synchronous).
  * params may be NULL (defaults).  Clips whose tensor-core FIR tables do not
  * fit in shared memory beside a window are TFX_ERR_UNSUPPORTED.
  * tfx_batch_execute -- y = chain_i(x) for every clip; x and y must not
@@ -396,10 +402,16 @@ typedef struct {
 } tfx_clip;
 
 typedef struct {
-    uint32_t plan_flags;   /* TFX_PLAN_* for every clip (TFX_PLAN_DEFAULT, _FIR_CUDA_CORES, _FIR_BF16_*);
-                              long FIRs stay on the tensor cores (_FIR_FFT is rejected) */
+    uint32_t plan_flags;   /* TFX_PLAN_* for every clip (TFX_PLAN_DEFAULT, _NO_COMPOSE, _FIR_CUDA_CORES,
+                              _FIR_BF16_*); long FIRs of clips that do not compose stay on the tensor
+                              cores (_FIR_FFT is rejected) */
     int32_t fir_nb;        /* tensor-core FIR output blocks of 128 per tile: 64, 128 or 256 (0: 128) */
     int32_t tc_min_taps;   /* FIRs with at least this many taps use the tensor cores (0: 64) */
+    int32_t fft_m[16];     /* composed clips whose composite response has Lc taps with
+                              floor(log2(Lc)) = k run with transforms of 2^fft_m[k] points
+                              (10..14; 0, or a size that cannot hold Lc - 1 taps with M/4
+                              outputs per block: the cost model's choice) -- the knob the
+                              autotuner sets per length bucket */
 } tfx_batch_params;
 
 typedef struct tfx_batch tfx_batch;
@@ -416,10 +428,15 @@ int tfx_batch_get_error(tfx_batch *b);
 void tfx_batch_destroy(tfx_batch *b);
 
 /* The batch's launches, for profiling: group g's kind (0 fused cascade +
- * CUDA-core FIR, 1 cascade, 2 tensor-core FIR), its level in the chains, its
+ * CUDA-core FIR, 1 cascade, 2 tensor-core FIR, 3 composed chains by FFT of
+ * one transform size), its level in the chains, its
  * tiles, the channel-samples it filters and its algorithmic flops (10 per
  * section-sample, 2 L per FIR sample); tfx_batch_execute_group runs group g
  * alone (its inputs must hold what the earlier levels write). */
+/* Clip i of a batch: whether it runs as a composed chain (1) or by grouped
+ * units (0), the taps of its composite response and its transform size
+ * exponent (both 0 when not composed). */
+int tfx_batch_clip_info(const tfx_batch *b, int32_t i, int32_t *composed, int32_t *taps, int32_t *fft_m);
 int tfx_batch_group_count(const tfx_batch *b);
 int tfx_batch_group_info(const tfx_batch *b, int32_t g, int32_t *kind, int32_t *level,
                          int64_t *tiles, int64_t *samples, double *flops);

@@ -53,7 +53,7 @@ EXPORTS = [
     "tfx_plan_backward", "tfx_plan_backward_launch_count", "tfx_mse",
     "tfx_batch_create", "tfx_batch_total_samples", "tfx_batch_clip_offset", "tfx_batch_workspace_size",
     "tfx_batch_launch_count", "tfx_batch_execute", "tfx_batch_get_error", "tfx_batch_destroy",
-    "tfx_batch_group_count", "tfx_batch_group_info", "tfx_batch_execute_group",
+    "tfx_batch_group_count", "tfx_batch_group_info", "tfx_batch_execute_group", "tfx_batch_clip_info",
     "tfx_design_sections", "tfx_design_device", "tfx_plan_update_sos", "tfx_plan_sos_rows",
     "tfx_fma_probe", "tfx_fma_probe_flops", "tfx_plan_update_coefs", "tfx_plan_update_coefs_launch_count",
 ]
@@ -84,7 +84,8 @@ DESIGN_KINDS = {"butter_low": 0, "butter_high": 1, "cheby1_low": 2, "peaking": 3
 
 
 class BatchParams(ctypes.Structure):
-    _fields_ = [("plan_flags", ctypes.c_uint32), ("fir_nb", ctypes.c_int32), ("tc_min_taps", ctypes.c_int32)]
+    _fields_ = [("plan_flags", ctypes.c_uint32), ("fir_nb", ctypes.c_int32), ("tc_min_taps", ctypes.c_int32),
+                ("fft_m", ctypes.c_int32 * 16)]
 
 
 _lib = None
@@ -165,6 +166,8 @@ def lib():
     L.tfx_batch_get_error.restype = ctypes.c_int
     L.tfx_batch_destroy.argtypes = [vp]
     L.tfx_batch_destroy.restype = None
+    L.tfx_batch_clip_info.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    L.tfx_batch_clip_info.restype = ctypes.c_int
     L.tfx_batch_group_count.argtypes = [vp]
     L.tfx_batch_group_count.restype = ctypes.c_int
     ip32, ip64 = ctypes.POINTER(i32), ctypes.POINTER(i64)

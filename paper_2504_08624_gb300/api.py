@@ -498,12 +498,13 @@ class Batch:
     """Many clips, each with its own (channels, samples, chain), filtered by a
     few batched launches over one packed input and one packed output buffer
     (``offsets[i]`` = first float of clip i; rows of its own length).
-    ``params``: ``fir_nb`` (tensor-core FIR output blocks of 128 per tile) and
-    ``tc_min_taps`` (tensor cores from this many taps), as picked by
-    ``autotune.tune_batch``."""
+    ``params``: ``fir_nb`` (tensor-core FIR output blocks of 128 per tile),
+    ``tc_min_taps`` (tensor cores from this many taps) and ``fft_m`` ({k: m}:
+    composed clips whose composite response has floor(log2(taps)) = k use
+    transforms of 2^m points), as picked by ``autotune.tune_batch``."""
 
     def __init__(self, clips, fir_nb: int = 128, tc_min_taps: int = 64, flags: int = 0,
-                 device: int | None = None):
+                 device: int | None = None, fft_m: dict | None = None):
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.clips = [(int(C), int(Ns), list(st)) for C, Ns, st in clips]
         self._keep = [N.StageList(st) for _, _, st in self.clips]
@@ -511,7 +512,10 @@ class Batch:
         for i, ((C, Ns, _), sl) in enumerate(zip(self.clips, self._keep)):
             arr[i].C, arr[i].N, arr[i].st, arr[i].nst = C, Ns, sl.arr, sl.n
         prm = N.BatchParams(flags, fir_nb, tc_min_taps)
-        self.params = {"fir_nb": fir_nb, "tc_min_taps": tc_min_taps, "flags": flags}
+        for k, m in (fft_m or {}).items():
+            prm.fft_m[int(k)] = int(m)
+        self.params = {"fir_nb": fir_nb, "tc_min_taps": tc_min_taps, "flags": flags,
+                       "fft_m": {int(k): int(m) for k, m in (fft_m or {}).items()}}
         self._h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             rc = N.lib().tfx_batch_create(ctypes.byref(self._h), arr, len(self.clips), ctypes.byref(prm))
@@ -555,6 +559,13 @@ class Batch:
                                            ctypes.c_void_p(w.data_ptr()), w.numel(), _stream_handle(self.device))
         N.check(rc, "tfx_batch_execute")
         return y
+
+    def clip_info(self, i: int) -> tuple:
+        """(composed, composite taps, transform size exponent) of clip i."""
+        c, t, m = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        N.check(N.lib().tfx_batch_clip_info(self._h, int(i), ctypes.byref(c), ctypes.byref(t), ctypes.byref(m)),
+                "tfx_batch_clip_info")
+        return bool(c.value), int(t.value), int(m.value)
 
     def groups(self) -> list:
         """[(kind, level, tiles, channel-samples, algorithmic flops)] per launch."""

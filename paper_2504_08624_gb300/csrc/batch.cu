@@ -4,12 +4,15 @@
 //
 // The clips are packed into one input and one output buffer (clip i at a
 // fixed offset, rows of its own length).  Each clip gets an ordinary plan
-// (validation, grouping into units, FP64 constants); the batch then groups
-// the units of all clips by position in their chain (level) and by kernel
-// (fused cascade + short FIR, cascade only, tensor-core FIR) and runs every
-// group as ONE launch whose tiles span all of its units: a CTA maps its
-// ticket (or block index) to a unit by binary search over the units' tile
-// prefix sums, so each unit's tiles keep their time-major order.  Buffer
+// (validation, grouping into units, FP64 constants).  Clips whose chain
+// composes into one FIR (the composite impulse response, as for a single
+// chain) run by FFT overlap-save, all clips of one transform size in ONE
+// launch.  The batch groups the other clips' units by position in their
+// chain (level) and by kernel (fused cascade + short FIR, cascade only,
+// tensor-core FIR) and runs every group as ONE launch whose tiles span all of
+// its units.  In either kind of launch a CTA maps its ticket (or block index)
+// to a unit by binary search over the units' tile prefix sums, so each
+// unit's tiles keep their time-major order.  Buffer
 // pointers in the descriptors are offsets into the packed input, the packed
 // output or the workspace, so an execution is pure pointer arithmetic on
 // three base addresses: no allocation, no host synchronisation, capturable
@@ -25,7 +28,7 @@ using namespace tfx;
 
 namespace {
 
-enum GroupKind { G_FUSED = 0, G_CASCADE = 1, G_FIR = 2 };
+enum GroupKind { G_FUSED = 0, G_CASCADE = 1, G_FIR = 2, G_CHAIN_FFT = 3 };
 
 struct Group {
     int level = 0;
@@ -39,6 +42,9 @@ struct Group {
     size_t hdr_off = 0, hdr_bytes = 0;    // workspace: ticket + flags + carries (zeroed per execution)
     std::vector<BatchUnit> units;
     std::vector<BatchFir> firs;
+    std::vector<BatchFft> ffts;
+    int fft_m = 0;                  // composed chains: transform size 2^fft_m
+    const float2* tw = nullptr;     // its twiddle tables (in one of the clips' plans)
     std::vector<int64_t> prefix;
 };
 
@@ -70,12 +76,17 @@ void batch_free(tfx_batch* b) {
 int batch_build(tfx_batch* b, const tfx_clip* clips, int32_t n, const tfx_batch_params& prm) {
     const int NB = prm.fir_nb > 0 ? prm.fir_nb : 128;
     if (NB != 64 && NB != 128 && NB != 256) return TFX_ERR_INVALID;
-    // the batched groups run FIRs on the tensor cores or fused with a cascade:
-    // no FFT units
+    // A clip whose chain composes (its cascades' response decays; see
+    // compose_chain) runs as one FFT FIR of its composite response, batched
+    // with every other composed clip of the same transform size in one
+    // launch.  The other clips' units run on the tensor cores or fused with a
+    // cascade, grouped by level and kernel.
     const uint32_t pflags = prm.plan_flags | TFX_PLAN_FIR_TC | TFX_PLAN_SCAN_LOOKBACK;
     if (pflags & (TFX_PLAN_SCAN_WARP_TILES | TFX_PLAN_TRAINABLE | TFX_PLAN_TEST_DROP_PUBLISH | TFX_PLAN_UNFUSED |
                   TFX_PLAN_FIR_FFT))
         return TFX_ERR_UNSUPPORTED;
+    const bool compose = !(prm.plan_flags & (TFX_PLAN_NO_COMPOSE | TFX_PLAN_FIR_CUDA_CORES |
+                                               TFX_PLAN_FIR_BF16_PLAIN | TFX_PLAN_FIR_BF16_SPLIT));
     b->nclips = n;
     b->plans.assign(n, nullptr);
     b->off.resize(n);
@@ -87,8 +98,16 @@ int batch_build(tfx_batch* b, const tfx_clip* clips, int32_t n, const tfx_batch_
         if (c.C > 0 && c.N > INT64_MAX / c.C) return TFX_ERR_INVALID;
         off += c.C * c.N;
         // the batched cascade kernel carries in FP32: no FP64-carry routing
-        const int rc = plan_create_ex(&b->plans[i], c.C, c.N, c.N > 0 ? c.N : 1, c.st, c.nst, pflags,
-                                      prm.tc_min_taps, false);
+        int rc = TFX_OK;
+        if (compose && c.C > 0 && c.N > 0) {
+            rc = plan_create_ex(&b->plans[i], c.C, c.N, c.N, c.st, c.nst, prm.plan_flags, prm.tc_min_taps, false,
+                                prm.fft_m);
+            if (rc != TFX_OK) return rc;
+            if (b->plans[i]->use_chain) continue;
+            tfx_plan_destroy(b->plans[i]);
+            b->plans[i] = nullptr;
+        }
+        rc = plan_create_ex(&b->plans[i], c.C, c.N, c.N > 0 ? c.N : 1, c.st, c.nst, pflags, prm.tc_min_taps, false);
         if (rc != TFX_OK) return rc;
     }
     b->total = off;
@@ -102,7 +121,7 @@ int batch_build(tfx_batch* b, const tfx_clip* clips, int32_t n, const tfx_batch_
     for (int i = 0; i < n; ++i) {
         const tfx_plan* p = b->plans[i];
         const int nu = (int)p->units.size();
-        if (p->C == 0 || p->N == 0) continue;
+        if (p->C == 0 || p->N == 0 || p->use_chain) continue;
         if (nu == 0) b->identity.push_back(i);
         const int nbuf = nu > 2 ? 2 : (nu == 2 ? 1 : 0);
         for (int k = 0; k < nbuf; ++k) {
@@ -110,9 +129,45 @@ int batch_build(tfx_batch* b, const tfx_clip* clips, int32_t n, const tfx_batch_
             ws = align_up(ws + (size_t)p->C * p->N * sizeof(float));
         }
     }
+    // composed clips: one group per transform size
+    for (int m = 10; m <= 14; ++m) {
+        Group g;
+        g.kind = G_CHAIN_FFT;
+        g.fft_m = m;
+        g.prefix.push_back(0);
+        for (int i = 0; i < n; ++i) {
+            tfx_plan* p = b->plans[i];
+            if (!p->use_chain || p->chain.fft_m != m) continue;
+            const HostUnit& u = p->chain;
+            BatchFft f{};
+            f.x_sel = 0;
+            f.y_sel = 1;
+            f.x_off = b->off[i];
+            f.y_off = b->off[i];
+            f.C = p->C;
+            f.N = p->N;
+            f.L = u.L;
+            f.B = u.fft_B;
+            f.nbpc = (p->N + u.fft_B - 1) / u.fft_B;
+            f.nb = p->C * f.nbpc;
+            f.H = reinterpret_cast<const float2*>(p->dconst + u.off_H);
+            if (!g.tw) g.tw = reinterpret_cast<const float2*>(p->dconst + u.off_tw);
+            g.ffts.push_back(f);
+            g.tiles += (f.nb + 1) / 2;
+            g.prefix.push_back(g.tiles);
+            g.samples += p->C * p->N;
+            const double Mm = (double)(1 << m);
+            g.flops += (10.0 * Mm * m + 6.0 * Mm) / (2.0 * u.fft_B) * (double)(p->C * p->N);
+        }
+        g.nunits = (int)g.ffts.size();
+        if (g.nunits == 0) continue;
+        if (g.tiles > (int64_t)INT32_MAX) return TFX_ERR_UNSUPPORTED;
+        b->groups.push_back(g);
+    }
     int maxlev = 0;
     for (int i = 0; i < n; ++i)
-        if (b->plans[i]->C > 0 && b->plans[i]->N > 0) maxlev = std::max(maxlev, (int)b->plans[i]->units.size());
+        if (b->plans[i]->C > 0 && b->plans[i]->N > 0 && !b->plans[i]->use_chain)
+            maxlev = std::max(maxlev, (int)b->plans[i]->units.size());
     for (int lev = 0; lev < maxlev; ++lev) {
         Group g[3];
         for (int k = 0; k < 3; ++k) {
@@ -126,7 +181,7 @@ int batch_build(tfx_batch* b, const tfx_clip* clips, int32_t n, const tfx_batch_
         for (int i = 0; i < n; ++i) {
             tfx_plan* p = b->plans[i];
             const int nu = (int)p->units.size();
-            if (p->C == 0 || p->N == 0 || lev >= nu) continue;
+            if (p->C == 0 || p->N == 0 || lev >= nu || p->use_chain) continue;
             HostUnit u = p->units[lev];
             // where this unit reads and writes: batch input/output or an intermediate
             const int ib = lev == 0 ? -1 : ((lev - 1) & 1);
@@ -239,10 +294,14 @@ int batch_build(tfx_batch* b, const tfx_clip* clips, int32_t n, const tfx_batch_
 
     // descriptors and prefix sums of every group in one device blob
     size_t blob = 0;
+    auto desc_bytes = [](const Group& gr) {
+        return gr.kind == G_FIR ? gr.firs.size() * sizeof(BatchFir)
+               : gr.kind == G_CHAIN_FFT ? gr.ffts.size() * sizeof(BatchFft)
+                                        : gr.units.size() * sizeof(BatchUnit);
+    };
     for (Group& gr : b->groups) {
         gr.desc_off = blob;
-        blob = align_up(blob + (gr.kind == G_FIR ? gr.firs.size() * sizeof(BatchFir)
-                                                 : gr.units.size() * sizeof(BatchUnit)));
+        blob = align_up(blob + desc_bytes(gr));
         gr.prefix_off = blob;
         blob = align_up(blob + gr.prefix.size() * sizeof(int64_t));
     }
@@ -251,6 +310,8 @@ int batch_build(tfx_batch* b, const tfx_clip* clips, int32_t n, const tfx_batch_
         for (const Group& gr : b->groups) {
             if (gr.kind == G_FIR)
                 std::memcpy(host.data() + gr.desc_off, gr.firs.data(), gr.firs.size() * sizeof(BatchFir));
+            else if (gr.kind == G_CHAIN_FFT)
+                std::memcpy(host.data() + gr.desc_off, gr.ffts.data(), gr.ffts.size() * sizeof(BatchFft));
             else
                 std::memcpy(host.data() + gr.desc_off, gr.units.data(), gr.units.size() * sizeof(BatchUnit));
             std::memcpy(host.data() + gr.prefix_off, gr.prefix.data(), gr.prefix.size() * sizeof(int64_t));
@@ -263,6 +324,11 @@ int batch_build(tfx_batch* b, const tfx_clip* clips, int32_t n, const tfx_batch_
 
 int run_group(tfx_batch* b, const Group& gr, const BatchBases& bases, char* w, cudaStream_t s) {
     const int64_t* prefix = reinterpret_cast<const int64_t*>(b->ddesc + gr.prefix_off);
+    if (gr.kind == G_CHAIN_FFT)
+        return launch_fir_fft_batched(gr.fft_m, reinterpret_cast<const BatchFft*>(b->ddesc + gr.desc_off), prefix,
+                                      gr.nunits, gr.tiles, bases, gr.tw, s) == cudaSuccess
+                   ? TFX_OK
+                   : TFX_ERR_CUDA;
     if (gr.kind == G_FIR)
         return launch_fir_tc_batched(reinterpret_cast<const BatchFir*>(b->ddesc + gr.desc_off), prefix, gr.nunits,
                                      gr.tiles, bases, gr.smem, s) == cudaSuccess
@@ -336,6 +402,15 @@ int tfx_batch_execute(tfx_batch* b, const float* x, float* y, void* ws, size_t w
         const int rc = run_group(b, gr, bases, w, s);
         if (rc != TFX_OK) return rc;
     }
+    return TFX_OK;
+}
+
+int tfx_batch_clip_info(const tfx_batch* b, int32_t i, int32_t* composed, int32_t* taps, int32_t* fft_m) {
+    if (!b || i < 0 || i >= b->nclips || !b->plans[i]) return TFX_ERR_INVALID;
+    const tfx_plan* p = b->plans[i];
+    if (composed) *composed = p->use_chain ? 1 : 0;
+    if (taps) *taps = p->use_chain ? p->chain.L : 0;
+    if (fft_m) *fft_m = p->use_chain ? p->chain.fft_m : 0;
     return TFX_OK;
 }
 

@@ -412,6 +412,49 @@ __global__ void __launch_bounds__((1 << LOGM) / 16, 16384 >> LOGM) k_fir_fft(Fir
     fft_block_pair<LOGM>(a, blockIdx.x, sb, threadIdx.x);
 }
 
+// Single-block overlap-save over many clips in one launch (a batch of
+// composed chains sharing one transform size): CTA k maps to its clip by a
+// binary search over the clips' block-pair prefix sums, then transforms that
+// clip's block pair k - prefix[clip] with the clip's own spectrum.
+template <int LOGM>
+__global__ void __launch_bounds__((1 << LOGM) / 16, 16384 >> LOGM)
+    k_fir_fft_batched(const BatchFft* __restrict__ units, const int64_t* __restrict__ prefix, int nunits,
+                      BatchBases bases, const float2* __restrict__ tw) {
+    extern __shared__ float2 sb[];
+    __shared__ int s_unit;
+    const int t = threadIdx.x;
+    const int64_t k = blockIdx.x;
+    if (t == 0) {
+        int lo = 0, hi = nunits - 1;  // the last unit whose first pair is <= k
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (prefix[mid] <= k) lo = mid;
+            else hi = mid - 1;
+        }
+        s_unit = lo;
+    }
+    __syncthreads();
+    const int u = s_unit;
+    const BatchFft d = units[u];
+    FirFftArgs a{};
+    a.x = bases.ptr(d.x_sel) + d.x_off;
+    a.y = bases.ptr(d.y_sel) + d.y_off;
+    a.ldx = d.N;
+    a.ldy = d.N;
+    a.C = d.C;
+    a.N = d.N;
+    a.L = d.L;
+    a.M = 1 << LOGM;
+    a.m = LOGM;
+    a.B = d.B;
+    a.nbpc = d.nbpc;
+    a.nb = d.nb;
+    a.H = d.H;
+    a.tw = tw;
+    a.P = 0;
+    fft_block_pair<LOGM>(a, k - prefix[u], sb, t);
+}
+
 // Partitioned overlap-save, step 1: the spectrum of segment b of a channel
 // pair, x[(b - 1) B, (b + 1) B) of channels 2r (re) and 2r + 1 (im), stored
 // like H: float4 q of thread t (positions 16t + 2q, 16t + 2q + 1) at q*T + t.
@@ -534,6 +577,8 @@ cudaError_t prepare_log() {
         e = cudaFuncSetAttribute(k_fir_fft_conv<LOGM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_fir_fft_spectrum<LOGM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fir_fft_batched<LOGM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     return e;
 }
 
@@ -548,6 +593,28 @@ cudaError_t prepare_fir_fft(int M) {
         case 4096: return prepare_log<12>();
         case 8192: return prepare_log<13>();
         case 16384: return prepare_log<14>();
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int LOGM>
+cudaError_t launch_batched_log(const BatchFft* units, const int64_t* prefix, int nunits, int64_t ctas,
+                               BatchBases bases, const float2* tw, cudaStream_t s) {
+    constexpr int T = (1 << LOGM) / 16;
+    const size_t smem = fir_fft_smem_bytes(1 << LOGM);
+    k_fir_fft_batched<LOGM><<<(unsigned)ctas, T, smem, s>>>(units, prefix, nunits, bases, tw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fir_fft_batched(int m, const BatchFft* units, const int64_t* prefix, int nunits, int64_t ctas,
+                                   BatchBases bases, const float2* tw, cudaStream_t s) {
+    if (ctas <= 0 || nunits <= 0) return cudaSuccess;
+    switch (m) {
+        case 10: return launch_batched_log<10>(units, prefix, nunits, ctas, bases, tw, s);
+        case 11: return launch_batched_log<11>(units, prefix, nunits, ctas, bases, tw, s);
+        case 12: return launch_batched_log<12>(units, prefix, nunits, ctas, bases, tw, s);
+        case 13: return launch_batched_log<13>(units, prefix, nunits, ctas, bases, tw, s);
+        case 14: return launch_batched_log<14>(units, prefix, nunits, ctas, bases, tw, s);
         default: return cudaErrorInvalidValue;
     }
 }

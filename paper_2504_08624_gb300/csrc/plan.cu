@@ -282,6 +282,24 @@ void host_fft(std::vector<std::complex<double>>& a) {
     }
 }
 
+// Linear convolution a * b by FP64 transforms (zero-padded to a power of
+// two), its first nout values.
+std::vector<double> conv_fft(const std::vector<double>& a, const std::vector<double>& b, size_t nout) {
+    const size_t need = a.size() + b.size() - 1;
+    size_t n = 1;
+    while (n < need) n <<= 1;
+    std::vector<std::complex<double>> fa(n, 0.0), fb(n, 0.0);
+    for (size_t i = 0; i < a.size(); ++i) fa[i] = a[i];
+    for (size_t i = 0; i < b.size(); ++i) fb[i] = b[i];
+    host_fft(fa);
+    host_fft(fb);
+    for (size_t i = 0; i < n; ++i) fa[i] = std::conj(fa[i] * fb[i]);
+    host_fft(fa);  // conj(FFT(conj(X))) / n is the inverse
+    std::vector<double> out(std::min(nout, need));
+    for (size_t i = 0; i < out.size(); ++i) out[i] = fa[i].real() / (double)n;
+    return out;
+}
+
 // Twiddle tables of the overlap-save transform of M = 2^m points: its passes
 // run over spans M, M/G0, ..., 16 (G0 = 2^(m mod 4), or 16), radix G0 first
 // and 16 after; a pass over span S with radix G and sub = S/G > 1 has the
@@ -512,15 +530,15 @@ void compose_chain(tfx_plan* p) {
         sec.insert(sec.end(), u.sec.begin(), u.sec.end());
         S += u.S;
         if (u.L > 0) {
-            std::vector<double> g(f.size() + u.taps.size() - 1, 0.0);
-            for (size_t i = 0; i < f.size(); ++i)
-                for (size_t k = 0; k < u.taps.size(); ++k) g[i + k] += f[i] * u.taps[k];
-            f.swap(g);
+            f = conv_fft(f, u.taps, f.size() + u.taps.size() - 1);
             maxL = std::max(maxL, u.L);
         }
-        separate += unit_cost_estimate(u);
+        // a cascade-only unit of <= 8 sections would run on the tensor cores by segments
+        HostUnit e = u;
+        e.seg = u.S > 0 && u.S <= SEG_SMAX && u.L == 0 && !u.warp;
+        separate += unit_cost_estimate(e);
     }
-    if (S == 0 || maxL < FFT_MIN_TAPS) return;
+    if (S == 0 || maxL == 0) return;  // a chain of cascades and at least one FIR
     const int W = 65536, HEAD = 16384;
     std::vector<double> g(W);
     std::vector<double> w1(S, 0.0), w2(S, 0.0);
@@ -545,10 +563,8 @@ void compose_chain(tfx_plan* p) {
     double f1 = 0.0, n2 = 0.0;
     for (double v : f) f1 += std::fabs(v);
     {
-        std::vector<double> hc(HEAD, 0.0);
-        for (int i = 0; i < HEAD; ++i)
-            for (int k = 0; k < Lf && i + k < HEAD; ++k) hc[i + k] += g[i] * f[k];
-        for (double v : hc) n2 += v * v;
+        const std::vector<double> head(g.begin(), g.begin() + HEAD);
+        for (double v : conv_fft(head, f, HEAD)) n2 += v * v;
         n2 = std::sqrt(n2);
     }
     if (!(n2 > 0.0)) return;
@@ -572,12 +588,19 @@ void compose_chain(tfx_plan* p) {
         const double c = fft_single_cost(m, (int)Lc);
         if (c > 0.0 && (bestm == 0 || c < best)) bestm = m, best = c;
     }
-    if (bestm == 0 || !(best < separate)) return;
+    // a transform size set for this length bucket (the batch autotuner's
+    // choice) where it holds the response with M/4 outputs per block
+    int lg = 0;
+    while (lg < 15 && (int64_t(2) << lg) <= Lc) ++lg;
+    const int om = p->compose_m[lg];
+    if (om >= 10 && om <= 14 && Lc - 1 <= (1 << om) - (1 << om) / 4) {
+        bestm = om;
+    } else if (bestm == 0 || !(best < separate)) {
+        return;
+    }
     HostUnit c;
     c.L = (int)Lc;
-    c.taps.assign((size_t)Lc, 0.0);
-    for (int i = 0; i < D; ++i)
-        for (int k = 0; k < Lf; ++k) c.taps[(size_t)i + k] += g[i] * f[k];
+    c.taps = conv_fft(std::vector<double>(g.begin(), g.begin() + D), f, (size_t)Lc);
     c.fft = true;
     c.fft_m = bestm;
     c.fft_M = 1 << bestm;
@@ -746,16 +769,6 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
     for (HostUnit& u : p->units)
         u.warp = (u.S > 0 && u.L == 0) && ((p->flags & TFX_PLAN_SCAN_WARP_TILES) || p->train || u.hiq);
 
-    // cascade-only block-tile units by channel segments where the free
-    // response decays early enough
-    if (!(p->flags & (TFX_PLAN_SCAN_LOOKBACK | TFX_PLAN_TEST_DROP_PUBLISH)) && p->C > 0 && p->N > 0) {
-        int sm_count = 152, dev = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess)
-            cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
-        for (HostUnit& u : p->units)
-            if (u.S > 0 && u.S <= SEG_SMAX && u.L == 0 && !u.warp && !u.hiq) choose_segments(p, u, sm_count);
-    }
-
     // the whole chain as one FFT FIR of its composite response
     p->use_chain = false;
     if (!(p->flags & (TFX_PLAN_NO_COMPOSE | TFX_PLAN_FIR_CUDA_CORES | TFX_PLAN_UNFUSED | TFX_PLAN_FIR_BF16_PLAIN |
@@ -763,6 +776,17 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
                       TFX_PLAN_TEST_DROP_PUBLISH | TFX_PLAN_FIR_FFT_LOG_MASK)) &&
         !p->train && p->C > 0 && p->N > 0)
         compose_chain(p);
+
+    // cascade-only block-tile units by channel segments where the free
+    // response decays early enough (not needed when the chain is composed:
+    // after a coefficient update its units run the look-back scan)
+    if (!(p->flags & (TFX_PLAN_SCAN_LOOKBACK | TFX_PLAN_TEST_DROP_PUBLISH)) && p->C > 0 && p->N > 0 && !p->use_chain) {
+        int sm_count = 152, dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess)
+            cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
+        for (HostUnit& u : p->units)
+            if (u.S > 0 && u.S <= SEG_SMAX && u.L == 0 && !u.warp && !u.hiq) choose_segments(p, u, sm_count);
+    }
 
     // constant blob layout
     size_t off = 0;
@@ -1471,7 +1495,7 @@ int tfx_plan_create(tfx_plan** out, int64_t C, int64_t N, int64_t ld, const tfx_
 }  // extern "C"
 
 int tfx::plan_create_ex(tfx_plan** out, int64_t C, int64_t N, int64_t ld, const tfx_stage* st, int32_t nst,
-                        uint32_t flags, int tc_min_taps, bool allow_hiq) {
+                        uint32_t flags, int tc_min_taps, bool allow_hiq, const int32_t* compose_m) {
     if (!out) return TFX_ERR_INVALID;
     *out = nullptr;
     int rc = check_dims(C, N, ld);
@@ -1491,6 +1515,7 @@ int tfx::plan_create_ex(tfx_plan** out, int64_t C, int64_t N, int64_t ld, const 
     p->flags = flags;
     p->tc_min_taps = tc_min_taps > 0 ? tc_min_taps : TC_MIN_TAPS;
     p->allow_hiq = allow_hiq;
+    if (compose_m) std::copy(compose_m, compose_m + 16, p->compose_m);
     rc = build_plan(p, st, nst, true);
     if (rc != TFX_OK) {
         tfx_plan_destroy(p);

@@ -113,6 +113,7 @@ struct tfx_plan {
     // (chain_fft); the separate units above stay built for after a
     // coefficient update
     bool use_chain = false;
+    int32_t compose_m[16] = {};  // transform size exponent per floor(log2(Lc)) (0: cost model)
     tfx::HostUnit chain;
     int chain_S = 0, chain_L = 0, chain_D = 0;  // sections, combined FIR length, cascade response length
 };
@@ -122,7 +123,7 @@ namespace tfx {
 void tc_geometry(HostUnit& u, int NB);
 // Create a plan with a tensor-core tap threshold other than the default.
 int plan_create_ex(tfx_plan** out, int64_t C, int64_t N, int64_t ld, const tfx_stage* st, int32_t nst,
-                   uint32_t flags, int tc_min_taps, bool allow_hiq = true);
+                   uint32_t flags, int tc_min_taps, bool allow_hiq = true, const int32_t* compose_m = nullptr);
 // Pole radius above which a cascade's cross-tile carries run in FP64.
 constexpr double HIQ_RADIUS = 0.999;
 // Recompute the plan's section constants on the GPU from raw FP64 rows (design.cu).

@@ -193,6 +193,17 @@ struct FirFftArgs {
     float2* Z;         // partitioned: [ceil(C/2)][nbpc][M] segment spectra (workspace)
 };
 
+// One composed clip of a batch (the whole chain as one FFT FIR): where its
+// samples are, its shape and block geometry, its spectrum.
+struct BatchFft {
+    int x_sel, y_sel;
+    int64_t x_off, y_off;  // in floats
+    int64_t C, N;
+    int L, B;
+    int64_t nbpc, nb;
+    const float2* H;
+};
+
 struct BatchFir {
     FirTcArgs a;           // x and y filled in from the offsets below
     int x_sel, y_sel;
@@ -367,6 +378,8 @@ cudaError_t launch_fir_tc(const FirTcArgs& a, cudaStream_t s);
 size_t fir_fft_smem_bytes(int M);
 cudaError_t prepare_fir_fft(int M);
 cudaError_t launch_fir_fft(const FirFftArgs& a, cudaStream_t s);
+cudaError_t launch_fir_fft_batched(int m, const BatchFft* units, const int64_t* prefix, int nunits, int64_t ctas,
+                                   BatchBases bases, const float2* tw, cudaStream_t s);
 cudaError_t launch_fir_fft_spectrum(const double* taps, int L, int M, int B, int P, const float2* tw, float2* H,
                                     cudaStream_t s);
 cudaError_t launch_fir_tc_batched(const BatchFir* units, const int64_t* prefix, int nunits, int64_t tiles,

@@ -85,8 +85,8 @@ def check_clip(got, xi, st, what):
     return rel, rel_plain
 
 
-@pytest.mark.parametrize("params", [{}, {"fir_nb": 64}, {"fir_nb": 256, "tc_min_taps": 128},
-                                    {"tc_min_taps": 32}])
+@pytest.mark.parametrize("params", [{}, {"fir_nb": 64, "flags": 1024}, {"fir_nb": 256, "tc_min_taps": 128, "flags": 1024},
+                                    {"tc_min_taps": 32, "flags": 1024}, {"fft_m": {9: 13, 10: 14}}])
 def test_batch_matches_oracle(params):
     clips = small_clips()
     from paper_2504_08624_gb300 import api
@@ -123,9 +123,11 @@ def test_batch_graph_capture_and_launch_count():
 
 
 def test_batch_argument_errors():
-    from paper_2504_08624_gb300 import api
+    from paper_2504_08624_gb300 import api, _native as N_
     clips = small_clips()[:3]
-    b = api.Batch(clips)
+    # grouped units (composed clips need no workspace)
+    b = api.Batch(clips, flags=N_.TFX_PLAN_NO_COMPOSE)
+    assert b.workspace_size > 0
     x = b.empty()
     with pytest.raises(api.TfxError):  # in place is not allowed for batches
         b.execute(x, x)
@@ -137,19 +139,33 @@ def test_batch_argument_errors():
 
 
 def test_autotuner_picks_and_caches(tmp_path):
+    """Composed clips are tuned per composite-length bucket (transform size),
+    the clips that keep their units as one group (tile width, tap threshold);
+    a second call finds everything in the cache, and a batch built with the
+    tuned parameters still matches the oracle."""
     from paper_2504_08624_gb300 import api, autotune
     clips = small_clips()[:10]
-    b = api.Batch(clips)
-    x = b.pack([torch.from_numpy(W.white_uniform(C, Ns, i)) for i, (C, Ns, _) in enumerate(clips)])
-    b.close()
+    # a clip whose cascade does not decay within the composition window (a
+    # pole at radius 0.99999) keeps its units, with a FIR on the tensor cores
+    r, th = 0.99999, 0.3
+    slow = np.array([[1e-3, 0.0, -1e-3, 1.0, -2 * r * np.cos(th), r * r]])
+    clips.append((2, 30000, [("sos", slow), ("fir", W.fir_lowpass(257, 9000.0, W.FS))]))
     path = str(tmp_path / "tune.json")
     cands = [{"fir_nb": 64, "tc_min_taps": 64}, {"fir_nb": 128, "tc_min_taps": 64}]
-    r1 = autotune.tune_batch(clips, x, cache_path=path, reps=2, candidates=cands)
-    assert not r1["cached"] and len(r1["tried"]) == 2
+    r1 = autotune.tune_batch(clips, cache_path=path, reps=2, candidates=cands)
+    assert not r1["cached"] and r1["tried"]
     assert {"fir_nb": r1["fir_nb"], "tc_min_taps": r1["tc_min_taps"]} in cands
-    r2 = autotune.tune_batch(clips, x, cache_path=path, reps=2, candidates=cands)
-    assert r2["cached"] and r2["fir_nb"] == r1["fir_nb"]
-    assert len(json.load(open(path))) == 1
+    assert all(m in autotune.FFT_SIZES for m in r1["fft_m"].values())
+    r2 = autotune.tune_batch(clips, cache_path=path, reps=2, candidates=cands)
+    assert r2["cached"] and r2["fir_nb"] == r1["fir_nb"] and r2["fft_m"] == r1["fft_m"]
+    b, xs, x, y = run_batch(clips, fir_nb=r1["fir_nb"], tc_min_taps=r1["tc_min_taps"], fft_m=r1["fft_m"])
+    composed = [b.clip_info(i)[0] for i in range(len(clips))]
+    assert any(composed) and not composed[-1]
+    for i, ((C, Ns, st), xi) in enumerate(zip(clips, xs)):
+        if C == 0 or Ns == 0:
+            continue
+        check_clip(b.view(y, i).cpu().numpy().astype(np.float64), xi, st, f"tuned clip {i}")
+    b.close()
 
 
 def test_batched_clips_workload_sampled():

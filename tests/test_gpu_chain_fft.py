@@ -114,13 +114,16 @@ def test_random_chains_with_long_firs(seed):
 
 
 def test_stays_separate_where_it_must():
-    """Short FIRs stay fused with the cascade on the CUDA cores; a pole beyond
-    0.999 keeps the FP64-carry scan; FIR-only and cascade-only chains have
-    nothing to compose; the flag keeps the units."""
+    """A pole beyond 0.999 keeps the FP64-carry scan; FIR-only and
+    cascade-only chains have nothing to compose; the flag keeps the units
+    (a cascade with a short FIR then stays fused on the CUDA cores; by
+    default that chain is composed too)."""
     from paper_2504_08624_gb300 import _native as N_
     x = W.white_uniform(2, 40_000, 720)
-    check(x, [("sos", W.butter_sos(4, 1000.0, W.FS)), ("fir", W.fir_lowpass(31, 9000.0, W.FS))],
-          expect_chain=False)
+    short = [("sos", W.butter_sos(4, 1000.0, W.FS)), ("fir", W.fir_lowpass(31, 9000.0, W.FS))]
+    check(x, short, expect_chain=True)
+    _, d = check(x, short, expect_chain=False, flags=N_.TFX_PLAN_NO_COMPOSE)
+    assert [u["kind"] for u in d] == ["fused"]
     r, th = 0.9995, 0.3
     hi = np.array([[1e-3, 0.0, -1e-3, 1.0, -2 * r * np.cos(th), r * r]])
     check(x, [("sos", hi), ("fir", W.fir_lowpass(513, 9000.0, W.FS))], expect_chain=False)

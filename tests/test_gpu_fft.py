@@ -226,7 +226,8 @@ def test_plan_describe_routes():
     assert [u["kind"] for u in d] == ["cascade", "fir_tc"] and d[1]["kernel"].startswith("k_fir_tc")
     d = api.Plan(2, 100000, W.long_fir().stages).describe()
     assert d[0]["kind"] == "fir_fft" and d[0]["P"] == -(-16384 // (d[0]["M"] // 2))
-    d = api.Plan(2, 100000, [("sos", W.butter_sos(4, 1000.0, W.FS)), ("fir", _taps(31, 1))]).describe()
+    d = api.Plan(2, 100000, [("sos", W.butter_sos(4, 1000.0, W.FS)), ("fir", _taps(31, 1))],
+                 flags=N_.TFX_PLAN_NO_COMPOSE).describe()
     assert [u["kind"] for u in d] == ["fused"]
     # the FFT route is the default from 64 taps; shorter FIRs stay on the CUDA cores
     assert api.Plan(2, 100000, [("fir", _taps(64, 2))]).describe()[0]["kind"] == "fir_fft"

@@ -23,7 +23,10 @@ TILE = 112 * 128
 
 
 def _run(x, stages, flags=0, inplace=False, ld=None):
-    from paper_2504_08624_gb300 import api
+    """Through a plan that keeps its units (the tensor-core cascade is what
+    these tests check, not the composed chain)."""
+    from paper_2504_08624_gb300 import api, _native as N_
+    flags |= N_.TFX_PLAN_NO_COMPOSE
     C, Ns = x.shape
     ld = Ns if ld is None else ld
     buf = torch.zeros(C * ld + 8, dtype=torch.float32, device="cuda")
