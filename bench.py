@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--flags", type=int, default=0, help="TFX_PLAN_* bits for the timed plan")
     ap.add_argument("--channels", type=int, default=None, help="override channel count (testing only)")
     ap.add_argument("--samples", type=int, default=None, help="override samples per channel (testing only)")
+    ap.add_argument("--clips", type=int, default=None, help="only the first K clips of the batched workload "
+                                                             "(profiling only)")
     ap.add_argument("--workload", default="multichannel_fused",
                     choices=["multichannel_fused", "plain_chain", "long_fir", "table4_chain", "differentiable_chain",
                              "batched_clips"],
@@ -892,13 +894,15 @@ def main():
 
 
 def measure_batched(dev, stream, torch, dist, ws, rank, local, pk, fp32, steps, warmup, with_e2e=True,
-                    with_plain=True, with_cpu=True, with_parity=True) -> dict:
+                    with_plain=True, with_cpu=True, with_parity=True, nclips=None) -> dict:
     """The many-clip workload: 1000 clips, each its own length, channel count
     and chain, filtered by the batched launches (composed chains by FFT, one
     launch per transform size; the other clips' units grouped by level and
     kernel) replayed from one CUDA graph, with the autotuned parameters."""
     from paper_2504_08624_gb300 import api, autotune, workloads as W
     clips = W.batched_clips()
+    if nclips:
+        clips = clips[:nclips]
     spec = [(c.C, c.N, c.stages) for c in clips]
     total = sum(C * Ns for C, Ns, _ in spec)
     gen = torch.Generator(device=dev).manual_seed(5)
@@ -916,7 +920,7 @@ def measure_batched(dev, stream, torch, dist, ws, rank, local, pk, fp32, steps, 
     if with_parity and rank == 0:
         # a sample of clips with their seeded signals against the oracle
         import oracle
-        sample = [0, 17, 333, 998]
+        sample = [i for i in (0, 17, 333, 998) if i < len(clips)]
         xp = x.clone()
         for i in sample:
             b.view(xp, i).copy_(torch.from_numpy(clips[i].make_signal()))
@@ -1059,7 +1063,8 @@ def run_batched_main(args, dev, torch, dist, ws, rank, local):
     props = torch.cuda.get_device_properties(dev)
     fp32 = measure_fp32_peak(dev, stream, torch, props.multi_processor_count, local)
     r = measure_batched(dev, stream, torch, dist, ws, rank, local, pk, fp32, min(args.steps, 30), args.warmup,
-                        not args.no_e2e, not args.no_plain, not args.no_cpu_baseline, not args.no_cpu_baseline)
+                        not args.no_e2e, not args.no_plain, not args.no_cpu_baseline, not args.no_cpu_baseline,
+                        nclips=args.clips)
     if rank == 0:
         out = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": r["steps"],
                "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
