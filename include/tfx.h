@@ -54,7 +54,9 @@ typedef enum {
     TFX_ERR_CUDA = -4,        /* a CUDA runtime call failed */
     TFX_ERR_TIMEOUT = -5,     /* a device-side bounded wait gave up (see tfx_plan_get_error) */
     TFX_ERR_UNSUPPORTED = -6, /* valid request outside what this build implements */
-    TFX_ERR_NOMEM = -7        /* host or device allocation failed */
+    TFX_ERR_NOMEM = -7,       /* host or device allocation failed */
+    TFX_ERR_DECAY = -8        /* after a coefficient update, a spectral training plan's chain
+                                 response no longer decays within its transform's overlap */
 } tfx_status;
 
 typedef enum { TFX_STAGE_FIR = 0, TFX_STAGE_SOS = 1 } tfx_stage_kind;

@@ -40,6 +40,7 @@ TFX_PLAN_NO_COMPOSE = 1024
 STATUS = {
     0: "TFX_OK", -1: "TFX_ERR_INVALID", -2: "TFX_ERR_UNSTABLE", -3: "TFX_ERR_WORKSPACE",
     -4: "TFX_ERR_CUDA", -5: "TFX_ERR_TIMEOUT", -6: "TFX_ERR_UNSUPPORTED", -7: "TFX_ERR_NOMEM",
+    -8: "TFX_ERR_DECAY",
 }
 
 # every symbol include/tfx.h declares

@@ -217,6 +217,11 @@ class Plan:
     def coef_count(self) -> int:
         return int(N.lib().tfx_plan_coef_count(self._h))
 
+    @property
+    def update_launches(self) -> int:
+        """Kernels one update_coefs call launches (-1: the plan cannot be updated)."""
+        return int(N.lib().tfx_plan_update_coefs_launch_count(self._h))
+
     def backward_launches(self, with_dx: bool = True, with_dcoef: bool = True) -> int:
         return int(N.lib().tfx_plan_backward_launch_count(self._h, int(with_dx), int(with_dcoef)))
 

@@ -382,10 +382,30 @@ int build_update_descriptors(tfx_plan* p) {
 
 // Coefficients derived on the host (the tensor-core cascade's GEMM tables,
 // a composed chain's spectrum) go stale with an update: such units run the
-// look-back scan, and the chain its separate units, from now on.
+// look-back scan, and the chain its separate units, from now on.  A spectral
+// plan's chain spectrum is recomputed on the device instead.
 void drop_host_derived(tfx_plan* p) {
     for (HostUnit& u : p->units) u.seg = false;
-    p->use_chain = false;
+    if (!p->spectral) p->use_chain = false;
+}
+
+// A spectral plan after its sections (and FIR taps) changed: the FIR's
+// spectrum at the chain's transform size from the new taps (coef, when
+// given), the chain's spectrum from the new raw rows, and the decay check of
+// the response against the overlap.
+int refresh_spectral(tfx_plan* p, const double* coef, cudaStream_t s) {
+    HostUnit& h = p->spec_fir;
+    const float2* tw = reinterpret_cast<const float2*>(p->dconst + h.off_tw);
+    float2* Hf = reinterpret_cast<float2*>(p->dconst + h.off_H);
+    float2* H = reinterpret_cast<float2*>(p->dconst + p->chain.off_H);
+    if (coef && p->spec_nfir &&
+        launch_fir_fft_spectrum(coef + p->spec_fir_dst, h.L, h.fft_M, h.fft_B, 0, tw, Hf, s) != cudaSuccess)
+        return TFX_ERR_CUDA;
+    if (launch_chain_spectrum(reinterpret_cast<const double*>(p->dconst + p->off_spec_raw), p->chain_S, Hf,
+                              p->chain.fft_m, H, s) != cudaSuccess)
+        return TFX_ERR_CUDA;
+    if (launch_chain_tail(p->chain.fft_m, H, tw, p->chain.L - 1, p->dstatus, s) != cudaSuccess) return TFX_ERR_CUDA;
+    return TFX_OK;
 }
 
 }  // namespace
@@ -397,7 +417,8 @@ int tfx::plan_update_sections(tfx_plan* p, const double* rows_dev, cudaStream_t 
     if (p->nsec <= 0) return TFX_OK;
     k_update_sections<<<(unsigned)p->nsec, 256, 0, s>>>(reinterpret_cast<const SecUpdate*>(p->dsec), rows_dev, 0,
                                                          p->dstatus);
-    return cudaGetLastError() == cudaSuccess ? TFX_OK : TFX_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return TFX_ERR_CUDA;
+    return p->spectral ? refresh_spectral(p, nullptr, s) : TFX_OK;
 }
 
 extern "C" int tfx_plan_update_sos(tfx_plan* p, const double* rows, tfx_stream s) {
@@ -427,6 +448,7 @@ extern "C" int tfx_plan_update_coefs(tfx_plan* p, const double* coef, tfx_stream
             reinterpret_cast<const FirUpdate*>(p->dsec + (size_t)p->nsec * sizeof(SecUpdate)), coef);
         if (cudaGetLastError() != cudaSuccess) return TFX_ERR_CUDA;
     }
+    if (p->spectral) return refresh_spectral(p, coef, s);  // the units do not run
     for (const HostUnit& u : p->units) {
         if (!u.fft) continue;
         if (launch_fir_fft_spectrum(coef + u.fir_dst, u.L, u.fft_M, u.fft_B, u.fft_P,
@@ -448,6 +470,7 @@ extern "C" int tfx_plan_update_coefs_launch_count(const tfx_plan* p) {
     }
     bool fir = false;
     for (const HostUnit& u : p->units) fir = fir || u.L > 0;
+    if (p->spectral) n = (p->spec_nfir ? 1 : 0) + 2;  // FIR spectrum, chain spectrum, decay check
     return (S > 0 ? 1 : 0) + (fir ? 1 : 0) + n;
 }
 

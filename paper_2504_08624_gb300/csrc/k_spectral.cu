@@ -1,0 +1,392 @@
+// Training kernels for chains run by their composite response (the spectral
+// route of a trainable plan).  The chain is one linear time-invariant filter
+// with impulse response h (TorchFX Sec. 3: the pipe composes the stages), so
+// for L = sum_c sum_n g[c][n] y[c][n] and every coefficient theta:
+//     dL/dtheta = sum_(j >= 0) (dh/dtheta)[j] r[j],
+//     r[j]      = sum_c sum_n g[c][n] x[c][n - j]     (cross-correlation of the
+//                                                      upstream gradient and
+//                                                      the input, lags >= 0)
+// and dL/dx is the chain applied to g in reverse time.  r is accumulated in
+// the frequency domain by blocks: block b of a channel pair takes the
+// gradient samples [bB, bB + B) at positions [J, M) of an M-point sequence
+// (zeros before) and the input window [bB - J, bB + B); the circular
+// correlation of the two equals the block's share of r at lags 0..J.  With
+// two channels as the real and imaginary parts of each sequence,
+// Zg conj(Zx) = S + i T where S (the wanted sum over both channels) and T are
+// both spectra of real sequences, so S = (P + conj(P mirrored)) / 2 once P is
+// summed over every block.  The gradients are then inner products with the
+// derivative spectra, taken from the sections' coefficients in closed form at
+// each bin (FP64): for section s with A_s = 1 + a1 z + a2 z^2 and
+// B_s = b0 + b1 z + b2 z^2 (a0-normalised, z = e^(-i w)), H = prod_s B_s/A_s
+// times the FIR's spectrum F,
+//     dH/db_k = z^k F prod_(j != s) H_j / A_s,   dH/da_k = -z^k H / A_s,
+// and for the FIR taps dL/dh_k is the inverse transform of conj(prod_s H_s) S
+// at sample k.  The derivative responses decay with the chain's poles, so
+// lags beyond J (where the circular correlation is not r) meet only their
+// negligible tails.
+#include "fft_core.cuh"
+
+namespace tfx {
+namespace {
+
+constexpr double TWO_PI = 6.283185307179586476925286766559;
+
+// Storage index i of the spectra (float4 q of thread t, halves e: i = 2(qT + t)
+// + e) <-> transform position k = 16t + 2q + e (the forward transform's output
+// slot), whose frequency bin is bitrev_m(k).
+__device__ __forceinline__ int pos_of_storage(int i, int T) {
+    const int e = i & 1, q = (i >> 1) / T, t = (i >> 1) % T;
+    return 16 * t + 2 * q + e;
+}
+__device__ __forceinline__ int storage_of_pos(int k, int T) {
+    const int t = k >> 4, q = (k & 15) >> 1, e = k & 1;
+    return 2 * (q * T + t) + e;
+}
+__device__ __forceinline__ int bitrev_bits(int k, int m) { return (int)(__brev((unsigned)k) >> (32 - m)); }
+
+struct dcplx {
+    double re, im;
+};
+__device__ __forceinline__ dcplx dmul(dcplx a, dcplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__device__ __forceinline__ dcplx ddiv(dcplx a, dcplx b) {
+    const double d = b.re * b.re + b.im * b.im;
+    return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+}
+
+// Section s's numerator and denominator at z (raw row: the a0 cancels in the
+// ratio; the derivative formulas take the normalised coefficients).
+__device__ __forceinline__ void section_at(const double* r, dcplx z1, dcplx z2, dcplx& Bn, dcplx& An) {
+    const double inv = 1.0 / r[3];
+    Bn = {r[0] * inv + r[1] * inv * z1.re + r[2] * inv * z2.re, r[1] * inv * z1.im + r[2] * inv * z2.im};
+    An = {1.0 + r[4] * inv * z1.re + r[5] * inv * z2.re, r[4] * inv * z1.im + r[5] * inv * z2.im};
+}
+
+// Block correlation spectra, accumulated per CTA over its (channel pair,
+// block) items and written as one M-point partial in storage layout.
+template <int LOGM>
+__global__ void __launch_bounds__((1 << LOGM) / 16, LOGM <= 12 ? 2 : 1) k_chain_xcorr(XcorrArgs a) {
+    using F = FftShape<LOGM>;
+    extern __shared__ float2 sb[];
+    float2* zx = sb + (F::M + F::M / 16);  // the input window's spectrum, each thread its own slots
+    const int t = threadIdx.x;
+    float2 acc[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[j] = make_float2(0.f, 0.f);
+    for (int64_t it = blockIdx.x; it < a.items; it += gridDim.x) {
+        const int64_t r = it / a.nbpc, b = it % a.nbpc;
+        const int64_t c0 = 2 * r;
+        const bool live1 = c0 + 1 < a.C;
+        const int64_t n0 = b * (int64_t)a.B;
+        float2 v[16];
+        __syncthreads();  // the previous transform's exchanges are done with sb
+        load_pair<LOGM>(v, a.x + c0 * a.ldx, a.x + (live1 ? c0 + 1 : c0) * a.ldx, live1, n0 - a.J, n0 - a.J, a.N, t);
+        forward_from<LOGM, 0>(v, a.tw, sb, t);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) zx[j * F::T + t] = v[j];
+        // gradient samples n0 + (p - J) at positions p >= J, zeros before
+        const float* g0 = a.g + c0 * a.ldg;
+        const float* g1 = a.g + (live1 ? c0 + 1 : c0) * a.ldg;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int p = t + F::T * j;
+            const int64_t n = n0 + p - a.J;
+            const bool in = p >= a.J && n < a.N;
+            v[j] = make_float2(in ? __ldg(g0 + n) : 0.f, (in && live1) ? __ldg(g1 + n) : 0.f);
+        }
+        __syncthreads();
+        forward_from<LOGM, 0>(v, a.tw, sb, t);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const float2 w = zx[j * F::T + t];
+            acc[j].x = fmaf(v[j].x, w.x, fmaf(v[j].y, w.y, acc[j].x));
+            acc[j].y = fmaf(v[j].y, w.x, fmaf(-v[j].x, w.y, acc[j].y));
+        }
+    }
+    float4* out = reinterpret_cast<float4*>(a.part + (int64_t)blockIdx.x * F::M) + t;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) out[q * F::T] = make_float4(acc[2 * q].x, acc[2 * q].y, acc[2 * q + 1].x, acc[2 * q + 1].y);
+}
+
+// P = sum of the CTAs' partials, in FP64 (storage layout).
+__global__ void k_xcorr_reduce(const float2* __restrict__ part, int G, int M, double2* __restrict__ P) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    double re = 0.0, im = 0.0;
+    for (int g = 0; g < G; ++g) {
+        const float2 v = part[(int64_t)g * M + i];
+        re += v.x;
+        im += v.y;
+    }
+    P[i] = make_double2(re, im);
+}
+
+// Composite spectrum in the filter's layout (storage index i, 1/M folded
+// in): the FIR's spectrum Hf (already scaled) times prod_s B_s / A_s at the
+// bin of i, in FP64.
+__global__ void k_chain_spectrum(const double* __restrict__ raw, int S, const float2* __restrict__ Hf, int m,
+                                 float2* __restrict__ H) {
+    const int M = 1 << m, T = M / 16;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const int bin = bitrev_bits(pos_of_storage(i, T), m);
+    double sn, cs;
+    sincos(-TWO_PI * (double)bin / (double)M, &sn, &cs);
+    const dcplx z1 = {cs, sn}, z2 = dmul(z1, z1);
+    dcplx h = {(double)Hf[i].x, (double)Hf[i].y};
+    for (int s = 0; s < S; ++s) {
+        dcplx Bn, An;
+        section_at(raw + 6 * s, z1, z2, Bn, An);
+        h = dmul(h, ddiv(Bn, An));
+    }
+    H[i] = make_float2((float)h.re, (float)h.im);
+}
+
+// Section coefficient gradients (a0-normalised b0 b1 b2 a1 a2 per section):
+// one bin per thread, FP64.  Each block writes its sums to bpart[block][5 S];
+// the last block to finish (counted on *done, zero on entry and reset by
+// that block) adds them in block order into sums[5 S], so the result does
+// not depend on the blocks' timing.  With wfir set, also conj(C) S at each
+// bin (C = prod_s H_s, the cascades' spectrum) for the FIR tap gradients, in
+// storage layout.
+__global__ void __launch_bounds__(128) k_chain_grads_sec(const double2* __restrict__ P, const double* __restrict__ raw,
+                                                         int S, const float2* __restrict__ Hf, int m,
+                                                         double* __restrict__ bpart, unsigned* __restrict__ done,
+                                                         double* __restrict__ sums, float2* __restrict__ wfir) {
+    __shared__ double red[5 * SPEC_SMAX][4];
+    __shared__ bool last;
+    const int M = 1 << m, T = M / 16;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc[5 * SPEC_SMAX];
+#pragma unroll
+    for (int q = 0; q < 5 * SPEC_SMAX; ++q) acc[q] = 0.0;
+    if (i < M) {
+        const int bin = bitrev_bits(pos_of_storage(i, T), m);
+        const int mir = (M - bin) & (M - 1);
+        const double2 p = P[i], pm = P[storage_of_pos(bitrev_bits(mir, m), T)];
+        const dcplx Sv = {0.5 * (p.x + pm.x), 0.5 * (p.y - pm.y)};
+        double sn, cs;
+        sincos(-TWO_PI * (double)bin / (double)M, &sn, &cs);
+        const dcplx z1 = {cs, sn}, z2 = dmul(z1, z1);
+        const dcplx F = {(double)Hf[i].x * M, (double)Hf[i].y * M};
+        dcplx Hs[SPEC_SMAX], As[SPEC_SMAX];
+        for (int s = 0; s < S; ++s) {
+            dcplx Bn;
+            section_at(raw + 6 * s, z1, z2, Bn, As[s]);
+            Hs[s] = ddiv(Bn, As[s]);
+        }
+        // prefix products of the sections, then a suffix sweep
+        dcplx pre[SPEC_SMAX];
+        dcplx run = {1.0, 0.0};
+        for (int s = 0; s < S; ++s) {
+            pre[s] = run;
+            run = dmul(run, Hs[s]);
+        }
+        const dcplx Cs = run, Ht = dmul(F, Cs);
+        if (wfir) {
+            const dcplx w = dmul({Cs.re, -Cs.im}, Sv);
+            wfir[i] = make_float2((float)w.re, (float)w.im);
+        }
+        dcplx suf = {1.0, 0.0};
+        for (int s = S - 1; s >= 0; --s) {
+            const dcplx oth = dmul(F, dmul(pre[s], suf));  // F prod_(j != s) H_j
+            const dcplx q0 = ddiv(oth, As[s]);             // dH/db_0
+            const dcplx q1 = dmul(q0, z1), q2 = dmul(q0, z2);
+            const dcplx a0 = ddiv(Ht, As[s]);              // -dH/da_k = z^k a0
+            const dcplx a1 = dmul(a0, z1), a2 = dmul(a0, z2);
+            // Re(conj(d) S)
+            acc[5 * s + 0] = q0.re * Sv.re + q0.im * Sv.im;
+            acc[5 * s + 1] = q1.re * Sv.re + q1.im * Sv.im;
+            acc[5 * s + 2] = q2.re * Sv.re + q2.im * Sv.im;
+            acc[5 * s + 3] = -(a1.re * Sv.re + a1.im * Sv.im);
+            acc[5 * s + 4] = -(a2.re * Sv.re + a2.im * Sv.im);
+            suf = dmul(suf, Hs[s]);
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double invM = 1.0 / (double)M;
+    for (int q = 0; q < 5 * S; ++q) {
+        double v = acc[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[q][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5 * S) {
+        const int q = threadIdx.x;
+        bpart[(int64_t)blockIdx.x * 5 * S + q] = (red[q][0] + red[q][1] + red[q][2] + red[q][3]) * invM;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int q = threadIdx.x; q < 5 * S; q += blockDim.x) {
+        double v = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) v += __ldcg(bpart + (int64_t)b * 5 * S + q);
+        sums[q] = v;
+    }
+    if (threadIdx.x == 0) *done = 0u;
+}
+
+// Inverse transform of a spectrum given in storage layout (position
+// 16t + j of thread t read from its storage index): afterwards register j of
+// thread t holds sample t + T j.
+template <int LOGM>
+__device__ __forceinline__ void inverse_of_storage(const float2* __restrict__ W, float2 (&v)[16],
+                                                   const float2* __restrict__ tw, float2* sb, int t) {
+    using F = FftShape<LOGM>;
+    const float4* w4 = reinterpret_cast<const float4*>(W) + t;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const float4 w = w4[q * F::T];
+        v[2 * q] = make_float2(w.x, w.y);
+        v[2 * q + 1] = make_float2(w.z, w.w);
+    }
+    inverse_from<LOGM, F::NP - 1>(v, tw, sb, t);
+}
+
+// FIR tap gradients: dL/dh_k = (1/M) sum_bins conj(C) S e^(+i w k) (C the
+// cascades' spectrum), the inverse transform of wfir at samples 0..L-1.
+template <int LOGM>
+__global__ void __launch_bounds__((1 << LOGM) / 16, 1) k_chain_grads_fir(const float2* __restrict__ wfir,
+                                                                         const float2* __restrict__ tw, int L,
+                                                                         double* __restrict__ dh) {
+    using F = FftShape<LOGM>;
+    extern __shared__ float2 sb[];
+    const int t = threadIdx.x;
+    float2 v[16];
+    inverse_of_storage<LOGM>(wfir, v, tw, sb, t);
+    const double invM = 1.0 / (double)F::M;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const int n = t + F::T * j;
+        if (n < L) dh[n] = (double)v[j].x * invM;
+    }
+}
+
+// Decay check of a composite spectrum H (storage layout, 1/M folded in): its
+// inverse transform is the chain's impulse response aliased M-periodically;
+// the absolute sum of samples J+1 .. M-1 (which the overlap-save blocks would
+// wrap onto other outputs) above 1e-4 of the whole sets TFX_ERR_DECAY.
+template <int LOGM>
+__global__ void __launch_bounds__((1 << LOGM) / 16, 1) k_chain_tail(const float2* __restrict__ H,
+                                                                    const float2* __restrict__ tw, int J,
+                                                                    int* __restrict__ status) {
+    using F = FftShape<LOGM>;
+    extern __shared__ float2 sb[];
+    __shared__ float red[2][32];
+    const int t = threadIdx.x;
+    float2 v[16];
+    inverse_of_storage<LOGM>(H, v, tw, sb, t);
+    float tot = 0.f, tail = 0.f;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const int n = t + F::T * j;
+        const float a = fabsf(v[j].x);
+        tot += a;
+        if (n > J) tail += a;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        tail += __shfl_xor_sync(0xffffffffu, tail, o);
+    }
+    if ((t & 31) == 0) {
+        red[0][t >> 5] = tot;
+        red[1][t >> 5] = tail;
+    }
+    __syncthreads();
+    if (t == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < F::T / 32; ++w) a += red[0][w], b += red[1][w];
+        if (!(b <= 1e-4 * a)) atomicCAS(status, 0, (int)TFX_ERR_DECAY);
+    }
+}
+
+template <int LOGM>
+cudaError_t launch_xcorr_log(const XcorrArgs& a, int grid, cudaStream_t s) {
+    constexpr int T = (1 << LOGM) / 16;
+    const size_t smem = xcorr_smem_bytes(1 << LOGM);
+    k_chain_xcorr<LOGM><<<(unsigned)grid, T, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int LOGM>
+cudaError_t prepare_spectral_log() {
+    const int smem = (int)fir_fft_smem_bytes(1 << LOGM);
+    cudaError_t e = cudaFuncSetAttribute(k_chain_xcorr<LOGM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)xcorr_smem_bytes(1 << LOGM));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_chain_grads_fir<LOGM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_chain_tail<LOGM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e;
+}
+
+}  // namespace
+
+size_t xcorr_smem_bytes(int M) { return fir_fft_smem_bytes(M) + (size_t)M * sizeof(float2); }
+
+int xcorr_ctas_per_sm(int m) { return m <= 12 ? 2 : 1; }
+
+cudaError_t prepare_spectral(int m) {
+    switch (m) {
+        case 12: return prepare_spectral_log<12>();
+        case 13: return prepare_spectral_log<13>();
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_chain_xcorr(int m, const XcorrArgs& a, int grid, cudaStream_t s) {
+    switch (m) {
+        case 12: return launch_xcorr_log<12>(a, grid, s);
+        case 13: return launch_xcorr_log<13>(a, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_xcorr_reduce(const float2* part, int G, int M, double2* P, cudaStream_t s) {
+    k_xcorr_reduce<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(part, G, M, P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chain_spectrum(const double* raw, int S, const float2* Hf, int m, float2* H, cudaStream_t s) {
+    const int M = 1 << m;
+    k_chain_spectrum<<<(unsigned)((M + 127) / 128), 128, 0, s>>>(raw, S, Hf, m, H);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chain_tail(int m, const float2* H, const float2* tw, int J, int* status, cudaStream_t s) {
+    const size_t smem = fir_fft_smem_bytes(1 << m);
+    switch (m) {
+        case 12: k_chain_tail<12><<<1, 256, smem, s>>>(H, tw, J, status); break;
+        case 13: k_chain_tail<13><<<1, 512, smem, s>>>(H, tw, J, status); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+size_t chain_grads_scratch_bytes(int m, int S) {
+    return 256 + (size_t)(((1 << m) + 127) / 128) * 5 * S * sizeof(double);
+}
+
+cudaError_t launch_chain_grads(int m, const double2* P, const double* raw, int S, const float2* Hf,
+                               const float2* tw, int L, void* scratch, double* sums, float2* wfir, double* dh,
+                               cudaStream_t s) {
+    if (S < 1 || S > SPEC_SMAX) return cudaErrorInvalidValue;
+    const int M = 1 << m;
+    unsigned* done = static_cast<unsigned*>(scratch);
+    double* bpart = reinterpret_cast<double*>(static_cast<char*>(scratch) + 256);
+    k_chain_grads_sec<<<(unsigned)((M + 127) / 128), 128, 0, s>>>(P, raw, S, Hf, m, bpart, done, sums,
+                                                                  dh ? wfir : nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !dh) return e;
+    const size_t smem = fir_fft_smem_bytes(M);
+    switch (m) {
+        case 12: k_chain_grads_fir<12><<<1, 256, smem, s>>>(wfir, tw, L, dh); break;
+        case 13: k_chain_grads_fir<13><<<1, 512, smem, s>>>(wfir, tw, L, dh); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace tfx

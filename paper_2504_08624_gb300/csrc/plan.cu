@@ -504,6 +504,55 @@ double unit_cost_estimate(const HostUnit& u) {
     return 40.0 + 2.0 * u.L;             // CUDA-core FIR
 }
 
+// The cascades' impulse response g (sections [S][5] in chain order, FP64,
+// zero state) over 65536 samples and the length D it is truncated to when it
+// is convolved with the FIR taps f: the first D for which
+// sum_(n >= D) |g[n]| * sum |f| <= 1e-8 ||g * f||_2.  False when g has not
+// decayed by the end (the absolute sum of its last 4096 samples above 1e-14
+// of the whole) or the chain's response is zero.
+bool cascade_decay(const std::vector<double>& sec, int S, const std::vector<double>& f, std::vector<double>& g,
+                   int& D) {
+    const int W = 65536, HEAD = 16384;
+    g.assign(W, 0.0);
+    std::vector<double> w1(S, 0.0), w2(S, 0.0);
+    for (int n = 0; n < W; ++n) {
+        double v = n == 0 ? 1.0 : 0.0;
+        for (int i = 0; i < S; ++i) {
+            const double* r = &sec[5 * (size_t)i];  // b0 b1 b2 a1 a2
+            const double c1 = r[1] - r[3] * r[0], c2 = r[2] - r[4] * r[0];
+            const double out = r[0] * v + w1[i];
+            const double n1 = c1 * v - r[3] * w1[i] + w2[i];
+            w2[i] = c2 * v - r[4] * w1[i];
+            w1[i] = n1;
+            v = out;
+        }
+        g[n] = v;
+    }
+    double total = 0.0, last = 0.0;
+    for (int n = 0; n < W; ++n) total += std::fabs(g[n]);
+    for (int n = W - 4096; n < W; ++n) last += std::fabs(g[n]);
+    if (!(total > 0.0) || !(last <= 1e-14 * total)) return false;
+    double f1 = 0.0, n2 = 0.0;
+    for (double v : f) f1 += std::fabs(v);
+    {
+        const std::vector<double> head(g.begin(), g.begin() + HEAD);
+        for (double v : conv_fft(head, f, HEAD)) n2 += v * v;
+        n2 = std::sqrt(n2);
+    }
+    if (!(n2 > 0.0)) return false;
+    D = W;
+    double tail = 0.0;
+    for (int n = W - 1; n >= 1; --n) {
+        if ((tail + std::fabs(g[n])) * f1 > 1e-8 * n2) {
+            D = n + 1;
+            break;
+        }
+        tail += std::fabs(g[n]);
+        D = n;
+    }
+    return true;
+}
+
 // The whole chain as one FIR (the pipe composes linear time-invariant stages,
 // so the chain is the convolution with its composite impulse response).  The
 // cascades' impulse response g (all sections in chain order, FP64, zero
@@ -539,45 +588,10 @@ void compose_chain(tfx_plan* p) {
         separate += unit_cost_estimate(e);
     }
     if (S == 0 || maxL == 0) return;  // a chain of cascades and at least one FIR
-    const int W = 65536, HEAD = 16384;
-    std::vector<double> g(W);
-    std::vector<double> w1(S, 0.0), w2(S, 0.0);
-    for (int n = 0; n < W; ++n) {
-        double v = n == 0 ? 1.0 : 0.0;
-        for (int i = 0; i < S; ++i) {
-            const double* r = &sec[5 * (size_t)i];  // b0 b1 b2 a1 a2
-            const double c1 = r[1] - r[3] * r[0], c2 = r[2] - r[4] * r[0];
-            const double out = r[0] * v + w1[i];
-            const double n1 = c1 * v - r[3] * w1[i] + w2[i];
-            w2[i] = c2 * v - r[4] * w1[i];
-            w1[i] = n1;
-            v = out;
-        }
-        g[n] = v;
-    }
-    double total = 0.0, last = 0.0;
-    for (int n = 0; n < W; ++n) total += std::fabs(g[n]);
-    for (int n = W - 4096; n < W; ++n) last += std::fabs(g[n]);
-    if (!(total > 0.0) || !(last <= 1e-14 * total)) return;
+    std::vector<double> g;
+    int D = 0;
+    if (!cascade_decay(sec, S, f, g, D)) return;
     const int Lf = (int)f.size();
-    double f1 = 0.0, n2 = 0.0;
-    for (double v : f) f1 += std::fabs(v);
-    {
-        const std::vector<double> head(g.begin(), g.begin() + HEAD);
-        for (double v : conv_fft(head, f, HEAD)) n2 += v * v;
-        n2 = std::sqrt(n2);
-    }
-    if (!(n2 > 0.0)) return;
-    int D = W;
-    double tail = 0.0;
-    for (int n = W - 1; n >= 1; --n) {
-        if ((tail + std::fabs(g[n])) * f1 > 1e-8 * n2) {
-            D = n + 1;
-            break;
-        }
-        tail += std::fabs(g[n]);
-        D = n;
-    }
     const int64_t Lc = (int64_t)D + Lf - 1;
     if (p->N < 2 * Lc) return;
     int bestm = 0;
@@ -610,6 +624,73 @@ void compose_chain(tfx_plan* p) {
     p->use_chain = true;
     p->chain_S = S;
     p->chain_L = Lf;
+    p->chain_D = D;
+}
+
+// A trainable chain whose stages all compose (cascades of at most SPEC_SMAX
+// sections together, none with a pole above HIQ_RADIUS, and at most one FIR)
+// trains by its composite spectrum.  The forward and the input gradient are
+// single-block overlap-save FFT FIRs whose spectrum is the chain's transfer
+// function evaluated in closed form at the transform's bins (the DFT of the
+// untruncated response aliased M-periodically), and the coefficient
+// gradients are inner products of the derivative spectra with the
+// accumulated gradient-input cross-spectrum (k_spectral.cu).  The overlap J
+// covers 1.5 D + Lf - 1 lags (D the decay length of cascade_decay; the
+// margin holds the slower n r^n decay of the derivative responses and pole
+// movement during training, and a device check after every coefficient
+// update reports a response that outgrows it), at least M/4, with the
+// smaller of 4096 and 8192 points that leaves M/4 outputs per block.  The
+// signal must hold 2 (J + 1) samples (as for a composed chain).
+void choose_spectral(tfx_plan* p) {
+    int S = 0, nfir = 0;
+    std::vector<double> sec, f(1, 1.0);
+    int64_t fir_dst = 0;
+    for (const HostUnit& u : p->units) {
+        if (u.hiq) return;
+        sec.insert(sec.end(), u.sec.begin(), u.sec.end());
+        S += u.S;
+        if (u.L > 0) {
+            ++nfir;
+            f = u.taps;
+            fir_dst = u.fir_dst;
+        }
+    }
+    if (S < 1 || S > SPEC_SMAX || nfir > 1) return;
+    std::vector<double> g;
+    int D = 0;
+    if (!cascade_decay(sec, S, f, g, D)) return;
+    const int Lf = (int)f.size();
+    const int64_t Jn = (3 * (int64_t)D + 1) / 2 + Lf - 1;
+    int m = 0;
+    for (int mm = 12; mm <= 13 && m == 0; ++mm)
+        if (Jn <= 3 * (int64_t(1) << mm) / 4) m = mm;
+    if (m == 0) return;
+    const int M = 1 << m;
+    const int J = (int)std::max<int64_t>(Jn, M / 4);
+    if (p->N < 2 * ((int64_t)J + 1)) return;
+    HostUnit h;
+    h.L = Lf;
+    h.taps = f;
+    h.fft = true;
+    h.fft_m = m;
+    h.fft_M = M;
+    h.fft_P = 0;
+    h.fft_B = M - (Lf - 1);
+    HostUnit c;
+    c.L = J + 1;
+    c.fft = true;
+    c.fft_m = m;
+    c.fft_M = M;
+    c.fft_P = 0;
+    c.fft_B = M - J;
+    p->spec_fir = h;
+    p->spec_nfir = nfir;
+    p->spec_fir_dst = fir_dst;
+    p->chain = c;
+    p->use_chain = true;
+    p->spectral = true;
+    p->chain_S = S;
+    p->chain_L = nfir ? Lf : 0;
     p->chain_D = D;
 }
 
@@ -774,8 +855,12 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
     if (!(p->flags & (TFX_PLAN_NO_COMPOSE | TFX_PLAN_FIR_CUDA_CORES | TFX_PLAN_UNFUSED | TFX_PLAN_FIR_BF16_PLAIN |
                       TFX_PLAN_FIR_BF16_SPLIT | TFX_PLAN_SCAN_WARP_TILES | TFX_PLAN_FIR_TC | TFX_PLAN_SCAN_LOOKBACK |
                       TFX_PLAN_TEST_DROP_PUBLISH | TFX_PLAN_FIR_FFT_LOG_MASK)) &&
-        !p->train && p->C > 0 && p->N > 0)
-        compose_chain(p);
+        p->C > 0 && p->N > 0) {
+        if (!p->train)
+            compose_chain(p);
+        else
+            choose_spectral(p);
+    }
 
     // cascade-only block-tile units by channel segments where the free
     // response decays early enough (not needed when the chain is composed:
@@ -788,8 +873,16 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
             if (u.S > 0 && u.S <= SEG_SMAX && u.L == 0 && !u.warp && !u.hiq) choose_segments(p, u, sm_count);
     }
 
-    // constant blob layout
+    // constant blob layout (a spectral plan: every section's raw row and
+    // gradient slot first, contiguous over the units)
     size_t off = 0;
+    size_t spec_rows = 0;
+    if (p->spectral) {
+        p->off_spec_raw = off;
+        off = align_up(off + (size_t)p->chain_S * 6 * sizeof(double));
+        p->off_spec_dst = off;
+        off = align_up(off + (size_t)p->chain_S * sizeof(int64_t));
+    }
     for (HostUnit& u : p->units) {
         u.off_coef = off;
         off = align_up(off + (size_t)u.S * 8 * sizeof(float));
@@ -818,18 +911,31 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
             u.off_tw = off;
             off = align_up(off + fft_pass_twiddles(u.fft_m).size() * sizeof(float2));
         }
-        if (p->train && u.S > 0) {
+        if (p->train && u.S > 0 && p->spectral) {
+            u.off_raw = p->off_spec_raw + spec_rows * 6 * sizeof(double);
+            u.off_dst = p->off_spec_dst + spec_rows * sizeof(int64_t);
+            spec_rows += (size_t)u.S;
+        } else if (p->train && u.S > 0) {
             u.off_raw = off;
             off = align_up(off + (size_t)u.S * 6 * sizeof(double));
             u.off_dst = off;
             off = align_up(off + (size_t)u.S * sizeof(int64_t));
         }
     }
+    if (p->spectral) {  // the FIR's spectrum Hf and the twiddles, shared with the chain
+        p->spec_fir.off_H = off;
+        off = align_up(off + (size_t)p->spec_fir.fft_M * sizeof(float2));
+        p->spec_fir.off_tw = off;
+        off = align_up(off + fft_pass_twiddles(p->spec_fir.fft_m).size() * sizeof(float2));
+        p->chain.off_tw = p->spec_fir.off_tw;
+    }
     if (p->use_chain) {
         p->chain.off_H = off;
         off = align_up(off + (size_t)p->chain.fft_M * sizeof(float2));
-        p->chain.off_tw = off;
-        off = align_up(off + fft_pass_twiddles(p->chain.fft_m).size() * sizeof(float2));
+        if (!p->spectral) {
+            p->chain.off_tw = off;
+            off = align_up(off + fft_pass_twiddles(p->chain.fft_m).size() * sizeof(float2));
+        }
     }
     for (int32_t i = 0; i < nst; ++i) {
         PlainStage ps{st[i].kind, st[i].n, off};
@@ -906,7 +1012,10 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
                     }
         }
     }
-    if (p->use_chain) fill_fft_tables(p->chain, host.data());
+    if (p->spectral)
+        fill_fft_tables(p->spec_fir, host.data());  // the chain's spectrum follows on the device
+    else if (p->use_chain)
+        fill_fft_tables(p->chain, host.data());
     for (int32_t i = 0; i < nst; ++i) {
         float* d = reinterpret_cast<float*>(host.data() + p->plain[i].off);
         if (st[i].kind == TFX_STAGE_SOS) {
@@ -962,6 +1071,15 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
                 if (u.L > 0 && prepare_fir_dh_tc() != cudaSuccess) return TFX_ERR_UNSUPPORTED;
         }
         if (p->use_chain && prepare_fir_fft(p->chain.fft_M) != cudaSuccess) return TFX_ERR_UNSUPPORTED;
+        if (p->spectral) {
+            if (prepare_spectral(p->chain.fft_m) != cudaSuccess) return TFX_ERR_UNSUPPORTED;
+            if (launch_chain_spectrum(reinterpret_cast<const double*>(p->dconst + p->off_spec_raw), p->chain_S,
+                                      reinterpret_cast<const float2*>(p->dconst + p->spec_fir.off_H),
+                                      p->chain.fft_m, reinterpret_cast<float2*>(p->dconst + p->chain.off_H),
+                                      nullptr) != cudaSuccess ||
+                cudaStreamSynchronize(nullptr) != cudaSuccess)
+                return TFX_ERR_CUDA;
+        }
     }
 
     // workspace layout
@@ -1009,7 +1127,24 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
     p->ws_fused = p->scratch_bytes + nbuf * p->buf_bytes;
     p->ws_plain = (nst > 0 ? 2 : 0) * p->buf_bytes;
 
-    if (p->train) {
+    if (p->train && p->spectral) {
+        // nothing saved (the backward reads x); backward workspace: the
+        // correlation CTAs' partial spectra, their FP64 sum, the section
+        // gradient sums, the FIR taps' gradient spectrum and a copy of the
+        // gradient for an in-place input gradient
+        const int M = p->chain.fft_M;
+        const int64_t items = (p->C + 1) / 2 * p->chain.ntt;
+        p->spec_grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)p->sm_count *
+                                                                               xcorr_ctas_per_sm(p->chain.fft_m)));
+        p->saved_bytes = 0;
+        p->b_sp_part = 0;
+        p->b_sp_P = align_up((size_t)p->spec_grid * M * sizeof(float2));
+        p->b_sp_sums = p->b_sp_P + align_up((size_t)M * sizeof(double2));
+        p->b_sp_w = p->b_sp_sums + align_up((size_t)p->chain_S * 5 * sizeof(double));
+        p->b_sp_gs = p->b_sp_w + align_up((size_t)M * sizeof(float2));
+        p->b_gbuf = p->b_sp_gs + align_up(chain_grads_scratch_bytes(p->chain.fft_m, p->chain_S));
+        p->bws_bytes = p->b_gbuf + p->buf_bytes;
+    } else if (p->train) {
         // saved for the backward: the input of every unit after the first (the
         // first unit's input is x itself) and each cascade's chunk-start states
         p->nch = p->N > 0 ? (p->N + T_CHUNK - 1) / T_CHUNK : 0;
@@ -1247,6 +1382,7 @@ int exec_plain(tfx_plan* p, const float* x, float* y, void* ws, cudaStream_t s) 
 // cascade storing its chunk-start states there.
 int exec_train(tfx_plan* p, const float* x, float* y, char* saved, void* ws, cudaStream_t s) {
     char* scratch = static_cast<char*>(ws);
+    if (p->spectral) return launch_unit_range(p, p->chain, x, p->ld, y, p->ld, 0, p->C, scratch, nullptr, s);
     const int nu = (int)p->units.size();
     if (nu == 0) return launch_copy_rows(x, y, p->C, p->N, p->ld, p->ld, s) == cudaSuccess ? TFX_OK : TFX_ERR_CUDA;
     for (int i = 0; i < nu; ++i) {
@@ -1262,6 +1398,88 @@ int exec_train(tfx_plan* p, const float* x, float* y, char* saved, void* ws, cud
     return TFX_OK;
 }
 
+// Backward of a spectral plan.  Coefficient gradients: the correlation
+// CTAs accumulate the block cross-spectra of g and x, their sum P (FP64)
+// gives the section gradients by the closed-form derivative spectra and the
+// FIR taps' gradient by one inverse transform, and the section sums map to
+// the raw rows (the a0 chain rule) in one launch.  Input gradient: the chain
+// applied to g in reverse time (its transpose), by the forward's kernel with
+// reversed rows, after the correlation (which reads g) when dx is g.
+int run_backward_spectral(tfx_plan* p, const float* x, const float* g, float* dx, double* dcoef, char* ws,
+                          cudaStream_t s, bool count_only, int* nlaunch) {
+    int nl = 0;
+#define TFX_LAUNCH(call)                                               \
+    do {                                                               \
+        ++nl;                                                          \
+        if (!count_only && (call) != cudaSuccess) return TFX_ERR_CUDA; \
+    } while (0)
+    const HostUnit& c = p->chain;
+    const int m = c.fft_m, M = c.fft_M, J = c.L - 1;
+    const float2* tw = reinterpret_cast<const float2*>(p->dconst + c.off_tw);
+    if (dcoef) {
+        double* sums = reinterpret_cast<double*>(ws + p->b_sp_sums);
+        double2* P = reinterpret_cast<double2*>(ws + p->b_sp_P);
+        float2* part = reinterpret_cast<float2*>(ws + p->b_sp_part);
+        if (!count_only && cudaMemsetAsync(ws + p->b_sp_gs, 0, sizeof(unsigned), s) != cudaSuccess)
+            return TFX_ERR_CUDA;
+        XcorrArgs a{};
+        a.x = x;
+        a.g = g;
+        a.ldx = p->ld;
+        a.ldg = p->ld;
+        a.C = p->C;
+        a.N = p->N;
+        a.J = J;
+        a.B = c.fft_B;
+        a.nbpc = c.ntt;
+        a.items = (p->C + 1) / 2 * c.ntt;
+        a.tw = tw;
+        a.part = part;
+        TFX_LAUNCH(launch_chain_xcorr(m, a, p->spec_grid, s));
+        TFX_LAUNCH(launch_xcorr_reduce(part, p->spec_grid, M, P, s));
+        const double* raw = reinterpret_cast<const double*>(p->dconst + p->off_spec_raw);
+        nl += p->spec_nfir ? 2 : 1;
+        if (!count_only &&
+            launch_chain_grads(m, P, raw, p->chain_S, reinterpret_cast<const float2*>(p->dconst + p->spec_fir.off_H),
+                               tw, p->spec_fir.L, ws + p->b_sp_gs, sums, reinterpret_cast<float2*>(ws + p->b_sp_w),
+                               p->spec_nfir ? dcoef + p->spec_fir_dst : nullptr, s) != cudaSuccess)
+            return TFX_ERR_CUDA;
+        TFX_LAUNCH(launch_sos_grad_finalize(sums, p->chain_S, raw,
+                                            reinterpret_cast<const int64_t*>(p->dconst + p->off_spec_dst), dcoef, s));
+    }
+    if (dx) {
+        const float* gin = g;
+        int64_t ldg = p->ld;
+        if (dx == g) {  // blocks read their neighbours' gradient samples
+            float* gb = reinterpret_cast<float*>(ws + p->b_gbuf);
+            TFX_LAUNCH(launch_copy_rows(g, gb, p->C, p->N, p->ld, p->N, s));
+            gin = gb;
+            ldg = p->N;
+        }
+        FirFftArgs f{};
+        f.x = gin;
+        f.ldx = ldg;
+        f.y = dx;
+        f.ldy = p->ld;
+        f.C = p->C;
+        f.N = p->N;
+        f.L = c.L;
+        f.M = M;
+        f.m = m;
+        f.B = c.fft_B;
+        f.P = 0;
+        f.nbpc = c.ntt;
+        f.nb = p->C * c.ntt;
+        f.H = reinterpret_cast<const float2*>(p->dconst + c.off_H);
+        f.tw = tw;
+        f.rev = 1;
+        TFX_LAUNCH(launch_fir_fft(f, s));
+    }
+#undef TFX_LAUNCH
+    if (nlaunch) *nlaunch = nl;
+    return TFX_OK;
+}
+
 // Backward over the units, last to first.  Between units the gradient is
 // kept either in time order or time-reversed: an FIR's input gradient is the
 // same FIR applied to the reversed gradient (FIR^T = J FIR J, J the time
@@ -1270,6 +1488,7 @@ int exec_train(tfx_plan* p, const float* x, float* y, char* saved, void* ws, cud
 // and *nlaunch receives the number of kernels a real call launches.
 int run_backward(tfx_plan* p, const float* x, const float* g, float* dx, double* dcoef, const char* saved, char* ws,
                  cudaStream_t s, bool count_only, int* nlaunch) {
+    if (p->spectral) return run_backward_spectral(p, x, g, dx, dcoef, ws, s, count_only, nlaunch);
     int nl = 0;
 #define TFX_LAUNCH(call)                                                     \
     do {                                                                     \
@@ -1545,7 +1764,12 @@ int tfx_plan_describe(const tfx_plan* p, char* buf, size_t len) {
     if (!p) return -1;
     std::string d;
     char item[160];
-    if (p->use_chain) {
+    if (p->spectral) {
+        const HostUnit& c = p->chain;
+        snprintf(item, sizeof item, "chain_spectral:S=%d,L=%d,D=%d,J=%d,M=%d,B=%d", p->chain_S, p->chain_L,
+                 p->chain_D, c.L - 1, c.fft_M, c.fft_B);
+        d = item;
+    } else if (p->use_chain) {
         const HostUnit& c = p->chain;
         snprintf(item, sizeof item, "chain_fft:S=%d,L=%d,D=%d,Lc=%d,M=%d,B=%d", p->chain_S, p->chain_L, p->chain_D,
                  c.L, c.fft_M, c.fft_B);
@@ -1734,6 +1958,7 @@ const char* tfx_strerror(int status) {
         case TFX_ERR_TIMEOUT: return "TFX_ERR_TIMEOUT: a device-side bounded wait gave up";
         case TFX_ERR_UNSUPPORTED: return "TFX_ERR_UNSUPPORTED: request outside what this build implements";
         case TFX_ERR_NOMEM: return "TFX_ERR_NOMEM: allocation failed";
+        case TFX_ERR_DECAY: return "TFX_ERR_DECAY: the chain's response outlasts the spectral plan's overlap";
         default: return "unknown tfx status";
     }
 }

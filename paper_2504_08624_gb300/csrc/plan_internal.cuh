@@ -116,6 +116,16 @@ struct tfx_plan {
     int32_t compose_m[16] = {};  // transform size exponent per floor(log2(Lc)) (0: cost model)
     tfx::HostUnit chain;
     int chain_S = 0, chain_L = 0, chain_D = 0;  // sections, combined FIR length, cascade response length
+    // trainable chains run by their composite spectrum: the chain unit above
+    // (overlap J = chain.L - 1, spectrum from the sections' closed form) runs
+    // the forward and, in reverse time, the input gradient
+    bool spectral = false;
+    tfx::HostUnit spec_fir;  // the FIR (a unit impulse without one) at the chain's transform size
+    int spec_nfir = 0;
+    int64_t spec_fir_dst = 0;
+    size_t off_spec_raw = 0, off_spec_dst = 0;  // every section's raw row and gradient slot, contiguous
+    int spec_grid = 0;                          // correlation CTAs
+    size_t b_sp_part = 0, b_sp_P = 0, b_sp_sums = 0, b_sp_w = 0, b_sp_gs = 0;  // backward workspace offsets
 };
 
 namespace tfx {

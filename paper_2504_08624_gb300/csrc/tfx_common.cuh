@@ -191,6 +191,7 @@ struct FirFftArgs {
     const float2* tw;  // per-pass twiddle tables (see k_fir_fft.cu)
     int P;             // 0: single-block overlap-save; else partitions of B = M/2 taps
     float2* Z;         // partitioned: [ceil(C/2)][nbpc][M] segment spectra (workspace)
+    int rev;           // single-block: rows of x and y in reverse time (the transposed filter)
 };
 
 // One composed clip of a batch (the whole chain as one FFT FIR): where its
@@ -202,6 +203,22 @@ struct BatchFft {
     int L, B;
     int64_t nbpc, nb;
     const float2* H;
+};
+
+// Sections a spectral training plan takes (all its cascades together).
+constexpr int SPEC_SMAX = 16;
+
+// Block correlation spectra of a training step (k_spectral.cu): channel
+// pairs x blocks of B gradient samples against input windows of J + B.
+struct XcorrArgs {
+    const float* x;
+    const float* g;
+    int64_t ldx, ldg;
+    int64_t C, N;
+    int J, B;             // lags kept (the composite response's halo) and gradient samples per block
+    int64_t nbpc, items;  // blocks per channel; channel pairs x blocks
+    const float2* tw;
+    float2* part;         // [grid][M] partial spectra (storage layout)
 };
 
 struct BatchFir {
@@ -378,6 +395,19 @@ cudaError_t launch_fir_tc(const FirTcArgs& a, cudaStream_t s);
 size_t fir_fft_smem_bytes(int M);
 cudaError_t prepare_fir_fft(int M);
 cudaError_t launch_fir_fft(const FirFftArgs& a, cudaStream_t s);
+size_t xcorr_smem_bytes(int M);
+int xcorr_ctas_per_sm(int m);
+cudaError_t prepare_spectral(int m);
+cudaError_t launch_chain_xcorr(int m, const XcorrArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_xcorr_reduce(const float2* part, int G, int M, double2* P, cudaStream_t s);
+cudaError_t launch_chain_spectrum(const double* raw, int S, const float2* Hf, int m, float2* H, cudaStream_t s);
+cudaError_t launch_chain_tail(int m, const float2* H, const float2* tw, int J, int* status, cudaStream_t s);
+// Scratch of launch_chain_grads: a completion counter (zeroed before the
+// launch) and the blocks' partial sums.
+size_t chain_grads_scratch_bytes(int m, int S);
+cudaError_t launch_chain_grads(int m, const double2* P, const double* raw, int S, const float2* Hf,
+                               const float2* tw, int L, void* scratch, double* sums, float2* wfir, double* dh,
+                               cudaStream_t s);
 cudaError_t launch_fir_fft_batched(int m, const BatchFft* units, const int64_t* prefix, int nunits, int64_t ctas,
                                    BatchBases bases, const float2* tw, cudaStream_t s);
 cudaError_t launch_fir_fft_spectrum(const double* taps, int L, int M, int B, int P, const float2* tw, float2* H,

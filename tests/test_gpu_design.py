@@ -88,8 +88,10 @@ def test_plan_update_sos_on_device(flags):
     assert p.get_error() == 0
     assert_close(y, oracle.chain(x, st1), 1e-4, "updated plan vs oracle")
     # the same route as the updated plan (an update leaves a composed chain's
-    # units running, so the fresh plan keeps its units too)
-    fresh = api.Plan(2, 40000, st1, flags=fl | N.TFX_PLAN_NO_COMPOSE).execute(xd).cpu().numpy().astype(np.float64)
+    # units running, so the fresh plan keeps its units too; a trainable plan
+    # keeps its spectral route and rebuilds the chain's spectrum)
+    keep = 0 if flags == "trainable" else N.TFX_PLAN_NO_COMPOSE
+    fresh = api.Plan(2, 40000, st1, flags=fl | keep).execute(xd).cpu().numpy().astype(np.float64)
     assert_close(y, fresh, 1e-5, "updated plan vs fresh plan")
     # an unstable row is reported through the status word
     bad = rows1.copy()

@@ -230,8 +230,9 @@ def test_grad_argument_errors():
 
 
 def test_launch_counts():
+    from paper_2504_08624_gb300 import _native
     stages = [("sos", W.random_stable_sos(6, 5, 0.5, 0.95)), ("fir", np.hanning(257))]
-    p = plan_for(4, 5000, stages)
+    p = plan_for(4, 5000, stages, _native.TFX_PLAN_NO_COMPOSE)  # the scan-adjoint route
     # cascade: adjoint scan + column sums + finalize; FIR: tap-gradient GEMM
     # (which also writes the reversed gradient) + column sums + FIR over the
     # reversed gradient; without coefficient gradients the FIR needs a flip
