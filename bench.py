@@ -530,13 +530,37 @@ def measure_fwdbwd(wl, steps, warmup, dev, stream, torch, dist, ws, rank, pk, sm
     launches = plan.launches_per_execute + 1 + plan.backward_launches(True, True)
     step_s = t / steps
 
-    # dominant kernel: the cascade's reverse-time adjoint scan, timed alone
-    # through a cascade-only trainable plan's backward with only dL/dx asked
-    # (then that kernel is the only launch)
-    sos_stages = [st for st in wl.stages if st[0] == "sos"]
+    route = plan.describe()
     roof = None
-    if S > 0:
-        sp = api.Plan(wl.C, wl.N, sos_stages, flags=NAT.TFX_PLAN_TRAINABLE)
+    parts = None
+    if route and route[0]["kind"] == "chain_spectral":
+        # spectral route: the forward and the input gradient are one FFT FIR
+        # launch each (8 B per sample: read one signal, write one), the
+        # coefficient gradients one correlation launch over x and g (8 B per
+        # sample read) and four launches of M-point size; each part timed
+        # alone through the plan's own calls
+        k_k = max(10, steps // 3)
+        t_dx = time_gpu(lambda: plan.backward(x, g, dx, None, saved, bws), k_k, 3, stream, torch, None) / k_k
+        t_dc = time_gpu(lambda: plan.backward(x, g, None, dcoef, saved, bws), k_k, 3, stream, torch, None) / k_k
+        parts = {"forward (k_fir_fft)": t_f, "dL/dx (k_fir_fft, reverse time)": t_dx,
+                 "dL/dcoef (k_chain_xcorr + k_xcorr_reduce + k_chain_grads_sec + k_chain_grads_fir + "
+                 "k_sos_grad_finalize)": t_dc}
+        name, t_k = max(parts.items(), key=lambda kv: kv[1])
+        ach = units * 8.0 / t_k / 1e9
+        kern = "k_chain_xcorr" if name.startswith("dL/dcoef") else "k_fir_fft"
+        roof = {"bound": "hbm", "kernel": kern, "part": name, "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "kernel_ms": t_k * 1e3, "share_of_step": t_k / step_s,
+                "traffic": traffic_for(kern, wl.name), "peak_source": pk["source"],
+                "route": route[0],
+                "note": "8 algorithmic bytes per channel-sample for each part (forward: read x, write y; dL/dx: "
+                        "read g, write dx; correlation: read x and g)"}
+        parts = {k: v * 1e3 for k, v in parts.items()}
+    elif S > 0:
+        # dominant kernel: the cascade's reverse-time adjoint scan, timed alone
+        # through a cascade-only trainable plan's backward with only dL/dx asked
+        # (then that kernel is the only launch)
+        sos_stages = [st for st in wl.stages if st[0] == "sos"]
+        sp = api.Plan(wl.C, wl.N, sos_stages, flags=NAT.TFX_PLAN_TRAINABLE | NAT.TFX_PLAN_NO_COMPOSE)
         ssaved = sp.new_saved()
         sp.forward_train(x, y, ssaved)
         assert sp.backward_launches(True, False) == (S + 7) // 8
@@ -614,6 +638,7 @@ def measure_fwdbwd(wl, steps, warmup, dev, stream, torch, dist, ws, rank, pk, sm
             "steps": steps, "step": "training forward + MSE loss and dL/dy + backward (dL/dx, dL/dcoef)",
             "cuda_graph": graph is not None, "eager_ms_per_step": t_eager / steps * 1e3,
             "fwd_ms": t_f * 1e3, "loss_ms": t_l * 1e3, "bwd_ms": t_b * 1e3, "gpu_launches_per_step": launches,
+            "route": route, "parts_ms": parts,
             "roofline": roof, "roofline_hbm": hbm, "e2e": e2e, "cpu_baseline": cpu, "parity": parity,
             "dtype": "f32", "plain_gpu": None}
 

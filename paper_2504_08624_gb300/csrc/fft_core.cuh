@@ -339,18 +339,21 @@ __device__ __forceinline__ void load_pair(float2 (&v)[16], const float* x0, cons
 
 // Points n >= first of each segment are outputs n - first of its block,
 // samples b0 + [0, m0) of row y0 (real parts) and b1 + [0, m1) of row y1
-// (imaginary parts); REV: rows in reverse time, as for load_pair.
+// (imaginary parts); REV: rows in reverse time, as for load_pair.  Register
+// j of thread t is point t + T j: one row pointer per thread, a constant
+// offset per register, and one unsigned compare per store.
 template <int LOGM, bool REV = false>
 __device__ __forceinline__ void store_pair(const float2 (&v)[16], float* y0, float* y1, int64_t b0, int64_t b1,
-                                           int64_t N, int first, int64_t m0, int64_t m1, int t) {
+                                           int64_t N, int first, int m0, int m1, int t) {
     using F = FftShape<LOGM>;
+    float* p0 = REV ? y0 + (N - 1 - b0 + first) - t : y0 + (b0 - first) + t;
+    float* p1 = REV ? y1 + (N - 1 - b1 + first) - t : y1 + (b1 - first) + t;
+    const int o0 = t - first;
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-        const int o = t + F::T * j - first;
-        if (o >= 0) {
-            if (o < m0) y0[REV ? N - 1 - (b0 + o) : b0 + o] = v[j].x;
-            if (o < m1) y1[REV ? N - 1 - (b1 + o) : b1 + o] = v[j].y;
-        }
+        const int o = o0 + F::T * j;
+        if ((unsigned)o < (unsigned)m0) p0[REV ? -F::T * j : F::T * j] = v[j].x;
+        if ((unsigned)o < (unsigned)m1) p1[REV ? -F::T * j : F::T * j] = v[j].y;
     }
 }
 

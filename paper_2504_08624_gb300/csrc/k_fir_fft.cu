@@ -51,10 +51,15 @@ template <int LOGM, bool REV = false>
 __device__ __forceinline__ void fft_block_pair(const FirFftArgs& a, int64_t pr, float2* sb, int t) {
     using F = FftShape<LOGM>;
     const int Hh = a.L - 1;
-    const int64_t k0 = 2 * pr;
-    const bool live1 = k0 + 1 < a.nb;
-    const int64_t c0 = k0 / a.nbpc, c1 = live1 ? (k0 + 1) / a.nbpc : c0;
-    const int64_t n00 = (k0 % a.nbpc) * (int64_t)a.B, n01 = live1 ? ((k0 + 1) % a.nbpc) * (int64_t)a.B : 0;
+    // block coordinates in 32 bits (the host keeps nb below 2^31): one
+    // division for block 2pr; block 2pr + 1 is the next one in its channel
+    // or the first of the next channel
+    const unsigned k0 = 2u * (unsigned)pr, nbpc = (unsigned)a.nbpc;
+    const bool live1 = k0 + 1u < (unsigned)a.nb;
+    const unsigned c0 = k0 / nbpc, r0 = k0 - c0 * nbpc;
+    const bool wrap = r0 + 1u == nbpc;
+    const unsigned c1 = live1 && wrap ? c0 + 1u : c0, r1 = live1 ? (wrap ? 0u : r0 + 1u) : 0u;
+    const int64_t n00 = (int64_t)r0 * a.B, n01 = (int64_t)r1 * a.B;
     float2 v[16];
     load_pair<LOGM, REV>(v, a.x + c0 * a.ldx, a.x + c1 * a.ldx, live1, n00 - Hh, n01 - Hh, a.N, t);
     forward_from<LOGM, 0>(v, a.tw, sb, t);
@@ -68,8 +73,8 @@ __device__ __forceinline__ void fft_block_pair(const FirFftArgs& a, int64_t pr, 
         v[2 * q + 1] = cmul(v[2 * q + 1], make_float2(h.z, h.w));
     }
     inverse_from<LOGM, F::NP - 1, last_forward_group<LOGM>()>(v, a.tw, sb, t);
-    const int64_t m0 = a.N - n00 < a.B ? a.N - n00 : a.B;
-    const int64_t m1 = live1 ? (a.N - n01 < a.B ? a.N - n01 : a.B) : 0;
+    const int m0 = (int)(a.N - n00 < a.B ? a.N - n00 : a.B);
+    const int m1 = live1 ? (int)(a.N - n01 < a.B ? a.N - n01 : a.B) : 0;
     store_pair<LOGM, REV>(v, a.y + c0 * a.ldy, a.y + c1 * a.ldy, n00, n01, a.N, Hh, m0, m1, t);
 }
 
@@ -131,11 +136,12 @@ __global__ void __launch_bounds__((1 << LOGM) / 16, 16384 >> LOGM) k_fir_fft_spe
     using F = FftShape<LOGM>;
     extern __shared__ float2 sb[];
     const int t = threadIdx.x;
-    const int64_t pb = blockIdx.x, r = pb / a.nbpc, b = pb % a.nbpc;
-    const int64_t c0 = 2 * r;
+    const int64_t pb = blockIdx.x;
+    const unsigned r = blockIdx.x / (unsigned)a.nbpc, b = blockIdx.x - r * (unsigned)a.nbpc;
+    const int64_t c0 = 2 * (int64_t)r;
     const bool live1 = c0 + 1 < a.C;
     const float* x0 = a.x + c0 * a.ldx;
-    const int64_t s0 = (b - 1) * (int64_t)a.B;
+    const int64_t s0 = ((int64_t)b - 1) * a.B;
     float2 v[16];
     load_pair<LOGM>(v, x0, live1 ? x0 + a.ldx : x0, live1, s0, s0, a.N, t);
     forward_from<LOGM, 0>(v, a.tw, sb, t);
@@ -153,13 +159,14 @@ __global__ void __launch_bounds__((1 << LOGM) / 16, 16384 >> LOGM) k_fir_fft_con
     using F = FftShape<LOGM>;
     extern __shared__ float2 sb[];
     const int t = threadIdx.x;
-    const int64_t pb = blockIdx.x, r = pb / a.nbpc, b = pb % a.nbpc;
-    const int64_t c0 = 2 * r;
+    const int64_t pb = blockIdx.x;
+    const unsigned r = blockIdx.x / (unsigned)a.nbpc, b = blockIdx.x - r * (unsigned)a.nbpc;
+    const int64_t c0 = 2 * (int64_t)r;
     const bool live1 = c0 + 1 < a.C;
     float2 v[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) v[j] = make_float2(0.f, 0.f);
-    const int np = (int)(b + 1 < a.P ? b + 1 : a.P);
+    const int np = (int)b + 1 < a.P ? (int)b + 1 : a.P;
     for (int p = 0; p < np; ++p) {
         const float4* h4 = reinterpret_cast<const float4*>(a.H + (int64_t)p * F::M) + t;
         const float4* z4 = reinterpret_cast<const float4*>(a.Z + (pb - p) * F::M) + t;
@@ -173,8 +180,8 @@ __global__ void __launch_bounds__((1 << LOGM) / 16, 16384 >> LOGM) k_fir_fft_con
         }
     }
     inverse_from<LOGM, F::NP - 1>(v, a.tw, sb, t);
-    const int64_t n0 = b * (int64_t)a.B;
-    const int64_t m0 = a.N - n0 < a.B ? a.N - n0 : a.B;
+    const int64_t n0 = (int64_t)b * a.B;
+    const int m0 = (int)(a.N - n0 < a.B ? a.N - n0 : a.B);
     float* y0 = a.y + c0 * a.ldy;
     store_pair<LOGM>(v, y0, live1 ? y0 + a.ldy : y0, n0, n0, a.N, F::M - a.B, m0, live1 ? m0 : 0, t);
 }
@@ -306,6 +313,7 @@ cudaError_t launch_fir_fft_spectrum(const double* taps, int L, int M, int B, int
 
 cudaError_t launch_fir_fft(const FirFftArgs& a, cudaStream_t s) {
     if (a.nb <= 0) return cudaSuccess;
+    if (a.nb > INT32_MAX || (a.P > 0 && (a.C + 1) / 2 * a.nbpc > INT32_MAX)) return cudaErrorInvalidValue;
     switch (a.m) {
         case 10: return launch_log<10>(a, s);
         case 11: return launch_log<11>(a, s);

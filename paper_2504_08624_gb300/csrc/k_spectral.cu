@@ -24,6 +24,8 @@
 // at sample k.  The derivative responses decay with the chain's poles, so
 // lags beyond J (where the circular correlation is not r) meet only their
 // negligible tails.
+#include <algorithm>
+
 #include "fft_core.cuh"
 
 namespace tfx {
@@ -48,9 +50,9 @@ struct dcplx {
     double re, im;
 };
 __device__ __forceinline__ dcplx dmul(dcplx a, dcplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
-__device__ __forceinline__ dcplx ddiv(dcplx a, dcplx b) {
-    const double d = b.re * b.re + b.im * b.im;
-    return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+__device__ __forceinline__ dcplx drecip(dcplx b) {
+    const double d = 1.0 / (b.re * b.re + b.im * b.im);
+    return {b.re * d, -b.im * d};
 }
 
 // Section s's numerator and denominator at z (raw row: the a0 cancels in the
@@ -72,11 +74,12 @@ __global__ void __launch_bounds__((1 << LOGM) / 16, LOGM <= 12 ? 2 : 1) k_chain_
     float2 acc[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) acc[j] = make_float2(0.f, 0.f);
-    for (int64_t it = blockIdx.x; it < a.items; it += gridDim.x) {
-        const int64_t r = it / a.nbpc, b = it % a.nbpc;
-        const int64_t c0 = 2 * r;
+    const unsigned nbpc = (unsigned)a.nbpc;
+    for (unsigned it = blockIdx.x; it < (unsigned)a.items; it += gridDim.x) {
+        const unsigned r = it / nbpc, b = it - r * nbpc;
+        const int64_t c0 = 2 * (int64_t)r;
         const bool live1 = c0 + 1 < a.C;
-        const int64_t n0 = b * (int64_t)a.B;
+        const int64_t n0 = (int64_t)b * a.B;
         float2 v[16];
         __syncthreads();  // the previous transform's exchanges are done with sb
         load_pair<LOGM>(v, a.x + c0 * a.ldx, a.x + (live1 ? c0 + 1 : c0) * a.ldx, live1, n0 - a.J, n0 - a.J, a.N, t);
@@ -84,14 +87,15 @@ __global__ void __launch_bounds__((1 << LOGM) / 16, LOGM <= 12 ? 2 : 1) k_chain_
 #pragma unroll
         for (int j = 0; j < 16; ++j) zx[j * F::T + t] = v[j];
         // gradient samples n0 + (p - J) at positions p >= J, zeros before
-        const float* g0 = a.g + c0 * a.ldg;
-        const float* g1 = a.g + (live1 ? c0 + 1 : c0) * a.ldg;
+        // (lim of them in this block)
+        const int lim = (int)(a.N - n0 < a.B ? a.N - n0 : a.B);
+        const float* g0 = a.g + c0 * a.ldg + (n0 - a.J) + t;
+        const float* g1 = live1 ? g0 + a.ldg : g0;
+        const int o0 = t - a.J;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-            const int p = t + F::T * j;
-            const int64_t n = n0 + p - a.J;
-            const bool in = p >= a.J && n < a.N;
-            v[j] = make_float2(in ? __ldg(g0 + n) : 0.f, (in && live1) ? __ldg(g1 + n) : 0.f);
+            const bool in = (unsigned)(o0 + F::T * j) < (unsigned)lim;
+            v[j] = make_float2(in ? __ldg(g0 + F::T * j) : 0.f, (in && live1) ? __ldg(g1 + F::T * j) : 0.f);
         }
         __syncthreads();
         forward_from<LOGM, 0>(v, a.tw, sb, t);
@@ -107,113 +111,160 @@ __global__ void __launch_bounds__((1 << LOGM) / 16, LOGM <= 12 ? 2 : 1) k_chain_
     for (int q = 0; q < 8; ++q) out[q * F::T] = make_float4(acc[2 * q].x, acc[2 * q].y, acc[2 * q + 1].x, acc[2 * q + 1].y);
 }
 
-// P = sum of the CTAs' partials, in FP64 (storage layout).
-__global__ void k_xcorr_reduce(const float2* __restrict__ part, int G, int M, double2* __restrict__ P) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= M) return;
+// P = sum of the CTAs' partials, in FP64 (storage layout).  Block b takes
+// bins [32b, 32b + 32): warp w sums partials w, w + 32, ... for its lane's
+// bin (coalesced rows), then the warp sums are added in warp order.
+constexpr int REDUCE_WARPS = 32;
+__global__ void __launch_bounds__(32 * REDUCE_WARPS) k_xcorr_reduce(const float2* __restrict__ part, int G, int M,
+                                                                   double2* __restrict__ P) {
+    __shared__ double2 red[REDUCE_WARPS][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
     double re = 0.0, im = 0.0;
-    for (int g = 0; g < G; ++g) {
-        const float2 v = part[(int64_t)g * M + i];
-        re += v.x;
-        im += v.y;
+    if (i < M) {
+#pragma unroll 4
+        for (int g = w; g < G; g += REDUCE_WARPS) {
+            const float2 v = __ldcs(part + (int64_t)g * M + i);
+            re += v.x;
+            im += v.y;
+        }
     }
-    P[i] = make_double2(re, im);
+    red[w][lane] = make_double2(re, im);
+    __syncthreads();
+    if (w == 0 && i < M) {
+        double2 s = red[0][lane];
+        for (int k = 1; k < REDUCE_WARPS; ++k) s.x += red[k][lane].x, s.y += red[k][lane].y;
+        P[i] = s;
+    }
+}
+
+// Complex shuffles (each part a 64-bit shuffle).
+__device__ __forceinline__ dcplx shfl_up_c(dcplx v, int d) {
+    return {__shfl_up_sync(0xffffffffu, v.re, d), __shfl_up_sync(0xffffffffu, v.im, d)};
+}
+__device__ __forceinline__ dcplx shfl_down_c(dcplx v, int d) {
+    return {__shfl_down_sync(0xffffffffu, v.re, d), __shfl_down_sync(0xffffffffu, v.im, d)};
+}
+__device__ __forceinline__ dcplx shfl_c(dcplx v, int src) {
+    return {__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src)};
 }
 
 // Composite spectrum in the filter's layout (storage index i, 1/M folded
 // in): the FIR's spectrum Hf (already scaled) times prod_s B_s / A_s at the
-// bin of i, in FP64.
-__global__ void k_chain_spectrum(const double* __restrict__ raw, int S, const float2* __restrict__ Hf, int m,
-                                 float2* __restrict__ H) {
+// bin of i, in FP64, one lane per (bin, section) as in k_chain_grads_sec.
+__global__ void __launch_bounds__(128) k_chain_spectrum(const double* __restrict__ raw, int S,
+                                                        const float2* __restrict__ Hf, int m, float2* __restrict__ H) {
     const int M = 1 << m, T = M / 16;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= M) return;
-    const int bin = bitrev_bits(pos_of_storage(i, T), m);
+    const int lane = threadIdx.x & 31;
+    const int NB = 32 / S, slot = lane / S, sec = lane % S;
+    const bool active = slot < NB;
+    const double* r = raw + 6 * (active ? sec : 0);
+    const double inv0 = 1.0 / r[3];
+    const double b0 = r[0] * inv0, b1 = r[1] * inv0, b2 = r[2] * inv0, a1 = r[4] * inv0, a2 = r[5] * inv0;
+    const int gi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int i = gi * NB + slot;
+    const bool live = active && i < M;
+    const int ii = live ? i : 0;
+    const int bin = bitrev_bits(pos_of_storage(ii, T), m);
     double sn, cs;
-    sincos(-TWO_PI * (double)bin / (double)M, &sn, &cs);
+    sincospi(-2.0 * (double)bin / (double)M, &sn, &cs);
     const dcplx z1 = {cs, sn}, z2 = dmul(z1, z1);
-    dcplx h = {(double)Hf[i].x, (double)Hf[i].y};
-    for (int s = 0; s < S; ++s) {
-        dcplx Bn, An;
-        section_at(raw + 6 * s, z1, z2, Bn, An);
-        h = dmul(h, ddiv(Bn, An));
+    const dcplx Bn = {b0 + b1 * z1.re + b2 * z2.re, b1 * z1.im + b2 * z2.im};
+    const dcplx An = {1.0 + a1 * z1.re + a2 * z2.re, a1 * z1.im + a2 * z2.im};
+    dcplx pin = dmul(Bn, drecip(An));
+    for (int d = 1; d < S; d <<= 1) {
+        const dcplx u = shfl_up_c(pin, d);
+        if (sec >= d) pin = dmul(u, pin);
     }
-    H[i] = make_float2((float)h.re, (float)h.im);
+    if (live && sec == S - 1) {
+        const dcplx h = dmul({(double)Hf[i].x, (double)Hf[i].y}, pin);
+        H[i] = make_float2((float)h.re, (float)h.im);
+    }
 }
 
-// Section coefficient gradients (a0-normalised b0 b1 b2 a1 a2 per section):
-// one bin per thread, FP64.  Each block writes its sums to bpart[block][5 S];
-// the last block to finish (counted on *done, zero on entry and reset by
-// that block) adds them in block order into sums[5 S], so the result does
-// not depend on the blocks' timing.  With wfir set, also conj(C) S at each
-// bin (C = prod_s H_s, the cascades' spectrum) for the FIR tap gradients, in
-// storage layout.
-__global__ void __launch_bounds__(128) k_chain_grads_sec(const double2* __restrict__ P, const double* __restrict__ raw,
-                                                         int S, const float2* __restrict__ Hf, int m,
-                                                         double* __restrict__ bpart, unsigned* __restrict__ done,
-                                                         double* __restrict__ sums, float2* __restrict__ wfir) {
-    __shared__ double red[5 * SPEC_SMAX][4];
+// Section coefficient gradients (a0-normalised b0 b1 b2 a1 a2 per section),
+// FP64.  A warp takes NB = floor(32 / S) bins at a time with one lane per
+// (bin, section): lane l is section l % S of bin slot l / S, so each lane
+// evaluates one section, the products over the other sections come from
+// segmented prefix and suffix scans across the bin's S lanes, and a lane
+// accumulates the gradient terms of one fixed section over all the bins it
+// visits (enough warps per SM to hide the FP64 latency).  Each block writes
+// its sums to bpart[block][5 S]; the last block to finish (counted on *done,
+// zero on entry and reset by that block) adds them in block order into
+// sums[5 S], so the result does not depend on the blocks' timing.  With wfir
+// set, also conj(C) S at each bin (C = prod_s H_s, the cascades' spectrum)
+// for the FIR tap gradients, in storage layout.
+constexpr int GRADS_WARPS = 4;
+__global__ void __launch_bounds__(32 * GRADS_WARPS) k_chain_grads_sec(
+    const double2* __restrict__ P, const double* __restrict__ raw, int S, const float2* __restrict__ Hf, int m,
+    double* __restrict__ bpart, unsigned* __restrict__ done, double* __restrict__ sums, float2* __restrict__ wfir) {
+    __shared__ double red[GRADS_WARPS][32][5];
     __shared__ bool last;
     const int M = 1 << m, T = M / 16;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double acc[5 * SPEC_SMAX];
-#pragma unroll
-    for (int q = 0; q < 5 * SPEC_SMAX; ++q) acc[q] = 0.0;
-    if (i < M) {
-        const int bin = bitrev_bits(pos_of_storage(i, T), m);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int NB = 32 / S, slot = lane / S, sec = lane % S;
+    const bool active = slot < NB;
+    const int first = slot * S;  // the bin's section-0 lane
+    // this lane's section, a0-normalised
+    const double* r = raw + 6 * (active ? sec : 0);
+    const double inv0 = 1.0 / r[3];
+    const double b0 = r[0] * inv0, b1 = r[1] * inv0, b2 = r[2] * inv0, a1 = r[4] * inv0, a2 = r[5] * inv0;
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    const int groups = (M + NB - 1) / NB;
+    for (int gi = blockIdx.x * GRADS_WARPS + warp; gi < groups; gi += gridDim.x * GRADS_WARPS) {
+        const int i = gi * NB + slot;  // storage index of this lane's bin
+        const bool live = active && i < M;
+        const int ii = live ? i : 0;
+        const int bin = bitrev_bits(pos_of_storage(ii, T), m);
         const int mir = (M - bin) & (M - 1);
-        const double2 p = P[i], pm = P[storage_of_pos(bitrev_bits(mir, m), T)];
+        const double2 p = P[ii], pm = P[storage_of_pos(bitrev_bits(mir, m), T)];
         const dcplx Sv = {0.5 * (p.x + pm.x), 0.5 * (p.y - pm.y)};
         double sn, cs;
-        sincos(-TWO_PI * (double)bin / (double)M, &sn, &cs);
+        sincospi(-2.0 * (double)bin / (double)M, &sn, &cs);
         const dcplx z1 = {cs, sn}, z2 = dmul(z1, z1);
-        const dcplx F = {(double)Hf[i].x * M, (double)Hf[i].y * M};
-        dcplx Hs[SPEC_SMAX], As[SPEC_SMAX];
-        for (int s = 0; s < S; ++s) {
-            dcplx Bn;
-            section_at(raw + 6 * s, z1, z2, Bn, As[s]);
-            Hs[s] = ddiv(Bn, As[s]);
+        const dcplx F = {(double)Hf[ii].x * M, (double)Hf[ii].y * M};
+        const dcplx Bn = {b0 + b1 * z1.re + b2 * z2.re, b1 * z1.im + b2 * z2.im};
+        const dcplx An = {1.0 + a1 * z1.re + a2 * z2.re, a1 * z1.im + a2 * z2.im};
+        const dcplx iA = drecip(An);
+        const dcplx Hs = dmul(Bn, iA);
+        // inclusive prefix and suffix products over the bin's sections
+        dcplx pin = Hs, sin_ = Hs;
+        for (int d = 1; d < S; d <<= 1) {
+            const dcplx u = shfl_up_c(pin, d), w = shfl_down_c(sin_, d);
+            if (sec >= d) pin = dmul(u, pin);
+            if (sec + d < S) sin_ = dmul(sin_, w);
         }
-        // prefix products of the sections, then a suffix sweep
-        dcplx pre[SPEC_SMAX];
-        dcplx run = {1.0, 0.0};
-        for (int s = 0; s < S; ++s) {
-            pre[s] = run;
-            run = dmul(run, Hs[s]);
-        }
-        const dcplx Cs = run, Ht = dmul(F, Cs);
-        if (wfir) {
+        dcplx pre = shfl_up_c(pin, 1), suf = shfl_down_c(sin_, 1);
+        if (sec == 0) pre = {1.0, 0.0};
+        if (sec == S - 1) suf = {1.0, 0.0};
+        const dcplx Cs = shfl_c(pin, first + S - 1);  // the product over every section
+        if (!live) continue;
+        if (wfir && sec == 0) {
             const dcplx w = dmul({Cs.re, -Cs.im}, Sv);
             wfir[i] = make_float2((float)w.re, (float)w.im);
         }
-        dcplx suf = {1.0, 0.0};
-        for (int s = S - 1; s >= 0; --s) {
-            const dcplx oth = dmul(F, dmul(pre[s], suf));  // F prod_(j != s) H_j
-            const dcplx q0 = ddiv(oth, As[s]);             // dH/db_0
-            const dcplx q1 = dmul(q0, z1), q2 = dmul(q0, z2);
-            const dcplx a0 = ddiv(Ht, As[s]);              // -dH/da_k = z^k a0
-            const dcplx a1 = dmul(a0, z1), a2 = dmul(a0, z2);
-            // Re(conj(d) S)
-            acc[5 * s + 0] = q0.re * Sv.re + q0.im * Sv.im;
-            acc[5 * s + 1] = q1.re * Sv.re + q1.im * Sv.im;
-            acc[5 * s + 2] = q2.re * Sv.re + q2.im * Sv.im;
-            acc[5 * s + 3] = -(a1.re * Sv.re + a1.im * Sv.im);
-            acc[5 * s + 4] = -(a2.re * Sv.re + a2.im * Sv.im);
-            suf = dmul(suf, Hs[s]);
-        }
+        const dcplx q0 = dmul(dmul(F, dmul(pre, suf)), iA);  // dH/db_0 = F prod_(j != s) H_j / A_s
+        const dcplx q1 = dmul(q0, z1), q2 = dmul(q0, z2);
+        const dcplx h0 = dmul(dmul(F, Cs), iA);              // -dH/da_k = z^k H / A_s
+        const dcplx h1 = dmul(h0, z1), h2 = dmul(h0, z2);
+        // Re(conj(d) S)
+        acc[0] += q0.re * Sv.re + q0.im * Sv.im;
+        acc[1] += q1.re * Sv.re + q1.im * Sv.im;
+        acc[2] += q2.re * Sv.re + q2.im * Sv.im;
+        acc[3] -= h1.re * Sv.re + h1.im * Sv.im;
+        acc[4] -= h2.re * Sv.re + h2.im * Sv.im;
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const double invM = 1.0 / (double)M;
-    for (int q = 0; q < 5 * S; ++q) {
-        double v = acc[q];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red[q][warp] = v;
-    }
+    for (int k = 0; k < 5; ++k) red[warp][lane][k] = acc[k];
     __syncthreads();
-    if (threadIdx.x < 5 * S) {
-        const int q = threadIdx.x;
-        bpart[(int64_t)blockIdx.x * 5 * S + q] = (red[q][0] + red[q][1] + red[q][2] + red[q][3]) * invM;
+    // block sums per (section, term), in warp and slot order
+    const double invM = 1.0 / (double)M;
+    for (int q = threadIdx.x; q < 5 * S; q += blockDim.x) {
+        const int sq = q / 5, k = q % 5;
+        double v = 0.0;
+        for (int w = 0; w < GRADS_WARPS; ++w)
+            for (int b = 0; b < NB; ++b) v += red[w][b * S + sq][k];
+        bpart[(int64_t)blockIdx.x * 5 * S + q] = v * invM;
     }
     __threadfence();
     __syncthreads();
@@ -221,10 +272,15 @@ __global__ void __launch_bounds__(128) k_chain_grads_sec(const double2* __restri
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int q = threadIdx.x; q < 5 * S; q += blockDim.x) {
+    // warp w adds values q = w, w + GRADS_WARPS, ...: lane l the blocks
+    // l, l + 32, ... (independent loads), then a fixed shuffle tree
+    for (int q = warp; q < 5 * S; q += GRADS_WARPS) {
         double v = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) v += __ldcg(bpart + (int64_t)b * 5 * S + q);
-        sums[q] = v;
+#pragma unroll 4
+        for (unsigned b = lane; b < gridDim.x; b += 32) v += __ldcg(bpart + (int64_t)b * 5 * S + q);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sums[q] = v;
     }
     if (threadIdx.x == 0) *done = 0u;
 }
@@ -337,6 +393,7 @@ cudaError_t prepare_spectral(int m) {
 }
 
 cudaError_t launch_chain_xcorr(int m, const XcorrArgs& a, int grid, cudaStream_t s) {
+    if (a.items > INT32_MAX) return cudaErrorInvalidValue;  // 32-bit item indices
     switch (m) {
         case 12: return launch_xcorr_log<12>(a, grid, s);
         case 13: return launch_xcorr_log<13>(a, grid, s);
@@ -345,13 +402,15 @@ cudaError_t launch_chain_xcorr(int m, const XcorrArgs& a, int grid, cudaStream_t
 }
 
 cudaError_t launch_xcorr_reduce(const float2* part, int G, int M, double2* P, cudaStream_t s) {
-    k_xcorr_reduce<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(part, G, M, P);
+    k_xcorr_reduce<<<(unsigned)((M + 31) / 32), 32 * REDUCE_WARPS, 0, s>>>(part, G, M, P);
     return cudaGetLastError();
 }
 
 cudaError_t launch_chain_spectrum(const double* raw, int S, const float2* Hf, int m, float2* H, cudaStream_t s) {
     const int M = 1 << m;
-    k_chain_spectrum<<<(unsigned)((M + 127) / 128), 128, 0, s>>>(raw, S, Hf, m, H);
+    if (S < 1 || S > SPEC_SMAX) return cudaErrorInvalidValue;
+    const int warps = (M + 32 / S - 1) / (32 / S);
+    k_chain_spectrum<<<(unsigned)((warps + 3) / 4), 128, 0, s>>>(raw, S, Hf, m, H);
     return cudaGetLastError();
 }
 
@@ -365,8 +424,15 @@ cudaError_t launch_chain_tail(int m, const float2* H, const float2* tw, int J, i
     return cudaGetLastError();
 }
 
+// Blocks of the section-gradient kernel: about 6 warps per SM of bin
+// groups, at most one group per warp.
+int chain_grads_blocks(int m, int S) {
+    const int groups = ((1 << m) + 32 / S - 1) / (32 / S);
+    return std::max(1, std::min((groups + GRADS_WARPS - 1) / GRADS_WARPS, 2 * 152));
+}
+
 size_t chain_grads_scratch_bytes(int m, int S) {
-    return 256 + (size_t)(((1 << m) + 127) / 128) * 5 * S * sizeof(double);
+    return 256 + (size_t)chain_grads_blocks(m, S) * 5 * S * sizeof(double);
 }
 
 cudaError_t launch_chain_grads(int m, const double2* P, const double* raw, int S, const float2* Hf,
@@ -376,8 +442,8 @@ cudaError_t launch_chain_grads(int m, const double2* P, const double* raw, int S
     const int M = 1 << m;
     unsigned* done = static_cast<unsigned*>(scratch);
     double* bpart = reinterpret_cast<double*>(static_cast<char*>(scratch) + 256);
-    k_chain_grads_sec<<<(unsigned)((M + 127) / 128), 128, 0, s>>>(P, raw, S, Hf, m, bpart, done, sums,
-                                                                  dh ? wfir : nullptr);
+    k_chain_grads_sec<<<(unsigned)chain_grads_blocks(m, S), 32 * GRADS_WARPS, 0, s>>>(P, raw, S, Hf, m, bpart, done,
+                                                                                   sums, dh ? wfir : nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !dh) return e;
     const size_t smem = fir_fft_smem_bytes(M);
