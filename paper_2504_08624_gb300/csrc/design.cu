@@ -402,6 +402,7 @@ int refresh_spectral(tfx_plan* p, const double* coef, cudaStream_t s) {
         launch_fir_fft_spectrum(coef + p->spec_fir_dst, h.L, h.fft_M, h.fft_B, 0, tw, Hf, s) != cudaSuccess)
         return TFX_ERR_CUDA;
     if (launch_chain_spectrum(reinterpret_cast<const double*>(p->dconst + p->off_spec_raw), p->chain_S, Hf,
+                              reinterpret_cast<const double2*>(p->dconst + p->off_spec_z),
                               p->chain.fft_m, H, s) != cudaSuccess)
         return TFX_ERR_CUDA;
     if (launch_chain_tail(p->chain.fft_m, H, tw, p->chain.L - 1, p->dstatus, s) != cudaSuccess) return TFX_ERR_CUDA;

@@ -50,9 +50,16 @@ struct dcplx {
     double re, im;
 };
 __device__ __forceinline__ dcplx dmul(dcplx a, dcplx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+// 1 / b: the reciprocal of |b|^2 from the FP32 estimate refined by two
+// Newton steps (each doubles the correct bits: 24 -> 48 -> full), cheaper
+// than an FP64 division on this part; |b|^2 stays within FP32 range for the
+// denominators of stable sections (>= (1 - r)^4 with r <= 0.999).
 __device__ __forceinline__ dcplx drecip(dcplx b) {
-    const double d = 1.0 / (b.re * b.re + b.im * b.im);
-    return {b.re * d, -b.im * d};
+    const double d = b.re * b.re + b.im * b.im;
+    double r = (double)__frcp_rn((float)d);
+    r = r * fma(-d, r, 2.0);
+    r = r * fma(-d, r, 2.0);
+    return {b.re * r, -b.im * r};
 }
 
 // Section s's numerator and denominator at z (raw row: the a0 cancels in the
@@ -120,16 +127,21 @@ __global__ void __launch_bounds__(32 * REDUCE_WARPS) k_xcorr_reduce(const float2
     __shared__ double2 red[REDUCE_WARPS][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int i = blockIdx.x * 32 + lane;
-    double re = 0.0, im = 0.0;
+    // compensated (Kahan) FP32 sums per thread: FP64 adds are scarce on this part
+    float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
     if (i < M) {
 #pragma unroll 4
         for (int g = w; g < G; g += REDUCE_WARPS) {
             const float2 v = __ldcs(part + (int64_t)g * M + i);
-            re += v.x;
-            im += v.y;
+            const float yr = v.x - cr, tr = sr + yr;
+            cr = (tr - sr) - yr;
+            sr = tr;
+            const float yi = v.y - ci, ti = si + yi;
+            ci = (ti - si) - yi;
+            si = ti;
         }
     }
-    red[w][lane] = make_double2(re, im);
+    red[w][lane] = make_double2((double)sr - (double)cr, (double)si - (double)ci);
     __syncthreads();
     if (w == 0 && i < M) {
         double2 s = red[0][lane];
@@ -153,7 +165,8 @@ __device__ __forceinline__ dcplx shfl_c(dcplx v, int src) {
 // in): the FIR's spectrum Hf (already scaled) times prod_s B_s / A_s at the
 // bin of i, in FP64, one lane per (bin, section) as in k_chain_grads_sec.
 __global__ void __launch_bounds__(128) k_chain_spectrum(const double* __restrict__ raw, int S,
-                                                        const float2* __restrict__ Hf, int m, float2* __restrict__ H) {
+                                                        const float2* __restrict__ Hf, const double2* __restrict__ zt,
+                                                        int m, float2* __restrict__ H) {
     const int M = 1 << m, T = M / 16;
     const int lane = threadIdx.x & 31;
     const int NB = 32 / S, slot = lane / S, sec = lane % S;
@@ -166,9 +179,8 @@ __global__ void __launch_bounds__(128) k_chain_spectrum(const double* __restrict
     const bool live = active && i < M;
     const int ii = live ? i : 0;
     const int bin = bitrev_bits(pos_of_storage(ii, T), m);
-    double sn, cs;
-    sincospi(-2.0 * (double)bin / (double)M, &sn, &cs);
-    const dcplx z1 = {cs, sn}, z2 = dmul(z1, z1);
+    const double2 zb = zt[bin];
+    const dcplx z1 = {zb.x, zb.y}, z2 = dmul(z1, z1);
     const dcplx Bn = {b0 + b1 * z1.re + b2 * z2.re, b1 * z1.im + b2 * z2.im};
     const dcplx An = {1.0 + a1 * z1.re + a2 * z2.re, a1 * z1.im + a2 * z2.im};
     dcplx pin = dmul(Bn, drecip(An));
@@ -196,8 +208,9 @@ __global__ void __launch_bounds__(128) k_chain_spectrum(const double* __restrict
 // for the FIR tap gradients, in storage layout.
 constexpr int GRADS_WARPS = 4;
 __global__ void __launch_bounds__(32 * GRADS_WARPS) k_chain_grads_sec(
-    const double2* __restrict__ P, const double* __restrict__ raw, int S, const float2* __restrict__ Hf, int m,
-    double* __restrict__ bpart, unsigned* __restrict__ done, double* __restrict__ sums, float2* __restrict__ wfir) {
+    const double2* __restrict__ P, const double* __restrict__ raw, int S, const float2* __restrict__ Hf,
+    const double2* __restrict__ zt, int m, double* __restrict__ bpart, unsigned* __restrict__ done,
+    double* __restrict__ sums, float2* __restrict__ wfir) {
     __shared__ double red[GRADS_WARPS][32][5];
     __shared__ bool last;
     const int M = 1 << m, T = M / 16;
@@ -219,9 +232,8 @@ __global__ void __launch_bounds__(32 * GRADS_WARPS) k_chain_grads_sec(
         const int mir = (M - bin) & (M - 1);
         const double2 p = P[ii], pm = P[storage_of_pos(bitrev_bits(mir, m), T)];
         const dcplx Sv = {0.5 * (p.x + pm.x), 0.5 * (p.y - pm.y)};
-        double sn, cs;
-        sincospi(-2.0 * (double)bin / (double)M, &sn, &cs);
-        const dcplx z1 = {cs, sn}, z2 = dmul(z1, z1);
+        const double2 zb = zt[bin];
+        const dcplx z1 = {zb.x, zb.y}, z2 = dmul(z1, z1);
         const dcplx F = {(double)Hf[ii].x * M, (double)Hf[ii].y * M};
         const dcplx Bn = {b0 + b1 * z1.re + b2 * z2.re, b1 * z1.im + b2 * z2.im};
         const dcplx An = {1.0 + a1 * z1.re + a2 * z2.re, a1 * z1.im + a2 * z2.im};
@@ -406,11 +418,12 @@ cudaError_t launch_xcorr_reduce(const float2* part, int G, int M, double2* P, cu
     return cudaGetLastError();
 }
 
-cudaError_t launch_chain_spectrum(const double* raw, int S, const float2* Hf, int m, float2* H, cudaStream_t s) {
+cudaError_t launch_chain_spectrum(const double* raw, int S, const float2* Hf, const double2* zt, int m, float2* H,
+                                  cudaStream_t s) {
     const int M = 1 << m;
     if (S < 1 || S > SPEC_SMAX) return cudaErrorInvalidValue;
     const int warps = (M + 32 / S - 1) / (32 / S);
-    k_chain_spectrum<<<(unsigned)((warps + 3) / 4), 128, 0, s>>>(raw, S, Hf, m, H);
+    k_chain_spectrum<<<(unsigned)((warps + 3) / 4), 128, 0, s>>>(raw, S, Hf, zt, m, H);
     return cudaGetLastError();
 }
 
@@ -436,14 +449,14 @@ size_t chain_grads_scratch_bytes(int m, int S) {
 }
 
 cudaError_t launch_chain_grads(int m, const double2* P, const double* raw, int S, const float2* Hf,
-                               const float2* tw, int L, void* scratch, double* sums, float2* wfir, double* dh,
-                               cudaStream_t s) {
+                               const double2* zt, const float2* tw, int L, void* scratch, double* sums, float2* wfir,
+                               double* dh, cudaStream_t s) {
     if (S < 1 || S > SPEC_SMAX) return cudaErrorInvalidValue;
     const int M = 1 << m;
     unsigned* done = static_cast<unsigned*>(scratch);
     double* bpart = reinterpret_cast<double*>(static_cast<char*>(scratch) + 256);
-    k_chain_grads_sec<<<(unsigned)chain_grads_blocks(m, S), 32 * GRADS_WARPS, 0, s>>>(P, raw, S, Hf, m, bpart, done,
-                                                                                   sums, dh ? wfir : nullptr);
+    k_chain_grads_sec<<<(unsigned)chain_grads_blocks(m, S), 32 * GRADS_WARPS, 0, s>>>(P, raw, S, Hf, zt, m, bpart,
+                                                                                   done, sums, dh ? wfir : nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !dh) return e;
     const size_t smem = fir_fft_smem_bytes(M);

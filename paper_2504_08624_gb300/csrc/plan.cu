@@ -922,7 +922,9 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
             off = align_up(off + (size_t)u.S * sizeof(int64_t));
         }
     }
-    if (p->spectral) {  // the FIR's spectrum Hf and the twiddles, shared with the chain
+    if (p->spectral) {  // the bins' z, the FIR's spectrum Hf and the twiddles (shared with the chain)
+        p->off_spec_z = off;
+        off = align_up(off + (size_t)p->spec_fir.fft_M * sizeof(double2));
         p->spec_fir.off_H = off;
         off = align_up(off + (size_t)p->spec_fir.fft_M * sizeof(float2));
         p->spec_fir.off_tw = off;
@@ -1012,8 +1014,15 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
                     }
         }
     }
-    if (p->spectral)
+    if (p->spectral) {
         fill_fft_tables(p->spec_fir, host.data());  // the chain's spectrum follows on the device
+        const int M = p->spec_fir.fft_M;
+        double2* zt = reinterpret_cast<double2*>(host.data() + p->off_spec_z);
+        for (int k = 0; k < M; ++k) {
+            const double ang = -2.0 * M_PI * (double)k / (double)M;
+            zt[k] = make_double2(std::cos(ang), std::sin(ang));
+        }
+    }
     else if (p->use_chain)
         fill_fft_tables(p->chain, host.data());
     for (int32_t i = 0; i < nst; ++i) {
@@ -1075,6 +1084,7 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
             if (prepare_spectral(p->chain.fft_m) != cudaSuccess) return TFX_ERR_UNSUPPORTED;
             if (launch_chain_spectrum(reinterpret_cast<const double*>(p->dconst + p->off_spec_raw), p->chain_S,
                                       reinterpret_cast<const float2*>(p->dconst + p->spec_fir.off_H),
+                                      reinterpret_cast<const double2*>(p->dconst + p->off_spec_z),
                                       p->chain.fft_m, reinterpret_cast<float2*>(p->dconst + p->chain.off_H),
                                       nullptr) != cudaSuccess ||
                 cudaStreamSynchronize(nullptr) != cudaSuccess)
@@ -1441,6 +1451,7 @@ int run_backward_spectral(tfx_plan* p, const float* x, const float* g, float* dx
         nl += p->spec_nfir ? 2 : 1;
         if (!count_only &&
             launch_chain_grads(m, P, raw, p->chain_S, reinterpret_cast<const float2*>(p->dconst + p->spec_fir.off_H),
+                               reinterpret_cast<const double2*>(p->dconst + p->off_spec_z),
                                tw, p->spec_fir.L, ws + p->b_sp_gs, sums, reinterpret_cast<float2*>(ws + p->b_sp_w),
                                p->spec_nfir ? dcoef + p->spec_fir_dst : nullptr, s) != cudaSuccess)
             return TFX_ERR_CUDA;

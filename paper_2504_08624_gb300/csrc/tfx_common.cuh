@@ -400,14 +400,16 @@ int xcorr_ctas_per_sm(int m);
 cudaError_t prepare_spectral(int m);
 cudaError_t launch_chain_xcorr(int m, const XcorrArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_xcorr_reduce(const float2* part, int G, int M, double2* P, cudaStream_t s);
-cudaError_t launch_chain_spectrum(const double* raw, int S, const float2* Hf, int m, float2* H, cudaStream_t s);
+// zt: e^(-2 pi i k / M) for bins k < M (FP64, plan constant).
+cudaError_t launch_chain_spectrum(const double* raw, int S, const float2* Hf, const double2* zt, int m, float2* H,
+                                  cudaStream_t s);
 cudaError_t launch_chain_tail(int m, const float2* H, const float2* tw, int J, int* status, cudaStream_t s);
 // Scratch of launch_chain_grads: a completion counter (zeroed before the
 // launch) and the blocks' partial sums.
 size_t chain_grads_scratch_bytes(int m, int S);
 cudaError_t launch_chain_grads(int m, const double2* P, const double* raw, int S, const float2* Hf,
-                               const float2* tw, int L, void* scratch, double* sums, float2* wfir, double* dh,
-                               cudaStream_t s);
+                               const double2* zt, const float2* tw, int L, void* scratch, double* sums, float2* wfir,
+                               double* dh, cudaStream_t s);
 cudaError_t launch_fir_fft_batched(int m, const BatchFft* units, const int64_t* prefix, int nunits, int64_t ctas,
                                    BatchBases bases, const float2* tw, cudaStream_t s);
 cudaError_t launch_fir_fft_spectrum(const double* taps, int L, int M, int B, int P, const float2* tw, float2* H,
