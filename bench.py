@@ -476,18 +476,22 @@ def measure_fwdbwd(wl, steps, warmup, dev, stream, torch, dist, ws, rank, pk, sm
     dx = torch.empty_like(x)
     dcoef = torch.empty(plan.coef_count, dtype=torch.float64, device=dev)
 
+    lossbuf = torch.empty(1, dtype=torch.float64, device=dev)
+
     def fwd():
         plan.forward_train(x, y, saved, fws)
 
     def loss_step():
         return api.mse(y, target, g)
 
+    def fwd_loss():  # the training forward with the loss fused (tfx_plan_forward_train_mse)
+        plan.forward_train_mse(x, y, target, g, lossbuf, saved, fws)
+
     def bwd():
         plan.backward(x, g, dx, dcoef, saved, bws)
 
     def step():
-        fwd()
-        loss_step()
+        fwd_loss()
         bwd()
 
     for _ in range(warmup):
@@ -524,10 +528,12 @@ def measure_fwdbwd(wl, steps, warmup, dev, stream, torch, dist, ws, rank, pk, sm
     t_f = time_gpu(fwd, k_parts, 2, stream, torch, None) / k_parts
     t_l = time_gpu(loss_step, k_parts, 2, stream, torch, None) / k_parts
     t_b = time_gpu(bwd, k_parts, 2, stream, torch, None) / k_parts
+    t_fl = time_gpu(fwd_loss, k_parts, 2, stream, torch, None) / k_parts
+    fwd_loss()
     torch.cuda.synchronize()
     # y, g, dx and dcoef now hold one consistent training step
     parity = fwdbwd_parity(wl, x, y, g, dx, torch, api, NAT) if (with_parity and rank == 0) else None
-    launches = plan.launches_per_execute + 1 + plan.backward_launches(True, True)
+    launches = plan.forward_train_mse_launches + plan.backward_launches(True, True)
     step_s = t / steps
 
     route = plan.describe()
@@ -635,9 +641,11 @@ def measure_fwdbwd(wl, steps, warmup, dev, stream, torch, dist, ws, rank, pk, sm
                          f"{dt:.1f} s"}
     plan.close()
     return {"workload": wl.name, "value": units * ws * steps / t_all, "unit": UNIT, "ms_per_step": step_s * 1e3,
-            "steps": steps, "step": "training forward + MSE loss and dL/dy + backward (dL/dx, dL/dcoef)",
+            "steps": steps, "step": "training forward with the MSE loss and dL/dy fused (tfx_plan_forward_train_mse) "
+                                    "+ backward (dL/dx, dL/dcoef)",
             "cuda_graph": graph is not None, "eager_ms_per_step": t_eager / steps * 1e3,
-            "fwd_ms": t_f * 1e3, "loss_ms": t_l * 1e3, "bwd_ms": t_b * 1e3, "gpu_launches_per_step": launches,
+            "fwd_ms": t_f * 1e3, "loss_ms": t_l * 1e3, "fwd_loss_ms": t_fl * 1e3, "bwd_ms": t_b * 1e3,
+            "gpu_launches_per_step": launches,
             "route": route, "parts_ms": parts,
             "roofline": roof, "roofline_hbm": hbm, "e2e": e2e, "cpu_baseline": cpu, "parity": parity,
             "dtype": "f32", "plain_gpu": None}
@@ -1131,7 +1139,7 @@ def run_fwdbwd_main(args, wl, dev, torch, dist, ws, rank, local):
             "roofline": r["roofline"], "roofline_hbm": r["roofline_hbm"], "cpu_baseline": r["cpu_baseline"],
             "e2e": r["e2e"], "plain_gpu": r["plain_gpu"],
             "gpu_launches": int(args.steps * r["gpu_launches_per_step"]), "clocks": clocks, "gpu": props.name,
-            "fwd_ms": r["fwd_ms"], "loss_ms": r["loss_ms"], "bwd_ms": r["bwd_ms"], "parity": r["parity"],
+            "fwd_ms": r["fwd_ms"], "loss_ms": r["loss_ms"], "fwd_loss_ms": r["fwd_loss_ms"], "bwd_ms": r["bwd_ms"], "parity": r["parity"],
             "fp32_peak": fp32,
         }), flush=True)
     if dist is not None:

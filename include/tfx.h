@@ -126,18 +126,24 @@ typedef struct {
  * cascades' impulse response g decays it is run by default as ONE kernel:
  * the composite impulse response h_c = g * f (f: every FIR's taps
  * convolved) is formed in FP64 at plan time, g truncated at the first D
- * samples beyond which sum|g| x sum|f| is below 1e-8 of the chain's RMS gain
+ * samples beyond which sum|g| x sum|f| is below 1e-7 of the chain's RMS gain
  * ||h_c||_2 (g must have decayed within 65536 samples: the last 4096 of them
  * below 1e-14 of sum|g|; otherwise the chain keeps its separate units), and
  * the signal is filtered by FFT overlap-save with h_c (single-block,
  * M = 4096..16384 points), so it crosses HBM once.  The truncation changes
- * no output by more than 1e-8 ||h_c||_2 max|x|; the FP32 transforms round
+ * no output by more than 1e-7 ||h_c||_2 max|x|; the FP32 transforms round
  * relative to each block's energy.  Chosen when the signal holds at least
  * 2 (D + L - 1) samples and a cost model fitted to GB300 timings predicts it
- * faster than the separate units; plans with TFX_PLAN_TRAINABLE, a
- * tensor-core, CUDA-core, transform-size or scan flag, or a pole of radius
- * > 0.999 never take it.  tfx_plan_update_sos switches such a plan back to
- * its separate units.  This flag disables the composition. */
+ * faster than the separate units; plans with a tensor-core, CUDA-core,
+ * transform-size or scan flag, or a pole of radius > 0.999 never take it.
+ * tfx_plan_update_sos switches such a plan back to its separate units.
+ * A TFX_PLAN_TRAINABLE plan composes by its closed-form spectrum instead
+ * (at most 16 sections, at most one FIR; see tfx_plan_backward): the
+ * transfer function is evaluated at the transform's bins, so the response
+ * is not truncated, the overlap J covers 1.5 D + L - 1 samples (at least
+ * M/4; M = 4096 or 8192), and coefficient updates rebuild the spectrum on
+ * the device and check that the response still decays within J
+ * (TFX_ERR_DECAY otherwise).  This flag disables the composition. */
 #define TFX_PLAN_NO_COMPOSE 1024u
 /* Test hook for failure detection: the first tile of channel 0 never publishes
  * its carries, so its successor's bounded wait runs out; the execution
@@ -234,7 +240,10 @@ void tfx_plan_destroy(tfx_plan *p);
  *                           the first (an intermediate of the chain), and
  *                           each cascade's state at every 32-sample chunk
  *                           start (8 bytes per section per chunk); 0 for a
- *                           plan without TFX_PLAN_TRAINABLE.
+ *                           plan without TFX_PLAN_TRAINABLE and for a plan
+ *                           on the spectral route (it saves nothing).
+ * tfx_plan_describe names the route: "chain_spectral:..." for the spectral
+ * route, the units otherwise.
  * tfx_plan_backward_workspace_size : bytes of backward workspace (0 likewise).
  * tfx_plan_coef_count     : doubles in dcoef (-1 for a NULL plan).
  */
@@ -256,15 +265,43 @@ int tfx_plan_forward_train(tfx_plan *p, const float *x, float *y, void *saved,
                            tfx_stream s);
 
 /*
+ * tfx_plan_forward_train_mse -- tfx_plan_forward_train followed by tfx_mse
+ * against `target` (device, [C x N], the plan's row stride): y, the saved
+ * state, g = dL/dy = 2 (y - target) / (C N) and *loss = mean((y - target)^2)
+ * (device FP64 scalar, reset on s first).  On the spectral route the loss
+ * is computed in the filter kernel's store (one launch: y is not read back);
+ * otherwise the units, then the loss kernel.  g may be target (it replaces
+ * it); no other buffers may overlap.  Asynchronous, no allocation,
+ * capturable.  The loss is summed in FP32 per thread and FP64 across
+ * threads, CTAs added by atomics (its last bits may vary between calls; y
+ * and g do not).
+ * tfx_plan_forward_train_mse_launch_count: kernels it launches (-1 if not
+ * trainable).
+ * Errors: as tfx_plan_forward_train; TFX_ERR_INVALID for a NULL loss, target
+ * or g, or overlapping buffers.
+ */
+int tfx_plan_forward_train_mse(tfx_plan *p, const float *x, float *y,
+                               const float *target, float *g, double *loss,
+                               void *saved, size_t saved_bytes, void *ws,
+                               size_t ws_bytes, tfx_stream s);
+int tfx_plan_forward_train_mse_launch_count(const tfx_plan *p);
+
+/*
  * tfx_plan_backward -- given the x and `saved` of a training forward (not
  * modified since) and g = dL/dy (device, [C x N], the plan's row stride),
  * write dx (may be NULL: not computed; may equal g; must not overlap x) and
  * dcoef (device FP64, tfx_plan_coef_count values, fully overwritten; may be
  * NULL: not computed).  ws: device, >= tfx_plan_backward_workspace_size
- * bytes, 256-byte aligned.  The SOS cascades run as reverse-time adjoint
- * scans that recompute their section outputs from the saved chunk-start
- * states; FIRs as the FIR over the time-reversed gradient plus a tap
- * correlation.  Asynchronous, no allocation, capturable; a device-side
+ * bytes, 256-byte aligned.  Spectral route (a chain that composes; see
+ * TFX_PLAN_NO_COMPOSE): dx is the chain over the time-reversed gradient
+ * by the forward's FFT kernel, and dcoef comes from the cross-spectrum of g
+ * and x (accumulated by blocks) paired with the closed-form derivative
+ * spectra of every section coefficient and one inverse transform for the
+ * FIR taps; every reduction has a fixed order, so repeated calls give
+ * bit-identical results.  Otherwise the SOS cascades run as reverse-time
+ * adjoint scans that recompute their section outputs from the saved
+ * chunk-start states; FIRs as the FIR over the time-reversed gradient plus a
+ * tap correlation.  Asynchronous, no allocation, capturable; a device-side
  * timeout is reported by tfx_plan_get_error.
  * Errors: TFX_ERR_INVALID, TFX_ERR_WORKSPACE, TFX_ERR_CUDA.
  */
@@ -510,7 +547,11 @@ int64_t tfx_plan_sos_rows(const tfx_plan *p);
  * their spectra (FP32 transform of the taps, as the filter's own).  The
  * plan's structure stays as created (units, kernels, transform sizes, the
  * FP64-carry routing); a tensor-core cascade runs the look-back scan and a
- * composed chain its separate units from the first update on.  FIRs on the
+ * composed chain its separate units from the first update on; a plan on
+ * the spectral route keeps it: the FIR's spectrum and the chain's
+ * closed-form spectrum are rebuilt on the GPU, and a response that no
+ * longer decays within the plan's overlap sets TFX_ERR_DECAY in the status
+ * read by tfx_plan_get_error (recreate the plan).  FIRs on the
  * tensor cores (tap tables scaled on the host) are TFX_ERR_UNSUPPORTED.  The
  * first call builds the update descriptors (host-synchronous: make it before
  * any capture); later calls are tfx_plan_update_coefs_launch_count launches,

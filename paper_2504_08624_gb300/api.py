@@ -243,6 +243,29 @@ class Plan:
         N.check(rc, "tfx_plan_forward_train")
         return y
 
+    def forward_train_mse(self, x: torch.Tensor, y: torch.Tensor, target: torch.Tensor, g: torch.Tensor,
+                          loss: torch.Tensor, saved: torch.Tensor, ws: torch.Tensor | None = None) -> torch.Tensor:
+        """Training forward with the MSE against ``target`` fused in
+        (tfx_plan_forward_train_mse): fills y, saved, g = dL/dy and the
+        device FP64 scalar ``loss``; returns loss."""
+        x2, y2, w = self._args(x, y, ws)
+        t2, g2, _ = self._args(target, g, ws)
+        if not loss.is_cuda or loss.dtype != torch.float64 or loss.numel() < 1:
+            raise ValueError("loss: CUDA float64 tensor")
+        with torch.cuda.device(self.device):
+            rc = N.lib().tfx_plan_forward_train_mse(
+                self._h, ctypes.c_void_p(x2.data_ptr()), ctypes.c_void_p(y2.data_ptr()),
+                ctypes.c_void_p(t2.data_ptr()), ctypes.c_void_p(g2.data_ptr()),
+                ctypes.cast(ctypes.c_void_p(loss.data_ptr()), ctypes.POINTER(ctypes.c_double)),
+                ctypes.c_void_p(saved.data_ptr()), saved.numel(), ctypes.c_void_p(w.data_ptr()), w.numel(),
+                _stream_handle(self.device))
+        N.check(rc, "tfx_plan_forward_train_mse")
+        return loss
+
+    @property
+    def forward_train_mse_launches(self) -> int:
+        return int(N.lib().tfx_plan_forward_train_mse_launch_count(self._h))
+
     def backward(self, x: torch.Tensor, g: torch.Tensor, dx: torch.Tensor | None, dcoef: torch.Tensor | None,
                  saved: torch.Tensor, ws: torch.Tensor | None = None) -> None:
         x2, g2, _ = self._args(x, g, None)

@@ -357,5 +357,53 @@ __device__ __forceinline__ void store_pair(const float2 (&v)[16], float* y0, flo
     }
 }
 
+// store_pair (forward time) with the MSE fused: each output y also gives
+// d = y - t (t the target at the same place) and the gradient gs d (rows
+// t0 / t1 and g0 / g1 laid out like y0 / y1); returns this thread's sum of
+// d^2 (FP32, at most 32 terms).
+template <int LOGM>
+__device__ __forceinline__ float store_pair_mse(const float2 (&v)[16], float* y0, float* y1, const float* t0,
+                                                const float* t1, float* g0, float* g1, int64_t b0, int64_t b1,
+                                                int first, int m0, int m1, int t, float gs) {
+    using F = FftShape<LOGM>;
+    const int64_t o0 = b0 - first + t, o1 = b1 - first + t;
+    float* py0 = y0 + o0;
+    float* py1 = y1 + o1;
+    const float* pt0 = t0 + o0;
+    const float* pt1 = t1 + o1;
+    float* pg0 = g0 + o0;
+    float* pg1 = g1 + o1;
+    const int oo = t - first;
+    float acc = 0.f;
+    // four registers' targets in flight at a time
+#pragma unroll
+    for (int j0 = 0; j0 < 16; j0 += 4) {
+        float tv0[4], tv1[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int o = oo + F::T * (j0 + j);
+            tv0[j] = (unsigned)o < (unsigned)m0 ? __ldcs(pt0 + F::T * (j0 + j)) : 0.f;
+            tv1[j] = (unsigned)o < (unsigned)m1 ? __ldcs(pt1 + F::T * (j0 + j)) : 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int o = oo + F::T * (j0 + j);
+            if ((unsigned)o < (unsigned)m0) {
+                py0[F::T * (j0 + j)] = v[j0 + j].x;
+                const float d = v[j0 + j].x - tv0[j];
+                pg0[F::T * (j0 + j)] = d * gs;
+                acc = fmaf(d, d, acc);
+            }
+            if ((unsigned)o < (unsigned)m1) {
+                py1[F::T * (j0 + j)] = v[j0 + j].y;
+                const float d = v[j0 + j].y - tv1[j];
+                pg1[F::T * (j0 + j)] = d * gs;
+                acc = fmaf(d, d, acc);
+            }
+        }
+    }
+    return acc;
+}
+
 }  // namespace
 }  // namespace tfx

@@ -46,8 +46,9 @@ namespace {
 
 // One block pair of the single-block scheme: blocks 2pr and 2pr + 1.  REV:
 // input and output rows in reverse time (the transposed chain, y = R h R x,
-// for the input gradient of a training step).
-template <int LOGM, bool REV = false>
+// for the input gradient of a training step).  MSE: the training loss and
+// its gradient fused into the store (FirFftArgs::loss).
+template <int LOGM, bool REV = false, bool MSE = false>
 __device__ __forceinline__ void fft_block_pair(const FirFftArgs& a, int64_t pr, float2* sb, int t) {
     using F = FftShape<LOGM>;
     const int Hh = a.L - 1;
@@ -75,14 +76,32 @@ __device__ __forceinline__ void fft_block_pair(const FirFftArgs& a, int64_t pr, 
     inverse_from<LOGM, F::NP - 1, last_forward_group<LOGM>()>(v, a.tw, sb, t);
     const int m0 = (int)(a.N - n00 < a.B ? a.N - n00 : a.B);
     const int m1 = live1 ? (int)(a.N - n01 < a.B ? a.N - n01 : a.B) : 0;
-    store_pair<LOGM, REV>(v, a.y + c0 * a.ldy, a.y + c1 * a.ldy, n00, n01, a.N, Hh, m0, m1, t);
+    if constexpr (!MSE) {
+        store_pair<LOGM, REV>(v, a.y + c0 * a.ldy, a.y + c1 * a.ldy, n00, n01, a.N, Hh, m0, m1, t);
+    } else {
+        __shared__ double red[32];
+        const float accf = store_pair_mse<LOGM>(v, a.y + c0 * a.ldy, a.y + c1 * a.ldy, a.tgt + c0 * a.ldy,
+                                                a.tgt + c1 * a.ldy, a.gout + c0 * a.ldy, a.gout + c1 * a.ldy, n00,
+                                                n01, Hh, m0, m1, t, a.gscale);
+        // FP32 per thread, FP64 across threads (as k_mse)
+        double acc = (double)accf;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((t & 31) == 0) red[t >> 5] = acc;
+        __syncthreads();
+        if (t == 0) {
+            double sum = 0.0;
+            for (int w = 0; w < FftShape<LOGM>::T / 32; ++w) sum += red[w];
+            atomicAdd(a.loss, sum * a.lscale);
+        }
+    }
 }
 
 // Single-block overlap-save: CTA k transforms blocks 2k and 2k + 1.
-template <int LOGM, bool REV>
+template <int LOGM, bool REV, bool MSE = false>
 __global__ void __launch_bounds__((1 << LOGM) / 16, 16384 >> LOGM) k_fir_fft(FirFftArgs a) {
     extern __shared__ float2 sb[];
-    fft_block_pair<LOGM, REV>(a, blockIdx.x, sb, threadIdx.x);
+    fft_block_pair<LOGM, REV, MSE>(a, blockIdx.x, sb, threadIdx.x);
 }
 
 // Single-block overlap-save over many clips in one launch (a batch of
@@ -231,7 +250,10 @@ cudaError_t launch_log(const FirFftArgs& a, cudaStream_t s) {
     constexpr int T = (1 << LOGM) / 16;
     const size_t smem = fir_fft_smem_bytes(1 << LOGM);
     if (a.P == 0) {
-        if (a.rev)
+        if (a.loss && a.rev) return cudaErrorInvalidValue;
+        if (a.loss)
+            k_fir_fft<LOGM, false, true><<<(unsigned)((a.nb + 1) / 2), T, smem, s>>>(a);
+        else if (a.rev)
             k_fir_fft<LOGM, true><<<(unsigned)((a.nb + 1) / 2), T, smem, s>>>(a);
         else
             k_fir_fft<LOGM, false><<<(unsigned)((a.nb + 1) / 2), T, smem, s>>>(a);
@@ -251,6 +273,8 @@ cudaError_t prepare_log() {
     cudaError_t e = cudaFuncSetAttribute(k_fir_fft<LOGM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_fir_fft<LOGM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fir_fft<LOGM, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_fir_fft_spec<LOGM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
@@ -314,6 +338,7 @@ cudaError_t launch_fir_fft_spectrum(const double* taps, int L, int M, int B, int
 cudaError_t launch_fir_fft(const FirFftArgs& a, cudaStream_t s) {
     if (a.nb <= 0) return cudaSuccess;
     if (a.nb > INT32_MAX || (a.P > 0 && (a.C + 1) / 2 * a.nbpc > INT32_MAX)) return cudaErrorInvalidValue;
+    if (a.loss && a.P > 0) return cudaErrorInvalidValue;  // the fused loss is single-block only
     switch (a.m) {
         case 10: return launch_log<10>(a, s);
         case 11: return launch_log<11>(a, s);

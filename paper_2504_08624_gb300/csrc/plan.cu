@@ -504,10 +504,15 @@ double unit_cost_estimate(const HostUnit& u) {
     return 40.0 + 2.0 * u.L;             // CUDA-core FIR
 }
 
+// Truncation threshold of the composite response, relative to the chain's
+// RMS gain: at this level the dropped tail is no larger than the FP32
+// transform's own rounding of the outputs (a few 1e-7 of the output peak).
+constexpr double COMPOSE_EPS = 1e-7;
+
 // The cascades' impulse response g (sections [S][5] in chain order, FP64,
 // zero state) over 65536 samples and the length D it is truncated to when it
 // is convolved with the FIR taps f: the first D for which
-// sum_(n >= D) |g[n]| * sum |f| <= 1e-8 ||g * f||_2.  False when g has not
+// sum_(n >= D) |g[n]| * sum |f| <= 1e-7 ||g * f||_2 (COMPOSE_EPS).  False when g has not
 // decayed by the end (the absolute sum of its last 4096 samples above 1e-14
 // of the whole) or the chain's response is zero.
 bool cascade_decay(const std::vector<double>& sec, int S, const std::vector<double>& f, std::vector<double>& g,
@@ -543,7 +548,7 @@ bool cascade_decay(const std::vector<double>& sec, int S, const std::vector<doub
     D = W;
     double tail = 0.0;
     for (int n = W - 1; n >= 1; --n) {
-        if ((tail + std::fabs(g[n])) * f1 > 1e-8 * n2) {
+        if ((tail + std::fabs(g[n])) * f1 > COMPOSE_EPS * n2) {
             D = n + 1;
             break;
         }
@@ -559,7 +564,7 @@ bool cascade_decay(const std::vector<double>& sec, int S, const std::vector<doub
 // state) is computed over 65536 samples and must have decayed there (the
 // absolute sum of its last 4096 samples below 1e-14 of the whole).  With f
 // every FIR's taps convolved (FP64), g is truncated at the first D for which
-// sum_(n >= D) |g[n]| * sum |f| <= 1e-8 ||h_c||_2: the truncated tail changes
+// sum_(n >= D) |g[n]| * sum |f| <= 1e-7 ||h_c||_2: the truncated tail changes
 // no output by more than that times max|x|, and ||h_c||_2 is the chain's RMS
 // gain for white input (taken over the first 16384 samples of h_c = g * f, a
 // lower bound).  The composite h_c = g[0, D) * f has Lc = D + Lf - 1 taps and
@@ -1868,6 +1873,65 @@ int tfx_plan_forward_train(tfx_plan* p, const float* x, float* y, void* saved, s
     if (bytes_overlap(saved, p->saved_bytes, x, span) || bytes_overlap(saved, p->saved_bytes, y, span))
         return TFX_ERR_INVALID;
     return exec_train(p, x, y, static_cast<char*>(saved), ws, reinterpret_cast<cudaStream_t>(s));
+}
+
+int tfx_plan_forward_train_mse(tfx_plan* p, const float* x, float* y, const float* target, float* g, double* loss,
+                               void* saved, size_t saved_bytes, void* ws, size_t ws_bytes, tfx_stream s) {
+    if (!p || !p->train || !loss) return TFX_ERR_INVALID;
+    int rc = check_exec_args(p, x, y, ws, ws_bytes, p->ws_fused);
+    if (rc != TFX_OK) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+    if (p->C == 0 || p->N == 0)
+        return cudaMemsetAsync(loss, 0, sizeof(double), st) == cudaSuccess ? TFX_OK : TFX_ERR_CUDA;
+    if (x == y || !target || !g) return TFX_ERR_INVALID;
+    const size_t span = signal_span(p->C, p->N, p->ld);
+    // g may take the target's place; nothing else may overlap
+    if (bytes_overlap(g, span, x, span) || bytes_overlap(g, span, y, span) ||
+        (g != target && bytes_overlap(g, span, target, span)) || bytes_overlap(target, span, y, span) ||
+        bytes_overlap(loss, sizeof(double), g, span) || bytes_overlap(loss, sizeof(double), y, span))
+        return TFX_ERR_INVALID;
+    if (p->saved_bytes > 0 &&
+        (!saved || saved_bytes < p->saved_bytes || reinterpret_cast<uintptr_t>(saved) % ALIGN != 0))
+        return TFX_ERR_WORKSPACE;
+    if (bytes_overlap(saved, p->saved_bytes, x, span) || bytes_overlap(saved, p->saved_bytes, y, span))
+        return TFX_ERR_INVALID;
+    const double inv = 1.0 / ((double)p->C * (double)p->N);
+    if (!p->spectral) {  // the units, then the loss kernel
+        rc = exec_train(p, x, y, static_cast<char*>(saved), ws, st);
+        if (rc != TFX_OK) return rc;
+        return launch_mse(y, target, g, p->C, p->N, p->ld, loss, st) == cudaSuccess ? TFX_OK : TFX_ERR_CUDA;
+    }
+    // spectral route: one FFT launch writes y, g and the loss
+    if (cudaMemsetAsync(loss, 0, sizeof(double), st) != cudaSuccess) return TFX_ERR_CUDA;
+    const HostUnit& c = p->chain;
+    FirFftArgs f{};
+    f.x = x;
+    f.ldx = p->ld;
+    f.y = y;
+    f.ldy = p->ld;
+    f.C = p->C;
+    f.N = p->N;
+    f.L = c.L;
+    f.M = c.fft_M;
+    f.m = c.fft_m;
+    f.B = c.fft_B;
+    f.P = 0;
+    f.nbpc = c.ntt;
+    f.nb = p->C * c.ntt;
+    f.H = reinterpret_cast<const float2*>(p->dconst + c.off_H);
+    f.tw = reinterpret_cast<const float2*>(p->dconst + c.off_tw);
+    f.tgt = target;
+    f.gout = g;
+    f.loss = loss;
+    f.gscale = (float)(2.0 * inv);
+    f.lscale = inv;
+    return launch_fir_fft(f, st) == cudaSuccess ? TFX_OK : TFX_ERR_CUDA;
+}
+
+int tfx_plan_forward_train_mse_launch_count(const tfx_plan* p) {
+    if (!p || !p->train) return -1;
+    if (p->C == 0 || p->N == 0) return 0;
+    return p->spectral ? 1 : tfx_plan_launch_count(p) + 1;
 }
 
 int tfx_plan_backward(tfx_plan* p, const float* x, const float* g, float* dx, double* dcoef, const void* saved,

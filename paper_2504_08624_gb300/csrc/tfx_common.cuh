@@ -192,6 +192,15 @@ struct FirFftArgs {
     int P;             // 0: single-block overlap-save; else partitions of B = M/2 taps
     float2* Z;         // partitioned: [ceil(C/2)][nbpc][M] segment spectra (workspace)
     int rev;           // single-block: rows of x and y in reverse time (the transposed filter)
+    // single-block, forward time: the MSE against tgt fused into the store
+    // (rows with stride ldy): gout = gscale (y - tgt), and the sum of
+    // (y - tgt)^2 times lscale added into *loss (one FP64 atomic per CTA);
+    // loss == nullptr: plain filter
+    const float* tgt;
+    float* gout;
+    double* loss;
+    float gscale;
+    double lscale;
 };
 
 // One composed clip of a batch (the whole chain as one FFT FIR): where its

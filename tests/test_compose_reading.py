@@ -3,8 +3,8 @@ cascades and FIRs is linear and time-invariant (TorchFX Sec. 3: the pipe
 composes the stages), so it equals the causal convolution with its
 composite impulse response h_c = g * f (g: the cascades' impulse response,
 f: every FIR's taps convolved).  The plan truncates g at the first D with
-sum_(n >= D) |g[n]| * sum|f| <= 1e-8 ||h_c||_2, which bounds the change of
-every output by 1e-8 ||h_c||_2 max|x|.
+sum_(n >= D) |g[n]| * sum|f| <= 1e-7 ||h_c||_2, which bounds the change of
+every output by 1e-7 ||h_c||_2 max|x|.
 
 Here D and h_c are derived in code of the test's own (g from the FP64
 oracle run on an impulse), and the premise is checked against the oracle's
@@ -17,7 +17,7 @@ import oracle
 from paper_2504_08624_gb300 import workloads as W
 
 
-def _composite(stages, W_len=65536, eps=1e-8):
+def _composite(stages, W_len=65536, eps=1e-7):
     lib = oracle.load()
     sos = [st for st in stages if st[0] == "sos"]
     imp = np.zeros(W_len)
@@ -48,7 +48,7 @@ def test_composite_matches_stage_by_stage_within_the_bound():
     assert decayed and 0 < D < 65536
     x = wl.make_signal(2, 60000).astype(np.float64)
     ref = oracle.chain(x, wl.stages)
-    bound = 1e-8 * n2 * np.max(np.abs(x))
+    bound = 1e-7 * n2 * np.max(np.abs(x))
     y = _conv_causal(x, np.convolve(g[:D], f))
     err = np.max(np.abs(y - ref))
     # FP64 transform rounding adds ~1e-15 of the signal on top of the truncation
@@ -68,7 +68,7 @@ def test_composite_of_interleaved_stages():
     x = W.white_uniform(2, 30000, 3).astype(np.float64)
     ref = oracle.chain(x, stages)
     y = _conv_causal(x, np.convolve(g[:D], f))
-    bound = 1e-8 * n2 * np.max(np.abs(x))
+    bound = 1e-7 * n2 * np.max(np.abs(x))
     assert np.max(np.abs(y - ref)) <= bound + 1e-13 * np.max(np.abs(ref))
 
 

@@ -246,3 +246,43 @@ def test_spectral_full_size_differentiable_chain():
         assert np.max(np.abs(dx[c, idx] - ref)) <= 1e-4 * np.max(np.abs(dx[c])), c
     assert_close(y[:2], lib.chain(x[:2], w.stages), 1e-4, "training forward")
     print(f"full-size spectral gradients: worst {worst:.2e} of the stage's largest gradient")
+
+
+@pytest.mark.parametrize("route", ["spectral", "units"])
+def test_forward_train_mse_fused(route):
+    """tfx_plan_forward_train_mse equals tfx_plan_forward_train followed by
+    tfx_mse: y and g bit for bit, the loss to FP64 summation order; g may
+    replace the target; the backward from the fused g is the same."""
+    from paper_2504_08624_gb300 import api, _native
+    stages = chain("differentiable_chain")
+    C, N = 5, 20000
+    p = plan(C, N, stages, 0 if route == "spectral" else _native.TFX_PLAN_NO_COMPOSE)
+    assert (p.describe()[0]["kind"] == "chain_spectral") == (route == "spectral")
+    assert p.forward_train_mse_launches == (1 if route == "spectral" else p.launches_per_execute + 1)
+    x = torch.from_numpy(W.white_gauss(C, N, 70).astype(np.float32)).cuda()
+    tgt = torch.from_numpy(W.white_gauss(C, N, 71).astype(np.float32)).cuda()
+    saved = p.new_saved()
+    y1, g1 = torch.empty_like(x), torch.empty_like(x)
+    p.forward_train(x, y1, saved)
+    l1 = api.mse(y1, tgt, g1)
+    y2, g2 = torch.full_like(x, float("nan")), torch.full_like(x, float("nan"))
+    l2 = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    saved2 = p.new_saved()
+    p.forward_train_mse(x, y2, tgt, g2, l2, saved2)
+    t3 = tgt.clone()
+    y3 = torch.empty_like(x)
+    l3 = torch.empty(1, dtype=torch.float64, device="cuda")
+    p.forward_train_mse(x, y3, t3, t3, l3, p.new_saved())  # g replaces the target
+    torch.cuda.synchronize()
+    assert p.get_error() == 0
+    assert torch.equal(y1, y2) and torch.equal(g1, g2) and torch.equal(y1, y3) and torch.equal(g1, t3)
+    assert abs(float(l2) - float(l1)) <= 1e-6 * abs(float(l1)) and abs(float(l3) - float(l1)) <= 1e-6 * abs(float(l1))
+    dc1 = torch.empty(p.coef_count, dtype=torch.float64, device="cuda")
+    dc2 = torch.empty_like(dc1)
+    p.backward(x, g1, None, dc1, saved)
+    p.backward(x, g2, None, dc2, saved2)
+    torch.cuda.synchronize()
+    assert torch.equal(dc1, dc2)
+    with pytest.raises(api.TfxError):  # the target may not overlap y
+        p.forward_train_mse(x, y2, y2, g2, l2, saved2)
+    p.close()
