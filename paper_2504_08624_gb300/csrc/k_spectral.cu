@@ -161,9 +161,38 @@ __device__ __forceinline__ dcplx shfl_c(dcplx v, int src) {
     return {__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src)};
 }
 
+__device__ __forceinline__ float2 fshfl_up(float2 v, int d) {
+    return make_float2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
+}
+__device__ __forceinline__ float2 fshfl_down(float2 v, int d) {
+    return make_float2(__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d));
+}
+__device__ __forceinline__ float2 fshfl(float2 v, int src) {
+    return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+__device__ __forceinline__ float2 frecip(float2 b) {
+    const float d = 1.0f / fmaf(b.x, b.x, b.y * b.y);
+    return make_float2(b.x * d, -b.y * d);
+}
+
+// A section's numerator B(z) and denominator A(z) (a0-normalised
+// coefficients) at z = zt[bin]: evaluated in FP64, where the cancellation
+// near a pole or a zero happens, then rounded to FP32 (relative error
+// ~6e-8 however small |A| is); the products and quotients that follow are
+// well conditioned and run in FP32 (FP64 throughput is scarce on this part;
+// measured on CPU against all-FP64: <= 1e-6 of each stage's largest
+// gradient on the test chains).
+__device__ __forceinline__ void section_poly(const double2* __restrict__ zt, int bin, double b0, double b1,
+                                             double b2, double a1, double a2, float2& Bn, float2& An) {
+    const double2 z = zt[bin];
+    const double z2r = z.x * z.x - z.y * z.y, z2i = 2.0 * z.x * z.y;
+    Bn = make_float2((float)(b0 + b1 * z.x + b2 * z2r), (float)(b1 * z.y + b2 * z2i));
+    An = make_float2((float)(1.0 + a1 * z.x + a2 * z2r), (float)(a1 * z.y + a2 * z2i));
+}
+
 // Composite spectrum in the filter's layout (storage index i, 1/M folded
 // in): the FIR's spectrum Hf (already scaled) times prod_s B_s / A_s at the
-// bin of i, in FP64, one lane per (bin, section) as in k_chain_grads_sec.
+// bin of i, one lane per (bin, section) as in k_chain_grads_sec.
 __global__ void __launch_bounds__(128) k_chain_spectrum(const double* __restrict__ raw, int S,
                                                         const float2* __restrict__ Hf, const double2* __restrict__ zt,
                                                         int m, float2* __restrict__ H) {
@@ -179,23 +208,19 @@ __global__ void __launch_bounds__(128) k_chain_spectrum(const double* __restrict
     const bool live = active && i < M;
     const int ii = live ? i : 0;
     const int bin = bitrev_bits(pos_of_storage(ii, T), m);
-    const double2 zb = zt[bin];
-    const dcplx z1 = {zb.x, zb.y}, z2 = dmul(z1, z1);
-    const dcplx Bn = {b0 + b1 * z1.re + b2 * z2.re, b1 * z1.im + b2 * z2.im};
-    const dcplx An = {1.0 + a1 * z1.re + a2 * z2.re, a1 * z1.im + a2 * z2.im};
-    dcplx pin = dmul(Bn, drecip(An));
+    float2 Bn, An;
+    section_poly(zt, bin, b0, b1, b2, a1, a2, Bn, An);
+    float2 pin = cmul(Bn, frecip(An));
     for (int d = 1; d < S; d <<= 1) {
-        const dcplx u = shfl_up_c(pin, d);
-        if (sec >= d) pin = dmul(u, pin);
+        const float2 u = fshfl_up(pin, d);
+        if (sec >= d) pin = cmul(u, pin);
     }
-    if (live && sec == S - 1) {
-        const dcplx h = dmul({(double)Hf[i].x, (double)Hf[i].y}, pin);
-        H[i] = make_float2((float)h.re, (float)h.im);
-    }
+    if (live && sec == S - 1) H[i] = cmul(Hf[i], pin);
 }
 
-// Section coefficient gradients (a0-normalised b0 b1 b2 a1 a2 per section),
-// FP64.  A warp takes NB = floor(32 / S) bins at a time with one lane per
+// Section coefficient gradients (a0-normalised b0 b1 b2 a1 a2 per section):
+// the section polynomials in FP64, the products in FP32 (section_poly), the
+// sums in FP64.  A warp takes NB = floor(32 / S) bins at a time with one lane per
 // (bin, section): lane l is section l % S of bin slot l / S, so each lane
 // evaluates one section, the products over the other sections come from
 // segmented prefix and suffix scans across the bin's S lanes, and a lane
@@ -231,40 +256,37 @@ __global__ void __launch_bounds__(32 * GRADS_WARPS) k_chain_grads_sec(
         const int bin = bitrev_bits(pos_of_storage(ii, T), m);
         const int mir = (M - bin) & (M - 1);
         const double2 p = P[ii], pm = P[storage_of_pos(bitrev_bits(mir, m), T)];
-        const dcplx Sv = {0.5 * (p.x + pm.x), 0.5 * (p.y - pm.y)};
+        const float2 Sv = make_float2((float)(0.5 * (p.x + pm.x)), (float)(0.5 * (p.y - pm.y)));
         const double2 zb = zt[bin];
-        const dcplx z1 = {zb.x, zb.y}, z2 = dmul(z1, z1);
-        const dcplx F = {(double)Hf[ii].x * M, (double)Hf[ii].y * M};
-        const dcplx Bn = {b0 + b1 * z1.re + b2 * z2.re, b1 * z1.im + b2 * z2.im};
-        const dcplx An = {1.0 + a1 * z1.re + a2 * z2.re, a1 * z1.im + a2 * z2.im};
-        const dcplx iA = drecip(An);
-        const dcplx Hs = dmul(Bn, iA);
+        const float2 z1 = make_float2((float)zb.x, (float)zb.y), z2 = cmul(z1, z1);
+        const float2 F = make_float2(Hf[ii].x * (float)M, Hf[ii].y * (float)M);
+        float2 Bn, An;
+        section_poly(zt, bin, b0, b1, b2, a1, a2, Bn, An);
+        const float2 iA = frecip(An);
+        const float2 Hs = cmul(Bn, iA);
         // inclusive prefix and suffix products over the bin's sections
-        dcplx pin = Hs, sin_ = Hs;
+        float2 pin = Hs, sin_ = Hs;
         for (int d = 1; d < S; d <<= 1) {
-            const dcplx u = shfl_up_c(pin, d), w = shfl_down_c(sin_, d);
-            if (sec >= d) pin = dmul(u, pin);
-            if (sec + d < S) sin_ = dmul(sin_, w);
+            const float2 u = fshfl_up(pin, d), w = fshfl_down(sin_, d);
+            if (sec >= d) pin = cmul(u, pin);
+            if (sec + d < S) sin_ = cmul(sin_, w);
         }
-        dcplx pre = shfl_up_c(pin, 1), suf = shfl_down_c(sin_, 1);
-        if (sec == 0) pre = {1.0, 0.0};
-        if (sec == S - 1) suf = {1.0, 0.0};
-        const dcplx Cs = shfl_c(pin, first + S - 1);  // the product over every section
+        float2 pre = fshfl_up(pin, 1), suf = fshfl_down(sin_, 1);
+        if (sec == 0) pre = make_float2(1.f, 0.f);
+        if (sec == S - 1) suf = make_float2(1.f, 0.f);
+        const float2 Cs = fshfl(pin, first + S - 1);  // the product over every section
         if (!live) continue;
-        if (wfir && sec == 0) {
-            const dcplx w = dmul({Cs.re, -Cs.im}, Sv);
-            wfir[i] = make_float2((float)w.re, (float)w.im);
-        }
-        const dcplx q0 = dmul(dmul(F, dmul(pre, suf)), iA);  // dH/db_0 = F prod_(j != s) H_j / A_s
-        const dcplx q1 = dmul(q0, z1), q2 = dmul(q0, z2);
-        const dcplx h0 = dmul(dmul(F, Cs), iA);              // -dH/da_k = z^k H / A_s
-        const dcplx h1 = dmul(h0, z1), h2 = dmul(h0, z2);
-        // Re(conj(d) S)
-        acc[0] += q0.re * Sv.re + q0.im * Sv.im;
-        acc[1] += q1.re * Sv.re + q1.im * Sv.im;
-        acc[2] += q2.re * Sv.re + q2.im * Sv.im;
-        acc[3] -= h1.re * Sv.re + h1.im * Sv.im;
-        acc[4] -= h2.re * Sv.re + h2.im * Sv.im;
+        if (wfir && sec == 0) wfir[i] = cmul(make_float2(Cs.x, -Cs.y), Sv);
+        const float2 q0 = cmul(cmul(F, cmul(pre, suf)), iA);  // dH/db_0 = F prod_(j != s) H_j / A_s
+        const float2 q1 = cmul(q0, z1), q2 = cmul(q0, z2);
+        const float2 h0 = cmul(cmul(F, Cs), iA);              // -dH/da_k = z^k H / A_s
+        const float2 h1 = cmul(h0, z1), h2 = cmul(h0, z2);
+        // Re(conj(d) S), added in FP64
+        acc[0] += (double)fmaf(q0.x, Sv.x, q0.y * Sv.y);
+        acc[1] += (double)fmaf(q1.x, Sv.x, q1.y * Sv.y);
+        acc[2] += (double)fmaf(q2.x, Sv.x, q2.y * Sv.y);
+        acc[3] -= (double)fmaf(h1.x, Sv.x, h1.y * Sv.y);
+        acc[4] -= (double)fmaf(h2.x, Sv.x, h2.y * Sv.y);
     }
 #pragma unroll
     for (int k = 0; k < 5; ++k) red[warp][lane][k] = acc[k];
