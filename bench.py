@@ -258,6 +258,51 @@ def unit_roofline(u, units, t, step_s, pk, fp32) -> dict:
     return row
 
 
+def measure_link(x_host, y_host, dev, torch, reps: int = 5) -> dict:
+    """Copy-engine rate of the host link for these pinned buffers: host to
+    device alone, device to host alone, and both at once on two streams
+    (GB/s, CUDA events around each; the end-to-end step cannot beat the
+    concurrent rate)."""
+    d_in = torch.empty(x_host.shape, dtype=x_host.dtype, device=dev)
+    d_out = torch.empty(y_host.shape, dtype=y_host.dtype, device=dev)
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    cur = torch.cuda.current_stream(dev)
+
+    def run(fn):
+        fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(cur)
+        for _ in range(reps):
+            s1.wait_stream(cur)
+            s2.wait_stream(cur)
+            fn()
+            cur.wait_stream(s1)
+            cur.wait_stream(s2)
+        b.record(cur)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3 / reps
+
+    def h2d():
+        with torch.cuda.stream(s1):
+            d_in.copy_(x_host, non_blocking=True)
+
+    def d2h():
+        with torch.cuda.stream(s2):
+            y_host.copy_(d_out, non_blocking=True)
+
+    def both():
+        h2d()
+        d2h()
+
+    nb_in, nb_out = x_host.numel() * x_host.element_size(), y_host.numel() * y_host.element_size()
+    t_in, t_out, t_both = run(h2d), run(d2h), run(both)
+    del d_in, d_out
+    return {"h2d": nb_in / t_in / 1e9, "d2h": nb_out / t_out / 1e9, "both": (nb_in + nb_out) / t_both / 1e9,
+            "both_ms": t_both * 1e3}
+
+
 def traffic_for(kernel: str, workload_name: str):
     """DRAM bytes per launch of ``kernel`` from the committed ncu summary, or
     None when the summary is missing or the kernel source changed since."""
@@ -806,6 +851,15 @@ def main():
         e2e = {"value": units * ws * k_e2e / t_e2e, "unit": UNIT,
                "h2d_bytes_per_step": int(x_host.numel() * 4), "d2h_bytes_per_step": int(y_host.numel() * 4),
                "ms_per_step": t_e2e / k_e2e * 1e3, "steps": k_e2e}
+        # the host link's own bound: the same bytes copied in and out at once
+        # by the copy engines (two streams, pinned buffers), no filtering
+        link = measure_link(x_host, y_host, dev, torch)
+        step_s = t_e2e / k_e2e
+        e2e["link"] = {"gbs_concurrent": link["both"], "gbs_h2d": link["h2d"], "gbs_d2h": link["d2h"],
+                       "copy_only_ms": link["both_ms"],
+                       "frac": (x_host.numel() + y_host.numel()) * 4 / step_s / 1e9 / link["both"],
+                       "note": "end-to-end bytes per step / step time, against the measured concurrent "
+                               "host->device + device->host copy rate of the same buffers"}
 
     # the same chain with its units kept separate (no composite response), for context
     separate = None
