@@ -2,6 +2,7 @@
 // device constants), workspace layout, launches, the one-shot plan cache and
 // the C-ABI entry points declared in include/tfx.h.
 #include <algorithm>
+#include <cassert>
 #include <array>
 #include <cmath>
 #include <complex>
@@ -875,7 +876,10 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         if (cudaGetDevice(&dev) == cudaSuccess)
             cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
         for (HostUnit& u : p->units)
-            if (u.S > 0 && u.S <= SEG_SMAX && u.L == 0 && !u.warp && !u.hiq) choose_segments(p, u, sm_count);
+            if (u.S > 0 && u.S <= SEG_SMAX && u.L == 0 && !u.warp && !u.hiq) {
+                assert(!p->train);  // launch_unit_range's training callers pass no copy buffer
+                choose_segments(p, u, sm_count);
+            }
     }
 
     // constant blob layout (a spectral plan: every section's raw row and
@@ -1214,7 +1218,14 @@ bool ranges_overlap_not_equal(const float* x, const float* y, int64_t C, int64_t
 }
 
 // Launch unit i for channels [c0, c0 + Cg) reading `in` (row stride ldin) and
-// writing `out` (row stride ldout).
+// writing `out` (row stride ldout).  copy_buf ([Cg x N] floats) takes a copy
+// of the input when a unit that reads other tiles' or segments' input runs
+// in place; callers without one (the training forward and backward) never
+// run such a unit in place: their inputs and outputs are distinct buffers
+// (x != y is required, intermediates go to the saved buffer or to the
+// gradient buffers), and trainable plans route cascades to the warp-tile
+// scan, never to segments (build_plan: u.warp for p->train), which an
+// assert in choose_segments' caller restates.
 int launch_unit_range(tfx_plan* p, const HostUnit& u, const float* in, int64_t ldin, float* out, int64_t ldout,
                       int64_t c0, int64_t Cg, char* scratch, float* copy_buf, cudaStream_t s, float2* ckpt = nullptr) {
     in += c0 * ldin;
