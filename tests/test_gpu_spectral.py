@@ -286,3 +286,30 @@ def test_forward_train_mse_fused(route):
     with pytest.raises(api.TfxError):  # the target may not overlap y
         p.forward_train_mse(x, y2, y2, g2, l2, saved2)
     p.close()
+
+
+def test_spectral_8192_points():
+    """A chain whose response needs an overlap beyond 3072 samples takes the
+    8192-point transforms (the correlation, tap-gradient and decay-check
+    kernels at that size): against the oracle, then an update that moves a
+    pole to radius 0.9995 is reported as TFX_ERR_DECAY."""
+    stages = [("sos", W.random_stable_sos(4, 82, 0.9, 0.99)), ("fir", W.fir_lowpass(1025, 3000.0, W.FS))]
+    C, N = 3, 30000
+    p = plan(C, N, stages)
+    d = p.describe()[0]
+    assert d["kind"] == "chain_spectral" and d["M"] == 8192 and 3072 < d["J"] <= 6144, d
+    x = W.white_gauss(C, N, 80)
+    g = W.white_gauss(C, N, 81)
+    y, dx, dc = grads(p, x, g)
+    lib = oracle.load()
+    assert_close(y, lib.chain(x, stages), 1e-4, "training forward")
+    dx_ref, gref = lib.chain_vjp(x, g, stages)
+    assert_close(dx, dx_ref, 1e-4, "dL/dx")
+    worst = check_coefs(split(dc, stages), gref, stages)
+    print(f"8192 points: {d}, worst coefficient error {worst:.2e}")
+    rows = np.asarray(stages[0][1]).copy()
+    rows[2] = W.biquad_rows([0.0], [-1.0], [[1.0, 0.2, 0.3]], rmin=0.9995, rspan=0.0)[0]
+    p.update_sos(torch.from_numpy(rows).cuda())
+    torch.cuda.synchronize()
+    assert p.get_error() == -8  # TFX_ERR_DECAY
+    p.close()
