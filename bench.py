@@ -595,7 +595,7 @@ def measure_fwdbwd(wl, steps, warmup, dev, stream, torch, dist, ws, rank, pk, sm
         t_dc = time_gpu(lambda: plan.backward(x, g, None, dcoef, saved, bws), k_k, 3, stream, torch, None) / k_k
         parts = {"forward (k_fir_fft)": t_f, "dL/dx (k_fir_fft, reverse time)": t_dx,
                  "dL/dcoef (k_chain_xcorr + k_xcorr_reduce + k_chain_grads_sec + k_chain_grads_fir + "
-                 "k_sos_grad_finalize)": t_dc}
+                 "k_spectral_finalize)": t_dc}
         name, t_k = max(parts.items(), key=lambda kv: kv[1])
         ach = units * 8.0 / t_k / 1e9
         kern = "k_chain_xcorr" if name.startswith("dL/dcoef") else "k_fir_fft"

@@ -225,19 +225,16 @@ __global__ void __launch_bounds__(128) k_chain_spectrum(const double* __restrict
 // evaluates one section, the products over the other sections come from
 // segmented prefix and suffix scans across the bin's S lanes, and a lane
 // accumulates the gradient terms of one fixed section over all the bins it
-// visits (enough warps per SM to hide the FP64 latency).  Each block writes
-// its sums to bpart[block][5 S]; the last block to finish (counted on *done,
-// zero on entry and reset by that block) adds them in block order into
-// sums[5 S], so the result does not depend on the blocks' timing.  With wfir
+// visits (enough warps per SM to hide the latency).  Each block writes its
+// sums to bpart[block][5 S] (k_spectral_finalize adds them in block order,
+// so the result does not depend on the blocks' timing).  With wfir
 // set, also conj(C) S at each bin (C = prod_s H_s, the cascades' spectrum)
 // for the FIR tap gradients, in storage layout.
 constexpr int GRADS_WARPS = 4;
 __global__ void __launch_bounds__(32 * GRADS_WARPS) k_chain_grads_sec(
     const double2* __restrict__ P, const double* __restrict__ raw, int S, const float2* __restrict__ Hf,
-    const double2* __restrict__ zt, int m, double* __restrict__ bpart, unsigned* __restrict__ done,
-    double* __restrict__ sums, float2* __restrict__ wfir) {
+    const double2* __restrict__ zt, int m, double* __restrict__ bpart, float2* __restrict__ wfir) {
     __shared__ double red[GRADS_WARPS][32][5];
-    __shared__ bool last;
     const int M = 1 << m, T = M / 16;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int NB = 32 / S, slot = lane / S, sec = lane % S;
@@ -300,23 +297,37 @@ __global__ void __launch_bounds__(32 * GRADS_WARPS) k_chain_grads_sec(
             for (int b = 0; b < NB; ++b) v += red[w][b * S + sq][k];
         bpart[(int64_t)blockIdx.x * 5 * S + q] = v * invM;
     }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    // warp w adds values q = w, w + GRADS_WARPS, ...: lane l the blocks
-    // l, l + 32, ... (independent loads), then a fixed shuffle tree
-    for (int q = warp; q < 5 * S; q += GRADS_WARPS) {
-        double v = 0.0;
-#pragma unroll 4
-        for (unsigned b = lane; b < gridDim.x; b += 32) v += __ldcg(bpart + (int64_t)b * 5 * S + q);
+}
+
+// The section gradients from the blocks' partial sums, then the a0 chain
+// rule to the raw rows: block s (one per section), warp k (of 5) adds term
+// k over the blocks b = lane, lane + 32, ... and then by a fixed shuffle
+// tree; with G the five sums of section s (normalised b0 b1 b2 a1 a2) and r
+// its raw row, dL/db_k = G_k / a0, dL/da_k = G_(k+2) / a0 (k = 1, 2) and
+// dL/da0 = -(sum of the raw coefficients times their G) / a0^2.
+__global__ void __launch_bounds__(160) k_spectral_finalize(const double* __restrict__ bpart, int nblk, int S,
+                                                           const double* __restrict__ raw,
+                                                           const int64_t* __restrict__ dst,
+                                                           double* __restrict__ dcoef) {
+    __shared__ double G[5];
+    const int sec = blockIdx.x, k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double v = 0.0;
+    for (int b = lane; b < nblk; b += 32) v += __ldcg(bpart + (int64_t)b * 5 * S + 5 * sec + k);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) sums[q] = v;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) G[k] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double* r = raw + 6 * sec;
+        const double inv = 1.0 / r[3];
+        double* o = dcoef + dst[sec];
+        o[0] = G[0] * inv;
+        o[1] = G[1] * inv;
+        o[2] = G[2] * inv;
+        o[4] = G[3] * inv;
+        o[5] = G[4] * inv;
+        o[3] = -(r[0] * G[0] + r[1] * G[1] + r[2] * G[2] + r[4] * G[3] + r[5] * G[4]) * inv * inv;
     }
-    if (threadIdx.x == 0) *done = 0u;
 }
 
 // Inverse transform of a spectrum given in storage layout (position
@@ -466,19 +477,24 @@ int chain_grads_blocks(int m, int S) {
     return std::max(1, std::min((groups + GRADS_WARPS - 1) / GRADS_WARPS, 2 * 152));
 }
 
-size_t chain_grads_scratch_bytes(int m, int S) {
-    return 256 + (size_t)chain_grads_blocks(m, S) * 5 * S * sizeof(double);
+size_t chain_grads_scratch_bytes(int m, int S) { return (size_t)chain_grads_blocks(m, S) * 5 * S * sizeof(double); }
+
+cudaError_t launch_spectral_finalize(int m, const void* scratch, int S, const double* raw, const int64_t* dst,
+                                     double* dcoef, cudaStream_t s) {
+    if (S < 1 || S > SPEC_SMAX) return cudaErrorInvalidValue;
+    k_spectral_finalize<<<(unsigned)S, 160, 0, s>>>(static_cast<const double*>(scratch), chain_grads_blocks(m, S), S,
+                                                    raw, dst, dcoef);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_chain_grads(int m, const double2* P, const double* raw, int S, const float2* Hf,
-                               const double2* zt, const float2* tw, int L, void* scratch, double* sums, float2* wfir,
-                               double* dh, cudaStream_t s) {
+                               const double2* zt, const float2* tw, int L, void* scratch, float2* wfir, double* dh,
+                               cudaStream_t s) {
     if (S < 1 || S > SPEC_SMAX) return cudaErrorInvalidValue;
     const int M = 1 << m;
-    unsigned* done = static_cast<unsigned*>(scratch);
-    double* bpart = reinterpret_cast<double*>(static_cast<char*>(scratch) + 256);
+    double* bpart = static_cast<double*>(scratch);
     k_chain_grads_sec<<<(unsigned)chain_grads_blocks(m, S), 32 * GRADS_WARPS, 0, s>>>(P, raw, S, Hf, zt, m, bpart,
-                                                                                   done, sums, dh ? wfir : nullptr);
+                                                                                   dh ? wfir : nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !dh) return e;
     const size_t smem = fir_fft_smem_bytes(M);

@@ -1148,9 +1148,9 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
 
     if (p->train && p->spectral) {
         // nothing saved (the backward reads x); backward workspace: the
-        // correlation CTAs' partial spectra, their FP64 sum, the section
-        // gradient sums, the FIR taps' gradient spectrum and a copy of the
-        // gradient for an in-place input gradient
+        // correlation CTAs' partial spectra, their FP64 sum, the FIR taps'
+        // gradient spectrum, the section-gradient blocks' partial sums and a
+        // copy of the gradient for an in-place input gradient
         const int M = p->chain.fft_M;
         const int64_t items = (p->C + 1) / 2 * p->chain.ntt;
         p->spec_grid = (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)p->sm_count *
@@ -1158,8 +1158,7 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         p->saved_bytes = 0;
         p->b_sp_part = 0;
         p->b_sp_P = align_up((size_t)p->spec_grid * M * sizeof(float2));
-        p->b_sp_sums = p->b_sp_P + align_up((size_t)M * sizeof(double2));
-        p->b_sp_w = p->b_sp_sums + align_up((size_t)p->chain_S * 5 * sizeof(double));
+        p->b_sp_w = p->b_sp_P + align_up((size_t)M * sizeof(double2));
         p->b_sp_gs = p->b_sp_w + align_up((size_t)M * sizeof(float2));
         p->b_gbuf = p->b_sp_gs + align_up(chain_grads_scratch_bytes(p->chain.fft_m, p->chain_S));
         p->bws_bytes = p->b_gbuf + p->buf_bytes;
@@ -1443,11 +1442,8 @@ int run_backward_spectral(tfx_plan* p, const float* x, const float* g, float* dx
     const int m = c.fft_m, M = c.fft_M, J = c.L - 1;
     const float2* tw = reinterpret_cast<const float2*>(p->dconst + c.off_tw);
     if (dcoef) {
-        double* sums = reinterpret_cast<double*>(ws + p->b_sp_sums);
         double2* P = reinterpret_cast<double2*>(ws + p->b_sp_P);
         float2* part = reinterpret_cast<float2*>(ws + p->b_sp_part);
-        if (!count_only && cudaMemsetAsync(ws + p->b_sp_gs, 0, sizeof(unsigned), s) != cudaSuccess)
-            return TFX_ERR_CUDA;
         XcorrArgs a{};
         a.x = x;
         a.g = g;
@@ -1468,10 +1464,10 @@ int run_backward_spectral(tfx_plan* p, const float* x, const float* g, float* dx
         if (!count_only &&
             launch_chain_grads(m, P, raw, p->chain_S, reinterpret_cast<const float2*>(p->dconst + p->spec_fir.off_H),
                                reinterpret_cast<const double2*>(p->dconst + p->off_spec_z),
-                               tw, p->spec_fir.L, ws + p->b_sp_gs, sums, reinterpret_cast<float2*>(ws + p->b_sp_w),
+                               tw, p->spec_fir.L, ws + p->b_sp_gs, reinterpret_cast<float2*>(ws + p->b_sp_w),
                                p->spec_nfir ? dcoef + p->spec_fir_dst : nullptr, s) != cudaSuccess)
             return TFX_ERR_CUDA;
-        TFX_LAUNCH(launch_sos_grad_finalize(sums, p->chain_S, raw,
+        TFX_LAUNCH(launch_spectral_finalize(m, ws + p->b_sp_gs, p->chain_S, raw,
                                             reinterpret_cast<const int64_t*>(p->dconst + p->off_spec_dst), dcoef, s));
     }
     if (dx) {

@@ -126,7 +126,7 @@ struct tfx_plan {
     size_t off_spec_raw = 0, off_spec_dst = 0;  // every section's raw row and gradient slot, contiguous
     size_t off_spec_z = 0;                      // e^(-2 pi i k / M), k < M (FP64)
     int spec_grid = 0;                          // correlation CTAs
-    size_t b_sp_part = 0, b_sp_P = 0, b_sp_sums = 0, b_sp_w = 0, b_sp_gs = 0;  // backward workspace offsets
+    size_t b_sp_part = 0, b_sp_P = 0, b_sp_w = 0, b_sp_gs = 0;  // backward workspace offsets
 };
 
 namespace tfx {

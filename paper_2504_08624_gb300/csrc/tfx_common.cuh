@@ -413,12 +413,15 @@ cudaError_t launch_xcorr_reduce(const float2* part, int G, int M, double2* P, cu
 cudaError_t launch_chain_spectrum(const double* raw, int S, const float2* Hf, const double2* zt, int m, float2* H,
                                   cudaStream_t s);
 cudaError_t launch_chain_tail(int m, const float2* H, const float2* tw, int J, int* status, cudaStream_t s);
-// Scratch of launch_chain_grads: a completion counter (zeroed before the
-// launch) and the blocks' partial sums.
+// Scratch of launch_chain_grads: the blocks' partial sums of the section
+// gradients, which launch_spectral_finalize adds up and maps to the raw rows
+// (dcoef at dst[s] for section s).
 size_t chain_grads_scratch_bytes(int m, int S);
 cudaError_t launch_chain_grads(int m, const double2* P, const double* raw, int S, const float2* Hf,
-                               const double2* zt, const float2* tw, int L, void* scratch, double* sums, float2* wfir,
-                               double* dh, cudaStream_t s);
+                               const double2* zt, const float2* tw, int L, void* scratch, float2* wfir, double* dh,
+                               cudaStream_t s);
+cudaError_t launch_spectral_finalize(int m, const void* scratch, int S, const double* raw, const int64_t* dst,
+                                     double* dcoef, cudaStream_t s);
 cudaError_t launch_fir_fft_batched(int m, const BatchFft* units, const int64_t* prefix, int nunits, int64_t ctas,
                                    BatchBases bases, const float2* tw, cudaStream_t s);
 cudaError_t launch_fir_fft_spectrum(const double* taps, int L, int M, int B, int P, const float2* tw, float2* H,
