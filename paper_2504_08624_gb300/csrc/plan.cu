@@ -1091,6 +1091,10 @@ int build_plan(tfx_plan* p, const tfx_stage* st, int32_t nst, bool upload) {
         if (p->use_chain && prepare_fir_fft(p->chain.fft_M) != cudaSuccess) return TFX_ERR_UNSUPPORTED;
         if (p->spectral) {
             if (prepare_spectral(p->chain.fft_m) != cudaSuccess) return TFX_ERR_UNSUPPORTED;
+            if (cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess)
+                return TFX_ERR_CUDA;
             if (launch_chain_spectrum(reinterpret_cast<const double*>(p->dconst + p->off_spec_raw), p->chain_S,
                                       reinterpret_cast<const float2*>(p->dconst + p->spec_fir.off_H),
                                       reinterpret_cast<const double2*>(p->dconst + p->off_spec_z),
@@ -1423,6 +1427,42 @@ int exec_train(tfx_plan* p, const float* x, float* y, char* saved, void* ws, cud
     return TFX_OK;
 }
 
+// The spectral input gradient: the chain over g in reverse time by the
+// forward's FFT kernel (after a copy of g when dx is g: blocks read their
+// neighbours' gradient samples), on stream s.
+int spectral_dx(tfx_plan* p, const float* g, float* dx, char* ws, cudaStream_t s, bool count_only, int* nlaunch) {
+    const HostUnit& c = p->chain;
+    const float* gin = g;
+    int64_t ldg = p->ld;
+    if (dx == g) {  // blocks read their neighbours' gradient samples
+        float* gb = reinterpret_cast<float*>(ws + p->b_gbuf);
+        ++*nlaunch;
+        if (!count_only && launch_copy_rows(g, gb, p->C, p->N, p->ld, p->N, s) != cudaSuccess) return TFX_ERR_CUDA;
+        gin = gb;
+        ldg = p->N;
+    }
+    FirFftArgs f{};
+    f.x = gin;
+    f.ldx = ldg;
+    f.y = dx;
+    f.ldy = p->ld;
+    f.C = p->C;
+    f.N = p->N;
+    f.L = c.L;
+    f.M = c.fft_M;
+    f.m = c.fft_m;
+    f.B = c.fft_B;
+    f.P = 0;
+    f.nbpc = c.ntt;
+    f.nb = p->C * c.ntt;
+    f.H = reinterpret_cast<const float2*>(p->dconst + c.off_H);
+    f.tw = reinterpret_cast<const float2*>(p->dconst + c.off_tw);
+    f.rev = 1;
+    ++*nlaunch;
+    if (!count_only && launch_fir_fft(f, s) != cudaSuccess) return TFX_ERR_CUDA;
+    return TFX_OK;
+}
+
 // Backward of a spectral plan.  Coefficient gradients: the correlation
 // CTAs accumulate the block cross-spectra of g and x, their sum P (FP64)
 // gives the section gradients by the closed-form derivative spectra and the
@@ -1458,6 +1498,16 @@ int run_backward_spectral(tfx_plan* p, const float* x, const float* g, float* dx
         a.tw = tw;
         a.part = part;
         TFX_LAUNCH(launch_chain_xcorr(m, a, p->spec_grid, s));
+        if (dx) {
+            // dx only needs g (which the correlation has read by now): it runs
+            // on the side stream beside the small gradient kernels below
+            if (!count_only && (cudaEventRecord(p->ev_fork, s) != cudaSuccess ||
+                                cudaStreamWaitEvent(p->side, p->ev_fork, 0) != cudaSuccess))
+                return TFX_ERR_CUDA;
+            const int rc = spectral_dx(p, g, dx, ws, p->side, count_only, &nl);
+            if (rc != TFX_OK) return rc;
+            if (!count_only && cudaEventRecord(p->ev_join, p->side) != cudaSuccess) return TFX_ERR_CUDA;
+        }
         TFX_LAUNCH(launch_xcorr_reduce(part, p->spec_grid, M, P, s));
         const double* raw = reinterpret_cast<const double*>(p->dconst + p->off_spec_raw);
         nl += p->spec_nfir ? 2 : 1;
@@ -1469,34 +1519,12 @@ int run_backward_spectral(tfx_plan* p, const float* x, const float* g, float* dx
             return TFX_ERR_CUDA;
         TFX_LAUNCH(launch_spectral_finalize(m, ws + p->b_sp_gs, p->chain_S, raw,
                                             reinterpret_cast<const int64_t*>(p->dconst + p->off_spec_dst), dcoef, s));
+        // join: the caller's stream continues once the input gradient is done
+        if (dx && !count_only && cudaStreamWaitEvent(s, p->ev_join, 0) != cudaSuccess) return TFX_ERR_CUDA;
     }
-    if (dx) {
-        const float* gin = g;
-        int64_t ldg = p->ld;
-        if (dx == g) {  // blocks read their neighbours' gradient samples
-            float* gb = reinterpret_cast<float*>(ws + p->b_gbuf);
-            TFX_LAUNCH(launch_copy_rows(g, gb, p->C, p->N, p->ld, p->N, s));
-            gin = gb;
-            ldg = p->N;
-        }
-        FirFftArgs f{};
-        f.x = gin;
-        f.ldx = ldg;
-        f.y = dx;
-        f.ldy = p->ld;
-        f.C = p->C;
-        f.N = p->N;
-        f.L = c.L;
-        f.M = M;
-        f.m = m;
-        f.B = c.fft_B;
-        f.P = 0;
-        f.nbpc = c.ntt;
-        f.nb = p->C * c.ntt;
-        f.H = reinterpret_cast<const float2*>(p->dconst + c.off_H);
-        f.tw = tw;
-        f.rev = 1;
-        TFX_LAUNCH(launch_fir_fft(f, s));
+    if (dx && !dcoef) {
+        const int rc = spectral_dx(p, g, dx, ws, s, count_only, &nl);
+        if (rc != TFX_OK) return rc;
     }
 #undef TFX_LAUNCH
     if (nlaunch) *nlaunch = nl;
@@ -1854,6 +1882,9 @@ int tfx_plan_get_error(tfx_plan* p) {
 void tfx_plan_destroy(tfx_plan* p) {
     if (!p) return;
     if (p->dconst || p->dstatus) cudaDeviceSynchronize();
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
+    if (p->side) cudaStreamDestroy(p->side);
     if (p->dconst) cudaFree(p->dconst);
     if (p->dstatus) cudaFree(p->dstatus);
     if (p->dsec) cudaFree(p->dsec);

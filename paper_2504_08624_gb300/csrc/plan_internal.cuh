@@ -126,6 +126,11 @@ struct tfx_plan {
     size_t off_spec_raw = 0, off_spec_dst = 0;  // every section's raw row and gradient slot, contiguous
     size_t off_spec_z = 0;                      // e^(-2 pi i k / M), k < M (FP64)
     int spec_grid = 0;                          // correlation CTAs
+    // the backward's input gradient runs on a side stream (forked from and
+    // joined back to the caller's stream by events) while the coefficient
+    // gradients' small kernels run on the caller's
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     size_t b_sp_part = 0, b_sp_P = 0, b_sp_w = 0, b_sp_gs = 0;  // backward workspace offsets
 };
 
