@@ -298,7 +298,11 @@ int tfx_plan_forward_train_mse_launch_count(const tfx_plan *p);
  * and x (accumulated by blocks) paired with the closed-form derivative
  * spectra of every section coefficient and one inverse transform for the
  * FIR taps; every reduction has a fixed order, so repeated calls give
- * bit-identical results.  Otherwise the SOS cascades run as reverse-time
+ * bit-identical results.  With both dx and dcoef asked, dx runs on a second,
+ * plan-owned stream forked from s by an event after the correlation and
+ * joined back into s before the call's work ends (a capture of s captures
+ * both); a plan's backward calls must therefore be issued from one host
+ * thread at a time.  Otherwise the SOS cascades run as reverse-time
  * adjoint scans that recompute their section outputs from the saved
  * chunk-start states; FIRs as the FIR over the time-reversed gradient plus a
  * tap correlation.  Asynchronous, no allocation, capturable; a device-side
