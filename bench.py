@@ -372,6 +372,16 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(t: float, dist, dev, torch) -> float:
+    """The largest of every rank's value t (each rank receives it); t itself
+    without a process group.  Timed regions report the slowest rank."""
+    if dist is None:
+        return t
+    tt = torch.tensor([t], dtype=torch.float64, device=dev)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
 def time_gpu(fn, steps, warmup, stream, torch, dist=None):
     for _ in range(warmup):
         fn()
@@ -564,11 +574,7 @@ def measure_fwdbwd(wl, steps, warmup, dev, stream, torch, dist, ws, rank, pk, sm
         graph_error = repr(exc)
     if plan.get_error() != 0:
         raise RuntimeError("device reported a timeout during the fwd+bwd run")
-    t_all = t
-    if dist is not None:
-        tt = torch.tensor([t], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_all = float(tt.item())
+    t_all = max_over_ranks(t, dist, dev, torch)
     k_parts = max(5, steps // 4)
     t_f = time_gpu(fwd, k_parts, 2, stream, torch, None) / k_parts
     t_l = time_gpu(loss_step, k_parts, 2, stream, torch, None) / k_parts
@@ -658,10 +664,7 @@ def measure_fwdbwd(wl, steps, warmup, dev, stream, torch, dist, ws, rank, pk, sm
 
         w_e, k_e = 3, max(5, min(steps // 5, 30))
         t_e = time_gpu(e2e_step, k_e, w_e, stream, torch, dist)
-        if dist is not None:
-            tt = torch.tensor([t_e], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_e = float(tt.item())
+        t_e = max_over_ranks(t_e, dist, dev, torch)
         e2e = {"value": units * ws * k_e / t_e, "unit": UNIT, "h2d_bytes_per_step": int(2 * units * 4),
                "d2h_bytes_per_step": int(8 + 8 * plan.coef_count), "ms_per_step": t_e / k_e * 1e3, "steps": k_e,
                "api": f"{type(model).__name__} (parameters on the GPU) + mse_loss + loss.backward() + SGD step; "
@@ -826,11 +829,7 @@ def main():
     err = plan.get_error()
     if err != 0:
         raise RuntimeError(f"device reported {NAT.STATUS.get(err, err)} during the timed run")
-    t_all = t_dev
-    if dist is not None:
-        tt = torch.tensor([t_dev], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_all = float(tt.item())
+    t_all = max_over_ranks(t_dev, dist, dev, torch)
     value = units * ws * args.steps / t_all
     ms = t_all / args.steps * 1e3
 
@@ -844,10 +843,7 @@ def main():
 
         w_e2e, k_e2e = max(3, min(args.warmup, 5)), max(5, min(args.steps // 10, 30))
         t_e2e = time_gpu(e2e_step, k_e2e, w_e2e, stream, torch, dist)
-        if dist is not None:
-            tt = torch.tensor([t_e2e], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_e2e = float(tt.item())
+        t_e2e = max_over_ranks(t_e2e, dist, dev, torch)
         e2e = {"value": units * ws * k_e2e / t_e2e, "unit": UNIT,
                "h2d_bytes_per_step": int(x_host.numel() * 4), "d2h_bytes_per_step": int(y_host.numel() * 4),
                "ms_per_step": t_e2e / k_e2e * 1e3, "steps": k_e2e}
@@ -1042,11 +1038,7 @@ def measure_batched(dev, stream, torch, dist, ws, rank, local, pk, fp32, steps, 
     clocks = sampler.stop()
     if b.get_error() != 0:
         raise RuntimeError("device reported a timeout during the batched run")
-    t_all = t
-    if dist is not None:
-        tt = torch.tensor([t], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_all = float(tt.item())
+    t_all = max_over_ranks(t, dist, dev, torch)
     step_s = t / steps
     # every launch timed alone; the dominant one against its roofline
     groups = []
