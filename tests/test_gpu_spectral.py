@@ -313,3 +313,43 @@ def test_spectral_8192_points():
     torch.cuda.synchronize()
     assert p.get_error() == -8  # TFX_ERR_DECAY
     p.close()
+
+
+@pytest.mark.parametrize("C,pad", [(1, 0), (3, 13)])
+def test_spectral_padded_rows(C, pad):
+    """The spectral route with one channel (the correlation's pair has no
+    second channel) and with padded rows (row stride N + 13): forward, dL/dx
+    and coefficient gradients against the oracle; the padding is not
+    written."""
+    from paper_2504_08624_gb300 import api, _native
+    stages = chain("split_cascades")
+    N = 9000
+    ld = N + pad
+    p = api.Plan(C, N, stages, ld=ld, flags=_native.TFX_PLAN_TRAINABLE)
+    assert p.describe()[0]["kind"] == "chain_spectral"
+    x = W.white_gauss(C, N, 90)
+    g = W.white_gauss(C, N, 91)
+
+    def padded(a, fill):
+        buf = torch.full((C * ld,), fill, dtype=torch.float32, device="cuda")
+        v = buf.view(C, ld)[:, :N]
+        v.copy_(torch.from_numpy(a.astype(np.float32)))
+        return buf, v
+    _, xd = padded(x, 0.0)
+    _, gd = padded(g, 0.0)
+    ybuf, y = padded(np.zeros_like(x), -7.0)
+    dxbuf, dx = padded(np.zeros_like(x), -7.0)
+    dc = torch.empty(p.coef_count, dtype=torch.float64, device="cuda")
+    saved = p.new_saved()
+    p.forward_train(xd, y, saved)
+    p.backward(xd, gd, dx, dc, saved)
+    torch.cuda.synchronize()
+    assert p.get_error() == 0
+    p.close()
+    lib = oracle.load()
+    assert_close(y.cpu().numpy().astype(np.float64), lib.chain(x, stages), 1e-4, "forward")
+    dx_ref, gref = lib.chain_vjp(x, g, stages)
+    assert_close(dx.cpu().numpy().astype(np.float64), dx_ref, 1e-4, "dL/dx")
+    check_coefs(split(dc.cpu().numpy(), stages), gref, stages)
+    if pad:
+        assert torch.all(ybuf.view(C, ld)[:, N:] == -7.0) and torch.all(dxbuf.view(C, ld)[:, N:] == -7.0)
