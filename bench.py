@@ -53,7 +53,7 @@ def parse():
                                                              "(profiling only)")
     ap.add_argument("--workload", default="multichannel_fused",
                     choices=["multichannel_fused", "plain_chain", "long_fir", "table4_chain", "differentiable_chain",
-                             "batched_clips"],
+                             "batched_clips", "paper_sweep"],
                     help="configuration to time (default: the one the headline metric is quoted on)")
     ap.add_argument("--part", choices=["chain", "iir", "fir"], default="chain",
                     help="time the whole chain (default) or only its IIR cascade / FIR stage (profiling)")
@@ -207,6 +207,20 @@ def fft_flops_per_output(u) -> float:
     return (10.0 * M * m + 8.0 * P * M) / M
 
 
+def kernel_name(u) -> str:
+    """The kernel (or kernel pair) that runs one unit of a plan description."""
+    k = u["kind"]
+    if k == "fir_tc":
+        return u["kernel"]
+    if k == "fir_fft":
+        return "k_fir_fft" if u.get("P", 0) == 0 else "k_fir_fft_spec+k_fir_fft_conv"
+    if k == "chain_fft":
+        return "k_fir_fft"
+    if k == "cascade" and u.get("scan") == "tc":
+        return "k_sos_tc"
+    return {"warp": "k_sos_warp"}.get(u.get("scan"), "k_unit")
+
+
 def unit_roofline(u, units, t, step_s, pk, fp32) -> dict:
     """One unit of a plan against its roofline (per-unit algorithmic work as
     stated in the module docstring).  The FFT FIR and the tensor-core cascade
@@ -228,9 +242,7 @@ def unit_roofline(u, units, t, step_s, pk, fp32) -> dict:
                     "note": "achieved counts algorithmic 2L flop/sample; executed counts 3 split products x (W+128) K"})
     elif k in ("fir_fft", "chain_fft"):
         f = fft_flops_per_output(u)
-        kern = {"fir_fft": "k_fir_fft" if u.get("P", 0) == 0 else "k_fir_fft_spec+k_fir_fft_conv",
-                "chain_fft": "k_fir_fft"}[k]
-        row.update({"bound": "hbm", "kernel": kern, "achieved": hbm_ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+        row.update({"bound": "hbm", "kernel": kernel_name(u), "achieved": hbm_ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "peak_source": f"{pk['source']} HBM copy bandwidth",
                     "config": {kk: u[kk] for kk in ("S", "L", "D", "Lc", "M", "B", "P") if kk in u},
                     "fft_tflops": units * f / t / 1e12,
@@ -242,14 +254,13 @@ def unit_roofline(u, units, t, step_s, pk, fp32) -> dict:
         # work (GEMM1 128 x 112 and GEMM2 128 x 16 per 112-sample block, 3 split
         # products) takes under half the time the HBM traffic does at peak
         execf = 2.0 * 3 * 128 * (112 + 16) / 112
-        row.update({"bound": "hbm", "kernel": "k_sos_tc", "achieved": hbm_ach,
+        row.update({"bound": "hbm", "kernel": kernel_name(u), "achieved": hbm_ach,
                     "peak": pk["hbm_gbs"], "unit": "GB/s", "peak_source": f"{pk['source']} HBM copy bandwidth",
                     "executed_tflops": units * execf / t / 1e12,
                     "note": "8 B per sample (FP32 read + write); executed tensor flop per sample %.0f" % execf})
     else:
         S, L = u.get("S", 0), u.get("L", 0)
-        kern = {"warp": "k_sos_warp"}.get(u.get("scan"), "k_unit")
-        row.update({"bound": "alu", "kernel": kern,
+        row.update({"bound": "alu", "kernel": kernel_name(u),
                     "achieved": units * (10.0 * S + 2.0 * L) / t / 1e12, "peak": fp32["tflops"], "unit": "TFLOP/s",
                     "peak_source": "measured FP32 FMA rate (bench.measure_fp32_peak)",
                     "note": "10 flop per SOS section, 2L per FIR tap, per sample"})
@@ -419,6 +430,8 @@ def reference_arm(args, ws, rank):
         return
     if args.workload == "batched_clips":
         return reference_arm_batched(args)
+    if args.workload == "paper_sweep":
+        return reference_arm_sweep(args)
     wl = workload(args)
     ncpu = os.cpu_count() or 1
     Cs = min(wl.C, max(1, ncpu))
@@ -438,9 +451,42 @@ def reference_arm(args, ws, rank):
         "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl.name, "channels": wl.C, "samples": wl.N, "chain": "cheby1(8)+4 peaking+fir1025"},
+        "config": {"workload": wl.name, "channels": wl.C, "samples": wl.N, "chain": chain_label(wl.stages)},
         "cpu_baseline": {"value": rate, "unit": UNIT, "cores": lib.num_threads(), "kind": "oracle",
                          "sample": sample},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def reference_arm_sweep(args):
+    """The oracle on the paper's timing grid: each step filters a bounded
+    sample (the first 240,000 samples of up to 12 channels) with each of the
+    grid's two filters."""
+    from paper_2504_08624_gb300 import workloads as W
+    import oracle
+    lib = oracle.load()
+    Cs = min(max(W.PAPER_SWEEP_CHANNELS), max(1, os.cpu_count() or 1))
+    Ns = 240000
+    cells = [W.paper_sweep(k, max(W.PAPER_SWEEP_SECONDS), Cs) for k in ("fir", "iir")]
+    xs = [wl.make_signal(Cs, Ns) for wl in cells]
+    for _ in range(args.warmup):
+        for wl, x in zip(cells, xs):
+            lib.chain(x, wl.stages)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for wl, x in zip(cells, xs):
+            lib.chain(x, wl.stages)
+    dt = (time.perf_counter() - t0) / max(1, args.steps)
+    rate = 2 * Cs * Ns / dt
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "paper_sweep_44k1", "filters": {k: chain_label(wl.stages) for k, wl in
+                                                              zip(("fir", "iir"), cells)}},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": lib.num_threads(), "kind": "oracle",
+                         "sample": f"{Cs} channels x first {Ns} samples through each of the two filters per step "
+                                   "(FP64 oracle, OpenMP over channels)"},
         "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -798,6 +844,9 @@ def main():
     if args.workload == "batched_clips":
         run_batched_main(args, dev, torch, dist, ws, rank, local)
         return
+    if args.workload == "paper_sweep":
+        run_paper_sweep_main(args, dev, torch, dist, ws, rank, local)
+        return
     wl = workload(args)
     bytes_ps, flops_ps, S, L = algorithmic(wl)
     units = wl.C * wl.N
@@ -1153,6 +1202,140 @@ def run_batched_main(args, dev, torch, dist, ws, rank, local):
         out["gpu"] = props.name
         out["fp32_peak"] = fp32
         print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def chain_label(stages) -> str:
+    """Short description of a chain's stages, in order."""
+    parts = []
+    for k, c in stages:
+        if k == "sos":
+            parts.append(f"{np.asarray(c).reshape(-1, 6).shape[0]} SOS")
+        else:
+            parts.append(f"FIR {np.asarray(c).size}")
+    return " + ".join(parts)
+
+
+def measure_paper_sweep(dev, stream, torch, dist, pk, reps, warmup, with_cpu):
+    """The paper's timing grid (Sec. 4, Tables 2 and 3): each filter (a
+    101-tap FIR and a 4th-order Butterworth, separately) on every cell of
+    durations x channels of 44.1 kHz Gaussian noise; per cell the median of
+    `reps` calls, each timed by its own pair of CUDA events (the paper's
+    protocol: the median of 50 calls after warm-up), the plan built
+    untimed.  The cells read prefixes of one resident 12 x 600 s buffer (row
+    stride = the full length) and write into a second one."""
+    from paper_2504_08624_gb300 import api, workloads as W
+    secs, chans = W.PAPER_SWEEP_SECONDS, W.PAPER_SWEEP_CHANNELS
+    top = W.paper_sweep("fir", max(secs), max(chans))
+    Cmax, Nmax = top.C, top.N
+    x = torch.from_numpy(top.make_signal()).to(dev)
+    y = torch.empty_like(x)
+    cells, launches = [], 0
+    for kind in ("fir", "iir"):
+        for sec in secs:
+            for C in chans:
+                wl = W.paper_sweep(kind, sec, C)
+                plan = api.Plan(C, wl.N, wl.stages, ld=Nmax)
+                wsb = plan.workspace()
+                xv, yv = x[:C, :wl.N], y[:C, :wl.N]
+                for _ in range(warmup):
+                    plan.execute(xv, yv, wsb)
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(reps)]
+                torch.cuda.synchronize()
+                if dist is not None:
+                    dist.barrier()
+                for a, b in ev:
+                    a.record(stream)
+                    plan.execute(xv, yv, wsb)
+                    b.record(stream)
+                torch.cuda.synchronize()
+                err = plan.get_error()
+                if err != 0:
+                    raise RuntimeError(f"{wl.name}: plan status {err}")
+                ts = [a.elapsed_time(b) / 1e3 for a, b in ev]
+                med = max_over_ranks(statistics.median(ts), dist, dev, torch)
+                mean = max_over_ranks(statistics.fmean(ts), dist, dev, torch)
+                launches += reps * plan.launches_per_execute
+                desc = plan.describe()
+                cells.append({"filter": kind, "seconds": sec, "channels": C, "samples": wl.N,
+                              "median_s": med, "mean_s": mean, "value": C * wl.N / med,
+                              "hbm_frac": 8.0 * C * wl.N / med / (pk["hbm_gbs"] * 1e9),
+                              "route": [u["kind"] for u in desc], "kernel": "+".join(kernel_name(u) for u in desc),
+                              "M": [u.get("M") for u in desc]})
+                plan.close()
+    total_cs = sum(c["channels"] * c["samples"] for c in cells)
+    total_t = sum(c["median_s"] for c in cells)
+    # the dominant kernel: the filter whose cells take the larger share of
+    # the grid's time, at its largest cell (one kernel per cell)
+    share = {k: sum(c["median_s"] for c in cells if c["filter"] == k) for k in ("fir", "iir")}
+    kd = max(share, key=share.get)
+    big = max((c for c in cells if c["filter"] == kd), key=lambda c: c["channels"] * c["samples"])
+    achieved = 8.0 * big["channels"] * big["samples"] / big["median_s"] / 1e9
+    roof = {"bound": "hbm", "kernel": big["kernel"], "cell": f"{kd} {big['seconds']} s x {big['channels']} ch",
+            "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+            "share_of_step": share[kd] / total_t, "traffic": None, "peak_source": pk["source"],
+            "note": "8 algorithmic bytes per channel-sample (FP32 read + write); the cell's median call time"}
+    cpu, parity = None, None
+    if with_cpu:
+        # the oracle on the 60 s x 12 channel cell of each filter: timed as it
+        # stands (the CPU baseline) and compared with that cell's GPU output
+        import oracle
+        lib = oracle.load()
+        n_cpu, t_cpu, parity = 0, 0.0, {"reference": "FP64 oracle", "cells": []}
+        for kind in ("fir", "iir"):
+            wl = W.paper_sweep(kind, 60, max(chans))
+            plan = api.Plan(wl.C, wl.N, wl.stages, ld=Nmax)
+            plan.execute(x[:wl.C, :wl.N], y[:wl.C, :wl.N], plan.workspace())
+            got = y[:wl.C, :wl.N].cpu().numpy()
+            plan.close()
+            xs = wl.make_signal()
+            t0 = time.perf_counter()
+            ref = lib.chain(xs, wl.stages)
+            t_cpu += time.perf_counter() - t0
+            n_cpu += wl.C * wl.N
+            e = channel_rel_err(got, ref)
+            parity["cells"].append({"filter": kind, "seconds": 60, "channels": wl.C, "tol": wl.tol,
+                                    "max_rel_err": float(max(e)), "per_channel": [float(v) for v in e]})
+        parity["max_rel_err"] = max(c["max_rel_err"] for c in parity["cells"])
+        cpu = {"value": n_cpu / t_cpu, "unit": UNIT, "cores": lib.num_threads(), "kind": "oracle",
+               "sample": f"the 60 s x {max(chans)} channel cell of each filter ({n_cpu} channel-samples), "
+                         f"FP64 oracle, {t_cpu:.1f} s"}
+    return {"value": total_cs / total_t, "ms_per_step": total_t * 1e3, "cells": cells, "roofline": roof,
+            "cpu_baseline": cpu, "parity": parity, "gpu_launches": launches,
+            "filters": {k: chain_label(W.paper_sweep(k, 5, 1).stages) for k in ("fir", "iir")},
+            "grid": {"seconds": list(secs), "channels": list(chans), "fs": W.PAPER_SWEEP_FS}}
+
+
+def run_paper_sweep_main(args, dev, torch, dist, ws, rank, local):
+    """--workload paper_sweep: the paper's timing grid; a step is one pass
+    over all of its cells (value = all cells' channel-samples / the sum of
+    their median call times)."""
+    stream = torch.cuda.current_stream(dev)
+    pk = peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    reps = max(1, min(args.steps, 50))
+    r = measure_paper_sweep(dev, stream, torch, dist, pk, reps, max(3, args.warmup), not args.no_cpu_baseline)
+    clocks = sampler.stop()
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": r["value"] * ws, "unit": UNIT, "n_gpus": ws, "steps": reps,
+            "warmup": max(3, args.warmup), "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "paper_sweep_44k1", "grid": r["grid"], "filters": r["filters"],
+                       "timing": "per cell: median (and mean) of the per-call CUDA-event times",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                       "l2": "no flush, as the paper's repeated calls: cells whose input and output fit in the "
+                             "129 MB L2 stay resident between calls"},
+            "roofline": r["roofline"], "cells": r["cells"], "cpu_baseline": r["cpu_baseline"],
+            "parity": r["parity"], "e2e": None, "gpu_launches": r["gpu_launches"], "clocks": clocks,
+            "gpu": props.name,
+        }), flush=True)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()

@@ -121,8 +121,9 @@ typedef struct {
  * fits within 65536 samples).  One launch.  With this flag such units run
  * the CUDA-core block-tile scan with decoupled look-back instead. */
 #define TFX_PLAN_SCAN_LOOKBACK 512u
-/* A whole chain of SOS cascades and FIRs is one linear time-invariant
- * filter (Sec. 3: the pipe composes the stages in order), and when its
+/* A whole chain of SOS cascades and FIRs (or of cascades alone) is one
+ * linear time-invariant filter (Sec. 3: the pipe composes the stages in
+ * order), and when its
  * cascades' impulse response g decays it is run by default as ONE kernel:
  * the composite impulse response h_c = g * f (f: every FIR's taps
  * convolved) is formed in FP64 at plan time, g truncated at the first D
@@ -130,7 +131,7 @@ typedef struct {
  * ||h_c||_2 (g must have decayed within 65536 samples: the last 4096 of them
  * below 1e-14 of sum|g|; otherwise the chain keeps its separate units), and
  * the signal is filtered by FFT overlap-save with h_c (single-block,
- * M = 4096..16384 points), so it crosses HBM once.  The truncation changes
+ * M = 1024..16384 points), so it crosses HBM once.  The truncation changes
  * no output by more than 1e-7 ||h_c||_2 max|x|; the FP32 transforms round
  * relative to each block's energy.  Chosen when the signal holds at least
  * 2 (D + L - 1) samples and a cost model fitted to GB300 timings predicts it

@@ -27,7 +27,7 @@ from ._native import TfxError
 CANDIDATES = [
     {"fir_nb": nb, "tc_min_taps": t} for nb in (64, 128, 256) for t in (32, 64, 128)
 ]
-FFT_SIZES = (12, 13, 14)
+FFT_SIZES = (10, 11, 12, 13, 14)
 SAMPLE_SAMPLES = 30_000_000  # channel-samples timed per bucket and candidate
 
 

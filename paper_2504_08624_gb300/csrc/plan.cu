@@ -220,9 +220,9 @@ void choose_segments(const tfx_plan* p, HostUnit& u, int sm_count) {
 // Overlap-save scheme for an L-tap FIR: transform size M = 2^m and number of
 // partitions P (0: single-block, B = M - (L - 1) outputs per block; else
 // partitions of B = M/2 taps).  The choice minimises a cost model fitted to
-// measured GB300 times per output (16 channels x 2.88M samples, microseconds
-// for the whole signal): single-block 30 + k_m M / B with
-// k = 71, 74, 85, 121 for m = 10..13 (the 30 is the memory traffic, the rest
+// measured GB300 times per output (16 channels x 2.88M samples, L2 flushed
+// between calls, microseconds for the whole signal): single-block
+// 30 + k_m M / B with k_m from FFT_K (the 30 is the memory traffic, the rest
 // the transforms); partitioned I_m + s_m P with I = 219, 230, 253, 326 and
 // s = 20, 21.4, 23.6, 24.7 for m = 10..13 (two launches and the spectra
 // traffic).  A single block must hold B >= M/8 outputs.  `force` (10..13)
@@ -232,8 +232,8 @@ struct FftScheme {
 };
 
 // Single-block cost per (M / B) for m = 10..14 (m = 14: one 1024-thread CTA
-// per SM, 16384 points).
-const double FFT_K[5] = {71.0, 74.0, 77.0, 113.0, 143.0};
+// per SM, 16384 points), measured with B between M/4 and 7M/8.
+const double FFT_K[5] = {60.0, 63.0, 72.0, 111.0, 140.0};
 
 double fft_single_cost(int m, int L) {
     const int M = 1 << m, B = M - (L - 1);
@@ -570,7 +570,8 @@ bool cascade_decay(const std::vector<double>& sec, int S, const std::vector<doub
 // gain for white input (taken over the first 16384 samples of h_c = g * f, a
 // lower bound).  The composite h_c = g[0, D) * f has Lc = D + Lf - 1 taps and
 // runs by single-block overlap-save with the transform size of least
-// modelled cost, if that beats the separate units; the signal must hold at
+// modelled cost, if that beats the separate units (a chain of cascades alone
+// too: f is then the unit impulse); the signal must hold at
 // least 2 Lc samples (the transform's rounding is relative to each block's
 // energy, so a signal shorter than the response would be compared with an
 // output made only of its smallest leading terms).
@@ -593,7 +594,7 @@ void compose_chain(tfx_plan* p) {
         e.seg = u.S > 0 && u.S <= SEG_SMAX && u.L == 0 && !u.warp;
         separate += unit_cost_estimate(e);
     }
-    if (S == 0 || maxL == 0) return;  // a chain of cascades and at least one FIR
+    if (S == 0) return;  // no cascade: a lone FIR is already one FFT FIR
     std::vector<double> g;
     int D = 0;
     if (!cascade_decay(sec, S, f, g, D)) return;
@@ -602,7 +603,7 @@ void compose_chain(tfx_plan* p) {
     if (p->N < 2 * Lc) return;
     int bestm = 0;
     double best = 0.0;
-    for (int m = 12; m <= 14; ++m) {
+    for (int m = 10; m <= 14; ++m) {
         const int M = 1 << m;
         if (Lc - 1 > M - M / 4) continue;  // at least M/4 outputs per block
         const double c = fft_single_cost(m, (int)Lc);

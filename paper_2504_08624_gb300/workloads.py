@@ -456,6 +456,32 @@ def batched_clips(n: int = 1000, seed: int = 5) -> list:
     return clips
 
 
+# The paper's timing grid (Sec. 4, Tables 2 and 3): signal durations in
+# seconds and channel counts, 44.1 kHz Gaussian noise, one filter at a time.
+PAPER_SWEEP_SECONDS = (5, 60, 180, 300, 600)
+PAPER_SWEEP_CHANNELS = (1, 2, 4, 8, 12)
+PAPER_SWEEP_FS = 44100.0
+
+
+def paper_sweep(kind: str, seconds: float, C: int) -> Workload:
+    """One cell of the paper's timing grid: C channels x `seconds` of N(0, 1)
+    noise at 44.1 kHz through ONE filter, kind "fir" (a 101-tap Hamming
+    low-pass at 1 kHz) or "iir" (a 4th-order Butterworth low-pass at 1 kHz,
+    two sections).  The paper states neither the FIR's taps nor the IIR's
+    order: these are stand-ins.  Channels and samples are prefixes of the
+    largest cell's signal (seed 7), so one buffer serves every cell."""
+    fs = PAPER_SWEEP_FS
+    N = int(round(seconds * fs))
+    if kind == "fir":
+        stages, tol = [("fir", fir_lowpass(101, 1000.0, fs))], 1e-5
+    elif kind == "iir":
+        stages, tol = [("sos", butter_sos(4, 1000.0, fs))], 1e-4
+    else:
+        raise ValueError(f"paper_sweep: kind must be 'fir' or 'iir', not {kind!r}")
+    return Workload(f"paper_sweep_{kind}_{C}x{N}", C, N, stages, tol, "gauss", 7,
+                    meta={"kind": kind, "seconds": seconds})
+
+
 WORKLOADS = {
     "plain_chain": plain_chain,
     "multichannel_fused": multichannel_fused,

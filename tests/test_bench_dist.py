@@ -69,3 +69,19 @@ def test_reference_arm_under_torchrun():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_reference_arm_sweep_and_chain_label():
+    """The reference arm on the paper's timing grid names both filters, and
+    on a fixed workload the chain it actually runs."""
+    for wl, want in [("paper_sweep", None), ("table4_chain", "2 SOS + 2 SOS + 2 SOS + 2 SOS")]:
+        r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", wl,
+                            "--steps", "1", "--warmup", "0"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        d = json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1])
+        assert d["impl"] == "reference" and d["value"] > 0
+        if want is None:
+            assert d["config"]["workload"] == "paper_sweep_44k1"
+            assert d["config"]["filters"] == {"fir": "FIR 101", "iir": "2 SOS"}
+        else:
+            assert d["config"]["chain"] == want

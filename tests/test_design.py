@@ -142,3 +142,34 @@ def test_shelving(kind, gain):
     assert abs(abs(H(0.0)) - lo) < 1e-12
     assert abs(abs(H(np.pi)) - hi) < 1e-12
     assert abs(abs(H(2 * np.pi * f0 / fs)) - 10.0 ** (gain / 40.0)) < 1e-12
+
+
+def test_paper_sweep_cells():
+    """The paper's timing grid (Sec. 4, Tables 2-3) with its stand-in filters:
+    5-600 s x 1-12 channels at 44.1 kHz; the FIR a symmetric 101-tap low-pass
+    of unit DC gain, the IIR a 4th-order Butterworth (two sections) at
+    1 kHz with |H| = 1/sqrt(2) there; channels and samples of a small cell
+    are prefixes of a larger cell's signal."""
+    import math
+    assert W.PAPER_SWEEP_SECONDS == (5, 60, 180, 300, 600)
+    assert W.PAPER_SWEEP_CHANNELS == (1, 2, 4, 8, 12)
+    fir = W.paper_sweep("fir", 5, 1)
+    assert fir.N == 220500 and fir.C == 1 and fir.tol == 1e-5
+    (kind, h), = fir.stages
+    h = np.asarray(h)
+    assert kind == "fir" and h.size == 101
+    assert np.allclose(h, h[::-1], rtol=0, atol=1e-15) and abs(h.sum() - 1.0) < 1e-12
+    iir = W.paper_sweep("iir", 600, 12)
+    assert iir.N == 26460000 and iir.tol == 1e-4
+    (kind, sos), = iir.stages
+    sos = np.asarray(sos)
+    assert kind == "sos" and sos.shape == (2, 6)
+    w = 2 * math.pi * 1000.0 / W.PAPER_SWEEP_FS
+    z = np.exp(-1j * np.arange(3) * w)
+    H = np.prod([(r[:3] @ z) / (r[3:] @ z) for r in sos])
+    assert abs(abs(H) - 2 ** -0.5) < 1e-9
+    big = W.paper_sweep("fir", 60, 12).make_signal(3, 1000)
+    small = W.paper_sweep("iir", 5, 2).make_signal(2, 500)
+    assert np.array_equal(big[:2, :500], small)
+    with pytest.raises(ValueError):
+        W.paper_sweep("fft", 5, 1)

@@ -114,10 +114,10 @@ def test_random_chains_with_long_firs(seed):
 
 
 def test_stays_separate_where_it_must():
-    """A pole beyond 0.999 keeps the FP64-carry scan; FIR-only and
-    cascade-only chains have nothing to compose; the flag keeps the units
-    (a cascade with a short FIR then stays fused on the CUDA cores; by
-    default that chain is composed too)."""
+    """A pole beyond 0.999 keeps the FP64-carry scan; an FIR-only chain has
+    nothing to compose; the flag keeps the units (a cascade with a short FIR
+    then stays fused on the CUDA cores; by default that chain is composed
+    too)."""
     from paper_2504_08624_gb300 import _native as N_
     x = W.white_uniform(2, 40_000, 720)
     short = [("sos", W.butter_sos(4, 1000.0, W.FS)), ("fir", W.fir_lowpass(31, 9000.0, W.FS))]
@@ -128,9 +128,38 @@ def test_stays_separate_where_it_must():
     hi = np.array([[1e-3, 0.0, -1e-3, 1.0, -2 * r * np.cos(th), r * r]])
     check(x, [("sos", hi), ("fir", W.fir_lowpass(513, 9000.0, W.FS))], expect_chain=False)
     check(x, [("fir", W.fir_lowpass(513, 9000.0, W.FS))], expect_chain=False)
-    check(x, [("sos", W.butter_sos(4, 1000.0, W.FS))], expect_chain=False)
+    check(x, [("sos", W.butter_sos(4, 1000.0, W.FS))], expect_chain=False, flags=N_.TFX_PLAN_NO_COMPOSE)
     wl = W.multichannel_fused()
     check(x, wl.stages, expect_chain=False, flags=N_.TFX_PLAN_NO_COMPOSE)
+
+
+def test_cascade_only_chains_compose():
+    """A chain of cascades alone composes too (the FIR factor is the unit
+    impulse): the Table-4 chain (four 4th-order filters, 8 sections, its
+    response decays within a few hundred samples) on ragged lengths and
+    channel counts, and one Butterworth; after a coefficient update the
+    plan runs its cascade unit with the new coefficients."""
+    from paper_2504_08624_gb300 import api
+    wl = W.table4_chain()
+    for C, Ns in [(1, 5_000), (3, 200_003), (2, 1_000_000)]:
+        x = wl.make_signal(C, Ns)
+        err, d = check(x, wl.stages)
+        assert d[0]["S"] == 8 and d[0]["L"] == 1 and d[0]["M"] <= 4096, d
+    x = W.white_uniform(2, 40_000, 721)
+    check(x, [("sos", W.butter_sos(4, 1000.0, W.FS))])
+    x = wl.make_signal(2, 60_000)
+    p = api.Plan(2, 60_000, wl.stages)
+    assert p.describe()[0]["kind"] == "chain_fft"
+    rows = np.concatenate([np.asarray(c).reshape(-1, 6) for k, c in wl.stages])
+    new_rows = rows.copy()
+    new_rows[:, :3] *= 0.5
+    p.update_sos(torch.from_numpy(new_rows).cuda())
+    assert p.describe()[0]["kind"] == "cascade"
+    y = p.execute(torch.from_numpy(x).cuda())
+    torch.cuda.synchronize()
+    assert p.get_error() == 0
+    p.close()
+    assert_close(y.cpu().numpy(), oracle_chain(x, [("sos", new_rows)]), 1e-4, "after update")
 
 
 def test_graph_capture():
