@@ -976,6 +976,15 @@ def main():
         cpu = {"value": Cs * Ns / dt, "unit": UNIT, "cores": thr, "kind": "oracle",
                "sample": f"{Cs} of {wl.C} channels x first {Ns} of {wl.N} samples, FP64 oracle chain, "
                          f"{dt:.1f} s on {thr} threads"}
+        # the same oracle on one thread (about 3e9 multiply-adds of the first channel)
+        N1 = int(min(Ns, max(16384, 3e9 / macs)))
+        lib.set_num_threads(1)
+        t0 = time.perf_counter()
+        lib.chain(xs[:1, :N1], wl.stages)
+        dt1 = time.perf_counter() - t0
+        lib.set_num_threads(thr)
+        cpu["single_core"] = {"value": N1 / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"channel 0 x first {N1} samples, {dt1:.1f} s on 1 thread"}
         # the timed plan's output on the same channels (causal: the first Ns
         # outputs depend on the first Ns inputs only) against the oracle's
         step()
