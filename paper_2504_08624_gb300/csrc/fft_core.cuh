@@ -42,20 +42,33 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
     return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
 }
 
+// cos(2 pi k / 32), k = 0..8 (FP32): the constant twiddles of the in-register
+// DFTs of up to 32 points are these and their negatives.
+__device__ __forceinline__ constexpr float cos32(int k) {
+    return k == 0 ? 1.0f
+         : k == 1 ? 0.98078528040323043f
+         : k == 2 ? 0.92387953251128674f
+         : k == 3 ? 0.83146961230254524f
+         : k == 4 ? 0.70710678118654752f
+         : k == 5 ? 0.55557023301960218f
+         : k == 6 ? 0.38268343236508978f
+         : k == 7 ? 0.19509032201612826f
+                  : 0.0f;
+}
+
 // v * e^(-2 pi i P / N) (INV: e^(+2 pi i P / N)) for the constant twiddles of
-// the in-register DFT (N <= 16, P < N/2): exact for P = 0 and a quarter turn.
+// the in-register DFT (N <= 32, P < N/2): exact for P = 0 and a quarter turn.
 template <int P, int N, bool INV>
 __device__ __forceinline__ float2 twc(float2 v) {
-    constexpr int Q = (16 / N) * P;  // sixteenths of a turn, 0..7
+    constexpr int Q = (32 / N) * P;  // thirty-seconds of a turn, 0..15
     if constexpr (Q == 0) {
         return v;
-    } else if constexpr (Q == 4) {
+    } else if constexpr (Q == 8) {
         return INV ? make_float2(-v.y, v.x) : make_float2(v.y, -v.x);
     } else {
-        constexpr float C1 = 0.92387953251128674f, S1 = 0.38268343236508978f, R2 = 0.70710678118654752f;
-        // cos and sin of 2 pi Q / 16
-        constexpr float c = Q == 1 ? C1 : Q == 2 ? R2 : Q == 3 ? S1 : Q == 5 ? -S1 : Q == 6 ? -R2 : -C1;
-        constexpr float s = Q == 1 ? S1 : Q == 2 ? R2 : Q == 3 ? C1 : Q == 5 ? C1 : Q == 6 ? R2 : S1;
+        // cos and sin of 2 pi Q / 32
+        constexpr float c = Q < 8 ? cos32(Q) : -cos32(16 - Q);
+        constexpr float s = Q < 8 ? cos32(8 - Q) : cos32(Q - 8);
         return INV ? make_float2(fmaf(v.x, c, -v.y * s), fmaf(v.y, c, v.x * s))
                    : make_float2(fmaf(v.x, c, v.y * s), fmaf(v.y, c, -v.x * s));
     }
@@ -66,18 +79,18 @@ __device__ __forceinline__ float2 twc(float2 v) {
 // differences are packed two-lane instructions; a quarter-turn twiddle
 // (multiplication by -i or +i, which swaps the lanes) is folded into scalar
 // sums and differences instead.
-template <int G, int ST, int OFF, int H, bool INV, int Q = 0>
-__device__ __forceinline__ void stage(float2 (&v)[16]) {
+template <int G, int ST, int OFF, int H, bool INV, int Q = 0, int NV>
+__device__ __forceinline__ void stage(float2 (&v)[NV]) {
     if constexpr (Q < G) {
         if constexpr ((Q / H) % 2 == 0) {
             constexpr int i0 = OFF + Q * ST, i1 = OFF + (Q + H) * ST;
-            constexpr int T16 = (16 / (2 * H)) * (Q % H);  // twiddle in sixteenths of a turn
+            constexpr int T32 = (32 / (2 * H)) * (Q % H);  // twiddle in thirty-seconds of a turn
             const float2 a = v[i0];
             const float2 c = v[i1];
-            if constexpr (T16 == 0) {
+            if constexpr (T32 == 0) {
                 v[i0] = cadd(a, c);
                 v[i1] = csub(a, c);
-            } else if constexpr (T16 == 4) {
+            } else if constexpr (T32 == 8) {
                 if constexpr (!INV) {  // DIF: (a + c, (a - c)(-i))
                     v[i0] = cadd(a, c);
                     v[i1] = make_float2(a.y - c.y, c.x - a.x);
@@ -98,22 +111,24 @@ __device__ __forceinline__ void stage(float2 (&v)[16]) {
     }
 }
 
-// G-point DFT.  DIF: natural order in, slot q holds output bitrev(q).  DIT
-// (inverse, unnormalised): bit-reversed in, natural out.
-template <int G, int ST, int OFF>
-__device__ __forceinline__ void dft_dif(float2 (&v)[16]) {
+// G-point DFT (G <= 32).  DIF: natural order in, slot q holds output
+// bitrev(q).  DIT (inverse, unnormalised): bit-reversed in, natural out.
+template <int G, int ST, int OFF, int NV>
+__device__ __forceinline__ void dft_dif(float2 (&v)[NV]) {
+    if constexpr (G >= 32) stage<G, ST, OFF, 16, false>(v);
     if constexpr (G >= 16) stage<G, ST, OFF, 8, false>(v);
     if constexpr (G >= 8) stage<G, ST, OFF, 4, false>(v);
     if constexpr (G >= 4) stage<G, ST, OFF, 2, false>(v);
     if constexpr (G >= 2) stage<G, ST, OFF, 1, false>(v);
 }
 
-template <int G, int ST, int OFF>
-__device__ __forceinline__ void dft_dit(float2 (&v)[16]) {
+template <int G, int ST, int OFF, int NV>
+__device__ __forceinline__ void dft_dit(float2 (&v)[NV]) {
     if constexpr (G >= 2) stage<G, ST, OFF, 1, true>(v);
     if constexpr (G >= 4) stage<G, ST, OFF, 2, true>(v);
     if constexpr (G >= 8) stage<G, ST, OFF, 4, true>(v);
     if constexpr (G >= 16) stage<G, ST, OFF, 8, true>(v);
+    if constexpr (G >= 32) stage<G, ST, OFF, 16, true>(v);
 }
 
 // A table entry by an ordinary global load, kept in program order: read-only
@@ -137,8 +152,8 @@ __device__ __forceinline__ float4 ld_tw4(const float4* p) {
 // interleaved as one float4 per group position i at float4 index k*sub + i
 // (one 16-byte load for two slots; consecutive i are consecutive words), and
 // the last slot of an odd count is a plain row of float2 after the pairs.
-template <int G, int ST, int OFF, bool INV, int Q = 1>
-__device__ __forceinline__ void twiddle_group(float2 (&v)[16], const float2* __restrict__ tp, int i, int sub) {
+template <int G, int ST, int OFF, bool INV, int Q = 1, int NV>
+__device__ __forceinline__ void twiddle_group(float2 (&v)[NV], const float2* __restrict__ tp, int i, int sub) {
     if constexpr (Q < G) {
         constexpr int j0 = OFF + Q * ST;
         if constexpr (Q + 1 < G) {
@@ -157,15 +172,28 @@ __device__ __forceinline__ void twiddle_group(float2 (&v)[16], const float2* __r
 // Padded shared-memory index: one float2 of padding per 16.
 __device__ __forceinline__ int pad(int n) { return n + (n >> 4); }
 
+// Shape of the M = 2^m point transform.  PT = 16 points per thread (T = M/16
+// threads): a first pass of radix G0 = 2^(m mod 4) (radix 16 when m is a
+// multiple of 4), then radix-16 passes.  PT = 32 (m = 14: 512 threads):
+// passes of radix 32 over spans M and M/32, then radix 16 over span 16, each
+// thread holding two 16-point groups; one shared-memory exchange fewer than
+// four passes need, and the second one stays within half-warps.
 template <int LOGM>
 struct FftShape {
     static constexpr int M = 1 << LOGM;
-    static constexpr int T = M / 16;
-    static constexpr int R0 = LOGM % 4;  // first pass radix 2^R0 (0: radix 16)
-    static constexpr int G0 = R0 ? 1 << R0 : 16;
-    static constexpr int NP = R0 ? 1 + LOGM / 4 : LOGM / 4;  // passes
-    static constexpr int span(int p) { return p == 0 ? M : (M / G0) >> (4 * (p - 1)); }
-    static constexpr int radix(int p) { return p == 0 ? G0 : 16; }
+    static constexpr int PT = fft_pt(LOGM);
+    static_assert(PT == 16 || LOGM == 14, "32 points per thread: 16384-point transforms only");
+    static constexpr int T = M / PT;
+    // CTAs per SM the launch bounds ask for: 1024 threads at 64 registers,
+    // or one 512-thread CTA of up to 128 registers (32 complex points each)
+    static constexpr int MINB = PT == 32 ? 1 : 16384 >> LOGM;
+    static constexpr int R0 = PT == 16 ? LOGM % 4 : 0;  // first pass radix 2^R0 (0: radix PT)
+    static constexpr int G0 = R0 ? 1 << R0 : PT;
+    static constexpr int NP = PT == 32 ? 3 : (R0 ? 1 + LOGM / 4 : LOGM / 4);  // passes
+    static constexpr int span(int p) {
+        return PT == 32 ? (p == 0 ? M : p == 1 ? M / 32 : 16) : (p == 0 ? M : (M / G0) >> (4 * (p - 1)));
+    }
+    static constexpr int radix(int p) { return PT == 32 ? (p < 2 ? 32 : 16) : (p == 0 ? G0 : 16); }
     static constexpr int sub(int p) { return span(p) / radix(p); }
     // offset of pass p's twiddle table ((radix - 1) rows of `sub` entries;
     // passes with sub = 1 have none)
@@ -175,26 +203,37 @@ struct FftShape {
             if (sub(q) > 1) o += (radix(q) - 1) * sub(q);
         return o;
     }
+    // padded shared-memory index: one float2 per 16 (PT = 16) or per 32
+    __host__ __device__ static constexpr int pad(int n) { return PT == 32 ? n + (n >> 5) : n + (n >> 4); }
 };
 
 // Padded shared-memory position of register j of thread t in pass P, as
-// base(t) + j * STRIDE.  Pass 0 (span M): point t + T*j.  A radix-16 pass over
-// span S (sub = S/16, which is 256, 16 or 1): point (t / sub) * S + t % sub +
-// j * sub; with sub a multiple of 16 the padding adds j * sub/16, and with
-// sub = 1 the point is 16t + j, padded 17t + j.
+// base(t) + off(j).  PT = 16: pass 0 (span M): point t + T*j.  A radix-16
+// pass over span S (sub = S/16, which is 256, 16 or 1): point
+// (t / sub) * S + t % sub + j * sub; with sub a multiple of 16 the padding
+// adds j * sub/16, and with sub = 1 the point is 16t + j, padded 17t + j.
+// PT = 32 (padding one per 32): pass 0: point t + 512 j, padded
+// pad(t) + 528 j; pass 1 (span 512, sub 16): point (t/16) * 512 + t%16 +
+// 16 j, padded base + 16 j + j/2 (t%16 < 16); pass 2 (span 16, two groups):
+// point 32t + j, padded 33t + j.  In each pattern the 16 lanes of a
+// half-warp touch 16 consecutive float2 (or a stride of 17 or 33): no bank
+// conflicts.
 template <int LOGM, int P>
 struct Layout {
     using F = FftShape<LOGM>;
-    static constexpr int S = F::span(P), SUB = P == 0 ? F::T : S / 16;
+    static constexpr int S = F::span(P), SUB = P == 0 ? F::T : F::sub(P);
     static_assert(SUB == 1 || SUB % 16 == 0, "pass layout");
-    static constexpr int STRIDE = SUB == 1 ? 1 : SUB + SUB / 16;
+    static constexpr int STRIDE = SUB == 1 ? 1 : SUB + SUB / (F::PT == 32 ? 32 : 16);
+    static constexpr int off(int j) {
+        return (F::PT == 32 && SUB == 16) ? 16 * j + j / 2 : j * STRIDE;
+    }
     __device__ static __forceinline__ int base(int t) {
         if constexpr (P == 0) {
-            return pad(t);
+            return F::pad(t);
         } else if constexpr (SUB == 1) {
-            return 17 * t;
+            return (F::PT + 1) * t;
         } else {
-            return pad((t / SUB) * S + t % SUB);
+            return F::pad((t / SUB) * S + t % SUB);
         }
     }
 };
@@ -219,30 +258,41 @@ __device__ __forceinline__ void first_groups(float2 (&v)[16], const float2* __re
 }
 
 template <int LOGM, int P, bool INV>
-__device__ __forceinline__ void run_pass(float2 (&v)[16], const float2* __restrict__ tw, int t) {
+__device__ __forceinline__ void run_pass(float2 (&v)[FftShape<LOGM>::PT], const float2* __restrict__ tw, int t) {
     using F = FftShape<LOGM>;
-    if constexpr (P == 0 && F::R0 != 0) {
+    if constexpr (F::PT == 16 && P == 0 && F::R0 != 0) {
         first_groups<LOGM, INV>(v, tw + F::tw_off(0), t);
+    } else if constexpr (F::radix(P) < F::PT) {
+        // 32 points per thread, last pass (span 16): groups in registers
+        // 0..15 and 16..31, no twiddles
+        static_assert(F::radix(P) == 16 && F::sub(P) == 1, "two 16-point groups");
+        if constexpr (!INV) {
+            dft_dif<16, 1, 0>(v);
+            dft_dif<16, 1, 16>(v);
+        } else {
+            dft_dit<16, 1, 0>(v);
+            dft_dit<16, 1, 16>(v);
+        }
     } else {
-        constexpr int sub = F::sub(P);
+        constexpr int R = F::radix(P), sub = F::sub(P);
         const float2* tp = tw + F::tw_off(P);
         const int i = t % sub;
         if constexpr (!INV) {
-            dft_dif<16, 1, 0>(v);
-            if constexpr (sub > 1) twiddle_group<16, 1, 0, false>(v, tp, i, sub);
+            dft_dif<R, 1, 0>(v);
+            if constexpr (sub > 1) twiddle_group<R, 1, 0, false>(v, tp, i, sub);
         } else {
-            if constexpr (sub > 1) twiddle_group<16, 1, 0, true>(v, tp, i, sub);
-            dft_dit<16, 1, 0>(v);
+            if constexpr (sub > 1) twiddle_group<R, 1, 0, true>(v, tp, i, sub);
+            dft_dit<R, 1, 0>(v);
         }
     }
 }
 
 // Threads that exchange points between pass p and pass p + 1 (either way):
-// those of one span block of pass p, a contiguous run of span(p) / 16
+// those of one span block of pass p, a contiguous run of span(p) / PT
 // threads (all of them after the first pass).
 template <int LOGM>
 constexpr int xgroup(int p) {
-    return p == 0 ? FftShape<LOGM>::T : FftShape<LOGM>::span(p) / 16;
+    return p == 0 ? FftShape<LOGM>::T : FftShape<LOGM>::span(p) / FftShape<LOGM>::PT;
 }
 
 // Barrier over the G-thread group of thread t: the whole CTA, a warp, or a
@@ -266,24 +316,25 @@ __device__ __forceinline__ void group_sync(int t) {
 // from the previous exchange (group size PREVG, 0: none) must be done, so the
 // barrier there covers the wider of the two groups.
 template <int LOGM, int P, int Q, int PREVG>
-__device__ __forceinline__ void exchange(float2 (&v)[16], float2* sb, int t) {
+__device__ __forceinline__ void exchange(float2 (&v)[FftShape<LOGM>::PT], float2* sb, int t) {
     constexpr int G = xgroup<LOGM>(P < Q ? P : Q);
     constexpr int PRE = PREVG > G ? PREVG : G;
     if constexpr (PREVG > 0) group_sync<LOGM, PRE>(t);
     float2* w = sb + Layout<LOGM, P>::base(t);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) w[j * Layout<LOGM, P>::STRIDE] = v[j];
+    for (int j = 0; j < FftShape<LOGM>::PT; ++j) w[Layout<LOGM, P>::off(j)] = v[j];
     group_sync<LOGM, G>(t);
     const float2* r = sb + Layout<LOGM, Q>::base(t);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = r[j * Layout<LOGM, Q>::STRIDE];
+    for (int j = 0; j < FftShape<LOGM>::PT; ++j) v[j] = r[Layout<LOGM, Q>::off(j)];
 }
 
 // Forward passes P.. and inverse passes ..0; PREVG is the group of the
 // exchange before (0: none).  Returns nothing; the exchange group sizes are
 // compile-time, so the barriers cost only what the data movement requires.
 template <int LOGM, int P, int PREVG = 0>
-__device__ __forceinline__ void forward_from(float2 (&v)[16], const float2* __restrict__ tw, float2* sb, int t) {
+__device__ __forceinline__ void forward_from(float2 (&v)[FftShape<LOGM>::PT], const float2* __restrict__ tw,
+                                             float2* sb, int t) {
     run_pass<LOGM, P, false>(v, tw, t);
     if constexpr (P + 1 < FftShape<LOGM>::NP) {
         exchange<LOGM, P, P + 1, PREVG>(v, sb, t);
@@ -292,7 +343,8 @@ __device__ __forceinline__ void forward_from(float2 (&v)[16], const float2* __re
 }
 
 template <int LOGM, int P, int PREVG = 0>
-__device__ __forceinline__ void inverse_from(float2 (&v)[16], const float2* __restrict__ tw, float2* sb, int t) {
+__device__ __forceinline__ void inverse_from(float2 (&v)[FftShape<LOGM>::PT], const float2* __restrict__ tw,
+                                             float2* sb, int t) {
     run_pass<LOGM, P, true>(v, tw, t);
     if constexpr (P > 0) {
         exchange<LOGM, P, P - 1, PREVG>(v, sb, t);
@@ -312,24 +364,24 @@ constexpr int last_forward_group() {
 // [0, N) or when !live1.  REV: the rows hold their samples in reverse time
 // (sample n at row[N - 1 - n]); the warps' reads stay contiguous.
 template <int LOGM, bool REV = false>
-__device__ __forceinline__ void load_pair(float2 (&v)[16], const float* x0, const float* x1, bool live1, int64_t s0,
-                                          int64_t s1, int64_t N, int t) {
+__device__ __forceinline__ void load_pair(float2 (&v)[FftShape<LOGM>::PT], const float* x0, const float* x1,
+                                          bool live1, int64_t s0, int64_t s1, int64_t N, int t) {
     using F = FftShape<LOGM>;
     if (live1 && s0 >= 0 && s1 >= 0 && s0 + F::M <= N && s1 + F::M <= N) {
         if constexpr (!REV) {
             const float* p0 = x0 + s0 + t;
             const float* p1 = x1 + s1 + t;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = make_float2(__ldg(p0 + F::T * j), __ldg(p1 + F::T * j));
+            for (int j = 0; j < F::PT; ++j) v[j] = make_float2(__ldg(p0 + F::T * j), __ldg(p1 + F::T * j));
         } else {
             const float* p0 = x0 + (N - 1 - s0) - t;
             const float* p1 = x1 + (N - 1 - s1) - t;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = make_float2(__ldg(p0 - F::T * j), __ldg(p1 - F::T * j));
+            for (int j = 0; j < F::PT; ++j) v[j] = make_float2(__ldg(p0 - F::T * j), __ldg(p1 - F::T * j));
         }
     } else {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
+        for (int j = 0; j < F::PT; ++j) {
             const int64_t n0 = s0 + t + F::T * j, n1 = s1 + t + F::T * j;
             v[j].x = (n0 >= 0 && n0 < N) ? __ldg(x0 + (REV ? N - 1 - n0 : n0)) : 0.f;
             v[j].y = (live1 && n1 >= 0 && n1 < N) ? __ldg(x1 + (REV ? N - 1 - n1 : n1)) : 0.f;
@@ -343,14 +395,14 @@ __device__ __forceinline__ void load_pair(float2 (&v)[16], const float* x0, cons
 // j of thread t is point t + T j: one row pointer per thread, a constant
 // offset per register, and one unsigned compare per store.
 template <int LOGM, bool REV = false>
-__device__ __forceinline__ void store_pair(const float2 (&v)[16], float* y0, float* y1, int64_t b0, int64_t b1,
-                                           int64_t N, int first, int m0, int m1, int t) {
+__device__ __forceinline__ void store_pair(const float2 (&v)[FftShape<LOGM>::PT], float* y0, float* y1, int64_t b0,
+                                           int64_t b1, int64_t N, int first, int m0, int m1, int t) {
     using F = FftShape<LOGM>;
     float* p0 = REV ? y0 + (N - 1 - b0 + first) - t : y0 + (b0 - first) + t;
     float* p1 = REV ? y1 + (N - 1 - b1 + first) - t : y1 + (b1 - first) + t;
     const int o0 = t - first;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
+    for (int j = 0; j < F::PT; ++j) {
         const int o = o0 + F::T * j;
         if ((unsigned)o < (unsigned)m0) p0[REV ? -F::T * j : F::T * j] = v[j].x;
         if ((unsigned)o < (unsigned)m1) p1[REV ? -F::T * j : F::T * j] = v[j].y;
@@ -362,7 +414,8 @@ __device__ __forceinline__ void store_pair(const float2 (&v)[16], float* y0, flo
 // t0 / t1 and g0 / g1 laid out like y0 / y1); returns this thread's sum of
 // d^2 (FP32, at most 32 terms).
 template <int LOGM>
-__device__ __forceinline__ float store_pair_mse(const float2 (&v)[16], float* y0, float* y1, const float* t0,
+__device__ __forceinline__ float store_pair_mse(const float2 (&v)[FftShape<LOGM>::PT], float* y0, float* y1,
+                                                const float* t0,
                                                 const float* t1, float* g0, float* g1, int64_t b0, int64_t b1,
                                                 int first, int m0, int m1, int t, float gs) {
     using F = FftShape<LOGM>;
@@ -377,7 +430,7 @@ __device__ __forceinline__ float store_pair_mse(const float2 (&v)[16], float* y0
     float acc = 0.f;
     // four registers' targets in flight at a time
 #pragma unroll
-    for (int j0 = 0; j0 < 16; j0 += 4) {
+    for (int j0 = 0; j0 < F::PT; j0 += 4) {
         float tv0[4], tv1[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {

@@ -16,29 +16,31 @@
 // product and one inverse FFT give both blocks' outputs (real part, imaginary
 // part).
 //
-// Register-resident radix-16 FFT.  M = 2^m (m = 10..13) points, T = M/16
-// threads, 16 points per thread.  The forward transform is decimation in
-// frequency in passes over spans M, M/G1, ..., 16: a first pass of radix
-// G1 = 2^(m mod 4) (radix 16 when m is a multiple of 4), then radix-16
-// passes.  A pass over span S = G * sub takes, for each i < sub, the G points
-// i + j*sub of each span, forms their G-point DFT in registers (radix-2 DIF
-// stages with constant twiddles; slot j then holds output bitrev(j)) and
-// multiplies slot j by w_S^(i * bitrev(j)), w_S = e^(-2 pi i / S).  Points move
-// between passes through shared memory padded by one word per 16 (no bank
+// Register-resident radix-16 FFT.  M = 2^m (m = 10..14) points, T = M/PT
+// threads, PT = 16 points per thread (32 at m = 14).  The forward transform
+// is decimation in frequency in passes over spans M, M/G1, ..., 16: a first
+// pass of radix G1 = 2^(m mod 4) (radix 16 when m is a multiple of 4), then
+// radix-16 passes; at m = 14 passes of radix 32, 32 and 16, each thread
+// taking two 16-point groups in the last.  A pass over span S = G * sub
+// takes, for each i < sub, the G points i + j*sub of each span, forms their
+// G-point DFT in registers (radix-2 DIF stages with constant twiddles; slot
+// j then holds output bitrev(j)) and multiplies slot j by
+// w_S^(i * bitrev(j)), w_S = e^(-2 pi i / S).  Points move between passes
+// through shared memory padded by one word per 16 (per 32 at m = 14; no bank
 // conflicts for any pass's pattern).  After the last pass (span 16) thread t
-// holds points 16t..16t+15 of the spectrum in bit-reversed order; the
-// spectrum of h is stored in that order with the 1/M scale folded in (float4
-// q of thread t, points 16t + 2q and 16t + 2q + 1, at index q*T + t, so that
-// a warp's reads are contiguous), the product needs no permutation, and the
-// inverse runs the passes backwards
-// (conjugate twiddles, then the DIT G-point DFT), ending in natural order in
-// the layout the input was loaded in: point t + T*j in register j, so both the
-// input loads and the output stores are coalesced.  Each pass with twiddles
-// reads them from its own table (two slots' twiddles per 16-byte word, by
-// group position), computed in FP64 at plan time and rounded once:
-// consecutive threads read consecutive words, and every point takes one
-// complex multiply per pass.  Complex sums and differences are packed
-// two-lane FP32 instructions (real and imaginary part in one register pair).
+// holds points PT t .. PT t + PT - 1 of the spectrum in bit-reversed order;
+// the spectrum of h is stored in that order with the 1/M scale folded in
+// (float4 q of thread t, points PT t + 2q and PT t + 2q + 1, at index
+// q*T + t, so that a warp's reads are contiguous), the product needs no
+// permutation, and the inverse runs the passes backwards (conjugate
+// twiddles, then the DIT G-point DFT), ending in natural order in the layout
+// the input was loaded in: point t + T*j in register j, so both the input
+// loads and the output stores are coalesced.  Each pass with twiddles reads
+// them from its own table (two slots' twiddles per 16-byte word, by group
+// position), computed in FP64 at plan time and rounded once: consecutive
+// threads read consecutive words, and every point takes one complex
+// multiply per pass.  Complex sums and differences are packed two-lane FP32
+// instructions (real and imaginary part in one register pair).
 #include "fft_core.cuh"
 
 namespace tfx {
@@ -61,14 +63,14 @@ __device__ __forceinline__ void fft_block_pair(const FirFftArgs& a, int64_t pr, 
     const bool wrap = r0 + 1u == nbpc;
     const unsigned c1 = live1 && wrap ? c0 + 1u : c0, r1 = live1 ? (wrap ? 0u : r0 + 1u) : 0u;
     const int64_t n00 = (int64_t)r0 * a.B, n01 = (int64_t)r1 * a.B;
-    float2 v[16];
+    float2 v[F::PT];
     load_pair<LOGM, REV>(v, a.x + c0 * a.ldx, a.x + c1 * a.ldx, live1, n00 - Hh, n01 - Hh, a.N, t);
     forward_from<LOGM, 0>(v, a.tw, sb, t);
-    // spectrum product: thread t holds positions 16t .. 16t + 15, stored as
-    // float4 q (positions 16t + 2q, 16t + 2q + 1) at index q*T + t
+    // spectrum product: thread t holds positions PT t .. PT t + PT - 1,
+    // stored as float4 q (positions PT t + 2q, PT t + 2q + 1) at index q*T + t
     const float4* h4 = reinterpret_cast<const float4*>(a.H) + t;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < F::PT / 2; ++q) {
         const float4 h = ld_tw4(h4 + q * F::T);
         v[2 * q] = cmul(v[2 * q], make_float2(h.x, h.y));
         v[2 * q + 1] = cmul(v[2 * q + 1], make_float2(h.z, h.w));
@@ -99,7 +101,7 @@ __device__ __forceinline__ void fft_block_pair(const FirFftArgs& a, int64_t pr, 
 
 // Single-block overlap-save: CTA k transforms blocks 2k and 2k + 1.
 template <int LOGM, bool REV, bool MSE = false>
-__global__ void __launch_bounds__((1 << LOGM) / 16, 16384 >> LOGM) k_fir_fft(FirFftArgs a) {
+__global__ void __launch_bounds__(FftShape<LOGM>::T, FftShape<LOGM>::MINB) k_fir_fft(FirFftArgs a) {
     extern __shared__ float2 sb[];
     fft_block_pair<LOGM, REV, MSE>(a, blockIdx.x, sb, threadIdx.x);
 }
@@ -109,7 +111,7 @@ __global__ void __launch_bounds__((1 << LOGM) / 16, 16384 >> LOGM) k_fir_fft(Fir
 // binary search over the clips' block-pair prefix sums, then transforms that
 // clip's block pair k - prefix[clip] with the clip's own spectrum.
 template <int LOGM>
-__global__ void __launch_bounds__((1 << LOGM) / 16, 16384 >> LOGM)
+__global__ void __launch_bounds__(FftShape<LOGM>::T, FftShape<LOGM>::MINB)
     k_fir_fft_batched(const BatchFft* __restrict__ units, const int64_t* __restrict__ prefix, int nunits,
                       BatchBases bases, const float2* __restrict__ tw) {
     extern __shared__ float2 sb[];
@@ -149,9 +151,9 @@ __global__ void __launch_bounds__((1 << LOGM) / 16, 16384 >> LOGM)
 
 // Partitioned overlap-save, step 1: the spectrum of segment b of a channel
 // pair, x[(b - 1) B, (b + 1) B) of channels 2r (re) and 2r + 1 (im), stored
-// like H: float4 q of thread t (positions 16t + 2q, 16t + 2q + 1) at q*T + t.
+// like H: float4 q of thread t (positions PT t + 2q, PT t + 2q + 1) at q*T + t.
 template <int LOGM>
-__global__ void __launch_bounds__((1 << LOGM) / 16, 16384 >> LOGM) k_fir_fft_spec(FirFftArgs a) {
+__global__ void __launch_bounds__(FftShape<LOGM>::T, FftShape<LOGM>::MINB) k_fir_fft_spec(FirFftArgs a) {
     using F = FftShape<LOGM>;
     extern __shared__ float2 sb[];
     const int t = threadIdx.x;
@@ -161,12 +163,12 @@ __global__ void __launch_bounds__((1 << LOGM) / 16, 16384 >> LOGM) k_fir_fft_spe
     const bool live1 = c0 + 1 < a.C;
     const float* x0 = a.x + c0 * a.ldx;
     const int64_t s0 = ((int64_t)b - 1) * a.B;
-    float2 v[16];
+    float2 v[F::PT];
     load_pair<LOGM>(v, x0, live1 ? x0 + a.ldx : x0, live1, s0, s0, a.N, t);
     forward_from<LOGM, 0>(v, a.tw, sb, t);
     float4* z = reinterpret_cast<float4*>(a.Z + pb * F::M) + t;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) z[q * F::T] = make_float4(v[2 * q].x, v[2 * q].y, v[2 * q + 1].x, v[2 * q + 1].y);
+    for (int q = 0; q < F::PT / 2; ++q) z[q * F::T] = make_float4(v[2 * q].x, v[2 * q].y, v[2 * q + 1].x, v[2 * q + 1].y);
 }
 
 // Partitioned overlap-save, step 2: block b of a channel pair is the inverse
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__((1 << LOGM) / 16, 16384 >> LOGM) k_fir_fft_spe
 // partitions of B taps, h_p[k] = h[pB + k]), whose last B points are outputs
 // [bB, (b + 1) B).
 template <int LOGM>
-__global__ void __launch_bounds__((1 << LOGM) / 16, 16384 >> LOGM) k_fir_fft_conv(FirFftArgs a) {
+__global__ void __launch_bounds__(FftShape<LOGM>::T, FftShape<LOGM>::MINB) k_fir_fft_conv(FirFftArgs a) {
     using F = FftShape<LOGM>;
     extern __shared__ float2 sb[];
     const int t = threadIdx.x;
@@ -182,15 +184,15 @@ __global__ void __launch_bounds__((1 << LOGM) / 16, 16384 >> LOGM) k_fir_fft_con
     const unsigned r = blockIdx.x / (unsigned)a.nbpc, b = blockIdx.x - r * (unsigned)a.nbpc;
     const int64_t c0 = 2 * (int64_t)r;
     const bool live1 = c0 + 1 < a.C;
-    float2 v[16];
+    float2 v[F::PT];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = make_float2(0.f, 0.f);
+    for (int j = 0; j < F::PT; ++j) v[j] = make_float2(0.f, 0.f);
     const int np = (int)b + 1 < a.P ? (int)b + 1 : a.P;
     for (int p = 0; p < np; ++p) {
         const float4* h4 = reinterpret_cast<const float4*>(a.H + (int64_t)p * F::M) + t;
         const float4* z4 = reinterpret_cast<const float4*>(a.Z + (pb - p) * F::M) + t;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < F::PT / 2; ++q) {
             const float4 h = __ldg(h4 + q * F::T), z = __ldg(z4 + q * F::T);
             v[2 * q].x = fmaf(z.x, h.x, fmaf(-z.y, h.y, v[2 * q].x));
             v[2 * q].y = fmaf(z.x, h.y, fmaf(z.y, h.x, v[2 * q].y));
@@ -212,7 +214,7 @@ __global__ void __launch_bounds__((1 << LOGM) / 16, 16384 >> LOGM) k_fir_fft_con
 // stores it as the filter reads it: scaled by 1/M, bit-reversed, float4 q of
 // thread t at q*T + t.
 template <int LOGM>
-__global__ void __launch_bounds__((1 << LOGM) / 16, 16384 >> LOGM)
+__global__ void __launch_bounds__(FftShape<LOGM>::T, FftShape<LOGM>::MINB)
     k_fir_fft_spectrum(const double* __restrict__ taps, int L, int B, int P, const float2* __restrict__ tw,
                        float2* __restrict__ H) {
     using F = FftShape<LOGM>;
@@ -221,9 +223,9 @@ __global__ void __launch_bounds__((1 << LOGM) / 16, 16384 >> LOGM)
     const int part = blockIdx.x;
     const int64_t first = P > 0 ? (int64_t)part * B : 0;
     const int len = P > 0 ? B : L;
-    float2 v[16];
+    float2 v[F::PT];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
+    for (int j = 0; j < F::PT; ++j) {
         const int n = t + F::T * j;
         const int64_t k = first + n;
         v[j] = make_float2(n < len && k < L ? (float)taps[k] : 0.f, 0.f);
@@ -232,14 +234,14 @@ __global__ void __launch_bounds__((1 << LOGM) / 16, 16384 >> LOGM)
     const float inv = 1.0f / (float)F::M;
     float4* h4 = reinterpret_cast<float4*>(H + (int64_t)part * F::M) + t;
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
+    for (int q = 0; q < F::PT / 2; ++q)
         h4[q * F::T] = make_float4(v[2 * q].x * inv, v[2 * q].y * inv, v[2 * q + 1].x * inv, v[2 * q + 1].y * inv);
 }
 
 template <int LOGM>
 cudaError_t launch_spectrum_log(const double* taps, int L, int B, int P, const float2* tw, float2* H,
                                 cudaStream_t s) {
-    constexpr int T = (1 << LOGM) / 16;
+    constexpr int T = FftShape<LOGM>::T;
     const size_t smem = fir_fft_smem_bytes(1 << LOGM);
     k_fir_fft_spectrum<LOGM><<<(unsigned)(P > 0 ? P : 1), T, smem, s>>>(taps, L, B, P, tw, H);
     return cudaGetLastError();
@@ -247,7 +249,7 @@ cudaError_t launch_spectrum_log(const double* taps, int L, int B, int P, const f
 
 template <int LOGM>
 cudaError_t launch_log(const FirFftArgs& a, cudaStream_t s) {
-    constexpr int T = (1 << LOGM) / 16;
+    constexpr int T = FftShape<LOGM>::T;
     const size_t smem = fir_fft_smem_bytes(1 << LOGM);
     if (a.P == 0) {
         if (a.loss && a.rev) return cudaErrorInvalidValue;
@@ -304,7 +306,7 @@ cudaError_t prepare_fir_fft(int M) {
 template <int LOGM>
 cudaError_t launch_batched_log(const BatchFft* units, const int64_t* prefix, int nunits, int64_t ctas,
                                BatchBases bases, const float2* tw, cudaStream_t s) {
-    constexpr int T = (1 << LOGM) / 16;
+    constexpr int T = FftShape<LOGM>::T;
     const size_t smem = fir_fft_smem_bytes(1 << LOGM);
     k_fir_fft_batched<LOGM><<<(unsigned)ctas, T, smem, s>>>(units, prefix, nunits, bases, tw);
     return cudaGetLastError();

@@ -75,6 +75,7 @@ __device__ __forceinline__ void section_at(const double* r, dcplx z1, dcplx z2, 
 template <int LOGM>
 __global__ void __launch_bounds__((1 << LOGM) / 16, LOGM <= 12 ? 2 : 1) k_chain_xcorr(XcorrArgs a) {
     using F = FftShape<LOGM>;
+    static_assert(F::PT == 16, "the spectral kernels use 4096- and 8192-point transforms");
     extern __shared__ float2 sb[];
     float2* zx = sb + (F::M + F::M / 16);  // the input window's spectrum, each thread its own slots
     const int t = threadIdx.x;
@@ -337,6 +338,7 @@ template <int LOGM>
 __device__ __forceinline__ void inverse_of_storage(const float2* __restrict__ W, float2 (&v)[16],
                                                    const float2* __restrict__ tw, float2* sb, int t) {
     using F = FftShape<LOGM>;
+    static_assert(F::PT == 16, "the spectral kernels use 4096- and 8192-point transforms");
     const float4* w4 = reinterpret_cast<const float4*>(W) + t;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -354,6 +356,7 @@ __global__ void __launch_bounds__((1 << LOGM) / 16, 1) k_chain_grads_fir(const f
                                                                          const float2* __restrict__ tw, int L,
                                                                          double* __restrict__ dh) {
     using F = FftShape<LOGM>;
+    static_assert(F::PT == 16, "the spectral kernels use 4096- and 8192-point transforms");
     extern __shared__ float2 sb[];
     const int t = threadIdx.x;
     float2 v[16];
@@ -375,6 +378,7 @@ __global__ void __launch_bounds__((1 << LOGM) / 16, 1) k_chain_tail(const float2
                                                                     const float2* __restrict__ tw, int J,
                                                                     int* __restrict__ status) {
     using F = FftShape<LOGM>;
+    static_assert(F::PT == 16, "the spectral kernels use 4096- and 8192-point transforms");
     extern __shared__ float2 sb[];
     __shared__ float red[2][32];
     const int t = threadIdx.x;

@@ -231,9 +231,9 @@ struct FftScheme {
     int M = 0, P = 0;
 };
 
-// Single-block cost per (M / B) for m = 10..14 (m = 14: one 1024-thread CTA
-// per SM, 16384 points), measured with B between M/4 and 7M/8.
-const double FFT_K[5] = {60.0, 63.0, 72.0, 111.0, 140.0};
+// Single-block cost per (M / B) for m = 10..14 (m = 14: one 512-thread CTA
+// per SM, 32 points per thread), measured with B between M/4 and 7M/8.
+const double FFT_K[5] = {60.0, 63.0, 72.0, 111.0, 125.0};
 
 double fft_single_cost(int m, int L) {
     const int M = 1 << m, B = M - (L - 1);
@@ -247,8 +247,6 @@ FftScheme fft_scheme_for(int L, int force, double* cost_out = nullptr) {
     double cost = 0.0;
     for (int m = 10; m <= 14; ++m) {
         if (force >= 10 && force <= 14 && m != force) continue;
-        // 16384 points: single-block only, and only where smaller transforms cannot hold the taps
-        if (m == 14 && force != 14 && L - 1 < 3 * 8192 / 4) continue;
         const double c1 = fft_single_cost(m, L);
         if (c1 > 0.0 && (best.M == 0 || c1 < cost)) best.M = 1 << m, best.P = 0, cost = c1;
         if (m <= 13 && (m >= 11 || force == m)) {
@@ -303,7 +301,8 @@ std::vector<double> conv_fft(const std::vector<double>& a, const std::vector<dou
 
 // Twiddle tables of the overlap-save transform of M = 2^m points: its passes
 // run over spans M, M/G0, ..., 16 (G0 = 2^(m mod 4), or 16), radix G0 first
-// and 16 after; a pass over span S with radix G and sub = S/G > 1 has the
+// and 16 after (32 points per thread, m = 14: spans M, M/32, 16 with radix
+// 32, 32, 16); a pass over span S with radix G and sub = S/G > 1 has the
 // twiddles w(q, i) = e^(-2 pi i * i * bitrev_G(q) / S), q = 1..G-1, i < sub,
 // stored as pairs (w(2k + 1, i), w(2k + 2, i)) at [k][i], then the row of
 // w(G - 1, i) when G - 1 is odd.
@@ -312,11 +311,16 @@ std::vector<std::complex<double>> fft_pass_twiddles(int m) {
     const int M = 1 << m, r = m % 4;
     std::vector<std::pair<int, int>> passes;
     int S = M;
-    if (r) {
-        passes.push_back({S, 1 << r});
-        S >>= r;
+    if (fft_pt(m) == 32) {
+        for (; S > 16; S >>= 5) passes.push_back({S, 32});
+        passes.push_back({16, 16});
+    } else {
+        if (r) {
+            passes.push_back({S, 1 << r});
+            S >>= r;
+        }
+        for (; S >= 16; S >>= 4) passes.push_back({S, 16});
     }
-    for (; S >= 16; S >>= 4) passes.push_back({S, 16});
     for (const auto& ps : passes) {
         const int Sp = ps.first, G = ps.second, sub = Sp / G;
         if (sub == 1) continue;
@@ -713,14 +717,15 @@ void fill_fft_tables(const HostUnit& u, char* host) {
         std::vector<std::complex<double>> Hc(M, 0.0);
         for (int k = 0; k < plen && q * plen + k < u.L; ++k) Hc[k] = u.taps[q * plen + k];
         host_fft(Hc);
-        // position k = 16t + 2c + e (thread t, float4 c, half e) holds
-        // H[bitrev(k)] / M and is stored at float2 index 2 (c T + t) + e
+        // position k = PT t + 2c + e (thread t, float4 c, half e; PT points
+        // per thread) holds H[bitrev(k)] / M and is stored at float2 index
+        // 2 (c T + t) + e
         float2* Hd = reinterpret_cast<float2*>(host + u.off_H) + (size_t)q * M;
-        const int T = M / 16;
+        const int PT = fft_pt(u.fft_m), T = M / PT;
         for (int k = 0; k < M; ++k) {
             int r = 0;
             for (int b = 0; b < u.fft_m; ++b) r |= ((k >> b) & 1) << (u.fft_m - 1 - b);
-            const int t = k / 16, c = (k % 16) / 2, e = k % 2;
+            const int t = k / PT, c = (k % PT) / 2, e = k % 2;
             Hd[2 * (c * T + t) + e] = make_float2((float)(Hc[r].real() / M), (float)(Hc[r].imag() / M));
         }
     }

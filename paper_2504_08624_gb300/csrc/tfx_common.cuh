@@ -29,6 +29,11 @@ constexpr int FIR_PAD = 32;
 // Device-side bounded waits give up after this long and record TFX_ERR_TIMEOUT.
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;
 
+// Points each thread holds in the register-resident FFT of M = 2^m points
+// (host and device agree on it: it fixes the spectra's storage order): 16,
+// or 32 for 16384 points (512 threads, radix-32 passes).
+__host__ __device__ constexpr int fft_pt(int m) { return m == 14 ? 32 : 16; }
+
 // Per-unit device constants (one "unit" = an optional SOS cascade followed
 // by an optional FIR; consecutive SOS stages are merged into one cascade).
 struct UnitConst {
