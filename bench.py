@@ -316,14 +316,18 @@ def measure_link(x_host, y_host, dev, torch, reps: int = 5) -> dict:
 
 def traffic_for(kernel: str, workload_name: str):
     """DRAM bytes per launch of ``kernel`` from the committed ncu summary, or
-    None when the summary is missing or the kernel source changed since."""
+    None when the summary is missing or the kernel's sources (one file, or
+    several hashed in order) changed since."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         e = d[kernel][workload_name]
-        src = os.path.join(ROOT, e["source"])
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        srcs = e["source"] if isinstance(e["source"], list) else [e["source"]]
+        hs = hashlib.sha256()
+        for src in srcs:
+            hs.update(open(os.path.join(ROOT, src), "rb").read())
+        h = hs.hexdigest()[:16]
         if h != e["source_sha256_16"]:
             return None
         return float(e["dram_bytes_per_launch"])
