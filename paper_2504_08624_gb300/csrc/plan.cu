@@ -223,10 +223,13 @@ void choose_segments(const tfx_plan* p, HostUnit& u, int sm_count) {
 // measured GB300 times per output (16 channels x 2.88M samples, L2 flushed
 // between calls, microseconds for the whole signal): single-block
 // 30 + k_m M / B with k_m from FFT_K (the 30 is the memory traffic, the rest
-// the transforms); partitioned I_m + s_m P with I = 219, 230, 253, 326 and
-// s = 20, 21.4, 23.6, 24.7 for m = 10..13 (two launches and the spectra
-// traffic).  A single block must hold B >= M/8 outputs.  `force` (10..13)
-// restricts the choice to that m.
+// the transforms); partitioned I_m + s_m P with I = 219, 230, 253, 326, 357
+// and s = 20, 21.4, 23.6, 24.7, 26 for m = 10..14 (two launches and the
+// spectra traffic; m = 14 from the 16384-tap FIR, 2 partitions, 0.96 of the
+// time of 8192 points with 4, its per-partition cost taken near m = 13's: the
+// spectra bytes per output and partition do not depend on M).  A single
+// block must hold B >= M/8 outputs.  `force` (10..14) restricts the choice
+// to that m.
 struct FftScheme {
     int M = 0, P = 0;
 };
@@ -241,15 +244,15 @@ double fft_single_cost(int m, int L) {
 }
 
 FftScheme fft_scheme_for(int L, int force, double* cost_out = nullptr) {
-    static const double I[4] = {219.0, 230.0, 253.0, 326.0};
-    static const double SP[4] = {20.0, 21.4, 23.6, 24.7};
+    static const double I[5] = {219.0, 230.0, 253.0, 326.0, 357.0};
+    static const double SP[5] = {20.0, 21.4, 23.6, 24.7, 26.0};
     FftScheme best;
     double cost = 0.0;
     for (int m = 10; m <= 14; ++m) {
         if (force >= 10 && force <= 14 && m != force) continue;
         const double c1 = fft_single_cost(m, L);
         if (c1 > 0.0 && (best.M == 0 || c1 < cost)) best.M = 1 << m, best.P = 0, cost = c1;
-        if (m <= 13 && (m >= 11 || force == m)) {
+        if (m >= 11 || force == m) {
             const int M = 1 << m;
             const int P = (L + M / 2 - 1) / (M / 2);
             const double c = I[m - 10] + SP[m - 10] * P;
