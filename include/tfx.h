@@ -360,7 +360,10 @@ int tfx_chain(const float *x, float *y, int64_t C, int64_t N, int64_t ld,
  * filtering.  The work is ordered after prior work on s and s waits for it:
  * synchronise s before reading y.  The first call for a configuration
  * builds its plans and allocates the device slots (host-synchronous); later
- * calls allocate nothing.
+ * calls allocate nothing.  With x and y page-locked the whole pipeline is
+ * captured once into a CUDA graph (again when x, y or ld change) and each
+ * call is one graph launch on s: the host thread's timing no longer paces
+ * the copies.  Do not call it while s is being captured.
  * Errors: as tfx_chain, plus TFX_ERR_NOMEM for the device slots.
  */
 int tfx_chain_host(const float *x, float *y, int64_t C, int64_t N, int64_t ld,
@@ -368,6 +371,14 @@ int tfx_chain_host(const float *x, float *y, int64_t C, int64_t N, int64_t ld,
 
 /* Release the cached host-buffer pipelines (synchronises the device). */
 void tfx_host_cache_clear(void);
+
+/* Introspection of the host-buffer pipelines: *pipes = the number cached,
+ * *graphed = how many of them hold a captured CUDA graph (each call of
+ * tfx_chain_host with page-locked x and y replays its configuration's
+ * graph, capturing it first when the buffers changed; pageable buffers
+ * enqueue the pipeline call by call).  Either pointer may be NULL.
+ * Returns TFX_OK. */
+int tfx_host_cache_info(int32_t *pipes, int32_t *graphed);
 
 /* Workspace tfx_chain needs for these arguments (SIZE_MAX if invalid). */
 size_t tfx_chain_workspace_size(int64_t C, int64_t N, int64_t ld,

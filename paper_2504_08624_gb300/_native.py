@@ -49,7 +49,7 @@ EXPORTS = [
     "tfx_plan_execute_plain",
     "tfx_plan_get_error", "tfx_plan_destroy", "tfx_fir", "tfx_sos", "tfx_chain",
     "tfx_chain_workspace_size", "tfx_cache_clear", "tfx_sos_noalloc", "tfx_strerror", "tfx_version",
-    "tfx_chain_host", "tfx_host_cache_clear",
+    "tfx_chain_host", "tfx_host_cache_clear", "tfx_host_cache_info",
     "tfx_plan_saved_size", "tfx_plan_backward_workspace_size", "tfx_plan_coef_count", "tfx_plan_forward_train",
     "tfx_plan_forward_train_mse", "tfx_plan_forward_train_mse_launch_count",
     "tfx_plan_backward", "tfx_plan_backward_launch_count", "tfx_mse",
@@ -132,6 +132,8 @@ def lib():
     L.tfx_chain_host.restype = ctypes.c_int
     L.tfx_host_cache_clear.argtypes = []
     L.tfx_host_cache_clear.restype = None
+    L.tfx_host_cache_info.argtypes = [ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    L.tfx_host_cache_info.restype = ctypes.c_int
     L.tfx_chain_workspace_size.argtypes = [i64, i64, i64, sp, i32]
     L.tfx_chain_workspace_size.restype = sz
     L.tfx_sos_noalloc.argtypes = [fp, fp, i64, i64, i64, dp, i32, vp]

@@ -4,6 +4,13 @@
 // ring of three device slots, so that the host<->device copies of
 // neighbouring groups overlap each other and the filtering.  The plans,
 // slots, streams and events are library-owned and cached per configuration.
+// With both host buffers page-locked the whole pipeline (every group's
+// copies, kernels and stream dependencies) is captured once into a CUDA
+// graph and replayed with one launch per call, so the host thread issues one
+// call instead of several per group and a delayed host thread no longer
+// delays the copies; it is captured again when the buffers change.
+// Pageable buffers (whose copies cannot be captured) run the same pipeline
+// enqueued call by call.
 #include <cstring>
 #include <list>
 #include <mutex>
@@ -30,11 +37,22 @@ struct HostPipe {
     cudaStream_t sin = nullptr, scomp = nullptr, sout = nullptr;
     cudaEvent_t ev_in[RING] = {}, ev_comp[RING] = {}, ev_out[RING] = {};
     cudaEvent_t ev_fork = nullptr, ev_join[3] = {};
+    // the captured pipeline and the buffers it was captured for
+    cudaStream_t scap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    const float* gx = nullptr;
+    float* gy = nullptr;
+    int64_t gld = 0;
+    int capture_failures = 0;
 };
 
 void destroy_pipe(HostPipe* h) {
     if (!h) return;
     cudaDeviceSynchronize();
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    if (h->scap) cudaStreamDestroy(h->scap);
     tfx_plan_destroy(h->plan_full);
     tfx_plan_destroy(h->plan_last);
     if (h->ws) cudaFree(h->ws);
@@ -82,6 +100,7 @@ int build_pipe(int64_t C, int64_t N, const tfx_stage* st, int32_t nst, HostPipe*
     ok = cudaStreamCreateWithFlags(&h->sin, cudaStreamNonBlocking) == cudaSuccess &&
          cudaStreamCreateWithFlags(&h->scomp, cudaStreamNonBlocking) == cudaSuccess &&
          cudaStreamCreateWithFlags(&h->sout, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&h->scap, cudaStreamNonBlocking) == cudaSuccess &&
          cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess;
     for (int r = 0; r < RING && ok; ++r)
         ok = cudaEventCreateWithFlags(&h->ev_in[r], cudaEventDisableTiming) == cudaSuccess &&
@@ -96,7 +115,8 @@ int build_pipe(int64_t C, int64_t N, const tfx_stage* st, int32_t nst, HostPipe*
     return TFX_OK;
 }
 
-int run_pipe(HostPipe* h, const float* x, float* y, int64_t ld, cudaStream_t s) {
+// Enqueue the pipeline on stream s (fork to the three streams, join back).
+int enqueue_pipe(HostPipe* h, const float* x, float* y, int64_t ld, cudaStream_t s) {
     const int64_t N = h->N;
 #define TFX_CK(call)                              \
     do {                                          \
@@ -131,6 +151,70 @@ int run_pipe(HostPipe* h, const float* x, float* y, int64_t ld, cudaStream_t s) 
     for (int k = 0; k < 3; ++k) TFX_CK(cudaStreamWaitEvent(s, h->ev_join[k], 0));
 #undef TFX_CK
     return TFX_OK;
+}
+
+bool page_locked(const void* p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+// Capture the pipeline for (x, y, ld) on the library's own stream (the
+// caller's may be the legacy default stream, which cannot capture) into
+// h->gexec: updated in place when the graph's shape allows, else
+// instantiated anew.  False if anything in the capture failed.
+bool capture_pipe(HostPipe* h, const float* x, float* y, int64_t ld) {
+    if (cudaStreamBeginCapture(h->scap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const int rc = enqueue_pipe(h, x, y, ld, h->scap);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->scap, &g);
+    if (rc != TFX_OK || e != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return false;
+    }
+    bool ok = false;
+    if (h->gexec) {
+        cudaGraphExecUpdateResultInfo info{};
+        ok = cudaGraphExecUpdate(h->gexec, g, &info) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(h->gexec);
+            h->gexec = nullptr;
+        }
+    }
+    if (!ok) ok = cudaGraphInstantiate(&h->gexec, g, 0) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        h->gexec = nullptr;
+        cudaGraphDestroy(g);
+        return false;
+    }
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->graph = g;
+    h->gx = x;
+    h->gy = y;
+    h->gld = ld;
+    return true;
+}
+
+// Replay the captured pipeline (capturing it first for new buffers) when
+// both buffers are page-locked; otherwise, or after two failed captures for
+// this configuration, enqueue it call by call.
+int run_pipe(HostPipe* h, const float* x, float* y, int64_t ld, cudaStream_t s) {
+    if (h->capture_failures < 2 && page_locked(x) && page_locked(y)) {
+        const bool have = h->gexec && h->gx == x && h->gy == y && h->gld == ld;
+        if (have || capture_pipe(h, x, y, ld))
+            return cudaGraphLaunch(h->gexec, s) == cudaSuccess ? TFX_OK : TFX_ERR_CUDA;
+        ++h->capture_failures;
+    }
+    return enqueue_pipe(h, x, y, ld, s);
 }
 
 std::mutex g_hmu;
@@ -206,4 +290,16 @@ extern "C" void tfx_host_cache_clear(void) {
     for (auto& kv : g_hcache) destroy_pipe(kv.second.first);
     g_hcache.clear();
     g_hlru.clear();
+}
+
+extern "C" int tfx_host_cache_info(int32_t* pipes, int32_t* graphed) {
+    std::lock_guard<std::mutex> lk(g_hmu);
+    int32_t n = 0, g = 0;
+    for (auto& kv : g_hcache) {
+        ++n;
+        if (kv.second.first->gexec) ++g;
+    }
+    if (pipes) *pipes = n;
+    if (graphed) *graphed = g;
+    return TFX_OK;
 }

@@ -326,6 +326,45 @@ def test_host_pipeline_groups(mode):
     assert_close(got, ref, tol_for(stages), mode)
 
 
+def test_host_pipeline_graph_replay():
+    """With page-locked buffers tfx_chain_host replays one captured CUDA
+    graph per configuration: the same buffers twice (replayed), then other
+    buffers with other content (captured again), each against the oracle;
+    pageable buffers run the pipeline call by call (no graph)."""
+    import ctypes
+    from paper_2504_08624_gb300 import api, _native as N
+    lib = N.lib()
+    stages = [("sos", W.butter_sos(2, 2000.0, 48000.0)), ("fir", W.fir_lowpass(33, 6000.0, 48000.0))]
+    C, Ns = 300, 100000
+    x = W.white_uniform(C, Ns, 62)
+    ref = oracle_chain(x, stages)
+
+    def info():
+        a, b = ctypes.c_int32(), ctypes.c_int32()
+        assert lib.tfx_host_cache_info(ctypes.byref(a), ctypes.byref(b)) == 0
+        return a.value, b.value
+
+    lib.tfx_host_cache_clear()
+    xp = torch.from_numpy(x).pin_memory()
+    yp = torch.empty(C, Ns, dtype=torch.float32).pin_memory()
+    for rep in range(2):
+        yp.fill_(0.0)
+        api.chain(xp, stages, out=yp)
+        assert_close(yp.numpy(), ref, tol_for(stages), f"replay {rep}")
+        assert info() == (1, 1)
+    xr = np.ascontiguousarray(x[::-1])
+    x2 = torch.from_numpy(xr).pin_memory()
+    y2 = torch.empty(C, Ns, dtype=torch.float32).pin_memory()
+    api.chain(x2, stages, out=y2)
+    assert_close(y2.numpy(), oracle_chain(xr, stages), tol_for(stages), "captured again")
+    assert info() == (1, 1)
+    lib.tfx_host_cache_clear()
+    got = api.chain(torch.from_numpy(x), stages).numpy()
+    assert_close(got, ref, tol_for(stages), "pageable")
+    assert info() == (1, 0)
+    lib.tfx_host_cache_clear()
+
+
 @pytest.mark.parametrize("mode", ["fp16_split", "bf16_split", "bf16_plain"])
 def test_long_fir_streamed_taps(mode):
     """The 16384-tap Kaiser band-pass of the long-FIR workload (tap tables
