@@ -1107,7 +1107,8 @@ def measure_batched(dev, stream, torch, dist, ws, rank, local, pk, fp32, steps, 
     for g, (kind, level, tiles, samples, flops) in enumerate(b.groups()):
         k_g = 5
         t_g = time_gpu(lambda: b.execute_group(g, x, y, wsb), k_g, 2, stream, torch, None) / k_g
-        groups.append({"kind": ["fused cascade+FIR", "cascade", "tensor-core FIR", "composed chain (FFT)"][kind],
+        groups.append({"kind": ["fused cascade+FIR", "cascade", "tensor-core FIR", "composed chain (FFT)",
+                                "FFT FIR"][kind],
                        "level": level,
                        "tiles": tiles, "channel_samples": samples, "ms": t_g * 1e3,
                        "algorithmic_tflops": flops / t_g / 1e12})
@@ -1117,7 +1118,7 @@ def measure_batched(dev, stream, torch, dist, ws, rank, local, pk, fp32, steps, 
         roof = {"bound": "tensor", "kernel": "k_fir_tc_batched", "peak": pk["bf16_tflops_sustained"],
                 "peak_source": f"{pk['source']} dense bf16/fp16 sustained", "achieved": dg["algorithmic_tflops"],
                 "unit": "TFLOP/s"}
-    elif dg["kind"] == "composed chain (FFT)":
+    elif dg["kind"] in ("composed chain (FFT)", "FFT FIR"):
         roof = {"bound": "hbm", "kernel": "k_fir_fft_batched", "peak": pk["hbm_gbs"],
                 "peak_source": f"{pk['source']} HBM copy bandwidth", "unit": "GB/s",
                 "achieved": dg["channel_samples"] * 8.0 / (dg["ms"] * 1e-3) / 1e9,

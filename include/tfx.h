@@ -484,7 +484,8 @@ void tfx_batch_destroy(tfx_batch *b);
 
 /* The batch's launches, for profiling: group g's kind (0 fused cascade +
  * CUDA-core FIR, 1 cascade, 2 tensor-core FIR, 3 composed chains by FFT of
- * one transform size), its level in the chains, its
+ * one transform size, 4 FIR units of clips that keep their units, by
+ * single-block FFT of one transform size), its level in the chains, its
  * tiles, the channel-samples it filters and its algorithmic flops (10 per
  * section-sample, 2 L per FIR sample); tfx_batch_execute_group runs group g
  * alone (its inputs must hold what the earlier levels write). */

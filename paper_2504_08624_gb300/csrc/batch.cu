@@ -9,7 +9,8 @@
 // chain) run by FFT overlap-save, all clips of one transform size in ONE
 // launch.  The batch groups the other clips' units by position in their
 // chain (level) and by kernel (fused cascade + short FIR, cascade only,
-// tensor-core FIR) and runs every group as ONE launch whose tiles span all of
+// FFT FIR by transform size, tensor-core FIR for FIRs a single FFT block
+// cannot hold) and runs every group as ONE launch whose tiles span all of
 // its units.  In either kind of launch a CTA maps its ticket (or block index)
 // to a unit by binary search over the units' tile prefix sums, so each
 // unit's tiles keep their time-major order.  Buffer
@@ -28,7 +29,7 @@ using namespace tfx;
 
 namespace {
 
-enum GroupKind { G_FUSED = 0, G_CASCADE = 1, G_FIR = 2, G_CHAIN_FFT = 3 };
+enum GroupKind { G_FUSED = 0, G_CASCADE = 1, G_FIR = 2, G_CHAIN_FFT = 3, G_FFT = 4 };
 
 struct Group {
     int level = 0;
@@ -43,7 +44,7 @@ struct Group {
     std::vector<BatchUnit> units;
     std::vector<BatchFir> firs;
     std::vector<BatchFft> ffts;
-    int fft_m = 0;                  // composed chains: transform size 2^fft_m
+    int fft_m = 0;                  // FFT groups: transform size 2^fft_m
     const float2* tw = nullptr;     // its twiddle tables (in one of the clips' plans)
     std::vector<int64_t> prefix;
 };
@@ -79,9 +80,10 @@ int batch_build(tfx_batch* b, const tfx_clip* clips, int32_t n, const tfx_batch_
     // A clip whose chain composes (its cascades' response decays; see
     // compose_chain) runs as one FFT FIR of its composite response, batched
     // with every other composed clip of the same transform size in one
-    // launch.  The other clips' units run on the tensor cores or fused with a
-    // cascade, grouped by level and kernel.
-    const uint32_t pflags = prm.plan_flags | TFX_PLAN_FIR_TC | TFX_PLAN_SCAN_LOOKBACK;
+    // launch.  The other clips' units run grouped by level and kernel: FIRs by
+    // single-block FFT overlap-save where a block holds the taps (else on the
+    // tensor cores), short FIRs fused with a cascade.
+    const uint32_t pflags = prm.plan_flags | TFX_PLAN_SCAN_LOOKBACK;
     if (pflags & (TFX_PLAN_SCAN_WARP_TILES | TFX_PLAN_TRAINABLE | TFX_PLAN_TEST_DROP_PUBLISH | TFX_PLAN_UNFUSED |
                   TFX_PLAN_FIR_FFT))
         return TFX_ERR_UNSUPPORTED;
@@ -109,6 +111,17 @@ int batch_build(tfx_batch* b, const tfx_clip* clips, int32_t n, const tfx_batch_
         }
         rc = plan_create_ex(&b->plans[i], c.C, c.N, c.N > 0 ? c.N : 1, c.st, c.nst, pflags, prm.tc_min_taps, false);
         if (rc != TFX_OK) return rc;
+        // a partitioned FFT FIR (two launches and a spectra workspace) is not
+        // batched: such a clip's FIRs go to the tensor cores
+        bool partitioned = false;
+        for (const HostUnit& u : b->plans[i]->units) partitioned = partitioned || (u.fft && u.fft_P > 0);
+        if (partitioned) {
+            tfx_plan_destroy(b->plans[i]);
+            b->plans[i] = nullptr;
+            rc = plan_create_ex(&b->plans[i], c.C, c.N, c.N > 0 ? c.N : 1, c.st, c.nst, pflags | TFX_PLAN_FIR_TC,
+                                prm.tc_min_taps, false);
+            if (rc != TFX_OK) return rc;
+        }
     }
     b->total = off;
     if (cudaMalloc(&b->dstatus, sizeof(int)) != cudaSuccess) return TFX_ERR_NOMEM;
@@ -175,6 +188,13 @@ int batch_build(tfx_batch* b, const tfx_clip* clips, int32_t n, const tfx_batch_
             g[k].kind = k;
             g[k].prefix.push_back(0);
         }
+        Group gf[5];  // FFT FIR units by transform size 2^(10 + k)
+        for (int k = 0; k < 5; ++k) {
+            gf[k].level = lev;
+            gf[k].kind = G_FFT;
+            gf[k].fft_m = 10 + k;
+            gf[k].prefix.push_back(0);
+        }
         // header offsets are relative to the group's header start for now
         size_t hdr[3] = {ALIGN, ALIGN, ALIGN};
         size_t tails[3] = {0, 0, 0};
@@ -189,6 +209,31 @@ int batch_build(tfx_batch* b, const tfx_clip* clips, int32_t n, const tfx_batch_
             const int x_sel = ib < 0 ? 0 : 2, y_sel = ob < 0 ? 1 : 2;
             const int64_t x_off = ib < 0 ? b->off[i] : (int64_t)(inter[i][ib] / sizeof(float));
             const int64_t y_off = ob < 0 ? b->off[i] : (int64_t)(inter[i][ob] / sizeof(float));
+            if (u.fft) {  // single-block (partitioned units were sent to the tensor cores)
+                int m = 0;
+                while ((1 << m) < u.fft_M) ++m;
+                if (u.fft_P != 0 || m < 10 || m > 14) return TFX_ERR_UNSUPPORTED;
+                Group& gr = gf[m - 10];
+                BatchFft f{};
+                f.x_sel = x_sel;
+                f.y_sel = y_sel;
+                f.x_off = x_off;
+                f.y_off = y_off;
+                f.C = p->C;
+                f.N = p->N;
+                f.L = u.L;
+                f.B = u.fft_B;
+                f.nbpc = (p->N + u.fft_B - 1) / u.fft_B;
+                f.nb = p->C * f.nbpc;
+                f.H = reinterpret_cast<const float2*>(p->dconst + u.off_H);
+                if (!gr.tw) gr.tw = reinterpret_cast<const float2*>(p->dconst + u.off_tw);
+                gr.ffts.push_back(f);
+                gr.tiles += (f.nb + 1) / 2;
+                gr.prefix.push_back(gr.tiles);
+                gr.samples += p->C * p->N;
+                gr.flops += 2.0 * u.L * (double)(p->C * p->N);
+                continue;
+            }
             if (u.tc) {
                 tc_geometry(u, NB);
                 if (u.tc_smem > SMEM_MAX) return TFX_ERR_UNSUPPORTED;  // tap tables too large to batch
@@ -289,15 +334,21 @@ int batch_build(tfx_batch* b, const tfx_clip* clips, int32_t n, const tfx_batch_
             if (k == G_FIR && prepare_fir_tc_batched(gr.smem) != cudaSuccess) return TFX_ERR_UNSUPPORTED;
             b->groups.push_back(gr);
         }
+        for (Group& gr : gf) {
+            gr.nunits = (int)gr.ffts.size();
+            if (gr.nunits == 0) continue;
+            if (gr.tiles > (int64_t)INT32_MAX) return TFX_ERR_UNSUPPORTED;
+            b->groups.push_back(gr);
+        }
     }
     b->ws_bytes = ws;
 
     // descriptors and prefix sums of every group in one device blob
     size_t blob = 0;
     auto desc_bytes = [](const Group& gr) {
-        return gr.kind == G_FIR ? gr.firs.size() * sizeof(BatchFir)
-               : gr.kind == G_CHAIN_FFT ? gr.ffts.size() * sizeof(BatchFft)
-                                        : gr.units.size() * sizeof(BatchUnit);
+        return gr.kind == G_FIR                             ? gr.firs.size() * sizeof(BatchFir)
+               : gr.kind == G_CHAIN_FFT || gr.kind == G_FFT ? gr.ffts.size() * sizeof(BatchFft)
+                                                            : gr.units.size() * sizeof(BatchUnit);
     };
     for (Group& gr : b->groups) {
         gr.desc_off = blob;
@@ -310,7 +361,7 @@ int batch_build(tfx_batch* b, const tfx_clip* clips, int32_t n, const tfx_batch_
         for (const Group& gr : b->groups) {
             if (gr.kind == G_FIR)
                 std::memcpy(host.data() + gr.desc_off, gr.firs.data(), gr.firs.size() * sizeof(BatchFir));
-            else if (gr.kind == G_CHAIN_FFT)
+            else if (gr.kind == G_CHAIN_FFT || gr.kind == G_FFT)
                 std::memcpy(host.data() + gr.desc_off, gr.ffts.data(), gr.ffts.size() * sizeof(BatchFft));
             else
                 std::memcpy(host.data() + gr.desc_off, gr.units.data(), gr.units.size() * sizeof(BatchUnit));
@@ -324,7 +375,7 @@ int batch_build(tfx_batch* b, const tfx_clip* clips, int32_t n, const tfx_batch_
 
 int run_group(tfx_batch* b, const Group& gr, const BatchBases& bases, char* w, cudaStream_t s) {
     const int64_t* prefix = reinterpret_cast<const int64_t*>(b->ddesc + gr.prefix_off);
-    if (gr.kind == G_CHAIN_FFT)
+    if (gr.kind == G_CHAIN_FFT || gr.kind == G_FFT)
         return launch_fir_fft_batched(gr.fft_m, reinterpret_cast<const BatchFft*>(b->ddesc + gr.desc_off), prefix,
                                       gr.nunits, gr.tiles, bases, gr.tw, s) == cudaSuccess
                    ? TFX_OK

@@ -56,9 +56,9 @@ def run_batch(clips, **params):
 
 
 def _single_tc(xi, st, plain=False):
-    """The single-clip path with the batch's routing: long FIRs on the tensor
-    cores (the default single-clip route sends FIRs of 64+ taps to the FFT);
-    with plain=True the plain sequential FP32 path of the same chain."""
+    """The single-clip path as an independent route: FIRs on the tensor cores
+    (the batch and the default single-clip route send FIRs of 64+ taps to the
+    FFT); with plain=True the plain sequential FP32 path of the same chain."""
     from paper_2504_08624_gb300 import _native as N_
     from paper_2504_08624_gb300 import api
     C, Ns = xi.shape
@@ -103,7 +103,9 @@ def test_batch_graph_capture_and_launch_count():
     from paper_2504_08624_gb300 import api
     clips = small_clips()
     b, xs, x, y = run_batch(clips)
-    assert 1 <= b.launches_per_execute <= 8  # a few batched launches, not one per clip
+    # a few batched launches, not one per clip (23 here): at most one per
+    # (level, kernel, transform size) and one copy per empty-chain clip
+    assert 1 <= b.launches_per_execute <= 12
     y2 = b.empty()
     ws = b.workspace()
     s = torch.cuda.Stream()
