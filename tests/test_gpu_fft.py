@@ -24,15 +24,12 @@ pytestmark = pytest.mark.gpu
 def _scheme(L, force=None):
     """(M, P) the plan's cost model picks (P = 0: single block): single-block
     30 + k_m M / B (B >= M/8), partitioned I_m + s_m P, fitted per m."""
-    K = {10: 71.0, 11: 74.0, 12: 77.0, 13: 113.0, 14: 143.0}
-    I = {10: 219.0, 11: 230.0, 12: 253.0, 13: 326.0}
-    SP = {10: 20.0, 11: 21.4, 12: 23.6, 13: 24.7}
+    K = {10: 60.0, 11: 63.0, 12: 72.0, 13: 111.0, 14: 125.0}
+    I = {10: 219.0, 11: 230.0, 12: 253.0, 13: 326.0, 14: 357.0}
+    SP = {10: 20.0, 11: 21.4, 12: 23.6, 13: 24.7, 14: 26.0}
     best = None
     for m in range(10, 15):
         if force is not None and m != force:
-            continue
-        # 16384 points: single-block only, where smaller transforms cannot hold the taps
-        if m == 14 and force != 14 and L - 1 < 3 * 8192 // 4:
             continue
         M = 1 << m
         B = M - (L - 1)
@@ -40,7 +37,7 @@ def _scheme(L, force=None):
             c = 30.0 + K[m] * M / B
             if best is None or c < best[0]:
                 best = (c, M, 0)
-        if m <= 13 and (m >= 11 or force == m):
+        if m >= 11 or force == m:
             P = -(-L // (M // 2))
             c = I[m] + SP[m] * P
             if best is None or c < best[0]:
@@ -154,7 +151,7 @@ def test_partitioned_fir_lengths(L):
         check_fft(x, [("fir", _taps(L, L))])
 
 
-@pytest.mark.parametrize("m", [10, 11, 12, 13])
+@pytest.mark.parametrize("m", [10, 11, 12, 13, 14])
 def test_partitioned_every_transform_size(m):
     """Partitioned scheme at each forced transform size, P from 2 to 5."""
     from paper_2504_08624_gb300 import _native as N_
@@ -172,19 +169,20 @@ def test_partitioned_inplace_and_stride(inplace):
 
 def test_partitioned_long_bandpass():
     """The 16384-tap Kaiser band-pass of the long-FIR workload, on its signal
-    recipe, partitioned (and at both of the large transform sizes)."""
+    recipe, partitioned (and at each of the large transform sizes)."""
     from paper_2504_08624_gb300 import _native as N_
     wl = W.long_fir()
     x = wl.make_signal(3, 3 * 16384 + 1234)
     check_fft(x, wl.stages, 1e-5)
-    for m in (12, 13):
+    for m in (12, 13, 14):
         check_fft(x, wl.stages, 1e-5, flags=N_.TFX_PLAN_FIR_FFT_LOG(m))
 
 
 @pytest.mark.parametrize("m", [10, 11, 12, 13, 14])
 def test_fft_fir_every_transform_size(m):
-    """Each transform size (radix-4, -8, -16, -2 and -4 first passes; 16384
-    points with 1024-thread CTAs) on a FIR it can hold, with a ragged tail."""
+    """Each transform size (radix-4, -8, -16 and -2 first passes; 16384
+    points with 512-thread CTAs of 32 points, radix 32, 32, 16) on a FIR it
+    can hold, with a ragged tail."""
     from paper_2504_08624_gb300 import _native as N_
     L = (1 << m) // 4 + 1
     B = (1 << m) - (L - 1)

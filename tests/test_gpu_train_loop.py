@@ -118,6 +118,28 @@ def test_update_coefs_forward_plan(flags):
     assert_close(yp.cpu().numpy(), ref, 1e-4, f"{flags}: plain path after update")
 
 
+@pytest.mark.parametrize("L", [7000, 16384])
+def test_update_coefs_long_fft_firs(L):
+    """FIR taps replaced on the device where the FFT unit uses 16384-point
+    transforms (32 points per thread): single-block at 7000 taps, two
+    partitions of 8192 taps at 16384; the spectra are rebuilt on the GPU by
+    the same transform the filter runs."""
+    from paper_2504_08624_gb300 import api
+    h0 = W.fir_lowpass(L, 3000.0, W.FS)
+    x = W.white_gauss(3, 3 * 16384 + 1234, 77)
+    xt = torch.from_numpy(x).cuda()
+    p = api.Plan(3, x.shape[1], [("fir", h0)])
+    d = p.describe()
+    assert d[0]["kind"] == "fir_fft" and d[0]["M"] == 16384 and (d[0]["P"] > 0) == (L > 12289), d
+    h1 = h0 * np.random.default_rng(L).uniform(0.5, 1.5, L)
+    p.update_coefs(torch.from_numpy(h1).cuda())
+    y = p.execute(xt)
+    torch.cuda.synchronize()
+    assert p.get_error() == 0
+    p.close()
+    assert_close(y.cpu().numpy(), oracle_chain(x, [("fir", h1)]), 1e-5, f"{L} taps after update")
+
+
 def test_update_coefs_refused_for_tensor_core_firs():
     from paper_2504_08624_gb300 import api, _native as N_
     wl = W.multichannel_fused()
