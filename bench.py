@@ -595,7 +595,12 @@ def measure_fwdbwd(wl, steps, warmup, dev, stream, torch, dist, ws, rank, pk, sm
     def bwd():
         plan.backward(x, g, dx, dcoef, saved, bws)
 
-    def step():
+    tws = plan.train_workspace()
+
+    def step():  # one call: forward, loss, backward (fused on the spectral route)
+        plan.train_step_mse(x, y, target, g, lossbuf, dx, dcoef, saved, tws)
+
+    def two_calls():  # the same step as forward_train_mse + backward
         fwd_loss()
         bwd()
 
@@ -630,37 +635,42 @@ def measure_fwdbwd(wl, steps, warmup, dev, stream, torch, dist, ws, rank, pk, sm
     t_l = time_gpu(loss_step, k_parts, 2, stream, torch, None) / k_parts
     t_b = time_gpu(bwd, k_parts, 2, stream, torch, None) / k_parts
     t_fl = time_gpu(fwd_loss, k_parts, 2, stream, torch, None) / k_parts
-    fwd_loss()
+    t_two = time_gpu(two_calls, k_parts, 2, stream, torch, None) / k_parts
+    step()
     torch.cuda.synchronize()
     # y, g, dx and dcoef now hold one consistent training step
     parity = fwdbwd_parity(wl, x, y, g, dx, torch, api, NAT) if (with_parity and rank == 0) else None
-    launches = plan.forward_train_mse_launches + plan.backward_launches(True, True)
+    launches = plan.train_step_launches(True, True)
     step_s = t / steps
 
     route = plan.describe()
     roof = None
     parts = None
     if route and route[0]["kind"] == "chain_spectral":
-        # spectral route: the forward and the input gradient are one FFT FIR
-        # launch each (8 B per sample: read one signal, write one), the
-        # coefficient gradients one correlation launch over x and g (8 B per
-        # sample read) and four launches of M-point size; each part timed
-        # alone through the plan's own calls
+        # spectral route: the step is one fused launch (forward, loss and the
+        # correlation of g with x: read x and the target, write y and g,
+        # 16 B per sample) with the coefficient gradients' four small
+        # launches after it, and the input gradient (one reverse-time FFT
+        # FIR: read g, write dx, 8 B per sample) on a side stream beside
+        # them; each part timed alone through the plan's own calls
         k_k = max(10, steps // 3)
         t_dx = time_gpu(lambda: plan.backward(x, g, dx, None, saved, bws), k_k, 3, stream, torch, None) / k_k
-        t_dc = time_gpu(lambda: plan.backward(x, g, None, dcoef, saved, bws), k_k, 3, stream, torch, None) / k_k
-        parts = {"forward (k_fir_fft)": t_f, "dL/dx (k_fir_fft, reverse time)": t_dx,
-                 "dL/dcoef (k_chain_xcorr + k_xcorr_reduce + k_chain_grads_sec + k_chain_grads_fir + "
-                 "k_spectral_finalize)": t_dc}
+        t_fz = time_gpu(lambda: plan.train_step_mse(x, y, target, g, lossbuf, None, dcoef, saved, tws), k_k, 3,
+                        stream, torch, None) / k_k
+        step()
+        name_f = ("forward + MSE + correlation (k_fir_fft_train) + coefficient gradients (k_xcorr_reduce + "
+                  "k_chain_grads_sec + k_chain_grads_fir + k_spectral_finalize)")
+        parts = {name_f: t_fz, "dL/dx (k_fir_fft, reverse time)": t_dx}
+        bytes_per = {name_f: 16.0, "dL/dx (k_fir_fft, reverse time)": 8.0}
         name, t_k = max(parts.items(), key=lambda kv: kv[1])
-        ach = units * 8.0 / t_k / 1e9
-        kern = "k_chain_xcorr" if name.startswith("dL/dcoef") else "k_fir_fft"
+        ach = units * bytes_per[name] / t_k / 1e9
+        kern = "k_fir_fft_train" if name == name_f else "k_fir_fft"
         roof = {"bound": "hbm", "kernel": kern, "part": name, "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / pk["hbm_gbs"], "kernel_ms": t_k * 1e3, "share_of_step": t_k / step_s,
                 "traffic": traffic_for(kern, wl.name), "peak_source": pk["source"],
                 "route": route[0],
-                "note": "8 algorithmic bytes per channel-sample for each part (forward: read x, write y; dL/dx: "
-                        "read g, write dx; correlation: read x and g)"}
+                "note": "algorithmic bytes per channel-sample of each part: the fused step 16 (read x and the "
+                        "target, write y and g), dL/dx 8 (read g, write dx)"}
         parts = {k: v * 1e3 for k, v in parts.items()}
     elif S > 0:
         # dominant kernel: the cascade's reverse-time adjoint scan, timed alone
@@ -739,8 +749,10 @@ def measure_fwdbwd(wl, steps, warmup, dev, stream, torch, dist, ws, rank, pk, sm
                          f"{dt:.1f} s"}
     plan.close()
     return {"workload": wl.name, "value": units * ws * steps / t_all, "unit": UNIT, "ms_per_step": step_s * 1e3,
-            "steps": steps, "step": "training forward with the MSE loss and dL/dy fused (tfx_plan_forward_train_mse) "
-                                    "+ backward (dL/dx, dL/dcoef)",
+            "steps": steps, "step": "one training step through tfx_plan_train_step_mse: forward, MSE loss and "
+                                    "dL/dy, backward (dL/dx, dL/dcoef); on the spectral route the forward, the "
+                                    "loss and the coefficient gradients' correlation are one launch",
+            "two_calls_ms": t_two * 1e3,
             "cuda_graph": graph is not None, "eager_ms_per_step": t_eager / steps * 1e3,
             "fwd_ms": t_f * 1e3, "loss_ms": t_l * 1e3, "fwd_loss_ms": t_fl * 1e3, "bwd_ms": t_b * 1e3,
             "gpu_launches_per_step": launches,
@@ -1382,7 +1394,8 @@ def run_fwdbwd_main(args, wl, dev, torch, dist, ws, rank, local):
             "roofline": r["roofline"], "roofline_hbm": r["roofline_hbm"], "cpu_baseline": r["cpu_baseline"],
             "e2e": r["e2e"], "plain_gpu": r["plain_gpu"],
             "gpu_launches": int(args.steps * r["gpu_launches_per_step"]), "clocks": clocks, "gpu": props.name,
-            "fwd_ms": r["fwd_ms"], "loss_ms": r["loss_ms"], "fwd_loss_ms": r["fwd_loss_ms"], "bwd_ms": r["bwd_ms"], "parity": r["parity"],
+            "fwd_ms": r["fwd_ms"], "loss_ms": r["loss_ms"], "fwd_loss_ms": r["fwd_loss_ms"], "bwd_ms": r["bwd_ms"],
+            "two_calls_ms": r["two_calls_ms"], "parts_ms": r["parts_ms"], "parity": r["parity"],
             "fp32_peak": fp32,
         }), flush=True)
     if dist is not None:

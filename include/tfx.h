@@ -319,6 +319,29 @@ int tfx_plan_backward(tfx_plan *p, const float *x, const float *g, float *dx,
 int tfx_plan_backward_launch_count(const tfx_plan *p, int with_dx, int with_dcoef);
 
 /*
+ * tfx_plan_train_step_mse -- one training step of the MSE loss: the result
+ * of tfx_plan_forward_train_mse (y, g = dL/dy, *loss, saved) followed by
+ * tfx_plan_backward with that g (dx and/or dcoef; both NULL: the forward
+ * alone), with the same arguments and the same rules for each pointer.  On a
+ * spectral plan (see TFX_PLAN_NO_COMPOSE) with dcoef requested, one fused
+ * launch does the forward, the loss and the block correlation of g with x
+ * (the forward's input spectra kept in shared memory, g transformed straight
+ * from the registers that store it), so x and g are not read a second time;
+ * the correlation is summed over other block pairings than in
+ * tfx_plan_backward, so dcoef agrees with the two calls to FP32 rounding
+ * (y, g and dx are the same).  ws: at least the larger of the two calls'
+ * sizes (tfx_plan_workspace_size, tfx_plan_backward_workspace_size).
+ * Errors: as the two calls.
+ */
+int tfx_plan_train_step_mse(tfx_plan *p, const float *x, float *y,
+                            const float *target, float *g, double *loss,
+                            float *dx, double *dcoef, void *saved,
+                            size_t saved_bytes, void *ws, size_t ws_bytes,
+                            tfx_stream s);
+/* Kernels one tfx_plan_train_step_mse launches (memsets excluded). */
+int tfx_plan_train_step_mse_launch_count(const tfx_plan *p, int with_dx, int with_dcoef);
+
+/*
  * tfx_mse -- mean squared error between y and target ([C x N], row stride
  * ld, device): *loss = mean((y - target)^2) (device FP64 scalar, written
  * after a reset on s), and g = dL/dy = 2 (y - target) / (C N) unless g is

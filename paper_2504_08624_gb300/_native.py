@@ -52,6 +52,7 @@ EXPORTS = [
     "tfx_chain_host", "tfx_host_cache_clear", "tfx_host_cache_info",
     "tfx_plan_saved_size", "tfx_plan_backward_workspace_size", "tfx_plan_coef_count", "tfx_plan_forward_train",
     "tfx_plan_forward_train_mse", "tfx_plan_forward_train_mse_launch_count",
+    "tfx_plan_train_step_mse", "tfx_plan_train_step_mse_launch_count",
     "tfx_plan_backward", "tfx_plan_backward_launch_count", "tfx_mse",
     "tfx_batch_create", "tfx_batch_total_samples", "tfx_batch_clip_offset", "tfx_batch_workspace_size",
     "tfx_batch_launch_count", "tfx_batch_execute", "tfx_batch_get_error", "tfx_batch_destroy",
@@ -152,6 +153,11 @@ def lib():
     L.tfx_plan_forward_train_mse.restype = ctypes.c_int
     L.tfx_plan_forward_train_mse_launch_count.argtypes = [vp]
     L.tfx_plan_forward_train_mse_launch_count.restype = ctypes.c_int
+    L.tfx_plan_train_step_mse.argtypes = [vp, fp, fp, fp, fp, ctypes.POINTER(ctypes.c_double), fp,
+                                          ctypes.POINTER(ctypes.c_double), vp, sz, vp, sz, vp]
+    L.tfx_plan_train_step_mse.restype = ctypes.c_int
+    L.tfx_plan_train_step_mse_launch_count.argtypes = [vp, i32, i32]
+    L.tfx_plan_train_step_mse_launch_count.restype = ctypes.c_int
     L.tfx_plan_backward.argtypes = [vp, fp, fp, fp, fp, vp, sz, vp, sz, vp]
     L.tfx_plan_backward.restype = ctypes.c_int
     L.tfx_plan_backward_launch_count.argtypes = [vp, ctypes.c_int, ctypes.c_int]

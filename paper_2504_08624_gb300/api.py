@@ -266,6 +266,42 @@ class Plan:
     def forward_train_mse_launches(self) -> int:
         return int(N.lib().tfx_plan_forward_train_mse_launch_count(self._h))
 
+    def train_workspace(self) -> torch.Tensor:
+        """A workspace large enough for both halves of a training step."""
+        if getattr(self, "_tws", None) is None:
+            n = max(1, self.workspace_size, self.backward_workspace_size)
+            self._tws = torch.empty(n, dtype=torch.uint8, device=self.device)
+        return self._tws
+
+    def train_step_mse(self, x: torch.Tensor, y: torch.Tensor, target: torch.Tensor, g: torch.Tensor,
+                       loss: torch.Tensor, dx: torch.Tensor | None, dcoef: torch.Tensor | None, saved: torch.Tensor,
+                       ws: torch.Tensor | None = None) -> torch.Tensor:
+        """One MSE training step (tfx_plan_train_step_mse): forward_train_mse
+        then backward with its g, fused on a spectral plan; returns loss."""
+        w = self.train_workspace() if ws is None else ws
+        x2, y2, _ = self._args(x, y, w)
+        t2, g2, _ = self._args(target, g, w)
+        if dx is not None:
+            self._args(dx, dx, w)
+        if not loss.is_cuda or loss.dtype != torch.float64 or loss.numel() < 1:
+            raise ValueError("loss: CUDA float64 tensor")
+        if dcoef is not None and (dcoef.dtype != torch.float64 or not dcoef.is_cuda
+                                  or dcoef.numel() < self.coef_count):
+            raise ValueError("dcoef must be a CUDA float64 tensor of coef_count values")
+        ptr = (lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None)
+        with torch.cuda.device(self.device):
+            rc = N.lib().tfx_plan_train_step_mse(
+                self._h, ptr(x2), ptr(y2), ptr(t2), ptr(g2),
+                ctypes.cast(ctypes.c_void_p(loss.data_ptr()), ctypes.POINTER(ctypes.c_double)), ptr(dx),
+                ctypes.cast(ptr(dcoef), ctypes.POINTER(ctypes.c_double)) if dcoef is not None else None,
+                ctypes.c_void_p(saved.data_ptr()), saved.numel(), ctypes.c_void_p(w.data_ptr()), w.numel(),
+                _stream_handle(self.device))
+        N.check(rc, "tfx_plan_train_step_mse")
+        return loss
+
+    def train_step_launches(self, with_dx: bool = True, with_dcoef: bool = True) -> int:
+        return int(N.lib().tfx_plan_train_step_mse_launch_count(self._h, int(with_dx), int(with_dcoef)))
+
     def backward(self, x: torch.Tensor, g: torch.Tensor, dx: torch.Tensor | None, dcoef: torch.Tensor | None,
                  saved: torch.Tensor, ws: torch.Tensor | None = None) -> None:
         x2, g2, _ = self._args(x, g, None)

@@ -412,12 +412,13 @@ __device__ __forceinline__ void store_pair(const float2 (&v)[FftShape<LOGM>::PT]
 // store_pair (forward time) with the MSE fused: each output y also gives
 // d = y - t (t the target at the same place) and the gradient gs d (rows
 // t0 / t1 and g0 / g1 laid out like y0 / y1); returns this thread's sum of
-// d^2 (FP32, at most 32 terms).
-template <int LOGM>
-__device__ __forceinline__ float store_pair_mse(const float2 (&v)[FftShape<LOGM>::PT], float* y0, float* y1,
-                                                const float* t0,
-                                                const float* t1, float* g0, float* g1, int64_t b0, int64_t b1,
-                                                int first, int m0, int m1, int t, float gs) {
+// d^2 (FP32, at most 2 PT terms).  KEEP_G: v is left holding the gradient at
+// every output position and zero elsewhere (the block's gradient window,
+// ready for its own transform).
+template <int LOGM, bool KEEP_G = false>
+__device__ __forceinline__ float store_pair_mse(float2 (&v)[FftShape<LOGM>::PT], float* y0, float* y1,
+                                                const float* t0, const float* t1, float* g0, float* g1, int64_t b0,
+                                                int64_t b1, int first, int m0, int m1, int t, float gs) {
     using F = FftShape<LOGM>;
     const int64_t o0 = b0 - first + t, o1 = b1 - first + t;
     float* py0 = y0 + o0;
@@ -441,18 +442,22 @@ __device__ __forceinline__ float store_pair_mse(const float2 (&v)[FftShape<LOGM>
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int o = oo + F::T * (j0 + j);
+            float ga = 0.f, gb = 0.f;
             if ((unsigned)o < (unsigned)m0) {
                 py0[F::T * (j0 + j)] = v[j0 + j].x;
                 const float d = v[j0 + j].x - tv0[j];
-                pg0[F::T * (j0 + j)] = d * gs;
+                ga = d * gs;
+                pg0[F::T * (j0 + j)] = ga;
                 acc = fmaf(d, d, acc);
             }
             if ((unsigned)o < (unsigned)m1) {
                 py1[F::T * (j0 + j)] = v[j0 + j].y;
                 const float d = v[j0 + j].y - tv1[j];
-                pg1[F::T * (j0 + j)] = d * gs;
+                gb = d * gs;
+                pg1[F::T * (j0 + j)] = gb;
                 acc = fmaf(d, d, acc);
             }
+            if constexpr (KEEP_G) v[j0 + j] = make_float2(ga, gb);
         }
     }
     return acc;

@@ -50,19 +50,37 @@ namespace {
 // input and output rows in reverse time (the transposed chain, y = R h R x,
 // for the input gradient of a training step).  MSE: the training loss and
 // its gradient fused into the store (FirFftArgs::loss).
+// Blocks 2pr and 2pr + 1 of the single-block scheme: their channels and
+// first outputs.  Coordinates in 32 bits (the host keeps nb below 2^31): one
+// division for block 2pr; block 2pr + 1 is the next one in its channel or
+// the first of the next channel.
+struct BlockPair {
+    unsigned c0, c1;
+    bool live1;
+    int64_t n00, n01;
+};
+__device__ __forceinline__ BlockPair block_pair(const FirFftArgs& a, int64_t pr) {
+    const unsigned k0 = 2u * (unsigned)pr, nbpc = (unsigned)a.nbpc;
+    BlockPair q;
+    q.live1 = k0 + 1u < (unsigned)a.nb;
+    q.c0 = k0 / nbpc;
+    const unsigned r0 = k0 - q.c0 * nbpc;
+    const bool wrap = r0 + 1u == nbpc;
+    q.c1 = q.live1 && wrap ? q.c0 + 1u : q.c0;
+    const unsigned r1 = q.live1 ? (wrap ? 0u : r0 + 1u) : 0u;
+    q.n00 = (int64_t)r0 * a.B;
+    q.n01 = (int64_t)r1 * a.B;
+    return q;
+}
+
 template <int LOGM, bool REV = false, bool MSE = false>
 __device__ __forceinline__ void fft_block_pair(const FirFftArgs& a, int64_t pr, float2* sb, int t) {
     using F = FftShape<LOGM>;
     const int Hh = a.L - 1;
-    // block coordinates in 32 bits (the host keeps nb below 2^31): one
-    // division for block 2pr; block 2pr + 1 is the next one in its channel
-    // or the first of the next channel
-    const unsigned k0 = 2u * (unsigned)pr, nbpc = (unsigned)a.nbpc;
-    const bool live1 = k0 + 1u < (unsigned)a.nb;
-    const unsigned c0 = k0 / nbpc, r0 = k0 - c0 * nbpc;
-    const bool wrap = r0 + 1u == nbpc;
-    const unsigned c1 = live1 && wrap ? c0 + 1u : c0, r1 = live1 ? (wrap ? 0u : r0 + 1u) : 0u;
-    const int64_t n00 = (int64_t)r0 * a.B, n01 = (int64_t)r1 * a.B;
+    const BlockPair q = block_pair(a, pr);
+    const unsigned c0 = q.c0, c1 = q.c1;
+    const bool live1 = q.live1;
+    const int64_t n00 = q.n00, n01 = q.n01;
     float2 v[F::PT];
     load_pair<LOGM, REV>(v, a.x + c0 * a.ldx, a.x + c1 * a.ldx, live1, n00 - Hh, n01 - Hh, a.N, t);
     forward_from<LOGM, 0>(v, a.tw, sb, t);
@@ -104,6 +122,80 @@ template <int LOGM, bool REV, bool MSE = false>
 __global__ void __launch_bounds__(FftShape<LOGM>::T, FftShape<LOGM>::MINB) k_fir_fft(FirFftArgs a) {
     extern __shared__ float2 sb[];
     fft_block_pair<LOGM, REV, MSE>(a, blockIdx.x, sb, threadIdx.x);
+}
+
+// One training step's forward on the spectral route, with the coefficient
+// gradients' correlation fused in.  Persistent CTAs take block pairs pr =
+// blockIdx.x, + gridDim.x, ...; for each: the forward transform X of the two
+// input windows (kept in shared memory, each thread its own slots), the
+// product with H and the inverse transform, the store of y with the MSE
+// against the target (g = gscale (y - t) stored, the loss summed), then the
+// forward transform G of the two gradient windows (zeros before the
+// outputs, g at them: the registers the store left) and acc += conj(X) G.
+// acc is the sum over the CTA's pairs of the block correlation spectra that
+// k_chain_xcorr computes from x and g in memory (any pairing of two blocks
+// as real and imaginary parts gives the same sum after the mirror step), so
+// the coefficient gradients follow from part[blockIdx.x] unchanged, and x
+// and g are not read again.  The loss: FP32 per thread and pair, FP64
+// across pairs and threads, one FP64 atomic per CTA.
+template <int LOGM>
+__global__ void __launch_bounds__(FftShape<LOGM>::T, LOGM <= 12 ? 2 : 1)
+    k_fir_fft_train(FirFftArgs a, float2* __restrict__ part) {
+    using F = FftShape<LOGM>;
+    static_assert(F::PT == 16, "spectral training transforms: 4096 and 8192 points");
+    extern __shared__ float2 sb[];
+    float2* zx = sb + (F::M + F::M / 16);  // X, each thread its own slots
+    const int t = threadIdx.x;
+    const int Hh = a.L - 1;
+    float2 acc[F::PT];
+#pragma unroll
+    for (int j = 0; j < F::PT; ++j) acc[j] = make_float2(0.f, 0.f);
+    double lsum = 0.0;
+    const int64_t npairs = (a.nb + 1) / 2;
+    for (int64_t pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
+        const BlockPair q = block_pair(a, pr);
+        float2 v[F::PT];
+        __syncthreads();  // the previous pair's last exchange is done with sb
+        load_pair<LOGM>(v, a.x + q.c0 * a.ldx, a.x + q.c1 * a.ldx, q.live1, q.n00 - Hh, q.n01 - Hh, a.N, t);
+        forward_from<LOGM, 0>(v, a.tw, sb, t);
+#pragma unroll
+        for (int j = 0; j < F::PT; ++j) zx[j * F::T + t] = v[j];
+        const float4* h4 = reinterpret_cast<const float4*>(a.H) + t;
+#pragma unroll
+        for (int k = 0; k < F::PT / 2; ++k) {
+            const float4 h = ld_tw4(h4 + k * F::T);
+            v[2 * k] = cmul(v[2 * k], make_float2(h.x, h.y));
+            v[2 * k + 1] = cmul(v[2 * k + 1], make_float2(h.z, h.w));
+        }
+        inverse_from<LOGM, F::NP - 1, last_forward_group<LOGM>()>(v, a.tw, sb, t);
+        const int m0 = (int)(a.N - q.n00 < a.B ? a.N - q.n00 : a.B);
+        const int m1 = q.live1 ? (int)(a.N - q.n01 < a.B ? a.N - q.n01 : a.B) : 0;
+        lsum += (double)store_pair_mse<LOGM, true>(v, a.y + q.c0 * a.ldy, a.y + q.c1 * a.ldy, a.tgt + q.c0 * a.ldy,
+                                                   a.tgt + q.c1 * a.ldy, a.gout + q.c0 * a.ldy,
+                                                   a.gout + q.c1 * a.ldy, q.n00, q.n01, Hh, m0, m1, t, a.gscale);
+        __syncthreads();  // the inverse's last exchange is done with sb
+        forward_from<LOGM, 0>(v, a.tw, sb, t);
+#pragma unroll
+        for (int j = 0; j < F::PT; ++j) {
+            const float2 w = zx[j * F::T + t];
+            acc[j].x = fmaf(v[j].x, w.x, fmaf(v[j].y, w.y, acc[j].x));
+            acc[j].y = fmaf(v[j].y, w.x, fmaf(-v[j].x, w.y, acc[j].y));
+        }
+    }
+    float4* out = reinterpret_cast<float4*>(part + (int64_t)blockIdx.x * F::M) + t;
+#pragma unroll
+    for (int k = 0; k < F::PT / 2; ++k)
+        out[k * F::T] = make_float4(acc[2 * k].x, acc[2 * k].y, acc[2 * k + 1].x, acc[2 * k + 1].y);
+    __shared__ double red[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if ((t & 31) == 0) red[t >> 5] = lsum;
+    __syncthreads();
+    if (t == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < F::T / 32; ++w) sum += red[w];
+        atomicAdd(a.loss, sum * a.lscale);
+    }
 }
 
 // Single-block overlap-save over many clips in one launch (a batch of
@@ -285,6 +377,10 @@ cudaError_t prepare_log() {
         e = cudaFuncSetAttribute(k_fir_fft_spectrum<LOGM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_fir_fft_batched<LOGM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if constexpr (LOGM == 12 || LOGM == 13)
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_fir_fft_train<LOGM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)xcorr_smem_bytes(1 << LOGM));
     return e;
 }
 
@@ -349,6 +445,21 @@ cudaError_t launch_fir_fft(const FirFftArgs& a, cudaStream_t s) {
         case 14: return launch_log<14>(a, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_fir_fft_train(const FirFftArgs& a, float2* part, int grid, cudaStream_t s) {
+    if (a.P != 0 || a.rev || !a.loss || !a.tgt || !a.gout || (a.nb + 1) / 2 > INT32_MAX || grid < 1)
+        return cudaErrorInvalidValue;
+    switch (a.m) {
+        case 12:
+            k_fir_fft_train<12><<<(unsigned)grid, FftShape<12>::T, xcorr_smem_bytes(4096), s>>>(a, part);
+            break;
+        case 13:
+            k_fir_fft_train<13><<<(unsigned)grid, FftShape<13>::T, xcorr_smem_bytes(8192), s>>>(a, part);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace tfx

@@ -1479,8 +1479,13 @@ int spectral_dx(tfx_plan* p, const float* g, float* dx, char* ws, cudaStream_t s
 // the raw rows (the a0 chain rule) in one launch.  Input gradient: the chain
 // applied to g in reverse time (its transpose), by the forward's kernel with
 // reversed rows, after the correlation (which reads g) when dx is g.
-int run_backward_spectral(tfx_plan* p, const float* x, const float* g, float* dx, double* dcoef, char* ws,
-                          cudaStream_t s, bool count_only, int* nlaunch) {
+// The backward of a spectral plan after the correlation partials are in
+// the workspace (ws + b_sp_part, p->spec_grid rows): dL/dx on the side
+// stream (it only needs g), the partials' sum P, the derivative spectra's
+// section and FIR-tap gradients, the a0 chain rule; the caller's stream
+// waits for dL/dx at the end.
+int spectral_grads_from_partials(tfx_plan* p, const float* g, float* dx, double* dcoef, char* ws, cudaStream_t s,
+                                 bool count_only, int* nlaunch) {
     int nl = 0;
 #define TFX_LAUNCH(call)                                               \
     do {                                                               \
@@ -1488,11 +1493,43 @@ int run_backward_spectral(tfx_plan* p, const float* x, const float* g, float* dx
         if (!count_only && (call) != cudaSuccess) return TFX_ERR_CUDA; \
     } while (0)
     const HostUnit& c = p->chain;
-    const int m = c.fft_m, M = c.fft_M, J = c.L - 1;
+    const int m = c.fft_m, M = c.fft_M;
     const float2* tw = reinterpret_cast<const float2*>(p->dconst + c.off_tw);
+    double2* P = reinterpret_cast<double2*>(ws + p->b_sp_P);
+    float2* part = reinterpret_cast<float2*>(ws + p->b_sp_part);
+    if (dx) {
+        // dx only needs g (complete by now): it runs on the side stream
+        // beside the small gradient kernels below
+        if (!count_only && (cudaEventRecord(p->ev_fork, s) != cudaSuccess ||
+                            cudaStreamWaitEvent(p->side, p->ev_fork, 0) != cudaSuccess))
+            return TFX_ERR_CUDA;
+        const int rc = spectral_dx(p, g, dx, ws, p->side, count_only, &nl);
+        if (rc != TFX_OK) return rc;
+        if (!count_only && cudaEventRecord(p->ev_join, p->side) != cudaSuccess) return TFX_ERR_CUDA;
+    }
+    TFX_LAUNCH(launch_xcorr_reduce(part, p->spec_grid, M, P, s));
+    const double* raw = reinterpret_cast<const double*>(p->dconst + p->off_spec_raw);
+    nl += p->spec_nfir ? 2 : 1;
+    if (!count_only &&
+        launch_chain_grads(m, P, raw, p->chain_S, reinterpret_cast<const float2*>(p->dconst + p->spec_fir.off_H),
+                           reinterpret_cast<const double2*>(p->dconst + p->off_spec_z), tw, p->spec_fir.L,
+                           ws + p->b_sp_gs, reinterpret_cast<float2*>(ws + p->b_sp_w),
+                           p->spec_nfir ? dcoef + p->spec_fir_dst : nullptr, s) != cudaSuccess)
+        return TFX_ERR_CUDA;
+    TFX_LAUNCH(launch_spectral_finalize(m, ws + p->b_sp_gs, p->chain_S, raw,
+                                        reinterpret_cast<const int64_t*>(p->dconst + p->off_spec_dst), dcoef, s));
+    // join: the caller's stream continues once the input gradient is done
+    if (dx && !count_only && cudaStreamWaitEvent(s, p->ev_join, 0) != cudaSuccess) return TFX_ERR_CUDA;
+#undef TFX_LAUNCH
+    if (nlaunch) *nlaunch += nl;
+    return TFX_OK;
+}
+
+int run_backward_spectral(tfx_plan* p, const float* x, const float* g, float* dx, double* dcoef, char* ws,
+                          cudaStream_t s, bool count_only, int* nlaunch) {
+    int nl = 0;
+    const HostUnit& c = p->chain;
     if (dcoef) {
-        double2* P = reinterpret_cast<double2*>(ws + p->b_sp_P);
-        float2* part = reinterpret_cast<float2*>(ws + p->b_sp_part);
         XcorrArgs a{};
         a.x = x;
         a.g = g;
@@ -1500,42 +1537,21 @@ int run_backward_spectral(tfx_plan* p, const float* x, const float* g, float* dx
         a.ldg = p->ld;
         a.C = p->C;
         a.N = p->N;
-        a.J = J;
+        a.J = c.L - 1;
         a.B = c.fft_B;
         a.nbpc = c.ntt;
         a.items = (p->C + 1) / 2 * c.ntt;
-        a.tw = tw;
-        a.part = part;
-        TFX_LAUNCH(launch_chain_xcorr(m, a, p->spec_grid, s));
-        if (dx) {
-            // dx only needs g (which the correlation has read by now): it runs
-            // on the side stream beside the small gradient kernels below
-            if (!count_only && (cudaEventRecord(p->ev_fork, s) != cudaSuccess ||
-                                cudaStreamWaitEvent(p->side, p->ev_fork, 0) != cudaSuccess))
-                return TFX_ERR_CUDA;
-            const int rc = spectral_dx(p, g, dx, ws, p->side, count_only, &nl);
-            if (rc != TFX_OK) return rc;
-            if (!count_only && cudaEventRecord(p->ev_join, p->side) != cudaSuccess) return TFX_ERR_CUDA;
-        }
-        TFX_LAUNCH(launch_xcorr_reduce(part, p->spec_grid, M, P, s));
-        const double* raw = reinterpret_cast<const double*>(p->dconst + p->off_spec_raw);
-        nl += p->spec_nfir ? 2 : 1;
-        if (!count_only &&
-            launch_chain_grads(m, P, raw, p->chain_S, reinterpret_cast<const float2*>(p->dconst + p->spec_fir.off_H),
-                               reinterpret_cast<const double2*>(p->dconst + p->off_spec_z),
-                               tw, p->spec_fir.L, ws + p->b_sp_gs, reinterpret_cast<float2*>(ws + p->b_sp_w),
-                               p->spec_nfir ? dcoef + p->spec_fir_dst : nullptr, s) != cudaSuccess)
-            return TFX_ERR_CUDA;
-        TFX_LAUNCH(launch_spectral_finalize(m, ws + p->b_sp_gs, p->chain_S, raw,
-                                            reinterpret_cast<const int64_t*>(p->dconst + p->off_spec_dst), dcoef, s));
-        // join: the caller's stream continues once the input gradient is done
-        if (dx && !count_only && cudaStreamWaitEvent(s, p->ev_join, 0) != cudaSuccess) return TFX_ERR_CUDA;
+        a.tw = reinterpret_cast<const float2*>(p->dconst + c.off_tw);
+        a.part = reinterpret_cast<float2*>(ws + p->b_sp_part);
+        ++nl;
+        if (!count_only && launch_chain_xcorr(c.fft_m, a, p->spec_grid, s) != cudaSuccess) return TFX_ERR_CUDA;
+        const int rc = spectral_grads_from_partials(p, g, dx, dcoef, ws, s, count_only, &nl);
+        if (rc != TFX_OK) return rc;
     }
     if (dx && !dcoef) {
         const int rc = spectral_dx(p, g, dx, ws, s, count_only, &nl);
         if (rc != TFX_OK) return rc;
     }
-#undef TFX_LAUNCH
     if (nlaunch) *nlaunch = nl;
     return TFX_OK;
 }
@@ -2014,6 +2030,79 @@ int tfx_plan_backward_launch_count(const tfx_plan* p, int with_dx, int with_dcoe
     double dummy_dc;
     run_backward(const_cast<tfx_plan*>(p), nullptr, nullptr, with_dx ? &dummy_dx : nullptr,
                  with_dcoef ? &dummy_dc : nullptr, nullptr, nullptr, nullptr, true, &n);
+    return n;
+}
+
+int tfx_plan_train_step_mse(tfx_plan* p, const float* x, float* y, const float* target, float* g, double* loss,
+                            float* dx, double* dcoef, void* saved, size_t saved_bytes, void* ws, size_t ws_bytes,
+                            tfx_stream s) {
+    if (!p || !p->train || !loss) return TFX_ERR_INVALID;
+    const bool fused = p->spectral && dcoef && p->C > 0 && p->N > 0;
+    if (!fused) {  // the two calls in order (each validates its own arguments)
+        const int rc = tfx_plan_forward_train_mse(p, x, y, target, g, loss, saved, saved_bytes, ws, ws_bytes, s);
+        if (rc != TFX_OK || (!dx && !dcoef)) return rc;
+        return tfx_plan_backward(p, x, g, dx, dcoef, saved, saved_bytes, ws, ws_bytes, s);
+    }
+    // the arguments of both calls, checked before anything is enqueued
+    const size_t need = std::max(p->ws_fused, p->bws_bytes);
+    int rc = check_exec_args(p, x, y, ws, ws_bytes, need);
+    if (rc != TFX_OK) return rc;
+    if (x == y || !target || !g) return TFX_ERR_INVALID;
+    const int64_t C = p->C, N = p->N;
+    const size_t span = signal_span(C, N, p->ld);
+    if (bytes_overlap(g, span, x, span) || bytes_overlap(g, span, y, span) ||
+        (g != target && bytes_overlap(g, span, target, span)) || bytes_overlap(target, span, y, span) ||
+        bytes_overlap(loss, sizeof(double), g, span) || bytes_overlap(loss, sizeof(double), y, span))
+        return TFX_ERR_INVALID;
+    if (dx && (ranges_overlap_not_equal(g, dx, C, N, p->ld) || bytes_overlap(x, span, dx, span)))
+        return TFX_ERR_INVALID;
+    if (bytes_overlap(dcoef, (size_t)p->ncoef * sizeof(double), g, span) ||
+        bytes_overlap(dcoef, (size_t)p->ncoef * sizeof(double), y, span) ||
+        bytes_overlap(loss, sizeof(double), dcoef, (size_t)p->ncoef * sizeof(double)))
+        return TFX_ERR_INVALID;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+    const HostUnit& c = p->chain;
+    const double inv = 1.0 / ((double)C * (double)N);
+    if (cudaMemsetAsync(loss, 0, sizeof(double), st) != cudaSuccess) return TFX_ERR_CUDA;
+    FirFftArgs f{};
+    f.x = x;
+    f.ldx = p->ld;
+    f.y = y;
+    f.ldy = p->ld;
+    f.C = C;
+    f.N = N;
+    f.L = c.L;
+    f.M = c.fft_M;
+    f.m = c.fft_m;
+    f.B = c.fft_B;
+    f.P = 0;
+    f.nbpc = c.ntt;
+    f.nb = C * c.ntt;
+    f.H = reinterpret_cast<const float2*>(p->dconst + c.off_H);
+    f.tw = reinterpret_cast<const float2*>(p->dconst + c.off_tw);
+    f.tgt = target;
+    f.gout = g;
+    f.loss = loss;
+    f.gscale = (float)(2.0 * inv);
+    f.lscale = inv;
+    char* w = static_cast<char*>(ws);
+    if (launch_fir_fft_train(f, reinterpret_cast<float2*>(w + p->b_sp_part), p->spec_grid, st) != cudaSuccess)
+        return TFX_ERR_CUDA;
+    return spectral_grads_from_partials(p, g, dx, dcoef, w, st, false, nullptr);
+}
+
+int tfx_plan_train_step_mse_launch_count(const tfx_plan* p, int with_dx, int with_dcoef) {
+    if (!p || !p->train) return -1;
+    if (p->C == 0 || p->N == 0) return 0;
+    if (!(p->spectral && with_dcoef)) {
+        const int b = (with_dx || with_dcoef) ? tfx_plan_backward_launch_count(p, with_dx, with_dcoef) : 0;
+        return tfx_plan_forward_train_mse_launch_count(p) + b;
+    }
+    int n = 1;
+    float dummy_dx;
+    double dummy_dc;
+    spectral_grads_from_partials(const_cast<tfx_plan*>(p), nullptr, with_dx ? &dummy_dx : nullptr, &dummy_dc, nullptr,
+                                 nullptr, true, &n);
     return n;
 }
 

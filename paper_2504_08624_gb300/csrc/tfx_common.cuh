@@ -409,6 +409,9 @@ cudaError_t launch_fir_tc(const FirTcArgs& a, cudaStream_t s);
 size_t fir_fft_smem_bytes(int M);
 cudaError_t prepare_fir_fft(int M);
 cudaError_t launch_fir_fft(const FirFftArgs& a, cudaStream_t s);
+// spectral training step: forward + MSE + the correlation partials, one CTA
+// per part[] row (k_fir_fft_train)
+cudaError_t launch_fir_fft_train(const FirFftArgs& a, float2* part, int grid, cudaStream_t s);
 size_t xcorr_smem_bytes(int M);
 int xcorr_ctas_per_sm(int m);
 cudaError_t prepare_spectral(int m);

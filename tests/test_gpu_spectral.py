@@ -288,6 +288,71 @@ def test_forward_train_mse_fused(route):
     p.close()
 
 
+@pytest.mark.parametrize("case", ["differentiable_chain", "odd_blocks", "8192_points", "units"])
+def test_train_step_mse(case):
+    """tfx_plan_train_step_mse against tfx_plan_forward_train_mse followed by
+    tfx_plan_backward on the same inputs: y, g and dL/dx bit for bit, the
+    loss to FP64 summation order, the coefficient gradients to FP32 rounding
+    (the fused correlation pairs other blocks as real and imaginary parts)
+    and against the oracle's vector-Jacobian product of the step's own g;
+    dx taking g's place and no dx give the same gradients; the launch count.
+    odd_blocks: an odd number of blocks in all (the last pair has no second
+    block) and pairs that straddle two channels.  units: a plan kept on its
+    units runs the two calls in order."""
+    from paper_2504_08624_gb300 import _native
+    if case == "8192_points":
+        stages = [("sos", W.random_stable_sos(4, 82, 0.9, 0.99)), ("fir", W.fir_lowpass(1025, 3000.0, W.FS))]
+        C, N = 3, 30000
+    else:
+        stages = chain("differentiable_chain")
+        C, N = {"differentiable_chain": (4, 20000), "odd_blocks": (5, 12345), "units": (4, 9000)}[case]
+    p = plan(C, N, stages, _native.TFX_PLAN_NO_COMPOSE if case == "units" else 0)
+    d = p.describe()[0]
+    spectral = d["kind"] == "chain_spectral"
+    assert spectral == (case != "units"), d
+    if case == "odd_blocks":
+        assert (C * -(-N // d["B"])) % 2 == 1, d
+    xn, tn = W.white_gauss(C, N, 90), W.white_gauss(C, N, 91)
+    x = torch.from_numpy(xn.astype(np.float32)).cuda()
+    tgt = torch.from_numpy(tn.astype(np.float32)).cuda()
+
+    def scalar():
+        return torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+
+    def coefs():
+        return torch.full((p.coef_count,), float("nan"), dtype=torch.float64, device="cuda")
+
+    y1, g1, dx1, l1, dc1 = torch.empty_like(x), torch.empty_like(x), torch.empty_like(x), scalar(), coefs()
+    s1 = p.new_saved()
+    p.forward_train_mse(x, y1, tgt, g1, l1, s1)
+    p.backward(x, g1, dx1, dc1, s1)
+    y2, g2, dx2 = (torch.full_like(x, float("nan")) for _ in range(3))
+    l2, dc2 = scalar(), coefs()
+    p.train_step_mse(x, y2, tgt, g2, l2, dx2, dc2, p.new_saved())
+    y3, g3, l3, dc3 = torch.empty_like(x), torch.empty_like(x), scalar(), coefs()
+    p.train_step_mse(x, y3, tgt, g3, l3, g3, dc3, p.new_saved())  # dL/dx in g's place
+    y4, g4, l4, dc4 = torch.empty_like(x), torch.empty_like(x), scalar(), coefs()
+    p.train_step_mse(x, y4, tgt, g4, l4, None, dc4, p.new_saved())
+    torch.cuda.synchronize()
+    assert p.get_error() == 0
+    assert torch.equal(y1, y2) and torch.equal(g1, g2) and torch.equal(dx1, dx2)
+    assert torch.equal(y1, y3) and torch.equal(dx1, g3) and torch.equal(y1, y4) and torch.equal(g1, g4)
+    for l in (l2, l3, l4):
+        assert abs(float(l) - float(l1)) <= 1e-9 * abs(float(l1))
+    assert torch.equal(dc2, dc3) and torch.equal(dc2, dc4)
+    a, b = dc1.cpu().numpy(), dc2.cpu().numpy()
+    for (kind, _), u, v in zip(stages, split(a, stages), split(b, stages)):
+        assert np.max(np.abs(u - v)) <= 1e-5 * np.max(np.abs(u)), kind
+    lib = oracle.load()
+    dx_ref, gref = lib.chain_vjp(xn, g1.cpu().numpy().astype(np.float64), stages)
+    assert_close(dx2.cpu().numpy().astype(np.float64), dx_ref, 1e-4, "dL/dx")
+    worst = check_coefs(split(b, stages), gref, stages)
+    n_two = p.forward_train_mse_launches + p.backward_launches(True, True)
+    assert p.train_step_launches(True, True) == (n_two - 1 if spectral else n_two)
+    print(f"train step {case}: {d}, coefficient gradients {worst:.2e} of the stage's largest (oracle)")
+    p.close()
+
+
 def test_spectral_8192_points():
     """A chain whose response needs an overlap beyond 3072 samples takes the
     8192-point transforms (the correlation, tap-gradient and decay-check
