@@ -90,12 +90,12 @@ typedef struct {
  * all leading transient); the flag forces it for any length, and keeps it when TFX_PLAN_FIR_TC,
  * _FIR_BF16_PLAIN or _FIR_BF16_SPLIT is set too, and FIR stages on CUDA cores
  * (TFX_PLAN_FIR_CUDA_CORES) never take it.  Hand-written register-resident
- * radix-16 FFTs of
- * M = 1024..16384 points (FP32; the error is ~log2(M) eps of each block's
- * energy rather than per product).  Up to 12289 taps: blocks of
- * B = M - (L - 1) outputs, two blocks per complex transform (16384 points
- * only in this single-block form).  Longer:
- * partitioned overlap-save, h cut into P = ceil(L / (M/2)) partitions, every
+ * radix-16 FFTs of M = 1024..16384 points (16 points per thread; 32 with
+ * radix-32 passes at 16384; FP32, the error is ~log2(M) eps of each block's
+ * energy rather than per product).  Single-block (up to 12289 taps): blocks
+ * of B = M - (L - 1) outputs, two blocks per complex transform.
+ * Partitioned (any length, where the model finds it cheaper):
+ * overlap-save with h cut into P = ceil(L / (M/2)) partitions, every
  * input segment transformed once (two channels per complex transform) into a
  * workspace of ceil(C/2) x ceil(N / (M/2)) x M complex values, and each output
  * block the inverse transform of the sum of the P partition products (two
