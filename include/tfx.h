@@ -458,8 +458,10 @@ int tfx_sos_noalloc(const float *x, float *y, int64_t C, int64_t N, int64_t ld,
  * transform size run as ONE launch (each CTA finds its clip by binary
  * search and uses the clip's own spectrum).  The units of the other clips
  * are grouped by position in their chain and by kernel (fused cascade +
- * short FIR / cascade / tensor-core FIR with NB output blocks per tile);
- * each group runs as ONE launch over the tiles of all its units.
+ * short FIR / cascade / FIR of 64+ taps by single-block FFT per transform
+ * size / tensor-core FIR with NB output blocks per tile, for a FIR one FFT
+ * block cannot hold); each group runs as ONE launch over the tiles of all
+ * its units.
  * TFX_PLAN_NO_COMPOSE in plan_flags keeps every clip on the grouped units.
  * Allocates device memory (host-synchronous).
  * params may be NULL (defaults).  Clips whose tensor-core FIR tables do not
@@ -481,10 +483,12 @@ typedef struct {
 
 typedef struct {
     uint32_t plan_flags;   /* TFX_PLAN_* for every clip (TFX_PLAN_DEFAULT, _NO_COMPOSE, _FIR_CUDA_CORES,
-                              _FIR_BF16_*); long FIRs of clips that do not compose stay on the tensor
-                              cores (_FIR_FFT is rejected) */
+                              _FIR_BF16_*); FIRs of clips that do not compose run by single-block FFT
+                              where one block holds the taps, else on the tensor cores (_FIR_FFT is
+                              rejected) */
     int32_t fir_nb;        /* tensor-core FIR output blocks of 128 per tile: 64, 128 or 256 (0: 128) */
-    int32_t tc_min_taps;   /* FIRs with at least this many taps use the tensor cores (0: 64) */
+    int32_t tc_min_taps;   /* FIRs not on the FFT with at least this many taps use the tensor
+                              cores (0: 64) */
     int32_t fft_m[16];     /* composed clips whose composite response has Lc taps with
                               floor(log2(Lc)) = k run with transforms of 2^fft_m[k] points
                               (10..14; 0, or a size that cannot hold Lc - 1 taps with M/4
