@@ -56,8 +56,8 @@ def test_max_over_ranks_single_process():
 
 
 def test_reference_arm_under_torchrun():
-    """`bench.py --impl reference` launched as the driver launches it for
-    N = 2: one JSON line (from rank 0), both ranks exit 0."""
+    """`bench.py --impl reference` launched under torchrun with two ranks
+    (the multi-GPU launch): one JSON line (from rank 0), both ranks exit 0."""
     port = _free_port()
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py", "--impl", "reference",
