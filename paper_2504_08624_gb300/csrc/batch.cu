@@ -40,6 +40,7 @@ struct Group {
     double flops = 0.0;   // algorithmic: 10 per section-sample, 2 L per FIR sample
     size_t smem = 0;
     size_t desc_off = 0, prefix_off = 0;  // in the batch's device descriptor blob
+    size_t map_off = 0;                   // FFT groups: the unit of every CTA (int32)
     size_t hdr_off = 0, hdr_bytes = 0;    // workspace: ticket + flags + carries (zeroed per execution)
     std::vector<BatchUnit> units;
     std::vector<BatchFir> firs;
@@ -350,11 +351,16 @@ int batch_build(tfx_batch* b, const tfx_clip* clips, int32_t n, const tfx_batch_
                : gr.kind == G_CHAIN_FFT || gr.kind == G_FFT ? gr.ffts.size() * sizeof(BatchFft)
                                                             : gr.units.size() * sizeof(BatchUnit);
     };
+    auto is_fft = [](const Group& gr) { return gr.kind == G_CHAIN_FFT || gr.kind == G_FFT; };
     for (Group& gr : b->groups) {
         gr.desc_off = blob;
         blob = align_up(blob + desc_bytes(gr));
         gr.prefix_off = blob;
         blob = align_up(blob + gr.prefix.size() * sizeof(int64_t));
+        if (is_fft(gr)) {
+            gr.map_off = blob;
+            blob = align_up(blob + (size_t)gr.tiles * sizeof(int32_t));
+        }
     }
     if (blob > 0) {
         std::vector<char> host(blob, 0);
@@ -366,6 +372,11 @@ int batch_build(tfx_batch* b, const tfx_clip* clips, int32_t n, const tfx_batch_
             else
                 std::memcpy(host.data() + gr.desc_off, gr.units.data(), gr.units.size() * sizeof(BatchUnit));
             std::memcpy(host.data() + gr.prefix_off, gr.prefix.data(), gr.prefix.size() * sizeof(int64_t));
+            if (is_fft(gr)) {
+                int32_t* map = reinterpret_cast<int32_t*>(host.data() + gr.map_off);
+                for (int u = 0; u < gr.nunits; ++u)
+                    for (int64_t k = gr.prefix[u]; k < gr.prefix[u + 1]; ++k) map[k] = u;
+            }
         }
         if (cudaMalloc(&b->ddesc, blob) != cudaSuccess) return TFX_ERR_NOMEM;
         if (cudaMemcpy(b->ddesc, host.data(), blob, cudaMemcpyHostToDevice) != cudaSuccess) return TFX_ERR_CUDA;
@@ -377,7 +388,8 @@ int run_group(tfx_batch* b, const Group& gr, const BatchBases& bases, char* w, c
     const int64_t* prefix = reinterpret_cast<const int64_t*>(b->ddesc + gr.prefix_off);
     if (gr.kind == G_CHAIN_FFT || gr.kind == G_FFT)
         return launch_fir_fft_batched(gr.fft_m, reinterpret_cast<const BatchFft*>(b->ddesc + gr.desc_off), prefix,
-                                      gr.nunits, gr.tiles, bases, gr.tw, s) == cudaSuccess
+                                      reinterpret_cast<const int32_t*>(b->ddesc + gr.map_off), gr.nunits, gr.tiles,
+                                      bases, gr.tw, s) == cudaSuccess
                    ? TFX_OK
                    : TFX_ERR_CUDA;
     if (gr.kind == G_FIR)

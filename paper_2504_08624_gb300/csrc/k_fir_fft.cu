@@ -201,26 +201,17 @@ __global__ void __launch_bounds__(FftShape<LOGM>::T, LOGM <= 12 ? 2 : 1)
 // Single-block overlap-save over many clips in one launch (a batch of
 // composed chains sharing one transform size): CTA k maps to its clip by a
 // binary search over the clips' block-pair prefix sums, then transforms that
-// clip's block pair k - prefix[clip] with the clip's own spectrum.
+// clip's block pair k - prefix[clip] with the clip's own spectrum.  The
+// clip of every CTA is precomputed on the host (unit_of[k], one load
+// instead of a serial binary search over the prefix sums).
 template <int LOGM>
 __global__ void __launch_bounds__(FftShape<LOGM>::T, FftShape<LOGM>::MINB)
-    k_fir_fft_batched(const BatchFft* __restrict__ units, const int64_t* __restrict__ prefix, int nunits,
-                      BatchBases bases, const float2* __restrict__ tw) {
+    k_fir_fft_batched(const BatchFft* __restrict__ units, const int64_t* __restrict__ prefix,
+                      const int32_t* __restrict__ unit_of, BatchBases bases, const float2* __restrict__ tw) {
     extern __shared__ float2 sb[];
-    __shared__ int s_unit;
     const int t = threadIdx.x;
     const int64_t k = blockIdx.x;
-    if (t == 0) {
-        int lo = 0, hi = nunits - 1;  // the last unit whose first pair is <= k
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) / 2;
-            if (prefix[mid] <= k) lo = mid;
-            else hi = mid - 1;
-        }
-        s_unit = lo;
-    }
-    __syncthreads();
-    const int u = s_unit;
+    const int u = __ldg(unit_of + k);
     const BatchFft d = units[u];
     FirFftArgs a{};
     a.x = bases.ptr(d.x_sel) + d.x_off;
@@ -400,23 +391,23 @@ cudaError_t prepare_fir_fft(int M) {
 }
 
 template <int LOGM>
-cudaError_t launch_batched_log(const BatchFft* units, const int64_t* prefix, int nunits, int64_t ctas,
+cudaError_t launch_batched_log(const BatchFft* units, const int64_t* prefix, const int32_t* unit_of, int64_t ctas,
                                BatchBases bases, const float2* tw, cudaStream_t s) {
     constexpr int T = FftShape<LOGM>::T;
     const size_t smem = fir_fft_smem_bytes(1 << LOGM);
-    k_fir_fft_batched<LOGM><<<(unsigned)ctas, T, smem, s>>>(units, prefix, nunits, bases, tw);
+    k_fir_fft_batched<LOGM><<<(unsigned)ctas, T, smem, s>>>(units, prefix, unit_of, bases, tw);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fir_fft_batched(int m, const BatchFft* units, const int64_t* prefix, int nunits, int64_t ctas,
-                                   BatchBases bases, const float2* tw, cudaStream_t s) {
+cudaError_t launch_fir_fft_batched(int m, const BatchFft* units, const int64_t* prefix, const int32_t* unit_of,
+                                   int nunits, int64_t ctas, BatchBases bases, const float2* tw, cudaStream_t s) {
     if (ctas <= 0 || nunits <= 0) return cudaSuccess;
     switch (m) {
-        case 10: return launch_batched_log<10>(units, prefix, nunits, ctas, bases, tw, s);
-        case 11: return launch_batched_log<11>(units, prefix, nunits, ctas, bases, tw, s);
-        case 12: return launch_batched_log<12>(units, prefix, nunits, ctas, bases, tw, s);
-        case 13: return launch_batched_log<13>(units, prefix, nunits, ctas, bases, tw, s);
-        case 14: return launch_batched_log<14>(units, prefix, nunits, ctas, bases, tw, s);
+        case 10: return launch_batched_log<10>(units, prefix, unit_of, ctas, bases, tw, s);
+        case 11: return launch_batched_log<11>(units, prefix, unit_of, ctas, bases, tw, s);
+        case 12: return launch_batched_log<12>(units, prefix, unit_of, ctas, bases, tw, s);
+        case 13: return launch_batched_log<13>(units, prefix, unit_of, ctas, bases, tw, s);
+        case 14: return launch_batched_log<14>(units, prefix, unit_of, ctas, bases, tw, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -430,8 +430,8 @@ cudaError_t launch_chain_grads(int m, const double2* P, const double* raw, int S
                                cudaStream_t s);
 cudaError_t launch_spectral_finalize(int m, const void* scratch, int S, const double* raw, const int64_t* dst,
                                      double* dcoef, cudaStream_t s);
-cudaError_t launch_fir_fft_batched(int m, const BatchFft* units, const int64_t* prefix, int nunits, int64_t ctas,
-                                   BatchBases bases, const float2* tw, cudaStream_t s);
+cudaError_t launch_fir_fft_batched(int m, const BatchFft* units, const int64_t* prefix, const int32_t* unit_of,
+                                   int nunits, int64_t ctas, BatchBases bases, const float2* tw, cudaStream_t s);
 cudaError_t launch_fir_fft_spectrum(const double* taps, int L, int M, int B, int P, const float2* tw, float2* H,
                                     cudaStream_t s);
 cudaError_t launch_fir_tc_batched(const BatchFir* units, const int64_t* prefix, int nunits, int64_t tiles,
