@@ -455,8 +455,8 @@ int tfx_sos_noalloc(const float *x, float *y, int64_t C, int64_t N, int64_t ld,
  * tfx_plan_create).  A clip whose chain composes into one FIR (its cascades'
  * impulse response decays: the composite-response reading of
  * TFX_PLAN_NO_COMPOSE) runs by FFT overlap-save, and all such clips of one
- * transform size run as ONE launch (each CTA finds its clip by binary
- * search and uses the clip's own spectrum).  The units of the other clips
+ * transform size run as ONE launch (each CTA reads its clip from a per-CTA
+ * table built with the batch and uses the clip's own spectrum).  The units of the other clips
  * are grouped by position in their chain and by kernel (fused cascade +
  * short FIR / cascade / FIR of 64+ taps by single-block FFT per transform
  * size / tensor-core FIR with NB output blocks per tile, for a FIR one FFT

@@ -11,9 +11,9 @@
 // chain (level) and by kernel (fused cascade + short FIR, cascade only,
 // FFT FIR by transform size, tensor-core FIR for FIRs a single FFT block
 // cannot hold) and runs every group as ONE launch whose tiles span all of
-// its units.  In either kind of launch a CTA maps its ticket (or block index)
-// to a unit by binary search over the units' tile prefix sums, so each
-// unit's tiles keep their time-major order.  Buffer
+// its units.  A CTA maps its ticket to a unit by binary search over the
+// units' tile prefix sums (an FFT launch's CTA reads its unit from a per-CTA
+// table built here), so each unit's tiles keep their time-major order.  Buffer
 // pointers in the descriptors are offsets into the packed input, the packed
 // output or the workspace, so an execution is pure pointer arithmetic on
 // three base addresses: no allocation, no host synchronisation, capturable
